@@ -1,0 +1,281 @@
+"""Seeded synthetic inputs: simplicial meshes, displacements and vertex densities.
+
+This module only SYNTHESISES inputs. It holds none of the projection arithmetic and is shared by
+the CUDA path's tests/benchmark and by the CPU oracle's tests, so both always see the same data.
+
+The meshes follow the structure of the paper's runs (Sect. 4.1, initial conditions): a regular
+simplicial tessellation of the Lagrangian (u = 0) sheet of a periodic box, whose vertices are then
+moved by a smooth displacement field, with a per-vertex density.
+
+* 3D: every Lagrangian cube is split into 6 tetrahedra (Kuhn/Freudenthal split: for each
+  permutation pi of the axes, {c, c+e_pi1, c+e_pi1+e_pi2, c+(1,1,1)}); it is translation
+  invariant, hence conforming on the torus.
+* 2D: every Lagrangian square is split along its (0,0)-(1,1) diagonal into 2 triangles.
+* Displacements: two orthogonal sine waves (the paper's 2-sine test, Sect. 5.1), or a seeded
+  curl-free Gaussian random field psi = grad(phi) whose power spectrum is proportional to k^-2
+  for 0 < |k| <= kmax (k in units of the fundamental mode), scaled to a stated rms.
+* Densities: uniform, or lognormal rho = exp(sigma * z), z ~ N(0, 1).
+
+All random numbers come from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import math
+
+import numpy as np
+
+__all__ = [
+    "Mesh",
+    "kuhn_mesh_3d",
+    "kuhn_box_mesh_3d",
+    "square_box_mesh_2d",
+    "square_mesh_2d",
+    "sine_displacement_2d",
+    "grf_displacement",
+    "lognormal_density",
+    "make_config",
+    "random_simplices",
+    "CONFIG_NAMES",
+]
+
+
+@dataclasses.dataclass
+class Mesh:
+    """One projection problem: a simplicial mesh with per-vertex density and a target grid.
+
+    pos       : float64 [D, Nv]  vertex positions (world units), SoA
+    simplices : int32   [Ns, D+1] vertex indices per simplex
+    rho       : float64 [Nv]     per-vertex density
+    grid      : tuple of D ints  cells per axis (axis 0 slowest in the output array)
+    box_lo    : tuple of D floats
+    box_len   : tuple of D floats
+    periodic  : bool
+    """
+
+    pos: np.ndarray
+    simplices: np.ndarray
+    rho: np.ndarray
+    grid: tuple
+    box_lo: tuple
+    box_len: tuple
+    periodic: bool = True
+    name: str = ""
+
+    @property
+    def dim(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def n_verts(self) -> int:
+        return int(self.pos.shape[1])
+
+    @property
+    def n_simplices(self) -> int:
+        return int(self.simplices.shape[0])
+
+    def subset(self, idx) -> "Mesh":
+        """Same vertices, only the simplices listed in ``idx``."""
+        return dataclasses.replace(self, simplices=np.ascontiguousarray(self.simplices[idx]))
+
+
+# --------------------------------------------------------------------------------------------
+# Tessellations of the periodic Lagrangian lattice
+# --------------------------------------------------------------------------------------------
+
+def kuhn_mesh_3d(n: int):
+    """Periodic n^3 lattice, 6 tetrahedra per cube. Returns (q [3, n^3] in [0,1), tets [6n^3, 4])."""
+    idx = np.arange(n, dtype=np.int64)
+    i, j, k = np.meshgrid(idx, idx, idx, indexing="ij")
+    q = np.stack([i.ravel(), j.ravel(), k.ravel()]).astype(np.float64) / n
+
+    def vid(a, b, c):
+        return ((a % n) * n + (b % n)) * n + (c % n)
+
+    ci, cj, ck = i.ravel(), j.ravel(), k.ravel()
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        off = np.zeros(3, dtype=np.int64)
+        verts = [vid(ci, cj, ck)]
+        for ax in perm[:2]:
+            off[ax] += 1
+            verts.append(vid(ci + off[0], cj + off[1], ck + off[2]))
+        verts.append(vid(ci + 1, cj + 1, ck + 1))
+        tets.append(np.stack(verts, axis=1))
+    # cube-major order: the 6 tetrahedra of one cube are adjacent in memory
+    tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return q, tets
+
+
+def kuhn_box_mesh_3d(n: int):
+    """Non-periodic n^3 cubes over [0,1]^3 ((n+1)^3 vertices), 6 tetrahedra per cube."""
+    m = n + 1
+    idx = np.arange(m, dtype=np.int64)
+    i, j, k = np.meshgrid(idx, idx, idx, indexing="ij")
+    q = np.stack([i.ravel(), j.ravel(), k.ravel()]).astype(np.float64) / n
+    c = np.arange(n, dtype=np.int64)
+    ci, cj, ck = (a.ravel() for a in np.meshgrid(c, c, c, indexing="ij"))
+
+    def vid(a, b, cc):
+        return (a * m + b) * m + cc
+
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        off = np.zeros(3, dtype=np.int64)
+        verts = [vid(ci, cj, ck)]
+        for ax in perm[:2]:
+            off[ax] += 1
+            verts.append(vid(ci + off[0], cj + off[1], ck + off[2]))
+        verts.append(vid(ci + 1, cj + 1, ck + 1))
+        tets.append(np.stack(verts, axis=1))
+    return q, np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+
+
+def square_box_mesh_2d(n: int):
+    """Non-periodic n^2 squares over [0,1]^2 ((n+1)^2 vertices), 2 triangles per square."""
+    m = n + 1
+    idx = np.arange(m, dtype=np.int64)
+    i, j = np.meshgrid(idx, idx, indexing="ij")
+    q = np.stack([i.ravel(), j.ravel()]).astype(np.float64) / n
+    c = np.arange(n, dtype=np.int64)
+    ci, cj = (a.ravel() for a in np.meshgrid(c, c, indexing="ij"))
+
+    def vid(a, b):
+        return a * m + b
+
+    t0 = np.stack([vid(ci, cj), vid(ci + 1, cj), vid(ci + 1, cj + 1)], axis=1)
+    t1 = np.stack([vid(ci, cj), vid(ci + 1, cj + 1), vid(ci, cj + 1)], axis=1)
+    return q, np.stack([t0, t1], axis=1).reshape(-1, 3).astype(np.int32)
+
+
+def square_mesh_2d(n: int):
+    """Periodic n^2 lattice, 2 triangles per square. Returns (q [2, n^2], tris [2n^2, 3])."""
+    idx = np.arange(n, dtype=np.int64)
+    i, j = np.meshgrid(idx, idx, indexing="ij")
+    q = np.stack([i.ravel(), j.ravel()]).astype(np.float64) / n
+
+    def vid(a, b):
+        return (a % n) * n + (b % n)
+
+    ci, cj = i.ravel(), j.ravel()
+    t0 = np.stack([vid(ci, cj), vid(ci + 1, cj), vid(ci + 1, cj + 1)], axis=1)
+    t1 = np.stack([vid(ci, cj), vid(ci + 1, cj + 1), vid(ci, cj + 1)], axis=1)
+    tris = np.stack([t0, t1], axis=1).reshape(-1, 3).astype(np.int32)
+    return q, tris
+
+
+# --------------------------------------------------------------------------------------------
+# Displacement fields and densities
+# --------------------------------------------------------------------------------------------
+
+def sine_displacement_2d(q: np.ndarray, a1: float, a2: float) -> np.ndarray:
+    """x = q_x + a1 sin(2 pi q_x), y = q_y + a2 sin(2 pi q_y) (two orthogonal sine waves)."""
+    x = q.copy()
+    x[0] += a1 * np.sin(2 * np.pi * q[0])
+    x[1] += a2 * np.sin(2 * np.pi * q[1])
+    return x
+
+
+def grf_displacement(n: int, dim: int, rms_cells: float, kmax: float, rng) -> np.ndarray:
+    """Curl-free Gaussian random displacement on the n^dim Lagrangian lattice.
+
+    psi = grad(phi); |psi_k|^2 proportional to k^-2 for 0 < |k| <= kmax, zero above (spherical
+    cutoff, k in units of the fundamental). White noise comes from ``rng``. The field is scaled so
+    that rms |psi| over the vertices equals ``rms_cells`` Lagrangian cells (cell = 1/n).
+    Returns psi as [dim, n^dim] (box units).
+    """
+    shape = (n,) * dim
+    white = rng.standard_normal(shape)
+    wk = np.fft.rfftn(white)
+    freqs = [np.fft.fftfreq(n, d=1.0 / n)] * (dim - 1) + [np.fft.rfftfreq(n, d=1.0 / n)]
+    kv = np.meshgrid(*freqs, indexing="ij")
+    k2 = sum(kk * kk for kk in kv)
+    k = np.sqrt(k2)
+    amp = np.zeros_like(k)
+    sel = (k > 0) & (k <= kmax)
+    amp[sel] = 1.0 / k2[sel]  # |phi_k|^2 ~ k^-4  =>  |psi_k|^2 ~ k^-2
+    phik = wk * amp
+    psi = np.empty((dim,) + shape)
+    for a in range(dim):
+        psi[a] = np.fft.irfftn(1j * 2 * np.pi * kv[a] * phik, s=shape, axes=tuple(range(dim)))
+    psi = psi.reshape(dim, -1)
+    rms = math.sqrt(float(np.mean(np.sum(psi * psi, axis=0))))
+    if rms > 0:
+        psi *= (rms_cells / n) / rms
+    return psi
+
+
+def lognormal_density(nv: int, sigma: float, rng) -> np.ndarray:
+    """rho = exp(sigma z), z ~ N(0,1) (median 1)."""
+    return np.exp(sigma * rng.standard_normal(nv))
+
+
+# --------------------------------------------------------------------------------------------
+# The workloads
+# --------------------------------------------------------------------------------------------
+
+CONFIG_NAMES = {
+    "c1a": "2D 64^2 Lagrangian squares (8192 triangles), two sine waves a=(0.15, 0.10), rho=1, 128^2 grid",
+    "c1b": "2D 64^2 Lagrangian squares (8192 triangles), two sine waves a=(0.45, 0.30) (folded), rho=1, 128^2 grid",
+    "c2": "3D 32^3 Kuhn cubes (196,608 tets), GRF k^-2 k<=16 rms 0.5 cell, rho=1, 128^3 grid",
+    "c3": "3D 128^3 Kuhn cubes (12,582,912 tets), GRF k^-2 k<=16 rms 4 cells, lognormal rho sigma=0.5, 256^3 grid",
+}
+
+
+def _wrap(x: np.ndarray) -> np.ndarray:
+    return x - np.floor(x)
+
+
+def make_config(name: str, scale: int | None = None) -> Mesh:
+    """Build one named workload.
+
+    c1a/c1b: 2D sine-wave meshes; c2/c3: 3D random-field meshes. ``scale`` overrides the
+    Lagrangian lattice size n (the grid keeps the same ratio to n), for reduced test cases.
+    """
+    if name in ("c1a", "c1b"):
+        n = scale or 64
+        q, tris = square_mesh_2d(n)
+        a1, a2 = (0.15, 0.10) if name == "c1a" else (0.45, 0.30)
+        x = _wrap(sine_displacement_2d(q, a1, a2))
+        rho = np.ones(q.shape[1])
+        g = 2 * n
+        return Mesh(x, tris, rho, (g, g), (0.0, 0.0), (1.0, 1.0), True, name)
+    if name == "c2":
+        n = scale or 32
+        rng = np.random.default_rng(1002)
+        q, tets = kuhn_mesh_3d(n)
+        x = _wrap(q + grf_displacement(n, 3, 0.5, 16.0, rng))
+        rho = np.ones(q.shape[1])
+        g = 4 * n
+        return Mesh(x, tets, rho, (g, g, g), (0.0,) * 3, (1.0,) * 3, True, name)
+    if name == "c3":
+        n = scale or 128
+        rng = np.random.default_rng(1003)
+        q, tets = kuhn_mesh_3d(n)
+        x = _wrap(q + grf_displacement(n, 3, 4.0, 16.0, rng))
+        rho = lognormal_density(q.shape[1], 0.5, rng)
+        g = 2 * n
+        return Mesh(x, tets, rho, (g, g, g), (0.0,) * 3, (1.0,) * 3, True, name)
+    raise ValueError(f"unknown workload {name!r}")
+
+
+def random_simplices(dim: int, ns: int, grid: int, size: float, rng, periodic: bool = True,
+                     rho_sigma: float = 0.5) -> Mesh:
+    """``ns`` independent random simplices (each with its own D+1 vertices) in a unit box.
+
+    Vertex 0 is uniform in the box; the others are vertex 0 plus uniform offsets in
+    [-size, size] grid cells. Used for small parity and stress cases.
+    """
+    h = 1.0 / grid
+    v0 = rng.random((dim, ns))
+    offs = (rng.random((dim, ns, dim)) * 2 - 1) * size * h
+    pos = np.empty((dim, ns * (dim + 1)))
+    pos[:, 0::dim + 1] = v0
+    for i in range(dim):
+        pos[:, i + 1::dim + 1] = v0 + offs[:, :, i]
+    if periodic:
+        pos = _wrap(pos)
+    simp = np.arange(ns * (dim + 1), dtype=np.int32).reshape(ns, dim + 1)
+    rho = lognormal_density(ns * (dim + 1), rho_sigma, rng) if rho_sigma > 0 else np.ones(ns * (dim + 1))
+    return Mesh(pos, simp, rho, (grid,) * dim, (0.0,) * dim, (1.0,) * dim, periodic, "random")

@@ -1,0 +1,146 @@
+/*
+ * coldproj — exact projection of a piecewise-linear density carried by a simplicial mesh onto a
+ * regular grid, on one NVIDIA GB300 (sm_103a), behind a plain C ABI.
+ *
+ * The method is the exact projection of Sousbie & Colombi, "ColDICE: a parallel Vlasov-Poisson
+ * solver using moving adaptive simplicial tessellation" (arXiv:1509.07720), Sect. 3 and
+ * Appendices C-E: the mass of every grid cell is the integral, over the cell, of the linear
+ * interpolation of the per-vertex densities inside every simplex, evaluated exactly as a sum of
+ * Franklin vertex/edge/facet contributions (Sect. 3.1, eqs. firstOrder, contrib, E0, E1) over the
+ * corners of every (simplex intersect cell) polyhedron (Sect. 3.2, corner types A-D), with exact
+ * predicates and simulation of simplicity (Sect. 3.3, eq. sos; Appendix E).
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers (current CUDA device of the context) unless stated
+ *    otherwise; the caller owns them and keeps them alive until the work on `stream` is done.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Every call
+ *    only enqueues work on it and returns; results are valid once the stream has reached them.
+ *  - Return value: CDP_OK (0) or a negative CDP_ERR_* code; no C++ exception crosses the ABI and
+ *    nothing aborts. Argument errors are detected on the host before anything is enqueued.
+ *    Errors found by the kernels (bad vertex index, non-finite coordinate, a simplex too large)
+ *    are recorded in the context and returned by cdp_check (or by cdp_project when it is given a
+ *    stats block, which makes it synchronise).
+ *  - A context is not thread-safe and its scratch memory is reused by every call: do not run two
+ *    calls with one context on two streams at the same time.
+ *  - Grids are C order with axis 0 slowest: cell (i, j, k) of an (n0, n1, n2) grid is element
+ *    (i * n1 + j) * n2 + k. Cell (i, j, k) covers [lo + i h, lo + (i + 1) h) per axis, h = len / n.
+ */
+#ifndef COLDPROJ_H
+#define COLDPROJ_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CDP_API __attribute__((visibility("default")))
+#else
+#define CDP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CDP_OK = 0,
+    CDP_ERR_ARG = -1,     /* invalid argument (null pointer, bad size, bad dimension) */
+    CDP_ERR_INDEX = -2,   /* a simplex refers to a vertex index outside [0, n_verts) */
+    CDP_ERR_NAN = -3,     /* a vertex coordinate or density is not finite, or absurdly far out */
+    CDP_ERR_EXTENT = -4,  /* a simplex spans half a periodic box or more, or > 2048 cells per axis */
+    CDP_ERR_OOM = -5,     /* device scratch allocation failed */
+    CDP_ERR_TIMEOUT = -6, /* a bounded device-side wait gave up */
+    CDP_ERR_CUDA = -7     /* a CUDA runtime or library call failed */
+};
+
+/* Arithmetic of the projection. Both paths take the same exact combinatorial decisions.
+ * CDP_FP64: every contribution in FP64 (error vs the exact result ~1e-13 of the largest cell).
+ * CDP_FP32_MIXED: contributions in FP32, classification exact (integer) with an FP32 filter,
+ *   accumulation of every (simplex, cell) piece into the FP64 grid (error ~1e-6 of the largest
+ *   cell). */
+enum { CDP_FP64 = 0, CDP_FP32_MIXED = 1 };
+
+typedef struct cdp_ctx cdp_ctx;
+
+/* One projection problem (Algorithm 2's inputs and output).
+ *   dim          2 (triangles) or 3 (tetrahedra)
+ *   n_verts      number of vertices; n_simplices number of simplices (0 allowed)
+ *   pos[a]       device, double[n_verts]: coordinate a of every vertex (world units), a < dim
+ *   simplices    device, int32[n_simplices * (dim + 1)]: vertex indices, one row per simplex;
+ *                any vertex order and orientation (inverted simplices are fine, mass is +|V| rho)
+ *   rho          device, double[n_verts]: density at every vertex (linear inside each simplex)
+ *   grid[a]      cells per axis (1 <= grid[a] <= 2^20), a < dim
+ *   box_lo/len   box origin and side lengths (len > 0)
+ *   periodic     1: the box is a torus, every simplex is taken at the minimal image of its
+ *                vertex 0 (every vertex offset must be < half a box length) and cells wrap;
+ *                0: mass outside the grid is dropped
+ *   cell_mass    device, double[prod(grid)]: OUTPUT, integral of rho over every cell */
+typedef struct {
+    int dim;
+    int64_t n_verts;
+    int64_t n_simplices;
+    const double* pos[3];
+    const int32_t* simplices;
+    const double* rho;
+    int32_t grid[3];
+    double box_lo[3];
+    double box_len[3];
+    int periodic;
+    double* cell_mass;
+} cdp_problem;
+
+/* Counters of one projection (filled when a stats block is passed). */
+typedef struct {
+    uint64_t n_zero_volume;   /* simplices of zero volume (no contribution) */
+    uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
+    uint64_t n_small;         /* simplices projected by one thread (bounding box <= 64 cells) */
+    uint64_t n_large;         /* simplices split into tiles */
+    uint64_t n_large_tiles;   /* tiles processed for them */
+    uint64_t corners_a;       /* (corner, cell) incidences of type A: grid node inside a simplex */
+    uint64_t corners_b;       /* type B: simplex vertex */
+    uint64_t corners_c;       /* type C: simplex edge x cell face */
+    uint64_t corners_d;       /* type D: simplex facet x cell edge (3D) */
+    uint64_t exact_fallbacks; /* predicate evaluations decided by the exact integer stage */
+    uint64_t large_corners[4];/* the part of corners_a..d found by the tiled kernel (A, B, C, D) */
+    uint32_t error_flags;     /* bit 0 bad index, bit 1 non-finite, bit 2 extent */
+    uint32_t reserved;
+} cdp_stats;
+
+/* Create a context on CUDA device `device` (scratch is allocated lazily and grown as needed).
+ * *out receives the context; returns CDP_ERR_ARG / CDP_ERR_CUDA on failure. */
+CDP_API int cdp_create(cdp_ctx** out, int device);
+
+/* Free the context and its scratch (synchronises the device first). NULL is ignored. */
+CDP_API void cdp_destroy(cdp_ctx* ctx);
+
+/* Exact projection of one mesh (Sect. 3; Algorithm 2): prob->cell_mass[V] = sum over simplices S
+ * of the integral over S intersect V of the linear interpolant of rho.
+ *   precision    CDP_FP64 or CDP_FP32_MIXED
+ *   accumulate   0: cell_mass is overwritten; 1: the projection is added to it
+ *   stats        NULL: asynchronous; otherwise the call synchronises `stream`, fills *stats and
+ *                returns any error the kernels found.
+ * Scratch: 32 bytes per vertex + 4 bytes per simplex (context-owned). */
+CDP_API int cdp_project(cdp_ctx* ctx, const cdp_problem* prob, int precision, int accumulate, void* stream,
+                cdp_stats* stats);
+
+/* Synchronise `stream` and return the first error the kernels recorded since the last check
+ * (and clear it). */
+CDP_API int cdp_check(cdp_ctx* ctx, void* stream);
+
+/* Per-kernel timing (instrumentation, off by default).  With `enable` != 0 every later
+ * cdp_project records CUDA events around each of its kernels on its stream and adds the elapsed
+ * times to per-kernel totals; enabling (or disabling) also resets the totals and the call count. */
+CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
+
+/* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1]:
+ * [0] vertex preparation, [1] one-thread simplices (and the single-cell closed form), [2] tiled
+ * large simplices.  *calls receives the number of timed cdp_project calls.  Returns the number
+ * of slots written. */
+CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
+
+/* Human-readable name of a return code (static string). */
+CDP_API const char* cdp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLDPROJ_H */

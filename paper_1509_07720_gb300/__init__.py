@@ -1,1 +1,236 @@
-"""GB300-native exact projection of piecewise-linear simplicial meshes onto regular grids."""
+"""GB300-native exact projection of piecewise-linear simplicial meshes onto regular grids.
+
+Thin Python binding of the C ABI declared in ``include/coldproj.h`` (library
+``libcoldproj.so``, built in-tree from ``csrc/`` by ``build.py``). The functions here only
+marshal arguments: every step of the projection runs in the CUDA kernels. PyTorch is used for
+device memory and streams only. There is no CPU fallback: if the library is missing or no GPU is
+present, the calls raise.
+
+Low-level names mirror the ABI (``cdp_create``, ``cdp_project``, ``cdp_check``, ...). The
+``Projector`` class wraps them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "CDP_FP64", "CDP_FP32_MIXED", "CdpError", "cdp_problem", "cdp_stats", "load_library", "library_path",
+    "cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror", "cdp_timing_enable",
+    "cdp_timing_read", "Projector", "EXPORTED_SYMBOLS",
+]
+
+CDP_FP64 = 0
+CDP_FP32_MIXED = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libcoldproj.so")
+_lib = None
+
+# every symbol the header declares (checked by the CPU tests)
+EXPORTED_SYMBOLS = ("cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror",
+                    "cdp_timing_enable", "cdp_timing_read")
+
+
+class CdpError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {cdp_strerror(code)} ({code})" if what else f"{cdp_strerror(code)} ({code})")
+
+
+class cdp_problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n_verts", ctypes.c_int64),
+        ("n_simplices", ctypes.c_int64),
+        ("pos", ctypes.c_void_p * 3),
+        ("simplices", ctypes.c_void_p),
+        ("rho", ctypes.c_void_p),
+        ("grid", ctypes.c_int32 * 3),
+        ("box_lo", ctypes.c_double * 3),
+        ("box_len", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int),
+        ("cell_mass", ctypes.c_void_p),
+    ]
+
+
+class cdp_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "n_zero_volume", "n_single_cell", "n_small", "n_large", "n_large_tiles",
+        "corners_a", "corners_b", "corners_c", "corners_d", "exact_fallbacks")] + [
+        ("large_corners", ctypes.c_uint64 * 4), ("error_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n not in ("reserved", "large_corners")}
+        d["large_corners"] = [int(v) for v in self.large_corners]
+        return d
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None):
+    """Load libcoldproj.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"{p} not found: build it with `python -m paper_1509_07720_gb300.build`")
+    lib = ctypes.CDLL(p)
+    vp = ctypes.c_void_p
+    lib.cdp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.cdp_create.restype = ctypes.c_int
+    lib.cdp_destroy.argtypes = [vp]
+    lib.cdp_destroy.restype = None
+    lib.cdp_project.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_int, vp,
+                                ctypes.POINTER(cdp_stats)]
+    lib.cdp_project.restype = ctypes.c_int
+    lib.cdp_check.argtypes = [vp, vp]
+    lib.cdp_check.restype = ctypes.c_int
+    lib.cdp_timing_enable.argtypes = [vp, ctypes.c_int]
+    lib.cdp_timing_enable.restype = ctypes.c_int
+    lib.cdp_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.cdp_timing_read.restype = ctypes.c_int
+    lib.cdp_strerror.argtypes = [ctypes.c_int]
+    lib.cdp_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def cdp_strerror(code: int) -> str:
+    try:
+        return load_library().cdp_strerror(int(code)).decode()
+    except OSError:
+        return f"error {code}"
+
+
+def _raise(rc, what):
+    if rc != 0:
+        raise CdpError(rc, what)
+
+
+def cdp_create(device: int = 0) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _raise(load_library().cdp_create(ctypes.byref(ctx), int(device)), "cdp_create")
+    return ctx
+
+
+def cdp_destroy(ctx) -> None:
+    load_library().cdp_destroy(ctx)
+
+
+def cdp_project(ctx, prob: cdp_problem, precision: int, accumulate: int = 0, stream: int = 0,
+                stats: cdp_stats | None = None) -> int:
+    """Raw call; returns the ABI's status code (0 = ok)."""
+    return load_library().cdp_project(ctx, ctypes.byref(prob), int(precision), int(accumulate),
+                                      ctypes.c_void_p(stream), ctypes.byref(stats) if stats is not None else None)
+
+
+def cdp_check(ctx, stream: int = 0) -> int:
+    return load_library().cdp_check(ctx, ctypes.c_void_p(stream))
+
+
+def cdp_timing_enable(ctx, enable: bool) -> int:
+    return load_library().cdp_timing_enable(ctx, int(bool(enable)))
+
+
+def cdp_timing_read(ctx):
+    """(per-kernel totals in ms [prep, one-thread, tiled], number of timed calls)."""
+    buf = (ctypes.c_double * 3)()
+    calls = ctypes.c_int(0)
+    rc = load_library().cdp_timing_read(ctx, buf, 3, ctypes.byref(calls))
+    if rc < 0:
+        raise CdpError(rc, "cdp_timing_read")
+    return list(buf), int(calls.value)
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Projector:
+    """Owns one library context on a CUDA device and projects meshes held in torch tensors.
+
+    pos: float64 tensor [D, Nv] (or a list of D tensors), simplices: int32 [Ns, D+1],
+    rho: float64 [Nv], all on the context's device, contiguous. Output: float64 tensor shaped
+    ``grid`` (new, or ``out`` when given).
+    """
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        self._ctx = cdp_create(self.device)
+
+    def close(self):
+        if self._ctx is not None:
+            cdp_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def make_problem(pos, simplices, rho, grid, box_lo, box_len, periodic, out) -> cdp_problem:
+        import torch
+
+        dim = len(grid)
+        p = cdp_problem()
+        p.dim = dim
+        rows = [pos[a] for a in range(dim)]
+        for a in range(dim):
+            t = rows[a]
+            if t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("pos rows must be contiguous float64")
+            p.pos[a] = t.data_ptr()
+        if simplices.dtype != torch.int32 or not simplices.is_contiguous() or simplices.dim() != 2 \
+                or simplices.shape[1] != dim + 1:
+            raise ValueError("simplices must be a contiguous int32 [Ns, D+1] tensor")
+        if rho.dtype != torch.float64 or not rho.is_contiguous():
+            raise ValueError("rho must be contiguous float64")
+        if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != tuple(grid):
+            raise ValueError("out must be a contiguous float64 tensor shaped like the grid")
+        p.n_verts = int(rho.numel())
+        p.n_simplices = int(simplices.shape[0])
+        p.simplices = simplices.data_ptr() if simplices.numel() else None
+        p.rho = rho.data_ptr() if rho.numel() else None
+        for a in range(dim):
+            p.grid[a] = int(grid[a])
+            p.box_lo[a] = float(box_lo[a])
+            p.box_len[a] = float(box_len[a])
+        p.periodic = 1 if periodic else 0
+        p.cell_mass = out.data_ptr()
+        return p
+
+    def project(self, pos, simplices, rho, grid, box_lo=None, box_len=None, periodic=True,
+                precision=CDP_FP32_MIXED, out=None, accumulate=False, stream=None, stats=False):
+        import torch
+
+        dim = len(grid)
+        box_lo = box_lo if box_lo is not None else (0.0,) * dim
+        box_len = box_len if box_len is not None else (1.0,) * dim
+        if out is None:
+            out = torch.empty(tuple(grid), dtype=torch.float64, device=f"cuda:{self.device}")
+        prob = self.make_problem(pos, simplices, rho, grid, box_lo, box_len, periodic, out)
+        st = cdp_stats() if stats else None
+        rc = cdp_project(self._ctx, prob, precision, int(bool(accumulate)), _stream_handle(stream), st)
+        _raise(rc, "cdp_project")
+        if stats:
+            return out, st.as_dict()
+        return out
+
+    def check(self, stream=None):
+        _raise(cdp_check(self._ctx, _stream_handle(stream)), "cdp_check")
+
+    def timing(self, enable=None):
+        """Enable/disable per-kernel timing, or (enable=None) read the totals."""
+        if enable is None:
+            return cdp_timing_read(self._ctx)
+        _raise(cdp_timing_enable(self._ctx, enable), "cdp_timing_enable")

@@ -1,0 +1,354 @@
+// C-ABI entry points (declared in include/coldproj.h): argument checking, scratch management and
+// the launch sequence of the projection.
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/coldproj.h"
+#include "cdp_project.h"
+
+struct cdp_ctx {
+    int device;
+    int num_sms;
+    int blocks_small[2];  // resident blocks per SM of the small kernel (fp64, fp32)
+    int blocks_big[2];
+    cdp::VertexRec* verts;
+    size_t verts_cap;
+    int* queue;
+    size_t queue_cap;
+    cdp::Counters* ctr;       // device
+    cdp::UnitCounts* stats;   // device
+    cdp::Counters* h_ctr;     // pinned host mirrors
+    cdp::UnitCounts* h_stats;
+    // per-kernel timing: 4 events per timed call (before prep, after prep, after the one-thread
+    // kernel, after the tiled kernel), folded into totals when read
+    int timing;
+    std::vector<cudaEvent_t>* pending;
+    std::vector<cudaEvent_t>* pool;
+    double totals[3];
+    int calls;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev;
+    bool changed;
+    explicit DeviceGuard(int dev) : prev(0), changed(false) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+int flags_to_code(unsigned f) {
+    if (f & cdp::CDP_FLAG_INDEX) return CDP_ERR_INDEX;
+    if (f & cdp::CDP_FLAG_NAN) return CDP_ERR_NAN;
+    if (f & cdp::CDP_FLAG_EXTENT) return CDP_ERR_EXTENT;
+    return CDP_OK;
+}
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t need) {
+    if (need <= *cap) return CDP_OK;
+    size_t n = need + need / 4 + 1024;
+    T* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_OOM;
+    }
+    if (*p) cudaFree(*p);
+    *p = q;
+    *cap = n;
+    return CDP_OK;
+}
+
+int check_problem(const cdp_problem* p) {
+    if (!p) return CDP_ERR_ARG;
+    if (p->dim != 2 && p->dim != 3) return CDP_ERR_ARG;
+    if (p->n_verts < 0 || p->n_simplices < 0 || p->n_verts > (int64_t)0x7fffffff ||
+        p->n_simplices > (int64_t)0x7fffffff)
+        return CDP_ERR_ARG;
+    if (!p->cell_mass) return CDP_ERR_ARG;
+    for (int a = 0; a < p->dim; ++a) {
+        if (p->grid[a] < 1 || p->grid[a] > (1 << 20)) return CDP_ERR_ARG;
+        if (!(p->box_len[a] > 0.0) || !(p->box_len[a] < 1e300)) return CDP_ERR_ARG;
+        if (!(p->box_lo[a] == p->box_lo[a])) return CDP_ERR_ARG;
+        if (p->n_verts > 0 && !p->pos[a]) return CDP_ERR_ARG;
+    }
+    if (p->n_simplices > 0 && (!p->simplices || !p->rho || p->n_verts == 0)) return CDP_ERR_ARG;
+    if (p->n_verts > 0 && !p->rho) return CDP_ERR_ARG;
+    long long cells = 1;
+    for (int a = 0; a < p->dim; ++a) {
+        cells *= p->grid[a];
+        if (cells > ((long long)1 << 40)) return CDP_ERR_ARG;
+    }
+    return CDP_OK;
+}
+
+cudaEvent_t take_event(cdp_ctx* c) {
+    if (!c->pool->empty()) {
+        cudaEvent_t e = c->pool->back();
+        c->pool->pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// fold the recorded event quadruples into the totals (synchronises on them)
+int fold_timing(cdp_ctx* c) {
+    std::vector<cudaEvent_t>& p = *c->pending;
+    for (size_t i = 0; i + 3 < p.size(); i += 4) {
+        if (cudaEventSynchronize(p[i + 3]) != cudaSuccess) {
+            cudaGetLastError();
+            return CDP_ERR_CUDA;
+        }
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p[i + k], p[i + k + 1]) == cudaSuccess) c->totals[k] += ms;
+            cudaGetLastError();
+        }
+        c->calls += 1;
+    }
+    for (cudaEvent_t e : p) c->pool->push_back(e);
+    p.clear();
+    return CDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdp_timing_enable(cdp_ctx* c, int enable) {
+    if (!c) return CDP_ERR_ARG;
+    DeviceGuard guard(c->device);
+    int rc = fold_timing(c);
+    c->timing = enable ? 1 : 0;
+    c->totals[0] = c->totals[1] = c->totals[2] = 0.0;
+    c->calls = 0;
+    return rc;
+}
+
+int cdp_timing_read(cdp_ctx* c, double* out_ms, int n, int* calls) {
+    if (!c || (n > 0 && !out_ms)) return CDP_ERR_ARG;
+    DeviceGuard guard(c->device);
+    int rc = fold_timing(c);
+    if (rc) return rc;
+    int m = n < 3 ? n : 3;
+    for (int k = 0; k < m; ++k) out_ms[k] = c->totals[k];
+    if (calls) *calls = c->calls;
+    return m;
+}
+
+const char* cdp_strerror(int code) {
+    switch (code) {
+        case CDP_OK: return "ok";
+        case CDP_ERR_ARG: return "invalid argument";
+        case CDP_ERR_INDEX: return "vertex index out of range";
+        case CDP_ERR_NAN: return "non-finite or out-of-range coordinate or density";
+        case CDP_ERR_EXTENT: return "simplex spans half a periodic box or more than 2048 cells";
+        case CDP_ERR_OOM: return "device scratch allocation failed";
+        case CDP_ERR_TIMEOUT: return "bounded device wait gave up";
+        case CDP_ERR_CUDA: return "CUDA error";
+        default: return "unknown error";
+    }
+}
+
+int cdp_create(cdp_ctx** out, int device) {
+    if (!out) return CDP_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return CDP_ERR_ARG;
+    DeviceGuard guard(device);
+    cdp_ctx* c = new (std::nothrow) cdp_ctx;
+    if (!c) return CDP_ERR_OOM;
+    memset(c, 0, sizeof(*c));
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cdp::configure_all() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return CDP_ERR_CUDA;
+    }
+    // resident blocks per SM, limited by the 64 slots x block of shared memory
+    c->blocks_small[0] = c->blocks_big[0] = 3;  // fp64: 64 KB per block
+    c->blocks_small[1] = c->blocks_big[1] = 6;  // fp32: 32 KB per block
+    if (cudaMalloc(&c->ctr, sizeof(cdp::Counters)) != cudaSuccess ||
+        cudaMalloc(&c->stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess ||
+        cudaMallocHost(&c->h_ctr, sizeof(cdp::Counters)) != cudaSuccess ||
+        cudaMallocHost(&c->h_stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess) {
+        cudaGetLastError();
+        cdp_destroy(c);
+        return CDP_ERR_OOM;
+    }
+    c->pending = new (std::nothrow) std::vector<cudaEvent_t>();
+    c->pool = new (std::nothrow) std::vector<cudaEvent_t>();
+    if (!c->pending || !c->pool) {
+        cdp_destroy(c);
+        return CDP_ERR_OOM;
+    }
+    if (cudaMemset(c->ctr, 0, sizeof(cdp::Counters)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        cdp_destroy(c);
+        return CDP_ERR_CUDA;
+    }
+    *out = c;
+    return CDP_OK;
+}
+
+void cdp_destroy(cdp_ctx* c) {
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    cudaDeviceSynchronize();
+    if (c->verts) cudaFree(c->verts);
+    if (c->queue) cudaFree(c->queue);
+    if (c->ctr) cudaFree(c->ctr);
+    if (c->stats) cudaFree(c->stats);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->pending) {
+        for (cudaEvent_t e : *c->pending) cudaEventDestroy(e);
+        delete c->pending;
+    }
+    if (c->pool) {
+        for (cudaEvent_t e : *c->pool) cudaEventDestroy(e);
+        delete c->pool;
+    }
+    cudaGetLastError();
+    delete c;
+}
+
+int cdp_check(cdp_ctx* c, void* stream) {
+    if (!c) return CDP_ERR_ARG;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(cdp::Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    unsigned f = c->h_ctr->flags;
+    if (f && cudaMemsetAsync(c->ctr, 0, sizeof(unsigned), st) != cudaSuccess) return CDP_ERR_CUDA;
+    return flags_to_code(f);
+}
+
+int cdp_project(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, void* stream, cdp_stats* stats) {
+    if (!c) return CDP_ERR_ARG;
+    int rc = check_problem(p);
+    if (rc) return rc;
+    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
+    if ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1)))) return rc;
+
+    cdp::LaunchArgs L;
+    memset(&L, 0, sizeof(L));
+    L.g.dim = p->dim;
+    L.g.periodic = p->periodic ? 1 : 0;
+    long long cells = 1;
+    L.cellvol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (a < p->dim) {
+            L.g.n[a] = p->grid[a];
+            L.g.lo[a] = p->box_lo[a];
+            L.g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
+            L.cellvol *= p->box_len[a] / (double)p->grid[a];
+            cells *= p->grid[a];
+        } else {
+            L.g.n[a] = 1;
+            L.g.lo[a] = 0.0;
+            L.g.inv_h[a] = 1.0;
+        }
+    }
+    L.nv = p->n_verts;
+    L.ns = p->n_simplices;
+    L.simplices = p->simplices;
+    L.verts = c->verts;
+    L.out = p->cell_mass;
+    L.queue = c->queue;
+    L.ctr = c->ctr;
+    L.stats = stats ? c->stats : nullptr;
+    L.num_sms = c->num_sms;
+    int fp32 = precision == CDP_FP32_MIXED;
+    L.small_blocks_per_sm = 16 * c->blocks_small[fp32];
+    L.big_blocks_per_sm = c->blocks_big[fp32];
+
+    // zero the per-call counters (the sticky error word at offset 0 is kept)
+    if (cudaMemsetAsync((char*)c->ctr + sizeof(unsigned), 0, sizeof(cdp::Counters) - sizeof(unsigned), st) !=
+        cudaSuccess)
+        return CDP_ERR_CUDA;
+    if (stats && cudaMemsetAsync(c->stats, 0, 2 * sizeof(cdp::UnitCounts), st) != cudaSuccess) return CDP_ERR_CUDA;
+    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
+        return CDP_ERR_CUDA;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (c->timing) {
+        if (c->pending->size() >= 4096) fold_timing(c);
+        for (int k = 0; k < 4; ++k) ev[k] = take_event(c);
+        if (!ev[0] || !ev[1] || !ev[2] || !ev[3]) {
+            for (int k = 0; k < 4; ++k)
+                if (ev[k]) c->pool->push_back(ev[k]);
+            return CDP_ERR_CUDA;
+        }
+        cudaEventRecord(ev[0], st);
+    }
+    if (cdp::launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    if (ev[1]) cudaEventRecord(ev[1], st);
+    if (cdp::launch_project(L, fp32, st, ev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    if (ev[3]) {
+        cudaEventRecord(ev[3], st);
+        for (int k = 0; k < 4; ++k) c->pending->push_back(ev[k]);
+    }
+    if (!stats) return CDP_OK;
+    if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(cdp::Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->h_stats, c->stats, 2 * sizeof(cdp::UnitCounts), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    memset(stats, 0, sizeof(*stats));
+    stats->n_zero_volume = c->h_ctr->n_zero;
+    stats->n_single_cell = c->h_ctr->n_class0;
+    stats->n_small = c->h_ctr->n_small;
+    stats->n_large = c->h_ctr->big_count;
+    stats->n_large_tiles = c->h_ctr->n_big_tiles;
+    const cdp::UnitCounts& s0 = c->h_stats[0];
+    const cdp::UnitCounts& s1 = c->h_stats[1];
+    stats->corners_a = s0.a + s1.a;
+    stats->corners_b = s0.b + s1.b;
+    stats->corners_c = s0.c + s1.c;
+    stats->corners_d = s0.d + s1.d;
+    stats->exact_fallbacks = s0.exact + s1.exact;
+    stats->large_corners[0] = s1.a;
+    stats->large_corners[1] = s1.b;
+    stats->large_corners[2] = s1.c;
+    stats->large_corners[3] = s1.d;
+    stats->error_flags = c->h_ctr->flags;
+    unsigned f = c->h_ctr->flags;
+    if (f && cudaMemsetAsync(c->ctr, 0, sizeof(unsigned), st) != cudaSuccess) return CDP_ERR_CUDA;
+    return flags_to_code(f);
+}
+
+}  // extern "C"

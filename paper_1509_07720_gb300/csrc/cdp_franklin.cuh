@@ -1,0 +1,820 @@
+// Exact projection of one simplex (or of one tile of its bounding box) onto the grid cells, by
+// enumerating the corners of every polyhedron (simplex intersect cell) and adding Franklin's
+// (vertex, edge, facet) contributions (Sect. 3.1, eqs. firstOrder, contrib, E0, E1; Appendix C).
+//
+// For a corner at position P (relative to an origin O chosen per (simplex, cell) piece) and one
+// incident (vertex, edge, facet) triple with unit vectors T (along the edge, leaving the corner),
+// N (in the facet, normal to T, pointing into the facet) and B (normal to the facet, pointing into
+// the polyhedron), the contribution in 3D is
+//     C = E0 [rho(O) + E1 . grad rho],  E0 = -1/6 (P.T)(P.N)(P.B),
+//     E1 = 1/4 ((P.T) T + 2 (P.N) N + 3 (P.B) B),
+// and in 2D E0 = 1/2 (P.T)(P.N), E1 = 1/3 ((P.T) T + 2 (P.N) N).  With rho(O) = rho(X) - grad.P
+// and T, N, B orthonormal the bracket becomes rho(X) - 3/4 (P.T)(T.g) - 1/2 (P.N)(N.g)
+// - 1/4 (P.B)(B.g) in 3D and rho(X) - 2/3 (P.T)(T.g) - 1/3 (P.N)(N.g) in 2D, which is what is
+// evaluated (rho(X) is the density at the corner itself, g = grad rho).
+//
+// The four corner types of Sect. 3.2 (Fig. cubeTetInter):
+//   A  a grid node inside the simplex: 6 triples (2 in 2D) with axis-aligned T, N, B; the sum
+//      over them is the closed form  sigma * prod_a P_a * (rho(X) - grad.P / 2), sigma = product
+//      of the signs telling on which side of the cell the node is;
+//   B  a simplex vertex: its 3 edges x 2 incident facets (2 triples in 2D);
+//   C  a simplex edge crossing a cell face: 6 triples (2 in 2D) for each of the 2 cells;
+//   D  a simplex facet crossing a cell edge (3D only): 6 triples for each of the 4 cells.
+// Every edge direction and in-facet normal is oriented by an exact sign (vertex order, exact
+// normal components, fixed parities of the vertex labels), never by a rounded dot product, and
+// every facet normal is converted from its exact integer value component by component, so that
+// nearly parallel planes do not lose the direction of their intersection line (Sect. 3.4: the
+// triplets need care in nearly degenerate configurations).
+//
+// Origin of each piece (reading of Sect. 3.1, which extrapolates rho to "the origin of
+// coordinates"): Franklin's sum over the corners of one closed polyhedron does not depend on the
+// origin, so every (simplex, cell) piece uses its own origin O = the simplex centroid clamped
+// into the cell.  Then |P| is bounded by both the cell diagonal and twice the simplex size,
+// which keeps the FP32 evaluation accurate.
+#pragma once
+
+#include "cdp_exact.cuh"
+
+namespace cdp {
+
+template <typename R>
+struct Eps;
+template <>
+struct Eps<float> {
+    // semi-static filter bounds (multiples of the unit roundoff 2^-24, see setup)
+    static constexpr float k2 = 3.814697265625e-06f;   // 2^-18
+    static constexpr float k3 = 3.814697265625e-06f;   // 2^-18
+};
+template <>
+struct Eps<double> {
+    static constexpr double k2 = 7.105427357601002e-15;  // 2^-47
+    static constexpr double k3 = 7.105427357601002e-15;  // 2^-47
+};
+
+template <typename R>
+CDP_HD R rsqrt_r(R v);
+template <>
+CDP_HD float rsqrt_r<float>(float v) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(v);
+#else
+    return 1.0f / sqrtf(v);
+#endif
+}
+template <>
+CDP_HD double rsqrt_r<double>(double v) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(v);
+#else
+    return 1.0 / sqrt(v);
+#endif
+}
+
+template <typename R>
+CDP_HD R floor_r(R v);
+template <>
+CDP_HD float floor_r<float>(float v) { return floorf(v); }
+template <>
+CDP_HD double floor_r<double>(double v) { return floor(v); }
+
+template <typename R>
+CDP_HD R dot3(const R a[3], const R b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+template <typename R>
+CDP_HD void cross3(const R a[3], const R b[3], R o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename R>
+CDP_HD R clamp_r(R v, R lo, R hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// One 3D (vertex, edge, facet) triple; the caller multiplies the sum by -1/6.
+template <typename R>
+CDP_HD R trip3(const R P[3], const R T[3], const R N[3], const R B[3], R rhoX, const R g[3]) {
+    R pt = dot3(P, T), pn = dot3(P, N), pb = dot3(P, B);
+    R gt = dot3(g, T), gn = dot3(g, N), gb = dot3(g, B);
+    return pt * pn * pb * (rhoX - R(0.75) * pt * gt - R(0.5) * pn * gn - R(0.25) * pb * gb);
+}
+
+// One 2D (vertex, edge) pair; the caller multiplies the sum by 1/2.
+template <typename R>
+CDP_HD R trip2(const R P[2], const R T[2], const R N[2], R rhoX, const R g[2]) {
+    R pt = P[0] * T[0] + P[1] * T[1], pn = P[0] * N[0] + P[1] * N[1];
+    R gt = g[0] * T[0] + g[1] * T[1], gn = g[0] * N[0] + g[1] * N[1];
+    return pt * pn * (rhoX - R(2.0 / 3.0) * pt * gt - R(1.0 / 3.0) * pn * gn);
+}
+
+// Counters of one projection (all optional, gathered only when requested).
+struct UnitCounts {
+    unsigned long long a, b, c, d, exact;
+};
+
+// ==========================================================================================
+// 3D
+// ==========================================================================================
+
+// A tetrahedron after canonicalisation: vertex coordinates in fixed point relative to the
+// integer cell `anchor` (absolute cell index of the frame origin), positively oriented.
+struct Tet {
+    i64 L[4][3];
+    double rho[4];
+    int cell[4][3];  // cell of every vertex, relative to the anchor
+    int lo[3], hi[3];
+    int anchor[3];
+};
+
+// the vertices of the edge e (a < b) and the two others (p < q)
+CDP_HD void tet_edge(int e, int& a, int& b, int& p, int& q) {
+    // (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
+    const int A[6] = {0, 0, 0, 1, 1, 2}, B[6] = {1, 2, 3, 2, 3, 3};
+    const int P[6] = {2, 1, 1, 0, 0, 0}, Qv[6] = {3, 3, 2, 3, 2, 1};
+    a = A[e];
+    b = B[e];
+    p = P[e];
+    q = Qv[e];
+}
+
+CDP_HD int tet_edge_index(int i, int j) {
+    int a = i < j ? i : j, b = i < j ? j : i;
+    return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+}
+
+// Per-unit working set of a tetrahedron: coordinates relative to the unit's tile origin.
+template <typename R>
+struct TetGeo {
+    i64 Lt[4][3];     // exact, relative to the tile origin
+    R x[4][3];        // rounded copies
+    R n[4][3];        // unit inward normals of the facets (facet f is opposite vertex f)
+    i128 nE[4][3];    // exact (unnormalised) inward normals, units 2^-2Q
+    R g[3];           // grad rho (per cell length)
+    R rho[4];
+    R c[3], rhoc;     // centroid and density there
+    R B2, B3;         // filter bounds for side2 / side3
+    int cell[4][3];   // vertex cells relative to the tile origin
+    int lo[3], hi[3]; // bounding box relative to the tile origin
+};
+
+// Fill the working set for the tile whose lowest cell is T (relative to the anchor).
+template <typename R>
+CDP_HD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
+    for (int k = 0; k < 4; ++k)
+        for (int a = 0; a < 3; ++a) {
+            G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
+            G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
+            G.cell[k][a] = S.cell[k][a] - T[a];
+        }
+    for (int a = 0; a < 3; ++a) {
+        G.lo[a] = S.lo[a] - T[a];
+        G.hi[a] = S.hi[a] - T[a];
+    }
+    i64 e1[3], e2[3], e3[3], f1[3], f2[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = G.Lt[1][a] - G.Lt[0][a];
+        e2[a] = G.Lt[2][a] - G.Lt[0][a];
+        e3[a] = G.Lt[3][a] - G.Lt[0][a];
+        f1[a] = G.Lt[3][a] - G.Lt[1][a];
+        f2[a] = G.Lt[2][a] - G.Lt[1][a];
+    }
+    // inward normals of a positively oriented tetrahedron
+    cross_exact(f1, f2, G.nE[0]);  // (x3-x1) x (x2-x1)
+    cross_exact(e2, e3, G.nE[1]);  // (x2-x0) x (x3-x0)
+    cross_exact(e3, e1, G.nE[2]);  // (x3-x0) x (x1-x0)
+    cross_exact(e1, e2, G.nE[3]);  // (x1-x0) x (x2-x0)
+    R nr[4][3];
+    for (int f = 0; f < 4; ++f) {
+        for (int a = 0; a < 3; ++a) nr[f][a] = i128_to_real<R>(G.nE[f][a], 2 * CDP_Q);
+        R inv = rsqrt_r<R>(dot3(nr[f], nr[f]));
+        for (int a = 0; a < 3; ++a) G.n[f][a] = nr[f][a] * inv;
+    }
+    // 6 |V| = e3 . (e1 x e2), exact, then rounded
+    double D = wide_to_double(dot3_wide(G.nE[3], e3), 3 * CDP_Q);
+    R invD = R(1.0 / D);
+    for (int k = 0; k < 4; ++k) G.rho[k] = (R)S.rho[k];
+    R d1 = G.rho[1] - G.rho[0], d2 = G.rho[2] - G.rho[0], d3 = G.rho[3] - G.rho[0];
+    for (int a = 0; a < 3; ++a) {
+        G.g[a] = (d1 * nr[1][a] + d2 * nr[2][a] + d3 * nr[3][a]) * invD;
+        G.c[a] = R(0.25) * (G.x[0][a] + G.x[1][a] + G.x[2][a] + G.x[3][a]);
+    }
+    G.rhoc = R(0.25) * (G.rho[0] + G.rho[1] + G.rho[2] + G.rho[3]);
+    int m = 1;
+    for (int a = 0; a < 3; ++a) {
+        int v = G.lo[a] < 0 ? -G.lo[a] : G.lo[a];
+        int w = G.hi[a] + 1 < 0 ? -(G.hi[a] + 1) : G.hi[a] + 1;
+        m = v > m ? v : m;
+        m = w > m ? w : m;
+    }
+    R Rm = R(m + 1);
+    G.B2 = Eps<R>::k2 * Rm * Rm;
+    G.B3 = Eps<R>::k3 * Rm;
+}
+
+// ------------------------------------------------------------------------------------------
+// predicates with a floating-point filter and the exact fallback
+// ------------------------------------------------------------------------------------------
+
+// perturbed orient2d of grid point (pu, pv) (integers, tile frame) against edge (i -> j) of the
+// projection on axes u < v
+template <typename R>
+CDP_HD int tet_side2(const TetGeo<R>& G, int i, int j, int u, int v, int pu, int pv, UnitCounts* cnt) {
+    R du = G.x[j][u] - G.x[i][u], dv = G.x[j][v] - G.x[i][v];
+    R val = du * (R(pv) - G.x[i][v]) - dv * (R(pu) - G.x[i][u]);
+    if (val > G.B2) return 1;
+    if (val < -G.B2) return -1;
+    if (cnt) cnt->exact++;
+    return side2_exact(G.Lt[i][u], G.Lt[i][v], G.Lt[j][u], G.Lt[j][v], (i64)pu << CDP_Q, (i64)pv << CDP_Q);
+}
+
+// perturbed side of grid node gn (tile frame) w.r.t. facet f: > 0 inside
+template <typename R>
+CDP_HD int tet_side3(const TetGeo<R>& G, int f, const int gn[3], UnitCounts* cnt) {
+    int a = f == 0 ? 1 : 0;  // a vertex of facet f
+    R val = G.n[f][0] * (R(gn[0]) - G.x[a][0]) + G.n[f][1] * (R(gn[1]) - G.x[a][1]) +
+            G.n[f][2] * (R(gn[2]) - G.x[a][2]);
+    if (val > G.B3) return 1;
+    if (val < -G.B3) return -1;
+    if (cnt) cnt->exact++;
+    i64 gp[3] = {(i64)gn[0] << CDP_Q, (i64)gn[1] << CDP_Q, (i64)gn[2] << CDP_Q};
+    return side3_exact(G.nE[f], G.Lt[a], gp);
+}
+
+// sign(X_j - d) for the crossing X of edge (a -> b) with grid plane x_k = c (perturbed)
+template <typename R>
+CDP_HD int tet_cross_side(const TetGeo<R>& G, int a, int b, int k, int c, int j, int d, int dirk,
+                          UnitCounts* cnt) {
+    int s = j < k ? tet_side2(G, a, b, j, k, d, c, cnt) : -tet_side2(G, a, b, k, j, c, d, cnt);
+    return dirk * s;
+}
+
+// cell index along j of the crossing of edge (a -> b) with plane x_k = c; `guess` from the
+// rounded crossing point, corrected by the exact predicate
+template <typename R>
+CDP_HD int tet_cross_cell(const TetGeo<R>& G, int a, int b, int k, int c, int j, int guess, int dirk,
+                          UnitCounts* cnt) {
+    int lo = G.cell[a][j] < G.cell[b][j] ? G.cell[a][j] : G.cell[b][j];
+    int hi = G.cell[a][j] < G.cell[b][j] ? G.cell[b][j] : G.cell[a][j];
+    int d = guess < lo ? lo : (guess > hi ? hi : guess);
+    // invariant wanted: side(d) > 0 (crossing above plane d) and side(d+1) < 0
+    for (int it = 0; it <= hi - lo + 1; ++it) {
+        if (d > lo && tet_cross_side(G, a, b, k, c, j, d, dirk, cnt) < 0) {
+            --d;
+            continue;
+        }
+        if (d < hi && tet_cross_side(G, a, b, k, c, j, d + 1, dirk, cnt) > 0) {
+            ++d;
+            continue;
+        }
+        break;
+    }
+    return d;
+}
+
+// cell index along l of the crossing of facet f with the grid line along l through (dj, dk)
+template <typename R>
+CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int j, int k, int dj, int dk, int guess,
+                               UnitCounts* cnt) {
+    int lo = G.lo[l], hi = G.hi[l];
+    int m = guess < lo ? lo : (guess > hi ? hi : guess);
+    int up = G.nE[f][l] > 0 ? 1 : -1;  // side3 grows along +l when the normal's l component is > 0
+    int gn[3];
+    gn[j] = dj;
+    gn[k] = dk;
+    for (int it = 0; it <= hi - lo + 1; ++it) {
+        gn[l] = m;
+        int s0 = tet_side3(G, f, gn, cnt);
+        if (m > lo && s0 == up) {  // node m already past the crossing
+            --m;
+            continue;
+        }
+        gn[l] = m + 1;
+        int s1 = tet_side3(G, f, gn, cnt);
+        if (m < hi && s1 == -up) {
+            ++m;
+            continue;
+        }
+        break;
+    }
+    return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// contributions of one (corner, cell) incidence; `v` = cell (tile frame)
+// ------------------------------------------------------------------------------------------
+
+template <typename R>
+CDP_HD void piece_origin(const TetGeo<R>& G, const int v[3], R O[3]) {
+    for (int a = 0; a < 3; ++a) O[a] = clamp_r(G.c[a], R(v[a]), R(v[a] + 1));
+}
+
+template <typename R>
+CDP_HD R rho_at(const TetGeo<R>& G, const R X[3]) {
+    return G.rhoc + G.g[0] * (X[0] - G.c[0]) + G.g[1] * (X[1] - G.c[1]) + G.g[2] * (X[2] - G.c[2]);
+}
+
+// unit vector of edge (a -> b), a < b
+template <typename R>
+CDP_HD void edge_unit(const TetGeo<R>& G, int a, int b, R ev[3]) {
+    for (int t = 0; t < 3; ++t) ev[t] = i64_to_real<R>(G.Lt[b][t] - G.Lt[a][t], CDP_Q);
+    R inv = rsqrt_r<R>(dot3(ev, ev));
+    for (int t = 0; t < 3; ++t) ev[t] *= inv;
+}
+
+// B: simplex vertex i in cell v
+template <typename R>
+CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const int v[3]) {
+    R O[3], P[3];
+    piece_origin(G, v, O);
+    for (int a = 0; a < 3; ++a) P[a] = G.x[i][a] - O[a];
+    R s = 0;
+    for (int j = 0; j < 4; ++j) {
+        if (j == i) continue;
+        int a = i < j ? i : j, b = i < j ? j : i;
+        R ev[3], T[3];
+        edge_unit(G, a, b, ev);
+        R sg = i == a ? R(1) : R(-1);
+        for (int t = 0; t < 3; ++t) T[t] = sg * ev[t];
+        for (int f = 0; f < 4; ++f) {
+            if (f == i || f == j) continue;
+            int r = 6 - i - j - f;  // third vertex of facet f
+            R N[3];
+            cross3(G.n[f], ev, N);
+            R ps = R(parity4(a, b, r, f));
+            for (int t = 0; t < 3; ++t) N[t] *= ps;
+            s += trip3(P, T, N, G.n[f], G.rho[i], G.g);
+        }
+    }
+    return R(-1.0 / 6.0) * s;
+}
+
+// C: edge e crossing the face x_k = (tile-frame plane) at X, cell on side sigma
+template <typename R>
+CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const R X[3], R rhoX, const int v[3]) {
+    int a, b, p, q;
+    tet_edge(e, a, b, p, q);
+    R O[3], P[3];
+    piece_origin(G, v, O);
+    for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
+    R ev[3];
+    edge_unit(G, a, b, ev);
+    R s = 0;
+    // the simplex edge, oriented into the cell, with its two facets (f_p contains q, f_q contains p)
+    R T[3], N[3];
+    R so = sigma * R(dirk);
+    for (int t = 0; t < 3; ++t) T[t] = so * ev[t];
+    cross3(G.n[p], ev, N);
+    R pp = R(parity4(a, b, q, p));
+    for (int t = 0; t < 3; ++t) N[t] *= pp;
+    s += trip3(P, T, N, G.n[p], rhoX, G.g);
+    cross3(G.n[q], ev, N);
+    R pq = R(parity4(a, b, p, q));
+    for (int t = 0; t < 3; ++t) N[t] *= pq;
+    s += trip3(P, T, N, G.n[q], rhoX, G.g);
+    // facet-face lines u_p (towards q's side) and u_q (towards p's side)
+    R lam = R(-parity4(a, b, p, q)) * R(dirk);
+    R Bk[3] = {0, 0, 0};
+    Bk[k] = sigma;
+    for (int w = 0; w < 2; ++w) {
+        const R* n = G.n[w == 0 ? p : q];
+        R su = w == 0 ? lam : -lam;
+        R r2 = R(0);
+        for (int t = 0; t < 3; ++t)
+            if (t != k) r2 += n[t] * n[t];
+        R ir = rsqrt_r<R>(r2);
+        R ek[3] = {0, 0, 0};
+        ek[k] = 1;
+        R U[3];
+        cross3(n, ek, U);
+        for (int t = 0; t < 3; ++t) U[t] *= su * ir;
+        R N1[3], N2[3];
+        for (int t = 0; t < 3; ++t) {
+            N1[t] = sigma * (ek[t] - n[k] * n[t]) * ir;  // in the facet, towards the cell face side
+            N2[t] = (n[t] - n[k] * ek[t]) * ir;          // in the face, towards the facet side
+        }
+        s += trip3(P, U, N1, n, rhoX, G.g);
+        s += trip3(P, U, N2, Bk, rhoX, G.g);
+    }
+    return R(-1.0 / 6.0) * s;
+}
+
+// D: facet f crossing the grid line along l at X; cell on sides (sj, sk) of the planes j, k
+template <typename R>
+CDP_HD R tet_corner_D(const TetGeo<R>& G, int f, int l, int j, int k, R sj, R sk, const R X[3], R rhoX,
+                      const int v[3]) {
+    R O[3], P[3];
+    piece_origin(G, v, O);
+    for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
+    const R* n = G.n[f];
+    R tau = G.nE[f][l] > 0 ? R(1) : R(-1);
+    R eps = (l == 1) ? R(-1) : R(1);  // Levi-Civita of (j, k, l) with j < k
+    R s = 0;
+    R El[3] = {0, 0, 0}, Ej[3] = {0, 0, 0}, Ek[3] = {0, 0, 0};
+    El[l] = tau;
+    Ej[j] = sj;
+    Ek[k] = sk;
+    s += trip3(P, El, Ek, Ej, rhoX, G.g);  // grid line with face j
+    s += trip3(P, El, Ej, Ek, rhoX, G.g);  // grid line with face k
+    // facet/face_j line, oriented towards the k side of the cell
+    {
+        R ej[3] = {0, 0, 0};
+        ej[j] = 1;
+        R ir = rsqrt_r<R>(n[k] * n[k] + n[l] * n[l]);
+        R U[3];
+        cross3(n, ej, U);
+        R su = sk * eps * tau * ir;
+        for (int t = 0; t < 3; ++t) U[t] *= su;
+        R N1[3], N2[3];
+        for (int t = 0; t < 3; ++t) {
+            N1[t] = sj * (ej[t] - n[j] * n[t]) * ir;
+            N2[t] = (n[t] - n[j] * ej[t]) * ir;
+        }
+        s += trip3(P, U, N1, n, rhoX, G.g);
+        s += trip3(P, U, N2, Ej, rhoX, G.g);
+    }
+    // facet/face_k line, oriented towards the j side of the cell
+    {
+        R ek[3] = {0, 0, 0};
+        ek[k] = 1;
+        R ir = rsqrt_r<R>(n[j] * n[j] + n[l] * n[l]);
+        R U[3];
+        cross3(n, ek, U);
+        R su = -sj * eps * tau * ir;
+        for (int t = 0; t < 3; ++t) U[t] *= su;
+        R N1[3], N2[3];
+        for (int t = 0; t < 3; ++t) {
+            N1[t] = sk * (ek[t] - n[k] * n[t]) * ir;
+            N2[t] = (n[t] - n[k] * ek[t]) * ir;
+        }
+        s += trip3(P, U, N1, n, rhoX, G.g);
+        s += trip3(P, U, N2, Ek, rhoX, G.g);
+    }
+    return R(-1.0 / 6.0) * s;
+}
+
+// A: grid node X (integer, tile frame) inside the simplex; cell on side s (s_a = +1 when the
+// node is the cell's upper corner along a)
+template <typename R>
+CDP_HD R tet_corner_A(const TetGeo<R>& G, const R X[3], R rhoX, const int v[3], R sgn) {
+    R O[3], P[3];
+    piece_origin(G, v, O);
+    for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
+    return sgn * P[0] * P[1] * P[2] * (rhoX - R(0.5) * dot3(G.g, P));
+}
+
+// ------------------------------------------------------------------------------------------
+// one unit = the part of a tetrahedron's projection that falls in the tile [0, td) (tile frame)
+// acc(vx, vy, vz, value) receives every (corner, cell) contribution, in cell-volume units.
+// ------------------------------------------------------------------------------------------
+template <typename R, class Acc>
+CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* cnt) {
+    // ---- B: simplex vertices
+    for (int i = 0; i < 4; ++i) {
+        const int* v = G.cell[i];
+        if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1] && v[2] >= 0 && v[2] < td[2]) {
+            acc(v[0], v[1], v[2], tet_corner_B(G, i, v));
+            if (cnt) cnt->b++;
+        }
+    }
+    // ---- C: edges crossing cell faces
+    for (int e = 0; e < 6; ++e) {
+        int a, b, p, q;
+        tet_edge(e, a, b, p, q);
+        for (int k = 0; k < 3; ++k) {
+            int ca = G.cell[a][k], cb = G.cell[b][k];
+            if (ca == cb) continue;
+            int dirk = cb > ca ? 1 : -1;
+            int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
+            if (c0 < 0) c0 = 0;
+            if (c1 > td[k]) c1 = td[k];
+            if (c0 > c1) continue;
+            int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+            R ev[3];
+            for (int t = 0; t < 3; ++t) ev[t] = G.x[b][t] - G.x[a][t];
+            R rinv = R(1) / ev[k];
+            for (int c = c0; c <= c1; ++c) {
+                R t = (R(c) - G.x[a][k]) * rinv;
+                R X[3];
+                for (int w = 0; w < 3; ++w) X[w] = G.x[a][w] + t * ev[w];
+                X[k] = R(c);
+                int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X[j1]), dirk, cnt);
+                if (cj1 < 0 || cj1 >= td[j1]) continue;
+                int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X[j2]), dirk, cnt);
+                if (cj2 < 0 || cj2 >= td[j2]) continue;
+                R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+                for (int side = 0; side < 2; ++side) {
+                    int vk = side == 0 ? c - 1 : c;
+                    if (vk < 0 || vk >= td[k]) continue;
+                    int v[3];
+                    v[k] = vk;
+                    v[j1] = cj1;
+                    v[j2] = cj2;
+                    acc(v[0], v[1], v[2], tet_corner_C(G, e, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
+                    if (cnt) cnt->c++;
+                }
+            }
+        }
+    }
+    // ---- D: facets crossing cell edges, and A: grid nodes inside (scanned along x lines)
+    for (int l = 0; l < 3; ++l) {
+        int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+        int dj0 = G.lo[j] + 1 > 0 ? G.lo[j] + 1 : 0, dj1 = G.hi[j] < td[j] ? G.hi[j] : td[j];
+        int dk0 = G.lo[k] + 1 > 0 ? G.lo[k] + 1 : 0, dk1 = G.hi[k] < td[k] ? G.hi[k] : td[k];
+        for (int dj = dj0; dj <= dj1; ++dj)
+            for (int dk = dk0; dk <= dk1; ++dk) {
+                int s[6];
+                for (int e = 0; e < 6; ++e) {
+                    int a, b, p, q;
+                    tet_edge(e, a, b, p, q);
+                    s[e] = tet_side2(G, a, b, j, k, dj, dk, cnt);
+                }
+                int mlo = 0, mhi = -1, nhit = 0;
+                for (int f = 0; f < 4; ++f) {
+                    // facet f = (a < b < c): inside iff orient(ab), orient(bc), orient(ca) agree
+                    int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, cc = f == 3 ? 2 : 3;
+                    int sab = s[tet_edge_index(a, b)], sbc = s[tet_edge_index(b, cc)], sac = s[tet_edge_index(a, cc)];
+                    if (!(sab == sbc && sbc == -sac)) continue;
+                    ++nhit;
+                    const R* n = G.n[f];
+                    int va = f == 0 ? 1 : 0;
+                    R X[3];
+                    X[j] = R(dj);
+                    X[k] = R(dk);
+                    X[l] = G.x[va][l] - (n[j] * (R(dj) - G.x[va][j]) + n[k] * (R(dk) - G.x[va][k])) / n[l];
+                    int m = tet_facet_line_cell(G, f, l, j, k, dj, dk, (int)floor_r(X[l]), cnt);
+                    if (G.nE[f][l] > 0)
+                        mlo = m;  // entry: nodes above m are inside w.r.t. this facet
+                    else
+                        mhi = m;  // exit: nodes up to m are inside
+                    if (m < 0 || m >= td[l]) continue;
+                    R rhoX = rho_at(G, X);
+                    for (int oj = 0; oj < 2; ++oj)
+                        for (int ok = 0; ok < 2; ++ok) {
+                            int v[3];
+                            v[l] = m;
+                            v[j] = dj - 1 + oj;
+                            v[k] = dk - 1 + ok;
+                            if (v[j] < 0 || v[j] >= td[j] || v[k] < 0 || v[k] >= td[k]) continue;
+                            // cell above plane j (oj = 1) has inward normal +e_j there
+                            acc(v[0], v[1], v[2],
+                                tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), X, rhoX, v));
+                            if (cnt) cnt->d++;
+                        }
+                }
+                if (l != 0 || nhit != 2) continue;
+                int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
+                for (int cx = n0; cx <= n1; ++cx) {
+                    R X[3] = {R(cx), R(dj), R(dk)};
+                    R rhoX = rho_at(G, X);
+                    for (int o = 0; o < 8; ++o) {
+                        int v[3] = {cx - 1 + (o & 1), dj - 1 + ((o >> 1) & 1), dk - 1 + ((o >> 2) & 1)};
+                        if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1] || v[2] < 0 || v[2] >= td[2])
+                            continue;
+                        // node is the cell's upper corner along a when the cell index is node-1
+                        R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
+                        acc(v[0], v[1], v[2], tet_corner_A(G, X, rhoX, v, sg));
+                        if (cnt) cnt->a++;
+                    }
+                }
+            }
+    }
+}
+
+// ==========================================================================================
+// 2D
+// ==========================================================================================
+
+struct Tri {
+    i64 L[3][2];
+    double rho[3];
+    int cell[3][2];
+    int lo[2], hi[2];
+    int anchor[2];
+};
+
+template <typename R>
+struct TriGeo {
+    i64 Lt[3][2];
+    R x[3][2];
+    R n[3][2];    // unit inward normal of the edge opposite vertex k
+    i64 nE[3][2]; // exact normals
+    R g[2];
+    R rho[3];
+    R c[2], rhoc;
+    R B2;
+    int cell[3][2];
+    int lo[2], hi[2];
+};
+
+template <typename R>
+CDP_HD void tri_setup(const Tri& S, const int T[2], TriGeo<R>& G) {
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 2; ++a) {
+            G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
+            G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
+            G.cell[k][a] = S.cell[k][a] - T[a];
+        }
+    for (int a = 0; a < 2; ++a) {
+        G.lo[a] = S.lo[a] - T[a];
+        G.hi[a] = S.hi[a] - T[a];
+    }
+    // n_k = perp(x_{k+2} - x_{k+1}), perp(v) = (-v_y, v_x), for a positively oriented triangle
+    for (int k = 0; k < 3; ++k) {
+        int i1 = (k + 1) % 3, i2 = (k + 2) % 3;
+        i64 dx = G.Lt[i2][0] - G.Lt[i1][0], dy = G.Lt[i2][1] - G.Lt[i1][1];
+        G.nE[k][0] = -dy;
+        G.nE[k][1] = dx;
+        R nx = i64_to_real<R>(-dy, CDP_Q), ny = i64_to_real<R>(dx, CDP_Q);
+        R inv = rsqrt_r<R>(nx * nx + ny * ny);
+        G.n[k][0] = nx * inv;
+        G.n[k][1] = ny * inv;
+    }
+    i64 e1x = G.Lt[1][0] - G.Lt[0][0], e1y = G.Lt[1][1] - G.Lt[0][1];
+    i64 e2x = G.Lt[2][0] - G.Lt[0][0], e2y = G.Lt[2][1] - G.Lt[0][1];
+    i128 Dq = mul64(e1x, e2y) - mul64(e1y, e2x);
+    double D = i128_to_real<double>(Dq, 2 * CDP_Q);
+    for (int k = 0; k < 3; ++k) G.rho[k] = (R)S.rho[k];
+    R d1 = G.rho[1] - G.rho[0], d2 = G.rho[2] - G.rho[0];
+    R ex1 = i64_to_real<R>(e1x, CDP_Q), ey1 = i64_to_real<R>(e1y, CDP_Q);
+    R ex2 = i64_to_real<R>(e2x, CDP_Q), ey2 = i64_to_real<R>(e2y, CDP_Q);
+    R invD = R(1.0 / D);
+    G.g[0] = (d1 * ey2 - d2 * ey1) * invD;
+    G.g[1] = (d2 * ex1 - d1 * ex2) * invD;
+    for (int a = 0; a < 2; ++a) G.c[a] = (G.x[0][a] + G.x[1][a] + G.x[2][a]) * R(1.0 / 3.0);
+    G.rhoc = (G.rho[0] + G.rho[1] + G.rho[2]) * R(1.0 / 3.0);
+    int m = 1;
+    for (int a = 0; a < 2; ++a) {
+        int v = G.lo[a] < 0 ? -G.lo[a] : G.lo[a];
+        int w = G.hi[a] + 1 < 0 ? -(G.hi[a] + 1) : G.hi[a] + 1;
+        m = v > m ? v : m;
+        m = w > m ? w : m;
+    }
+    R Rm = R(m + 1);
+    G.B2 = Eps<R>::k2 * Rm * Rm;
+}
+
+template <typename R>
+CDP_HD int tri_side2(const TriGeo<R>& G, int i, int j, int pu, int pv, UnitCounts* cnt) {
+    R du = G.x[j][0] - G.x[i][0], dv = G.x[j][1] - G.x[i][1];
+    R val = du * (R(pv) - G.x[i][1]) - dv * (R(pu) - G.x[i][0]);
+    if (val > G.B2) return 1;
+    if (val < -G.B2) return -1;
+    if (cnt) cnt->exact++;
+    return side2_exact(G.Lt[i][0], G.Lt[i][1], G.Lt[j][0], G.Lt[j][1], (i64)pu << CDP_Q, (i64)pv << CDP_Q);
+}
+
+// sign(X_j - d) for the crossing of edge (a -> b) with the line x_k = c (j = 1 - k)
+template <typename R>
+CDP_HD int tri_cross_side(const TriGeo<R>& G, int a, int b, int k, int c, int d, int dirk, UnitCounts* cnt) {
+    // j < k: orient2d(a, b, (d, c)); j > k: -orient2d(a, b, (c, d)) in (x, y) order
+    int s = k == 1 ? tri_side2(G, a, b, d, c, cnt) : -tri_side2(G, a, b, c, d, cnt);
+    return dirk * s;
+}
+
+template <typename R>
+CDP_HD int tri_cross_cell(const TriGeo<R>& G, int a, int b, int k, int c, int guess, int dirk, UnitCounts* cnt) {
+    int j = 1 - k;
+    int lo = G.cell[a][j] < G.cell[b][j] ? G.cell[a][j] : G.cell[b][j];
+    int hi = G.cell[a][j] < G.cell[b][j] ? G.cell[b][j] : G.cell[a][j];
+    int d = guess < lo ? lo : (guess > hi ? hi : guess);
+    for (int it = 0; it <= hi - lo + 1; ++it) {
+        if (d > lo && tri_cross_side(G, a, b, k, c, d, dirk, cnt) < 0) {
+            --d;
+            continue;
+        }
+        if (d < hi && tri_cross_side(G, a, b, k, c, d + 1, dirk, cnt) > 0) {
+            ++d;
+            continue;
+        }
+        break;
+    }
+    return d;
+}
+
+template <typename R>
+CDP_HD void tri_origin(const TriGeo<R>& G, const int v[2], R O[2]) {
+    for (int a = 0; a < 2; ++a) O[a] = clamp_r(G.c[a], R(v[a]), R(v[a] + 1));
+}
+
+// B: vertex i in cell v
+template <typename R>
+CDP_HD R tri_corner_B(const TriGeo<R>& G, int i, const int v[2]) {
+    R O[2], P[2];
+    tri_origin(G, v, O);
+    P[0] = G.x[i][0] - O[0];
+    P[1] = G.x[i][1] - O[1];
+    R s = 0;
+    for (int j = 0; j < 3; ++j) {
+        if (j == i) continue;
+        int k = 3 - i - j;  // edge (i, j) is opposite vertex k
+        R T[2] = {i64_to_real<R>(G.Lt[j][0] - G.Lt[i][0], CDP_Q), i64_to_real<R>(G.Lt[j][1] - G.Lt[i][1], CDP_Q)};
+        R inv = rsqrt_r<R>(T[0] * T[0] + T[1] * T[1]);
+        T[0] *= inv;
+        T[1] *= inv;
+        s += trip2(P, T, G.n[k], G.rho[i], G.g);
+    }
+    return R(0.5) * s;
+}
+
+// C: edge (a, b) (opposite o) crossing the grid line x_k = X_k; cell on side sigma
+template <typename R>
+CDP_HD R tri_corner_C(const TriGeo<R>& G, int a, int b, int o, int k, int dirk, R sigma, const R X[2], R rhoX,
+                      const int v[2]) {
+    int j = 1 - k;
+    R O[2], P[2];
+    tri_origin(G, v, O);
+    P[0] = X[0] - O[0];
+    P[1] = X[1] - O[1];
+    R T[2] = {i64_to_real<R>(G.Lt[b][0] - G.Lt[a][0], CDP_Q), i64_to_real<R>(G.Lt[b][1] - G.Lt[a][1], CDP_Q)};
+    R inv = rsqrt_r<R>(T[0] * T[0] + T[1] * T[1]) * sigma * R(dirk);
+    T[0] *= inv;
+    T[1] *= inv;
+    R s = trip2(P, T, G.n[o], rhoX, G.g);
+    R T2[2] = {0, 0}, N2[2] = {0, 0};
+    T2[j] = G.nE[o][j] > 0 ? R(1) : R(-1);  // along the grid line, into the triangle
+    N2[k] = sigma;                           // inward normal of the cell side
+    s += trip2(P, T2, N2, rhoX, G.g);
+    return R(0.5) * s;
+}
+
+template <typename R, class Acc>
+CDP_HD void tri_unit(const TriGeo<R>& G, const int td[2], Acc& acc, UnitCounts* cnt) {
+    for (int i = 0; i < 3; ++i) {
+        const int* v = G.cell[i];
+        if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1]) {
+            acc(v[0], v[1], 0, tri_corner_B(G, i, v));
+            if (cnt) cnt->b++;
+        }
+    }
+    for (int o = 0; o < 3; ++o) {
+        int a = o == 0 ? 1 : 0, b = o == 2 ? 1 : 2;  // edge opposite o, a < b
+        for (int k = 0; k < 2; ++k) {
+            int ca = G.cell[a][k], cb = G.cell[b][k];
+            if (ca == cb) continue;
+            int j = 1 - k;
+            int dirk = cb > ca ? 1 : -1;
+            int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
+            // rows along x (k = 1) are needed over the whole tile for the A scan; columns only inside
+            if (c0 < 0) c0 = 0;
+            if (c1 > td[k]) c1 = td[k];
+            R ev[2] = {G.x[b][0] - G.x[a][0], G.x[b][1] - G.x[a][1]};
+            R rinv = R(1) / ev[k];
+            for (int c = c0; c <= c1; ++c) {
+                R t = (R(c) - G.x[a][k]) * rinv;
+                R X[2];
+                X[j] = G.x[a][j] + t * ev[j];
+                X[k] = R(c);
+                int cj = tri_cross_cell(G, a, b, k, c, (int)floor_r(X[j]), dirk, cnt);
+                if (cj < 0 || cj >= td[j]) continue;
+                R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+                for (int side = 0; side < 2; ++side) {
+                    int vk = side == 0 ? c - 1 : c;
+                    if (vk < 0 || vk >= td[k]) continue;
+                    int v[2];
+                    v[k] = vk;
+                    v[j] = cj;
+                    acc(v[0], v[1], 0, tri_corner_C(G, a, b, o, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
+                    if (cnt) cnt->c++;
+                }
+            }
+        }
+    }
+    // A: nodes inside, scanned along rows y = dy
+    int dy0 = G.lo[1] + 1 > 0 ? G.lo[1] + 1 : 0, dy1 = G.hi[1] < td[1] ? G.hi[1] : td[1];
+    for (int dy = dy0; dy <= dy1; ++dy) {
+        int mlo = 0, mhi = -1, nhit = 0;
+        for (int o = 0; o < 3; ++o) {
+            int a = o == 0 ? 1 : 0, b = o == 2 ? 1 : 2;
+            int ca = G.cell[a][1], cb = G.cell[b][1];
+            int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
+            if (dy < c0 || dy > c1) continue;
+            int dirk = cb > ca ? 1 : -1;
+            R t = (R(dy) - G.x[a][1]) / (G.x[b][1] - G.x[a][1]);
+            R xx = G.x[a][0] + t * (G.x[b][0] - G.x[a][0]);
+            int m = tri_cross_cell(G, a, b, 1, dy, (int)floor_r(xx), dirk, cnt);
+            ++nhit;
+            if (G.nE[o][0] > 0)
+                mlo = m;
+            else
+                mhi = m;
+        }
+        if (nhit != 2) continue;
+        int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
+        for (int cx = n0; cx <= n1; ++cx) {
+            R X[2] = {R(cx), R(dy)};
+            R rhoX = G.rhoc + G.g[0] * (X[0] - G.c[0]) + G.g[1] * (X[1] - G.c[1]);
+            for (int o = 0; o < 4; ++o) {
+                int v[2] = {cx - 1 + (o & 1), dy - 1 + ((o >> 1) & 1)};
+                if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1]) continue;
+                R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1);
+                R O[2], P[2];
+                tri_origin(G, v, O);
+                P[0] = X[0] - O[0];
+                P[1] = X[1] - O[1];
+                acc(v[0], v[1], 0, sg * P[0] * P[1] * (rhoX - R(0.5) * (G.g[0] * P[0] + G.g[1] * P[1])));
+                if (cnt) cnt->a++;
+            }
+        }
+    }
+}
+
+}  // namespace cdp

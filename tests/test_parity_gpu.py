@@ -1,0 +1,171 @@
+"""Parity of the CUDA projection (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances (the stated accuracy targets of the two arithmetic paths):
+  FP64 path       max |m_gpu - m_oracle| / max m_oracle <= 1e-11, total mass rel. error <= 1e-12
+  FP32-mixed path max |m_gpu - m_oracle| / max m_oracle <= 1e-5
+The combinatorial decisions (which corners exist) are exact integer predicates, so both paths
+must also report identical corner counts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_07720_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-11, 1: 1e-5}
+TOTAL_TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def proj():
+    import paper_1509_07720_gb300 as pkg
+    from paper_1509_07720_gb300 import build
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build_library()
+    p = pkg.Projector(0)
+    yield p
+    p.close()
+
+
+def _dev(mesh):
+    d = torch.device("cuda:0")
+    return (torch.from_numpy(np.ascontiguousarray(mesh.pos)).to(d),
+            torch.from_numpy(np.ascontiguousarray(mesh.simplices)).to(d),
+            torch.from_numpy(np.ascontiguousarray(mesh.rho)).to(d))
+
+
+def _run(proj, mesh, prec, stats=False):
+    pos, simp, rho = _dev(mesh)
+    res = proj.project(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, mesh.periodic, precision=prec,
+                       stats=stats)
+    torch.cuda.synchronize()
+    if stats:
+        return res[0].cpu().numpy(), res[1]
+    proj.check()
+    return res.cpu().numpy()
+
+
+def _cases():
+    rng = np.random.default_rng(7)
+    q8, t8 = mg.kuhn_mesh_3d(8)
+    qb, tb = mg.kuhn_box_mesh_3d(4)
+    return {
+        "c1a": mg.make_config("c1a"),
+        "c1b": mg.make_config("c1b"),
+        "c2_16": mg.make_config("c2", 16),
+        "c2": mg.make_config("c2"),
+        "rand3d_small": mg.random_simplices(3, 500, 16, 0.7, rng),
+        "rand3d_mid": mg.random_simplices(3, 500, 16, 2.5, rng),
+        "rand3d_tiled": mg.random_simplices(3, 40, 32, 9.0, rng),
+        "rand3d_lognormal1": mg.random_simplices(3, 300, 16, 3.0, rng, rho_sigma=1.0),
+        "rand2d": mg.random_simplices(2, 800, 32, 3.0, rng),
+        "rand2d_tiled": mg.random_simplices(2, 60, 64, 20.0, rng),
+        "aligned_kuhn_16": mg.Mesh(q8, t8, np.ones(q8.shape[1]), (16,) * 3, (0.0,) * 3, (1.0,) * 3, True),
+        "aligned_kuhn_8": mg.Mesh(q8, t8, np.ones(q8.shape[1]), (8,) * 3, (0.0,) * 3, (1.0,) * 3, True),
+        "box_linear_rho": mg.Mesh(qb * 0.8 + 0.1, tb, 1.0 + qb[0] - 0.5 * qb[2], (12, 10, 9), (0.0,) * 3,
+                                  (1.0,) * 3, False),
+        "ragged_grid": mg.Mesh(*(lambda m: (m.pos, m.simplices, m.rho))(mg.make_config("c2", 8)), (29, 31, 33),
+                               (0.0,) * 3, (1.0,) * 3, True),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_parity(proj, name, prec):
+    mesh = CASES[name]
+    ref = oracle.project(mesh)
+    got = _run(proj, mesh, prec)
+    scale = np.max(np.abs(ref))
+    err = np.max(np.abs(got - ref)) / scale
+    assert err <= TOL[prec], f"{name}: max rel error {err:.3e}"
+    if prec == 0:
+        tot = abs(got.sum() - ref.sum()) / abs(ref.sum())
+        assert tot <= TOTAL_TOL_FP64, f"{name}: total mass rel error {tot:.3e}"
+
+
+@pytest.mark.parametrize("name", ["c2", "rand3d_tiled", "aligned_kuhn_16", "c1b", "rand2d_tiled"])
+def test_same_decisions_both_precisions(proj, name):
+    mesh = CASES[name]
+    _, s64 = _run(proj, mesh, 0, stats=True)
+    _, s32 = _run(proj, mesh, 1, stats=True)
+    for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell", "n_small", "n_large",
+              "n_large_tiles", "n_zero_volume"):
+        assert s64[k] == s32[k], k
+    assert s64["error_flags"] == 0
+
+
+def test_total_mass_against_simplex_masses(proj):
+    mesh = CASES["c2"]
+    ref = oracle.simplex_mass(mesh).sum()
+    got = _run(proj, mesh, 0)
+    assert abs(got.sum() - ref) <= TOTAL_TOL_FP64 * ref
+
+
+def test_empty_and_accumulate(proj):
+    mesh = CASES["c2_16"]
+    pos, simp, rho = _dev(mesh)
+    out = proj.project(pos, simp[:0].contiguous(), rho, mesh.grid)
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0
+    a = proj.project(pos, simp, rho, mesh.grid, precision=0)
+    b = a.clone()
+    proj.project(pos, simp, rho, mesh.grid, precision=0, out=b, accumulate=True)
+    torch.cuda.synchronize()
+    assert torch.allclose(b, 2 * a, rtol=1e-14, atol=0)
+
+
+def test_device_detected_errors(proj):
+    import paper_1509_07720_gb300 as pkg
+
+    mesh = CASES["rand3d_small"]
+    pos, simp, rho = _dev(mesh)
+    bad = simp.clone()
+    bad[3, 2] = mesh.n_verts + 5
+    with pytest.raises(pkg.CdpError) as e:
+        proj.project(pos, bad, rho, mesh.grid, stats=True)
+    assert e.value.code == -2
+    nanpos = pos.clone()
+    nanpos[0, 7] = float("nan")
+    with pytest.raises(pkg.CdpError) as e:
+        proj.project(nanpos, simp, rho, mesh.grid)
+        proj.check()
+    assert e.value.code == -3
+    proj.check()  # cleared
+
+
+def test_extent_error(proj):
+    import paper_1509_07720_gb300 as pkg
+
+    pos = torch.tensor([[0.125, 0.625, 0.25], [0.125, 0.125, 0.25]], dtype=torch.float64, device="cuda:0")
+    simp = torch.tensor([[0, 1, 2]], dtype=torch.int32, device="cuda:0")
+    rho = torch.ones(3, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(pkg.CdpError) as e:
+        proj.project(pos, simp, rho, (4, 4), stats=True)
+    assert e.value.code == -4
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
+def test_headline_workload_sampled(proj, prec):
+    """Full-size 128^3 Kuhn mesh (12.6M tets) on 256^3, in the benchmark's launch configuration:
+    sampled cells against the oracle cell by cell, and the total mass against the simplex masses."""
+    mesh = mg.make_config("c3")
+    got = _run(proj, mesh, prec)
+    rng = np.random.default_rng(99)
+    cells = rng.choice(got.size, 256, replace=False)
+    # also the densest cells
+    cells = np.unique(np.concatenate([cells, np.argsort(got.ravel())[-32:]]))
+    ref = oracle.project_cells(mesh, cells)
+    scale = float(np.max(got))
+    err = np.max(np.abs(got.ravel()[cells] - ref)) / scale
+    assert err <= TOL[prec], f"sampled max rel error {err:.3e}"
+    tot = oracle.simplex_mass(mesh).sum()
+    rel = abs(got.sum() - tot) / tot
+    assert rel <= (TOTAL_TOL_FP64 if prec == 0 else 1e-6), f"total mass rel error {rel:.3e}"

@@ -67,7 +67,7 @@ typedef struct cdp_ctx cdp_ctx;
  *   simplices    device, int32[n_simplices * (dim + 1)]: vertex indices, one row per simplex;
  *                any vertex order and orientation (inverted simplices are fine, mass is +|V| rho)
  *   rho          device, double[n_verts]: density at every vertex (linear inside each simplex)
- *   grid[a]      cells per axis (1 <= grid[a] <= 2^20), a < dim
+ *   grid[a]      cells per axis (1 <= grid[a] <= 2^20, at most 2^32 cells in total), a < dim
  *   box_lo/len   box origin and side lengths (len > 0)
  *   periodic     1: the box is a torus, every simplex is taken at the minimal image of its
  *                vertex 0 (every vertex offset must be < half a box length) and cells wrap;
@@ -91,7 +91,7 @@ typedef struct {
 typedef struct {
     uint64_t n_zero_volume;   /* simplices of zero volume (no contribution) */
     uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
-    uint64_t n_small;         /* simplices projected by one thread (bounding box <= 64 cells) */
+    uint64_t n_small;         /* simplices projected by one thread (bounding box <= 512 cells) */
     uint64_t n_large;         /* simplices split into tiles */
     uint64_t n_large_tiles;   /* tiles processed for them */
     uint64_t corners_a;       /* (corner, cell) incidences of type A: grid node inside a simplex */

@@ -87,7 +87,7 @@ int check_problem(const cdp_problem* p) {
     long long cells = 1;
     for (int a = 0; a < p->dim; ++a) {
         cells *= p->grid[a];
-        if (cells > ((long long)1 << 40)) return CDP_ERR_ARG;
+        if (cells > ((long long)1 << 32)) return CDP_ERR_ARG;
     }
     return CDP_OK;
 }
@@ -185,9 +185,9 @@ int cdp_create(cdp_ctx** out, int device) {
         delete c;
         return CDP_ERR_CUDA;
     }
-    // resident blocks per SM, limited by the 64 slots x block of shared memory
-    c->blocks_small[0] = c->blocks_big[0] = 3;  // fp64: 64 KB per block
-    c->blocks_small[1] = c->blocks_big[1] = 6;  // fp32: 32 KB per block
+    // resident blocks per SM, limited by the per-thread piece tables in shared memory
+    c->blocks_small[0] = c->blocks_big[0] = 2;  // fp64: 96 KB per block
+    c->blocks_small[1] = c->blocks_big[1] = 3;  // fp32: 64 KB per block
     if (cudaMalloc(&c->ctr, sizeof(cdp::Counters)) != cudaSuccess ||
         cudaMalloc(&c->stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess ||
         cudaMallocHost(&c->h_ctr, sizeof(cdp::Counters)) != cudaSuccess ||
@@ -277,6 +277,7 @@ int cdp_project(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate,
             L.g.inv_h[a] = 1.0;
         }
     }
+    L.g.cell_volume = L.cellvol;
     L.nv = p->n_verts;
     L.ns = p->n_simplices;
     L.simplices = p->simplices;

@@ -183,6 +183,7 @@ CDP_HD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
     cross_exact(e3, e1, G.nE[2]);  // (x3-x0) x (x1-x0)
     cross_exact(e1, e2, G.nE[3]);  // (x1-x0) x (x2-x0)
     R nr[4][3];
+    #pragma unroll
     for (int f = 0; f < 4; ++f) {
         for (int a = 0; a < 3; ++a) nr[f][a] = i128_to_real<R>(G.nE[f][a], 2 * CDP_Q);
         R inv = rsqrt_r<R>(dot3(nr[f], nr[f]));
@@ -327,6 +328,7 @@ CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const int v[3]) {
     piece_origin(G, v, O);
     for (int a = 0; a < 3; ++a) P[a] = G.x[i][a] - O[a];
     R s = 0;
+    #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j == i) continue;
         int a = i < j ? i : j, b = i < j ? j : i;
@@ -334,6 +336,7 @@ CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const int v[3]) {
         edge_unit(G, a, b, ev);
         R sg = i == a ? R(1) : R(-1);
         for (int t = 0; t < 3; ++t) T[t] = sg * ev[t];
+        #pragma unroll
         for (int f = 0; f < 4; ++f) {
             if (f == i || f == j) continue;
             int r = 6 - i - j - f;  // third vertex of facet f
@@ -374,6 +377,7 @@ CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const
     R lam = R(-parity4(a, b, p, q)) * R(dirk);
     R Bk[3] = {0, 0, 0};
     Bk[k] = sigma;
+    #pragma unroll
     for (int w = 0; w < 2; ++w) {
         const R* n = G.n[w == 0 ? p : q];
         R su = w == 0 ? lam : -lam;
@@ -468,6 +472,7 @@ CDP_HD R tet_corner_A(const TetGeo<R>& G, const R X[3], R rhoX, const int v[3], 
 template <typename R, class Acc>
 CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* cnt) {
     // ---- B: simplex vertices
+    #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int* v = G.cell[i];
         if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1] && v[2] >= 0 && v[2] < td[2]) {
@@ -476,9 +481,11 @@ CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* 
         }
     }
     // ---- C: edges crossing cell faces
+    #pragma unroll
     for (int e = 0; e < 6; ++e) {
         int a, b, p, q;
         tet_edge(e, a, b, p, q);
+        #pragma unroll
         for (int k = 0; k < 3; ++k) {
             int ca = G.cell[a][k], cb = G.cell[b][k];
             if (ca == cb) continue;
@@ -515,6 +522,7 @@ CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* 
         }
     }
     // ---- D: facets crossing cell edges, and A: grid nodes inside (scanned along x lines)
+    #pragma unroll
     for (int l = 0; l < 3; ++l) {
         int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
         int dj0 = G.lo[j] + 1 > 0 ? G.lo[j] + 1 : 0, dj1 = G.hi[j] < td[j] ? G.hi[j] : td[j];
@@ -522,12 +530,14 @@ CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* 
         for (int dj = dj0; dj <= dj1; ++dj)
             for (int dk = dk0; dk <= dk1; ++dk) {
                 int s[6];
+                #pragma unroll
                 for (int e = 0; e < 6; ++e) {
                     int a, b, p, q;
                     tet_edge(e, a, b, p, q);
                     s[e] = tet_side2(G, a, b, j, k, dj, dk, cnt);
                 }
                 int mlo = 0, mhi = -1, nhit = 0;
+                #pragma unroll
                 for (int f = 0; f < 4; ++f) {
                     // facet f = (a < b < c): inside iff orient(ab), orient(bc), orient(ca) agree
                     int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, cc = f == 3 ? 2 : 3;

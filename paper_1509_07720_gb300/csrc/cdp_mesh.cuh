@@ -23,7 +23,9 @@ struct GridDesc {
     int dim;
     int n[3];
     double lo[3];
-    double inv_h[3];  // cells per unit length
+    double inv_h[3];    // cells per unit length
+    double cell_volume; // world volume of one cell: densities are stored premultiplied by it, so
+                        // every contribution (computed in cell units) is directly a world mass
     int periodic;
 };
 
@@ -52,8 +54,8 @@ CDP_HD unsigned vertex_to_fixed(const GridDesc& g, const double p[3], double rho
         }
         out.x[a] = X;
     }
-    out.rho = rho;
-    if (!(rho == rho)) flag |= CDP_FLAG_NAN;
+    out.rho = rho * g.cell_volume;
+    if (!(rho == rho) || rho > 1.0e300 || rho < -1.0e300) flag |= CDP_FLAG_NAN;
     return flag;
 }
 
@@ -160,7 +162,7 @@ CDP_HD unsigned canon_tri(const GridDesc& g, const VertexRec* v[3], Tri& S) {
     return 0;
 }
 
-// Exact mass (cell-volume units) of a tetrahedron lying in one cell: |V| mean(rho), in double.
+// Exact mass of a tetrahedron, |V| mean(rho) (densities premultiplied by the cell volume), in double.
 CDP_HD double tet_mass_cells(const Tet& S) {
     i64 e1[3], e2[3], e3[3];
     for (int a = 0; a < 3; ++a) {

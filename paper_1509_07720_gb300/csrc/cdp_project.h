@@ -7,10 +7,9 @@
 
 namespace cdp {
 
-constexpr int CDP_BLOCK = 128;        // threads per block of the projection kernels
-constexpr int CDP_SMALL_CELLS = 64;   // bounding boxes up to this many cells: one thread, one unit
-constexpr int CDP_TILE = 4;           // tile edge (cells) for large tetrahedra: 4^3 = 64 slots
-constexpr int CDP_TILE2 = 8;          // tile edge for large triangles: 8^2 = 64 slots
+constexpr int CDP_BLOCK = 128;             // threads per block of the projection kernels
+constexpr int CDP_ONE_THREAD_CELLS = 512;  // bounding boxes up to this many cells: one thread
+constexpr int CDP_TILE = 8;                // tile edge (cells) of the larger simplices
 
 // Per-call device counters (zeroed at the start of every projection).
 struct Counters {

@@ -121,6 +121,60 @@ CDP_API void cdp_destroy(cdp_ctx* ctx);
 CDP_API int cdp_project(cdp_ctx* ctx, const cdp_problem* prob, int precision, int accumulate, void* stream,
                 cdp_stats* stats);
 
+/* Several projections in one call, enqueued back to back on `stream` (each as cdp_project with
+ * accumulate = 0 and no stats).  The scratch is sized once for the largest problem first. */
+CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, int precision, void* stream);
+
+/* Vertex densities from simplex masses (Sect. 4.4): rho_out[j] = sum of simplex_mass[i] over the
+ * simplices incident to vertex j divided by the sum of their volumes |V_i| (world units,
+ * periodic minimal image when prob->periodic).  Uses dim, n_verts, n_simplices, pos, simplices,
+ * box_len and periodic of `prob` (its rho and cell_mass are ignored).  simplex_mass: device
+ * double[n_simplices]; rho_out: device double[n_verts] (0 for a vertex with no simplex).
+ * Scratch: 16 bytes per vertex. */
+CDP_API int cdp_vertex_density(cdp_ctx* ctx, const cdp_problem* prob, const double* simplex_mass, double* rho_out,
+                               void* stream);
+
+/* Periodic FFT Poisson solve (Sect. 4.4): laplacian(phi) = four_pi_G (rho - mean(rho)) with
+ * rho = cell_mass / cell volume, continuous Green function -1/k^2 (k = 2 pi n / L), zero mode
+ * removed.  cell_mass, phi: device double[prod(grid)] (C order, cell-centred); phi may alias
+ * cell_mass.  cuFFT plans and the spectrum buffer are cached in the context per grid shape. */
+CDP_API int cdp_poisson(cdp_ctx* ctx, int dim, const int32_t grid[3], const double box_len[3], double four_pi_G,
+                        const double* cell_mass, double* phi, void* stream);
+
+/* Acceleration at n points (Sect. 4.4): acc = - sum over the 3^dim nearest cell centres of the
+ * triangular-shaped-cloud weight times the 4-point central difference
+ * (8 (phi[i+1] - phi[i-1]) - (phi[i+2] - phi[i-2])) / (12 h) of phi there (periodic grid).
+ * pos[a], acc[a]: device double[n], a < dim. */
+CDP_API int cdp_force(cdp_ctx* ctx, int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3],
+                      const double* phi, int64_t n, const double* const pos[3], double* const acc[3], void* stream);
+
+/* Drift (eqs. drift1, drift2): pos[a] += vel[a] * dt, wrapped into [box_lo, box_lo + box_len)
+ * when periodic.  Kick (eq. kick): vel[a] += acc[a] * dt.  Device double[n] arrays, a < dim. */
+CDP_API int cdp_drift(cdp_ctx* ctx, int dim, int64_t n, double* const pos[3], const double* const vel[3], double dt,
+                      const double box_lo[3], const double box_len[3], int periodic, void* stream);
+CDP_API int cdp_kick(cdp_ctx* ctx, int dim, int64_t n, double* const vel[3], const double* const acc[3], double dt,
+                     void* stream);
+
+/* One mesh of a batched time step.  mesh.pos is updated in place by the drifts (the pointers
+ * are written through), mesh.rho receives the vertex densities, mesh.cell_mass the projection;
+ * the box must be periodic. */
+typedef struct {
+    cdp_problem mesh;
+    double* vel[3];             /* device double[n_verts]: velocities, updated by the kick */
+    double* acc[3];             /* device double[n_verts]: accelerations, written */
+    const double* simplex_mass; /* device double[n_simplices]: fixed masses of the simplices */
+    double* phi;                /* device double[prod(grid)]: potential, written */
+} cdp_step_problem;
+
+/* One time step of n independent meshes (Sect. 4, steps (ii)-(iv)): drift dt/2 (eq. drift1),
+ * vertex densities from the simplex masses, exact projection, FFT Poisson solve, force at the
+ * vertices, kick dt (eq. kick), drift dt/2 (eq. drift2).  use_graph != 0: the first call with a
+ * given argument array captures the whole sequence into a CUDA graph owned by the context and
+ * every later call with byte-identical arguments (dt may differ) replays it in one launch.  The
+ * first call also creates the FFT plans and sizes the scratch outside the capture. */
+CDP_API int cdp_step_batched(cdp_ctx* ctx, const cdp_step_problem* probs, int n, int precision, double dt,
+                             double four_pi_G, int use_graph, void* stream);
+
 /* Synchronise `stream` and return the first error the kernels recorded since the last check
  * (and clear it). */
 CDP_API int cdp_check(cdp_ctx* ctx, void* stream);

@@ -17,7 +17,8 @@ import os
 __all__ = [
     "CDP_FP64", "CDP_FP32_MIXED", "CdpError", "cdp_problem", "cdp_stats", "load_library", "library_path",
     "cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror", "cdp_timing_enable",
-    "cdp_timing_read", "Projector", "EXPORTED_SYMBOLS",
+    "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density", "cdp_poisson", "cdp_force", "cdp_drift",
+    "cdp_kick", "cdp_step_batched", "cdp_step_problem", "Projector", "EXPORTED_SYMBOLS",
 ]
 
 CDP_FP64 = 0
@@ -29,7 +30,8 @@ _lib = None
 
 # every symbol the header declares (checked by the CPU tests)
 EXPORTED_SYMBOLS = ("cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror",
-                    "cdp_timing_enable", "cdp_timing_read")
+                    "cdp_timing_enable", "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density",
+                    "cdp_poisson", "cdp_force", "cdp_drift", "cdp_kick", "cdp_step_batched")
 
 
 class CdpError(RuntimeError):
@@ -51,6 +53,16 @@ class cdp_problem(ctypes.Structure):
         ("box_len", ctypes.c_double * 3),
         ("periodic", ctypes.c_int),
         ("cell_mass", ctypes.c_void_p),
+    ]
+
+
+class cdp_step_problem(ctypes.Structure):
+    _fields_ = [
+        ("mesh", cdp_problem),
+        ("vel", ctypes.c_void_p * 3),
+        ("acc", ctypes.c_void_p * 3),
+        ("simplex_mass", ctypes.c_void_p),
+        ("phi", ctypes.c_void_p),
     ]
 
 
@@ -93,6 +105,25 @@ def load_library(path: str | None = None):
     lib.cdp_timing_enable.restype = ctypes.c_int
     lib.cdp_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.cdp_timing_read.restype = ctypes.c_int
+    dp = ctypes.c_void_p
+    arr3 = ctypes.c_void_p * 3
+    lib.cdp_project_batched.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_int, vp]
+    lib.cdp_project_batched.restype = ctypes.c_int
+    lib.cdp_vertex_density.argtypes = [vp, ctypes.POINTER(cdp_problem), dp, dp, vp]
+    lib.cdp_vertex_density.restype = ctypes.c_int
+    lib.cdp_poisson.argtypes = [vp, ctypes.c_int, ctypes.c_int32 * 3, ctypes.c_double * 3, ctypes.c_double, dp, dp, vp]
+    lib.cdp_poisson.restype = ctypes.c_int
+    lib.cdp_force.argtypes = [vp, ctypes.c_int, ctypes.c_int32 * 3, ctypes.c_double * 3, ctypes.c_double * 3, dp,
+                              ctypes.c_int64, arr3, arr3, vp]
+    lib.cdp_force.restype = ctypes.c_int
+    lib.cdp_drift.argtypes = [vp, ctypes.c_int, ctypes.c_int64, arr3, arr3, ctypes.c_double, ctypes.c_double * 3,
+                              ctypes.c_double * 3, ctypes.c_int, vp]
+    lib.cdp_drift.restype = ctypes.c_int
+    lib.cdp_kick.argtypes = [vp, ctypes.c_int, ctypes.c_int64, arr3, arr3, ctypes.c_double, vp]
+    lib.cdp_kick.restype = ctypes.c_int
+    lib.cdp_step_batched.argtypes = [vp, ctypes.POINTER(cdp_step_problem), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    lib.cdp_step_batched.restype = ctypes.c_int
     lib.cdp_strerror.argtypes = [ctypes.c_int]
     lib.cdp_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -144,6 +175,65 @@ def cdp_timing_read(ctx):
     if rc < 0:
         raise CdpError(rc, "cdp_timing_read")
     return list(buf), int(calls.value)
+
+
+def _i3(v):
+    a = (ctypes.c_int32 * 3)()
+    for i, x in enumerate(v):
+        a[i] = int(x)
+    return a
+
+
+def _d3(v):
+    a = (ctypes.c_double * 3)()
+    for i, x in enumerate(v):
+        a[i] = float(x)
+    return a
+
+
+def _p3(ts):
+    a = (ctypes.c_void_p * 3)()
+    for i, t in enumerate(ts):
+        a[i] = t.data_ptr() if t is not None else None
+    return a
+
+
+def cdp_project_batched(ctx, probs, precision: int, stream: int = 0) -> int:
+    arr = (cdp_problem * len(probs))(*probs)
+    return load_library().cdp_project_batched(ctx, arr, len(probs), int(precision), ctypes.c_void_p(stream))
+
+
+def cdp_vertex_density(ctx, prob: cdp_problem, simplex_mass_ptr: int, rho_out_ptr: int, stream: int = 0) -> int:
+    return load_library().cdp_vertex_density(ctx, ctypes.byref(prob), ctypes.c_void_p(simplex_mass_ptr),
+                                             ctypes.c_void_p(rho_out_ptr), ctypes.c_void_p(stream))
+
+
+def cdp_poisson(ctx, dim, grid, box_len, four_pi_G, mass_ptr, phi_ptr, stream: int = 0) -> int:
+    return load_library().cdp_poisson(ctx, int(dim), _i3(grid), _d3(box_len), float(four_pi_G),
+                                      ctypes.c_void_p(mass_ptr), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(stream))
+
+
+def cdp_force(ctx, dim, grid, box_lo, box_len, phi_ptr, n, pos, acc, stream: int = 0) -> int:
+    return load_library().cdp_force(ctx, int(dim), _i3(grid), _d3(box_lo), _d3(box_len), ctypes.c_void_p(phi_ptr),
+                                    int(n), _p3(pos), _p3(acc), ctypes.c_void_p(stream))
+
+
+def cdp_drift(ctx, dim, n, pos, vel, dt, box_lo, box_len, periodic, stream: int = 0) -> int:
+    return load_library().cdp_drift(ctx, int(dim), int(n), _p3(pos), _p3(vel), float(dt), _d3(box_lo),
+                                    _d3(box_len), int(bool(periodic)), ctypes.c_void_p(stream))
+
+
+def cdp_kick(ctx, dim, n, vel, acc, dt, stream: int = 0) -> int:
+    return load_library().cdp_kick(ctx, int(dim), int(n), _p3(vel), _p3(acc), float(dt), ctypes.c_void_p(stream))
+
+
+def cdp_step_batched(ctx, steps, precision: int, dt: float, four_pi_G: float, use_graph: bool,
+                     stream: int = 0) -> int:
+    """steps: a ctypes array (or list) of cdp_step_problem; keep the same array object to replay a graph."""
+    if not isinstance(steps, ctypes.Array):
+        steps = (cdp_step_problem * len(steps))(*steps)
+    return load_library().cdp_step_batched(ctx, steps, len(steps), int(precision), float(dt), float(four_pi_G),
+                                           int(bool(use_graph)), ctypes.c_void_p(stream))
 
 
 def _stream_handle(stream):

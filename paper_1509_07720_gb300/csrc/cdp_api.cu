@@ -10,27 +10,7 @@
 #include "../../include/coldproj.h"
 #include "cdp_project.h"
 
-struct cdp_ctx {
-    int device;
-    int num_sms;
-    int blocks_small[2];  // resident blocks per SM of the small kernel (fp64, fp32)
-    int blocks_big[2];
-    cdp::VertexRec* verts;
-    size_t verts_cap;
-    int* queue;
-    size_t queue_cap;
-    cdp::Counters* ctr;       // device
-    cdp::UnitCounts* stats;   // device
-    cdp::Counters* h_ctr;     // pinned host mirrors
-    cdp::UnitCounts* h_stats;
-    // per-kernel timing: 4 events per timed call (before prep, after prep, after the one-thread
-    // kernel, after the tiled kernel), folded into totals when read
-    int timing;
-    std::vector<cudaEvent_t>* pending;
-    std::vector<cudaEvent_t>* pool;
-    double totals[3];
-    int calls;
-};
+#include "cdp_ctx.h"
 
 namespace {
 
@@ -128,6 +108,130 @@ int fold_timing(cdp_ctx* c) {
 
 }  // namespace
 
+namespace cdp {
+
+// grow the scratch to hold the largest of `n` problems (allocation happens here, never inside
+// a captured sequence)
+int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
+    size_t nv = 1, ns = 1;
+    for (int i = 0; i < n; ++i) {
+        if ((size_t)probs[i].n_verts > nv) nv = (size_t)probs[i].n_verts;
+        if ((size_t)probs[i].n_simplices > ns) ns = (size_t)probs[i].n_simplices;
+    }
+    int rc = grow(&c->verts, &c->verts_cap, nv);
+    if (rc) return rc;
+    return grow(&c->queue, &c->queue_cap, ns);
+}
+
+// enqueue one projection on `st` (arguments already checked)
+int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats) {
+    int rc;
+    if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
+    if ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1)))) return rc;
+
+    LaunchArgs L;
+    memset(&L, 0, sizeof(L));
+    L.g.dim = p->dim;
+    L.g.periodic = p->periodic ? 1 : 0;
+    long long cells = 1;
+    L.cellvol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (a < p->dim) {
+            L.g.n[a] = p->grid[a];
+            L.g.lo[a] = p->box_lo[a];
+            L.g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
+            L.cellvol *= p->box_len[a] / (double)p->grid[a];
+            cells *= p->grid[a];
+        } else {
+            L.g.n[a] = 1;
+            L.g.lo[a] = 0.0;
+            L.g.inv_h[a] = 1.0;
+        }
+    }
+    L.g.cell_volume = L.cellvol;
+    L.nv = p->n_verts;
+    L.ns = p->n_simplices;
+    L.simplices = p->simplices;
+    L.verts = c->verts;
+    L.out = p->cell_mass;
+    L.queue = c->queue;
+    L.ctr = c->ctr;
+    L.stats = want_stats ? c->stats : nullptr;
+    L.num_sms = c->num_sms;
+    int fp32 = precision == CDP_FP32_MIXED;
+    L.small_blocks_per_sm = 16 * c->blocks_small[fp32];
+    L.big_blocks_per_sm = c->blocks_big[fp32];
+
+    // zero the per-call counters (the sticky error word at offset 0 is kept)
+    if (cudaMemsetAsync((char*)c->ctr + sizeof(unsigned), 0, sizeof(Counters) - sizeof(unsigned), st) !=
+        cudaSuccess)
+        return CDP_ERR_CUDA;
+    if (want_stats && cudaMemsetAsync(c->stats, 0, 2 * sizeof(UnitCounts), st) != cudaSuccess) return CDP_ERR_CUDA;
+    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
+        return CDP_ERR_CUDA;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (c->timing) {
+        if (c->pending->size() >= 4096) fold_timing(c);
+        for (int k = 0; k < 4; ++k) ev[k] = take_event(c);
+        if (!ev[0] || !ev[1] || !ev[2] || !ev[3]) {
+            for (int k = 0; k < 4; ++k)
+                if (ev[k]) c->pool->push_back(ev[k]);
+            return CDP_ERR_CUDA;
+        }
+        cudaEventRecord(ev[0], st);
+    }
+    if (launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    if (ev[1]) cudaEventRecord(ev[1], st);
+    if (launch_project(L, fp32, st, ev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    if (ev[3]) {
+        cudaEventRecord(ev[3], st);
+        for (int k = 0; k < 4; ++k) c->pending->push_back(ev[k]);
+    }
+    return CDP_OK;
+}
+
+}  // namespace cdp
+
+namespace {
+
+int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
+    if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(cdp::Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->h_stats, c->stats, 2 * sizeof(cdp::UnitCounts), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    memset(stats, 0, sizeof(*stats));
+    stats->n_zero_volume = c->h_ctr->n_zero;
+    stats->n_single_cell = c->h_ctr->n_class0;
+    stats->n_small = c->h_ctr->n_small;
+    stats->n_large = c->h_ctr->big_count;
+    stats->n_large_tiles = c->h_ctr->n_big_tiles;
+    const cdp::UnitCounts& s0 = c->h_stats[0];
+    const cdp::UnitCounts& s1 = c->h_stats[1];
+    stats->corners_a = s0.a + s1.a;
+    stats->corners_b = s0.b + s1.b;
+    stats->corners_c = s0.c + s1.c;
+    stats->corners_d = s0.d + s1.d;
+    stats->exact_fallbacks = s0.exact + s1.exact;
+    stats->large_corners[0] = s1.a;
+    stats->large_corners[1] = s1.b;
+    stats->large_corners[2] = s1.c;
+    stats->large_corners[3] = s1.d;
+    stats->error_flags = c->h_ctr->flags;
+    unsigned f = c->h_ctr->flags;
+    if (f && cudaMemsetAsync(c->ctr, 0, sizeof(unsigned), st) != cudaSuccess) return CDP_ERR_CUDA;
+    return flags_to_code(f);
+}
+
+}  // namespace
+
 extern "C" {
 
 int cdp_timing_enable(cdp_ctx* c, int enable) {
@@ -198,7 +302,8 @@ int cdp_create(cdp_ctx** out, int device) {
     }
     c->pending = new (std::nothrow) std::vector<cudaEvent_t>();
     c->pool = new (std::nothrow) std::vector<cudaEvent_t>();
-    if (!c->pending || !c->pool) {
+    c->plans = new (std::nothrow) std::vector<cdp::FftPlan>();
+    if (!c->pending || !c->pool || !c->plans) {
         cdp_destroy(c);
         return CDP_ERR_OOM;
     }
@@ -230,6 +335,8 @@ void cdp_destroy(cdp_ctx* c) {
         for (cudaEvent_t e : *c->pool) cudaEventDestroy(e);
         delete c->pool;
     }
+    cdp::step_release(c);
+    cdp::solver_release(c);
     cudaGetLastError();
     delete c;
 }
@@ -255,101 +362,27 @@ int cdp_project(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate,
     if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
-    if ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1)))) return rc;
+    rc = cdp::project_enqueue(c, p, precision, accumulate, st, stats != nullptr);
+    if (rc || !stats) return rc;
+    return read_stats(c, st, stats);
+}
 
-    cdp::LaunchArgs L;
-    memset(&L, 0, sizeof(L));
-    L.g.dim = p->dim;
-    L.g.periodic = p->periodic ? 1 : 0;
-    long long cells = 1;
-    L.cellvol = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        if (a < p->dim) {
-            L.g.n[a] = p->grid[a];
-            L.g.lo[a] = p->box_lo[a];
-            L.g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
-            L.cellvol *= p->box_len[a] / (double)p->grid[a];
-            cells *= p->grid[a];
-        } else {
-            L.g.n[a] = 1;
-            L.g.lo[a] = 0.0;
-            L.g.inv_h[a] = 1.0;
-        }
+int cdp_project_batched(cdp_ctx* c, const cdp_problem* probs, int n, int precision, void* stream) {
+    if (!c || n < 0 || (n > 0 && !probs)) return CDP_ERR_ARG;
+    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_problem(probs + i);
+        if (rc) return rc;
     }
-    L.g.cell_volume = L.cellvol;
-    L.nv = p->n_verts;
-    L.ns = p->n_simplices;
-    L.simplices = p->simplices;
-    L.verts = c->verts;
-    L.out = p->cell_mass;
-    L.queue = c->queue;
-    L.ctr = c->ctr;
-    L.stats = stats ? c->stats : nullptr;
-    L.num_sms = c->num_sms;
-    int fp32 = precision == CDP_FP32_MIXED;
-    L.small_blocks_per_sm = 16 * c->blocks_small[fp32];
-    L.big_blocks_per_sm = c->blocks_big[fp32];
-
-    // zero the per-call counters (the sticky error word at offset 0 is kept)
-    if (cudaMemsetAsync((char*)c->ctr + sizeof(unsigned), 0, sizeof(cdp::Counters) - sizeof(unsigned), st) !=
-        cudaSuccess)
-        return CDP_ERR_CUDA;
-    if (stats && cudaMemsetAsync(c->stats, 0, 2 * sizeof(cdp::UnitCounts), st) != cudaSuccess) return CDP_ERR_CUDA;
-    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
-        return CDP_ERR_CUDA;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    if (c->timing) {
-        if (c->pending->size() >= 4096) fold_timing(c);
-        for (int k = 0; k < 4; ++k) ev[k] = take_event(c);
-        if (!ev[0] || !ev[1] || !ev[2] || !ev[3]) {
-            for (int k = 0; k < 4; ++k)
-                if (ev[k]) c->pool->push_back(ev[k]);
-            return CDP_ERR_CUDA;
-        }
-        cudaEventRecord(ev[0], st);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cdp::reserve_scratch(c, probs, n);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        rc = cdp::project_enqueue(c, probs + i, precision, 0, st, false);
+        if (rc) return rc;
     }
-    if (cdp::launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess) {
-        cudaGetLastError();
-        return CDP_ERR_CUDA;
-    }
-    if (ev[1]) cudaEventRecord(ev[1], st);
-    if (cdp::launch_project(L, fp32, st, ev[2]) != cudaSuccess) {
-        cudaGetLastError();
-        return CDP_ERR_CUDA;
-    }
-    if (ev[3]) {
-        cudaEventRecord(ev[3], st);
-        for (int k = 0; k < 4; ++k) c->pending->push_back(ev[k]);
-    }
-    if (!stats) return CDP_OK;
-    if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(cdp::Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(c->h_stats, c->stats, 2 * sizeof(cdp::UnitCounts), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaGetLastError();
-        return CDP_ERR_CUDA;
-    }
-    memset(stats, 0, sizeof(*stats));
-    stats->n_zero_volume = c->h_ctr->n_zero;
-    stats->n_single_cell = c->h_ctr->n_class0;
-    stats->n_small = c->h_ctr->n_small;
-    stats->n_large = c->h_ctr->big_count;
-    stats->n_large_tiles = c->h_ctr->n_big_tiles;
-    const cdp::UnitCounts& s0 = c->h_stats[0];
-    const cdp::UnitCounts& s1 = c->h_stats[1];
-    stats->corners_a = s0.a + s1.a;
-    stats->corners_b = s0.b + s1.b;
-    stats->corners_c = s0.c + s1.c;
-    stats->corners_d = s0.d + s1.d;
-    stats->exact_fallbacks = s0.exact + s1.exact;
-    stats->large_corners[0] = s1.a;
-    stats->large_corners[1] = s1.b;
-    stats->large_corners[2] = s1.c;
-    stats->large_corners[3] = s1.d;
-    stats->error_flags = c->h_ctr->flags;
-    unsigned f = c->h_ctr->flags;
-    if (f && cudaMemsetAsync(c->ctr, 0, sizeof(unsigned), st) != cudaSuccess) return CDP_ERR_CUDA;
-    return flags_to_code(f);
+    return CDP_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,59 @@
+// Definition of the context object shared by the C-ABI translation units (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <vector>
+
+#include "cdp_project.h"
+
+namespace cdp {
+
+// cached cuFFT plans and spectrum buffer of one grid shape
+struct FftPlan {
+    int dim;
+    int n[3];
+    cufftHandle r2c, c2r;
+    cufftDoubleComplex* spec;
+    size_t spec_elems;
+};
+
+}  // namespace cdp
+
+struct cdp_ctx;
+struct cdp_problem_tag;
+
+namespace cdp {
+void solver_release(cdp_ctx* c);
+void step_release(cdp_ctx* c);
+}  // namespace cdp
+
+struct cdp_ctx {
+    int device;
+    int num_sms;
+    int blocks_small[2];  // resident blocks per SM of the small kernel (fp64, fp32)
+    int blocks_big[2];
+    cdp::VertexRec* verts;
+    size_t verts_cap;
+    int* queue;
+    size_t queue_cap;
+    cdp::Counters* ctr;       // device
+    cdp::UnitCounts* stats;   // device
+    cdp::Counters* h_ctr;     // pinned host mirrors
+    cdp::UnitCounts* h_stats;
+    // per-kernel timing: 4 events per timed call (before prep, after prep, after the one-thread
+    // kernel, after the tiled kernel), folded into totals when read
+    int timing;
+    std::vector<cudaEvent_t>* pending;
+    std::vector<cudaEvent_t>* pool;
+    double totals[3];
+    int calls;
+    // solver scratch
+    std::vector<cdp::FftPlan>* plans;
+    double* vsum;  // per-vertex accumulators of the vertex density (mass, volume)
+    size_t vsum_cap;
+    // captured time steps (see cdp_step_batched) and the device copy of their dt
+    struct StepGraph* graphs;
+    double* d_dt;
+};

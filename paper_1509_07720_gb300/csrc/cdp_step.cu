@@ -1,0 +1,192 @@
+// One time step of many independent meshes (Sect. 4, steps (ii)-(iv)), optionally captured once
+// into a CUDA graph and replayed:  drift dt/2 -> vertex densities -> exact projection -> FFT
+// Poisson -> force at the vertices -> kick dt -> drift dt/2.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/coldproj.h"
+#include "cdp_ctx.h"
+
+namespace cdp {
+int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n);
+int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats);
+int poisson_enqueue(cdp_ctx* c, int dim, const int32_t grid[3], const double box_len[3], double four_pi_G,
+                    const double* mass, double* phi, cudaStream_t st);
+int force_enqueue(int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3], const double* phi,
+                  long long n, const double* const pos[3], double* const acc[3], cudaStream_t st);
+int drift_enqueue(int dim, long long n, double* const pos[3], const double* const vel[3], double dt,
+                  const double* dtp, double fac, const double box_lo[3], const double box_len[3], int periodic,
+                  cudaStream_t st);
+int kick_enqueue(int dim, long long n, double* const vel[3], const double* const acc[3], double dt,
+                 const double* dtp, double fac, cudaStream_t st);
+int vertex_density_enqueue(cdp_ctx* c, const cdp_problem* p, const double* mass, double* rho_out, cudaStream_t st);
+}  // namespace cdp
+
+// a captured step: the exact arguments it was recorded with, and its executable graph
+struct StepGraph {
+    std::vector<cdp_step_problem> key;
+    int precision;
+    double four_pi_G;
+    cudaGraphExec_t exec;
+    StepGraph* next;
+};
+
+namespace {
+
+struct Guard {
+    int prev;
+    bool changed;
+    explicit Guard(int dev) : prev(0), changed(false) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~Guard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// every kernel of the step, in order; `dtp` is the device scalar holding dt
+int enqueue_step(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision, double four_pi_G, const double* dtp,
+                 cudaStream_t st) {
+    int rc;
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem& m = probs[i].mesh;
+        double* pos[3] = {const_cast<double*>(m.pos[0]), const_cast<double*>(m.pos[1]),
+                          const_cast<double*>(m.pos[2])};
+        if ((rc = cdp::drift_enqueue(m.dim, m.n_verts, pos, probs[i].vel, 0.0, dtp, 0.5, m.box_lo, m.box_len,
+                                     m.periodic, st)))
+            return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem& m = probs[i].mesh;
+        if ((rc = cdp::vertex_density_enqueue(c, &m, probs[i].simplex_mass, const_cast<double*>(m.rho), st)))
+            return rc;
+        if ((rc = cdp::project_enqueue(c, &m, precision, 0, st, false))) return rc;
+        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st)))
+            return rc;
+        if ((rc = cdp::force_enqueue(m.dim, m.grid, m.box_lo, m.box_len, probs[i].phi, m.n_verts, m.pos,
+                                     probs[i].acc, st)))
+            return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem& m = probs[i].mesh;
+        double* pos[3] = {const_cast<double*>(m.pos[0]), const_cast<double*>(m.pos[1]),
+                          const_cast<double*>(m.pos[2])};
+        if ((rc = cdp::kick_enqueue(m.dim, m.n_verts, probs[i].vel, probs[i].acc, 0.0, dtp, 1.0, st))) return rc;
+        if ((rc = cdp::drift_enqueue(m.dim, m.n_verts, pos, probs[i].vel, 0.0, dtp, 0.5, m.box_lo, m.box_len,
+                                     m.periodic, st)))
+            return rc;
+    }
+    return CDP_OK;
+}
+
+int check_step_problem(const cdp_step_problem& s) {
+    const cdp_problem& m = s.mesh;
+    if (m.dim != 2 && m.dim != 3) return CDP_ERR_ARG;
+    if (m.n_verts < 0 || m.n_simplices < 0 || m.n_verts > 0x7fffffffLL || m.n_simplices > 0x7fffffffLL)
+        return CDP_ERR_ARG;
+    if (!m.cell_mass || !s.phi || (m.n_simplices > 0 && (!m.simplices || !s.simplex_mass))) return CDP_ERR_ARG;
+    if (!m.periodic) return CDP_ERR_ARG;  // the FFT Poisson solve is periodic
+    long long cells = 1;
+    for (int a = 0; a < m.dim; ++a) {
+        if (m.grid[a] < 1 || m.grid[a] > (1 << 20) || !(m.box_len[a] > 0.0)) return CDP_ERR_ARG;
+        if (m.n_verts > 0 && (!m.pos[a] || !s.vel[a] || !s.acc[a])) return CDP_ERR_ARG;
+        cells *= m.grid[a];
+        if (cells > (1LL << 32)) return CDP_ERR_ARG;
+    }
+    if (m.n_verts > 0 && !m.rho) return CDP_ERR_ARG;
+    return CDP_OK;
+}
+
+}  // namespace
+
+namespace cdp {
+void step_release(cdp_ctx* c) {
+    StepGraph* g = c->graphs;
+    while (g) {
+        StepGraph* nx = g->next;
+        cudaGraphExecDestroy(g->exec);
+        delete g;
+        g = nx;
+    }
+    c->graphs = nullptr;
+    if (c->d_dt) cudaFree(c->d_dt);
+    c->d_dt = nullptr;
+}
+}  // namespace cdp
+
+extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision, double dt,
+                                double four_pi_G, int use_graph, void* stream) {
+    if (!c || n < 0 || (n > 0 && !probs)) return CDP_ERR_ARG;
+    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    if (!(dt == dt) || !(four_pi_G == four_pi_G)) return CDP_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_step_problem(probs[i]);
+        if (rc) return rc;
+    }
+    Guard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->d_dt && cudaMalloc(&c->d_dt, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_OOM;
+    }
+    // dt travels through device memory so that a replayed graph picks up the current value
+    if (cudaMemcpyAsync(c->d_dt, &dt, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) return CDP_ERR_CUDA;
+    if (!use_graph) return enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, st);
+
+    for (StepGraph* g = c->graphs; g; g = g->next) {
+        if ((int)g->key.size() == n && g->precision == precision && g->four_pi_G == four_pi_G &&
+            memcmp(g->key.data(), probs, (size_t)n * sizeof(cdp_step_problem)) == 0) {
+            return cudaGraphLaunch(g->exec, st) == cudaSuccess ? CDP_OK : CDP_ERR_CUDA;
+        }
+    }
+    // first call with these arguments: size every scratch buffer and create every FFT plan before
+    // the capture (nothing may allocate inside it)
+    std::vector<cdp_problem> meshes((size_t)n);
+    for (int i = 0; i < n; ++i) meshes[(size_t)i] = probs[i].mesh;
+    int rc = cdp::reserve_scratch(c, meshes.data(), n);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        // creates the FFT plan (and its spectrum buffer) of every grid shape; the vertex-density
+        // accumulators are grown here too, with a harmless solve on the problem's own arrays
+        const cdp_problem& m = probs[i].mesh;
+        if ((rc = cdp::vertex_density_enqueue(c, &m, probs[i].simplex_mass, const_cast<double*>(m.rho), st)))
+            return rc;
+        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st)))
+            return rc;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CDP_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CDP_ERR_CUDA;
+    int timing = c->timing;
+    c->timing = 0;  // no event bookkeeping inside the captured sequence
+    rc = enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, st);
+    c->timing = timing;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc ? rc : CDP_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    StepGraph* g = new (std::nothrow) StepGraph;
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        return CDP_ERR_OOM;
+    }
+    g->key.assign(probs, probs + n);
+    g->precision = precision;
+    g->four_pi_G = four_pi_G;
+    g->exec = exec;
+    g->next = c->graphs;
+    c->graphs = g;
+    return cudaGraphLaunch(exec, st) == cudaSuccess ? CDP_OK : CDP_ERR_CUDA;
+}

@@ -7,8 +7,8 @@ beside it in the same run). Workload (synthetic, seeded): a 128^3 Lagrangian lat
 power spectrum k^-2 for |k| <= 16 and rms 4 Lagrangian cells (post shell-crossing), lognormal
 vertex density (sigma = 0.5), periodic unit box, 256^3 FP64 output grid.
 
-One step = one full projection: zeroing the grid, vertex preparation, the one-thread kernel and
-the tiled kernel, all through the C ABI. Inputs (201 MB of simplices, 67 MB of vertex records,
+One step = one full projection: zeroing the grid, vertex preparation and the warp-cooperative
+projection kernel, all through the C ABI. Inputs (201 MB of simplices, 67 MB of vertex records,
 134 MB grid) exceed the 129 MB L2, so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -52,6 +52,7 @@ def _args():
     ap.add_argument("--scale", type=int, default=None, help="Lagrangian lattice size override (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 plain path")
     return ap.parse_args()
 
 
@@ -252,7 +253,7 @@ def run_ours(a):
     value = ws * ns / (ms32 / 1000.0)
 
     # FP64 plain path on the same GPU, same workload (fewer steps: it is much slower)
-    k64 = max(2, min(a.steps, 3))
+    k64 = max(1, a.fp64_steps)
     ms64, kern64 = timed(pkg.CDP_FP64, k64, 1)
     ms64 = max_over_ranks(ms64)
 
@@ -294,15 +295,12 @@ def run_ours(a):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the one-thread kernel carries nearly all of the work)
-    names = ["k_prep_vertices", "k_project_small3<float>", "k_project_big3<float>"]
+    # roofline of the dominant kernel (the warp-cooperative projection kernel)
+    names = ["k_prep_vertices", "k_project_warp<3,float>", "(none)"]
+    kern32 = kern32[:2]
     dom = int(np.argmax(kern32))
-    lc = st32["large_corners"]
     if dom == 1:
-        inc = {"a": st32["corners_a"] - lc[0], "b": st32["corners_b"] - lc[1], "c": st32["corners_c"] - lc[2],
-               "d": st32["corners_d"] - lc[3]}
-    elif dom == 2:
-        inc = dict(zip("abcd", lc))
+        inc = {k: st32["corners_" + k] for k in "abcd"}
     else:
         inc = None
     if inc is not None:
@@ -330,10 +328,10 @@ def run_ours(a):
                        "kernel_ms": kern64, "speedup_fp32_mixed_vs_fp64": ms64 / ms32},
         "kernel_ms": dict(zip(names, kern32)),
         "corners": {k: st32[k] for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell",
-                                         "n_small", "n_large", "n_large_tiles", "exact_fallbacks")},
+                                         "n_small", "n_zero_volume", "exact_fallbacks")},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 3 * a.steps,
+        "gpu_launches": 2 * a.steps,
         "e2e": e2e,
     }
     if ws == 1 and not a.no_cpu_baseline:

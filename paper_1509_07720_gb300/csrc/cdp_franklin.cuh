@@ -127,13 +127,11 @@ struct Tet {
 
 // the vertices of the edge e (a < b) and the two others (p < q)
 CDP_HD void tet_edge(int e, int& a, int& b, int& p, int& q) {
-    // (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
-    const int A[6] = {0, 0, 0, 1, 1, 2}, B[6] = {1, 2, 3, 2, 3, 3};
-    const int P[6] = {2, 1, 1, 0, 0, 0}, Qv[6] = {3, 3, 2, 3, 2, 1};
-    a = A[e];
-    b = B[e];
-    p = P[e];
-    q = Qv[e];
+    // (0,1),(0,2),(0,3),(1,2),(1,3),(2,3); nibble e of each constant
+    a = (0x211000 >> (4 * e)) & 15;
+    b = (0x332321 >> (4 * e)) & 15;
+    p = (0x000112 >> (4 * e)) & 15;
+    q = (0x123233 >> (4 * e)) & 15;
 }
 
 CDP_HD int tet_edge_index(int i, int j) {
@@ -144,17 +142,35 @@ CDP_HD int tet_edge_index(int i, int j) {
 // Per-unit working set of a tetrahedron: coordinates relative to the unit's tile origin.
 template <typename R>
 struct TetGeo {
-    i64 Lt[4][3];     // exact, relative to the tile origin
-    R x[4][3];        // rounded copies
-    R n[4][3];        // unit inward normals of the facets (facet f is opposite vertex f)
-    i128 nE[4][3];    // exact (unnormalised) inward normals, units 2^-2Q
-    R g[3];           // grad rho (per cell length)
+    i64 Lt[4][3];          // exact, relative to the tile origin
+    R x[4][3];             // rounded copies
+    R n[4][3];             // unit inward normals of the facets (facet f is opposite vertex f)
+    R g[3];                // grad rho (per cell length)
     R rho[4];
-    R c[3], rhoc;     // centroid and density there
-    R B2, B3;         // filter bounds for side2 / side3
-    int cell[4][3];   // vertex cells relative to the tile origin
-    int lo[3], hi[3]; // bounding box relative to the tile origin
+    R c[3], rhoc;          // centroid and density there
+    R B2, B3;              // filter bounds for side2 / side3
+    int cell[4][3];        // vertex cells relative to the tile origin
+    int lo[3], hi[3];      // bounding box relative to the tile origin
+    int anchor[3];         // absolute cell of the tile origin
+    signed char ns[4][3];  // signs of the exact normal components
+    double mexact;         // |V| mean(rho) in FP64 (closed form, for the mass closure)
 };
+
+// exact inward normal of facet f (the facet opposite vertex f) of a positively oriented tetrahedron
+CDP_HD void facet_normal_exact(const i64 L[4][3], int f, i128 out[3]) {
+    int o = f == 0 ? 1 : 0;  // reference vertex of the facet
+    int u, v;                // the normal is (x_u - x_o) x (x_v - x_o)
+    if (f == 0) { u = 3; v = 2; }
+    else if (f == 1) { u = 2; v = 3; }
+    else if (f == 2) { u = 3; v = 1; }
+    else { u = 1; v = 2; }
+    i64 d1[3], d2[3];
+    for (int a = 0; a < 3; ++a) {
+        d1[a] = L[u][a] - L[o][a];
+        d2[a] = L[v][a] - L[o][a];
+    }
+    cross_exact(d1, d2, out);
+}
 
 // Fill the working set for the tile whose lowest cell is T (relative to the anchor).
 template <typename R>
@@ -169,29 +185,26 @@ CDP_HD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
         G.lo[a] = S.lo[a] - T[a];
         G.hi[a] = S.hi[a] - T[a];
     }
-    i64 e1[3], e2[3], e3[3], f1[3], f2[3];
-    for (int a = 0; a < 3; ++a) {
-        e1[a] = G.Lt[1][a] - G.Lt[0][a];
-        e2[a] = G.Lt[2][a] - G.Lt[0][a];
-        e3[a] = G.Lt[3][a] - G.Lt[0][a];
-        f1[a] = G.Lt[3][a] - G.Lt[1][a];
-        f2[a] = G.Lt[2][a] - G.Lt[1][a];
-    }
-    // inward normals of a positively oriented tetrahedron
-    cross_exact(f1, f2, G.nE[0]);  // (x3-x1) x (x2-x1)
-    cross_exact(e2, e3, G.nE[1]);  // (x2-x0) x (x3-x0)
-    cross_exact(e3, e1, G.nE[2]);  // (x3-x0) x (x1-x0)
-    cross_exact(e1, e2, G.nE[3]);  // (x1-x0) x (x2-x0)
+    i64 e3[3];
+    for (int a = 0; a < 3; ++a) e3[a] = G.Lt[3][a] - G.Lt[0][a];
     R nr[4][3];
-    #pragma unroll
+    i128 n3[3];
     for (int f = 0; f < 4; ++f) {
-        for (int a = 0; a < 3; ++a) nr[f][a] = i128_to_real<R>(G.nE[f][a], 2 * CDP_Q);
+        i128 nE[3];
+        facet_normal_exact(G.Lt, f, nE);
+        for (int a = 0; a < 3; ++a) {
+            nr[f][a] = i128_to_real<R>(nE[a], 2 * CDP_Q);
+            G.ns[f][a] = (signed char)sgn_i128(nE[a]);
+            if (f == 3) n3[a] = nE[a];
+        }
         R inv = rsqrt_r<R>(dot3(nr[f], nr[f]));
         for (int a = 0; a < 3; ++a) G.n[f][a] = nr[f][a] * inv;
     }
     // 6 |V| = e3 . (e1 x e2), exact, then rounded
-    double D = wide_to_double(dot3_wide(G.nE[3], e3), 3 * CDP_Q);
-    R invD = R(1.0 / D);
+    double D = wide_to_double(dot3_wide(n3, e3), 3 * CDP_Q);
+    R invD = R(1) / R(D);
+    G.mexact = D * (1.0 / 6.0) * 0.25 * (S.rho[0] + S.rho[1] + S.rho[2] + S.rho[3]);
+    for (int a = 0; a < 3; ++a) G.anchor[a] = S.anchor[a] + T[a];
     for (int k = 0; k < 4; ++k) G.rho[k] = (R)S.rho[k];
     R d1 = G.rho[1] - G.rho[0], d2 = G.rho[2] - G.rho[0], d3 = G.rho[3] - G.rho[0];
     for (int a = 0; a < 3; ++a) {
@@ -237,7 +250,9 @@ CDP_HD int tet_side3(const TetGeo<R>& G, int f, const int gn[3], UnitCounts* cnt
     if (val < -G.B3) return -1;
     if (cnt) cnt->exact++;
     i64 gp[3] = {(i64)gn[0] << CDP_Q, (i64)gn[1] << CDP_Q, (i64)gn[2] << CDP_Q};
-    return side3_exact(G.nE[f], G.Lt[a], gp);
+    i128 nE[3];
+    facet_normal_exact(G.Lt, f, nE);
+    return side3_exact(nE, G.Lt[a], gp);
 }
 
 // sign(X_j - d) for the crossing X of edge (a -> b) with grid plane x_k = c (perturbed)
@@ -277,7 +292,7 @@ CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int j, int k, i
                                UnitCounts* cnt) {
     int lo = G.lo[l], hi = G.hi[l];
     int m = guess < lo ? lo : (guess > hi ? hi : guess);
-    int up = G.nE[f][l] > 0 ? 1 : -1;  // side3 grows along +l when the normal's l component is > 0
+    int up = G.ns[f][l] > 0 ? 1 : -1;  // side3 grows along +l when the normal's l component is > 0
     int gn[3];
     gn[j] = dj;
     gn[k] = dk;
@@ -328,7 +343,6 @@ CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const int v[3]) {
     piece_origin(G, v, O);
     for (int a = 0; a < 3; ++a) P[a] = G.x[i][a] - O[a];
     R s = 0;
-    #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j == i) continue;
         int a = i < j ? i : j, b = i < j ? j : i;
@@ -336,7 +350,6 @@ CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const int v[3]) {
         edge_unit(G, a, b, ev);
         R sg = i == a ? R(1) : R(-1);
         for (int t = 0; t < 3; ++t) T[t] = sg * ev[t];
-        #pragma unroll
         for (int f = 0; f < 4; ++f) {
             if (f == i || f == j) continue;
             int r = 6 - i - j - f;  // third vertex of facet f
@@ -377,7 +390,6 @@ CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const
     R lam = R(-parity4(a, b, p, q)) * R(dirk);
     R Bk[3] = {0, 0, 0};
     Bk[k] = sigma;
-    #pragma unroll
     for (int w = 0; w < 2; ++w) {
         const R* n = G.n[w == 0 ? p : q];
         R su = w == 0 ? lam : -lam;
@@ -409,7 +421,7 @@ CDP_HD R tet_corner_D(const TetGeo<R>& G, int f, int l, int j, int k, R sj, R sk
     piece_origin(G, v, O);
     for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
     const R* n = G.n[f];
-    R tau = G.nE[f][l] > 0 ? R(1) : R(-1);
+    R tau = G.ns[f][l] > 0 ? R(1) : R(-1);
     R eps = (l == 1) ? R(-1) : R(1);  // Levi-Civita of (j, k, l) with j < k
     R s = 0;
     R El[3] = {0, 0, 0}, Ej[3] = {0, 0, 0}, Ek[3] = {0, 0, 0};
@@ -466,126 +478,147 @@ CDP_HD R tet_corner_A(const TetGeo<R>& G, const R X[3], R rhoX, const int v[3], 
 }
 
 // ------------------------------------------------------------------------------------------
-// one unit = the part of a tetrahedron's projection that falls in the tile [0, td) (tile frame)
-// acc(vx, vy, vz, value) receives every (corner, cell) contribution, in cell-volume units.
+// The work of one unit (the part of a tetrahedron's projection that falls in the tile [0, td),
+// tile frame) comes in three kinds of independent items, so that a warp can spread them over its
+// lanes:  a vertex (corner B), a (edge, axis, plane) crossing (corner C), a grid line along one
+// axis (corners D where it pierces two facets, and for lines along x the grid nodes between them,
+// corners A).  acc(vx, vy, vz, value) receives every (corner, cell) contribution.
 // ------------------------------------------------------------------------------------------
+
 template <typename R, class Acc>
-CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* cnt) {
-    // ---- B: simplex vertices
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int* v = G.cell[i];
-        if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1] && v[2] >= 0 && v[2] < td[2]) {
-            acc(v[0], v[1], v[2], tet_corner_B(G, i, v));
-            if (cnt) cnt->b++;
-        }
+CDP_HD void tet_item_vertex(const TetGeo<R>& G, int i, const int td[3], Acc& acc, UnitCounts* cnt) {
+    const int v[3] = {G.cell[i][0], G.cell[i][1], G.cell[i][2]};
+    if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1] && v[2] >= 0 && v[2] < td[2]) {
+        acc(v[0], v[1], v[2], tet_corner_B(G, i, v));
+        if (cnt) cnt->b++;
     }
-    // ---- C: edges crossing cell faces
-    #pragma unroll
+}
+
+// number of grid planes x_k = c crossed by edge e inside the tile
+template <typename R>
+CDP_HD int tet_crossings(const TetGeo<R>& G, int e, int k, const int td[3], int& c0) {
+    int a, b, p, q;
+    tet_edge(e, a, b, p, q);
+    int ca = G.cell[a][k], cb = G.cell[b][k];
+    c0 = (ca < cb ? ca : cb) + 1;
+    int c1 = ca < cb ? cb : ca;
+    if (c0 < 0) c0 = 0;
+    if (c1 > td[k]) c1 = td[k];
+    return c1 >= c0 ? c1 - c0 + 1 : 0;
+}
+
+template <typename R, class Acc>
+CDP_HD void tet_item_crossing(const TetGeo<R>& G, int e, int k, int c, const int td[3], Acc& acc, UnitCounts* cnt) {
+    int a, b, p, q;
+    tet_edge(e, a, b, p, q);
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+    R ev[3];
+    for (int t = 0; t < 3; ++t) ev[t] = G.x[b][t] - G.x[a][t];
+    R t = (R(c) - G.x[a][k]) / ev[k];
+    R X[3];
+    for (int w = 0; w < 3; ++w) X[w] = G.x[a][w] + t * ev[w];
+    X[k] = R(c);
+    int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X[j1]), dirk, cnt);
+    if (cj1 < 0 || cj1 >= td[j1]) return;
+    int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X[j2]), dirk, cnt);
+    if (cj2 < 0 || cj2 >= td[j2]) return;
+    R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+    for (int side = 0; side < 2; ++side) {
+        int vk = side == 0 ? c - 1 : c;
+        if (vk < 0 || vk >= td[k]) continue;
+        int v[3];
+        v[k] = vk;
+        v[j1] = cj1;
+        v[j2] = cj2;
+        acc(v[0], v[1], v[2], tet_corner_C(G, e, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
+        if (cnt) cnt->c++;
+    }
+}
+
+// grid lines along axis l inside the tile: (dj, dk) in [dj0, dj1] x [dk0, dk1]
+template <typename R>
+CDP_HD int tet_lines(const TetGeo<R>& G, int l, const int td[3], int& dj0, int& nj, int& dk0) {
+    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    dj0 = G.lo[j] + 1 > 0 ? G.lo[j] + 1 : 0;
+    int dj1 = G.hi[j] < td[j] ? G.hi[j] : td[j];
+    dk0 = G.lo[k] + 1 > 0 ? G.lo[k] + 1 : 0;
+    int dk1 = G.hi[k] < td[k] ? G.hi[k] : td[k];
+    nj = dj1 >= dj0 ? dj1 - dj0 + 1 : 0;
+    int nk = dk1 >= dk0 ? dk1 - dk0 + 1 : 0;
+    return nj * nk;
+}
+
+template <typename R, class Acc>
+CDP_HD void tet_item_line(const TetGeo<R>& G, int l, int dj, int dk, const int td[3], Acc& acc, UnitCounts* cnt) {
+    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    int s[6];
     for (int e = 0; e < 6; ++e) {
         int a, b, p, q;
         tet_edge(e, a, b, p, q);
-        #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            int ca = G.cell[a][k], cb = G.cell[b][k];
-            if (ca == cb) continue;
-            int dirk = cb > ca ? 1 : -1;
-            int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
-            if (c0 < 0) c0 = 0;
-            if (c1 > td[k]) c1 = td[k];
-            if (c0 > c1) continue;
-            int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-            R ev[3];
-            for (int t = 0; t < 3; ++t) ev[t] = G.x[b][t] - G.x[a][t];
-            R rinv = R(1) / ev[k];
-            for (int c = c0; c <= c1; ++c) {
-                R t = (R(c) - G.x[a][k]) * rinv;
-                R X[3];
-                for (int w = 0; w < 3; ++w) X[w] = G.x[a][w] + t * ev[w];
-                X[k] = R(c);
-                int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X[j1]), dirk, cnt);
-                if (cj1 < 0 || cj1 >= td[j1]) continue;
-                int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X[j2]), dirk, cnt);
-                if (cj2 < 0 || cj2 >= td[j2]) continue;
-                R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
-                for (int side = 0; side < 2; ++side) {
-                    int vk = side == 0 ? c - 1 : c;
-                    if (vk < 0 || vk >= td[k]) continue;
-                    int v[3];
-                    v[k] = vk;
-                    v[j1] = cj1;
-                    v[j2] = cj2;
-                    acc(v[0], v[1], v[2], tet_corner_C(G, e, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
-                    if (cnt) cnt->c++;
-                }
+        s[e] = tet_side2(G, a, b, j, k, dj, dk, cnt);
+    }
+    int mlo = 0, mhi = -1, nhit = 0;
+    for (int f = 0; f < 4; ++f) {
+        // facet f = (a < b < c): inside iff orient(ab), orient(bc), orient(ca) agree
+        int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, cc = f == 3 ? 2 : 3;
+        int sab = s[tet_edge_index(a, b)], sbc = s[tet_edge_index(b, cc)], sac = s[tet_edge_index(a, cc)];
+        if (!(sab == sbc && sbc == -sac)) continue;
+        ++nhit;
+        const R* n = G.n[f];
+        int va = f == 0 ? 1 : 0;
+        R X[3];
+        X[j] = R(dj);
+        X[k] = R(dk);
+        X[l] = G.x[va][l] - (n[j] * (R(dj) - G.x[va][j]) + n[k] * (R(dk) - G.x[va][k])) / n[l];
+        int m = tet_facet_line_cell(G, f, l, j, k, dj, dk, (int)floor_r(X[l]), cnt);
+        if (G.ns[f][l] > 0)
+            mlo = m;  // entry: nodes above m are inside w.r.t. this facet
+        else
+            mhi = m;  // exit: nodes up to m are inside
+        if (m < 0 || m >= td[l]) continue;
+        R rhoX = rho_at(G, X);
+        for (int oj = 0; oj < 2; ++oj)
+            for (int ok = 0; ok < 2; ++ok) {
+                int v[3];
+                v[l] = m;
+                v[j] = dj - 1 + oj;
+                v[k] = dk - 1 + ok;
+                if (v[j] < 0 || v[j] >= td[j] || v[k] < 0 || v[k] >= td[k]) continue;
+                // cell above plane j (oj = 1) has inward normal +e_j there
+                acc(v[0], v[1], v[2], tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), X, rhoX, v));
+                if (cnt) cnt->d++;
             }
+    }
+    if (l != 0 || nhit != 2) return;
+    int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
+    for (int cx = n0; cx <= n1; ++cx) {
+        R X[3] = {R(cx), R(dj), R(dk)};
+        R rhoX = rho_at(G, X);
+        for (int o = 0; o < 8; ++o) {
+            int v[3] = {cx - 1 + (o & 1), dj - 1 + ((o >> 1) & 1), dk - 1 + ((o >> 2) & 1)};
+            if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1] || v[2] < 0 || v[2] >= td[2]) continue;
+            // node is the cell's upper corner along a when the cell index is node-1
+            R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
+            acc(v[0], v[1], v[2], tet_corner_A(G, X, rhoX, v, sg));
+            if (cnt) cnt->a++;
         }
     }
-    // ---- D: facets crossing cell edges, and A: grid nodes inside (scanned along x lines)
-    #pragma unroll
+}
+
+// all items of a unit, one after the other (host reference runs and single-thread use)
+template <typename R, class Acc>
+CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* cnt) {
+    for (int i = 0; i < 4; ++i) tet_item_vertex(G, i, td, acc, cnt);
+    for (int e = 0; e < 6; ++e)
+        for (int k = 0; k < 3; ++k) {
+            int c0, n = tet_crossings(G, e, k, td, c0);
+            for (int c = c0; c < c0 + n; ++c) tet_item_crossing(G, e, k, c, td, acc, cnt);
+        }
     for (int l = 0; l < 3; ++l) {
-        int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-        int dj0 = G.lo[j] + 1 > 0 ? G.lo[j] + 1 : 0, dj1 = G.hi[j] < td[j] ? G.hi[j] : td[j];
-        int dk0 = G.lo[k] + 1 > 0 ? G.lo[k] + 1 : 0, dk1 = G.hi[k] < td[k] ? G.hi[k] : td[k];
-        for (int dj = dj0; dj <= dj1; ++dj)
-            for (int dk = dk0; dk <= dk1; ++dk) {
-                int s[6];
-                #pragma unroll
-                for (int e = 0; e < 6; ++e) {
-                    int a, b, p, q;
-                    tet_edge(e, a, b, p, q);
-                    s[e] = tet_side2(G, a, b, j, k, dj, dk, cnt);
-                }
-                int mlo = 0, mhi = -1, nhit = 0;
-                #pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    // facet f = (a < b < c): inside iff orient(ab), orient(bc), orient(ca) agree
-                    int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, cc = f == 3 ? 2 : 3;
-                    int sab = s[tet_edge_index(a, b)], sbc = s[tet_edge_index(b, cc)], sac = s[tet_edge_index(a, cc)];
-                    if (!(sab == sbc && sbc == -sac)) continue;
-                    ++nhit;
-                    const R* n = G.n[f];
-                    int va = f == 0 ? 1 : 0;
-                    R X[3];
-                    X[j] = R(dj);
-                    X[k] = R(dk);
-                    X[l] = G.x[va][l] - (n[j] * (R(dj) - G.x[va][j]) + n[k] * (R(dk) - G.x[va][k])) / n[l];
-                    int m = tet_facet_line_cell(G, f, l, j, k, dj, dk, (int)floor_r(X[l]), cnt);
-                    if (G.nE[f][l] > 0)
-                        mlo = m;  // entry: nodes above m are inside w.r.t. this facet
-                    else
-                        mhi = m;  // exit: nodes up to m are inside
-                    if (m < 0 || m >= td[l]) continue;
-                    R rhoX = rho_at(G, X);
-                    for (int oj = 0; oj < 2; ++oj)
-                        for (int ok = 0; ok < 2; ++ok) {
-                            int v[3];
-                            v[l] = m;
-                            v[j] = dj - 1 + oj;
-                            v[k] = dk - 1 + ok;
-                            if (v[j] < 0 || v[j] >= td[j] || v[k] < 0 || v[k] >= td[k]) continue;
-                            // cell above plane j (oj = 1) has inward normal +e_j there
-                            acc(v[0], v[1], v[2],
-                                tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), X, rhoX, v));
-                            if (cnt) cnt->d++;
-                        }
-                }
-                if (l != 0 || nhit != 2) continue;
-                int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
-                for (int cx = n0; cx <= n1; ++cx) {
-                    R X[3] = {R(cx), R(dj), R(dk)};
-                    R rhoX = rho_at(G, X);
-                    for (int o = 0; o < 8; ++o) {
-                        int v[3] = {cx - 1 + (o & 1), dj - 1 + ((o >> 1) & 1), dk - 1 + ((o >> 2) & 1)};
-                        if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1] || v[2] < 0 || v[2] >= td[2])
-                            continue;
-                        // node is the cell's upper corner along a when the cell index is node-1
-                        R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
-                        acc(v[0], v[1], v[2], tet_corner_A(G, X, rhoX, v, sg));
-                        if (cnt) cnt->a++;
-                    }
-                }
-            }
+        int dj0, nj, dk0;
+        int n = tet_lines(G, l, td, dj0, nj, dk0);
+        for (int t = 0; t < n; ++t) tet_item_line(G, l, dj0 + t % nj, dk0 + t / nj, td, acc, cnt);
     }
 }
 
@@ -613,6 +646,8 @@ struct TriGeo {
     R B2;
     int cell[3][2];
     int lo[2], hi[2];
+    int anchor[3];  // absolute cell of the tile origin (third entry 0)
+    double mexact;  // |V| mean(rho) in FP64
 };
 
 template <typename R>
@@ -642,11 +677,15 @@ CDP_HD void tri_setup(const Tri& S, const int T[2], TriGeo<R>& G) {
     i64 e2x = G.Lt[2][0] - G.Lt[0][0], e2y = G.Lt[2][1] - G.Lt[0][1];
     i128 Dq = mul64(e1x, e2y) - mul64(e1y, e2x);
     double D = i128_to_real<double>(Dq, 2 * CDP_Q);
+    G.mexact = D * 0.5 * (S.rho[0] + S.rho[1] + S.rho[2]) * (1.0 / 3.0);
+    G.anchor[0] = S.anchor[0] + T[0];
+    G.anchor[1] = S.anchor[1] + T[1];
+    G.anchor[2] = 0;
     for (int k = 0; k < 3; ++k) G.rho[k] = (R)S.rho[k];
     R d1 = G.rho[1] - G.rho[0], d2 = G.rho[2] - G.rho[0];
     R ex1 = i64_to_real<R>(e1x, CDP_Q), ey1 = i64_to_real<R>(e1y, CDP_Q);
     R ex2 = i64_to_real<R>(e2x, CDP_Q), ey2 = i64_to_real<R>(e2y, CDP_Q);
-    R invD = R(1.0 / D);
+    R invD = R(1) / R(D);
     G.g[0] = (d1 * ey2 - d2 * ey1) * invD;
     G.g[1] = (d2 * ex1 - d1 * ex2) * invD;
     for (int a = 0; a < 2; ++a) G.c[a] = (G.x[0][a] + G.x[1][a] + G.x[2][a]) * R(1.0 / 3.0);
@@ -747,84 +786,114 @@ CDP_HD R tri_corner_C(const TriGeo<R>& G, int a, int b, int o, int k, int dirk, 
 }
 
 template <typename R, class Acc>
-CDP_HD void tri_unit(const TriGeo<R>& G, const int td[2], Acc& acc, UnitCounts* cnt) {
-    for (int i = 0; i < 3; ++i) {
-        const int* v = G.cell[i];
-        if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1]) {
-            acc(v[0], v[1], 0, tri_corner_B(G, i, v));
-            if (cnt) cnt->b++;
-        }
+CDP_HD void tri_item_vertex(const TriGeo<R>& G, int i, const int td[2], Acc& acc, UnitCounts* cnt) {
+    const int v[2] = {G.cell[i][0], G.cell[i][1]};
+    if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1]) {
+        acc(v[0], v[1], 0, tri_corner_B(G, i, v));
+        if (cnt) cnt->b++;
     }
+}
+
+// edge opposite vertex o as (a < b)
+CDP_HD void tri_edge(int o, int& a, int& b) {
+    a = o == 0 ? 1 : 0;
+    b = o == 2 ? 1 : 2;
+}
+
+template <typename R>
+CDP_HD int tri_crossings(const TriGeo<R>& G, int o, int k, const int td[2], int& c0) {
+    int a, b;
+    tri_edge(o, a, b);
+    int ca = G.cell[a][k], cb = G.cell[b][k];
+    c0 = (ca < cb ? ca : cb) + 1;
+    int c1 = ca < cb ? cb : ca;
+    if (c0 < 0) c0 = 0;
+    if (c1 > td[k]) c1 = td[k];
+    return c1 >= c0 ? c1 - c0 + 1 : 0;
+}
+
+template <typename R, class Acc>
+CDP_HD void tri_item_crossing(const TriGeo<R>& G, int o, int k, int c, const int td[2], Acc& acc, UnitCounts* cnt) {
+    int a, b;
+    tri_edge(o, a, b);
+    int j = 1 - k;
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    R ev[2] = {G.x[b][0] - G.x[a][0], G.x[b][1] - G.x[a][1]};
+    R t = (R(c) - G.x[a][k]) / ev[k];
+    R X[2];
+    X[j] = G.x[a][j] + t * ev[j];
+    X[k] = R(c);
+    int cj = tri_cross_cell(G, a, b, k, c, (int)floor_r(X[j]), dirk, cnt);
+    if (cj < 0 || cj >= td[j]) return;
+    R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+    for (int side = 0; side < 2; ++side) {
+        int vk = side == 0 ? c - 1 : c;
+        if (vk < 0 || vk >= td[k]) continue;
+        int v[2];
+        v[k] = vk;
+        v[j] = cj;
+        acc(v[0], v[1], 0, tri_corner_C(G, a, b, o, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
+        if (cnt) cnt->c++;
+    }
+}
+
+// rows of grid nodes along x inside the tile: y = dy0 .. dy0 + n - 1
+template <typename R>
+CDP_HD int tri_rows(const TriGeo<R>& G, const int td[2], int& dy0) {
+    dy0 = G.lo[1] + 1 > 0 ? G.lo[1] + 1 : 0;
+    int dy1 = G.hi[1] < td[1] ? G.hi[1] : td[1];
+    return dy1 >= dy0 ? dy1 - dy0 + 1 : 0;
+}
+
+// A: the grid nodes of row y = dy inside the triangle (between the two crossing edges)
+template <typename R, class Acc>
+CDP_HD void tri_item_row(const TriGeo<R>& G, int dy, const int td[2], Acc& acc, UnitCounts* cnt) {
+    int mlo = 0, mhi = -1, nhit = 0;
     for (int o = 0; o < 3; ++o) {
-        int a = o == 0 ? 1 : 0, b = o == 2 ? 1 : 2;  // edge opposite o, a < b
+        int a, b;
+        tri_edge(o, a, b);
+        int ca = G.cell[a][1], cb = G.cell[b][1];
+        int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
+        if (dy < c0 || dy > c1) continue;
+        int dirk = cb > ca ? 1 : -1;
+        R t = (R(dy) - G.x[a][1]) / (G.x[b][1] - G.x[a][1]);
+        R xx = G.x[a][0] + t * (G.x[b][0] - G.x[a][0]);
+        int m = tri_cross_cell(G, a, b, 1, dy, (int)floor_r(xx), dirk, cnt);
+        ++nhit;
+        if (G.nE[o][0] > 0)
+            mlo = m;
+        else
+            mhi = m;
+    }
+    if (nhit != 2) return;
+    int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
+    for (int cx = n0; cx <= n1; ++cx) {
+        R X[2] = {R(cx), R(dy)};
+        R rhoX = G.rhoc + G.g[0] * (X[0] - G.c[0]) + G.g[1] * (X[1] - G.c[1]);
+        for (int o = 0; o < 4; ++o) {
+            int v[2] = {cx - 1 + (o & 1), dy - 1 + ((o >> 1) & 1)};
+            if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1]) continue;
+            R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1);
+            R O[2], P[2];
+            tri_origin(G, v, O);
+            P[0] = X[0] - O[0];
+            P[1] = X[1] - O[1];
+            acc(v[0], v[1], 0, sg * P[0] * P[1] * (rhoX - R(0.5) * (G.g[0] * P[0] + G.g[1] * P[1])));
+            if (cnt) cnt->a++;
+        }
+    }
+}
+
+template <typename R, class Acc>
+CDP_HD void tri_unit(const TriGeo<R>& G, const int td[2], Acc& acc, UnitCounts* cnt) {
+    for (int i = 0; i < 3; ++i) tri_item_vertex(G, i, td, acc, cnt);
+    for (int o = 0; o < 3; ++o)
         for (int k = 0; k < 2; ++k) {
-            int ca = G.cell[a][k], cb = G.cell[b][k];
-            if (ca == cb) continue;
-            int j = 1 - k;
-            int dirk = cb > ca ? 1 : -1;
-            int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
-            // rows along x (k = 1) are needed over the whole tile for the A scan; columns only inside
-            if (c0 < 0) c0 = 0;
-            if (c1 > td[k]) c1 = td[k];
-            R ev[2] = {G.x[b][0] - G.x[a][0], G.x[b][1] - G.x[a][1]};
-            R rinv = R(1) / ev[k];
-            for (int c = c0; c <= c1; ++c) {
-                R t = (R(c) - G.x[a][k]) * rinv;
-                R X[2];
-                X[j] = G.x[a][j] + t * ev[j];
-                X[k] = R(c);
-                int cj = tri_cross_cell(G, a, b, k, c, (int)floor_r(X[j]), dirk, cnt);
-                if (cj < 0 || cj >= td[j]) continue;
-                R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
-                for (int side = 0; side < 2; ++side) {
-                    int vk = side == 0 ? c - 1 : c;
-                    if (vk < 0 || vk >= td[k]) continue;
-                    int v[2];
-                    v[k] = vk;
-                    v[j] = cj;
-                    acc(v[0], v[1], 0, tri_corner_C(G, a, b, o, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
-                    if (cnt) cnt->c++;
-                }
-            }
+            int c0, n = tri_crossings(G, o, k, td, c0);
+            for (int c = c0; c < c0 + n; ++c) tri_item_crossing(G, o, k, c, td, acc, cnt);
         }
-    }
-    // A: nodes inside, scanned along rows y = dy
-    int dy0 = G.lo[1] + 1 > 0 ? G.lo[1] + 1 : 0, dy1 = G.hi[1] < td[1] ? G.hi[1] : td[1];
-    for (int dy = dy0; dy <= dy1; ++dy) {
-        int mlo = 0, mhi = -1, nhit = 0;
-        for (int o = 0; o < 3; ++o) {
-            int a = o == 0 ? 1 : 0, b = o == 2 ? 1 : 2;
-            int ca = G.cell[a][1], cb = G.cell[b][1];
-            int c0 = (ca < cb ? ca : cb) + 1, c1 = ca < cb ? cb : ca;
-            if (dy < c0 || dy > c1) continue;
-            int dirk = cb > ca ? 1 : -1;
-            R t = (R(dy) - G.x[a][1]) / (G.x[b][1] - G.x[a][1]);
-            R xx = G.x[a][0] + t * (G.x[b][0] - G.x[a][0]);
-            int m = tri_cross_cell(G, a, b, 1, dy, (int)floor_r(xx), dirk, cnt);
-            ++nhit;
-            if (G.nE[o][0] > 0)
-                mlo = m;
-            else
-                mhi = m;
-        }
-        if (nhit != 2) continue;
-        int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
-        for (int cx = n0; cx <= n1; ++cx) {
-            R X[2] = {R(cx), R(dy)};
-            R rhoX = G.rhoc + G.g[0] * (X[0] - G.c[0]) + G.g[1] * (X[1] - G.c[1]);
-            for (int o = 0; o < 4; ++o) {
-                int v[2] = {cx - 1 + (o & 1), dy - 1 + ((o >> 1) & 1)};
-                if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1]) continue;
-                R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1);
-                R O[2], P[2];
-                tri_origin(G, v, O);
-                P[0] = X[0] - O[0];
-                P[1] = X[1] - O[1];
-                acc(v[0], v[1], 0, sg * P[0] * P[1] * (rhoX - R(0.5) * (G.g[0] * P[0] + G.g[1] * P[1])));
-                if (cnt) cnt->a++;
-            }
-        }
-    }
+    int dy0, n = tri_rows(G, td, dy0);
+    for (int t = 0; t < n; ++t) tri_item_row(G, dy0 + t, td, acc, cnt);
 }
 
 }  // namespace cdp

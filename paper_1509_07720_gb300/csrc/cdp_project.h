@@ -7,9 +7,10 @@
 
 namespace cdp {
 
-constexpr int CDP_BLOCK = 128;             // threads per block of the projection kernels
-constexpr int CDP_ONE_THREAD_CELLS = 512;  // bounding boxes up to this many cells: one thread
-constexpr int CDP_TILE = 8;                // tile edge (cells) of the larger simplices
+constexpr int CDP_WBLOCK = 128;   // threads per block of the projection kernel (4 warps)
+constexpr int CDP_CHUNK = 16;     // simplices per warp chunk (one per lane during set-up)
+constexpr int CDP_LOG_WTBL = 10;  // per-warp piece table: 2^10 entries
+constexpr int CDP_WTBL = 1 << CDP_LOG_WTBL;
 
 // Per-call device counters (zeroed at the start of every projection).
 struct Counters {
@@ -36,6 +37,8 @@ struct LaunchArgs {
 };
 
 cudaError_t configure_all();
+// resident blocks per SM of the projection kernel (occupancy calculator)
+int resident_blocks(int dim, int fp32);
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
                         const double* rho, cudaStream_t st);
 // `mid` (optional) is recorded between the one-thread kernel and the tiled kernel

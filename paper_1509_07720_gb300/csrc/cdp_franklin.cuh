@@ -139,11 +139,17 @@ CDP_HD int tet_edge_index(int i, int j) {
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
+// Register-friendly access to 3-vectors with a run-time index (a runtime-indexed local array
+// would be placed in local memory).
+template <typename T>
+CDP_HD T pick3(T a0, T a1, T a2, int i) { return i == 0 ? a0 : (i == 1 ? a1 : a2); }
+
 // Per-unit working set of a tetrahedron: coordinates relative to the unit's tile origin.
 template <typename R>
 struct TetGeo {
     i64 Lt[4][3];          // exact, relative to the tile origin
-    R x[4][3];             // rounded copies
+    R x[4][3];             // rounded copies (high part)
+    R xl[4][3];            // low part: x + xl is the exact coordinate to twice the precision of R
     R n[4][3];             // unit inward normals of the facets (facet f is opposite vertex f)
     R g[3];                // grad rho (per cell length)
     R rho[4];
@@ -172,6 +178,16 @@ CDP_HD void facet_normal_exact(const i64 L[4][3], int f, i128 out[3]) {
     cross_exact(d1, d2, out);
 }
 
+template <typename R>
+CDP_HD R low_part(i64 L, R hi);
+template <>
+CDP_HD float low_part<float>(i64 L, float hi) {
+    i64 Lhi = (i64)llrintf(ldexpf(hi, CDP_Q));  // exact: hi has 24 bits and |hi| < 2^13
+    return ldexpf((float)(L - Lhi), -CDP_Q);
+}
+template <>
+CDP_HD double low_part<double>(i64, double) { return 0.0; }
+
 // Fill the working set for the tile whose lowest cell is T (relative to the anchor).
 template <typename R>
 CDP_HD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
@@ -179,6 +195,7 @@ CDP_HD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
         for (int a = 0; a < 3; ++a) {
             G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
             G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
+            G.xl[k][a] = low_part<R>(G.Lt[k][a], G.x[k][a]);
             G.cell[k][a] = S.cell[k][a] - T[a];
         }
     for (int a = 0; a < 3; ++a) {
@@ -240,16 +257,15 @@ CDP_HD int tet_side2(const TetGeo<R>& G, int i, int j, int u, int v, int pu, int
     return side2_exact(G.Lt[i][u], G.Lt[i][v], G.Lt[j][u], G.Lt[j][v], (i64)pu << CDP_Q, (i64)pv << CDP_Q);
 }
 
-// perturbed side of grid node gn (tile frame) w.r.t. facet f: > 0 inside
+// perturbed side of grid node (g0, g1, g2) (tile frame) w.r.t. facet f: > 0 inside
 template <typename R>
-CDP_HD int tet_side3(const TetGeo<R>& G, int f, const int gn[3], UnitCounts* cnt) {
+CDP_HD int tet_side3(const TetGeo<R>& G, int f, int g0, int g1, int g2, UnitCounts* cnt) {
     int a = f == 0 ? 1 : 0;  // a vertex of facet f
-    R val = G.n[f][0] * (R(gn[0]) - G.x[a][0]) + G.n[f][1] * (R(gn[1]) - G.x[a][1]) +
-            G.n[f][2] * (R(gn[2]) - G.x[a][2]);
+    R val = G.n[f][0] * (R(g0) - G.x[a][0]) + G.n[f][1] * (R(g1) - G.x[a][1]) + G.n[f][2] * (R(g2) - G.x[a][2]);
     if (val > G.B3) return 1;
     if (val < -G.B3) return -1;
     if (cnt) cnt->exact++;
-    i64 gp[3] = {(i64)gn[0] << CDP_Q, (i64)gn[1] << CDP_Q, (i64)gn[2] << CDP_Q};
+    i64 gp[3] = {(i64)g0 << CDP_Q, (i64)g1 << CDP_Q, (i64)g2 << CDP_Q};
     i128 nE[3];
     facet_normal_exact(G.Lt, f, nE);
     return side3_exact(nE, G.Lt[a], gp);
@@ -288,23 +304,20 @@ CDP_HD int tet_cross_cell(const TetGeo<R>& G, int a, int b, int k, int c, int j,
 
 // cell index along l of the crossing of facet f with the grid line along l through (dj, dk)
 template <typename R>
-CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int j, int k, int dj, int dk, int guess,
-                               UnitCounts* cnt) {
+CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int dj, int dk, int guess, UnitCounts* cnt) {
     int lo = G.lo[l], hi = G.hi[l];
     int m = guess < lo ? lo : (guess > hi ? hi : guess);
     int up = G.ns[f][l] > 0 ? 1 : -1;  // side3 grows along +l when the normal's l component is > 0
-    int gn[3];
-    gn[j] = dj;
-    gn[k] = dk;
+    // node (coordinate t along l) in (x, y, z): l = 0 -> (t, dj, dk), l = 1 -> (dj, t, dk), l = 2 -> (dj, dk, t)
     for (int it = 0; it <= hi - lo + 1; ++it) {
-        gn[l] = m;
-        int s0 = tet_side3(G, f, gn, cnt);
+        int s0 = l == 0 ? tet_side3(G, f, m, dj, dk, cnt)
+                        : (l == 1 ? tet_side3(G, f, dj, m, dk, cnt) : tet_side3(G, f, dj, dk, m, cnt));
         if (m > lo && s0 == up) {  // node m already past the crossing
             --m;
             continue;
         }
-        gn[l] = m + 1;
-        int s1 = tet_side3(G, f, gn, cnt);
+        int s1 = l == 0 ? tet_side3(G, f, m + 1, dj, dk, cnt)
+                        : (l == 1 ? tet_side3(G, f, dj, m + 1, dk, cnt) : tet_side3(G, f, dj, dk, m + 1, cnt));
         if (m < hi && s1 == -up) {
             ++m;
             continue;
@@ -315,97 +328,81 @@ CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int j, int k, i
 }
 
 // ------------------------------------------------------------------------------------------
-// contributions of one (corner, cell) incidence; `v` = cell (tile frame)
+// contributions of one (corner, cell) incidence; P = corner - O with O the piece's origin
 // ------------------------------------------------------------------------------------------
 
+// origin of the piece in cell (v0, v1, v2): the centroid clamped into the cell
 template <typename R>
-CDP_HD void piece_origin(const TetGeo<R>& G, const int v[3], R O[3]) {
-    for (int a = 0; a < 3; ++a) O[a] = clamp_r(G.c[a], R(v[a]), R(v[a] + 1));
+CDP_HD void piece_origin(const TetGeo<R>& G, int v0, int v1, int v2, R O[3]) {
+    O[0] = clamp_r(G.c[0], R(v0), R(v0 + 1));
+    O[1] = clamp_r(G.c[1], R(v1), R(v1 + 1));
+    O[2] = clamp_r(G.c[2], R(v2), R(v2 + 1));
 }
 
+// B: simplex vertex i; P = x_i - O
 template <typename R>
-CDP_HD R rho_at(const TetGeo<R>& G, const R X[3]) {
-    return G.rhoc + G.g[0] * (X[0] - G.c[0]) + G.g[1] * (X[1] - G.c[1]) + G.g[2] * (X[2] - G.c[2]);
-}
-
-// unit vector of edge (a -> b), a < b
-template <typename R>
-CDP_HD void edge_unit(const TetGeo<R>& G, int a, int b, R ev[3]) {
-    for (int t = 0; t < 3; ++t) ev[t] = i64_to_real<R>(G.Lt[b][t] - G.Lt[a][t], CDP_Q);
-    R inv = rsqrt_r<R>(dot3(ev, ev));
-    for (int t = 0; t < 3; ++t) ev[t] *= inv;
-}
-
-// B: simplex vertex i in cell v
-template <typename R>
-CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const int v[3]) {
-    R O[3], P[3];
-    piece_origin(G, v, O);
-    for (int a = 0; a < 3; ++a) P[a] = G.x[i][a] - O[a];
+CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const R P[3]) {
     R s = 0;
     for (int j = 0; j < 4; ++j) {
         if (j == i) continue;
         int a = i < j ? i : j, b = i < j ? j : i;
-        R ev[3], T[3];
-        edge_unit(G, a, b, ev);
+        R ev[3];
+        for (int t = 0; t < 3; ++t) ev[t] = (G.x[b][t] - G.x[a][t]) + (G.xl[b][t] - G.xl[a][t]);
+        R inv = rsqrt_r<R>(dot3(ev, ev));
+        for (int t = 0; t < 3; ++t) ev[t] *= inv;
         R sg = i == a ? R(1) : R(-1);
-        for (int t = 0; t < 3; ++t) T[t] = sg * ev[t];
+        R T[3] = {sg * ev[0], sg * ev[1], sg * ev[2]};
         for (int f = 0; f < 4; ++f) {
             if (f == i || f == j) continue;
             int r = 6 - i - j - f;  // third vertex of facet f
+            const R nf[3] = {G.n[f][0], G.n[f][1], G.n[f][2]};
             R N[3];
-            cross3(G.n[f], ev, N);
+            cross3(nf, ev, N);
             R ps = R(parity4(a, b, r, f));
             for (int t = 0; t < 3; ++t) N[t] *= ps;
-            s += trip3(P, T, N, G.n[f], G.rho[i], G.g);
+            s += trip3(P, T, N, nf, G.rho[i], G.g);
         }
     }
     return R(-1.0 / 6.0) * s;
 }
 
-// C: edge e crossing the face x_k = (tile-frame plane) at X, cell on side sigma
+// C: edge e crossing the face x_k = c (cell on side sigma); ev = unit edge vector (a -> b)
 template <typename R>
-CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const R X[3], R rhoX, const int v[3]) {
+CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const R ev[3], const R P[3], R rhoX) {
     int a, b, p, q;
     tet_edge(e, a, b, p, q);
-    R O[3], P[3];
-    piece_origin(G, v, O);
-    for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
-    R ev[3];
-    edge_unit(G, a, b, ev);
     R s = 0;
     // the simplex edge, oriented into the cell, with its two facets (f_p contains q, f_q contains p)
-    R T[3], N[3];
     R so = sigma * R(dirk);
-    for (int t = 0; t < 3; ++t) T[t] = so * ev[t];
-    cross3(G.n[p], ev, N);
+    const R T[3] = {so * ev[0], so * ev[1], so * ev[2]};
+    const R np_[3] = {G.n[p][0], G.n[p][1], G.n[p][2]};
+    const R nq_[3] = {G.n[q][0], G.n[q][1], G.n[q][2]};
+    R N[3];
+    cross3(np_, ev, N);
     R pp = R(parity4(a, b, q, p));
     for (int t = 0; t < 3; ++t) N[t] *= pp;
-    s += trip3(P, T, N, G.n[p], rhoX, G.g);
-    cross3(G.n[q], ev, N);
+    s += trip3(P, T, N, np_, rhoX, G.g);
+    cross3(nq_, ev, N);
     R pq = R(parity4(a, b, p, q));
     for (int t = 0; t < 3; ++t) N[t] *= pq;
-    s += trip3(P, T, N, G.n[q], rhoX, G.g);
+    s += trip3(P, T, N, nq_, rhoX, G.g);
     // facet-face lines u_p (towards q's side) and u_q (towards p's side)
     R lam = R(-parity4(a, b, p, q)) * R(dirk);
-    R Bk[3] = {0, 0, 0};
-    Bk[k] = sigma;
+    const R ek[3] = {R(k == 0), R(k == 1), R(k == 2)};
+    const R Bk[3] = {sigma * ek[0], sigma * ek[1], sigma * ek[2]};
     for (int w = 0; w < 2; ++w) {
-        const R* n = G.n[w == 0 ? p : q];
+        const R* n = w == 0 ? np_ : nq_;
         R su = w == 0 ? lam : -lam;
-        R r2 = R(0);
-        for (int t = 0; t < 3; ++t)
-            if (t != k) r2 += n[t] * n[t];
+        R nk = pick3(n[0], n[1], n[2], k);
+        R r2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2] - nk * nk;
         R ir = rsqrt_r<R>(r2);
-        R ek[3] = {0, 0, 0};
-        ek[k] = 1;
         R U[3];
         cross3(n, ek, U);
         for (int t = 0; t < 3; ++t) U[t] *= su * ir;
         R N1[3], N2[3];
         for (int t = 0; t < 3; ++t) {
-            N1[t] = sigma * (ek[t] - n[k] * n[t]) * ir;  // in the facet, towards the cell face side
-            N2[t] = (n[t] - n[k] * ek[t]) * ir;          // in the face, towards the facet side
+            N1[t] = sigma * (ek[t] - nk * n[t]) * ir;  // in the facet, towards the cell face side
+            N2[t] = (n[t] - nk * ek[t]) * ir;          // in the face, towards the facet side
         }
         s += trip3(P, U, N1, n, rhoX, G.g);
         s += trip3(P, U, N2, Bk, rhoX, G.g);
@@ -413,53 +410,47 @@ CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const
     return R(-1.0 / 6.0) * s;
 }
 
-// D: facet f crossing the grid line along l at X; cell on sides (sj, sk) of the planes j, k
+// D: facet f crossing the grid line along l (other axes j < k); cell on sides (sj, sk)
 template <typename R>
-CDP_HD R tet_corner_D(const TetGeo<R>& G, int f, int l, int j, int k, R sj, R sk, const R X[3], R rhoX,
-                      const int v[3]) {
-    R O[3], P[3];
-    piece_origin(G, v, O);
-    for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
-    const R* n = G.n[f];
+CDP_HD R tet_corner_D(const TetGeo<R>& G, int f, int l, int j, int k, R sj, R sk, const R P[3], R rhoX) {
+    const R n[3] = {G.n[f][0], G.n[f][1], G.n[f][2]};
     R tau = G.ns[f][l] > 0 ? R(1) : R(-1);
     R eps = (l == 1) ? R(-1) : R(1);  // Levi-Civita of (j, k, l) with j < k
+    const R ej[3] = {R(j == 0), R(j == 1), R(j == 2)};
+    const R ek[3] = {R(k == 0), R(k == 1), R(k == 2)};
+    const R El[3] = {tau * R(l == 0), tau * R(l == 1), tau * R(l == 2)};
+    const R Ej[3] = {sj * ej[0], sj * ej[1], sj * ej[2]};
+    const R Ek[3] = {sk * ek[0], sk * ek[1], sk * ek[2]};
+    R nj = pick3(n[0], n[1], n[2], j), nk = pick3(n[0], n[1], n[2], k), nl = pick3(n[0], n[1], n[2], l);
     R s = 0;
-    R El[3] = {0, 0, 0}, Ej[3] = {0, 0, 0}, Ek[3] = {0, 0, 0};
-    El[l] = tau;
-    Ej[j] = sj;
-    Ek[k] = sk;
     s += trip3(P, El, Ek, Ej, rhoX, G.g);  // grid line with face j
     s += trip3(P, El, Ej, Ek, rhoX, G.g);  // grid line with face k
     // facet/face_j line, oriented towards the k side of the cell
     {
-        R ej[3] = {0, 0, 0};
-        ej[j] = 1;
-        R ir = rsqrt_r<R>(n[k] * n[k] + n[l] * n[l]);
+        R ir = rsqrt_r<R>(nk * nk + nl * nl);
         R U[3];
         cross3(n, ej, U);
         R su = sk * eps * tau * ir;
         for (int t = 0; t < 3; ++t) U[t] *= su;
         R N1[3], N2[3];
         for (int t = 0; t < 3; ++t) {
-            N1[t] = sj * (ej[t] - n[j] * n[t]) * ir;
-            N2[t] = (n[t] - n[j] * ej[t]) * ir;
+            N1[t] = sj * (ej[t] - nj * n[t]) * ir;
+            N2[t] = (n[t] - nj * ej[t]) * ir;
         }
         s += trip3(P, U, N1, n, rhoX, G.g);
         s += trip3(P, U, N2, Ej, rhoX, G.g);
     }
     // facet/face_k line, oriented towards the j side of the cell
     {
-        R ek[3] = {0, 0, 0};
-        ek[k] = 1;
-        R ir = rsqrt_r<R>(n[j] * n[j] + n[l] * n[l]);
+        R ir = rsqrt_r<R>(nj * nj + nl * nl);
         R U[3];
         cross3(n, ek, U);
         R su = -sj * eps * tau * ir;
         for (int t = 0; t < 3; ++t) U[t] *= su;
         R N1[3], N2[3];
         for (int t = 0; t < 3; ++t) {
-            N1[t] = sk * (ek[t] - n[k] * n[t]) * ir;
-            N2[t] = (n[t] - n[k] * ek[t]) * ir;
+            N1[t] = sk * (ek[t] - nk * n[t]) * ir;
+            N2[t] = (n[t] - nk * ek[t]) * ir;
         }
         s += trip3(P, U, N1, n, rhoX, G.g);
         s += trip3(P, U, N2, Ek, rhoX, G.g);
@@ -467,14 +458,18 @@ CDP_HD R tet_corner_D(const TetGeo<R>& G, int f, int l, int j, int k, R sj, R sk
     return R(-1.0 / 6.0) * s;
 }
 
-// A: grid node X (integer, tile frame) inside the simplex; cell on side s (s_a = +1 when the
-// node is the cell's upper corner along a)
+// A: grid node inside the simplex; cell on side s (sgn = product of s_a, s_a = +1 when the node is
+// the cell's upper corner along a)
 template <typename R>
-CDP_HD R tet_corner_A(const TetGeo<R>& G, const R X[3], R rhoX, const int v[3], R sgn) {
-    R O[3], P[3];
-    piece_origin(G, v, O);
-    for (int t = 0; t < 3; ++t) P[t] = X[t] - O[t];
+CDP_HD R tet_corner_A(const TetGeo<R>& G, const R P[3], R rhoX, R sgn) {
     return sgn * P[0] * P[1] * P[2] * (rhoX - R(0.5) * dot3(G.g, P));
+}
+
+// density at the corner whose offset from the origin O of its piece is P
+template <typename R>
+CDP_HD R rho_from_P(const TetGeo<R>& G, const R P[3], const R O[3]) {
+    return G.rhoc + G.g[0] * (P[0] + (O[0] - G.c[0])) + G.g[1] * (P[1] + (O[1] - G.c[1])) +
+           G.g[2] * (P[2] + (O[2] - G.c[2]));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -487,9 +482,12 @@ CDP_HD R tet_corner_A(const TetGeo<R>& G, const R X[3], R rhoX, const int v[3], 
 
 template <typename R, class Acc>
 CDP_HD void tet_item_vertex(const TetGeo<R>& G, int i, const int td[3], Acc& acc, UnitCounts* cnt) {
-    const int v[3] = {G.cell[i][0], G.cell[i][1], G.cell[i][2]};
-    if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1] && v[2] >= 0 && v[2] < td[2]) {
-        acc(v[0], v[1], v[2], tet_corner_B(G, i, v));
+    const int v0 = G.cell[i][0], v1 = G.cell[i][1], v2 = G.cell[i][2];
+    if (v0 >= 0 && v0 < td[0] && v1 >= 0 && v1 < td[1] && v2 >= 0 && v2 < td[2]) {
+        R O[3], P[3];
+        piece_origin(G, v0, v1, v2, O);
+        for (int a = 0; a < 3; ++a) P[a] = (G.x[i][a] - O[a]) + G.xl[i][a];
+        acc(v0, v1, v2, tet_corner_B(G, i, P));
         if (cnt) cnt->b++;
     }
 }
@@ -503,7 +501,8 @@ CDP_HD int tet_crossings(const TetGeo<R>& G, int e, int k, const int td[3], int&
     c0 = (ca < cb ? ca : cb) + 1;
     int c1 = ca < cb ? cb : ca;
     if (c0 < 0) c0 = 0;
-    if (c1 > td[k]) c1 = td[k];
+    int tk = pick3(td[0], td[1], td[2], k);
+    if (c1 > tk) c1 = tk;
     return c1 >= c0 ? c1 - c0 + 1 : 0;
 }
 
@@ -514,24 +513,36 @@ CDP_HD void tet_item_crossing(const TetGeo<R>& G, int e, int k, int c, const int
     int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
     int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
     R ev[3];
-    for (int t = 0; t < 3; ++t) ev[t] = G.x[b][t] - G.x[a][t];
-    R t = (R(c) - G.x[a][k]) / ev[k];
-    R X[3];
-    for (int w = 0; w < 3; ++w) X[w] = G.x[a][w] + t * ev[w];
-    X[k] = R(c);
-    int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X[j1]), dirk, cnt);
-    if (cj1 < 0 || cj1 >= td[j1]) return;
-    int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X[j2]), dirk, cnt);
-    if (cj2 < 0 || cj2 >= td[j2]) return;
+    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
+    R evk = pick3(ev[0], ev[1], ev[2], k);
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    // rounded crossing point (for the cell guesses and rho) and its exact-ish offsets from vertex a
+    R d[3] = {t * ev[0], t * ev[1], t * ev[2]};
+    R X1 = G.x[a][j1] + pick3(d[0], d[1], d[2], j1);
+    R X2 = G.x[a][j2] + pick3(d[0], d[1], d[2], j2);
+    int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X1), dirk, cnt);
+    if (cj1 < 0 || cj1 >= pick3(td[0], td[1], td[2], j1)) return;
+    int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X2), dirk, cnt);
+    if (cj2 < 0 || cj2 >= pick3(td[0], td[1], td[2], j2)) return;
     R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+    R inv = rsqrt_r<R>(dot3(ev, ev));
+    R eu[3] = {ev[0] * inv, ev[1] * inv, ev[2] * inv};
+    int tk = pick3(td[0], td[1], td[2], k);
     for (int side = 0; side < 2; ++side) {
         int vk = side == 0 ? c - 1 : c;
-        if (vk < 0 || vk >= td[k]) continue;
-        int v[3];
-        v[k] = vk;
-        v[j1] = cj1;
-        v[j2] = cj2;
-        acc(v[0], v[1], v[2], tet_corner_C(G, e, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
+        if (vk < 0 || vk >= tk) continue;
+        int v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
+        int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
+        int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
+        R O[3], P[3];
+        piece_origin(G, v0, v1, v2, O);
+        for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + d[w]);
+        // the crossing lies exactly on the plane
+        R Pk = R(c) - pick3(O[0], O[1], O[2], k);
+        P[0] = k == 0 ? Pk : P[0];
+        P[1] = k == 1 ? Pk : P[1];
+        P[2] = k == 2 ? Pk : P[2];
+        acc(v0, v1, v2, tet_corner_C(G, e, k, dirk, side == 0 ? R(-1) : R(1), eu, P, rhoX));
         if (cnt) cnt->c++;
     }
 }
@@ -541,69 +552,222 @@ template <typename R>
 CDP_HD int tet_lines(const TetGeo<R>& G, int l, const int td[3], int& dj0, int& nj, int& dk0) {
     int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
     dj0 = G.lo[j] + 1 > 0 ? G.lo[j] + 1 : 0;
-    int dj1 = G.hi[j] < td[j] ? G.hi[j] : td[j];
+    int tj = pick3(td[0], td[1], td[2], j), tk = pick3(td[0], td[1], td[2], k);
+    int dj1 = G.hi[j] < tj ? G.hi[j] : tj;
     dk0 = G.lo[k] + 1 > 0 ? G.lo[k] + 1 : 0;
-    int dk1 = G.hi[k] < td[k] ? G.hi[k] : td[k];
+    int dk1 = G.hi[k] < tk ? G.hi[k] : tk;
     nj = dj1 >= dj0 ? dj1 - dj0 + 1 : 0;
     int nk = dk1 >= dk0 ? dk1 - dk0 + 1 : 0;
     return nj * nk;
 }
 
-template <typename R, class Acc>
-CDP_HD void tet_item_line(const TetGeo<R>& G, int l, int dj, int dk, const int td[3], Acc& acc, UnitCounts* cnt) {
-    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    int s[6];
+// signs of the 6 projected edges against the line point (dj, dk): bit e set when positive
+template <typename R>
+CDP_HD unsigned tet_line_signs(const TetGeo<R>& G, int j, int k, int dj, int dk, UnitCounts* cnt) {
+    unsigned m = 0;
     for (int e = 0; e < 6; ++e) {
         int a, b, p, q;
         tet_edge(e, a, b, p, q);
-        s[e] = tet_side2(G, a, b, j, k, dj, dk, cnt);
+        if (tet_side2(G, a, b, j, k, dj, dk, cnt) > 0) m |= 1u << e;
     }
-    int mlo = 0, mhi = -1, nhit = 0;
+    return m;
+}
+
+// facets pierced by the line: bit f set (projection of facet f contains the line point)
+CDP_HD unsigned tet_pierced(unsigned sgn) {
+    unsigned hits = 0;
     for (int f = 0; f < 4; ++f) {
-        // facet f = (a < b < c): inside iff orient(ab), orient(bc), orient(ca) agree
         int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, cc = f == 3 ? 2 : 3;
-        int sab = s[tet_edge_index(a, b)], sbc = s[tet_edge_index(b, cc)], sac = s[tet_edge_index(a, cc)];
-        if (!(sab == sbc && sbc == -sac)) continue;
-        ++nhit;
-        const R* n = G.n[f];
+        unsigned sab = (sgn >> tet_edge_index(a, b)) & 1u, sbc = (sgn >> tet_edge_index(b, cc)) & 1u,
+                 sac = (sgn >> tet_edge_index(a, cc)) & 1u;
+        // orient(a,b), orient(b,c), orient(c,a) = -orient(a,c) all of one sign
+        if (sab == sbc && sbc != sac) hits |= 1u << f;
+    }
+    return hits;
+}
+
+template <typename R, class Acc>
+CDP_HD void tet_item_line(const TetGeo<R>& G, int l, int dj, int dk, const int td[3], Acc& acc, UnitCounts* cnt) {
+    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    unsigned hits = tet_pierced(tet_line_signs(G, j, k, dj, dk, cnt));
+    if (!hits) return;
+    int mlo = 0, mhi = -1;
+    int tj = pick3(td[0], td[1], td[2], j), tk = pick3(td[0], td[1], td[2], k), tl = pick3(td[0], td[1], td[2], l);
+    for (int f = 0; f < 4; ++f) {
+        if (!((hits >> f) & 1u)) continue;
         int va = f == 0 ? 1 : 0;
-        R X[3];
-        X[j] = R(dj);
-        X[k] = R(dk);
-        X[l] = G.x[va][l] - (n[j] * (R(dj) - G.x[va][j]) + n[k] * (R(dk) - G.x[va][k])) / n[l];
-        int m = tet_facet_line_cell(G, f, l, j, k, dj, dk, (int)floor_r(X[l]), cnt);
+        R nj = G.n[f][j], nk = G.n[f][k], nl = G.n[f][l];
+        // crossing coordinate along l, relative to vertex va: exact-ish offset
+        R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
+        R Xl = G.x[va][l] + off;
+        int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(Xl), cnt);
         if (G.ns[f][l] > 0)
             mlo = m;  // entry: nodes above m are inside w.r.t. this facet
         else
             mhi = m;  // exit: nodes up to m are inside
-        if (m < 0 || m >= td[l]) continue;
-        R rhoX = rho_at(G, X);
+        if (m < 0 || m >= tl) continue;
         for (int oj = 0; oj < 2; ++oj)
             for (int ok = 0; ok < 2; ++ok) {
-                int v[3];
-                v[l] = m;
-                v[j] = dj - 1 + oj;
-                v[k] = dk - 1 + ok;
-                if (v[j] < 0 || v[j] >= td[j] || v[k] < 0 || v[k] >= td[k]) continue;
+                int vj = dj - 1 + oj, vk = dk - 1 + ok;
+                if (vj < 0 || vj >= tj || vk < 0 || vk >= tk) continue;
+                int v0 = l == 0 ? m : vj;
+                int v1 = l == 1 ? m : (l == 0 ? vj : vk);
+                int v2 = l == 2 ? m : vk;
+                R O[3];
+                piece_origin(G, v0, v1, v2, O);
+                R Pl = (G.x[va][l] - pick3(O[0], O[1], O[2], l)) + (G.xl[va][l] + off);
+                R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
+                R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
+                R rhoX = rho_from_P(G, P, O);
                 // cell above plane j (oj = 1) has inward normal +e_j there
-                acc(v[0], v[1], v[2], tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), X, rhoX, v));
+                acc(v0, v1, v2, tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), P, rhoX));
                 if (cnt) cnt->d++;
             }
     }
-    if (l != 0 || nhit != 2) return;
+    // A: for lines along x, the grid nodes between the entry and the exit facet
+    if (l != 0 || ((hits & 1u) + ((hits >> 1) & 1u) + ((hits >> 2) & 1u) + ((hits >> 3) & 1u)) != 2u) return;
     int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
     for (int cx = n0; cx <= n1; ++cx) {
-        R X[3] = {R(cx), R(dj), R(dk)};
-        R rhoX = rho_at(G, X);
         for (int o = 0; o < 8; ++o) {
-            int v[3] = {cx - 1 + (o & 1), dj - 1 + ((o >> 1) & 1), dk - 1 + ((o >> 2) & 1)};
-            if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1] || v[2] < 0 || v[2] >= td[2]) continue;
+            int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
+            if (v0 < 0 || v0 >= td[0] || v1 < 0 || v1 >= td[1] || v2 < 0 || v2 >= td[2]) continue;
+            R O[3];
+            piece_origin(G, v0, v1, v2, O);
+            R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
             // node is the cell's upper corner along a when the cell index is node-1
             R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
-            acc(v[0], v[1], v[2], tet_corner_A(G, X, rhoX, v, sg));
+            acc(v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
             if (cnt) cnt->a++;
         }
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Split form for a work queue: the locate step of a crossing / a line yields compact records of
+// (corner, cell) incidences, and the evaluate step turns one record into its contribution, so
+// that the (costly) evaluations of a warp can run in full batches of identical work.
+//   C record: bits 0-10 c, 11-21 cj1, 22-32 cj2, 33 side, 34-35 k, 36-38 e
+//   D record: bits 0-10 m, 11-21 dj, 22-32 dk, 33 oj, 34 ok, 35-36 l, 37-38 f
+// (coordinates in the tile frame, 0 <= value < 2048).  Bits 40 and up are left to the caller.
+// ------------------------------------------------------------------------------------------
+typedef unsigned long long Rec;
+
+template <typename R, class Push>
+CDP_HD void tet_locate_crossing(const TetGeo<R>& G, int e, int k, int c, const int td[3], Push& push,
+                                UnitCounts* cnt) {
+    int a, b, p, q;
+    tet_edge(e, a, b, p, q);
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+    R ev[3];
+    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
+    R evk = pick3(ev[0], ev[1], ev[2], k);
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    R X1 = G.x[a][j1] + t * pick3(ev[0], ev[1], ev[2], j1);
+    R X2 = G.x[a][j2] + t * pick3(ev[0], ev[1], ev[2], j2);
+    int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X1), dirk, cnt);
+    if (cj1 < 0 || cj1 >= pick3(td[0], td[1], td[2], j1)) return;
+    int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X2), dirk, cnt);
+    if (cj2 < 0 || cj2 >= pick3(td[0], td[1], td[2], j2)) return;
+    int tk = pick3(td[0], td[1], td[2], k);
+    Rec base = (Rec)c | ((Rec)cj1 << 11) | ((Rec)cj2 << 22) | ((Rec)k << 34) | ((Rec)e << 36);
+    if (c - 1 >= 0 && c - 1 < tk) push(base);
+    if (c < tk) push(base | (1ull << 33));
+}
+
+// contribution of a C record; (v0, v1, v2) receives its cell
+template <typename R>
+CDP_HD R tet_eval_crossing(const TetGeo<R>& G, Rec r, int& v0, int& v1, int& v2) {
+    int c = (int)(r & 2047), cj1 = (int)((r >> 11) & 2047), cj2 = (int)((r >> 22) & 2047);
+    int side = (int)((r >> 33) & 1), k = (int)((r >> 34) & 3), e = (int)((r >> 36) & 7);
+    int a, b, p, q;
+    tet_edge(e, a, b, p, q);
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    int j1 = k == 0 ? 1 : 0;
+    R ev[3];
+    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
+    R evk = pick3(ev[0], ev[1], ev[2], k);
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    int vk = side ? c : c - 1;
+    v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
+    v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
+    v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
+    R O[3], P[3];
+    piece_origin(G, v0, v1, v2, O);
+    for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + t * ev[w]);
+    R Pk = R(c) - pick3(O[0], O[1], O[2], k);
+    P[0] = k == 0 ? Pk : P[0];
+    P[1] = k == 1 ? Pk : P[1];
+    P[2] = k == 2 ? Pk : P[2];
+    R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+    R inv = rsqrt_r<R>(dot3(ev, ev));
+    const R eu[3] = {ev[0] * inv, ev[1] * inv, ev[2] * inv};
+    return tet_corner_C(G, e, k, dirk, side ? R(1) : R(-1), eu, P, rhoX);
+}
+
+// locate the D corners of a grid line (records pushed) and add its A corners (grid nodes) directly
+template <typename R, class Push, class Acc>
+CDP_HD void tet_locate_line(const TetGeo<R>& G, int l, int dj, int dk, const int td[3], Push& push, Acc& acc,
+                            UnitCounts* cnt) {
+    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    unsigned hits = tet_pierced(tet_line_signs(G, j, k, dj, dk, cnt));
+    if (!hits) return;
+    int mlo = 0, mhi = -1;
+    int tj = pick3(td[0], td[1], td[2], j), tk = pick3(td[0], td[1], td[2], k), tl = pick3(td[0], td[1], td[2], l);
+    for (int f = 0; f < 4; ++f) {
+        if (!((hits >> f) & 1u)) continue;
+        int va = f == 0 ? 1 : 0;
+        R nj = G.n[f][j], nk = G.n[f][k], nl = G.n[f][l];
+        R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
+        int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(G.x[va][l] + off), cnt);
+        if (G.ns[f][l] > 0)
+            mlo = m;
+        else
+            mhi = m;
+        if (m < 0 || m >= tl) continue;
+        Rec base = (Rec)m | ((Rec)dj << 11) | ((Rec)dk << 22) | ((Rec)l << 35) | ((Rec)f << 37);
+        for (int oj = 0; oj < 2; ++oj)
+            for (int ok = 0; ok < 2; ++ok) {
+                int vj = dj - 1 + oj, vk = dk - 1 + ok;
+                if (vj < 0 || vj >= tj || vk < 0 || vk >= tk) continue;
+                push(base | ((Rec)oj << 33) | ((Rec)ok << 34));
+            }
+    }
+    if (l != 0 || ((hits & 1u) + ((hits >> 1) & 1u) + ((hits >> 2) & 1u) + ((hits >> 3) & 1u)) != 2u) return;
+    int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
+    for (int cx = n0; cx <= n1; ++cx) {
+        for (int o = 0; o < 8; ++o) {
+            int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
+            if (v0 < 0 || v0 >= td[0] || v1 < 0 || v1 >= td[1] || v2 < 0 || v2 >= td[2]) continue;
+            R O[3];
+            piece_origin(G, v0, v1, v2, O);
+            R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
+            R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
+            acc(v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
+            if (cnt) cnt->a++;
+        }
+    }
+}
+
+// contribution of a D record; (v0, v1, v2) receives its cell
+template <typename R>
+CDP_HD R tet_eval_line(const TetGeo<R>& G, Rec r, int& v0, int& v1, int& v2) {
+    int m = (int)(r & 2047), dj = (int)((r >> 11) & 2047), dk = (int)((r >> 22) & 2047);
+    int oj = (int)((r >> 33) & 1), ok = (int)((r >> 34) & 1), l = (int)((r >> 35) & 3), f = (int)((r >> 37) & 3);
+    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    int va = f == 0 ? 1 : 0;
+    R nj = G.n[f][j], nk = G.n[f][k], nl = G.n[f][l];
+    R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
+    int vj = dj - 1 + oj, vk = dk - 1 + ok;
+    v0 = l == 0 ? m : vj;
+    v1 = l == 1 ? m : (l == 0 ? vj : vk);
+    v2 = l == 2 ? m : vk;
+    R O[3];
+    piece_origin(G, v0, v1, v2, O);
+    R Pl = (G.x[va][l] - pick3(O[0], O[1], O[2], l)) + (G.xl[va][l] + off);
+    R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
+    R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
+    return tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), P, rho_from_P(G, P, O));
 }
 
 // all items of a unit, one after the other (host reference runs and single-thread use)
@@ -638,6 +802,7 @@ template <typename R>
 struct TriGeo {
     i64 Lt[3][2];
     R x[3][2];
+    R xl[3][2];   // low parts (x + xl exact to twice the precision of R)
     R n[3][2];    // unit inward normal of the edge opposite vertex k
     i64 nE[3][2]; // exact normals
     R g[2];
@@ -656,6 +821,7 @@ CDP_HD void tri_setup(const Tri& S, const int T[2], TriGeo<R>& G) {
         for (int a = 0; a < 2; ++a) {
             G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
             G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
+            G.xl[k][a] = low_part<R>(G.Lt[k][a], G.x[k][a]);
             G.cell[k][a] = S.cell[k][a] - T[a];
         }
     for (int a = 0; a < 2; ++a) {
@@ -740,56 +906,52 @@ CDP_HD int tri_cross_cell(const TriGeo<R>& G, int a, int b, int k, int c, int gu
 }
 
 template <typename R>
-CDP_HD void tri_origin(const TriGeo<R>& G, const int v[2], R O[2]) {
-    for (int a = 0; a < 2; ++a) O[a] = clamp_r(G.c[a], R(v[a]), R(v[a] + 1));
+CDP_HD void tri_origin(const TriGeo<R>& G, int v0, int v1, R O[2]) {
+    O[0] = clamp_r(G.c[0], R(v0), R(v0 + 1));
+    O[1] = clamp_r(G.c[1], R(v1), R(v1 + 1));
 }
 
-// B: vertex i in cell v
+// B: vertex i; P = x_i - O
 template <typename R>
-CDP_HD R tri_corner_B(const TriGeo<R>& G, int i, const int v[2]) {
-    R O[2], P[2];
-    tri_origin(G, v, O);
-    P[0] = G.x[i][0] - O[0];
-    P[1] = G.x[i][1] - O[1];
+CDP_HD R tri_corner_B(const TriGeo<R>& G, int i, const R P[2]) {
     R s = 0;
     for (int j = 0; j < 3; ++j) {
         if (j == i) continue;
         int k = 3 - i - j;  // edge (i, j) is opposite vertex k
-        R T[2] = {i64_to_real<R>(G.Lt[j][0] - G.Lt[i][0], CDP_Q), i64_to_real<R>(G.Lt[j][1] - G.Lt[i][1], CDP_Q)};
+        R T[2] = {(G.x[j][0] - G.x[i][0]) + (G.xl[j][0] - G.xl[i][0]),
+                  (G.x[j][1] - G.x[i][1]) + (G.xl[j][1] - G.xl[i][1])};
         R inv = rsqrt_r<R>(T[0] * T[0] + T[1] * T[1]);
         T[0] *= inv;
         T[1] *= inv;
-        s += trip2(P, T, G.n[k], G.rho[i], G.g);
+        const R N[2] = {G.n[k][0], G.n[k][1]};
+        s += trip2(P, T, N, G.rho[i], G.g);
     }
     return R(0.5) * s;
 }
 
-// C: edge (a, b) (opposite o) crossing the grid line x_k = X_k; cell on side sigma
+// C: edge (a, b) (opposite o) crossing the grid line x_k = c; cell on side sigma; eu = unit (a -> b)
 template <typename R>
-CDP_HD R tri_corner_C(const TriGeo<R>& G, int a, int b, int o, int k, int dirk, R sigma, const R X[2], R rhoX,
-                      const int v[2]) {
-    int j = 1 - k;
-    R O[2], P[2];
-    tri_origin(G, v, O);
-    P[0] = X[0] - O[0];
-    P[1] = X[1] - O[1];
-    R T[2] = {i64_to_real<R>(G.Lt[b][0] - G.Lt[a][0], CDP_Q), i64_to_real<R>(G.Lt[b][1] - G.Lt[a][1], CDP_Q)};
-    R inv = rsqrt_r<R>(T[0] * T[0] + T[1] * T[1]) * sigma * R(dirk);
-    T[0] *= inv;
-    T[1] *= inv;
-    R s = trip2(P, T, G.n[o], rhoX, G.g);
-    R T2[2] = {0, 0}, N2[2] = {0, 0};
-    T2[j] = G.nE[o][j] > 0 ? R(1) : R(-1);  // along the grid line, into the triangle
-    N2[k] = sigma;                           // inward normal of the cell side
+CDP_HD R tri_corner_C(const TriGeo<R>& G, int o, int k, int dirk, R sigma, const R eu[2], const R P[2], R rhoX) {
+    R so = sigma * R(dirk);
+    const R T[2] = {so * eu[0], so * eu[1]};
+    const R N[2] = {G.n[o][0], G.n[o][1]};
+    R s = trip2(P, T, N, rhoX, G.g);
+    // along the grid line (axis j = 1 - k), into the triangle; inward normal of the cell side
+    R tj = (k == 1 ? G.nE[o][0] : G.nE[o][1]) > 0 ? R(1) : R(-1);
+    const R T2[2] = {k == 1 ? tj : R(0), k == 0 ? tj : R(0)};
+    const R N2[2] = {k == 0 ? sigma : R(0), k == 1 ? sigma : R(0)};
     s += trip2(P, T2, N2, rhoX, G.g);
     return R(0.5) * s;
 }
 
 template <typename R, class Acc>
 CDP_HD void tri_item_vertex(const TriGeo<R>& G, int i, const int td[2], Acc& acc, UnitCounts* cnt) {
-    const int v[2] = {G.cell[i][0], G.cell[i][1]};
-    if (v[0] >= 0 && v[0] < td[0] && v[1] >= 0 && v[1] < td[1]) {
-        acc(v[0], v[1], 0, tri_corner_B(G, i, v));
+    const int v0 = G.cell[i][0], v1 = G.cell[i][1];
+    if (v0 >= 0 && v0 < td[0] && v1 >= 0 && v1 < td[1]) {
+        R O[2];
+        tri_origin(G, v0, v1, O);
+        const R P[2] = {(G.x[i][0] - O[0]) + G.xl[i][0], (G.x[i][1] - O[1]) + G.xl[i][1]};
+        acc(v0, v1, 0, tri_corner_B(G, i, P));
         if (cnt) cnt->b++;
     }
 }
@@ -808,7 +970,8 @@ CDP_HD int tri_crossings(const TriGeo<R>& G, int o, int k, const int td[2], int&
     c0 = (ca < cb ? ca : cb) + 1;
     int c1 = ca < cb ? cb : ca;
     if (c0 < 0) c0 = 0;
-    if (c1 > td[k]) c1 = td[k];
+    int tk = k == 0 ? td[0] : td[1];
+    if (c1 > tk) c1 = tk;
     return c1 >= c0 ? c1 - c0 + 1 : 0;
 }
 
@@ -818,21 +981,28 @@ CDP_HD void tri_item_crossing(const TriGeo<R>& G, int o, int k, int c, const int
     tri_edge(o, a, b);
     int j = 1 - k;
     int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
-    R ev[2] = {G.x[b][0] - G.x[a][0], G.x[b][1] - G.x[a][1]};
-    R t = (R(c) - G.x[a][k]) / ev[k];
-    R X[2];
-    X[j] = G.x[a][j] + t * ev[j];
-    X[k] = R(c);
-    int cj = tri_cross_cell(G, a, b, k, c, (int)floor_r(X[j]), dirk, cnt);
-    if (cj < 0 || cj >= td[j]) return;
+    R ev[2] = {(G.x[b][0] - G.x[a][0]) + (G.xl[b][0] - G.xl[a][0]),
+               (G.x[b][1] - G.x[a][1]) + (G.xl[b][1] - G.xl[a][1])};
+    R evk = k == 0 ? ev[0] : ev[1], evj = k == 0 ? ev[1] : ev[0];
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    R dj = t * evj;
+    R Xj = G.x[a][j] + dj;
+    int cj = tri_cross_cell(G, a, b, k, c, (int)floor_r(Xj), dirk, cnt);
+    int tj = j == 0 ? td[0] : td[1], tk = k == 0 ? td[0] : td[1];
+    if (cj < 0 || cj >= tj) return;
     R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+    R inv = rsqrt_r<R>(ev[0] * ev[0] + ev[1] * ev[1]);
+    const R eu[2] = {ev[0] * inv, ev[1] * inv};
     for (int side = 0; side < 2; ++side) {
         int vk = side == 0 ? c - 1 : c;
-        if (vk < 0 || vk >= td[k]) continue;
-        int v[2];
-        v[k] = vk;
-        v[j] = cj;
-        acc(v[0], v[1], 0, tri_corner_C(G, a, b, o, k, dirk, side == 0 ? R(-1) : R(1), X, rhoX, v));
+        if (vk < 0 || vk >= tk) continue;
+        int v0 = k == 0 ? vk : cj, v1 = k == 1 ? vk : cj;
+        R O[2];
+        tri_origin(G, v0, v1, O);
+        R Pk = R(c) - (k == 0 ? O[0] : O[1]);
+        R Pj = (G.x[a][j] - (j == 0 ? O[0] : O[1])) + (G.xl[a][j] + dj);
+        const R P[2] = {k == 0 ? Pk : Pj, k == 1 ? Pk : Pj};
+        acc(v0, v1, 0, tri_corner_C(G, o, k, dirk, side == 0 ? R(-1) : R(1), eu, P, rhoX));
         if (cnt) cnt->c++;
     }
 }
@@ -868,20 +1038,65 @@ CDP_HD void tri_item_row(const TriGeo<R>& G, int dy, const int td[2], Acc& acc, 
     if (nhit != 2) return;
     int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
     for (int cx = n0; cx <= n1; ++cx) {
-        R X[2] = {R(cx), R(dy)};
-        R rhoX = G.rhoc + G.g[0] * (X[0] - G.c[0]) + G.g[1] * (X[1] - G.c[1]);
         for (int o = 0; o < 4; ++o) {
-            int v[2] = {cx - 1 + (o & 1), dy - 1 + ((o >> 1) & 1)};
-            if (v[0] < 0 || v[0] >= td[0] || v[1] < 0 || v[1] >= td[1]) continue;
+            int v0 = cx - 1 + (o & 1), v1 = dy - 1 + ((o >> 1) & 1);
+            if (v0 < 0 || v0 >= td[0] || v1 < 0 || v1 >= td[1]) continue;
             R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1);
-            R O[2], P[2];
-            tri_origin(G, v, O);
-            P[0] = X[0] - O[0];
-            P[1] = X[1] - O[1];
-            acc(v[0], v[1], 0, sg * P[0] * P[1] * (rhoX - R(0.5) * (G.g[0] * P[0] + G.g[1] * P[1])));
+            R O[2];
+            tri_origin(G, v0, v1, O);
+            R P0 = R(cx) - O[0], P1 = R(dy) - O[1];
+            R rhoX = G.rhoc + G.g[0] * (P0 + (O[0] - G.c[0])) + G.g[1] * (P1 + (O[1] - G.c[1]));
+            acc(v0, v1, 0, sg * P0 * P1 * (rhoX - R(0.5) * (G.g[0] * P0 + G.g[1] * P1)));
             if (cnt) cnt->a++;
         }
     }
+}
+
+// Split form of a 2D crossing for a work queue.
+//   C record: bits 0-10 c, 11-21 cj, 22 side, 23 k, 24-25 o (edge opposite vertex o)
+template <typename R, class Push>
+CDP_HD void tri_locate_crossing(const TriGeo<R>& G, int o, int k, int c, const int td[2], Push& push,
+                                UnitCounts* cnt) {
+    int a, b;
+    tri_edge(o, a, b);
+    int j = 1 - k;
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    R evk = (G.x[b][k] - G.x[a][k]) + (G.xl[b][k] - G.xl[a][k]);
+    R evj = (G.x[b][j] - G.x[a][j]) + (G.xl[b][j] - G.xl[a][j]);
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    int cj = tri_cross_cell(G, a, b, k, c, (int)floor_r(G.x[a][j] + t * evj), dirk, cnt);
+    int tj = j == 0 ? td[0] : td[1], tk = k == 0 ? td[0] : td[1];
+    if (cj < 0 || cj >= tj) return;
+    unsigned long long base = (unsigned long long)c | ((unsigned long long)cj << 11) | ((unsigned long long)k << 23) |
+                              ((unsigned long long)o << 24);
+    if (c - 1 >= 0 && c - 1 < tk) push(base);
+    if (c < tk) push(base | (1ull << 22));
+}
+
+template <typename R>
+CDP_HD R tri_eval_crossing(const TriGeo<R>& G, unsigned long long r, int& v0, int& v1, int& v2) {
+    int c = (int)(r & 2047), cj = (int)((r >> 11) & 2047), side = (int)((r >> 22) & 1), k = (int)((r >> 23) & 1),
+        o = (int)((r >> 24) & 3);
+    int a, b;
+    tri_edge(o, a, b);
+    int j = 1 - k;
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    R ev[2] = {(G.x[b][0] - G.x[a][0]) + (G.xl[b][0] - G.xl[a][0]),
+               (G.x[b][1] - G.x[a][1]) + (G.xl[b][1] - G.xl[a][1])};
+    R evk = k == 0 ? ev[0] : ev[1], evj = k == 0 ? ev[1] : ev[0];
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    int vk = side ? c : c - 1;
+    v0 = k == 0 ? vk : cj;
+    v1 = k == 1 ? vk : cj;
+    v2 = 0;
+    R O[2];
+    tri_origin(G, v0, v1, O);
+    R Pk = R(c) - (k == 0 ? O[0] : O[1]);
+    R Pj = (G.x[a][j] - (j == 0 ? O[0] : O[1])) + (G.xl[a][j] + t * evj);
+    const R P[2] = {k == 0 ? Pk : Pj, k == 1 ? Pk : Pj};
+    R inv = rsqrt_r<R>(ev[0] * ev[0] + ev[1] * ev[1]);
+    const R eu[2] = {ev[0] * inv, ev[1] * inv};
+    return tri_corner_C(G, o, k, dirk, side ? R(1) : R(-1), eu, P, G.rho[a] + t * (G.rho[b] - G.rho[a]));
 }
 
 template <typename R, class Acc>

@@ -63,6 +63,19 @@ struct WarpShared {
     R vals[CDP_WTBL];
     double csum[CDP_CHUNK];
     unsigned long long cmax[CDP_CHUNK];
+    unsigned long long queue[CDP_QCAP];  // (corner, cell) records awaiting evaluation
+    unsigned qtail;
+};
+
+// appends records of simplex `owner` to the warp's queue
+struct QueuePush {
+    unsigned long long* q;
+    unsigned* tail;
+    unsigned long long owner_bits;
+    __device__ __forceinline__ void operator()(unsigned long long r) {
+        unsigned pos = atomicAdd(tail, 1u);
+        q[pos & (CDP_QCAP - 1)] = r | owner_bits;
+    }
 };
 
 // Adds into the per-warp table on behalf of simplex `owner` of the chunk; cells that do not fit
@@ -229,7 +242,101 @@ __device__ __forceinline__ void tri_item(const TriGeo<R>& G, int ph, int t, Acc&
 }
 
 template <int DIM, typename R>
-__global__ void __launch_bounds__(CDP_WBLOCK) k_project_warp(GridDesc g, long long ns, long long nv,
+__device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int own, const GridDesc& g, double* out,
+                                                    bool closure) {
+    const typename GeoOf<DIM, R>::T& G = sh->geo[own];
+    WarpAcc<DIM, R> acc;
+    acc.sh = sh;
+    acc.owner = own;
+    acc.ex = G.hi[0] + 1;
+    acc.ey = G.hi[1] + 1;
+    long long cells = (long long)acc.ex * acc.ey * (DIM == 3 ? (G.hi[DIM - 1] + 1) : 1);
+    acc.direct_only = cells >= (1ll << KEY_BITS);
+    acc.g = &g;
+    acc.out = out;
+    acc.closure = closure;
+    return acc;
+}
+
+// phase items with the queue: 0 vertex (evaluated), 1 crossing (queued), 2 line (D queued, A evaluated)
+template <typename R, class Acc, class Push>
+__device__ __forceinline__ void tet_phase_item(const TetGeo<R>& G, int ph, int t, Acc& acc, Push& push,
+                                               UnitCounts* cnt) {
+    const int td[3] = {G.hi[0] + 1, G.hi[1] + 1, G.hi[2] + 1};
+    if (ph == 0) {
+        tet_item_vertex(G, t, td, acc, cnt);
+    } else if (ph == 1) {
+        for (int e = 0; e < 6; ++e)
+            for (int k = 0; k < 3; ++k) {
+                int c0, n = tet_crossings(G, e, k, td, c0);
+                if (t < n) {
+                    tet_locate_crossing(G, e, k, c0 + t, td, push, cnt);
+                    return;
+                }
+                t -= n;
+            }
+    } else {
+        for (int l = 0; l < 3; ++l) {
+            int dj0, nj, dk0;
+            int n = tet_lines(G, l, td, dj0, nj, dk0);
+            if (t < n) {
+                tet_locate_line(G, l, dj0 + t % nj, dk0 + t / nj, td, push, acc, cnt);
+                return;
+            }
+            t -= n;
+        }
+    }
+}
+
+template <typename R, class Acc, class Push>
+__device__ __forceinline__ void tri_phase_item(const TriGeo<R>& G, int ph, int t, Acc& acc, Push& push,
+                                               UnitCounts* cnt) {
+    const int td[2] = {G.hi[0] + 1, G.hi[1] + 1};
+    if (ph == 0) {
+        tri_item_vertex(G, t, td, acc, cnt);
+    } else if (ph == 1) {
+        for (int o = 0; o < 3; ++o)
+            for (int k = 0; k < 2; ++k) {
+                int c0, n = tri_crossings(G, o, k, td, c0);
+                if (t < n) {
+                    tri_locate_crossing(G, o, k, c0 + t, td, push, cnt);
+                    return;
+                }
+                t -= n;
+            }
+    } else {
+        int dy0;
+        tri_rows(G, td, dy0);
+        tri_item_row(G, dy0 + t, td, acc, cnt);
+    }
+}
+
+// evaluate one queued record of phase ph and add it to its simplex's piece
+template <int DIM, typename R>
+__device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned long long r, int ph, const GridDesc& g,
+                                            double* out, bool closure, UnitCounts* cnt) {
+    const int own = (int)((r >> 40) & 31);
+    const typename GeoOf<DIM, R>::T& G = sh->geo[own];
+    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, closure);
+    int v0, v1, v2;
+    R val;
+    if constexpr (DIM == 3) {
+        if (ph == 1) {
+            val = tet_eval_crossing(G, r, v0, v1, v2);
+            if (cnt) cnt->c++;
+        } else {
+            val = tet_eval_line(G, r, v0, v1, v2);
+            if (cnt) cnt->d++;
+        }
+    } else {
+        val = tri_eval_crossing(G, r, v0, v1, v2);
+        if (cnt) cnt->c++;
+    }
+    acc(v0, v1, v2, val);
+}
+
+template <int DIM, typename R>
+__global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long long ns, long long nv,
                                                             const int* __restrict__ simp,
                                                             const VertexRec* __restrict__ V,
                                                             double* __restrict__ out, Counters* __restrict__ ctr,
@@ -242,6 +349,8 @@ __global__ void __launch_bounds__(CDP_WBLOCK) k_project_warp(GridDesc g, long lo
         sh->keys[e] = EMPTY_KEY;
         sh->vals[e] = R(0);
     }
+    if (lane == 0) sh->qtail = 0u;
+    __syncwarp();
     UnitCounts cnt = {0, 0, 0, 0, 0};
     UnitCounts* pc = stats ? &cnt : nullptr;
     unsigned long long n0 = 0, nact = 0, nzero = 0;
@@ -300,7 +409,10 @@ __global__ void __launch_bounds__(CDP_WBLOCK) k_project_warp(GridDesc g, long lo
         nact += active ? 1 : 0;
         __syncwarp();
         if (__ballot_sync(0xffffffffu, active) == 0u) continue;
-        // ---- the three phases, items dealt over the lanes
+        // ---- the three phases, items dealt over the lanes.  Phase 0 evaluates its corners (B) at
+        // once; phases 1 and 2 locate their corners (C, and D with the A nodes evaluated at once)
+        // and queue them, and the queue is drained in full batches of 32 identical evaluations.
+        unsigned head = sh->qtail;
         for (int ph = 0; ph < 3; ++ph) {
             int mine = active ? n[ph] : 0;
             int pre = mine;
@@ -313,23 +425,31 @@ __global__ void __launch_bounds__(CDP_WBLOCK) k_project_warp(GridDesc g, long lo
                 const int u = u0 + lane;
                 const int own = owner_of(pre, u);
                 const int before = __shfl_sync(0xffffffffu, pre - mine, own);
-                if (u >= tot) continue;
-                const typename GeoOf<DIM, R>::T& G = sh->geo[own];
-                WarpAcc<DIM, R> acc;
-                acc.sh = sh;
-                acc.owner = own;
-                acc.ex = G.hi[0] + 1;
-                acc.ey = G.hi[1] + 1;
-                long long cells = (long long)acc.ex * acc.ey * (DIM == 3 ? (G.hi[DIM - 1] + 1) : 1);
-                acc.direct_only = cells >= (1ll << KEY_BITS);
-                acc.g = &g;
-                acc.out = out;
-                acc.closure = fp32;
-                if constexpr (DIM == 3)
-                    tet_item(G, ph, u - before, acc, pc);
-                else
-                    tri_item(G, ph, u - before, acc, pc);
+                if (u < tot) {
+                    const typename GeoOf<DIM, R>::T& G = sh->geo[own];
+                    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, fp32);
+                    QueuePush push{sh->queue, &sh->qtail, (unsigned long long)own << 40};
+                    const int t = u - before;
+                    if constexpr (DIM == 3)
+                        tet_phase_item(G, ph, t, acc, push, pc);
+                    else
+                        tri_phase_item(G, ph, t, acc, push, pc);
+                }
+                __syncwarp();
+                // evaluate every full batch of queued records
+                const unsigned tail = *(volatile unsigned*)&sh->qtail;
+                while (tail - head >= 32u) {
+                    eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, g, out, fp32, pc);
+                    head += 32u;
+                }
+                __syncwarp();
             }
+            // the last partial batch of the phase
+            const unsigned tail = *(volatile unsigned*)&sh->qtail;
+            if ((unsigned)lane < tail - head)
+                eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, g, out, fp32, pc);
+            head = tail;
+            __syncwarp();
         }
         __syncwarp();
         // ---- flush the table: one FP64 atomic per (simplex, cell) piece

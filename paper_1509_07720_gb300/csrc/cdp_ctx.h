@@ -56,4 +56,5 @@ struct cdp_ctx {
     // captured time steps (see cdp_step_batched) and the device copy of their dt
     struct StepGraph* graphs;
     double* d_dt;
+    cudaStream_t capture_stream;  // private stream the step graphs are recorded on
 };

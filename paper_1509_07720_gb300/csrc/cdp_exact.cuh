@@ -25,6 +25,11 @@
 #ifndef CDP_HD
 #define CDP_HD __host__ __device__ __forceinline__
 #endif
+// rarely executed or once-per-simplex code: kept out of line so that the hot loops stay small
+// enough for the instruction cache
+#ifndef CDP_COLD
+#define CDP_COLD inline __host__ __device__ __noinline__
+#endif
 
 namespace cdp {
 
@@ -142,7 +147,7 @@ CDP_HD void cross_exact(const i64 a[3], const i64 b[3], i128 out[3]) {
 //   (b_u - a_u)(p_v - a_v) - (b_v - a_v)(p_u - a_u)
 //   - delta_v (b_u - a_u) + delta_u (b_v - a_v).
 // au, av, bu, bv, pu, pv are fixed-point coordinates in one frame.
-CDP_HD int side2_exact(i64 au, i64 av, i64 bu, i64 bv, i64 pu, i64 pv) {
+CDP_COLD int side2_exact(i64 au, i64 av, i64 bu, i64 bv, i64 pu, i64 pv) {
     i64 du = bu - au, dv = bv - av;
     i128 d0 = mul64(du, pv - av) - mul64(dv, pu - au);
     if (d0 != 0) return d0 > 0 ? 1 : -1;
@@ -152,7 +157,7 @@ CDP_HD int side2_exact(i64 au, i64 av, i64 bu, i64 bv, i64 pu, i64 pv) {
 
 // side3: sign of n.(g - delta - a) for the exact facet normal n (any vertex a of the facet):
 //   D0 = n.(g - a); perturbation -n.delta, dominated by the first non-zero component of n.
-CDP_HD int side3_exact(const i128 n[3], const i64 a[3], const i64 g[3]) {
+CDP_COLD int side3_exact(const i128 n[3], const i64 a[3], const i64 g[3]) {
     i64 d[3] = {g[0] - a[0], g[1] - a[1], g[2] - a[2]};
     int s = sgn_wide(dot3_wide(n, d));
     if (s != 0) return s;

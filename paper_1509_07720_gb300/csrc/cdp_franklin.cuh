@@ -160,10 +160,11 @@ struct TetGeo {
     int anchor[3];         // absolute cell of the tile origin
     signed char ns[4][3];  // signs of the exact normal components
     double mexact;         // |V| mean(rho) in FP64 (closed form, for the mass closure)
+    int pad_[2];           // odd multiple of 8 bytes: consecutive records start in different banks
 };
 
 // exact inward normal of facet f (the facet opposite vertex f) of a positively oriented tetrahedron
-CDP_HD void facet_normal_exact(const i64 L[4][3], int f, i128 out[3]) {
+CDP_COLD void facet_normal_exact(const i64 L[4][3], int f, i128 out[3]) {
     int o = f == 0 ? 1 : 0;  // reference vertex of the facet
     int u, v;                // the normal is (x_u - x_o) x (x_v - x_o)
     if (f == 0) { u = 3; v = 2; }
@@ -190,7 +191,7 @@ CDP_HD double low_part<double>(i64, double) { return 0.0; }
 
 // Fill the working set for the tile whose lowest cell is T (relative to the anchor).
 template <typename R>
-CDP_HD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
+CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
     for (int k = 0; k < 4; ++k)
         for (int a = 0; a < 3; ++a) {
             G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
@@ -341,7 +342,7 @@ CDP_HD void piece_origin(const TetGeo<R>& G, int v0, int v1, int v2, R O[3]) {
 
 // B: simplex vertex i; P = x_i - O
 template <typename R>
-CDP_HD R tet_corner_B(const TetGeo<R>& G, int i, const R P[3]) {
+CDP_COLD R tet_corner_B(const TetGeo<R>& G, int i, const R P[3]) {
     R s = 0;
     for (int j = 0; j < 4; ++j) {
         if (j == i) continue;
@@ -816,7 +817,7 @@ struct TriGeo {
 };
 
 template <typename R>
-CDP_HD void tri_setup(const Tri& S, const int T[2], TriGeo<R>& G) {
+CDP_COLD void tri_setup(const Tri& S, const int T[2], TriGeo<R>& G) {
     for (int k = 0; k < 3; ++k)
         for (int a = 0; a < 2; ++a) {
             G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
@@ -913,7 +914,7 @@ CDP_HD void tri_origin(const TriGeo<R>& G, int v0, int v1, R O[2]) {
 
 // B: vertex i; P = x_i - O
 template <typename R>
-CDP_HD R tri_corner_B(const TriGeo<R>& G, int i, const R P[2]) {
+CDP_COLD R tri_corner_B(const TriGeo<R>& G, int i, const R P[2]) {
     R s = 0;
     for (int j = 0; j < 3; ++j) {
         if (j == i) continue;

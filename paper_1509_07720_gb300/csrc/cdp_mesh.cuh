@@ -70,7 +70,7 @@ CDP_HD bool unwrap(i64& d, int n, int periodic) {
 
 // Canonical tetrahedron from its 4 vertex records.  Returns 0 (ok), 1 (zero volume: contributes
 // nothing) or an error flag.
-CDP_HD unsigned canon_tet(const GridDesc& g, const VertexRec* v[4], Tet& S) {
+CDP_COLD unsigned canon_tet(const GridDesc& g, const VertexRec* v[4], Tet& S) {
     const i64 lim = (i64)CDP_MAX_EXTENT << CDP_Q;
     for (int a = 0; a < 3; ++a) {
         i64 X0 = v[0]->x[a];
@@ -120,7 +120,7 @@ CDP_HD unsigned canon_tet(const GridDesc& g, const VertexRec* v[4], Tet& S) {
     return 0;
 }
 
-CDP_HD unsigned canon_tri(const GridDesc& g, const VertexRec* v[3], Tri& S) {
+CDP_COLD unsigned canon_tri(const GridDesc& g, const VertexRec* v[3], Tri& S) {
     const i64 lim = (i64)CDP_MAX_EXTENT << CDP_Q;
     for (int a = 0; a < 2; ++a) {
         i64 X0 = v[0]->x[a];

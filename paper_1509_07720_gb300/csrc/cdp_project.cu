@@ -61,8 +61,10 @@ struct WarpShared {
     typename GeoOf<DIM, R>::T geo[CDP_CHUNK];
     unsigned keys[CDP_WTBL];
     R vals[CDP_WTBL];
-    double csum[CDP_CHUNK];
-    unsigned long long cmax[CDP_CHUNK];
+    double csum[CDP_CHUNK];              // FP64 sum of a simplex's pieces (mass closure)
+    float asum[CDP_CHUNK];               // sum of |piece| over its table entries
+    double resid[CDP_CHUNK];             // closure residual, spread over the table entries
+    unsigned long long cmax[CDP_CHUNK];  // largest piece sent straight to the grid (packed |v|, cell)
     unsigned long long queue[CDP_QCAP];  // (corner, cell) records awaiting evaluation
     unsigned qtail;
 };
@@ -404,6 +406,8 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
         }
         if (lane < CDP_CHUNK) {
             sh->csum[lane] = 0.0;
+            sh->asum[lane] = 0.f;
+            sh->resid[lane] = 0.0;
             sh->cmax[lane] = 0ull;
         }
         nact += active ? 1 : 0;
@@ -452,14 +456,38 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
             __syncwarp();
         }
         __syncwarp();
-        // ---- flush the table: one FP64 atomic per (simplex, cell) piece
+        // ---- flush the table: one FP64 atomic per (simplex, cell) piece.  FP32 path: first the
+        // FP64 sum of every simplex's pieces, then its closure residual (FP64 closed-form mass
+        // minus that sum) is spread over its pieces in proportion to their size while they are
+        // flushed (a simplex whose pieces all went straight to the grid gives it to its largest).
+        if (fp32) {
+            for (int e = lane; e < CDP_WTBL; e += 32) {
+                unsigned k = sh->keys[e];
+                if (k == EMPTY_KEY) continue;
+                R v = sh->vals[e];
+                int own = (int)(k >> KEY_BITS);
+                atomicAdd(&sh->csum[own], (double)v);
+                atomicAdd(&sh->asum[own], fabsf((float)v));
+            }
+            __syncwarp();
+            if (active) {
+                double r = sh->geo[lane].mexact - sh->csum[lane];
+                if (sh->asum[lane] > 0.f) {
+                    sh->resid[lane] = r / (double)sh->asum[lane];
+                } else {
+                    sh->resid[lane] = 0.0;
+                    if (sh->cmax[lane] != 0ull)
+                        atomicAdd(out + (long long)(unsigned)(sh->cmax[lane] & 0xffffffffull), r);
+                }
+            }
+            __syncwarp();
+        }
         for (int e = lane; e < CDP_WTBL; e += 32) {
             unsigned k = sh->keys[e];
             if (k == EMPTY_KEY) continue;
             R v = sh->vals[e];
             sh->keys[e] = EMPTY_KEY;
             sh->vals[e] = R(0);
-            if (v == R(0)) continue;
             int own = (int)(k >> KEY_BITS);
             unsigned lk = k & ((1u << KEY_BITS) - 1u);
             const typename GeoOf<DIM, R>::T& G = sh->geo[own];
@@ -468,18 +496,9 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
             int y = r % ey, z = r / ey;
             long long idx = flat_cell(g, G.anchor[0] + x, G.anchor[1] + y, G.anchor[2] + z);
             if (idx < 0) continue;
-            atomicAdd(out + idx, (double)v);
-            if (fp32) {
-                atomicAdd(&sh->csum[own], (double)v);
-                unsigned long long packed = ((unsigned long long)__float_as_uint(fabsf((float)v)) << 32) |
-                                            (unsigned long long)(unsigned)idx;
-                atomicMax(&sh->cmax[own], packed);
-            }
-        }
-        __syncwarp();
-        if (fp32 && active && sh->cmax[lane] != 0ull) {
-            long long idx = (long long)(unsigned)(sh->cmax[lane] & 0xffffffffull);
-            atomicAdd(out + idx, sh->geo[lane].mexact - sh->csum[lane]);
+            double dv = (double)v;
+            if (fp32) dv += sh->resid[own] * (double)fabsf((float)v);
+            if (dv != 0.0) atomicAdd(out + idx, dv);
         }
         __syncwarp();
     }

@@ -114,6 +114,8 @@ void step_release(cdp_ctx* c) {
     c->graphs = nullptr;
     if (c->d_dt) cudaFree(c->d_dt);
     c->d_dt = nullptr;
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->capture_stream = nullptr;
 }
 }  // namespace cdp
 
@@ -158,13 +160,23 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
             return rc;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) return CDP_ERR_CUDA;
+    // the sequence is recorded on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is then launched on the caller's stream
+    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    cudaStream_t cs = c->capture_stream;
     cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CDP_ERR_CUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
     int timing = c->timing;
     c->timing = 0;  // no event bookkeeping inside the captured sequence
-    rc = enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, st);
+    rc = enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, cs);
     c->timing = timing;
-    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (rc || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();

@@ -332,12 +332,14 @@ CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int dj, int dk,
 // contributions of one (corner, cell) incidence; P = corner - O with O the piece's origin
 // ------------------------------------------------------------------------------------------
 
-// origin of the piece in cell (v0, v1, v2): the centroid clamped into the cell
+// origin of the piece in cell (v0, v1, v2): the centroid clamped into the central half of the
+// cell, so that |P| stays below both twice the simplex size plus half a cell and 3/4 of a cell
+// per axis (small simplices keep a nearby origin, large ones get one near the cell centre)
 template <typename R>
 CDP_HD void piece_origin(const TetGeo<R>& G, int v0, int v1, int v2, R O[3]) {
-    O[0] = clamp_r(G.c[0], R(v0), R(v0 + 1));
-    O[1] = clamp_r(G.c[1], R(v1), R(v1 + 1));
-    O[2] = clamp_r(G.c[2], R(v2), R(v2 + 1));
+    O[0] = clamp_r(G.c[0], R(v0) + R(0.25), R(v0) + R(0.75));
+    O[1] = clamp_r(G.c[1], R(v1) + R(0.25), R(v1) + R(0.75));
+    O[2] = clamp_r(G.c[2], R(v2) + R(0.25), R(v2) + R(0.75));
 }
 
 // B: simplex vertex i; P = x_i - O
@@ -644,11 +646,155 @@ CDP_HD void tet_item_line(const TetGeo<R>& G, int l, int dj, int dk, const int t
 }
 
 // ------------------------------------------------------------------------------------------
+// Closed forms of the C and D corners for all the cells around the corner at once.  The six
+// (vertex, edge, facet) triples of such a corner are built from the unit normal(s) of the
+// simplex facet(s) and the cell faces; expanding them gives short polynomials in P (the corner
+// relative to its piece's origin) whose coefficients depend only on the corner, so they are
+// computed once for the 4 (D) or 2 (C) cells.  Same values as tet_corner_D / tet_corner_C.
+// ------------------------------------------------------------------------------------------
+
+// (a x b) component i
+template <typename R>
+CDP_HD R cross_comp(const R a[3], const R b[3], int i) {
+    R c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+    return pick3(c0, c1, c2, i);
+}
+
+// Facet-face triples of one simplex facet (unit normal n) meeting the cell face normal to axis k:
+// the line facet/face oriented by `su`, sigma = side of the cell, P and g, Pn = P.n, gn = g.n,
+// h = (g x n)_k, ir2 = 1 / (1 - n_k^2).  Returns the sum of the two triple terms (times -6).
+template <typename R>
+CDP_HD R facet_face_terms(const R n[3], int k, R su, R sigma, const R P[3], R Pn, R gn, R h, R ir2, R rhoX,
+                          const R g[3]) {
+    R nk = pick3(n[0], n[1], n[2], k), Pk = pick3(P[0], P[1], P[2], k), gk = pick3(g[0], g[1], g[2], k);
+    R cpk = cross_comp(P, n, k);
+    R lead = R(0.75) * cpk * h * ir2;
+    R d3 = Pk - nk * Pn, e3 = gk - nk * gn;
+    R d4 = Pn - nk * Pk, e4 = gn - nk * gk;
+    R br3 = rhoX - lead - R(0.5) * d3 * e3 * ir2 - R(0.25) * Pn * gn;
+    R br4 = rhoX - lead - R(0.5) * d4 * e4 * ir2 - R(0.25) * Pk * gk;
+    return su * sigma * cpk * ir2 * (d3 * Pn * br3 + d4 * Pk * br4);
+}
+
+// D corner (facet f pierced by the grid line along l at (dj, dk), in cell column m): the values
+// of the 4 cells (oj, ok) = (0,0), (0,1), (1,0), (1,1) and their cells
+template <typename R>
+CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m, R val[4], int cell[4][3]) {
+    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    int va = f == 0 ? 1 : 0;
+    const R n[3] = {G.n[f][0], G.n[f][1], G.n[f][2]};
+    R nj = pick3(n[0], n[1], n[2], j), nk = pick3(n[0], n[1], n[2], k), nl = pick3(n[0], n[1], n[2], l);
+    R tau = G.ns[f][l] > 0 ? R(1) : R(-1);
+    R eps = (l == 1) ? R(-1) : R(1);
+    R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
+    const R g[3] = {G.g[0], G.g[1], G.g[2]};
+    R gn = dot3(g, n);
+    R hj = cross_comp(g, n, j), hk = cross_comp(g, n, k);
+    R irj2 = R(1) / (nk * nk + nl * nl), irk2 = R(1) / (nj * nj + nl * nl);
+    R gj = pick3(g[0], g[1], g[2], j), gk = pick3(g[0], g[1], g[2], k), gl = pick3(g[0], g[1], g[2], l);
+    R xl_ = G.x[va][l], xll = G.xl[va][l] + off;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int oj = q >> 1, ok = q & 1;
+        int vj = dj - 1 + oj, vk = dk - 1 + ok;
+        int v0 = l == 0 ? m : vj;
+        int v1 = l == 1 ? m : (l == 0 ? vj : vk);
+        int v2 = l == 2 ? m : vk;
+        cell[q][0] = v0;
+        cell[q][1] = v1;
+        cell[q][2] = v2;
+        R O[3];
+        piece_origin(G, v0, v1, v2, O);
+        R Pl = (xl_ - pick3(O[0], O[1], O[2], l)) + xll;
+        R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
+        const R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
+        R rhoX = rho_from_P(G, P, O);
+        R sj = oj ? R(1) : R(-1), sk = ok ? R(1) : R(-1);
+        R Pn = dot3(P, n);
+        R s12 = tau * sj * sk * Pj * Pk * Pl * (R(2) * rhoX - R(1.5) * Pl * gl - R(0.75) * (Pj * gj + Pk * gk));
+        // facet/face_j line oriented towards the k side (sign sk eps tau), facet/face_k towards j
+        R s34 = facet_face_terms(n, j, sk * eps * tau, sj, P, Pn, gn, hj, irj2, rhoX, g);
+        R s56 = facet_face_terms(n, k, -sj * eps * tau, sk, P, Pn, gn, hk, irk2, rhoX, g);
+        val[q] = R(-1.0 / 6.0) * (s12 + s34 + s56);
+    }
+}
+
+// C corner (edge e crossing the plane x_k = c): the values of the 2 cells (below, above) and cells
+template <typename R>
+CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj2, R val[2], int cell[2][3]) {
+    int a, b, p, q;
+    tet_edge(e, a, b, p, q);
+    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
+    int j1 = k == 0 ? 1 : 0;
+    R ev[3];
+    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
+    R evk = pick3(ev[0], ev[1], ev[2], k);
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
+    R inv = rsqrt_r<R>(dot3(ev, ev));
+    const R eu[3] = {ev[0] * inv, ev[1] * inv, ev[2] * inv};
+    const R g[3] = {G.g[0], G.g[1], G.g[2]};
+    const R np_[3] = {G.n[p][0], G.n[p][1], G.n[p][2]};
+    const R nq_[3] = {G.n[q][0], G.n[q][1], G.n[q][2]};
+    // in-facet normals of the edge: m_p in facet p (towards q), m_q in facet q (towards p)
+    R mp[3], mq[3];
+    cross3(np_, eu, mp);
+    cross3(nq_, eu, mq);
+    R pp = R(parity4(a, b, q, p)), pq = R(parity4(a, b, p, q));
+    for (int w = 0; w < 3; ++w) {
+        mp[w] *= pp;
+        mq[w] *= pq;
+    }
+    R ge = dot3(g, eu), gmp = dot3(g, mp), gmq = dot3(g, mq), gnp = dot3(g, np_), gnq = dot3(g, nq_);
+    R hp = cross_comp(g, np_, k), hq = cross_comp(g, nq_, k);
+    R npk = pick3(np_[0], np_[1], np_[2], k), nqk = pick3(nq_[0], nq_[1], nq_[2], k);
+    R irp2 = R(1) / (R(1) - npk * npk), irq2 = R(1) / (R(1) - nqk * nqk);
+    {
+        // 1 - n_k^2 from the other two components (no cancellation when n_k is near 1)
+        R a0 = pick3(np_[1], np_[0], np_[0], k), a1 = pick3(np_[2], np_[2], np_[1], k);
+        R b0 = pick3(nq_[1], nq_[0], nq_[0], k), b1 = pick3(nq_[2], nq_[2], nq_[1], k);
+        irp2 = R(1) / (a0 * a0 + a1 * a1);
+        irq2 = R(1) / (b0 * b0 + b1 * b1);
+    }
+    R lam = R(-parity4(a, b, p, q)) * R(dirk);
+    R d[3] = {t * ev[0], t * ev[1], t * ev[2]};
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        int vk = side ? c : c - 1;
+        int v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
+        int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
+        int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
+        cell[side][0] = v0;
+        cell[side][1] = v1;
+        cell[side][2] = v2;
+        R O[3], P[3];
+        piece_origin(G, v0, v1, v2, O);
+        for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + d[w]);
+        R Pk = R(c) - pick3(O[0], O[1], O[2], k);
+        P[0] = k == 0 ? Pk : P[0];
+        P[1] = k == 1 ? Pk : P[1];
+        P[2] = k == 2 ? Pk : P[2];
+        R sigma = side ? R(1) : R(-1);
+        R so = sigma * R(dirk);
+        R Pe = dot3(P, eu), Pmp = dot3(P, mp), Pmq = dot3(P, mq), Pnp = dot3(P, np_), Pnq = dot3(P, nq_);
+        // the simplex edge with its two facets
+        R s12 = so * Pe *
+                (Pmp * Pnp * (rhoX - R(0.75) * Pe * ge - R(0.5) * Pmp * gmp - R(0.25) * Pnp * gnp) +
+                 Pmq * Pnq * (rhoX - R(0.75) * Pe * ge - R(0.5) * Pmq * gmq - R(0.25) * Pnq * gnq));
+        R s34 = facet_face_terms(np_, k, lam, sigma, P, Pnp, gnp, hp, irp2, rhoX, g);
+        R s56 = facet_face_terms(nq_, k, -lam, sigma, P, Pnq, gnq, hq, irq2, rhoX, g);
+        val[side] = R(-1.0 / 6.0) * (s12 + s34 + s56);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Split form for a work queue: the locate step of a crossing / a line yields compact records of
-// (corner, cell) incidences, and the evaluate step turns one record into its contribution, so
-// that the (costly) evaluations of a warp can run in full batches of identical work.
-//   C record: bits 0-10 c, 11-21 cj1, 22-32 cj2, 33 side, 34-35 k, 36-38 e
-//   D record: bits 0-10 m, 11-21 dj, 22-32 dk, 33 oj, 34 ok, 35-36 l, 37-38 f
+// corners, and the evaluate step (tet_eval_C2 / tet_eval_D4) turns one record into the
+// contributions of all the cells around it, so that the (costly) evaluations of a warp can run in
+// full batches of identical work.  The records assume the tile is the whole bounding box (every
+// cell around an interior crossing or line lies in it).
+//   C record: bits 0-10 c, 11-21 cj1, 22-32 cj2, 34-35 k, 36-38 e
+//   D record: bits 0-10 m, 11-21 dj, 22-32 dk, 35-36 l, 37-38 f
 // (coordinates in the tile frame, 0 <= value < 2048).  Bits 40 and up are left to the caller.
 // ------------------------------------------------------------------------------------------
 typedef unsigned long long Rec;
@@ -670,40 +816,7 @@ CDP_HD void tet_locate_crossing(const TetGeo<R>& G, int e, int k, int c, const i
     if (cj1 < 0 || cj1 >= pick3(td[0], td[1], td[2], j1)) return;
     int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X2), dirk, cnt);
     if (cj2 < 0 || cj2 >= pick3(td[0], td[1], td[2], j2)) return;
-    int tk = pick3(td[0], td[1], td[2], k);
-    Rec base = (Rec)c | ((Rec)cj1 << 11) | ((Rec)cj2 << 22) | ((Rec)k << 34) | ((Rec)e << 36);
-    if (c - 1 >= 0 && c - 1 < tk) push(base);
-    if (c < tk) push(base | (1ull << 33));
-}
-
-// contribution of a C record; (v0, v1, v2) receives its cell
-template <typename R>
-CDP_HD R tet_eval_crossing(const TetGeo<R>& G, Rec r, int& v0, int& v1, int& v2) {
-    int c = (int)(r & 2047), cj1 = (int)((r >> 11) & 2047), cj2 = (int)((r >> 22) & 2047);
-    int side = (int)((r >> 33) & 1), k = (int)((r >> 34) & 3), e = (int)((r >> 36) & 7);
-    int a, b, p, q;
-    tet_edge(e, a, b, p, q);
-    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
-    int j1 = k == 0 ? 1 : 0;
-    R ev[3];
-    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
-    R evk = pick3(ev[0], ev[1], ev[2], k);
-    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
-    int vk = side ? c : c - 1;
-    v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
-    v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
-    v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
-    R O[3], P[3];
-    piece_origin(G, v0, v1, v2, O);
-    for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + t * ev[w]);
-    R Pk = R(c) - pick3(O[0], O[1], O[2], k);
-    P[0] = k == 0 ? Pk : P[0];
-    P[1] = k == 1 ? Pk : P[1];
-    P[2] = k == 2 ? Pk : P[2];
-    R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
-    R inv = rsqrt_r<R>(dot3(ev, ev));
-    const R eu[3] = {ev[0] * inv, ev[1] * inv, ev[2] * inv};
-    return tet_corner_C(G, e, k, dirk, side ? R(1) : R(-1), eu, P, rhoX);
+    push((Rec)c | ((Rec)cj1 << 11) | ((Rec)cj2 << 22) | ((Rec)k << 34) | ((Rec)e << 36));
 }
 
 // locate the D corners of a grid line (records pushed) and add its A corners (grid nodes) directly
@@ -726,13 +839,7 @@ CDP_HD void tet_locate_line(const TetGeo<R>& G, int l, int dj, int dk, const int
         else
             mhi = m;
         if (m < 0 || m >= tl) continue;
-        Rec base = (Rec)m | ((Rec)dj << 11) | ((Rec)dk << 22) | ((Rec)l << 35) | ((Rec)f << 37);
-        for (int oj = 0; oj < 2; ++oj)
-            for (int ok = 0; ok < 2; ++ok) {
-                int vj = dj - 1 + oj, vk = dk - 1 + ok;
-                if (vj < 0 || vj >= tj || vk < 0 || vk >= tk) continue;
-                push(base | ((Rec)oj << 33) | ((Rec)ok << 34));
-            }
+        push((Rec)m | ((Rec)dj << 11) | ((Rec)dk << 22) | ((Rec)l << 35) | ((Rec)f << 37));
     }
     if (l != 0 || ((hits & 1u) + ((hits >> 1) & 1u) + ((hits >> 2) & 1u) + ((hits >> 3) & 1u)) != 2u) return;
     int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
@@ -750,25 +857,20 @@ CDP_HD void tet_locate_line(const TetGeo<R>& G, int l, int dj, int dk, const int
     }
 }
 
-// contribution of a D record; (v0, v1, v2) receives its cell
-template <typename R>
-CDP_HD R tet_eval_line(const TetGeo<R>& G, Rec r, int& v0, int& v1, int& v2) {
-    int m = (int)(r & 2047), dj = (int)((r >> 11) & 2047), dk = (int)((r >> 22) & 2047);
-    int oj = (int)((r >> 33) & 1), ok = (int)((r >> 34) & 1), l = (int)((r >> 35) & 3), f = (int)((r >> 37) & 3);
-    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    int va = f == 0 ? 1 : 0;
-    R nj = G.n[f][j], nk = G.n[f][k], nl = G.n[f][l];
-    R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
-    int vj = dj - 1 + oj, vk = dk - 1 + ok;
-    v0 = l == 0 ? m : vj;
-    v1 = l == 1 ? m : (l == 0 ? vj : vk);
-    v2 = l == 2 ? m : vk;
-    R O[3];
-    piece_origin(G, v0, v1, v2, O);
-    R Pl = (G.x[va][l] - pick3(O[0], O[1], O[2], l)) + (G.xl[va][l] + off);
-    R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
-    R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
-    return tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), P, rho_from_P(G, P, O));
+CDP_HD void decode_C(Rec r, int& e, int& k, int& c, int& cj1, int& cj2) {
+    c = (int)(r & 2047);
+    cj1 = (int)((r >> 11) & 2047);
+    cj2 = (int)((r >> 22) & 2047);
+    k = (int)((r >> 34) & 3);
+    e = (int)((r >> 36) & 7);
+}
+
+CDP_HD void decode_D(Rec r, int& f, int& l, int& dj, int& dk, int& m) {
+    m = (int)(r & 2047);
+    dj = (int)((r >> 11) & 2047);
+    dk = (int)((r >> 22) & 2047);
+    l = (int)((r >> 35) & 3);
+    f = (int)((r >> 37) & 3);
 }
 
 // all items of a unit, one after the other (host reference runs and single-thread use)
@@ -908,8 +1010,8 @@ CDP_HD int tri_cross_cell(const TriGeo<R>& G, int a, int b, int k, int c, int gu
 
 template <typename R>
 CDP_HD void tri_origin(const TriGeo<R>& G, int v0, int v1, R O[2]) {
-    O[0] = clamp_r(G.c[0], R(v0), R(v0 + 1));
-    O[1] = clamp_r(G.c[1], R(v1), R(v1 + 1));
+    O[0] = clamp_r(G.c[0], R(v0) + R(0.25), R(v0) + R(0.75));
+    O[1] = clamp_r(G.c[1], R(v1) + R(0.25), R(v1) + R(0.75));
 }
 
 // B: vertex i; P = x_i - O

@@ -313,28 +313,39 @@ __device__ __forceinline__ void tri_phase_item(const TriGeo<R>& G, int ph, int t
     }
 }
 
-// evaluate one queued record of phase ph and add it to its simplex's piece
+// evaluate one queued corner record of phase ph and add its cells to its simplex's pieces
 template <int DIM, typename R>
 __device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned long long r, int ph, const GridDesc& g,
                                             double* out, bool closure, UnitCounts* cnt) {
     const int own = (int)((r >> 40) & 31);
     const typename GeoOf<DIM, R>::T& G = sh->geo[own];
     WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, closure);
-    int v0, v1, v2;
-    R val;
     if constexpr (DIM == 3) {
         if (ph == 1) {
-            val = tet_eval_crossing(G, r, v0, v1, v2);
-            if (cnt) cnt->c++;
+            int e, k, c, cj1, cj2;
+            decode_C(r, e, k, c, cj1, cj2);
+            R v[2];
+            int cl[2][3];
+            tet_eval_C2(G, e, k, c, cj1, cj2, v, cl);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) acc(cl[q][0], cl[q][1], cl[q][2], v[q]);
+            if (cnt) cnt->c += 2;
         } else {
-            val = tet_eval_line(G, r, v0, v1, v2);
-            if (cnt) cnt->d++;
+            int f, l, dj, dk, m;
+            decode_D(r, f, l, dj, dk, m);
+            R v[4];
+            int cl[4][3];
+            tet_eval_D4(G, f, l, dj, dk, m, v, cl);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc(cl[q][0], cl[q][1], cl[q][2], v[q]);
+            if (cnt) cnt->d += 4;
         }
     } else {
-        val = tri_eval_crossing(G, r, v0, v1, v2);
+        int v0, v1, v2;
+        R val = tri_eval_crossing(G, r, v0, v1, v2);
         if (cnt) cnt->c++;
+        acc(v0, v1, v2, val);
     }
-    acc(v0, v1, v2, val);
 }
 
 template <int DIM, typename R>

@@ -125,6 +125,31 @@ CDP_API int cdp_project(cdp_ctx* ctx, const cdp_problem* prob, int precision, in
  * accumulate = 0 and no stats).  The scratch is sized once for the largest problem first. */
 CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, int precision, void* stream);
 
+/* Largest n_verts accepted by cdp_project_noalloc (32 bytes of static device scratch each: 8 MiB). */
+#define CDP_NOALLOC_MAX_VERTS 262144
+
+/* The projection of cdp_project (same kernels, same results), for callers that must not allocate
+ * or free memory when they call: for instance a caller whose framework has reserved the device
+ * memory for its own pool, or one that cannot afford the device-wide synchronisation that
+ * cudaFree implies while other streams are busy.  It takes no context: its scratch (vertex
+ * records and counters) is one fixed device array of this library, sized for
+ * CDP_NOALLOC_MAX_VERTS vertices, and it calls no allocating routine.  The paper has no
+ * counterpart of this entry point; it exists only for the allocation constraint above.
+ *  - Runs on the CURRENT CUDA device.  The first call on a device looks up the scratch address
+ *    and the launch parameters of that device (no allocation); make that first call before any
+ *    stream capture is begun.
+ *  - n_verts > CDP_NOALLOC_MAX_VERTS returns CDP_ERR_ARG before anything is enqueued; other
+ *    argument checks are those of cdp_project.
+ *  - Every call on a device shares the one scratch array: two calls whose work overlaps on the
+ *    GPU (two streams, or two host threads) race and both results are undefined.  Serialise them
+ *    (one stream, or events between the streams).
+ *  - error_flags: optional device pointer to one uint32_t; when the call's work has run it holds
+ *    the bits of cdp_stats.error_flags for this call (0 = no error).  NULL: errors are not
+ *    reported.
+ *  - accumulate and precision as in cdp_project.  Only enqueues; nothing synchronises. */
+CDP_API int cdp_project_noalloc(const cdp_problem* prob, int precision, int accumulate, uint32_t* error_flags,
+                                void* stream);
+
 /* Vertex densities from simplex masses (Sect. 4.4): rho_out[j] = sum of simplex_mass[i] over the
  * simplices incident to vertex j divided by the sum of their volumes |V_i| (world units,
  * periodic minimal image when prob->periodic).  Uses dim, n_verts, n_simplices, pos, simplices,

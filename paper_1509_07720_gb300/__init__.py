@@ -19,6 +19,7 @@ __all__ = [
     "cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror", "cdp_timing_enable",
     "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density", "cdp_poisson", "cdp_force", "cdp_drift",
     "cdp_kick", "cdp_step_batched", "cdp_step_problem", "Projector", "EXPORTED_SYMBOLS",
+    "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS",
 ]
 
 CDP_FP64 = 0
@@ -31,7 +32,8 @@ _lib = None
 # every symbol the header declares (checked by the CPU tests)
 EXPORTED_SYMBOLS = ("cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror",
                     "cdp_timing_enable", "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density",
-                    "cdp_poisson", "cdp_force", "cdp_drift", "cdp_kick", "cdp_step_batched")
+                    "cdp_poisson", "cdp_force", "cdp_drift", "cdp_kick", "cdp_step_batched",
+                    "cdp_project_noalloc")
 
 
 class CdpError(RuntimeError):
@@ -124,6 +126,8 @@ def load_library(path: str | None = None):
     lib.cdp_step_batched.argtypes = [vp, ctypes.POINTER(cdp_step_problem), ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     lib.cdp_step_batched.restype = ctypes.c_int
+    lib.cdp_project_noalloc.argtypes = [ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.cdp_project_noalloc.restype = ctypes.c_int
     lib.cdp_strerror.argtypes = [ctypes.c_int]
     lib.cdp_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -201,6 +205,17 @@ def _p3(ts):
 def cdp_project_batched(ctx, probs, precision: int, stream: int = 0) -> int:
     arr = (cdp_problem * len(probs))(*probs)
     return load_library().cdp_project_batched(ctx, arr, len(probs), int(precision), ctypes.c_void_p(stream))
+
+
+# largest vertex count of cdp_project_noalloc (its static device scratch)
+CDP_NOALLOC_MAX_VERTS = 262144
+
+
+def cdp_project_noalloc(prob: cdp_problem, precision: int, accumulate: int = 0, error_flags_ptr: int = 0,
+                        stream: int = 0) -> int:
+    """Projection on the current device with library-owned static scratch (no allocation)."""
+    return load_library().cdp_project_noalloc(ctypes.byref(prob), int(precision), int(accumulate),
+                                              ctypes.c_void_p(error_flags_ptr), ctypes.c_void_p(stream))
 
 
 def cdp_vertex_density(ctx, prob: cdp_problem, simplex_mass_ptr: int, rho_out_ptr: int, stream: int = 0) -> int:

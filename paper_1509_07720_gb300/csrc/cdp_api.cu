@@ -110,6 +110,9 @@ int fold_timing(cdp_ctx* c) {
 
 namespace cdp {
 
+// argument check of one problem, for the entry points defined in other translation units
+int check_problem_args(const cdp_problem* p) { return check_problem(p); }
+
 // grow the scratch to hold the largest of `n` problems (allocation happens here, never inside
 // a captured sequence)
 int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {

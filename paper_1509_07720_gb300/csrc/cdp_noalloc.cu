@@ -1,0 +1,127 @@
+// Projection entry point that allocates nothing (declared in include/coldproj.h as
+// cdp_project_noalloc).  Its scratch (the vertex records and the per-call counters) is one
+// statically sized device array of this module instead of context-owned memory; the kernels are
+// the ones cdp_project launches.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/coldproj.h"
+#include "cdp_project.h"
+
+namespace cdp {
+int check_problem_args(const cdp_problem* p);
+}
+
+namespace {
+
+constexpr long long kMaxVerts = CDP_NOALLOC_MAX_VERTS;
+constexpr size_t kCounterBytes = 256;  // the counters, padded so that the records stay 256-aligned
+constexpr size_t kScratchBytes = kCounterBytes + (size_t)kMaxVerts * sizeof(cdp::VertexRec);
+static_assert(sizeof(cdp::Counters) <= kCounterBytes, "counters do not fit their slot");
+
+// [counters | vertex records]; shared by every call on the device
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+
+// per-device launch parameters and the scratch address, filled once with the device current
+struct DeviceSetup {
+    bool ready;
+    unsigned char* scratch;
+    int num_sms;
+    int blocks[2][2];  // [dim == 3][fp32]: resident blocks per SM of the projection kernel
+};
+
+DeviceSetup g_setup[kMaxDevices];
+std::mutex g_setup_lock;
+
+int setup_device(int dev, DeviceSetup** out) {
+    if (dev < 0 || dev >= kMaxDevices) return CDP_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_setup_lock);
+    DeviceSetup& s = g_setup[dev];
+    if (!s.ready) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return CDP_ERR_CUDA;
+        }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cdp::configure_all() != cudaSuccess) {
+            cudaGetLastError();
+            return CDP_ERR_CUDA;
+        }
+        s.scratch = (unsigned char*)ptr;
+        s.num_sms = sms;
+        for (int d3 = 0; d3 < 2; ++d3)
+            for (int f = 0; f < 2; ++f) s.blocks[d3][f] = cdp::resident_blocks(d3 ? 3 : 2, f);
+        s.ready = true;
+    }
+    *out = &s;
+    return CDP_OK;
+}
+
+}  // namespace
+
+extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accumulate, uint32_t* error_flags,
+                                   void* stream) {
+    int rc = cdp::check_problem_args(p);
+    if (rc) return rc;
+    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    if (p->n_verts > kMaxVerts) return CDP_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    DeviceSetup* s = nullptr;
+    if ((rc = setup_device(dev, &s))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    cdp::LaunchArgs L;
+    memset(&L, 0, sizeof(L));
+    L.g.dim = p->dim;
+    L.g.periodic = p->periodic ? 1 : 0;
+    long long cells = 1;
+    L.cellvol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (a < p->dim) {
+            L.g.n[a] = p->grid[a];
+            L.g.lo[a] = p->box_lo[a];
+            L.g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
+            L.cellvol *= p->box_len[a] / (double)p->grid[a];
+            cells *= p->grid[a];
+        } else {
+            L.g.n[a] = 1;
+            L.g.lo[a] = 0.0;
+            L.g.inv_h[a] = 1.0;
+        }
+    }
+    L.g.cell_volume = L.cellvol;
+    L.nv = p->n_verts;
+    L.ns = p->n_simplices;
+    L.simplices = p->simplices;
+    L.ctr = (cdp::Counters*)s->scratch;
+    L.verts = (cdp::VertexRec*)(s->scratch + kCounterBytes);
+    L.out = p->cell_mass;
+    L.stats = nullptr;
+    L.num_sms = s->num_sms;
+    int fp32 = precision == CDP_FP32_MIXED;
+    L.small_blocks_per_sm = 4 * s->blocks[p->dim == 3][fp32];
+
+    // every counter, the error word included, starts at zero on each call
+    if (cudaMemsetAsync(s->scratch, 0, sizeof(cdp::Counters), st) != cudaSuccess) return CDP_ERR_CUDA;
+    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
+        return CDP_ERR_CUDA;
+    if (cdp::launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess ||
+        cdp::launch_project(L, fp32, st, nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    if (error_flags &&
+        cudaMemcpyAsync(error_flags, &L.ctr->flags, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return CDP_ERR_CUDA;
+    return CDP_OK;
+}

@@ -295,12 +295,12 @@ def run_ours(a):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the warp-cooperative projection kernel)
-    names = ["k_prep_vertices", "k_project_warp<3,float>", "(none)"]
-    kern32 = kern32[:2]
-    dom = int(np.argmax(kern32))
+    # roofline of the dominant kernel (the tetrahedron projection kernel); its incidences are all
+    # corners but those of the FP64 large-simplex pass
+    names = ["k_prep_vertices", "k_project_tet<float>", "k_project_warp<3,double> (large-simplex pass)"]
+    dom = int(np.argmax(kern32[:2]))
     if dom == 1:
-        inc = {k: st32["corners_" + k] for k in "abcd"}
+        inc = {k: st32["corners_" + k] - st32["large_corners"][i] for i, k in enumerate("abcd")}
     else:
         inc = None
     if inc is not None:
@@ -328,10 +328,10 @@ def run_ours(a):
                        "kernel_ms": kern64, "speedup_fp32_mixed_vs_fp64": ms64 / ms32},
         "kernel_ms": dict(zip(names, kern32)),
         "corners": {k: st32[k] for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell",
-                                         "n_small", "n_zero_volume", "exact_fallbacks")},
+                                         "n_small", "n_large", "n_zero_volume", "exact_fallbacks")},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 2 * a.steps,
+        "gpu_launches": 3 * a.steps,  # vertex records, main kernel, large-simplex pass
         "e2e": e2e,
     }
     if ws == 1 and not a.no_cpu_baseline:

@@ -91,15 +91,15 @@ typedef struct {
 typedef struct {
     uint64_t n_zero_volume;   /* simplices of zero volume (no contribution) */
     uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
-    uint64_t n_small;         /* simplices projected by one thread (bounding box <= 512 cells) */
-    uint64_t n_large;         /* simplices split into tiles */
-    uint64_t n_large_tiles;   /* tiles processed for them */
+    uint64_t n_small;         /* simplices projected by the main kernel (3D: bounding box <= 1280 cells) */
+    uint64_t n_large;         /* tetrahedra with a larger bounding box: projected by the FP64 large-simplex pass */
+    uint64_t n_large_tiles;   /* always 0 (reserved) */
     uint64_t corners_a;       /* (corner, cell) incidences of type A: grid node inside a simplex */
     uint64_t corners_b;       /* type B: simplex vertex */
     uint64_t corners_c;       /* type C: simplex edge x cell face */
     uint64_t corners_d;       /* type D: simplex facet x cell edge (3D) */
     uint64_t exact_fallbacks; /* predicate evaluations decided by the exact integer stage */
-    uint64_t large_corners[4];/* the part of corners_a..d found by the tiled kernel (A, B, C, D) */
+    uint64_t large_corners[4];/* the part of corners_a..d found by the large-simplex pass (A, B, C, D) */
     uint32_t error_flags;     /* bit 0 bad index, bit 1 non-finite, bit 2 extent */
     uint32_t reserved;
 } cdp_stats;
@@ -125,8 +125,10 @@ CDP_API int cdp_project(cdp_ctx* ctx, const cdp_problem* prob, int precision, in
  * accumulate = 0 and no stats).  The scratch is sized once for the largest problem first. */
 CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, int precision, void* stream);
 
-/* Largest n_verts accepted by cdp_project_noalloc (32 bytes of static device scratch each: 8 MiB). */
+/* Largest n_verts and n_simplices accepted by cdp_project_noalloc (static device scratch of 32
+ * bytes per vertex and 4 per simplex: 8 MiB + 6 MiB). */
 #define CDP_NOALLOC_MAX_VERTS 262144
+#define CDP_NOALLOC_MAX_SIMPLICES 1572864
 
 /* The projection of cdp_project (same kernels, same results), for callers that must not allocate
  * or free memory when they call: for instance a caller whose framework has reserved the device
@@ -138,7 +140,8 @@ CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, i
  *  - Runs on the CURRENT CUDA device.  The first call on a device looks up the scratch address
  *    and the launch parameters of that device (no allocation); make that first call before any
  *    stream capture is begun.
- *  - n_verts > CDP_NOALLOC_MAX_VERTS returns CDP_ERR_ARG before anything is enqueued; other
+ *  - n_verts > CDP_NOALLOC_MAX_VERTS or n_simplices > CDP_NOALLOC_MAX_SIMPLICES returns
+ *    CDP_ERR_ARG before anything is enqueued; other
  *    argument checks are those of cdp_project.
  *  - Every call on a device shares the one scratch array: two calls whose work overlaps on the
  *    GPU (two streams, or two host threads) race and both results are undefined.  Serialise them

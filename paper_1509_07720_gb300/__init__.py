@@ -19,7 +19,7 @@ __all__ = [
     "cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror", "cdp_timing_enable",
     "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density", "cdp_poisson", "cdp_force", "cdp_drift",
     "cdp_kick", "cdp_step_batched", "cdp_step_problem", "Projector", "EXPORTED_SYMBOLS",
-    "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS",
+    "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS", "CDP_NOALLOC_MAX_SIMPLICES",
 ]
 
 CDP_FP64 = 0
@@ -207,8 +207,9 @@ def cdp_project_batched(ctx, probs, precision: int, stream: int = 0) -> int:
     return load_library().cdp_project_batched(ctx, arr, len(probs), int(precision), ctypes.c_void_p(stream))
 
 
-# largest vertex count of cdp_project_noalloc (its static device scratch)
+# largest vertex and simplex counts of cdp_project_noalloc (its static device scratch)
 CDP_NOALLOC_MAX_VERTS = 262144
+CDP_NOALLOC_MAX_SIMPLICES = 1572864
 
 
 def cdp_project_noalloc(prob: cdp_problem, precision: int, accumulate: int = 0, error_flags_ptr: int = 0,

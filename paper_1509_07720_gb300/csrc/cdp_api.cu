@@ -121,14 +121,17 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
         if ((size_t)probs[i].n_verts > nv) nv = (size_t)probs[i].n_verts;
         if ((size_t)probs[i].n_simplices > ns) ns = (size_t)probs[i].n_simplices;
     }
-    (void)ns;
-    return grow(&c->verts, &c->verts_cap, nv);
+    int rc = grow(&c->verts, &c->verts_cap, nv);
+    if (rc) return rc;
+    return grow(&c->queue, &c->queue_cap, ns);
 }
 
 // enqueue one projection on `st` (arguments already checked)
 int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats) {
     int rc;
     if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
+    if (p->dim == 3 && (rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1))))
+        return rc;
 
     LaunchArgs L;
     memset(&L, 0, sizeof(L));
@@ -161,7 +164,9 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     int fp32 = precision == CDP_FP32_MIXED;
     // a persistent grid: every resident block slot of the device, four times over
     L.small_blocks_per_sm = 4 * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
-    L.big_blocks_per_sm = 0;
+    L.big_blocks_per_sm = c->blocks_large;
+    L.big_list = c->queue;
+    L.big_cap = (long long)c->queue_cap;
 
     // zero the per-call counters (the sticky error word at offset 0 is kept)
     if (cudaMemsetAsync((char*)c->ctr + sizeof(unsigned), 0, sizeof(Counters) - sizeof(unsigned), st) !=
@@ -212,7 +217,7 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     stats->n_zero_volume = c->h_ctr->n_zero;
     stats->n_single_cell = c->h_ctr->n_class0;
     stats->n_small = c->h_ctr->n_small;
-    stats->n_large = 0;
+    stats->n_large = c->h_ctr->big_count;
     stats->n_large_tiles = 0;
     const cdp::UnitCounts& s0 = c->h_stats[0];
     const cdp::UnitCounts& s1 = c->h_stats[1];
@@ -221,7 +226,7 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     stats->corners_c = s0.c + s1.c;
     stats->corners_d = s0.d + s1.d;
     stats->exact_fallbacks = s0.exact + s1.exact;
-    stats->large_corners[0] = s1.a;  // zero: every simplex goes through the warp kernel
+    stats->large_corners[0] = s1.a;  // found by the FP64 large-simplex pass
     stats->large_corners[1] = s1.b;
     stats->large_corners[2] = s1.c;
     stats->large_corners[3] = s1.d;
@@ -295,6 +300,7 @@ int cdp_create(cdp_ctx** out, int device) {
     c->blocks_small[1] = cdp::resident_blocks(3, 1);
     c->blocks_big[0] = cdp::resident_blocks(2, 0);
     c->blocks_big[1] = cdp::resident_blocks(2, 1);
+    c->blocks_large = cdp::resident_blocks_large();
     if (cudaMalloc(&c->ctr, sizeof(cdp::Counters)) != cudaSuccess ||
         cudaMalloc(&c->stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess ||
         cudaMallocHost(&c->h_ctr, sizeof(cdp::Counters)) != cudaSuccess ||

@@ -32,11 +32,12 @@ void step_release(cdp_ctx* c);
 struct cdp_ctx {
     int device;
     int num_sms;
-    int blocks_small[2];  // resident blocks per SM of the small kernel (fp64, fp32)
-    int blocks_big[2];
+    int blocks_small[2];  // resident blocks per SM of the 3D kernel (fp64, fp32)
+    int blocks_big[2];    // of the 2D kernel
+    int blocks_large;     // of the FP64 large-simplex pass
     cdp::VertexRec* verts;
     size_t verts_cap;
-    int* queue;
+    int* queue;           // list of the tetrahedra for the large-simplex pass
     size_t queue_cap;
     cdp::Counters* ctr;       // device
     cdp::UnitCounts* stats;   // device

@@ -1,5 +1,6 @@
 // Projection entry point that allocates nothing (declared in include/coldproj.h as
-// cdp_project_noalloc).  Its scratch (the vertex records and the per-call counters) is one
+// cdp_project_noalloc).  Its scratch (the per-call counters, the vertex records and the list of
+// the large-simplex pass) is one
 // statically sized device array of this module instead of context-owned memory; the kernels are
 // the ones cdp_project launches.
 #include <cuda_runtime.h>
@@ -17,11 +18,13 @@ int check_problem_args(const cdp_problem* p);
 namespace {
 
 constexpr long long kMaxVerts = CDP_NOALLOC_MAX_VERTS;
+constexpr long long kMaxSimplices = CDP_NOALLOC_MAX_SIMPLICES;
 constexpr size_t kCounterBytes = 256;  // the counters, padded so that the records stay 256-aligned
-constexpr size_t kScratchBytes = kCounterBytes + (size_t)kMaxVerts * sizeof(cdp::VertexRec);
+constexpr size_t kListOffset = kCounterBytes + (size_t)kMaxVerts * sizeof(cdp::VertexRec);
+constexpr size_t kScratchBytes = kListOffset + (size_t)kMaxSimplices * sizeof(int);
 static_assert(sizeof(cdp::Counters) <= kCounterBytes, "counters do not fit their slot");
 
-// [counters | vertex records]; shared by every call on the device
+// [counters | vertex records | large-simplex list]; shared by every call on the device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -32,6 +35,7 @@ struct DeviceSetup {
     unsigned char* scratch;
     int num_sms;
     int blocks[2][2];  // [dim == 3][fp32]: resident blocks per SM of the projection kernel
+    int blocks_large;  // of the FP64 large-simplex pass
 };
 
 DeviceSetup g_setup[kMaxDevices];
@@ -57,6 +61,7 @@ int setup_device(int dev, DeviceSetup** out) {
         s.num_sms = sms;
         for (int d3 = 0; d3 < 2; ++d3)
             for (int f = 0; f < 2; ++f) s.blocks[d3][f] = cdp::resident_blocks(d3 ? 3 : 2, f);
+        s.blocks_large = cdp::resident_blocks_large();
         s.ready = true;
     }
     *out = &s;
@@ -70,7 +75,7 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     int rc = cdp::check_problem_args(p);
     if (rc) return rc;
     if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
-    if (p->n_verts > kMaxVerts) return CDP_ERR_ARG;
+    if (p->n_verts > kMaxVerts || p->n_simplices > kMaxSimplices) return CDP_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -110,6 +115,9 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     L.num_sms = s->num_sms;
     int fp32 = precision == CDP_FP32_MIXED;
     L.small_blocks_per_sm = 4 * s->blocks[p->dim == 3][fp32];
+    L.big_blocks_per_sm = s->blocks_large;
+    L.big_list = (int*)(s->scratch + kListOffset);
+    L.big_cap = kMaxSimplices;
 
     // every counter, the error word included, starts at zero on each call
     if (cudaMemsetAsync(s->scratch, 0, sizeof(cdp::Counters), st) != cudaSuccess) return CDP_ERR_CUDA;

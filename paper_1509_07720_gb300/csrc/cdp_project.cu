@@ -353,7 +353,8 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                                                             const int* __restrict__ simp,
                                                             const VertexRec* __restrict__ V,
                                                             double* __restrict__ out, Counters* __restrict__ ctr,
-                                                            UnitCounts* __restrict__ stats) {
+                                                            UnitCounts* __restrict__ stats,
+                                                            const int* __restrict__ list, long long list_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
@@ -367,17 +368,24 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
     UnitCounts cnt = {0, 0, 0, 0, 0};
     UnitCounts* pc = stats ? &cnt : nullptr;
     unsigned long long n0 = 0, nact = 0, nzero = 0;
-    const long long nchunks = (ns + CDP_CHUNK - 1) / CDP_CHUNK;
+    if (list) {
+        // large-simplex pass: the simplices listed by the main kernel
+        const long long cnt_listed = (long long)*(volatile unsigned*)&ctr->big_count;
+        ns = cnt_listed < list_cap ? cnt_listed : list_cap;
+    }
+    // the large-simplex pass gives each listed simplex a warp of its own
+    const int cs = list ? 1 : CDP_CHUNK;
+    const long long nchunks = (ns + cs - 1) / cs;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
          chunk += warps) {
         // ---- setup: one simplex per lane
-        const long long s = chunk * CDP_CHUNK + lane;
+        const long long s = chunk * cs + lane;
         bool active = false;
         int n[3] = {0, 0, 0};
-        if (lane < CDP_CHUNK && s < ns) {
+        if (lane < cs && s < ns) {
             const VertexRec* v[4];
-            if (!fetch_vertices(simp, s, DIM + 1, nv, V, v)) {
+            if (!fetch_vertices(simp, list ? (long long)list[s] : s, DIM + 1, nv, V, v)) {
                 atomicOr(&ctr->flags, CDP_FLAG_INDEX);
             } else if constexpr (DIM == 3) {
                 Tet S;
@@ -516,7 +524,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
     if (stats) {
         add_counts(stats, cnt);
         if (n0) atomicAdd(&ctr->n_class0, n0);
-        if (nact) atomicAdd(&ctr->n_small, nact);
+        if (nact && !list) atomicAdd(&ctr->n_small, nact);  // listed ones are counted as large
         if (nzero) atomicAdd(&ctr->n_zero, nzero);
     }
 }
@@ -530,37 +538,40 @@ static size_t shared_bytes() {
     return sizeof(WarpShared<DIM, R>) * (CDP_WBLOCK / 32);
 }
 
-template <typename R>
-static cudaError_t configure_kernels() {
+cudaError_t configure_all() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_project_warp<3, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)shared_bytes<3, R>())))
+    if ((e = cudaFuncSetAttribute(k_project_warp<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shared_bytes<2, float>())))
         return e;
-    if ((e = cudaFuncSetAttribute(k_project_warp<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)shared_bytes<2, R>())))
+    if ((e = cudaFuncSetAttribute(k_project_warp<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shared_bytes<2, double>())))
         return e;
-    return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(k_project_warp<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shared_bytes<3, double>())))
+        return e;
+    return configure_tet();
 }
 
-cudaError_t configure_all() {
-    cudaError_t e = configure_kernels<float>();
-    if (e) return e;
-    return configure_kernels<double>();
+int resident_blocks_large() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_warp<3, double>, CDP_WBLOCK,
+                                                      shared_bytes<3, double>()) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
 }
 
 int resident_blocks(int dim, int fp32) {
+    if (dim == 3) return resident_blocks_tet(fp32);
     int n = 0;
     cudaError_t e;
-    if (dim == 3)
-        e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_warp<3, float>, CDP_WBLOCK,
-                                                                 shared_bytes<3, float>())
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_warp<3, double>, CDP_WBLOCK,
-                                                                 shared_bytes<3, double>());
-    else
+    {
         e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_warp<2, float>, CDP_WBLOCK,
                                                                  shared_bytes<2, float>())
                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_warp<2, double>, CDP_WBLOCK,
                                                                  shared_bytes<2, double>());
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -576,8 +587,17 @@ static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t 
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(
-        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats);
+        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, nullptr, 0);
     if (mid) cudaEventRecord(mid, st);
+    return cudaGetLastError();
+}
+
+// FP64 pass over the tetrahedra the main kernel listed (their number is read on the device)
+static cudaError_t launch_large(const LaunchArgs& L, cudaStream_t st) {
+    long long blocks = (long long)L.num_sms * (L.big_blocks_per_sm > 0 ? L.big_blocks_per_sm : 1);
+    k_project_warp<3, double><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<3, double>(), st>>>(
+        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats ? L.stats + 1 : nullptr, L.big_list,
+        L.big_cap);
     return cudaGetLastError();
 }
 
@@ -595,7 +615,12 @@ cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaE
         if (mid) cudaEventRecord(mid, st);
         return cudaSuccess;
     }
-    if (L.g.dim == 3) return fp32 ? launch_dim<3, float>(L, st, mid) : launch_dim<3, double>(L, st, mid);
+    if (L.g.dim == 3) {
+        cudaError_t e = launch_tet(L, fp32, st);
+        if (e != cudaSuccess) return e;
+        if (mid) cudaEventRecord(mid, st);
+        return launch_large(L, st);
+    }
     return fp32 ? launch_dim<2, float>(L, st, mid) : launch_dim<2, double>(L, st, mid);
 }
 

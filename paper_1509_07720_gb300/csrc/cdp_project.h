@@ -16,8 +16,8 @@ constexpr int CDP_QCAP = 512;     // per-warp queue of (corner, cell) records (p
 // Per-call device counters (zeroed at the start of every projection).
 struct Counters {
     unsigned flags;       // CDP_FLAG_* bits
-    unsigned big_count;   // simplices queued for the tiled kernel
-    unsigned big_next;    // work cursor of the tiled kernel
+    unsigned big_count;   // tetrahedra listed for the large-simplex pass
+    unsigned big_next;    // (unused)
     unsigned pad;
     unsigned long long n_class0, n_small, n_zero, n_big_tiles;
 };
@@ -31,18 +31,26 @@ struct LaunchArgs {
     double cellvol;
     int* queue;
     Counters* ctr;
-    UnitCounts* stats;  // may be null
+    UnitCounts* stats;  // may be null (else two blocks: main kernel, large-simplex pass)
     int num_sms;
     int small_blocks_per_sm;
     int big_blocks_per_sm;
+    int* big_list;      // tetrahedra whose bounding box exceeds the shared box (capacity big_cap)
+    long long big_cap;
 };
 
 cudaError_t configure_all();
-// resident blocks per SM of the projection kernel (occupancy calculator)
+// resident blocks per SM of the projection kernel of dimension `dim` (occupancy calculator)
 int resident_blocks(int dim, int fp32);
+// resident blocks per SM of the FP64 large-simplex pass (3D)
+int resident_blocks_large();
+// the tetrahedron kernel (cdp_tetproj.cu)
+cudaError_t configure_tet();
+int resident_blocks_tet(int fp32);
+cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st);
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
                         const double* rho, cudaStream_t st);
-// `mid` (optional) is recorded between the one-thread kernel and the tiled kernel
+// `mid` (optional) is recorded between the main kernel and the large-simplex pass
 cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t mid);
 
 }  // namespace cdp

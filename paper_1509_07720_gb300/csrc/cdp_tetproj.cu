@@ -1,0 +1,518 @@
+// Projection kernel of tetrahedral meshes (Sect. 3; Algorithm 2 organised per simplex).
+//
+// k_project_tet<R> is a persistent warp-cooperative kernel.  A warp takes TB_CHUNK consecutive
+// tetrahedra; each lane of the first half canonicalises one of them (exact orientation, periodic
+// unwrap, cells) and writes its geometry to shared memory.  A tetrahedron inside one cell deposits
+// |V| mean(rho) at once (Algorithm 2, step 1).  Every other tetrahedron receives a dense box of
+// per-cell accumulators in shared memory, one slot per cell of its bounding box; the tetrahedra of
+// the chunk are packed into rounds whose boxes fit the warp's TB_BOX slots together (a
+// tetrahedron whose box alone exceeds them is listed for the large-simplex pass).
+//
+// The work of a round is split into three phases of independent items -- the vertices (corners
+// B), the (edge, axis, plane) crossings (corners C) and the grid lines (corners D, and along x the
+// grid nodes between the two pierced facets, corners A) -- whose items of all tetrahedra of the
+// round are numbered consecutively and dealt to the 32 lanes in turn.  Locating a corner costs a
+// few exact-sign predicates; evaluating it (all the cells around it at once) costs most of the
+// arithmetic, so located corners are queued as compact records and evaluated in full batches of
+// 32 identical evaluations.  Every (corner, cell) contribution is one shared-memory add into the
+// box of its tetrahedron.  At the end of the round each box is flushed with one FP64 global
+// atomic per non-zero (tetrahedron, cell) piece.
+//
+// FP32-mixed path only: the mass closure (not in the paper).  The FP64 closed-form mass of each
+// tetrahedron minus the FP64 sum of its FP32 pieces is spread over its pieces in proportion to
+// their magnitude, so the total mass is exact to FP64 rounding and no piece moves by more than
+// the FP32 rounding of the tetrahedron's own sum.
+#include <cuda_runtime.h>
+
+#include "cdp_mesh.cuh"
+#include "cdp_project.h"
+
+namespace cdp {
+
+namespace {
+
+constexpr int TB_CHUNK = 16;   // tetrahedra per warp chunk (one per lane during set-up)
+constexpr int TB_QCAP = 128;   // C / D corner records awaiting evaluation (power of two)
+constexpr int TB_ACAP = 64;    // runs of A nodes awaiting evaluation (power of two)
+constexpr unsigned FULL = 0xffffffffu;
+
+// box slots per warp: 1280 FP32 or FP64 accumulators
+template <typename R>
+struct BoxCap {
+    static constexpr int value = 1280;
+};
+
+template <typename R>
+struct TetShared {
+    TetGeo<R> geo[TB_CHUNK];
+    R box[BoxCap<R>::value];
+    Rec q[TB_QCAP];
+    unsigned long long aq[TB_ACAP];
+    unsigned short xcum[TB_CHUNK][18];  // running count of the crossings of the (edge, axis) pairs
+    int boff[TB_CHUNK];                 // first box slot of each tetrahedron of the round
+};
+
+// ------------------------------------------------------------------------------------------
+// accumulation into the box of tetrahedron `own` (cell (x, y, z) of its bounding box)
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void box_add(TetShared<R>* sh, int own, int x, int y, int z, R v) {
+    const TetGeo<R>& G = sh->geo[own];
+    const int ex = G.hi[0] + 1, ey = G.hi[1] + 1, ez = G.hi[2] + 1;
+    if ((unsigned)x < (unsigned)ex && (unsigned)y < (unsigned)ey && (unsigned)z < (unsigned)ez)
+        atomicAdd(&sh->box[sh->boff[own] + x + ex * (y + ey * z)], v);
+}
+
+// ------------------------------------------------------------------------------------------
+// items
+// ------------------------------------------------------------------------------------------
+
+// B: vertex i of tetrahedron own
+template <typename R>
+__device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
+    const TetGeo<R>& G = sh->geo[own];
+    const int v0 = G.cell[i][0], v1 = G.cell[i][1], v2 = G.cell[i][2];
+    R O[3], P[3];
+    piece_origin(G, v0, v1, v2, O);
+    for (int a = 0; a < 3; ++a) P[a] = (G.x[i][a] - O[a]) + G.xl[i][a];
+    box_add(sh, own, v0, v1, v2, tet_corner_B(G, i, P));
+}
+
+// crossing t of tetrahedron own: the C record, or 0 when it has no cell in the box
+template <typename R>
+__device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, int t, UnitCounts* cnt) {
+    const unsigned short* cum = sh->xcum[own];
+    // first (edge, axis) pair whose running count exceeds t
+    int p = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (p + step <= 17 && (int)cum[p + step - 1] <= t) p += step;
+    const int before = p > 0 ? (int)cum[p - 1] : 0;
+    const int e = p / 3, k = p - 3 * e;
+    const TetGeo<R>& G = sh->geo[own];
+    int a, b, pp, qq;
+    tet_edge(e, a, b, pp, qq);
+    const int ca = G.cell[a][k], cb = G.cell[b][k];
+    const int c = (ca < cb ? ca : cb) + 1 + (t - before);
+    const int td[3] = {G.hi[0] + 1, G.hi[1] + 1, G.hi[2] + 1};
+    Rec r = 0;
+    auto keep = [&](Rec x) { r = x; };
+    tet_locate_crossing(G, e, k, c, td, keep, cnt);
+    return r;
+}
+
+// line t of tetrahedron own: up to two D records and the run of A nodes (x lines only)
+template <typename R>
+__device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t, Rec& r0, Rec& r1,
+                                         unsigned long long& arun, UnitCounts* cnt) {
+    const TetGeo<R>& G = sh->geo[own];
+    const int h0 = G.hi[0], h1 = G.hi[1], h2 = G.hi[2];
+    // lines along l through the interior grid points (dj, dk) in [1, h_j] x [1, h_k]
+    int l, nj;
+    if (t < h1 * h2) {
+        l = 0;
+        nj = h1;
+    } else if ((t -= h1 * h2) < h0 * h2) {
+        l = 1;
+        nj = h0;
+    } else {
+        t -= h0 * h2;
+        l = 2;
+        nj = h0;
+    }
+    const int tq = t / nj;
+    const int dj = 1 + t - tq * nj, dk = 1 + tq;
+    const int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    const unsigned hits = tet_pierced(tet_line_signs(G, j, k, dj, dk, cnt));
+    int nr = 0;
+    arun = 0;
+    if (!hits) return 0;
+    int mlo = 0, mhi = -1;
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        if (!((hits >> f) & 1u)) continue;
+        const int va = f == 0 ? 1 : 0;
+        const R fj = G.n[f][j], fk = G.n[f][k], fl = G.n[f][l];
+        const R off =
+            -(fj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + fk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / fl;
+        const int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(G.x[va][l] + off), cnt);
+        if (G.ns[f][l] > 0)
+            mlo = m;
+        else
+            mhi = m;
+        const Rec r = (Rec)m | ((Rec)dj << 11) | ((Rec)dk << 22) | ((Rec)l << 35) | ((Rec)f << 37);
+        if (nr == 0)
+            r0 = r;
+        else
+            r1 = r;
+        ++nr;
+    }
+    // grid nodes strictly inside: (cx, dj, dk) for cx in [mlo + 1, mhi] (x lines only)
+    if (l == 0 && nr == 2 && mhi >= mlo + 1)
+        arun = (unsigned long long)(mlo + 1) | ((unsigned long long)mhi << 11) | ((unsigned long long)dj << 22) |
+               ((unsigned long long)dk << 33);
+    return nr;
+}
+
+// ------------------------------------------------------------------------------------------
+// evaluation of queued corners
+// ------------------------------------------------------------------------------------------
+
+template <typename R>
+__device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, UnitCounts& cnt) {
+    const int own = (int)((r >> 40) & 15);
+    const TetGeo<R>& G = sh->geo[own];
+    if (is_c) {
+        int e, k, c, cj1, cj2;
+        decode_C(r, e, k, c, cj1, cj2);
+        R v[2];
+        int cl[2][3];
+        tet_eval_C2(G, e, k, c, cj1, cj2, v, cl);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) box_add(sh, own, cl[q][0], cl[q][1], cl[q][2], v[q]);
+        cnt.c += 2;
+    } else {
+        int f, l, dj, dk, m;
+        decode_D(r, f, l, dj, dk, m);
+        R v[4];
+        int cl[4][3];
+        tet_eval_D4(G, f, l, dj, dk, m, v, cl);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) box_add(sh, own, cl[q][0], cl[q][1], cl[q][2], v[q]);
+        cnt.d += 4;
+    }
+}
+
+// a run of A nodes (grid nodes inside the tetrahedron on one x line): the 8 cells of each node
+template <typename R>
+__device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, UnitCounts& cnt) {
+    const int own = (int)((r >> 44) & 15);
+    const int cx0 = (int)(r & 2047), cx1 = (int)((r >> 11) & 2047);
+    const int dj = (int)((r >> 22) & 2047), dk = (int)((r >> 33) & 2047);
+    const TetGeo<R>& G = sh->geo[own];
+#pragma unroll 1
+    for (int cx = cx0; cx <= cx1; ++cx) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
+            R O[3];
+            piece_origin(G, v0, v1, v2, O);
+            const R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
+            // the node is the cell's upper corner along a when the cell index is node - 1
+            const R sg = R(((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1));
+            box_add(sh, own, v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
+        }
+        cnt.a += 8;
+    }
+}
+
+// absolute cell index along one axis (periodic wrap without a division in the common case)
+__device__ __forceinline__ int wrap_axis(int v, int n, int periodic, bool& ok) {
+    if (!periodic) {
+        ok = ok && v >= 0 && v < n;
+        return v;
+    }
+    if (v >= n) v -= n;
+    if (v < 0) v += n;
+    if ((unsigned)v >= (unsigned)n) {
+        v %= n;
+        if (v < 0) v += n;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// owner lane of flat item u: the first lane whose inclusive prefix exceeds u
+__device__ __forceinline__ int owner_lane(int pre, int u) {
+    int own = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int p = __shfl_sync(FULL, pre, own + step - 1);
+        if (p <= u) own += step;
+    }
+    return own > 31 ? 31 : own;
+}
+
+__device__ __forceinline__ int inclusive_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+}  // namespace
+
+template <typename R>
+__global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
+    k_project_tet(GridDesc g, long long ns, long long nv, const int* __restrict__ simp, const VertexRec* __restrict__ V,
+                  double* __restrict__ out, Counters* __restrict__ ctr, UnitCounts* __restrict__ stats,
+                  int* __restrict__ big_list, long long big_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool fp32 = sizeof(R) == 4;
+    constexpr int BOX = BoxCap<R>::value;
+    const int lane = threadIdx.x & 31;
+    TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw) + (threadIdx.x >> 5);
+    for (int e = lane; e < BOX; e += 32) sh->box[e] = R(0);
+    __syncwarp();
+    UnitCounts cnt = {0, 0, 0, 0, 0};     // corner counts (registers)
+    UnitCounts xcnt = {0, 0, 0, 0, 0};    // exact-predicate count, updated through a pointer
+    UnitCounts* pc = stats ? &xcnt : nullptr;
+    unsigned long long n0 = 0, nact = 0, nzero = 0;
+    const long long nchunks = (ns + TB_CHUNK - 1) / TB_CHUNK;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
+         chunk += warps) {
+        // ---- set-up: one tetrahedron per lane
+        const long long s = chunk * TB_CHUNK + lane;
+        int need = 0;  // box slots of this lane's tetrahedron (0: nothing more to do)
+        if (lane < TB_CHUNK && s < ns) {
+            const VertexRec* v[4];
+            bool ok = true;
+            for (int k = 0; k < 4; ++k) {
+                const int id = __ldg(simp + s * 4 + k);
+                if (id < 0 || id >= nv) ok = false;
+                v[k] = V + (ok ? id : 0);
+            }
+            if (!ok) {
+                atomicOr(&ctr->flags, CDP_FLAG_INDEX);
+            } else {
+                Tet S;
+                const unsigned rc = canon_tet(g, v, S);
+                if (rc == 1) {
+                    ++nzero;
+                } else if (rc) {
+                    atomicOr(&ctr->flags, rc);
+                } else if (S.lo[0] == S.hi[0] && S.lo[1] == S.hi[1] && S.lo[2] == S.hi[2]) {
+                    const long long idx =
+                        flat_cell(g, S.anchor[0] + S.lo[0], S.anchor[1] + S.lo[1], S.anchor[2] + S.lo[2]);
+                    if (idx >= 0) atomicAdd(out + idx, tet_mass_cells(S));
+                    ++n0;
+                } else {
+                    const long long cells = (long long)(S.hi[0] - S.lo[0] + 1) * (S.hi[1] - S.lo[1] + 1) *
+                                            (S.hi[2] - S.lo[2] + 1);
+                    if (cells > BOX) {
+                        // listed for the large-simplex pass
+                        const unsigned long long at = atomicAdd(&ctr->big_count, 1u);
+                        if ((long long)at < big_cap) big_list[at] = (int)s;
+                    } else {
+                        TetGeo<R>& G = sh->geo[lane];
+                        tet_setup(S, S.lo, G);
+                        need = (int)cells;
+                        int run = 0;
+#pragma unroll 1
+                        for (int p = 0; p < 18; ++p) {
+                            const int e = p / 3, k = p - 3 * e;
+                            int a, b, pp, qq;
+                            tet_edge(e, a, b, pp, qq);
+                            const int d = G.cell[a][k] - G.cell[b][k];
+                            run += d < 0 ? -d : d;
+                            sh->xcum[lane][p] = (unsigned short)run;
+                        }
+                        ++nact;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        unsigned pending = __ballot_sync(FULL, need > 0);
+        // ---- rounds: tetrahedra in lane order while their boxes fit together
+        while (pending) {
+            const bool mine_pending = (pending >> lane) & 1u;
+            const int pre_box = inclusive_scan(mine_pending ? need : 0, lane);
+            const bool in = mine_pending && pre_box <= BOX;
+            const unsigned round = __ballot_sync(FULL, in);
+            pending &= ~round;
+            if (in) sh->boff[lane] = pre_box - need;
+            // item counts of the three phases
+            int n_ph[3] = {0, 0, 0};
+            if (in) {
+                const TetGeo<R>& G = sh->geo[lane];
+                n_ph[0] = 4;
+                n_ph[1] = sh->xcum[lane][17];
+                n_ph[2] = G.hi[1] * G.hi[2] + G.hi[0] * G.hi[2] + G.hi[0] * G.hi[1];
+            }
+            __syncwarp();
+            unsigned head = 0, tail = 0, ahead = 0, atail = 0;
+#pragma unroll 1
+            for (int ph = 0; ph < 3; ++ph) {
+                const int mine = ph == 0 ? n_ph[0] : (ph == 1 ? n_ph[1] : n_ph[2]);
+                const int pre = inclusive_scan(mine, lane);
+                const int tot = __shfl_sync(FULL, pre, 31);
+#pragma unroll 1
+                for (int u0 = 0; u0 < tot; u0 += 32) {
+                    const int u = u0 + lane;
+                    const int own = owner_lane(pre, u);
+                    const int before = __shfl_sync(FULL, pre - mine, own);
+                    Rec r0 = 0, r1 = 0;
+                    unsigned long long arun = 0;
+                    int nr = 0;
+                    if (u < tot) {
+                        const int t = u - before;
+                        if (ph == 0) {
+                            item_vertex(sh, own, t);
+                            cnt.b++;
+                        } else if (ph == 1) {
+                            r0 = item_crossing(sh, own, t, pc);
+                            nr = r0 != 0 ? 1 : 0;
+                        } else {
+                            nr = item_line(sh, own, t, r0, r1, arun, pc);
+                        }
+                    }
+                    // append the located corners to the queues (warp-aggregated, no atomics)
+                    const Rec ob = (Rec)own << 40;
+                    const unsigned b0 = __ballot_sync(FULL, nr >= 1), b1 = __ballot_sync(FULL, nr >= 2);
+                    const unsigned off = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
+                    if (nr >= 1) sh->q[(tail + off) & (TB_QCAP - 1)] = r0 | ob;
+                    if (nr >= 2) sh->q[(tail + off + 1) & (TB_QCAP - 1)] = r1 | ob;
+                    tail += __popc(b0) + __popc(b1);
+                    const unsigned ba = __ballot_sync(FULL, arun != 0);
+                    if (arun) sh->aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] = arun | ((unsigned long long)own << 44);
+                    atail += __popc(ba);
+                    __syncwarp();
+                    // evaluate full batches (and, after the phase's last items, what is left)
+                    const bool last = u0 + 32 >= tot;
+#pragma unroll 1
+                    for (;;) {
+                        const unsigned avail = tail - head;
+                        if (avail == 0u || (!last && avail < 32u)) break;
+                        if ((unsigned)lane < avail) eval_CD(sh, sh->q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
+                        head += avail < 32u ? avail : 32u;
+                    }
+#pragma unroll 1
+                    for (;;) {
+                        const unsigned avail = atail - ahead;
+                        if (avail == 0u || (!last && avail < 32u)) break;
+                        if ((unsigned)lane < avail) eval_A(sh, sh->aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
+                        ahead += avail < 32u ? avail : 32u;
+                    }
+                    __syncwarp();
+                }
+            }
+            // ---- flush every box of the round: one FP64 atomic per non-zero piece (FP32 path:
+            // with its share of the tetrahedron's mass-closure residual)
+            unsigned todo = round;
+#pragma unroll 1
+            while (todo) {
+                const int own = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const TetGeo<R>& G = sh->geo[own];
+                const int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
+                const int size = ex * ey * (G.hi[2] + 1);
+                R* box = sh->box + sh->boff[own];
+                double scale = 0.0;
+                if (fp32) {
+                    double sum = 0.0;
+                    float asum = 0.f;
+                    for (int e = lane; e < size; e += 32) {
+                        const R v = box[e];
+                        sum += (double)v;
+                        asum += fabsf((float)v);
+                    }
+                    sum = warp_sum(sum);
+                    asum = warp_sumf(asum);
+                    const double resid = G.mexact - sum;
+                    if (asum > 0.f) {
+                        scale = resid / (double)asum;
+                    } else if (lane == 0) {
+                        const long long idx = flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1],
+                                                        G.anchor[2] + G.cell[0][2]);
+                        if (idx >= 0) atomicAdd(out + idx, resid);
+                    }
+                }
+                const float inv_ex = 1.0f / (float)ex, inv_ey = 1.0f / (float)ey;
+                for (int e = lane; e < size; e += 32) {
+                    const R v = box[e];
+                    if (v == R(0)) continue;
+                    box[e] = R(0);
+                    // e = x + ex (y + ey z)
+                    int r = (int)((float)e * inv_ex);
+                    r += (r + 1) * ex <= e ? 1 : 0;
+                    r -= r * ex > e ? 1 : 0;
+                    const int x = e - r * ex;
+                    int z = (int)((float)r * inv_ey);
+                    z += (z + 1) * ey <= r ? 1 : 0;
+                    z -= z * ey > r ? 1 : 0;
+                    const int y = r - z * ey;
+                    bool ok = true;
+                    const int cx = wrap_axis(G.anchor[0] + x, g.n[0], g.periodic, ok);
+                    const int cy = wrap_axis(G.anchor[1] + y, g.n[1], g.periodic, ok);
+                    const int cz = wrap_axis(G.anchor[2] + z, g.n[2], g.periodic, ok);
+                    if (!ok) continue;
+                    double dv = (double)v;
+                    if (fp32) dv += scale * (double)fabsf((float)v);
+                    atomicAdd(out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz, dv);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (stats) {
+        if (cnt.a) atomicAdd(&stats->a, cnt.a);
+        if (cnt.b) atomicAdd(&stats->b, cnt.b);
+        if (cnt.c) atomicAdd(&stats->c, cnt.c);
+        if (cnt.d) atomicAdd(&stats->d, cnt.d);
+        if (xcnt.exact) atomicAdd(&stats->exact, xcnt.exact);
+        if (n0) atomicAdd(&ctr->n_class0, n0);
+        if (nact) atomicAdd(&ctr->n_small, nact);
+        if (nzero) atomicAdd(&ctr->n_zero, nzero);
+    }
+}
+
+template <typename R>
+static size_t tet_shared_bytes() {
+    return sizeof(TetShared<R>) * (CDP_WBLOCK / 32);
+}
+
+cudaError_t configure_tet() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_project_tet<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tet_shared_bytes<float>())))
+        return e;
+    return cudaFuncSetAttribute(k_project_tet<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tet_shared_bytes<double>());
+}
+
+int resident_blocks_tet(int fp32) {
+    int n = 0;
+    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<float>, CDP_WBLOCK,
+                                                                         tet_shared_bytes<float>())
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<double>, CDP_WBLOCK,
+                                                                         tet_shared_bytes<double>());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st) {
+    const long long chunks = (L.ns + TB_CHUNK - 1) / TB_CHUNK;
+    long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
+    const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (fp32)
+        k_project_tet<float><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<float>(), st>>>(
+            L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, L.big_list, L.big_cap);
+    else
+        k_project_tet<double><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<double>(), st>>>(
+            L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, L.big_list, L.big_cap);
+    return cudaGetLastError();
+}
+
+}  // namespace cdp

@@ -297,9 +297,10 @@ def run_ours(a):
         return
     # roofline of the dominant kernel (the tetrahedron projection kernel); its incidences are all
     # corners but those of the FP64 large-simplex pass
-    names = ["k_prep_vertices", "k_project_tet<float>", "k_project_warp<3,double> (large-simplex pass)"]
-    dom = int(np.argmax(kern32[:2]))
-    if dom == 1:
+    names = ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>",
+             "k_project_warp<3,double> (large-simplex pass)"]
+    dom = int(np.argmax(kern32[:3]))
+    if dom == 2:
         inc = {k: st32["corners_" + k] - st32["large_corners"][i] for i, k in enumerate("abcd")}
     else:
         inc = None
@@ -331,7 +332,7 @@ def run_ours(a):
                                          "n_small", "n_large", "n_zero_volume", "exact_fallbacks")},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 3 * a.steps,  # vertex records, main kernel, large-simplex pass
+        "gpu_launches": 4 * a.steps,  # vertex records, set-up, main kernel, large-simplex pass
         "e2e": e2e,
     }
     if ws == 1 and not a.no_cpu_baseline:

@@ -212,10 +212,11 @@ CDP_API int cdp_check(cdp_ctx* ctx, void* stream);
  * times to per-kernel totals; enabling (or disabling) also resets the totals and the call count. */
 CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 
-/* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1]:
- * [0] vertex preparation, [1] one-thread simplices (and the single-cell closed form), [2] tiled
- * large simplices.  *calls receives the number of timed cdp_project calls.  Returns the number
- * of slots written. */
+/* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 4:
+ * [0] vertex records, [1] per-simplex set-up (3D: the first batch's; the single-cell closed form
+ * is applied there), [2] main projection kernel (3D: with the set-up of any later batch),
+ * [3] FP64 large-simplex pass (3D).  *calls receives the number of timed cdp_project calls.
+ * Returns the number of slots written. */
 CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
 
 /* Human-readable name of a return code (static string). */

@@ -172,10 +172,10 @@ def cdp_timing_enable(ctx, enable: bool) -> int:
 
 
 def cdp_timing_read(ctx):
-    """(per-kernel totals in ms [prep, one-thread, tiled], number of timed calls)."""
-    buf = (ctypes.c_double * 3)()
+    """(per-kernel totals in ms [vertex records, set-up, main kernel, large-simplex pass], timed calls)."""
+    buf = (ctypes.c_double * 4)()
     calls = ctypes.c_int(0)
-    rc = load_library().cdp_timing_read(ctx, buf, 3, ctypes.byref(calls))
+    rc = load_library().cdp_timing_read(ctx, buf, 4, ctypes.byref(calls))
     if rc < 0:
         raise CdpError(rc, "cdp_timing_read")
     return list(buf), int(calls.value)

@@ -86,15 +86,16 @@ cudaEvent_t take_event(cdp_ctx* c) {
     return e;
 }
 
-// fold the recorded event quadruples into the totals (synchronises on them)
+// fold the recorded event groups into the totals (synchronises on them)
 int fold_timing(cdp_ctx* c) {
     std::vector<cudaEvent_t>& p = *c->pending;
-    for (size_t i = 0; i + 3 < p.size(); i += 4) {
-        if (cudaEventSynchronize(p[i + 3]) != cudaSuccess) {
+    constexpr int T = cdp::CDP_TEV;
+    for (size_t i = 0; i + T - 1 < p.size(); i += T) {
+        if (cudaEventSynchronize(p[i + T - 1]) != cudaSuccess) {
             cudaGetLastError();
             return CDP_ERR_CUDA;
         }
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < T - 1; ++k) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, p[i + k], p[i + k + 1]) == cudaSuccess) c->totals[k] += ms;
             cudaGetLastError();
@@ -104,6 +105,19 @@ int fold_timing(cdp_ctx* c) {
     for (cudaEvent_t e : p) c->pool->push_back(e);
     p.clear();
     return CDP_OK;
+}
+
+// largest batch of tetrahedra whose geometry records are held at once
+constexpr size_t kGeoBatch = (size_t)1 << 24;
+
+// geometry records and box sizes for min(ns, kGeoBatch) tetrahedra (both precisions)
+int grow_geo(cdp_ctx* c, size_t ns) {
+    size_t n = ns < kGeoBatch ? ns : kGeoBatch;
+    if (n < 1) n = 1;
+    size_t rec = cdp::tet_geo_bytes(0) > cdp::tet_geo_bytes(1) ? cdp::tet_geo_bytes(0) : cdp::tet_geo_bytes(1);
+    int rc = grow(&c->geo, &c->geo_cap, n * rec);
+    if (rc) return rc;
+    return grow(&c->need, &c->need_cap, n);
 }
 
 }  // namespace
@@ -123,14 +137,16 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
     }
     int rc = grow(&c->verts, &c->verts_cap, nv);
     if (rc) return rc;
-    return grow(&c->queue, &c->queue_cap, ns);
+    if ((rc = grow(&c->queue, &c->queue_cap, ns))) return rc;
+    return grow_geo(c, ns);
 }
 
 // enqueue one projection on `st` (arguments already checked)
 int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats) {
     int rc;
     if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
-    if (p->dim == 3 && (rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1))))
+    if (p->dim == 3 && ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1))) ||
+                        (rc = grow_geo(c, (size_t)p->n_simplices))))
         return rc;
 
     LaunchArgs L;
@@ -167,6 +183,13 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     L.big_blocks_per_sm = c->blocks_large;
     L.big_list = c->queue;
     L.big_cap = (long long)c->queue_cap;
+    L.geo = c->geo;
+    L.need = c->need;
+    {
+        size_t rec = cdp::tet_geo_bytes(fp32);
+        long long by_bytes = rec ? (long long)(c->geo_cap / rec) : 0;
+        L.geo_cap = by_bytes < (long long)c->need_cap ? by_bytes : (long long)c->need_cap;
+    }
 
     // zero the per-call counters (the sticky error word at offset 0 is kept)
     if (cudaMemsetAsync((char*)c->ctr + sizeof(unsigned), 0, sizeof(Counters) - sizeof(unsigned), st) !=
@@ -175,12 +198,14 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     if (want_stats && cudaMemsetAsync(c->stats, 0, 2 * sizeof(UnitCounts), st) != cudaSuccess) return CDP_ERR_CUDA;
     if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
         return CDP_ERR_CUDA;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    constexpr int T = CDP_TEV;
+    cudaEvent_t ev[T] = {};
     if (c->timing) {
         if (c->pending->size() >= 4096) fold_timing(c);
-        for (int k = 0; k < 4; ++k) ev[k] = take_event(c);
-        if (!ev[0] || !ev[1] || !ev[2] || !ev[3]) {
-            for (int k = 0; k < 4; ++k)
+        bool ok = true;
+        for (int k = 0; k < T; ++k) ok = (ev[k] = take_event(c)) != nullptr && ok;
+        if (!ok) {
+            for (int k = 0; k < T; ++k)
                 if (ev[k]) c->pool->push_back(ev[k]);
             return CDP_ERR_CUDA;
         }
@@ -191,13 +216,13 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
         return CDP_ERR_CUDA;
     }
     if (ev[1]) cudaEventRecord(ev[1], st);
-    if (launch_project(L, fp32, st, ev[2]) != cudaSuccess) {
+    if (launch_project(L, fp32, st, ev[2], ev[3]) != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;
     }
-    if (ev[3]) {
-        cudaEventRecord(ev[3], st);
-        for (int k = 0; k < 4; ++k) c->pending->push_back(ev[k]);
+    if (ev[T - 1]) {
+        cudaEventRecord(ev[T - 1], st);
+        for (int k = 0; k < T; ++k) c->pending->push_back(ev[k]);
     }
     return CDP_OK;
 }
@@ -245,7 +270,7 @@ int cdp_timing_enable(cdp_ctx* c, int enable) {
     DeviceGuard guard(c->device);
     int rc = fold_timing(c);
     c->timing = enable ? 1 : 0;
-    c->totals[0] = c->totals[1] = c->totals[2] = 0.0;
+    for (int k = 0; k < 4; ++k) c->totals[k] = 0.0;
     c->calls = 0;
     return rc;
 }
@@ -255,7 +280,7 @@ int cdp_timing_read(cdp_ctx* c, double* out_ms, int n, int* calls) {
     DeviceGuard guard(c->device);
     int rc = fold_timing(c);
     if (rc) return rc;
-    int m = n < 3 ? n : 3;
+    int m = n < 4 ? n : 4;
     for (int k = 0; k < m; ++k) out_ms[k] = c->totals[k];
     if (calls) *calls = c->calls;
     return m;
@@ -332,6 +357,8 @@ void cdp_destroy(cdp_ctx* c) {
     cudaDeviceSynchronize();
     if (c->verts) cudaFree(c->verts);
     if (c->queue) cudaFree(c->queue);
+    if (c->geo) cudaFree(c->geo);
+    if (c->need) cudaFree(c->need);
     if (c->ctr) cudaFree(c->ctr);
     if (c->stats) cudaFree(c->stats);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);

@@ -25,6 +25,7 @@ struct cdp_ctx;
 struct cdp_problem_tag;
 
 namespace cdp {
+constexpr int CDP_TEV = 5;
 void solver_release(cdp_ctx* c);
 void step_release(cdp_ctx* c);
 }  // namespace cdp
@@ -39,16 +40,21 @@ struct cdp_ctx {
     size_t verts_cap;
     int* queue;           // list of the tetrahedra for the large-simplex pass
     size_t queue_cap;
+    unsigned char* geo;   // geometry records of one batch of tetrahedra (bytes)
+    size_t geo_cap;
+    int* need;            // their box sizes
+    size_t need_cap;
     cdp::Counters* ctr;       // device
     cdp::UnitCounts* stats;   // device
     cdp::Counters* h_ctr;     // pinned host mirrors
     cdp::UnitCounts* h_stats;
-    // per-kernel timing: 4 events per timed call (before prep, after prep, after the one-thread
-    // kernel, after the tiled kernel), folded into totals when read
+    // per-kernel timing: CDP_TEV events per timed call (before the vertex records, after them,
+    // after the set-up kernel, after the main kernel, after the large-simplex pass), folded into
+    // totals[CDP_TEV - 1] when read
     int timing;
     std::vector<cudaEvent_t>* pending;
     std::vector<cudaEvent_t>* pool;
-    double totals[3];
+    double totals[4];
     int calls;
     // solver scratch
     std::vector<cdp::FftPlan>* plans;

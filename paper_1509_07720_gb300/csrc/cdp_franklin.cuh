@@ -346,6 +346,7 @@ CDP_HD void piece_origin(const TetGeo<R>& G, int v0, int v1, int v2, R O[3]) {
 template <typename R>
 CDP_COLD R tet_corner_B(const TetGeo<R>& G, int i, const R P[3]) {
     R s = 0;
+#pragma unroll 1
     for (int j = 0; j < 4; ++j) {
         if (j == i) continue;
         int a = i < j ? i : j, b = i < j ? j : i;
@@ -568,6 +569,7 @@ CDP_HD int tet_lines(const TetGeo<R>& G, int l, const int td[3], int& dj0, int& 
 template <typename R>
 CDP_HD unsigned tet_line_signs(const TetGeo<R>& G, int j, int k, int dj, int dk, UnitCounts* cnt) {
     unsigned m = 0;
+#pragma unroll 1
     for (int e = 0; e < 6; ++e) {
         int a, b, p, q;
         tet_edge(e, a, b, p, q);
@@ -677,9 +679,9 @@ CDP_HD R facet_face_terms(const R n[3], int k, R su, R sigma, const R P[3], R Pn
 }
 
 // D corner (facet f pierced by the grid line along l at (dj, dk), in cell column m): the values
-// of the 4 cells (oj, ok) = (0,0), (0,1), (1,0), (1,1) and their cells
-template <typename R>
-CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m, R val[4], int cell[4][3]) {
+// of the 4 cells (oj, ok) = (0,0), (0,1), (1,0), (1,1), passed to acc(cell, value)
+template <typename R, class Acc>
+CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m, Acc& acc) {
     int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
     int va = f == 0 ? 1 : 0;
     const R n[3] = {G.n[f][0], G.n[f][1], G.n[f][2]};
@@ -693,16 +695,13 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
     R irj2 = R(1) / (nk * nk + nl * nl), irk2 = R(1) / (nj * nj + nl * nl);
     R gj = pick3(g[0], g[1], g[2], j), gk = pick3(g[0], g[1], g[2], k), gl = pick3(g[0], g[1], g[2], l);
     R xl_ = G.x[va][l], xll = G.xl[va][l] + off;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < 4; ++q) {
         int oj = q >> 1, ok = q & 1;
         int vj = dj - 1 + oj, vk = dk - 1 + ok;
         int v0 = l == 0 ? m : vj;
         int v1 = l == 1 ? m : (l == 0 ? vj : vk);
         int v2 = l == 2 ? m : vk;
-        cell[q][0] = v0;
-        cell[q][1] = v1;
-        cell[q][2] = v2;
         R O[3];
         piece_origin(G, v0, v1, v2, O);
         R Pl = (xl_ - pick3(O[0], O[1], O[2], l)) + xll;
@@ -715,13 +714,14 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
         // facet/face_j line oriented towards the k side (sign sk eps tau), facet/face_k towards j
         R s34 = facet_face_terms(n, j, sk * eps * tau, sj, P, Pn, gn, hj, irj2, rhoX, g);
         R s56 = facet_face_terms(n, k, -sj * eps * tau, sk, P, Pn, gn, hk, irk2, rhoX, g);
-        val[q] = R(-1.0 / 6.0) * (s12 + s34 + s56);
+        acc(v0, v1, v2, R(-1.0 / 6.0) * (s12 + s34 + s56));
     }
 }
 
-// C corner (edge e crossing the plane x_k = c): the values of the 2 cells (below, above) and cells
-template <typename R>
-CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj2, R val[2], int cell[2][3]) {
+// C corner (edge e crossing the plane x_k = c): the values of the 2 cells (below, above), passed to
+// acc(cell, value)
+template <typename R, class Acc>
+CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj2, Acc& acc) {
     int a, b, p, q;
     tet_edge(e, a, b, p, q);
     int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
@@ -758,15 +758,12 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
     }
     R lam = R(-parity4(a, b, p, q)) * R(dirk);
     R d[3] = {t * ev[0], t * ev[1], t * ev[2]};
-#pragma unroll
+#pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         int vk = side ? c : c - 1;
         int v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
         int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
         int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
-        cell[side][0] = v0;
-        cell[side][1] = v1;
-        cell[side][2] = v2;
         R O[3], P[3];
         piece_origin(G, v0, v1, v2, O);
         for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + d[w]);
@@ -783,7 +780,7 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
                  Pmq * Pnq * (rhoX - R(0.75) * Pe * ge - R(0.5) * Pmq * gmq - R(0.25) * Pnq * gnq));
         R s34 = facet_face_terms(np_, k, lam, sigma, P, Pnp, gnp, hp, irp2, rhoX, g);
         R s56 = facet_face_terms(nq_, k, -lam, sigma, P, Pnq, gnq, hq, irq2, rhoX, g);
-        val[side] = R(-1.0 / 6.0) * (s12 + s34 + s56);
+        acc(v0, v1, v2, R(-1.0 / 6.0) * (s12 + s34 + s56));
     }
 }
 

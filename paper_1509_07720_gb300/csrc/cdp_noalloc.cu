@@ -1,6 +1,6 @@
 // Projection entry point that allocates nothing (declared in include/coldproj.h as
-// cdp_project_noalloc).  Its scratch (the per-call counters, the vertex records and the list of
-// the large-simplex pass) is one
+// cdp_project_noalloc).  Its scratch (the per-call counters, the vertex records, the list of the
+// large-simplex pass and the geometry records of one batch of tetrahedra) is one
 // statically sized device array of this module instead of context-owned memory; the kernels are
 // the ones cdp_project launches.
 #include <cuda_runtime.h>
@@ -20,11 +20,17 @@ namespace {
 constexpr long long kMaxVerts = CDP_NOALLOC_MAX_VERTS;
 constexpr long long kMaxSimplices = CDP_NOALLOC_MAX_SIMPLICES;
 constexpr size_t kCounterBytes = 256;  // the counters, padded so that the records stay 256-aligned
+constexpr long long kGeoBatch = 16384;  // tetrahedra set up per batch
+constexpr size_t kGeoRec = sizeof(cdp::TetGeo<double>) > sizeof(cdp::TetGeo<float>) ? sizeof(cdp::TetGeo<double>)
+                                                                                     : sizeof(cdp::TetGeo<float>);
 constexpr size_t kListOffset = kCounterBytes + (size_t)kMaxVerts * sizeof(cdp::VertexRec);
-constexpr size_t kScratchBytes = kListOffset + (size_t)kMaxSimplices * sizeof(int);
+constexpr size_t kNeedOffset = kListOffset + (size_t)kMaxSimplices * sizeof(int);
+constexpr size_t kGeoOffset = (kNeedOffset + (size_t)kGeoBatch * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kGeoOffset + (size_t)kGeoBatch * kGeoRec;
 static_assert(sizeof(cdp::Counters) <= kCounterBytes, "counters do not fit their slot");
 
-// [counters | vertex records | large-simplex list]; shared by every call on the device
+// [counters | vertex records | large-simplex list | box sizes | geometry records of one batch];
+// shared by every call on the device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -118,13 +124,16 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     L.big_blocks_per_sm = s->blocks_large;
     L.big_list = (int*)(s->scratch + kListOffset);
     L.big_cap = kMaxSimplices;
+    L.need = (int*)(s->scratch + kNeedOffset);
+    L.geo = s->scratch + kGeoOffset;
+    L.geo_cap = kGeoBatch;
 
     // every counter, the error word included, starts at zero on each call
     if (cudaMemsetAsync(s->scratch, 0, sizeof(cdp::Counters), st) != cudaSuccess) return CDP_ERR_CUDA;
     if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
         return CDP_ERR_CUDA;
     if (cdp::launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess ||
-        cdp::launch_project(L, fp32, st, nullptr) != cudaSuccess) {
+        cdp::launch_project(L, fp32, st, nullptr, nullptr) != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;
     }

@@ -324,20 +324,12 @@ __device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned lon
         if (ph == 1) {
             int e, k, c, cj1, cj2;
             decode_C(r, e, k, c, cj1, cj2);
-            R v[2];
-            int cl[2][3];
-            tet_eval_C2(G, e, k, c, cj1, cj2, v, cl);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) acc(cl[q][0], cl[q][1], cl[q][2], v[q]);
+            tet_eval_C2(G, e, k, c, cj1, cj2, acc);
             if (cnt) cnt->c += 2;
         } else {
             int f, l, dj, dk, m;
             decode_D(r, f, l, dj, dk, m);
-            R v[4];
-            int cl[4][3];
-            tet_eval_D4(G, f, l, dj, dk, m, v, cl);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc(cl[q][0], cl[q][1], cl[q][2], v[q]);
+            tet_eval_D4(G, f, l, dj, dk, m, acc);
             if (cnt) cnt->d += 4;
         }
     } else {
@@ -610,17 +602,20 @@ cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py,
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t mid) {
+cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,
+                           cudaEvent_t mid) {
     if (L.ns == 0) {
+        if (after_setup) cudaEventRecord(after_setup, st);
         if (mid) cudaEventRecord(mid, st);
         return cudaSuccess;
     }
     if (L.g.dim == 3) {
-        cudaError_t e = launch_tet(L, fp32, st);
+        cudaError_t e = launch_tet(L, fp32, st, after_setup);
         if (e != cudaSuccess) return e;
         if (mid) cudaEventRecord(mid, st);
         return launch_large(L, st);
     }
+    if (after_setup) cudaEventRecord(after_setup, st);
     return fp32 ? launch_dim<2, float>(L, st, mid) : launch_dim<2, double>(L, st, mid);
 }
 

@@ -37,6 +37,9 @@ struct LaunchArgs {
     int big_blocks_per_sm;
     int* big_list;      // tetrahedra whose bounding box exceeds the shared box (capacity big_cap)
     long long big_cap;
+    void* geo;          // geometry records of one batch of tetrahedra (capacity geo_cap records)
+    int* need;          // their box sizes (geo_cap entries)
+    long long geo_cap;
 };
 
 cudaError_t configure_all();
@@ -47,10 +50,16 @@ int resident_blocks_large();
 // the tetrahedron kernel (cdp_tetproj.cu)
 cudaError_t configure_tet();
 int resident_blocks_tet(int fp32);
-cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st);
+// bytes of one geometry record of the tetrahedron kernel
+size_t tet_geo_bytes(int fp32);
+// set-up and main kernel over batches of geo_cap tetrahedra; `after_setup` (optional) is recorded
+// after the first batch's set-up kernel
+cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup);
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
                         const double* rho, cudaStream_t st);
-// `mid` (optional) is recorded between the main kernel and the large-simplex pass
-cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t mid);
+// `after_setup` and `mid` (optional) are recorded after the (first) set-up kernel and between the
+// main kernel and the large-simplex pass
+cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,
+                           cudaEvent_t mid);
 
 }  // namespace cdp

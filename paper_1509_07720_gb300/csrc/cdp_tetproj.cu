@@ -162,23 +162,16 @@ template <typename R>
 __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, UnitCounts& cnt) {
     const int own = (int)((r >> 40) & 15);
     const TetGeo<R>& G = sh->geo[own];
+    auto acc = [&](int x, int y, int z, R v) { box_add(sh, own, x, y, z, v); };
     if (is_c) {
         int e, k, c, cj1, cj2;
         decode_C(r, e, k, c, cj1, cj2);
-        R v[2];
-        int cl[2][3];
-        tet_eval_C2(G, e, k, c, cj1, cj2, v, cl);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) box_add(sh, own, cl[q][0], cl[q][1], cl[q][2], v[q]);
+        tet_eval_C2(G, e, k, c, cj1, cj2, acc);
         cnt.c += 2;
     } else {
         int f, l, dj, dk, m;
         decode_D(r, f, l, dj, dk, m);
-        R v[4];
-        int cl[4][3];
-        tet_eval_D4(G, f, l, dj, dk, m, v, cl);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) box_add(sh, own, cl[q][0], cl[q][1], cl[q][2], v[q]);
+        tet_eval_D4(G, f, l, dj, dk, m, acc);
         cnt.d += 4;
     }
 }
@@ -192,7 +185,7 @@ __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, U
     const TetGeo<R>& G = sh->geo[own];
 #pragma unroll 1
     for (int cx = cx0; cx <= cx1; ++cx) {
-#pragma unroll
+#pragma unroll 1
         for (int o = 0; o < 8; ++o) {
             const int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
             R O[3];
@@ -255,11 +248,73 @@ __device__ __forceinline__ int inclusive_scan(int v, int lane) {
 
 }  // namespace
 
+// One thread per tetrahedron of the batch [s0, s0 + nb): canonicalise it (exact orientation, periodic
+// unwrap, cells), deposit a tetrahedron inside one cell at once (Algorithm 2, step 1), list one
+// whose bounding box exceeds the shared box for the large-simplex pass, and write the geometry of
+// every other one to geo[i] with need[i] = its bounding-box cell count (0: nothing more to do).
+template <typename R>
+__global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, long long nb, long long nv,
+                                                   const int* __restrict__ simp, const VertexRec* __restrict__ V,
+                                                   double* __restrict__ out, Counters* __restrict__ ctr,
+                                                   TetGeo<R>* __restrict__ geo, int* __restrict__ need,
+                                                   int* __restrict__ big_list, long long big_cap, int count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int n_zero = 0, n_single = 0, n_box = 0;
+    if (i < nb) {
+        const long long s = s0 + i;
+        int my_need = 0;
+        const VertexRec* v[4];
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) {
+            const int id = __ldg(simp + s * 4 + k);
+            if (id < 0 || id >= nv) ok = false;
+            v[k] = V + (ok ? id : 0);
+        }
+        if (!ok) {
+            atomicOr(&ctr->flags, CDP_FLAG_INDEX);
+        } else {
+            Tet S;
+            const unsigned rc = canon_tet(g, v, S);
+            if (rc == 1) {
+                n_zero = 1;
+            } else if (rc) {
+                atomicOr(&ctr->flags, rc);
+            } else if (S.lo[0] == S.hi[0] && S.lo[1] == S.hi[1] && S.lo[2] == S.hi[2]) {
+                const long long idx =
+                    flat_cell(g, S.anchor[0] + S.lo[0], S.anchor[1] + S.lo[1], S.anchor[2] + S.lo[2]);
+                if (idx >= 0) atomicAdd(out + idx, tet_mass_cells(S));
+                n_single = 1;
+            } else {
+                const long long cells =
+                    (long long)(S.hi[0] - S.lo[0] + 1) * (S.hi[1] - S.lo[1] + 1) * (S.hi[2] - S.lo[2] + 1);
+                if (cells > BoxCap<R>::value) {
+                    const unsigned at = atomicAdd(&ctr->big_count, 1u);
+                    if ((long long)at < big_cap) big_list[at] = (int)s;
+                } else {
+                    tet_setup(S, S.lo, geo[i]);
+                    my_need = (int)cells;
+                    n_box = 1;
+                }
+            }
+        }
+        need[i] = my_need;
+    }
+    if (count) {
+        n_zero = __reduce_add_sync(FULL, n_zero);
+        n_single = __reduce_add_sync(FULL, n_single);
+        n_box = __reduce_add_sync(FULL, n_box);
+        if ((threadIdx.x & 31) == 0) {
+            if (n_zero) atomicAdd(&ctr->n_zero, (unsigned long long)n_zero);
+            if (n_single) atomicAdd(&ctr->n_class0, (unsigned long long)n_single);
+            if (n_box) atomicAdd(&ctr->n_small, (unsigned long long)n_box);
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
-    k_project_tet(GridDesc g, long long ns, long long nv, const int* __restrict__ simp, const VertexRec* __restrict__ V,
-                  double* __restrict__ out, Counters* __restrict__ ctr, UnitCounts* __restrict__ stats,
-                  int* __restrict__ big_list, long long big_cap) {
+    k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
+                  double* __restrict__ out, UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
     constexpr int BOX = BoxCap<R>::value;
@@ -270,62 +325,37 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
     UnitCounts cnt = {0, 0, 0, 0, 0};     // corner counts (registers)
     UnitCounts xcnt = {0, 0, 0, 0, 0};    // exact-predicate count, updated through a pointer
     UnitCounts* pc = stats ? &xcnt : nullptr;
-    unsigned long long n0 = 0, nact = 0, nzero = 0;
-    const long long nchunks = (ns + TB_CHUNK - 1) / TB_CHUNK;
+    const long long nchunks = (nb + TB_CHUNK - 1) / TB_CHUNK;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const unsigned lt_mask = (1u << lane) - 1u;
 
     for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
          chunk += warps) {
-        // ---- set-up: one tetrahedron per lane
+        // ---- the chunk's geometry records (written by k_tet_setup) into shared memory
         const long long s = chunk * TB_CHUNK + lane;
-        int need = 0;  // box slots of this lane's tetrahedron (0: nothing more to do)
-        if (lane < TB_CHUNK && s < ns) {
-            const VertexRec* v[4];
-            bool ok = true;
-            for (int k = 0; k < 4; ++k) {
-                const int id = __ldg(simp + s * 4 + k);
-                if (id < 0 || id >= nv) ok = false;
-                v[k] = V + (ok ? id : 0);
-            }
-            if (!ok) {
-                atomicOr(&ctr->flags, CDP_FLAG_INDEX);
-            } else {
-                Tet S;
-                const unsigned rc = canon_tet(g, v, S);
-                if (rc == 1) {
-                    ++nzero;
-                } else if (rc) {
-                    atomicOr(&ctr->flags, rc);
-                } else if (S.lo[0] == S.hi[0] && S.lo[1] == S.hi[1] && S.lo[2] == S.hi[2]) {
-                    const long long idx =
-                        flat_cell(g, S.anchor[0] + S.lo[0], S.anchor[1] + S.lo[1], S.anchor[2] + S.lo[2]);
-                    if (idx >= 0) atomicAdd(out + idx, tet_mass_cells(S));
-                    ++n0;
-                } else {
-                    const long long cells = (long long)(S.hi[0] - S.lo[0] + 1) * (S.hi[1] - S.lo[1] + 1) *
-                                            (S.hi[2] - S.lo[2] + 1);
-                    if (cells > BOX) {
-                        // listed for the large-simplex pass
-                        const unsigned long long at = atomicAdd(&ctr->big_count, 1u);
-                        if ((long long)at < big_cap) big_list[at] = (int)s;
-                    } else {
-                        TetGeo<R>& G = sh->geo[lane];
-                        tet_setup(S, S.lo, G);
-                        need = (int)cells;
-                        int run = 0;
+        const int need = (lane < TB_CHUNK && s < nb) ? __ldg(need_in + s) : 0;
+        {
+            const long long first = chunk * TB_CHUNK;
+            const long long last = first + TB_CHUNK < nb ? first + TB_CHUNK : nb;
+            constexpr int W = sizeof(TetGeo<R>) / 8;
+            static_assert(sizeof(TetGeo<R>) % 8 == 0, "geometry records are copied in 8-byte words");
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(geo + first);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh->geo);
+            const int words = (int)(last - first) * W;
+            for (int w = lane; w < words; w += 32) dst[w] = __ldg(src + w);
+        }
+        __syncwarp();
+        if (need > 0) {
+            const TetGeo<R>& G = sh->geo[lane];
+            int run = 0;
 #pragma unroll 1
-                        for (int p = 0; p < 18; ++p) {
-                            const int e = p / 3, k = p - 3 * e;
-                            int a, b, pp, qq;
-                            tet_edge(e, a, b, pp, qq);
-                            const int d = G.cell[a][k] - G.cell[b][k];
-                            run += d < 0 ? -d : d;
-                            sh->xcum[lane][p] = (unsigned short)run;
-                        }
-                        ++nact;
-                    }
-                }
+            for (int p = 0; p < 18; ++p) {
+                const int e = p / 3, k = p - 3 * e;
+                int a, b, pp, qq;
+                tet_edge(e, a, b, pp, qq);
+                const int d = G.cell[a][k] - G.cell[b][k];
+                run += d < 0 ? -d : d;
+                sh->xcum[lane][p] = (unsigned short)run;
             }
         }
         __syncwarp();
@@ -467,9 +497,6 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
         if (cnt.c) atomicAdd(&stats->c, cnt.c);
         if (cnt.d) atomicAdd(&stats->d, cnt.d);
         if (xcnt.exact) atomicAdd(&stats->exact, xcnt.exact);
-        if (n0) atomicAdd(&ctr->n_class0, n0);
-        if (nact) atomicAdd(&ctr->n_small, nact);
-        if (nzero) atomicAdd(&ctr->n_zero, nzero);
     }
 }
 
@@ -500,19 +527,30 @@ int resident_blocks_tet(int fp32) {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st) {
-    const long long chunks = (L.ns + TB_CHUNK - 1) / TB_CHUNK;
-    long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
-    const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    if (fp32)
-        k_project_tet<float><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<float>(), st>>>(
-            L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, L.big_list, L.big_cap);
-    else
-        k_project_tet<double><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<double>(), st>>>(
-            L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, L.big_list, L.big_cap);
+size_t tet_geo_bytes(int fp32) { return fp32 ? sizeof(TetGeo<float>) : sizeof(TetGeo<double>); }
+
+template <typename R>
+static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_t after_setup) {
+    const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
+    for (long long s0 = 0; s0 < L.ns; s0 += batch) {
+        const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
+        k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(
+            L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, reinterpret_cast<TetGeo<R>*>(L.geo), L.need,
+            L.big_list, L.big_cap, L.stats != nullptr);
+        if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
+        const long long chunks = (nb + TB_CHUNK - 1) / TB_CHUNK;
+        long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
+        const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        k_project_tet<R><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<R>(), st>>>(
+            L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, L.stats);
+    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup) {
+    return fp32 ? launch_tet_r<float>(L, st, after_setup) : launch_tet_r<double>(L, st, after_setup);
 }
 
 }  // namespace cdp

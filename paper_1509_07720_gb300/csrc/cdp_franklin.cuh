@@ -70,6 +70,18 @@ CDP_HD double rsqrt_r<double>(double v) {
 #endif
 }
 
+// a / b where the quotient only seeds a guess that exact predicates then confirm or correct
+template <typename R>
+CDP_HD R div_guess(R a, R b) { return a / b; }
+template <>
+CDP_HD float div_guess<float>(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
 template <typename R>
 CDP_HD R floor_r(R v);
 template <>
@@ -160,7 +172,8 @@ struct TetGeo {
     int anchor[3];         // absolute cell of the tile origin
     signed char ns[4][3];  // signs of the exact normal components
     double mexact;         // |V| mean(rho) in FP64 (closed form, for the mass closure)
-    int pad_[2];           // odd multiple of 8 bytes: consecutive records start in different banks
+    float mexact_hi;       // (float)mexact
+    float mexact_lo;       // mexact - mexact_hi: mexact as an unevaluated sum of two floats
 };
 
 // exact inward normal of facet f (the facet opposite vertex f) of a positively oriented tetrahedron
@@ -222,6 +235,8 @@ CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
     double D = wide_to_double(dot3_wide(n3, e3), 3 * CDP_Q);
     R invD = R(1) / R(D);
     G.mexact = D * (1.0 / 6.0) * 0.25 * (S.rho[0] + S.rho[1] + S.rho[2] + S.rho[3]);
+    G.mexact_hi = (float)G.mexact;
+    G.mexact_lo = (float)(G.mexact - (double)G.mexact_hi);
     for (int a = 0; a < 3; ++a) G.anchor[a] = S.anchor[a] + T[a];
     for (int k = 0; k < 4; ++k) G.rho[k] = (R)S.rho[k];
     R d1 = G.rho[1] - G.rho[0], d2 = G.rho[2] - G.rho[0], d3 = G.rho[3] - G.rho[0];
@@ -246,6 +261,22 @@ CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
 // predicates with a floating-point filter and the exact fallback
 // ------------------------------------------------------------------------------------------
 
+// exact stages of the two predicates below (out of line: rarely reached, and kept out of the hot
+// loops' instruction footprint)
+template <typename R>
+CDP_COLD int tet_side2_exact(const TetGeo<R>& G, int i, int j, int u, int v, int pu, int pv) {
+    return side2_exact(G.Lt[i][u], G.Lt[i][v], G.Lt[j][u], G.Lt[j][v], (i64)pu << CDP_Q, (i64)pv << CDP_Q);
+}
+
+template <typename R>
+CDP_COLD int tet_side3_exact(const TetGeo<R>& G, int f, int g0, int g1, int g2) {
+    int a = f == 0 ? 1 : 0;
+    i64 gp[3] = {(i64)g0 << CDP_Q, (i64)g1 << CDP_Q, (i64)g2 << CDP_Q};
+    i128 nE[3];
+    facet_normal_exact(G.Lt, f, nE);
+    return side3_exact(nE, G.Lt[a], gp);
+}
+
 // perturbed orient2d of grid point (pu, pv) (integers, tile frame) against edge (i -> j) of the
 // projection on axes u < v
 template <typename R>
@@ -255,7 +286,7 @@ CDP_HD int tet_side2(const TetGeo<R>& G, int i, int j, int u, int v, int pu, int
     if (val > G.B2) return 1;
     if (val < -G.B2) return -1;
     if (cnt) cnt->exact++;
-    return side2_exact(G.Lt[i][u], G.Lt[i][v], G.Lt[j][u], G.Lt[j][v], (i64)pu << CDP_Q, (i64)pv << CDP_Q);
+    return tet_side2_exact(G, i, j, u, v, pu, pv);
 }
 
 // perturbed side of grid node (g0, g1, g2) (tile frame) w.r.t. facet f: > 0 inside
@@ -266,10 +297,7 @@ CDP_HD int tet_side3(const TetGeo<R>& G, int f, int g0, int g1, int g2, UnitCoun
     if (val > G.B3) return 1;
     if (val < -G.B3) return -1;
     if (cnt) cnt->exact++;
-    i64 gp[3] = {(i64)g0 << CDP_Q, (i64)g1 << CDP_Q, (i64)g2 << CDP_Q};
-    i128 nE[3];
-    facet_normal_exact(G.Lt, f, nE);
-    return side3_exact(nE, G.Lt[a], gp);
+    return tet_side3_exact(G, f, g0, g1, g2);
 }
 
 // sign(X_j - d) for the crossing X of edge (a -> b) with grid plane x_k = c (perturbed)
@@ -806,7 +834,7 @@ CDP_HD void tet_locate_crossing(const TetGeo<R>& G, int e, int k, int c, const i
     R ev[3];
     for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
     R evk = pick3(ev[0], ev[1], ev[2], k);
-    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    R t = div_guess(((R(c) - G.x[a][k]) - G.xl[a][k]), evk);
     R X1 = G.x[a][j1] + t * pick3(ev[0], ev[1], ev[2], j1);
     R X2 = G.x[a][j2] + t * pick3(ev[0], ev[1], ev[2], j2);
     int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X1), dirk, cnt);

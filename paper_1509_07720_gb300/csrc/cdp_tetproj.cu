@@ -133,8 +133,8 @@ __device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t,
         if (!((hits >> f) & 1u)) continue;
         const int va = f == 0 ? 1 : 0;
         const R fj = G.n[f][j], fk = G.n[f][k], fl = G.n[f][l];
-        const R off =
-            -(fj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + fk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / fl;
+        const R off = div_guess(
+            -(fj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + fk * ((R(dk) - G.x[va][k]) - G.xl[va][k])), fl);
         const int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(G.x[va][l] + off), cnt);
         if (G.ns[f][l] > 0)
             mlo = m;
@@ -158,7 +158,7 @@ __device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t,
 // evaluation of queued corners
 // ------------------------------------------------------------------------------------------
 
-template <typename R>
+template <typename R, bool STATS>
 __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, UnitCounts& cnt) {
     const int own = (int)((r >> 40) & 15);
     const TetGeo<R>& G = sh->geo[own];
@@ -167,17 +167,17 @@ __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, Unit
         int e, k, c, cj1, cj2;
         decode_C(r, e, k, c, cj1, cj2);
         tet_eval_C2(G, e, k, c, cj1, cj2, acc);
-        cnt.c += 2;
+        if (STATS) cnt.c += 2;
     } else {
         int f, l, dj, dk, m;
         decode_D(r, f, l, dj, dk, m);
         tet_eval_D4(G, f, l, dj, dk, m, acc);
-        cnt.d += 4;
+        if (STATS) cnt.d += 4;
     }
 }
 
 // a run of A nodes (grid nodes inside the tetrahedron on one x line): the 8 cells of each node
-template <typename R>
+template <typename R, bool STATS>
 __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, UnitCounts& cnt) {
     const int own = (int)((r >> 44) & 15);
     const int cx0 = (int)(r & 2047), cx1 = (int)((r >> 11) & 2047);
@@ -195,7 +195,7 @@ __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, U
             const R sg = R(((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1));
             box_add(sh, own, v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
         }
-        cnt.a += 8;
+        if (STATS) cnt.a += 8;
     }
 }
 
@@ -214,16 +214,13 @@ __device__ __forceinline__ int wrap_axis(int v, int n, int periodic, bool& ok) {
     return v;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float warp_sumf(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
+// (hi, lo) += v with the rounding error of hi + v kept in lo (Knuth's two-sum, FP32 only)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bv = s - hi;
+    const float err = (hi - (s - bv)) + (v - bv);
+    hi = s;
+    lo += err;
 }
 
 // owner lane of flat item u: the first lane whose inclusive prefix exceeds u
@@ -311,7 +308,7 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
     }
 }
 
-template <typename R>
+template <typename R, bool STATS>
 __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
     k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
                   double* __restrict__ out, UnitCounts* __restrict__ stats) {
@@ -324,7 +321,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
     __syncwarp();
     UnitCounts cnt = {0, 0, 0, 0, 0};     // corner counts (registers)
     UnitCounts xcnt = {0, 0, 0, 0, 0};    // exact-predicate count, updated through a pointer
-    UnitCounts* pc = stats ? &xcnt : nullptr;
+    UnitCounts* pc = STATS ? &xcnt : nullptr;
     const long long nchunks = (nb + TB_CHUNK - 1) / TB_CHUNK;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -395,7 +392,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                         const int t = u - before;
                         if (ph == 0) {
                             item_vertex(sh, own, t);
-                            cnt.b++;
+                            if (STATS) cnt.b++;
                         } else if (ph == 1) {
                             r0 = item_crossing(sh, own, t, pc);
                             nr = r0 != 0 ? 1 : 0;
@@ -420,14 +417,14 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                     for (;;) {
                         const unsigned avail = tail - head;
                         if (avail == 0u || (!last && avail < 32u)) break;
-                        if ((unsigned)lane < avail) eval_CD(sh, sh->q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
+                        if ((unsigned)lane < avail) eval_CD<R, STATS>(sh, sh->q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
                         head += avail < 32u ? avail : 32u;
                     }
 #pragma unroll 1
                     for (;;) {
                         const unsigned avail = atail - ahead;
                         if (avail == 0u || (!last && avail < 32u)) break;
-                        if ((unsigned)lane < avail) eval_A(sh, sh->aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
+                        if ((unsigned)lane < avail) eval_A<R, STATS>(sh, sh->aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
                         ahead += avail < 32u ? avail : 32u;
                     }
                     __syncwarp();
@@ -444,24 +441,30 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                 const int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
                 const int size = ex * ey * (G.hi[2] + 1);
                 R* box = sh->box + sh->boff[own];
-                double scale = 0.0;
+                float scale = 0.f;
                 if (fp32) {
-                    double sum = 0.0;
-                    float asum = 0.f;
+                    // the tetrahedron's FP32 pieces summed exactly enough (two-float accumulation,
+                    // FP32 arithmetic only) and the residual against its closed-form mass
+                    float hi = 0.f, lo = 0.f, asum = 0.f;
                     for (int e = lane; e < size; e += 32) {
-                        const R v = box[e];
-                        sum += (double)v;
-                        asum += fabsf((float)v);
+                        const float v = (float)box[e];
+                        two_sum_acc(hi, lo, v);
+                        asum += fabsf(v);
                     }
-                    sum = warp_sum(sum);
-                    asum = warp_sumf(asum);
-                    const double resid = G.mexact - sum;
+#pragma unroll 1
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float ohi = __shfl_xor_sync(FULL, hi, o), olo = __shfl_xor_sync(FULL, lo, o);
+                        lo += olo;
+                        two_sum_acc(hi, lo, ohi);
+                        asum += __shfl_xor_sync(FULL, asum, o);
+                    }
+                    const float resid = (G.mexact_hi - hi) + (G.mexact_lo - lo);
                     if (asum > 0.f) {
-                        scale = resid / (double)asum;
+                        scale = resid * __frcp_rn(asum);
                     } else if (lane == 0) {
                         const long long idx = flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1],
                                                         G.anchor[2] + G.cell[0][2]);
-                        if (idx >= 0) atomicAdd(out + idx, resid);
+                        if (idx >= 0) atomicAdd(out + idx, (double)resid);
                     }
                 }
                 const float inv_ex = 1.0f / (float)ex, inv_ey = 1.0f / (float)ey;
@@ -483,15 +486,16 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                     const int cy = wrap_axis(G.anchor[1] + y, g.n[1], g.periodic, ok);
                     const int cz = wrap_axis(G.anchor[2] + z, g.n[2], g.periodic, ok);
                     if (!ok) continue;
-                    double dv = (double)v;
-                    if (fp32) dv += scale * (double)fabsf((float)v);
-                    atomicAdd(out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz, dv);
+                    double* cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
+                    atomicAdd(cell, (double)v);
+                    // the piece's share of the closure residual (FP64 atomics are cheap here)
+                    if (fp32) atomicAdd(cell, (double)(scale * fabsf((float)v)));
                 }
             }
             __syncwarp();
         }
     }
-    if (stats) {
+    if (STATS) {
         if (cnt.a) atomicAdd(&stats->a, cnt.a);
         if (cnt.b) atomicAdd(&stats->b, cnt.b);
         if (cnt.c) atomicAdd(&stats->c, cnt.c);
@@ -505,21 +509,26 @@ static size_t tet_shared_bytes() {
     return sizeof(TetShared<R>) * (CDP_WBLOCK / 32);
 }
 
+template <typename R, bool STATS>
+static cudaError_t configure_one() {
+    return cudaFuncSetAttribute(k_project_tet<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tet_shared_bytes<R>());
+}
+
 cudaError_t configure_tet() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_project_tet<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tet_shared_bytes<float>())))
+    if ((e = configure_one<float, false>()) || (e = configure_one<float, true>()) ||
+        (e = configure_one<double, false>()))
         return e;
-    return cudaFuncSetAttribute(k_project_tet<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tet_shared_bytes<double>());
+    return configure_one<double, true>();
 }
 
 int resident_blocks_tet(int fp32) {
     int n = 0;
-    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<float>, CDP_WBLOCK,
-                                                                         tet_shared_bytes<float>())
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<double>, CDP_WBLOCK,
-                                                                         tet_shared_bytes<double>());
+    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<float, false>,
+                                                                         CDP_WBLOCK, tet_shared_bytes<float>())
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<double, false>,
+                                                                         CDP_WBLOCK, tet_shared_bytes<double>());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -543,8 +552,12 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
         const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        k_project_tet<R><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<R>(), st>>>(
-            L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, L.stats);
+        if (L.stats)
+            k_project_tet<R, true><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<R>(), st>>>(
+                L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, L.stats);
+        else
+            k_project_tet<R, false><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<R>(), st>>>(
+                L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, nullptr);
     }
     return cudaGetLastError();
 }

@@ -18,10 +18,10 @@
 // box of its tetrahedron.  At the end of the round each box is flushed with one FP64 global
 // atomic per non-zero (tetrahedron, cell) piece.
 //
-// FP32-mixed path only: the mass closure (not in the paper).  The FP64 closed-form mass of each
-// tetrahedron minus the FP64 sum of its FP32 pieces is spread over its pieces in proportion to
-// their magnitude, so the total mass is exact to FP64 rounding and no piece moves by more than
-// the FP32 rounding of the tetrahedron's own sum.
+// FP32-mixed path only: the mass closure (not in the paper).  The FP64 closed-form masses of the
+// tetrahedra of a round minus the (two-float, exact enough) sum of their FP32 pieces is spread over
+// those pieces in proportion to their magnitude, so the total mass is exact to FP64 rounding and
+// no piece moves by more than about the FP32 rounding of the pieces themselves.
 #include <cuda_runtime.h>
 
 #include "cdp_mesh.cuh"
@@ -430,8 +430,41 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                     __syncwarp();
                 }
             }
-            // ---- flush every box of the round: one FP64 atomic per non-zero piece (FP32 path:
-            // with its share of the tetrahedron's mass-closure residual)
+            // ---- flush every box of the round: one FP64 atomic per non-zero piece (FP32 path: and
+            // one more for its share of the round's mass-closure residual)
+            float scale = 0.f;
+            if (fp32) {
+                // FP32 pieces of the round minus the closed-form masses of its tetrahedra, summed as
+                // two floats (exact enough, FP32 arithmetic only); the residual is then spread over
+                // the pieces in proportion to their magnitude
+                const int used = __shfl_sync(FULL, pre_box, 31 - __clz(round));
+                float hi = 0.f, lo = 0.f, asum = 0.f;
+                if (in) {
+                    two_sum_acc(hi, lo, -sh->geo[lane].mexact_hi);
+                    lo -= sh->geo[lane].mexact_lo;
+                }
+                for (int e = lane; e < used; e += 32) {
+                    const float v = (float)sh->box[e];
+                    two_sum_acc(hi, lo, v);
+                    asum += fabsf(v);
+                }
+#pragma unroll 1
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ohi = __shfl_xor_sync(FULL, hi, o), olo = __shfl_xor_sync(FULL, lo, o);
+                    lo += olo;
+                    two_sum_acc(hi, lo, ohi);
+                    asum += __shfl_xor_sync(FULL, asum, o);
+                }
+                const float resid = -(hi + lo);
+                if (asum > 0.f) {
+                    scale = resid * __frcp_rn(asum);
+                } else if (lane == 0) {
+                    const TetGeo<R>& G = sh->geo[__ffs(round) - 1];
+                    const long long idx = flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1],
+                                                    G.anchor[2] + G.cell[0][2]);
+                    if (idx >= 0) atomicAdd(out + idx, (double)resid);
+                }
+            }
             unsigned todo = round;
 #pragma unroll 1
             while (todo) {
@@ -441,32 +474,6 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                 const int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
                 const int size = ex * ey * (G.hi[2] + 1);
                 R* box = sh->box + sh->boff[own];
-                float scale = 0.f;
-                if (fp32) {
-                    // the tetrahedron's FP32 pieces summed exactly enough (two-float accumulation,
-                    // FP32 arithmetic only) and the residual against its closed-form mass
-                    float hi = 0.f, lo = 0.f, asum = 0.f;
-                    for (int e = lane; e < size; e += 32) {
-                        const float v = (float)box[e];
-                        two_sum_acc(hi, lo, v);
-                        asum += fabsf(v);
-                    }
-#pragma unroll 1
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float ohi = __shfl_xor_sync(FULL, hi, o), olo = __shfl_xor_sync(FULL, lo, o);
-                        lo += olo;
-                        two_sum_acc(hi, lo, ohi);
-                        asum += __shfl_xor_sync(FULL, asum, o);
-                    }
-                    const float resid = (G.mexact_hi - hi) + (G.mexact_lo - lo);
-                    if (asum > 0.f) {
-                        scale = resid * __frcp_rn(asum);
-                    } else if (lane == 0) {
-                        const long long idx = flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1],
-                                                        G.anchor[2] + G.cell[0][2]);
-                        if (idx >= 0) atomicAdd(out + idx, (double)resid);
-                    }
-                }
                 const float inv_ex = 1.0f / (float)ex, inv_ey = 1.0f / (float)ey;
                 for (int e = lane; e < size; e += 32) {
                     const R v = box[e];

@@ -370,6 +370,31 @@ CDP_HD void piece_origin(const TetGeo<R>& G, int v0, int v1, int v2, R O[3]) {
     O[2] = clamp_r(G.c[2], R(v2) + R(0.25), R(v2) + R(0.75));
 }
 
+// The per-simplex values that every (corner, cell) evaluation reads (centroid, density there and
+// gradient), copied to registers once before a loop over cells.
+template <typename R>
+struct TetFrame {
+    R c[3], rhoc, g[3];
+};
+
+template <typename R>
+CDP_HD TetFrame<R> tet_frame(const TetGeo<R>& G) {
+    TetFrame<R> F;
+    for (int a = 0; a < 3; ++a) {
+        F.c[a] = G.c[a];
+        F.g[a] = G.g[a];
+    }
+    F.rhoc = G.rhoc;
+    return F;
+}
+
+template <typename R>
+CDP_HD void piece_origin(const TetFrame<R>& F, int v0, int v1, int v2, R O[3]) {
+    O[0] = clamp_r(F.c[0], R(v0) + R(0.25), R(v0) + R(0.75));
+    O[1] = clamp_r(F.c[1], R(v1) + R(0.25), R(v1) + R(0.75));
+    O[2] = clamp_r(F.c[2], R(v2) + R(0.25), R(v2) + R(0.75));
+}
+
 // B: simplex vertex i; P = x_i - O
 template <typename R>
 CDP_COLD R tet_corner_B(const TetGeo<R>& G, int i, const R P[3]) {
@@ -502,6 +527,17 @@ template <typename R>
 CDP_HD R rho_from_P(const TetGeo<R>& G, const R P[3], const R O[3]) {
     return G.rhoc + G.g[0] * (P[0] + (O[0] - G.c[0])) + G.g[1] * (P[1] + (O[1] - G.c[1])) +
            G.g[2] * (P[2] + (O[2] - G.c[2]));
+}
+
+template <typename R>
+CDP_HD R rho_from_P(const TetFrame<R>& F, const R P[3], const R O[3]) {
+    return F.rhoc + F.g[0] * (P[0] + (O[0] - F.c[0])) + F.g[1] * (P[1] + (O[1] - F.c[1])) +
+           F.g[2] * (P[2] + (O[2] - F.c[2]));
+}
+
+template <typename R>
+CDP_HD R tet_corner_A(const TetFrame<R>& F, const R P[3], R rhoX, R sgn) {
+    return sgn * P[0] * P[1] * P[2] * (rhoX - R(0.5) * dot3(F.g, P));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -723,6 +759,7 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
     R irj2 = R(1) / (nk * nk + nl * nl), irk2 = R(1) / (nj * nj + nl * nl);
     R gj = pick3(g[0], g[1], g[2], j), gk = pick3(g[0], g[1], g[2], k), gl = pick3(g[0], g[1], g[2], l);
     R xl_ = G.x[va][l], xll = G.xl[va][l] + off;
+    const TetFrame<R> F = tet_frame(G);
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
         int oj = q >> 1, ok = q & 1;
@@ -731,11 +768,11 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
         int v1 = l == 1 ? m : (l == 0 ? vj : vk);
         int v2 = l == 2 ? m : vk;
         R O[3];
-        piece_origin(G, v0, v1, v2, O);
+        piece_origin(F, v0, v1, v2, O);
         R Pl = (xl_ - pick3(O[0], O[1], O[2], l)) + xll;
         R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
         const R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
-        R rhoX = rho_from_P(G, P, O);
+        R rhoX = rho_from_P(F, P, O);
         R sj = oj ? R(1) : R(-1), sk = ok ? R(1) : R(-1);
         R Pn = dot3(P, n);
         R s12 = tau * sj * sk * Pj * Pk * Pl * (R(2) * rhoX - R(1.5) * Pl * gl - R(0.75) * (Pj * gj + Pk * gk));
@@ -785,7 +822,10 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
         irq2 = R(1) / (b0 * b0 + b1 * b1);
     }
     R lam = R(-parity4(a, b, p, q)) * R(dirk);
-    R d[3] = {t * ev[0], t * ev[1], t * ev[2]};
+    // the crossing point as vertex a (high part) plus a small offset
+    const R xa[3] = {G.x[a][0], G.x[a][1], G.x[a][2]};
+    const R dx[3] = {G.xl[a][0] + t * ev[0], G.xl[a][1] + t * ev[1], G.xl[a][2] + t * ev[2]};
+    const TetFrame<R> F = tet_frame(G);
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         int vk = side ? c : c - 1;
@@ -793,8 +833,8 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
         int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
         int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
         R O[3], P[3];
-        piece_origin(G, v0, v1, v2, O);
-        for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + d[w]);
+        piece_origin(F, v0, v1, v2, O);
+        for (int w = 0; w < 3; ++w) P[w] = (xa[w] - O[w]) + dx[w];
         R Pk = R(c) - pick3(O[0], O[1], O[2], k);
         P[0] = k == 0 ? Pk : P[0];
         P[1] = k == 1 ? Pk : P[1];

@@ -67,6 +67,147 @@ __device__ __forceinline__ void box_add(TetShared<R>* sh, int own, int x, int y,
 // items
 // ------------------------------------------------------------------------------------------
 
+// Facets pierced by a grid line, as a function of the signs of the 6 projected edges (the rule of
+// tet_pierced), packed 4 bits per sign mask into four 64-bit words at compile time.
+constexpr unsigned long long pierced_word(int w) {
+    unsigned long long v = 0;
+    for (int i = 0; i < 16; ++i) {
+        const unsigned sgn = (unsigned)(w * 16 + i);
+        unsigned hits = 0;
+        for (int f = 0; f < 4; ++f) {
+            const int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, c = f == 3 ? 2 : 3;
+            const int eab = a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+            const int ebc = b == 0 ? c - 1 : (b == 1 ? c + 1 : 5);
+            const int eac = a == 0 ? c - 1 : (a == 1 ? c + 1 : 5);
+            const unsigned sab = (sgn >> eab) & 1u, sbc = (sgn >> ebc) & 1u, sac = (sgn >> eac) & 1u;
+            if (sab == sbc && sbc != sac) hits |= 1u << f;
+        }
+        v |= (unsigned long long)hits << (4 * i);
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned pierced_lut(unsigned sgn) {
+    constexpr unsigned long long w0 = pierced_word(0), w1 = pierced_word(1), w2 = pierced_word(2),
+                                 w3 = pierced_word(3);
+    const unsigned hi = sgn >> 4;
+    const unsigned long long w = hi == 0 ? w0 : (hi == 1 ? w1 : (hi == 2 ? w2 : w3));
+    return (unsigned)(w >> ((sgn & 15u) * 4u)) & 15u;
+}
+
+// Exact stage of the crossing-side predicate: sign(X_j - d) (before the dirk orientation) for the
+// crossing X of edge a -> b with the grid plane x_k = c, with the argument order of tet_cross_side.
+template <typename R>
+CDP_COLD int cross_side_exact(const TetGeo<R>& G, int a, int b, int j, int k, int c, int d) {
+    return j < k ? tet_side2_exact(G, a, b, j, k, d, c) : -tet_side2_exact(G, a, b, k, j, c, d);
+}
+
+// Exact stage of the line signs: bit e of `amb` marks an edge whose filtered orient2d was not
+// conclusive; its exact sign replaces bit e of sgn.
+template <typename R>
+CDP_COLD unsigned line_signs_exact(const TetGeo<R>& G, int j, int k, int dj, int dk, unsigned sgn, unsigned amb) {
+    for (int e = 0; e < 6; ++e) {
+        if (!((amb >> e) & 1u)) continue;
+        int a, b, p, q;
+        tet_edge(e, a, b, p, q);
+        if (tet_side2_exact(G, a, b, j, k, dj, dk) > 0)
+            sgn |= 1u << e;
+        else
+            sgn &= ~(1u << e);
+    }
+    return sgn;
+}
+
+// Cell along axis j of the crossing of edge a -> b (coordinates in registers: xa_j, xa_k, xb_j, xb_k)
+// with the grid plane x_k = c: the d in [lo, hi] with the crossing above plane d and below plane
+// d + 1, found from `guess` by the exact-sign search of tet_cross_cell (one predicate per step).
+template <typename R>
+__device__ __forceinline__ int cross_cell_regs(const TetGeo<R>& G, int a, int b, int j, int k, int c, R xaj, R xak,
+                                               R xbj, R xbk, int lo, int hi, int guess, int dirk, R B2,
+                                               UnitCounts* cnt) {
+    int d = guess < lo ? lo : (guess > hi ? hi : guess);
+    const R du = xbj - xaj, dv = xbk - xak;
+    const R A = du * (R(c) - xak);
+    bool upper = false;  // false: checking plane d (want the crossing above it), true: plane d + 1
+#pragma unroll 1
+    for (int it = 0; it < 2 * (hi - lo) + 4; ++it) {
+        if (!upper && d == lo) {
+            upper = true;
+            continue;
+        }
+        if (upper && d == hi) break;
+        const int dd = upper ? d + 1 : d;
+        // orient2d of (dd, c) against the projected edge, the expression of tet_side2
+        const R val = A - dv * (R(dd) - xaj);
+        int sd;
+        if (val > B2) {
+            sd = 1;
+        } else if (val < -B2) {
+            sd = -1;
+        } else {
+            if (cnt) cnt->exact++;
+            sd = cross_side_exact(G, a, b, j, k, c, dd);
+        }
+        sd *= dirk;
+        if (!upper) {
+            if (sd < 0)
+                --d;
+            else
+                upper = true;
+        } else {
+            if (sd > 0)
+                ++d;
+            else
+                break;
+        }
+    }
+    return d;
+}
+
+// Cell along l of the crossing of facet f (unit normal nf, reference vertex xf) with the grid line
+// along l through (dj, dk): the m in [lo, hi] with node m on the near side and node m + 1 on the
+// far side, found from `guess` by the search of tet_facet_line_cell (one predicate per step).
+template <typename R>
+__device__ __forceinline__ int facet_line_cell_regs(const TetGeo<R>& G, int f, int l, int dj, int dk, int guess,
+                                                    int lo, int hi, int up, const R nf[3], const R xf[3], R B3,
+                                                    UnitCounts* cnt) {
+    int m = guess < lo ? lo : (guess > hi ? hi : guess);
+    bool upper = false;
+#pragma unroll 1
+    for (int it = 0; it < 2 * (hi - lo) + 4; ++it) {
+        if (!upper && m == lo) {
+            upper = true;
+            continue;
+        }
+        if (upper && m == hi) break;
+        const int t = upper ? m + 1 : m;
+        // node (t along l, dj, dk) in axis order, the expression of tet_side3
+        const int g0 = l == 0 ? t : dj, g1 = l == 1 ? t : (l == 0 ? dj : dk), g2 = l == 2 ? t : dk;
+        const R val = nf[0] * (R(g0) - xf[0]) + nf[1] * (R(g1) - xf[1]) + nf[2] * (R(g2) - xf[2]);
+        int st;
+        if (val > B3) {
+            st = 1;
+        } else if (val < -B3) {
+            st = -1;
+        } else {
+            if (cnt) cnt->exact++;
+            st = tet_side3_exact(G, f, g0, g1, g2);
+        }
+        if (!upper) {
+            if (st == up)
+                --m;  // node m already past the crossing
+            else
+                upper = true;
+        } else {
+            if (st == -up)
+                ++m;
+            else
+                break;
+        }
+    }
+    return m;
+}
+
 // B: vertex i of tetrahedron own
 template <typename R>
 __device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
@@ -78,7 +219,8 @@ __device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
     box_add(sh, own, v0, v1, v2, tet_corner_B(G, i, P));
 }
 
-// crossing t of tetrahedron own: the C record, or 0 when it has no cell in the box
+// crossing t of tetrahedron own: its C record (the crossing point's cells along the two other axes
+// located with the exact-sign search, vertex coordinates read once into registers)
 template <typename R>
 __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, int t, UnitCounts* cnt) {
     const unsigned short* cum = sh->xcum[own];
@@ -92,13 +234,35 @@ __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, in
     const TetGeo<R>& G = sh->geo[own];
     int a, b, pp, qq;
     tet_edge(e, a, b, pp, qq);
-    const int ca = G.cell[a][k], cb = G.cell[b][k];
-    const int c = (ca < cb ? ca : cb) + 1 + (t - before);
-    const int td[3] = {G.hi[0] + 1, G.hi[1] + 1, G.hi[2] + 1};
-    Rec r = 0;
-    auto keep = [&](Rec x) { r = x; };
-    tet_locate_crossing(G, e, k, c, td, keep, cnt);
-    return r;
+    const R xa0 = G.x[a][0], xa1 = G.x[a][1], xa2 = G.x[a][2];
+    const R xb0 = G.x[b][0], xb1 = G.x[b][1], xb2 = G.x[b][2];
+    const int ca0 = G.cell[a][0], ca1 = G.cell[a][1], ca2 = G.cell[a][2];
+    const int cb0 = G.cell[b][0], cb1 = G.cell[b][1], cb2 = G.cell[b][2];
+    const int cak = pick3(ca0, ca1, ca2, k), cbk = pick3(cb0, cb1, cb2, k);
+    const int c = (cak < cbk ? cak : cbk) + 1 + (t - before);
+    const int dirk = cbk > cak ? 1 : -1;
+    const R B2 = G.B2;
+    // rounded crossing point: guesses of its cells
+    const R xak = pick3(xa0, xa1, xa2, k), xbk = pick3(xb0, xb1, xb2, k);
+    const R evk = (xbk - xak) + (G.xl[b][k] - G.xl[a][k]);
+    const R tt = div_guess((R(c) - xak) - G.xl[a][k], evk);
+    const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+    int cj0 = 0, cj1 = 0;
+#pragma unroll 1
+    for (int w = 0; w < 2; ++w) {
+        const int j = w == 0 ? j1 : j2;
+        const R xaj = pick3(xa0, xa1, xa2, j), xbj = pick3(xb0, xb1, xb2, j);
+        const R evj = (xbj - xaj) + (G.xl[b][j] - G.xl[a][j]);
+        const int caj = pick3(ca0, ca1, ca2, j), cbj = pick3(cb0, cb1, cb2, j);
+        const int lo = caj < cbj ? caj : cbj, hi = caj < cbj ? cbj : caj;
+        const int cw = cross_cell_regs(G, a, b, j, k, c, xaj, xak, xbj, xbk, lo, hi, (int)floor_r(xaj + tt * evj),
+                                       dirk, B2, cnt);
+        if (w == 0)
+            cj0 = cw;
+        else
+            cj1 = cw;
+    }
+    return (Rec)c | ((Rec)cj0 << 11) | ((Rec)cj1 << 22) | ((Rec)k << 34) | ((Rec)e << 36);
 }
 
 // line t of tetrahedron own: up to two D records and the run of A nodes (x lines only)
@@ -123,20 +287,53 @@ __device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t,
     const int tq = t / nj;
     const int dj = 1 + t - tq * nj, dk = 1 + tq;
     const int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    const unsigned hits = tet_pierced(tet_line_signs(G, j, k, dj, dk, cnt));
+    // signs of the 6 projected edges against (dj, dk) (the filtered orient2d of tet_side2, from the
+    // projected vertices read once; inconclusive ones settled exactly)
+    unsigned sgn = 0, amb = 0;
+    {
+        const R B2 = G.B2;
+        R pj[4], pk[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            pj[v] = G.x[v][j];
+            pk[v] = G.x[v][k];
+        }
+        const R fj = R(dj), fk = R(dk);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            const int a = e < 3 ? 0 : (e < 5 ? 1 : 2), b = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+            const R du = pj[b] - pj[a], dv = pk[b] - pk[a];
+            const R val = du * (fk - pk[a]) - dv * (fj - pj[a]);
+            sgn |= (val > R(0) ? 1u : 0u) << e;
+            amb |= (val <= B2 && val >= -B2 ? 1u : 0u) << e;
+        }
+    }
+    if (amb) {
+        if (cnt) cnt->exact += __popc(amb);
+        sgn = line_signs_exact(G, j, k, dj, dk, sgn, amb);
+    }
+    const unsigned hits = pierced_lut(sgn);
     int nr = 0;
     arun = 0;
     if (!hits) return 0;
     int mlo = 0, mhi = -1;
+    const int lol = pick3(G.lo[0], G.lo[1], G.lo[2], l), hil = pick3(h0, h1, h2, l);
+    const R B3 = G.B3;
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
         if (!((hits >> f) & 1u)) continue;
         const int va = f == 0 ? 1 : 0;
-        const R fj = G.n[f][j], fk = G.n[f][k], fl = G.n[f][l];
-        const R off = div_guess(
-            -(fj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + fk * ((R(dk) - G.x[va][k]) - G.xl[va][k])), fl);
-        const int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(G.x[va][l] + off), cnt);
-        if (G.ns[f][l] > 0)
+        const R nf[3] = {G.n[f][0], G.n[f][1], G.n[f][2]};
+        const R xf[3] = {G.x[va][0], G.x[va][1], G.x[va][2]};
+        const R fj = pick3(nf[0], nf[1], nf[2], j), fk = pick3(nf[0], nf[1], nf[2], k),
+                fl = pick3(nf[0], nf[1], nf[2], l);
+        const R off = div_guess(-(fj * ((R(dj) - pick3(xf[0], xf[1], xf[2], j)) - G.xl[va][j]) +
+                                  fk * ((R(dk) - pick3(xf[0], xf[1], xf[2], k)) - G.xl[va][k])),
+                                fl);
+        const int up = G.ns[f][l] > 0 ? 1 : -1;
+        const int m = facet_line_cell_regs(G, f, l, dj, dk, (int)floor_r(pick3(xf[0], xf[1], xf[2], l) + off), lol,
+                                           hil, up, nf, xf, B3, cnt);
+        if (up > 0)
             mlo = m;
         else
             mhi = m;
@@ -182,18 +379,18 @@ __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, U
     const int own = (int)((r >> 44) & 15);
     const int cx0 = (int)(r & 2047), cx1 = (int)((r >> 11) & 2047);
     const int dj = (int)((r >> 22) & 2047), dk = (int)((r >> 33) & 2047);
-    const TetGeo<R>& G = sh->geo[own];
+    const TetFrame<R> F = tet_frame(sh->geo[own]);
 #pragma unroll 1
     for (int cx = cx0; cx <= cx1; ++cx) {
 #pragma unroll 1
         for (int o = 0; o < 8; ++o) {
             const int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
             R O[3];
-            piece_origin(G, v0, v1, v2, O);
+            piece_origin(F, v0, v1, v2, O);
             const R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
             // the node is the cell's upper corner along a when the cell index is node - 1
             const R sg = R(((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1));
-            box_add(sh, own, v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
+            box_add(sh, own, v0, v1, v2, tet_corner_A(F, P, rho_from_P(F, P, O), sg));
         }
         if (STATS) cnt.a += 8;
     }

@@ -37,6 +37,11 @@ UNIT = "tets/s"
 # (vertex, edge, facet) triples of 3+3 dot products (5 flops each), the bracket (9) and the triple
 # product (3) = 42 flops each; the type-A closed form is 12 flops.
 FLOPS_PER_INCIDENCE = {"a": 12, "b": 252, "c": 252, "d": 252}
+# DRAM bytes (read + write) of one k_project_tet<float> launch per tetrahedron, from the ncu capture
+# summarised in profiles/k_project_tet_c3s64_full.md (1,572,864 tetrahedra, 754.0 MB); the traffic
+# is the geometry records plus vertex gathers, so it scales with the tetrahedron count.  Set to
+# None when the kernel changes until a new capture is taken.
+TRAFFIC_BYTES_PER_TET = 754.0e6 / 1572864
 # ALU peaks derived from unit counts and the maximum SM clock (no measured FP32 figure exists):
 # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 1.25 TFLOP/s nominal.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -308,7 +313,10 @@ def run_ours(a):
         flops = sum(FLOPS_PER_INCIDENCE[k] * v for k, v in inc.items())
         achieved = flops / (kern32[dom] / 1000.0) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": names[dom],
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None if TRAFFIC_BYTES_PER_TET is None else TRAFFIC_BYTES_PER_TET * ns,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                "scale-64 capture scaled by tetrahedra)", "kernel": names[dom],
                 "kernel_ms": kern32[dom], "flops_per_launch": flops,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     else:

@@ -1,22 +1,25 @@
 // Projection kernel of tetrahedral meshes (Sect. 3; Algorithm 2 organised per simplex).
 //
-// k_project_tet<R> is a persistent warp-cooperative kernel.  A warp takes TB_CHUNK consecutive
-// tetrahedra; each lane of the first half canonicalises one of them (exact orientation, periodic
-// unwrap, cells) and writes its geometry to shared memory.  A tetrahedron inside one cell deposits
-// |V| mean(rho) at once (Algorithm 2, step 1).  Every other tetrahedron receives a dense box of
-// per-cell accumulators in shared memory, one slot per cell of its bounding box; the tetrahedra of
-// the chunk are packed into rounds whose boxes fit the warp's TB_BOX slots together (a
-// tetrahedron whose box alone exceeds them is listed for the large-simplex pass).
+// k_tet_setup: one thread per tetrahedron canonicalises it (exact orientation, periodic unwrap,
+// cells), deposits a tetrahedron inside one cell at once (Algorithm 2, step 1), lists one whose
+// bounding box exceeds TB_MAX_CELLS for the FP64 large-simplex pass, and writes the geometry
+// record of every other one to HBM.
 //
-// The work of a round is split into three phases of independent items -- the vertices (corners
-// B), the (edge, axis, plane) crossings (corners C) and the grid lines (corners D, and along x the
-// grid nodes between the two pierced facets, corners A) -- whose items of all tetrahedra of the
-// round are numbered consecutively and dealt to the 32 lanes in turn.  Locating a corner costs a
-// few exact-sign predicates; evaluating it (all the cells around it at once) costs most of the
-// arithmetic, so located corners are queued as compact records and evaluated in full batches of
-// 32 identical evaluations.  Every (corner, cell) contribution is one shared-memory add into the
-// box of its tetrahedron.  At the end of the round each box is flushed with one FP64 global
-// atomic per non-zero (tetrahedron, cell) piece.
+// k_project_tet<R> is a persistent block-cooperative kernel.  A block takes TB_NT consecutive
+// tetrahedra, copies their records into shared memory and gives each a dense box of per-cell
+// accumulators, one slot per cell of its bounding box; the tetrahedra are packed, in order, into
+// rounds whose boxes fit the block's slots together.  The work of a round is split into three
+// phases of independent items -- the vertices (corners B), the (edge, axis, plane) crossings
+// (corners C) and the grid lines (corners D, and along x the grid nodes between the two pierced
+// facets, corners A) -- whose items of all tetrahedra of the round are numbered consecutively and
+// dealt to the block's warps 32 at a time.  All warps of a block run the same phase between two
+// barriers: the instruction footprint of the block is that phase's code, and the items are
+// balanced over the warps.  Locating a corner costs a few exact-sign predicates; evaluating it
+// (all the cells around it at once) costs most of the arithmetic, so each warp queues the corners
+// it locates as compact records and evaluates them in full batches of 32 identical evaluations.
+// Every (corner, cell) contribution is one shared-memory add into the box of its tetrahedron.  At
+// the end of the round the boxes are flushed with one FP64 global atomic per non-zero
+// (tetrahedron, cell) piece.
 //
 // FP32-mixed path only: the mass closure (not in the paper).  The FP64 closed-form masses of the
 // tetrahedra of a round minus the (two-float, exact enough) sum of their FP32 pieces is spread over
@@ -31,25 +34,34 @@ namespace cdp {
 
 namespace {
 
-constexpr int TB_CHUNK = 16;   // tetrahedra per warp chunk (one per lane during set-up)
-constexpr int TB_QCAP = 128;   // C / D corner records awaiting evaluation (power of two)
-constexpr int TB_ACAP = 64;    // runs of A nodes awaiting evaluation (power of two)
+constexpr int TB_WARPS = 8;                 // warps per block
+constexpr int TB_THREADS = 32 * TB_WARPS;   // threads per block
+constexpr int TB_NT = 16 * TB_WARPS;        // tetrahedra per block chunk (power of two, <= TB_THREADS)
+constexpr int TB_QCAP = 128;                // C / D corner records awaiting evaluation, per warp
+constexpr int TB_ACAP = 64;                 // runs of A nodes awaiting evaluation, per warp
+constexpr int TB_OWN_BITS = 7;              // tetrahedron-of-chunk index in a queued record
 constexpr unsigned FULL = 0xffffffffu;
+static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS, "chunk index does not fit");
 
-// box slots per warp: 1280 FP32 or FP64 accumulators
+// largest bounding box (cells) projected by the main kernel, and the block's box slots
+constexpr int TB_MAX_CELLS = 1280;
 template <typename R>
 struct BoxCap {
-    static constexpr int value = 1280;
+    static constexpr int value = TB_MAX_CELLS * TB_WARPS;
 };
 
 template <typename R>
 struct TetShared {
-    TetGeo<R> geo[TB_CHUNK];
+    TetGeo<R> geo[TB_NT];
     R box[BoxCap<R>::value];
-    Rec q[TB_QCAP];
-    unsigned long long aq[TB_ACAP];
-    unsigned short xcum[TB_CHUNK][18];  // running count of the crossings of the (edge, axis) pairs
-    int boff[TB_CHUNK];                 // first box slot of each tetrahedron of the round
+    Rec q[TB_WARPS][TB_QCAP];
+    unsigned long long aq[TB_WARPS][TB_ACAP];
+    unsigned short xcum[TB_NT][18];  // running count of the crossings of the (edge, axis) pairs
+    int boff[TB_NT];                 // first box slot of each tetrahedron of the round
+    int pre[TB_NT];                  // inclusive prefix of the current phase's item counts; in the
+                                     // flush, of the round's box sizes
+    int wsum[TB_WARPS];              // block-scan scratch
+    float red[3][TB_WARPS];          // block-reduction scratch of the mass closure
 };
 
 // ------------------------------------------------------------------------------------------
@@ -357,7 +369,7 @@ __device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t,
 
 template <typename R, bool STATS>
 __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, UnitCounts& cnt) {
-    const int own = (int)((r >> 40) & 15);
+    const int own = (int)((r >> 40) & ((1 << TB_OWN_BITS) - 1));
     const TetGeo<R>& G = sh->geo[own];
     auto acc = [&](int x, int y, int z, R v) { box_add(sh, own, x, y, z, v); };
     if (is_c) {
@@ -376,7 +388,7 @@ __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, Unit
 // a run of A nodes (grid nodes inside the tetrahedron on one x line): the 8 cells of each node
 template <typename R, bool STATS>
 __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, UnitCounts& cnt) {
-    const int own = (int)((r >> 44) & 15);
+    const int own = (int)((r >> 44) & ((1 << TB_OWN_BITS) - 1));
     const int cx0 = (int)(r & 2047), cx1 = (int)((r >> 11) & 2047);
     const int dj = (int)((r >> 22) & 2047), dk = (int)((r >> 33) & 2047);
     const TetFrame<R> F = tet_frame(sh->geo[own]);
@@ -420,24 +432,29 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     lo += err;
 }
 
-// owner lane of flat item u: the first lane whose inclusive prefix exceeds u
-__device__ __forceinline__ int owner_lane(int pre, int u) {
-    int own = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int p = __shfl_sync(FULL, pre, own + step - 1);
-        if (p <= u) own += step;
-    }
-    return own > 31 ? 31 : own;
-}
-
-__device__ __forceinline__ int inclusive_scan(int v, int lane) {
+// inclusive prefix sum over the block of one value per thread (thread order)
+__device__ __forceinline__ int block_scan(int v, int* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(FULL, v, o);
         if (lane >= o) v += t;
     }
-    return v;
+    __syncthreads();  // wsum free
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    return v + off;
+}
+
+// first index t of the non-decreasing pre[0, TB_NT) with pre[t] > u (u < pre[TB_NT - 1])
+__device__ __forceinline__ int upper_index(const int* pre, int u) {
+    int pos = 0;
+#pragma unroll
+    for (int step = TB_NT / 2; step > 0; step >>= 1)
+        if (pre[pos + step - 1] <= u) pos += step;
+    return pos;
 }
 
 }  // namespace
@@ -481,7 +498,7 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
             } else {
                 const long long cells =
                     (long long)(S.hi[0] - S.lo[0] + 1) * (S.hi[1] - S.lo[1] + 1) * (S.hi[2] - S.lo[2] + 1);
-                if (cells > BoxCap<R>::value) {
+                if (cells > TB_MAX_CELLS) {
                     const unsigned at = atomicAdd(&ctr->big_count, 1u);
                     if ((long long)at < big_cap) big_list[at] = (int)s;
                 } else {
@@ -506,41 +523,41 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
 }
 
 template <typename R, bool STATS>
-__global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
     k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
                   double* __restrict__ out, UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
     constexpr int BOX = BoxCap<R>::value;
-    const int lane = threadIdx.x & 31;
-    TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw) + (threadIdx.x >> 5);
-    for (int e = lane; e < BOX; e += 32) sh->box[e] = R(0);
-    __syncwarp();
+    TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Rec* const q = sh->q[warp];
+    unsigned long long* const aq = sh->aq[warp];
+    for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
     UnitCounts cnt = {0, 0, 0, 0, 0};     // corner counts (registers)
     UnitCounts xcnt = {0, 0, 0, 0, 0};    // exact-predicate count, updated through a pointer
     UnitCounts* pc = STATS ? &xcnt : nullptr;
-    const long long nchunks = (nb + TB_CHUNK - 1) / TB_CHUNK;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long nchunks = (nb + TB_NT - 1) / TB_NT;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
-         chunk += warps) {
-        // ---- the chunk's geometry records (written by k_tet_setup) into shared memory
-        const long long s = chunk * TB_CHUNK + lane;
-        const int need = (lane < TB_CHUNK && s < nb) ? __ldg(need_in + s) : 0;
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        // ---- the chunk's geometry records (written by k_tet_setup) into shared memory; thread
+        // t < TB_NT speaks for tetrahedron t of the chunk
+        const long long first = chunk * TB_NT;
+        const long long last = first + TB_NT < nb ? first + TB_NT : nb;
+        __syncthreads();  // the previous chunk is done with the records
         {
-            const long long first = chunk * TB_CHUNK;
-            const long long last = first + TB_CHUNK < nb ? first + TB_CHUNK : nb;
             constexpr int W = sizeof(TetGeo<R>) / 8;
             static_assert(sizeof(TetGeo<R>) % 8 == 0, "geometry records are copied in 8-byte words");
             const unsigned long long* src = reinterpret_cast<const unsigned long long*>(geo + first);
             unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh->geo);
             const int words = (int)(last - first) * W;
-            for (int w = lane; w < words; w += 32) dst[w] = __ldg(src + w);
+            for (int w = tid; w < words; w += TB_THREADS) dst[w] = __ldg(src + w);
         }
-        __syncwarp();
+        const int need = (tid < TB_NT && first + tid < nb) ? __ldg(need_in + first + tid) : 0;
+        __syncthreads();
         if (need > 0) {
-            const TetGeo<R>& G = sh->geo[lane];
+            const TetGeo<R>& G = sh->geo[tid];
             int run = 0;
 #pragma unroll 1
             for (int p = 0; p < 18; ++p) {
@@ -549,44 +566,45 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                 tet_edge(e, a, b, pp, qq);
                 const int d = G.cell[a][k] - G.cell[b][k];
                 run += d < 0 ? -d : d;
-                sh->xcum[lane][p] = (unsigned short)run;
+                sh->xcum[tid][p] = (unsigned short)run;
             }
         }
-        __syncwarp();
-        unsigned pending = __ballot_sync(FULL, need > 0);
-        // ---- rounds: tetrahedra in lane order while their boxes fit together
-        while (pending) {
-            const bool mine_pending = (pending >> lane) & 1u;
-            const int pre_box = inclusive_scan(mine_pending ? need : 0, lane);
-            const bool in = mine_pending && pre_box <= BOX;
-            const unsigned round = __ballot_sync(FULL, in);
-            pending &= ~round;
-            if (in) sh->boff[lane] = pre_box - need;
+        bool pending = need > 0;
+        // ---- rounds: tetrahedra in chunk order while their boxes fit the block's slots together
+#pragma unroll 1
+        while (__syncthreads_or(pending)) {
+            const int pre_box = block_scan(pending ? need : 0, sh->wsum);
+            const bool in = pending && pre_box <= BOX;
+            pending = pending && !in;
+            if (in) sh->boff[tid] = pre_box - need;
             // item counts of the three phases
-            int n_ph[3] = {0, 0, 0};
+            int n_ph1 = 0, n_ph2 = 0;
             if (in) {
-                const TetGeo<R>& G = sh->geo[lane];
-                n_ph[0] = 4;
-                n_ph[1] = sh->xcum[lane][17];
-                n_ph[2] = G.hi[1] * G.hi[2] + G.hi[0] * G.hi[2] + G.hi[0] * G.hi[1];
+                const TetGeo<R>& G = sh->geo[tid];
+                n_ph1 = sh->xcum[tid][17];
+                n_ph2 = G.hi[1] * G.hi[2] + G.hi[0] * G.hi[2] + G.hi[0] * G.hi[1];
             }
-            __syncwarp();
-            unsigned head = 0, tail = 0, ahead = 0, atail = 0;
-#pragma unroll 1
+        #pragma unroll 1
             for (int ph = 0; ph < 3; ++ph) {
-                const int mine = ph == 0 ? n_ph[0] : (ph == 1 ? n_ph[1] : n_ph[2]);
-                const int pre = inclusive_scan(mine, lane);
-                const int tot = __shfl_sync(FULL, pre, 31);
+                const int mine = in ? (ph == 0 ? 4 : (ph == 1 ? n_ph1 : n_ph2)) : 0;
+                const int pre = block_scan(mine, sh->wsum);
+                if (tid < TB_NT) sh->pre[tid] = pre;
+                __syncthreads();
+                const int tot = sh->pre[TB_NT - 1];
+                // item rounds of 32 dealt to the warps in turn; each warp queues and evaluates its
+                // own located corners
+                const int nrounds = (tot + 31) >> 5;
+                const int my_rounds = nrounds > warp ? (nrounds - warp + TB_WARPS - 1) / TB_WARPS : 0;
+                unsigned head = 0, tail = 0, ahead = 0, atail = 0;
 #pragma unroll 1
-                for (int u0 = 0; u0 < tot; u0 += 32) {
-                    const int u = u0 + lane;
-                    const int own = owner_lane(pre, u);
-                    const int before = __shfl_sync(FULL, pre - mine, own);
+                for (int i = 0; i < my_rounds; ++i) {
+                    const int u = ((warp + i * TB_WARPS) << 5) + lane;
                     Rec r0 = 0, r1 = 0;
                     unsigned long long arun = 0;
-                    int nr = 0;
+                    int nr = 0, own = 0;
                     if (u < tot) {
-                        const int t = u - before;
+                        own = upper_index(sh->pre, u);
+                        const int t = u - (own > 0 ? sh->pre[own - 1] : 0);
                         if (ph == 0) {
                             item_vertex(sh, own, t);
                             if (STATS) cnt.b++;
@@ -597,50 +615,72 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                             nr = item_line(sh, own, t, r0, r1, arun, pc);
                         }
                     }
-                    // append the located corners to the queues (warp-aggregated, no atomics)
+                    // append the located corners to the warp's queues (warp-aggregated, no atomics)
                     const Rec ob = (Rec)own << 40;
                     const unsigned b0 = __ballot_sync(FULL, nr >= 1), b1 = __ballot_sync(FULL, nr >= 2);
                     const unsigned off = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
-                    if (nr >= 1) sh->q[(tail + off) & (TB_QCAP - 1)] = r0 | ob;
-                    if (nr >= 2) sh->q[(tail + off + 1) & (TB_QCAP - 1)] = r1 | ob;
+                    if (nr >= 1) q[(tail + off) & (TB_QCAP - 1)] = r0 | ob;
+                    if (nr >= 2) q[(tail + off + 1) & (TB_QCAP - 1)] = r1 | ob;
                     tail += __popc(b0) + __popc(b1);
                     const unsigned ba = __ballot_sync(FULL, arun != 0);
-                    if (arun) sh->aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] = arun | ((unsigned long long)own << 44);
+                    if (arun)
+                        aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] =
+                            arun | ((unsigned long long)own << 44);
                     atail += __popc(ba);
                     __syncwarp();
-                    // evaluate full batches (and, after the phase's last items, what is left)
-                    const bool last = u0 + 32 >= tot;
+                    // evaluate full batches (and, after the warp's last items, what is left)
+                    const bool last_round = i + 1 == my_rounds;
 #pragma unroll 1
                     for (;;) {
                         const unsigned avail = tail - head;
-                        if (avail == 0u || (!last && avail < 32u)) break;
-                        if ((unsigned)lane < avail) eval_CD<R, STATS>(sh, sh->q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
+                        if (avail == 0u || (!last_round && avail < 32u)) break;
+                        if ((unsigned)lane < avail) eval_CD<R, STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
                         head += avail < 32u ? avail : 32u;
                     }
 #pragma unroll 1
                     for (;;) {
                         const unsigned avail = atail - ahead;
-                        if (avail == 0u || (!last && avail < 32u)) break;
-                        if ((unsigned)lane < avail) eval_A<R, STATS>(sh, sh->aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
+                        if (avail == 0u || (!last_round && avail < 32u)) break;
+                        if ((unsigned)lane < avail) eval_A<R, STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
                         ahead += avail < 32u ? avail : 32u;
                     }
                     __syncwarp();
                 }
+                // (the next block_scan's barrier orders this phase before the next one)
             }
             // ---- flush every box of the round: one FP64 atomic per non-zero piece (FP32 path: and
-            // one more for its share of the round's mass-closure residual)
+            // one more for its share of the round's mass-closure residual).  pre[t] becomes the end
+            // of tetrahedron t's slots, clamped to the round's last slot, so that the owner of a
+            // slot is the first t with pre[t] above it.
+            __syncthreads();  // every warp has finished the line phase
+            int used_slots = 0;
+            {
+                // the round's tetrahedra are a prefix (in chunk order) of the pending ones: the last
+                // in-round end is the largest pre_box <= BOX among them
+                const int mine_end = in ? pre_box : 0;
+                int m = mine_end;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+                if (lane == 0) sh->wsum[warp] = m;
+                __syncthreads();
+                for (int w = 0; w < TB_WARPS; ++w) used_slots = max(used_slots, sh->wsum[w]);
+            }
+            if (tid < TB_NT) {
+                // tetrahedra outside the round own no slot
+                const int end = in ? pre_box : min(pre_box, used_slots);
+                sh->pre[tid] = end;
+            }
             float scale = 0.f;
             if (fp32) {
                 // FP32 pieces of the round minus the closed-form masses of its tetrahedra, summed as
                 // two floats (exact enough, FP32 arithmetic only); the residual is then spread over
                 // the pieces in proportion to their magnitude
-                const int used = __shfl_sync(FULL, pre_box, 31 - __clz(round));
                 float hi = 0.f, lo = 0.f, asum = 0.f;
                 if (in) {
-                    two_sum_acc(hi, lo, -sh->geo[lane].mexact_hi);
-                    lo -= sh->geo[lane].mexact_lo;
+                    two_sum_acc(hi, lo, -sh->geo[tid].mexact_hi);
+                    lo -= sh->geo[tid].mexact_lo;
                 }
-                for (int e = lane; e < used; e += 32) {
+                for (int e = tid; e < used_slots; e += TB_THREADS) {
                     const float v = (float)sh->box[e];
                     two_sum_acc(hi, lo, v);
                     asum += fabsf(v);
@@ -652,51 +692,58 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
                     two_sum_acc(hi, lo, ohi);
                     asum += __shfl_xor_sync(FULL, asum, o);
                 }
+                __syncthreads();  // wsum reads above are done; red is free
+                if (lane == 0) {
+                    sh->red[0][warp] = hi;
+                    sh->red[1][warp] = lo;
+                    sh->red[2][warp] = asum;
+                }
+                __syncthreads();
+                hi = 0.f;
+                lo = 0.f;
+                asum = 0.f;
+                for (int w = 0; w < TB_WARPS; ++w) {
+                    lo += sh->red[1][w];
+                    two_sum_acc(hi, lo, sh->red[0][w]);
+                    asum += sh->red[2][w];
+                }
                 const float resid = -(hi + lo);
                 if (asum > 0.f) {
                     scale = resid * __frcp_rn(asum);
-                } else if (lane == 0) {
-                    const TetGeo<R>& G = sh->geo[__ffs(round) - 1];
+                } else if (tid == 0) {
+                    const TetGeo<R>& G = sh->geo[upper_index(sh->pre, 0)];
                     const long long idx = flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1],
                                                     G.anchor[2] + G.cell[0][2]);
                     if (idx >= 0) atomicAdd(out + idx, (double)resid);
                 }
+            } else {
+                __syncthreads();
             }
-            unsigned todo = round;
 #pragma unroll 1
-            while (todo) {
-                const int own = __ffs(todo) - 1;
-                todo &= todo - 1u;
+            for (int e = tid; e < used_slots; e += TB_THREADS) {
+                const R v = sh->box[e];
+                if (v == R(0)) continue;
+                sh->box[e] = R(0);
+                const int own = upper_index(sh->pre, e);
                 const TetGeo<R>& G = sh->geo[own];
                 const int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
-                const int size = ex * ey * (G.hi[2] + 1);
-                R* box = sh->box + sh->boff[own];
-                const float inv_ex = 1.0f / (float)ex, inv_ey = 1.0f / (float)ey;
-                for (int e = lane; e < size; e += 32) {
-                    const R v = box[e];
-                    if (v == R(0)) continue;
-                    box[e] = R(0);
-                    // e = x + ex (y + ey z)
-                    int r = (int)((float)e * inv_ex);
-                    r += (r + 1) * ex <= e ? 1 : 0;
-                    r -= r * ex > e ? 1 : 0;
-                    const int x = e - r * ex;
-                    int z = (int)((float)r * inv_ey);
-                    z += (z + 1) * ey <= r ? 1 : 0;
-                    z -= z * ey > r ? 1 : 0;
-                    const int y = r - z * ey;
-                    bool ok = true;
-                    const int cx = wrap_axis(G.anchor[0] + x, g.n[0], g.periodic, ok);
-                    const int cy = wrap_axis(G.anchor[1] + y, g.n[1], g.periodic, ok);
-                    const int cz = wrap_axis(G.anchor[2] + z, g.n[2], g.periodic, ok);
-                    if (!ok) continue;
-                    double* cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
-                    atomicAdd(cell, (double)v);
-                    // the piece's share of the closure residual (FP64 atomics are cheap here)
-                    if (fp32) atomicAdd(cell, (double)(scale * fabsf((float)v)));
-                }
+                const int le = e - sh->boff[own];
+                // le = x + ex (y + ey z)
+                const int r = le / ex;
+                const int x = le - r * ex;
+                const int z = r / ey;
+                const int y = r - z * ey;
+                bool ok = true;
+                const int cx = wrap_axis(G.anchor[0] + x, g.n[0], g.periodic, ok);
+                const int cy = wrap_axis(G.anchor[1] + y, g.n[1], g.periodic, ok);
+                const int cz = wrap_axis(G.anchor[2] + z, g.n[2], g.periodic, ok);
+                if (!ok) continue;
+                double* cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
+                atomicAdd(cell, (double)v);
+                // the piece's share of the closure residual (FP64 atomics are cheap here)
+                if (fp32) atomicAdd(cell, (double)(scale * fabsf((float)v)));
             }
-            __syncwarp();
+            // (the next round's block_scan barrier orders the flush before new box writes)
         }
     }
     if (STATS) {
@@ -710,7 +757,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, sizeof(R) == 4 ? 4 : 2)
 
 template <typename R>
 static size_t tet_shared_bytes() {
-    return sizeof(TetShared<R>) * (CDP_WBLOCK / 32);
+    return sizeof(TetShared<R>);
 }
 
 template <typename R, bool STATS>
@@ -730,9 +777,9 @@ cudaError_t configure_tet() {
 int resident_blocks_tet(int fp32) {
     int n = 0;
     cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<float, false>,
-                                                                         CDP_WBLOCK, tet_shared_bytes<float>())
+                                                                         TB_THREADS, tet_shared_bytes<float>())
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<double, false>,
-                                                                         CDP_WBLOCK, tet_shared_bytes<double>());
+                                                                         TB_THREADS, tet_shared_bytes<double>());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -751,16 +798,15 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
             L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, reinterpret_cast<TetGeo<R>*>(L.geo), L.need,
             L.big_list, L.big_cap, L.stats != nullptr);
         if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
-        const long long chunks = (nb + TB_CHUNK - 1) / TB_CHUNK;
-        long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
+        long long blocks = (nb + TB_NT - 1) / TB_NT;
         const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
         if (L.stats)
-            k_project_tet<R, true><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<R>(), st>>>(
+            k_project_tet<R, true><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
                 L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, L.stats);
         else
-            k_project_tet<R, false><<<(unsigned)blocks, CDP_WBLOCK, tet_shared_bytes<R>(), st>>>(
+            k_project_tet<R, false><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
                 L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, nullptr);
     }
     return cudaGetLastError();

@@ -82,6 +82,19 @@ CDP_HD float div_guess<float>(float a, float b) {
 #endif
 }
 
+// 1 / x for the FP32 contributions: the hardware reciprocal (relative error ~1e-7, far below the
+// FP32-mixed tolerance); FP64 keeps the correctly rounded quotient
+template <typename R>
+CDP_HD R rcp_fast(R x) { return R(1) / x; }
+template <>
+CDP_HD float rcp_fast<float>(float x) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.0f, x);
+#else
+    return 1.0f / x;
+#endif
+}
+
 template <typename R>
 CDP_HD R floor_r(R v);
 template <>
@@ -145,6 +158,24 @@ CDP_HD void tet_edge(int e, int& a, int& b, int& p, int& q) {
     p = (0x000112 >> (4 * e)) & 15;
     q = (0x123233 >> (4 * e)) & 15;
 }
+
+// Bit e set when the permutation (a, b, p, q) of edge e (tet_edge order) is odd, computed at
+// compile time from the same nibble tables.
+constexpr unsigned tet_edge_odd_mask() {
+    unsigned m = 0;
+    for (int e = 0; e < 6; ++e) {
+        const int v[4] = {(0x211000 >> (4 * e)) & 15, (0x332321 >> (4 * e)) & 15, (0x000112 >> (4 * e)) & 15,
+                          (0x123233 >> (4 * e)) & 15};
+        int inv = 0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = i + 1; j < 4; ++j) inv += v[i] > v[j];
+        if (inv & 1) m |= 1u << e;
+    }
+    return m;
+}
+
+// parity4(a, b, p, q) of edge e: +1 even, -1 odd
+CDP_HD int tet_edge_parity(int e) { return ((tet_edge_odd_mask() >> e) & 1u) ? -1 : 1; }
 
 CDP_HD int tet_edge_index(int i, int j) {
     int a = i < j ? i : j, b = i < j ? j : i;
@@ -752,11 +783,11 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
     R nj = pick3(n[0], n[1], n[2], j), nk = pick3(n[0], n[1], n[2], k), nl = pick3(n[0], n[1], n[2], l);
     R tau = G.ns[f][l] > 0 ? R(1) : R(-1);
     R eps = (l == 1) ? R(-1) : R(1);
-    R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
+    R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) * rcp_fast(nl);
     const R g[3] = {G.g[0], G.g[1], G.g[2]};
     R gn = dot3(g, n);
     R hj = cross_comp(g, n, j), hk = cross_comp(g, n, k);
-    R irj2 = R(1) / (nk * nk + nl * nl), irk2 = R(1) / (nj * nj + nl * nl);
+    R irj2 = rcp_fast(nk * nk + nl * nl), irk2 = rcp_fast(nj * nj + nl * nl);
     R gj = pick3(g[0], g[1], g[2], j), gk = pick3(g[0], g[1], g[2], k), gl = pick3(g[0], g[1], g[2], l);
     R xl_ = G.x[va][l], xll = G.xl[va][l] + off;
     const TetFrame<R> F = tet_frame(G);
@@ -794,34 +825,30 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
     R ev[3];
     for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
     R evk = pick3(ev[0], ev[1], ev[2], k);
-    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
+    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) * rcp_fast(evk);
     R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
     R inv = rsqrt_r<R>(dot3(ev, ev));
     const R eu[3] = {ev[0] * inv, ev[1] * inv, ev[2] * inv};
     const R g[3] = {G.g[0], G.g[1], G.g[2]};
     const R np_[3] = {G.n[p][0], G.n[p][1], G.n[p][2]};
     const R nq_[3] = {G.n[q][0], G.n[q][1], G.n[q][2]};
-    // in-facet normals of the edge: m_p in facet p (towards q), m_q in facet q (towards p)
+    // in-facet normals of the edge: m_p in facet p (towards q), m_q in facet q (towards p); the
+    // orientations are the parities of (a, b, q, p) = -(a, b, p, q) and of (a, b, p, q)
+    const R pq = R(tet_edge_parity(e)), pp = -pq;
     R mp[3], mq[3];
     cross3(np_, eu, mp);
     cross3(nq_, eu, mq);
-    R pp = R(parity4(a, b, q, p)), pq = R(parity4(a, b, p, q));
     for (int w = 0; w < 3; ++w) {
         mp[w] *= pp;
         mq[w] *= pq;
     }
     R ge = dot3(g, eu), gmp = dot3(g, mp), gmq = dot3(g, mq), gnp = dot3(g, np_), gnq = dot3(g, nq_);
     R hp = cross_comp(g, np_, k), hq = cross_comp(g, nq_, k);
-    R npk = pick3(np_[0], np_[1], np_[2], k), nqk = pick3(nq_[0], nq_[1], nq_[2], k);
-    R irp2 = R(1) / (R(1) - npk * npk), irq2 = R(1) / (R(1) - nqk * nqk);
-    {
-        // 1 - n_k^2 from the other two components (no cancellation when n_k is near 1)
-        R a0 = pick3(np_[1], np_[0], np_[0], k), a1 = pick3(np_[2], np_[2], np_[1], k);
-        R b0 = pick3(nq_[1], nq_[0], nq_[0], k), b1 = pick3(nq_[2], nq_[2], nq_[1], k);
-        irp2 = R(1) / (a0 * a0 + a1 * a1);
-        irq2 = R(1) / (b0 * b0 + b1 * b1);
-    }
-    R lam = R(-parity4(a, b, p, q)) * R(dirk);
+    // 1 / (1 - n_k^2) from the other two components (no cancellation when n_k is near 1)
+    R a0 = pick3(np_[1], np_[0], np_[0], k), a1 = pick3(np_[2], np_[2], np_[1], k);
+    R b0 = pick3(nq_[1], nq_[0], nq_[0], k), b1 = pick3(nq_[2], nq_[2], nq_[1], k);
+    R irp2 = rcp_fast(a0 * a0 + a1 * a1), irq2 = rcp_fast(b0 * b0 + b1 * b1);
+    R lam = -pq * R(dirk);
     // the crossing point as vertex a (high part) plus a small offset
     const R xa[3] = {G.x[a][0], G.x[a][1], G.x[a][2]};
     const R dx[3] = {G.xl[a][0] + t * ev[0], G.xl[a][1] + t * ev[1], G.xl[a][2] + t * ev[2]};

@@ -39,6 +39,7 @@ constexpr int TB_THREADS = 32 * TB_WARPS;   // threads per block
 constexpr int TB_NT = 16 * TB_WARPS;        // tetrahedra per block chunk (power of two, <= TB_THREADS)
 constexpr int TB_QCAP = 128;                // C / D corner records awaiting evaluation, per warp
 constexpr int TB_ACAP = 64;                 // runs of A nodes awaiting evaluation, per warp
+constexpr int TB_PCAP = 64;                 // pierced grid lines awaiting their facet searches, per warp
 constexpr int TB_OWN_BITS = 7;              // tetrahedron-of-chunk index in a queued record
 constexpr unsigned FULL = 0xffffffffu;
 static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS, "chunk index does not fit");
@@ -56,6 +57,7 @@ struct TetShared {
     R box[BoxCap<R>::value];
     Rec q[TB_WARPS][TB_QCAP];
     unsigned long long aq[TB_WARPS][TB_ACAP];
+    unsigned long long pq[TB_WARPS][TB_PCAP];  // pierced lines awaiting their facet searches
     unsigned short xcum[TB_NT][18];  // running count of the crossings of the (edge, axis) pairs
     int boff[TB_NT];                 // first box slot of each tetrahedron of the round
     int pre[TB_NT];                  // inclusive prefix of the current phase's item counts; in the
@@ -277,10 +279,11 @@ __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, in
     return (Rec)c | ((Rec)cj0 << 11) | ((Rec)cj1 << 22) | ((Rec)k << 34) | ((Rec)e << 36);
 }
 
-// line t of tetrahedron own: up to two D records and the run of A nodes (x lines only)
+// Line t of tetrahedron own: which facets the grid line pierces.  Returns the pierced-line record
+// (facet mask in bits 0-3, l in 4-5, dj in 6-16, dk in 17-27; 0 when the line misses).
 template <typename R>
-__device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t, Rec& r0, Rec& r1,
-                                         unsigned long long& arun, UnitCounts* cnt) {
+__device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>* sh, int own, int t,
+                                                             UnitCounts* cnt) {
     const TetGeo<R>& G = sh->geo[own];
     const int h0 = G.hi[0], h1 = G.hi[1], h2 = G.hi[2];
     // lines along l through the interior grid points (dj, dk) in [1, h_j] x [1, h_k]
@@ -325,11 +328,24 @@ __device__ __forceinline__ int item_line(const TetShared<R>* sh, int own, int t,
         sgn = line_signs_exact(G, j, k, dj, dk, sgn, amb);
     }
     const unsigned hits = pierced_lut(sgn);
+    if (!hits) return 0ull;
+    return (unsigned long long)hits | ((unsigned long long)l << 4) | ((unsigned long long)dj << 6) |
+           ((unsigned long long)dk << 17);
+}
+
+// A pierced line (record of item_line_test): its D records (one per pierced facet, the cell along
+// the line located with the exact-sign search) and the run of A nodes between them (x lines only).
+template <typename R>
+__device__ __forceinline__ int item_line_facets(const TetShared<R>* sh, int own, unsigned long long pr, Rec& r0,
+                                                Rec& r1, unsigned long long& arun, UnitCounts* cnt) {
+    const TetGeo<R>& G = sh->geo[own];
+    const unsigned hits = (unsigned)(pr & 15u);
+    const int l = (int)((pr >> 4) & 3u), dj = (int)((pr >> 6) & 2047u), dk = (int)((pr >> 17) & 2047u);
+    const int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
     int nr = 0;
     arun = 0;
-    if (!hits) return 0;
     int mlo = 0, mhi = -1;
-    const int lol = pick3(G.lo[0], G.lo[1], G.lo[2], l), hil = pick3(h0, h1, h2, l);
+    const int lol = pick3(G.lo[0], G.lo[1], G.lo[2], l), hil = pick3(G.hi[0], G.hi[1], G.hi[2], l);
     const R B3 = G.B3;
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
@@ -533,6 +549,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Rec* const q = sh->q[warp];
     unsigned long long* const aq = sh->aq[warp];
+    unsigned long long* const pq = sh->pq[warp];
     for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
     UnitCounts cnt = {0, 0, 0, 0, 0};     // corner counts (registers)
     UnitCounts xcnt = {0, 0, 0, 0, 0};    // exact-predicate count, updated through a pointer
@@ -576,7 +593,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
             const int pre_box = block_scan(pending ? need : 0, sh->wsum);
             const bool in = pending && pre_box <= BOX;
             pending = pending && !in;
-            if (in) sh->boff[tid] = pre_box - need;
+            if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
             // item counts of the three phases
             int n_ph1 = 0, n_ph2 = 0;
             if (in) {
@@ -595,13 +612,13 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
                 // own located corners
                 const int nrounds = (tot + 31) >> 5;
                 const int my_rounds = nrounds > warp ? (nrounds - warp + TB_WARPS - 1) / TB_WARPS : 0;
-                unsigned head = 0, tail = 0, ahead = 0, atail = 0;
+                unsigned head = 0, tail = 0, ahead = 0, atail = 0, phead = 0, ptail = 0;
 #pragma unroll 1
                 for (int i = 0; i < my_rounds; ++i) {
                     const int u = ((warp + i * TB_WARPS) << 5) + lane;
-                    Rec r0 = 0, r1 = 0;
-                    unsigned long long arun = 0;
-                    int nr = 0, own = 0;
+                    Rec r0 = 0;
+                    unsigned long long pline = 0;
+                    int own = 0;
                     if (u < tot) {
                         own = upper_index(sh->pre, u);
                         const int t = u - (own > 0 ? sh->pre[own - 1] : 0);
@@ -610,41 +627,69 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
                             if (STATS) cnt.b++;
                         } else if (ph == 1) {
                             r0 = item_crossing(sh, own, t, pc);
-                            nr = r0 != 0 ? 1 : 0;
                         } else {
-                            nr = item_line(sh, own, t, r0, r1, arun, pc);
+                            pline = item_line_test(sh, own, t, pc);
                         }
                     }
-                    // append the located corners to the warp's queues (warp-aggregated, no atomics)
-                    const Rec ob = (Rec)own << 40;
-                    const unsigned b0 = __ballot_sync(FULL, nr >= 1), b1 = __ballot_sync(FULL, nr >= 2);
-                    const unsigned off = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
-                    if (nr >= 1) q[(tail + off) & (TB_QCAP - 1)] = r0 | ob;
-                    if (nr >= 2) q[(tail + off + 1) & (TB_QCAP - 1)] = r1 | ob;
-                    tail += __popc(b0) + __popc(b1);
-                    const unsigned ba = __ballot_sync(FULL, arun != 0);
-                    if (arun)
-                        aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] =
-                            arun | ((unsigned long long)own << 44);
-                    atail += __popc(ba);
+                    // append located corners (C) or pierced lines to the warp's queues
+                    // (warp-aggregated, no atomics)
+                    {
+                        const unsigned bc = __ballot_sync(FULL, r0 != 0);
+                        if (r0) q[(tail + __popc(bc & lt_mask)) & (TB_QCAP - 1)] = r0 | ((Rec)own << 40);
+                        tail += __popc(bc);
+                        const unsigned bp = __ballot_sync(FULL, pline != 0);
+                        if (pline)
+                            pq[(ptail + __popc(bp & lt_mask)) & (TB_PCAP - 1)] = pline | ((unsigned long long)own << 28);
+                        ptail += __popc(bp);
+                    }
                     __syncwarp();
-                    // evaluate full batches (and, after the warp's last items, what is left)
                     const bool last_round = i + 1 == my_rounds;
+                    // Work off the queues in full batches of 32 (after the warp's last items, down to
+                    // empty): facet searches of pierced lines (which feed the D and A queues, when they
+                    // have room), then C / D corners, then runs of A nodes.  One call site each.
 #pragma unroll 1
                     for (;;) {
-                        const unsigned avail = tail - head;
-                        if (avail == 0u || (!last_round && avail < 32u)) break;
-                        if ((unsigned)lane < avail) eval_CD<R, STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
-                        head += avail < 32u ? avail : 32u;
+                        const unsigned pav = ptail - phead, cav = tail - head, aav = atail - ahead;
+                        const bool p_ready = pav >= 32u || (last_round && pav > 0u);
+                        if (p_ready && cav <= TB_QCAP - 64u && aav <= TB_ACAP - 32u) {
+                            Rec d0 = 0, d1 = 0;
+                            unsigned long long arun = 0;
+                            int nr = 0, lown = 0;
+                            if ((unsigned)lane < pav) {
+                                const unsigned long long pr = pq[(phead + lane) & (TB_PCAP - 1)];
+                                lown = (int)((pr >> 28) & ((1u << TB_OWN_BITS) - 1u));
+                                nr = item_line_facets(sh, lown, pr, d0, d1, arun, pc);
+                            }
+                            phead += pav < 32u ? pav : 32u;
+                            const Rec ob = (Rec)lown << 40;
+                            const unsigned b0 = __ballot_sync(FULL, nr >= 1), b1 = __ballot_sync(FULL, nr >= 2);
+                            const unsigned off = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
+                            if (nr >= 1) q[(tail + off) & (TB_QCAP - 1)] = d0 | ob;
+                            if (nr >= 2) q[(tail + off + 1) & (TB_QCAP - 1)] = d1 | ob;
+                            tail += __popc(b0) + __popc(b1);
+                            const unsigned ba = __ballot_sync(FULL, arun != 0);
+                            if (arun)
+                                aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] =
+                                    arun | ((unsigned long long)lown << 44);
+                            atail += __popc(ba);
+                            __syncwarp();
+                            continue;
+                        }
+                        const bool drain = last_round && pav == 0u;
+                        if (cav >= 32u || (drain && cav > 0u)) {
+                            if ((unsigned)lane < cav) eval_CD<R, STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
+                            head += cav < 32u ? cav : 32u;
+                            __syncwarp();
+                            continue;
+                        }
+                        if (aav >= 32u || (drain && aav > 0u)) {
+                            if ((unsigned)lane < aav) eval_A<R, STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
+                            ahead += aav < 32u ? aav : 32u;
+                            __syncwarp();
+                            continue;
+                        }
+                        break;
                     }
-#pragma unroll 1
-                    for (;;) {
-                        const unsigned avail = atail - ahead;
-                        if (avail == 0u || (!last_round && avail < 32u)) break;
-                        if ((unsigned)lane < avail) eval_A<R, STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
-                        ahead += avail < 32u ? avail : 32u;
-                    }
-                    __syncwarp();
                 }
                 // (the next block_scan's barrier orders this phase before the next one)
             }
@@ -719,29 +764,40 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
             } else {
                 __syncthreads();
             }
+            // each warp flushes the boxes of every TB_WARPS-th tetrahedron of the round
 #pragma unroll 1
-            for (int e = tid; e < used_slots; e += TB_THREADS) {
-                const R v = sh->box[e];
-                if (v == R(0)) continue;
-                sh->box[e] = R(0);
-                const int own = upper_index(sh->pre, e);
-                const TetGeo<R>& G = sh->geo[own];
+            for (int t = warp; t < TB_NT; t += TB_WARPS) {
+                const int base = sh->boff[t];
+                if (base < 0) continue;
+                const TetGeo<R>& G = sh->geo[t];
                 const int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
-                const int le = e - sh->boff[own];
-                // le = x + ex (y + ey z)
-                const int r = le / ex;
-                const int x = le - r * ex;
-                const int z = r / ey;
-                const int y = r - z * ey;
-                bool ok = true;
-                const int cx = wrap_axis(G.anchor[0] + x, g.n[0], g.periodic, ok);
-                const int cy = wrap_axis(G.anchor[1] + y, g.n[1], g.periodic, ok);
-                const int cz = wrap_axis(G.anchor[2] + z, g.n[2], g.periodic, ok);
-                if (!ok) continue;
-                double* cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
-                atomicAdd(cell, (double)v);
-                // the piece's share of the closure residual (FP64 atomics are cheap here)
-                if (fp32) atomicAdd(cell, (double)(scale * fabsf((float)v)));
+                const int size = ex * ey * (G.hi[2] + 1);
+                const int ax = G.anchor[0], ay = G.anchor[1], az = G.anchor[2];
+                const float inv_ex = __frcp_rn((float)ex), inv_ey = __frcp_rn((float)ey);
+#pragma unroll 1
+                for (int e = lane; e < size; e += 32) {
+                    const R v = sh->box[base + e];
+                    if (v == R(0)) continue;
+                    sh->box[base + e] = R(0);
+                    // e = x + ex (y + ey z): quotients from float reciprocals, corrected exactly
+                    int r = (int)((float)e * inv_ex);
+                    r += (r + 1) * ex <= e ? 1 : 0;
+                    r -= r * ex > e ? 1 : 0;
+                    const int x = e - r * ex;
+                    int z = (int)((float)r * inv_ey);
+                    z += (z + 1) * ey <= r ? 1 : 0;
+                    z -= z * ey > r ? 1 : 0;
+                    const int y = r - z * ey;
+                    bool ok = true;
+                    const int cx = wrap_axis(ax + x, g.n[0], g.periodic, ok);
+                    const int cy = wrap_axis(ay + y, g.n[1], g.periodic, ok);
+                    const int cz = wrap_axis(az + z, g.n[2], g.periodic, ok);
+                    if (!ok) continue;
+                    double* cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
+                    atomicAdd(cell, (double)v);
+                    // the piece's share of the closure residual (FP64 atomics are cheap here)
+                    if (fp32) atomicAdd(cell, (double)(scale * fabsf((float)v)));
+                }
             }
             // (the next round's block_scan barrier orders the flush before new box writes)
         }

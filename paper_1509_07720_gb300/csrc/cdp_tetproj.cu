@@ -485,6 +485,9 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
                                                    double* __restrict__ out, Counters* __restrict__ ctr,
                                                    TetGeo<R>* __restrict__ geo, int* __restrict__ need,
                                                    int* __restrict__ big_list, long long big_cap, int count) {
+    // the block's records are assembled in shared memory and written out with coalesced stores
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TetGeo<R>* stage = reinterpret_cast<TetGeo<R>*>(smem_raw);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int n_zero = 0, n_single = 0, n_box = 0;
     if (i < nb) {
@@ -518,13 +521,22 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
                     const unsigned at = atomicAdd(&ctr->big_count, 1u);
                     if ((long long)at < big_cap) big_list[at] = (int)s;
                 } else {
-                    tet_setup(S, S.lo, geo[i]);
+                    tet_setup(S, S.lo, stage[threadIdx.x]);
                     my_need = (int)cells;
                     n_box = 1;
                 }
             }
         }
         need[i] = my_need;
+    }
+    __syncthreads();
+    {
+        constexpr int W = sizeof(TetGeo<R>) / 8;
+        const long long first = (long long)blockIdx.x * blockDim.x;
+        const int n = (int)(nb - first < (long long)blockDim.x ? nb - first : (long long)blockDim.x);
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(stage);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(geo + first);
+        for (int w = threadIdx.x; w < n * W; w += blockDim.x) dst[w] = src[w];
     }
     if (count) {
         n_zero = __reduce_add_sync(FULL, n_zero);
@@ -824,6 +836,11 @@ static cudaError_t configure_one() {
 
 cudaError_t configure_tet() {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tet_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(128 * sizeof(TetGeo<float>)))) ||
+        (e = cudaFuncSetAttribute(k_tet_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(128 * sizeof(TetGeo<double>)))))
+        return e;
     if ((e = configure_one<float, false>()) || (e = configure_one<float, true>()) ||
         (e = configure_one<double, false>()))
         return e;
@@ -850,7 +867,7 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
     for (long long s0 = 0; s0 < L.ns; s0 += batch) {
         const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
-        k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(
+        k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, 128 * sizeof(TetGeo<R>), st>>>(
             L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, reinterpret_cast<TetGeo<R>*>(L.geo), L.need,
             L.big_list, L.big_cap, L.stats != nullptr);
         if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);

@@ -439,6 +439,19 @@ __device__ __forceinline__ int wrap_axis(int v, int n, int periodic, bool& ok) {
     return v;
 }
 
+// The FP64 value of a float, assembled from its bits with integer operations (this GPU's FP64
+// pipe, which also converts, runs at a small fraction of the FP32 rate); zero, subnormal and
+// non-finite inputs take the converting instruction.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 // (hi, lo) += v with the rounding error of hi + v kept in lo (Knuth's two-sum, FP32 only)
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     const float s = hi + v;
@@ -786,6 +799,10 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
                 const int size = ex * ey * (G.hi[2] + 1);
                 const int ax = G.anchor[0], ay = G.anchor[1], az = G.anchor[2];
                 const float inv_ex = __frcp_rn((float)ex), inv_ey = __frcp_rn((float)ey);
+                // a box inside the grid needs no wrap: flat index = base + (x n1 + y) n2 + z
+                const bool inside = ax >= 0 && ay >= 0 && az >= 0 && ax + ex <= g.n[0] && ay + ey <= g.n[1] &&
+                                    az + (G.hi[2] + 1) <= g.n[2];
+                const long long cbase = ((long long)ax * g.n[1] + ay) * g.n[2] + az;
 #pragma unroll 1
                 for (int e = lane; e < size; e += 32) {
                     const R v = sh->box[base + e];
@@ -800,15 +817,24 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
                     z += (z + 1) * ey <= r ? 1 : 0;
                     z -= z * ey > r ? 1 : 0;
                     const int y = r - z * ey;
-                    bool ok = true;
-                    const int cx = wrap_axis(ax + x, g.n[0], g.periodic, ok);
-                    const int cy = wrap_axis(ay + y, g.n[1], g.periodic, ok);
-                    const int cz = wrap_axis(az + z, g.n[2], g.periodic, ok);
-                    if (!ok) continue;
-                    double* cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
-                    atomicAdd(cell, (double)v);
-                    // the piece's share of the closure residual (FP64 atomics are cheap here)
-                    if (fp32) atomicAdd(cell, (double)(scale * fabsf((float)v)));
+                    double* cell;
+                    if (inside) {
+                        cell = out + cbase + ((long long)x * g.n[1] + y) * g.n[2] + z;
+                    } else {
+                        bool ok = true;
+                        const int cx = wrap_axis(ax + x, g.n[0], g.periodic, ok);
+                        const int cy = wrap_axis(ay + y, g.n[1], g.periodic, ok);
+                        const int cz = wrap_axis(az + z, g.n[2], g.periodic, ok);
+                        if (!ok) continue;
+                        cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
+                    }
+                    if constexpr (fp32) {
+                        atomicAdd(cell, f32_to_f64((float)v));
+                        // the piece's share of the closure residual (FP64 atomics are cheap here)
+                        atomicAdd(cell, f32_to_f64(scale * fabsf((float)v)));
+                    } else {
+                        atomicAdd(cell, (double)v);
+                    }
                 }
             }
             // (the next round's block_scan barrier orders the flush before new box writes)

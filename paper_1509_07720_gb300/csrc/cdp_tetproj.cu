@@ -36,7 +36,7 @@ namespace {
 
 constexpr int TB_WARPS = 8;                 // warps per block
 constexpr int TB_THREADS = 32 * TB_WARPS;   // threads per block
-constexpr int TB_NT = 16 * TB_WARPS;        // tetrahedra per block chunk (power of two, <= TB_THREADS)
+constexpr int TB_NT = 8 * TB_WARPS;         // tetrahedra per block chunk (power of two, <= TB_THREADS)
 constexpr int TB_QCAP = 128;                // C / D corner records awaiting evaluation, per warp
 constexpr int TB_ACAP = 64;                 // runs of A nodes awaiting evaluation, per warp
 constexpr int TB_PCAP = 64;                 // pierced grid lines awaiting their facet searches, per warp
@@ -44,12 +44,14 @@ constexpr int TB_OWN_BITS = 7;              // tetrahedron-of-chunk index in a q
 constexpr unsigned FULL = 0xffffffffu;
 static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS, "chunk index does not fit");
 
-// largest bounding box (cells) projected by the main kernel, and the block's box slots
+// largest bounding box (cells) projected by the main kernel, and the block's box slots (FP32: sized
+// with the rest of the block's shared memory for three resident blocks per SM)
 constexpr int TB_MAX_CELLS = 1280;
 template <typename R>
 struct BoxCap {
-    static constexpr int value = TB_MAX_CELLS * TB_WARPS;
+    static constexpr int value = sizeof(R) == 4 ? 6144 : TB_MAX_CELLS * TB_WARPS;
 };
+static_assert(BoxCap<float>::value >= TB_MAX_CELLS, "one tetrahedron's box must fit the block's slots");
 
 template <typename R>
 struct TetShared {
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
 }
 
 template <typename R, bool STATS>
-__global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
                   double* __restrict__ out, UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

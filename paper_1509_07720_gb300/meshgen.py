@@ -38,6 +38,9 @@ __all__ = [
     "make_config",
     "random_simplices",
     "CONFIG_NAMES",
+    "smooth_field_3d",
+    "bisection_levels",
+    "bisect_mesh",
 ]
 
 
@@ -220,6 +223,8 @@ CONFIG_NAMES = {
     "c1b": "2D 64^2 Lagrangian squares (8192 triangles), two sine waves a=(0.45, 0.30) (folded), rho=1, 128^2 grid",
     "c2": "3D 32^3 Kuhn cubes (196,608 tets), GRF k^-2 k<=16 rms 0.5 cell, rho=1, 128^3 grid",
     "c3": "3D 128^3 Kuhn cubes (12,582,912 tets), GRF k^-2 k<=16 rms 4 cells, lognormal rho sigma=0.5, 256^3 grid",
+    "c4": "3D undisplaced 64^3 Kuhn base bisected along longest edges to 50,331,953 tets (levels 0-14, "
+          "volumes over 4 decades), lognormal rho sigma=1, 512^3 grid",
 }
 
 
@@ -227,11 +232,97 @@ def _wrap(x: np.ndarray) -> np.ndarray:
     return x - np.floor(x)
 
 
+def smooth_field_3d(pts: np.ndarray, rng, kmax: int = 3) -> np.ndarray:
+    """A seeded smooth periodic field at points [3, N] of the unit box: a sum of the Fourier modes
+    0 < |k| <= kmax with Gaussian amplitudes and uniform phases."""
+    out = np.zeros(pts.shape[1])
+    r = np.arange(-kmax, kmax + 1)
+    for kx in r:
+        for ky in r:
+            for kz in r:
+                k2 = kx * kx + ky * ky + kz * kz
+                if k2 == 0 or k2 > kmax * kmax:
+                    continue
+                amp = rng.standard_normal() / k2
+                ph = rng.uniform(0.0, 2.0 * np.pi)
+                out += amp * np.cos(2.0 * np.pi * (kx * pts[0] + ky * pts[1] + kz * pts[2]) + ph)
+    return out
+
+
+def bisection_levels(field: np.ndarray, target: int, max_level: int = 13, spread: float = 4.0) -> np.ndarray:
+    """Refinement level of every base simplex, floor(c + spread z) clipped to [0, max_level] with z
+    the standardised field; c is the smallest offset (bisection search) for which the refined
+    count sum(2^level) reaches ``target``."""
+    z = (field - field.mean()) / field.std()
+
+    def levels(c):
+        return np.clip(np.floor(c + spread * z), 0, max_level).astype(np.int64)
+
+    lo, hi = -4.0 * spread, float(max_level) + 4.0 * spread
+    if int(np.sum(1 << levels(hi))) < target:
+        raise ValueError("target count out of reach")
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if int(np.sum(1 << levels(mid))) >= target:
+            hi = mid
+        else:
+            lo = mid
+    return levels(hi)
+
+
+def bisect_mesh(q: np.ndarray, tets: np.ndarray, levels: np.ndarray):
+    """Non-conforming longest-edge bisection on the periodic unit box.  Base tetrahedron b is split
+    levels[b] times: each split cuts a tetrahedron through the midpoint of its longest edge (ties to
+    the first edge in the order (0,1), (0,2), (0,3), (1,2), (1,3), (2,3)) into two children, and
+    every split makes its own midpoint vertex (hanging nodes are allowed).  Returns
+    (positions [3, Nv] in [0, 1), tetrahedra [Ns, 4] int32, number of base vertices)."""
+    nbase = q.shape[1]
+    total_new = int(np.sum((1 << levels.astype(np.int64)) - 1))
+    pos = np.empty((3, nbase + total_new))
+    pos[:, :nbase] = q
+    nv = nbase
+    done = []
+    cur = tets.astype(np.int64)
+    lev = levels.astype(np.int64)
+    ea = np.array([0, 0, 0, 1, 1, 2])
+    eb = np.array([1, 2, 3, 2, 3, 3])
+    # the two vertices off each edge
+    ep = np.array([2, 1, 1, 0, 0, 0])
+    eq = np.array([3, 3, 2, 3, 2, 1])
+    while cur.shape[0]:
+        split = lev > 0
+        done.append(cur[~split])
+        t = cur[split]
+        left = lev[split] - 1
+        if t.shape[0] == 0:
+            break
+        x = pos[:, t]                           # [3, n, 4]
+        d = x - x[:, :, :1]
+        d -= np.round(d)                        # minimal image relative to vertex 0
+        xu = x[:, :, :1] + d
+        e2 = np.stack([np.sum((xu[:, :, eb[e]] - xu[:, :, ea[e]]) ** 2, axis=0) for e in range(6)], axis=1)
+        e = np.argmax(e2, axis=1)
+        rows = np.arange(t.shape[0])
+        a, b = t[rows, ea[e]], t[rows, eb[e]]
+        p, r = t[rows, ep[e]], t[rows, eq[e]]
+        mid = 0.5 * (xu[:, rows, ea[e]] + xu[:, rows, eb[e]])
+        m = np.arange(nv, nv + t.shape[0])
+        pos[:, m] = _wrap(mid)
+        nv += t.shape[0]
+        c1 = np.stack([a, m, p, r], axis=1)
+        c2 = np.stack([m, b, p, r], axis=1)
+        cur = np.concatenate([c1, c2])
+        lev = np.concatenate([left, left])
+    out = np.concatenate(done).astype(np.int32)
+    return pos[:, :nv], out, nbase
+
+
 def make_config(name: str, scale: int | None = None) -> Mesh:
     """Build one named workload.
 
-    c1a/c1b: 2D sine-wave meshes; c2/c3: 3D random-field meshes. ``scale`` overrides the
-    Lagrangian lattice size n (the grid keeps the same ratio to n), for reduced test cases.
+    c1a/c1b: 2D sine-wave meshes; c2/c3: 3D random-field meshes; c4: a bisected (adaptive) 3D mesh.
+    ``scale`` overrides the Lagrangian lattice size n (the grid keeps the same ratio to n), for
+    reduced test cases.
     """
     if name in ("c1a", "c1b"):
         n = scale or 64
@@ -257,6 +348,23 @@ def make_config(name: str, scale: int | None = None) -> Mesh:
         rho = lognormal_density(q.shape[1], 0.5, rng)
         g = 2 * n
         return Mesh(x, tets, rho, (g, g, g), (0.0,) * 3, (1.0,) * 3, True, name)
+    if name == "c4":
+        # undisplaced n^3 Kuhn base (vertices on grid nodes and planes), bisected to 32x the base
+        # count with refinement levels 0..14 (volumes over 4 decades) set by a smooth seeded field,
+        # lognormal(1) densities
+        n = scale or 64
+        rng = np.random.default_rng(1004)
+        q, tets = kuhn_mesh_3d(n)
+        # base centroids, at the minimal image of vertex 0
+        x = q[:, tets]
+        d = x - x[:, :, :1]
+        d -= np.round(d)
+        cen = _wrap(x[:, :, 0] + d.mean(axis=2))
+        lev = bisection_levels(smooth_field_3d(cen, rng), 32 * tets.shape[0], max_level=14, spread=7.0)
+        pos, t2, _ = bisect_mesh(q, tets, lev)
+        rho = lognormal_density(pos.shape[1], 1.0, rng)
+        g = 8 * n
+        return Mesh(pos, t2, rho, (g, g, g), (0.0,) * 3, (1.0,) * 3, True, name)
     raise ValueError(f"unknown workload {name!r}")
 
 

@@ -136,6 +136,32 @@ def test_tiling_smooth_periodic_3d():
     assert np.max(np.abs(m * 12 ** 3 - 1.0)) < 1e-13
 
 
+def test_tiling_bisected_mesh():
+    """The bisected adaptive mesh (workload c4 at base 4^3: hanging nodes, volumes over 3-4 decades,
+    vertices on grid planes) still partitions the periodic box: with rho = 1 every cell gets h^3,
+    and the simplex volumes add up to the box volume."""
+    m = mg.make_config("c4", 4)
+    ones = mg.Mesh(m.pos, m.simplices, np.ones(m.n_verts), m.grid, m.box_lo, m.box_len, True)
+    vol = oracle.simplex_mass(ones)
+    assert abs(vol.sum() - 1.0) < 1e-14
+    assert vol.max() / vol.min() >= 2 ** 11
+    cm = oracle.project(ones)
+    assert np.max(np.abs(cm * 32 ** 3 - 1.0)) < 1e-12
+
+
+def test_bisection_generator_counts():
+    """The level rule reaches its target count exactly as sum(2^level), and every split adds one
+    vertex and one simplex."""
+    q, tets = mg.kuhn_mesh_3d(4)
+    rng = np.random.default_rng(3)
+    lev = mg.bisection_levels(rng.standard_normal(tets.shape[0]), 8 * tets.shape[0], max_level=6, spread=2.0)
+    assert int(np.sum(1 << lev.astype(np.int64))) >= 8 * tets.shape[0]
+    pos, t2, nb = mg.bisect_mesh(q, tets, lev)
+    assert t2.shape[0] == int(np.sum(1 << lev.astype(np.int64)))
+    assert pos.shape[1] - nb == t2.shape[0] - tets.shape[0]
+    assert np.all((pos >= 0) & (pos < 1))
+
+
 def test_tiling_sine_waves_2d():
     """Workload c1a (two sine waves, single stream): h^2 in every cell."""
     mesh = mg.make_config("c1a")

@@ -61,6 +61,8 @@ def _cases():
         "c1b": mg.make_config("c1b"),
         "c2_16": mg.make_config("c2", 16),
         "c2": mg.make_config("c2"),
+        "c4_4": mg.make_config("c4", 4),
+        "c4_8": mg.make_config("c4", 8),
         "rand3d_small": mg.random_simplices(3, 500, 16, 0.7, rng),
         "rand3d_mid": mg.random_simplices(3, 500, 16, 2.5, rng),
         "rand3d_tiled": mg.random_simplices(3, 40, 32, 9.0, rng),
@@ -170,3 +172,37 @@ def test_headline_workload_sampled(proj, prec):
     tot = oracle.simplex_mass(mesh).sum()
     rel = abs(got.sum() - tot) / tot
     assert rel <= TOTAL_TOL, f"total mass rel error {rel:.3e}"
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
+def test_adaptive_workload_sampled(proj, prec):
+    """Full-size bisected mesh (50.3M tets, volumes over 4 decades, hanging nodes, base vertices on
+    grid planes) on a 512^3 grid: sampled cells against the oracle, total mass against the simplex
+    masses, and the same corner decisions in both precisions."""
+    mesh = _c4_full()
+    got, st = _run(proj, mesh, prec, stats=True)
+    assert st["error_flags"] == 0
+    rng = np.random.default_rng(98)
+    cells = rng.choice(got.size, 256, replace=False)
+    cells = np.unique(np.concatenate([cells, np.argsort(got.ravel())[-32:]]))
+    ref = oracle.project_cells(mesh, cells)
+    scale = float(np.max(got))
+    err = np.max(np.abs(got.ravel()[cells] - ref)) / scale
+    assert err <= TOL[prec], f"sampled max rel error {err:.3e}"
+    tot = oracle.simplex_mass(mesh).sum()
+    rel = abs(got.sum() - tot) / tot
+    assert rel <= TOTAL_TOL, f"total mass rel error {rel:.3e}"
+    _C4_STATS[prec] = st
+    if len(_C4_STATS) == 2:
+        for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell", "n_small", "n_large"):
+            assert _C4_STATS[0][k] == _C4_STATS[1][k], k
+
+
+_C4 = {}
+_C4_STATS = {}
+
+
+def _c4_full():
+    if "m" not in _C4:
+        _C4["m"] = mg.make_config("c4")
+    return _C4["m"]

@@ -41,6 +41,10 @@ __all__ = [
     "smooth_field_3d",
     "bisection_levels",
     "bisect_mesh",
+    "StepProblem",
+    "simplex_volumes",
+    "make_batch",
+    "cfl_dt",
 ]
 
 
@@ -366,6 +370,64 @@ def make_config(name: str, scale: int | None = None) -> Mesh:
         g = 8 * n
         return Mesh(pos, t2, rho, (g, g, g), (0.0,) * 3, (1.0,) * 3, True, name)
     raise ValueError(f"unknown workload {name!r}")
+
+
+@dataclasses.dataclass
+class StepProblem:
+    """One problem of the batched time step: the mesh (rho is recomputed by the step from the
+    simplex masses), vertex velocities [D, Nv] (box units per time) and simplex masses [Ns]."""
+
+    mesh: Mesh
+    vel: np.ndarray
+    masses: np.ndarray
+
+
+def simplex_volumes(mesh: Mesh) -> np.ndarray:
+    """|V| of every simplex at the minimal image of its vertex 0 (world units)."""
+    p = mesh.pos[:, mesh.simplices]
+    e = p[:, :, 1:] - p[:, :, :1]
+    L = np.asarray(mesh.box_len, dtype=np.float64)[:, None, None]
+    e -= np.round(e / L) * L
+    if mesh.dim == 3:
+        return np.abs(np.einsum("in,in->n", e[:, :, 0], np.cross(e[:, :, 1].T, e[:, :, 2].T).T)) / 6.0
+    return np.abs(e[0, :, 0] * e[1, :, 1] - e[1, :, 0] * e[0, :, 1]) / 2.0
+
+
+def make_batch(name: str = "c5", count: int = 64, ns_range=(1e3, 2e6)) -> list:
+    """The batched workload: ``count`` independent problems, dimension alternating 3D / 2D, simplex
+    counts log-uniform in ``ns_range`` (rounded to a Lagrangian lattice), grids drawn from
+    {64, 128, 256}^D, seeded GRF (3D, rms 0.5 Lagrangian cell) or two-sine (2D) displacements.
+    Every simplex carries the mass of a unit density over its displaced volume, and the vertices
+    move with the displacement itself as velocity (growth rate 1), so the step's densities start
+    near 1 where the sheet is single-stream."""
+    if name != "c5":
+        raise ValueError(f"unknown batch {name!r}")
+    rng = np.random.default_rng(1005)
+    out = []
+    for i in range(count):
+        dim = 3 if i % 2 == 0 else 2
+        ns = math.exp(rng.uniform(math.log(ns_range[0]), math.log(ns_range[1])))
+        g = int(rng.choice([64, 128, 256]))
+        if dim == 3:
+            n = max(2, int(round((ns / 6.0) ** (1.0 / 3.0))))
+            q, simp = kuhn_mesh_3d(n)
+            psi = grf_displacement(n, 3, 0.5, 16.0, rng)
+        else:
+            n = max(2, int(round(math.sqrt(ns / 2.0))))
+            q, simp = square_mesh_2d(n)
+            a1, a2 = rng.uniform(0.02, 0.12, size=2)
+            psi = sine_displacement_2d(q, a1, a2) - q
+        x = _wrap(q + psi)
+        mesh = Mesh(x, simp, np.ones(x.shape[1]), (g,) * dim, (0.0,) * dim, (1.0,) * dim, True, f"c5[{i}]")
+        out.append(StepProblem(mesh, np.ascontiguousarray(psi), simplex_volumes(mesh)))
+    return out
+
+
+def cfl_dt(problems, courant: float = 0.25) -> float:
+    """Common time step: courant x (smallest cell) / (largest vertex speed), 1e-3 if all are at rest."""
+    vmax = max(float(np.max(np.abs(p.vel))) for p in problems)
+    h = min(min(p.mesh.box_len[a] / p.mesh.grid[a] for a in range(p.mesh.dim)) for p in problems)
+    return courant * h / vmax if vmax > 0 else 1e-3
 
 
 def random_simplices(dim: int, ns: int, grid: int, size: float, rng, periodic: bool = True,

@@ -134,3 +134,40 @@ def test_graph_replay_matches_eager(ctx):
         assert np.max(_periodic_diff(sa[0], sb[0])) <= 1e-13
         for x, y in zip(sa[1:], sb[1:]):
             assert np.max(np.abs(x - y)) <= 1e-11 * max(1e-300, np.max(np.abs(y)))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
+def test_batched_workload_c5(ctx, prec):
+    """The batched workload (64 problems, 2D and 3D, 18.3M simplices, grids 64..256 per axis) in one
+    graph-captured step.  Every problem: the projected total equals the simplex masses of the
+    drifted mesh at the step's own vertex densities.  The six smallest problems: the whole step
+    against the oracle composition (FP64 strictly, FP32-mixed to its projection tolerance)."""
+    import paper_1509_07720_gb300 as pkg
+
+    batch = mg.make_batch("c5")
+    dt = mg.cfl_dt(batch)
+    devs = [_Dev(p.mesh, p.vel, p.masses) for p in batch]
+    arr = (pkg.cdp_step_problem * len(devs))(*[d.sp for d in devs])
+    st = torch.cuda.current_stream().cuda_stream
+    assert pkg.cdp_step_batched(ctx, arr, prec, dt, FPG, 1, st) == 0
+    torch.cuda.synchronize()
+    small = set(np.argsort([p.mesh.n_simplices for p in batch])[:6].tolist())
+    for i, (p, d) in enumerate(zip(batch, devs)):
+        m = p.mesh
+        gp, gv, grho, gcm, gphi, gacc = d.state()
+        pos_mid = solver.drift(m.pos, p.vel, 0.5 * dt, m.box_lo, m.box_len)
+        want_tot = oracle.simplex_mass(mg.Mesh(pos_mid, m.simplices, grho, m.grid, m.box_lo, m.box_len, True)).sum()
+        assert abs(gcm.sum() - want_tot) <= 1e-12 * want_tot, f"problem {i}"
+        if i not in small:
+            continue
+        p2, v2, rho, cm, phi, acc = _oracle_step(m, p.vel, p.masses, dt)
+        assert np.max(np.abs(grho - rho)) <= 1e-12 * np.max(rho), f"problem {i}"
+        if prec == 0:
+            assert np.max(np.abs(gcm - cm)) <= 1e-11 * np.max(cm), f"problem {i}"
+            assert np.max(np.abs(gphi - phi)) <= 1e-10 * np.max(np.abs(phi)), f"problem {i}"
+            assert np.max(np.abs(gacc - acc)) <= 1e-9 * np.max(np.abs(acc)), f"problem {i}"
+            assert np.max(np.abs(gv - v2)) <= 1e-9 * np.max(np.abs(v2)), f"problem {i}"
+        else:
+            assert np.max(np.abs(gcm - cm)) <= 1e-5 * np.max(cm), f"problem {i}"
+            assert np.max(np.abs(gphi - phi)) <= 1e-4 * np.max(np.abs(phi)), f"problem {i}"
+        assert np.max(_periodic_diff(gp, p2)) <= 1e-9, f"problem {i}"

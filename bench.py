@@ -38,10 +38,10 @@ UNIT = "tets/s"
 # product (3) = 42 flops each; the type-A closed form is 12 flops.
 FLOPS_PER_INCIDENCE = {"a": 12, "b": 252, "c": 252, "d": 252}
 # DRAM bytes (read + write) of one k_project_tet<float> launch per tetrahedron, from the ncu capture
-# summarised in profiles/k_project_tet_c3s64_full.md (1,572,864 tetrahedra, 754.0 MB); the traffic
-# is the geometry records plus vertex gathers, so it scales with the tetrahedron count.  Set to
-# None when the kernel changes until a new capture is taken.
-TRAFFIC_BYTES_PER_TET = 754.0e6 / 1572864
+# summarised in profiles/k_project_tet_c3s64_full.md; the traffic is the geometry records plus the
+# grid atomics, so it scales with the tetrahedron count.  None while the kernel has changed since
+# the capture.
+TRAFFIC_BYTES_PER_TET = None
 # ALU peaks derived from unit counts and the maximum SM clock (no measured FP32 figure exists):
 # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 1.25 TFLOP/s nominal.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -63,11 +63,11 @@ def _args():
 
 
 def _batched_step(pkg, mg, proj, dev, stream, steps=3, warmup=3):
-    import torch
-
     """The batched workload c5: 64 independent 2D/3D problems advanced by one time step each (drift,
     vertex density, FP32-mixed projection, FFT Poisson, force, kick, drift) as one replayed CUDA
     graph.  Inputs resident on the device; CUDA events around the replays."""
+    import torch
+
     batch = mg.make_batch("c5")
     dt = mg.cfl_dt(batch)
     keep = []
@@ -356,13 +356,14 @@ def run_ours(a):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the tetrahedron projection kernel); its incidences are all
-    # corners but those of the FP64 large-simplex pass
-    names = ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>",
-             "k_project_warp<3,double> (large-simplex pass)"]
-    dom = int(np.argmax(kern32[:3]))
+    # roofline of the dominant kernel (the tetrahedron projection kernel, which also tiles the large
+    # tetrahedra: its incidences are all corners)
+    names = ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>"]
+    kern32 = kern32[:3]
+    kern64 = kern64[:3]
+    dom = int(np.argmax(kern32))
     if dom == 2:
-        inc = {k: st32["corners_" + k] - st32["large_corners"][i] for i, k in enumerate("abcd")}
+        inc = {k: st32["corners_" + k] for k in "abcd"}
     else:
         inc = None
     if inc is not None:
@@ -396,7 +397,7 @@ def run_ours(a):
                                          "n_small", "n_large", "n_zero_volume", "exact_fallbacks")},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 4 * a.steps,  # vertex records, set-up, main kernel, large-simplex pass
+        "gpu_launches": 3 * a.steps,  # vertex records, set-up, main kernel (one batch: <= 2^24 tets)
         "e2e": e2e,
     }
     if not a.no_batched:

@@ -92,14 +92,16 @@ typedef struct {
     uint64_t n_zero_volume;   /* simplices of zero volume (no contribution) */
     uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
     uint64_t n_small;         /* simplices projected by the main kernel (3D: bounding box <= 1280 cells) */
-    uint64_t n_large;         /* tetrahedra with a larger bounding box: projected by the FP64 large-simplex pass */
-    uint64_t n_large_tiles;   /* always 0 (reserved) */
+    uint64_t n_large;         /* tetrahedra with a larger bounding box: projected tile by tile (18^3 cells)
+                                 by the main kernel after its chunks */
+    uint64_t n_large_tiles;   /* tiles of those tetrahedra */
     uint64_t corners_a;       /* (corner, cell) incidences of type A: grid node inside a simplex */
     uint64_t corners_b;       /* type B: simplex vertex */
     uint64_t corners_c;       /* type C: simplex edge x cell face */
     uint64_t corners_d;       /* type D: simplex facet x cell edge (3D) */
     uint64_t exact_fallbacks; /* predicate evaluations decided by the exact integer stage */
-    uint64_t large_corners[4];/* the part of corners_a..d found by the large-simplex pass (A, B, C, D) */
+    uint64_t large_corners[4];/* the part of corners_a..d found on the tiles of the large tetrahedra (A, B, C, D);
+                                 a corner on a tile face is evaluated, and counted, in each tile it touches */
     uint32_t error_flags;     /* bit 0 bad index, bit 1 non-finite, bit 2 extent */
     uint32_t reserved;
 } cdp_stats;
@@ -215,7 +217,7 @@ CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 /* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 4:
  * [0] vertex records, [1] per-simplex set-up (3D: the first batch's; the single-cell closed form
  * is applied there), [2] main projection kernel (3D: with the set-up of any later batch),
- * [3] FP64 large-simplex pass (3D).  *calls receives the number of timed cdp_project calls.
+ * [3] always ~0 (kept for the layout: the large tetrahedra are projected inside the main kernel).  *calls receives the number of timed cdp_project calls.
  * Returns the number of slots written. */
 CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
 

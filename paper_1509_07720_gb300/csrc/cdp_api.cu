@@ -180,7 +180,6 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     int fp32 = precision == CDP_FP32_MIXED;
     // a persistent grid: every resident block slot of the device, four times over
     L.small_blocks_per_sm = 4 * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
-    L.big_blocks_per_sm = c->blocks_large;
     L.big_list = c->queue;
     L.big_cap = (long long)c->queue_cap;
     L.geo = c->geo;
@@ -243,7 +242,7 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     stats->n_single_cell = c->h_ctr->n_class0;
     stats->n_small = c->h_ctr->n_small;
     stats->n_large = c->h_ctr->big_count;
-    stats->n_large_tiles = 0;
+    stats->n_large_tiles = c->h_ctr->n_big_tiles;
     const cdp::UnitCounts& s0 = c->h_stats[0];
     const cdp::UnitCounts& s1 = c->h_stats[1];
     stats->corners_a = s0.a + s1.a;
@@ -251,7 +250,7 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     stats->corners_c = s0.c + s1.c;
     stats->corners_d = s0.d + s1.d;
     stats->exact_fallbacks = s0.exact + s1.exact;
-    stats->large_corners[0] = s1.a;  // found by the FP64 large-simplex pass
+    stats->large_corners[0] = s1.a;  // found on the tiles of the large tetrahedra
     stats->large_corners[1] = s1.b;
     stats->large_corners[2] = s1.c;
     stats->large_corners[3] = s1.d;
@@ -325,7 +324,6 @@ int cdp_create(cdp_ctx** out, int device) {
     c->blocks_small[1] = cdp::resident_blocks(3, 1);
     c->blocks_big[0] = cdp::resident_blocks(2, 0);
     c->blocks_big[1] = cdp::resident_blocks(2, 1);
-    c->blocks_large = cdp::resident_blocks_large();
     if (cudaMalloc(&c->ctr, sizeof(cdp::Counters)) != cudaSuccess ||
         cudaMalloc(&c->stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess ||
         cudaMallocHost(&c->h_ctr, sizeof(cdp::Counters)) != cudaSuccess ||

@@ -35,10 +35,9 @@ struct cdp_ctx {
     int num_sms;
     int blocks_small[2];  // resident blocks per SM of the 3D kernel (fp64, fp32)
     int blocks_big[2];    // of the 2D kernel
-    int blocks_large;     // of the FP64 large-simplex pass
     cdp::VertexRec* verts;
     size_t verts_cap;
-    int* queue;           // list of the tetrahedra for the large-simplex pass
+    int* queue;           // list of the large tetrahedra (tiled by the main kernel)
     size_t queue_cap;
     unsigned char* geo;   // geometry records of one batch of tetrahedra (bytes)
     size_t geo_cap;
@@ -49,7 +48,7 @@ struct cdp_ctx {
     cdp::Counters* h_ctr;     // pinned host mirrors
     cdp::UnitCounts* h_stats;
     // per-kernel timing: CDP_TEV events per timed call (before the vertex records, after them,
-    // after the set-up kernel, after the main kernel, after the large-simplex pass), folded into
+    // after the set-up kernel, after the main kernel, and once more at the end), folded into
     // totals[CDP_TEV - 1] when read
     int timing;
     std::vector<cudaEvent_t>* pending;

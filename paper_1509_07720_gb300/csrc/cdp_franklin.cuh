@@ -233,8 +233,9 @@ CDP_HD float low_part<float>(i64 L, float hi) {
 template <>
 CDP_HD double low_part<double>(i64, double) { return 0.0; }
 
-// Fill the working set for the tile whose lowest cell is T (relative to the anchor).
-template <typename R>
+// Fill the working set for the tile whose lowest cell is T (relative to the anchor).  COPY only
+// gives a caller its own out-of-line instance (register allocation of its own).
+template <typename R, int COPY = 0>
 CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
     for (int k = 0; k < 4; ++k)
         for (int a = 0; a < 3; ++a) {

@@ -69,7 +69,8 @@ CDP_HD bool unwrap(i64& d, int n, int periodic) {
 }
 
 // Canonical tetrahedron from its 4 vertex records.  Returns 0 (ok), 1 (zero volume: contributes
-// nothing) or an error flag.
+// nothing) or an error flag.  COPY only gives a caller its own out-of-line instance.
+template <int COPY = 0>
 CDP_COLD unsigned canon_tet(const GridDesc& g, const VertexRec* v[4], Tet& S) {
     const i64 lim = (i64)CDP_MAX_EXTENT << CDP_Q;
     for (int a = 0; a < 3; ++a) {

@@ -1,6 +1,6 @@
 // Projection entry point that allocates nothing (declared in include/coldproj.h as
 // cdp_project_noalloc).  Its scratch (the per-call counters, the vertex records, the list of the
-// large-simplex pass and the geometry records of one batch of tetrahedra) is one
+// large tetrahedra and the geometry records of one batch of tetrahedra) is one
 // statically sized device array of this module instead of context-owned memory; the kernels are
 // the ones cdp_project launches.
 #include <cuda_runtime.h>
@@ -29,7 +29,7 @@ constexpr size_t kGeoOffset = (kNeedOffset + (size_t)kGeoBatch * sizeof(int) + 2
 constexpr size_t kScratchBytes = kGeoOffset + (size_t)kGeoBatch * kGeoRec;
 static_assert(sizeof(cdp::Counters) <= kCounterBytes, "counters do not fit their slot");
 
-// [counters | vertex records | large-simplex list | box sizes | geometry records of one batch];
+// [counters | vertex records | list of large tetrahedra | box sizes | geometry records of one batch];
 // shared by every call on the device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -41,7 +41,6 @@ struct DeviceSetup {
     unsigned char* scratch;
     int num_sms;
     int blocks[2][2];  // [dim == 3][fp32]: resident blocks per SM of the projection kernel
-    int blocks_large;  // of the FP64 large-simplex pass
 };
 
 DeviceSetup g_setup[kMaxDevices];
@@ -67,7 +66,6 @@ int setup_device(int dev, DeviceSetup** out) {
         s.num_sms = sms;
         for (int d3 = 0; d3 < 2; ++d3)
             for (int f = 0; f < 2; ++f) s.blocks[d3][f] = cdp::resident_blocks(d3 ? 3 : 2, f);
-        s.blocks_large = cdp::resident_blocks_large();
         s.ready = true;
     }
     *out = &s;
@@ -121,7 +119,6 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     L.num_sms = s->num_sms;
     int fp32 = precision == CDP_FP32_MIXED;
     L.small_blocks_per_sm = 4 * s->blocks[p->dim == 3][fp32];
-    L.big_blocks_per_sm = s->blocks_large;
     L.big_list = (int*)(s->scratch + kListOffset);
     L.big_cap = kMaxSimplices;
     L.need = (int*)(s->scratch + kNeedOffset);

@@ -538,20 +538,7 @@ cudaError_t configure_all() {
     if ((e = cudaFuncSetAttribute(k_project_warp<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)shared_bytes<2, double>())))
         return e;
-    if ((e = cudaFuncSetAttribute(k_project_warp<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)shared_bytes<3, double>())))
-        return e;
     return configure_tet();
-}
-
-int resident_blocks_large() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_warp<3, double>, CDP_WBLOCK,
-                                                      shared_bytes<3, double>()) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    return n > 0 ? n : 1;
 }
 
 int resident_blocks(int dim, int fp32) {
@@ -584,15 +571,6 @@ static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t 
     return cudaGetLastError();
 }
 
-// FP64 pass over the tetrahedra the main kernel listed (their number is read on the device)
-static cudaError_t launch_large(const LaunchArgs& L, cudaStream_t st) {
-    long long blocks = (long long)L.num_sms * (L.big_blocks_per_sm > 0 ? L.big_blocks_per_sm : 1);
-    k_project_warp<3, double><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<3, double>(), st>>>(
-        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats ? L.stats + 1 : nullptr, L.big_list,
-        L.big_cap);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
                         const double* rho, cudaStream_t st) {
     if (L.nv > 0) {
@@ -611,9 +589,8 @@ cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaE
     }
     if (L.g.dim == 3) {
         cudaError_t e = launch_tet(L, fp32, st, after_setup);
-        if (e != cudaSuccess) return e;
         if (mid) cudaEventRecord(mid, st);
-        return launch_large(L, st);
+        return e;
     }
     if (after_setup) cudaEventRecord(after_setup, st);
     return fp32 ? launch_dim<2, float>(L, st, mid) : launch_dim<2, double>(L, st, mid);

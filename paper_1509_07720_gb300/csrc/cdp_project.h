@@ -16,8 +16,8 @@ constexpr int CDP_QCAP = 512;     // per-warp queue of (corner, cell) records (p
 // Per-call device counters (zeroed at the start of every projection).
 struct Counters {
     unsigned flags;       // CDP_FLAG_* bits
-    unsigned big_count;   // tetrahedra listed for the large-simplex pass
-    unsigned big_next;    // (unused)
+    unsigned big_count;   // tetrahedra listed as large (bounding box above the main kernel's box)
+    unsigned big_next;    // next entry of that list to be tiled by the main kernel's blocks
     unsigned pad;
     unsigned long long n_class0, n_small, n_zero, n_big_tiles;
 };
@@ -31,11 +31,11 @@ struct LaunchArgs {
     double cellvol;
     int* queue;
     Counters* ctr;
-    UnitCounts* stats;  // may be null (else two blocks: main kernel, large-simplex pass)
+    UnitCounts* stats;  // may be null (else two blocks: chunks of the main kernel, tiled large tetrahedra)
     int num_sms;
     int small_blocks_per_sm;
-    int big_blocks_per_sm;
-    int* big_list;      // tetrahedra whose bounding box exceeds the shared box (capacity big_cap)
+    int* big_list;      // tetrahedra whose bounding box exceeds the shared box (capacity big_cap),
+                        // projected tile by tile by the main kernel
     long long big_cap;
     void* geo;          // geometry records of one batch of tetrahedra (capacity geo_cap records)
     int* need;          // their box sizes (geo_cap entries)
@@ -45,8 +45,6 @@ struct LaunchArgs {
 cudaError_t configure_all();
 // resident blocks per SM of the projection kernel of dimension `dim` (occupancy calculator)
 int resident_blocks(int dim, int fp32);
-// resident blocks per SM of the FP64 large-simplex pass (3D)
-int resident_blocks_large();
 // the tetrahedron kernel (cdp_tetproj.cu)
 cudaError_t configure_tet();
 int resident_blocks_tet(int fp32);
@@ -57,8 +55,8 @@ size_t tet_geo_bytes(int fp32);
 cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup);
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
                         const double* rho, cudaStream_t st);
-// `after_setup` and `mid` (optional) are recorded after the (first) set-up kernel and between the
-// main kernel and the large-simplex pass
+// `after_setup` and `mid` (optional) are recorded after the (first) set-up kernel and after the
+// main kernel
 cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,
                            cudaEvent_t mid);
 

@@ -2,8 +2,8 @@
 //
 // k_tet_setup: one thread per tetrahedron canonicalises it (exact orientation, periodic unwrap,
 // cells), deposits a tetrahedron inside one cell at once (Algorithm 2, step 1), lists one whose
-// bounding box exceeds TB_MAX_CELLS for the FP64 large-simplex pass, and writes the geometry
-// record of every other one to HBM.
+// bounding box exceeds TB_MAX_CELLS as large, and writes the geometry record of every other one to
+// HBM.
 //
 // k_project_tet<R> is a persistent block-cooperative kernel.  A block takes TB_NT consecutive
 // tetrahedra, copies their records into shared memory and gives each a dense box of per-cell
@@ -21,10 +21,18 @@
 // the end of the round the boxes are flushed with one FP64 global atomic per non-zero
 // (tetrahedron, cell) piece.
 //
+// Once its chunks are done, a block takes the large tetrahedra of the list one at a time and
+// projects each in tiles of 18^3 cells: one unit per tile, its record set up in the tile's frame,
+// its items (planes, lines, vertices) clipped to the tile, its box flushed by the whole block.
+// A corner on a tile face is evaluated in both tiles, each keeping the cells of its own.
+//
 // FP32-mixed path only: the mass closure (not in the paper).  The FP64 closed-form masses of the
 // tetrahedra of a round minus the (two-float, exact enough) sum of their FP32 pieces is spread over
 // those pieces in proportion to their magnitude, so the total mass is exact to FP64 rounding and
-// no piece moves by more than about the FP32 rounding of the pieces themselves.
+// no piece moves by more than about the FP32 rounding of the pieces themselves.  A tiled
+// tetrahedron is closed on its own, in two passes over its tiles: the first only sums the pieces,
+// the second flushes them with the closure scale and adds what its rounded pieces still miss, in
+// FP64, to the cell of vertex 0.
 #include <cuda_runtime.h>
 
 #include "cdp_mesh.cuh"
@@ -53,6 +61,16 @@ struct BoxCap {
 };
 static_assert(BoxCap<float>::value >= TB_MAX_CELLS, "one tetrahedron's box must fit the block's slots");
 
+// Tiling state of a block's current large tetrahedron: uniform over the block, written by thread 0
+// only, between barriers.
+struct BigState {
+    int ext[3], nt[3];  // bounding-box extent (cells) and tiles along each axis
+    int ntiles, tile;   // tiles, next tile; ntiles < 0: the list is exhausted
+    int pass;           // FP32 path: 0 sums the tiles' pieces, 1 flushes them (FP64 path: always 1)
+    float scale;        // closure scale of the flush pass
+    float s[3];         // sum of the pieces as two floats (hi, lo) and the sum of their magnitudes
+};
+
 template <typename R>
 struct TetShared {
     TetGeo<R> geo[TB_NT];
@@ -62,6 +80,11 @@ struct TetShared {
     unsigned long long pq[TB_WARPS][TB_PCAP];  // pierced lines awaiting their facet searches
     unsigned short xcum[TB_NT][18];  // running count of the crossings of the (edge, axis) pairs
     int boff[TB_NT];                 // first box slot of each tetrahedron of the round
+    int lr[TB_NT][6];                // grid-line ranges of each unit (unit_line_ranges: r0[3], n[3])
+    int td[TB_NT][3];                // box (tile) dimensions of each unit: its bounding box, or one tile
+                                     // of a tetrahedron whose bounding box exceeds TB_MAX_CELLS
+    Tet big;                         // the large tetrahedron being tiled
+    BigState bs;                     // its tiling state
     int pre[TB_NT];                  // inclusive prefix of the current phase's item counts; in the
                                      // flush, of the round's box sizes
     int wsum[TB_WARPS];              // block-scan scratch
@@ -73,8 +96,7 @@ struct TetShared {
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void box_add(TetShared<R>* sh, int own, int x, int y, int z, R v) {
-    const TetGeo<R>& G = sh->geo[own];
-    const int ex = G.hi[0] + 1, ey = G.hi[1] + 1, ez = G.hi[2] + 1;
+    const int ex = sh->td[own][0], ey = sh->td[own][1], ez = sh->td[own][2];
     if ((unsigned)x < (unsigned)ex && (unsigned)y < (unsigned)ey && (unsigned)z < (unsigned)ez)
         atomicAdd(&sh->box[sh->boff[own] + x + ex * (y + ey * z)], v);
 }
@@ -224,11 +246,55 @@ __device__ __forceinline__ int facet_line_cell_regs(const TetGeo<R>& G, int f, i
     return m;
 }
 
+// Grid lines of a unit: along every axis a, the grid points strictly inside the bounding box
+// (lo_a, hi_a] clipped to the unit's box [0, td_a]: first point r0[a], count n[a].
+template <typename R>
+__device__ __forceinline__ void unit_line_ranges(const TetGeo<R>& G, const int td[3], int r0[3], int n[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lo = G.lo[a] + 1 > 0 ? G.lo[a] + 1 : 0;
+        const int hi = G.hi[a] < td[a] ? G.hi[a] : td[a];
+        r0[a] = lo;
+        n[a] = hi >= lo ? hi - lo + 1 : 0;
+    }
+}
+
+// Item counts of a unit (its crossings per (edge, axis) pair, as running counts in xcum, and its
+// grid lines, whose ranges go to lr), with the planes and lines clipped to the unit's box.
+template <typename R>
+__device__ __forceinline__ void unit_prepare(TetShared<R>* sh, int u, int& n_cross, int& n_lines) {
+    const TetGeo<R>& G = sh->geo[u];
+    const int* td = sh->td[u];
+    int run = 0;
+#pragma unroll 1
+    for (int p = 0; p < 18; ++p) {
+        const int e = p / 3, k = p - 3 * e;
+        int a, b, pp, qq;
+        tet_edge(e, a, b, pp, qq);
+        const int ca = G.cell[a][k], cb = G.cell[b][k];
+        const int lo = (ca < cb ? ca : cb) + 1, hi = ca < cb ? cb : ca;
+        const int c0 = lo > 0 ? lo : 0, c1 = hi < td[k] ? hi : td[k];
+        run += c1 >= c0 ? c1 - c0 + 1 : 0;
+        sh->xcum[u][p] = (unsigned short)run;
+    }
+    n_cross = run;
+    int r0[3], n[3];
+    unit_line_ranges(G, td, r0, n);
+    for (int a = 0; a < 3; ++a) {
+        sh->lr[u][a] = r0[a];
+        sh->lr[u][3 + a] = n[a];
+    }
+    n_lines = n[1] * n[2] + n[0] * n[2] + n[0] * n[1];
+}
+
 // B: vertex i of tetrahedron own
 template <typename R>
 __device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
     const TetGeo<R>& G = sh->geo[own];
     const int v0 = G.cell[i][0], v1 = G.cell[i][1], v2 = G.cell[i][2];
+    if ((unsigned)v0 >= (unsigned)sh->td[own][0] || (unsigned)v1 >= (unsigned)sh->td[own][1] ||
+        (unsigned)v2 >= (unsigned)sh->td[own][2])
+        return;  // the vertex lies in another tile
     R O[3], P[3];
     piece_origin(G, v0, v1, v2, O);
     for (int a = 0; a < 3; ++a) P[a] = (G.x[i][a] - O[a]) + G.xl[i][a];
@@ -255,7 +321,8 @@ __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, in
     const int ca0 = G.cell[a][0], ca1 = G.cell[a][1], ca2 = G.cell[a][2];
     const int cb0 = G.cell[b][0], cb1 = G.cell[b][1], cb2 = G.cell[b][2];
     const int cak = pick3(ca0, ca1, ca2, k), cbk = pick3(cb0, cb1, cb2, k);
-    const int c = (cak < cbk ? cak : cbk) + 1 + (t - before);
+    const int c0 = (cak < cbk ? cak : cbk) + 1;
+    const int c = (c0 > 0 ? c0 : 0) + (t - before);  // planes clipped to the unit's box
     const int dirk = cbk > cak ? 1 : -1;
     const R B2 = G.B2;
     // rounded crossing point: guesses of its cells
@@ -278,7 +345,9 @@ __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, in
         else
             cj1 = cw;
     }
-    return (Rec)c | ((Rec)cj0 << 11) | ((Rec)cj1 << 22) | ((Rec)k << 34) | ((Rec)e << 36);
+    if ((unsigned)cj0 >= (unsigned)sh->td[own][j1] || (unsigned)cj1 >= (unsigned)sh->td[own][j2]) return 0;
+    // bit 39 marks the record as present (every field may be 0 in a tile)
+    return (Rec)c | ((Rec)cj0 << 11) | ((Rec)cj1 << 22) | ((Rec)k << 34) | ((Rec)e << 36) | (1ull << 39);
 }
 
 // Line t of tetrahedron own: which facets the grid line pierces.  Returns the pierced-line record
@@ -287,23 +356,24 @@ template <typename R>
 __device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>* sh, int own, int t,
                                                              UnitCounts* cnt) {
     const TetGeo<R>& G = sh->geo[own];
-    const int h0 = G.hi[0], h1 = G.hi[1], h2 = G.hi[2];
-    // lines along l through the interior grid points (dj, dk) in [1, h_j] x [1, h_k]
+    // lines along l through the grid points (dj, dk) inside the bounding box and the unit's box
+    const int* lr = sh->lr[own];
+    const int r0[3] = {lr[0], lr[1], lr[2]}, n[3] = {lr[3], lr[4], lr[5]};
     int l, nj;
-    if (t < h1 * h2) {
+    if (t < n[1] * n[2]) {
         l = 0;
-        nj = h1;
-    } else if ((t -= h1 * h2) < h0 * h2) {
+        nj = n[1];
+    } else if ((t -= n[1] * n[2]) < n[0] * n[2]) {
         l = 1;
-        nj = h0;
+        nj = n[0];
     } else {
-        t -= h0 * h2;
+        t -= n[0] * n[2];
         l = 2;
-        nj = h0;
+        nj = n[0];
     }
-    const int tq = t / nj;
-    const int dj = 1 + t - tq * nj, dk = 1 + tq;
     const int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
+    const int tq = t / nj;
+    const int dj = pick3(r0[0], r0[1], r0[2], j) + t - tq * nj, dk = pick3(r0[0], r0[1], r0[2], k) + tq;
     // signs of the 6 projected edges against (dj, dk) (the filtered orient2d of tet_side2, from the
     // projected vertices read once; inconclusive ones settled exactly)
     unsigned sgn = 0, amb = 0;
@@ -344,7 +414,7 @@ __device__ __forceinline__ int item_line_facets(const TetShared<R>* sh, int own,
     const unsigned hits = (unsigned)(pr & 15u);
     const int l = (int)((pr >> 4) & 3u), dj = (int)((pr >> 6) & 2047u), dk = (int)((pr >> 17) & 2047u);
     const int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    int nr = 0;
+    int nr = 0, npierced = 0;
     arun = 0;
     int mlo = 0, mhi = -1;
     const int lol = pick3(G.lo[0], G.lo[1], G.lo[2], l), hil = pick3(G.hi[0], G.hi[1], G.hi[2], l);
@@ -367,6 +437,8 @@ __device__ __forceinline__ int item_line_facets(const TetShared<R>* sh, int own,
             mlo = m;
         else
             mhi = m;
+        ++npierced;
+        if ((unsigned)m >= (unsigned)pick3(sh->td[own][0], sh->td[own][1], sh->td[own][2], l)) continue;
         const Rec r = (Rec)m | ((Rec)dj << 11) | ((Rec)dk << 22) | ((Rec)l << 35) | ((Rec)f << 37);
         if (nr == 0)
             r0 = r;
@@ -374,10 +446,12 @@ __device__ __forceinline__ int item_line_facets(const TetShared<R>* sh, int own,
             r1 = r;
         ++nr;
     }
-    // grid nodes strictly inside: (cx, dj, dk) for cx in [mlo + 1, mhi] (x lines only)
-    if (l == 0 && nr == 2 && mhi >= mlo + 1)
-        arun = (unsigned long long)(mlo + 1) | ((unsigned long long)mhi << 11) | ((unsigned long long)dj << 22) |
-               ((unsigned long long)dk << 33);
+    // grid nodes strictly inside: (cx, dj, dk) for cx in [mlo + 1, mhi] within the unit's box
+    // [0, td_0] (x lines only); bit 51 marks the record as present
+    const int cx0 = mlo + 1 > 0 ? mlo + 1 : 0, cx1 = mhi < sh->td[own][0] ? mhi : sh->td[own][0];
+    if (l == 0 && npierced == 2 && cx1 >= cx0)
+        arun = (unsigned long long)cx0 | ((unsigned long long)cx1 << 11) | ((unsigned long long)dj << 22) |
+               ((unsigned long long)dk << 33) | (1ull << 51);
     return nr;
 }
 
@@ -488,6 +562,264 @@ __device__ __forceinline__ int upper_index(const int* pre, int u) {
     return pos;
 }
 
+// The three phases of one round over the units of the block's shared records whose thread (index
+// < TB_NT) has `in` set: items dealt to the warps 32 at a time, located corners queued per warp and
+// evaluated in full batches into the units' boxes.  Every thread of the block calls it.
+template <typename R, bool STATS>
+__device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cross, int n_lines, UnitCounts& cnt,
+                                             UnitCounts* pc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Rec* const q = sh->q[warp];
+    unsigned long long* const aq = sh->aq[warp];
+    unsigned long long* const pq = sh->pq[warp];
+    const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll 1
+    for (int ph = 0; ph < 3; ++ph) {
+        const int mine = in ? (ph == 0 ? 4 : (ph == 1 ? n_cross : n_lines)) : 0;
+        const int pre = block_scan(mine, sh->wsum);
+        if (tid < TB_NT) sh->pre[tid] = pre;
+        __syncthreads();
+        const int tot = sh->pre[TB_NT - 1];
+        // item rounds of 32 dealt to the warps in turn; each warp queues and evaluates its own
+        // located corners
+        const int nrounds = (tot + 31) >> 5;
+        const int my_rounds = nrounds > warp ? (nrounds - warp + TB_WARPS - 1) / TB_WARPS : 0;
+        unsigned head = 0, tail = 0, ahead = 0, atail = 0, phead = 0, ptail = 0;
+#pragma unroll 1
+        for (int i = 0; i < my_rounds; ++i) {
+            const int u = ((warp + i * TB_WARPS) << 5) + lane;
+            Rec r0 = 0;
+            unsigned long long pline = 0;
+            int own = 0;
+            if (u < tot) {
+                own = upper_index(sh->pre, u);
+                const int t = u - (own > 0 ? sh->pre[own - 1] : 0);
+                if (ph == 0) {
+                    item_vertex(sh, own, t);
+                    if (STATS) cnt.b++;
+                } else if (ph == 1) {
+                    r0 = item_crossing(sh, own, t, pc);
+                } else {
+                    pline = item_line_test(sh, own, t, pc);
+                }
+            }
+            // append located corners (C) or pierced lines to the warp's queues (warp-aggregated,
+            // no atomics)
+            {
+                const unsigned bc = __ballot_sync(FULL, r0 != 0);
+                if (r0) q[(tail + __popc(bc & lt_mask)) & (TB_QCAP - 1)] = r0 | ((Rec)own << 40);
+                tail += __popc(bc);
+                const unsigned bp = __ballot_sync(FULL, pline != 0);
+                if (pline) pq[(ptail + __popc(bp & lt_mask)) & (TB_PCAP - 1)] = pline | ((unsigned long long)own << 28);
+                ptail += __popc(bp);
+            }
+            __syncwarp();
+            const bool last_round = i + 1 == my_rounds;
+            // Work off the queues in full batches of 32 (after the warp's last items, down to empty):
+            // facet searches of pierced lines (which feed the D and A queues, when they have room),
+            // then C / D corners, then runs of A nodes.  One call site each.
+#pragma unroll 1
+            for (;;) {
+                const unsigned pav = ptail - phead, cav = tail - head, aav = atail - ahead;
+                const bool p_ready = pav >= 32u || (last_round && pav > 0u);
+                if (p_ready && cav <= TB_QCAP - 64u && aav <= TB_ACAP - 32u) {
+                    Rec d0 = 0, d1 = 0;
+                    unsigned long long arun = 0;
+                    int nr = 0, lown = 0;
+                    if ((unsigned)lane < pav) {
+                        const unsigned long long pr = pq[(phead + lane) & (TB_PCAP - 1)];
+                        lown = (int)((pr >> 28) & ((1u << TB_OWN_BITS) - 1u));
+                        nr = item_line_facets(sh, lown, pr, d0, d1, arun, pc);
+                    }
+                    phead += pav < 32u ? pav : 32u;
+                    const Rec ob = (Rec)lown << 40;
+                    const unsigned b0 = __ballot_sync(FULL, nr >= 1), b1 = __ballot_sync(FULL, nr >= 2);
+                    const unsigned off = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
+                    if (nr >= 1) q[(tail + off) & (TB_QCAP - 1)] = d0 | ob;
+                    if (nr >= 2) q[(tail + off + 1) & (TB_QCAP - 1)] = d1 | ob;
+                    tail += __popc(b0) + __popc(b1);
+                    const unsigned ba = __ballot_sync(FULL, arun != 0);
+                    if (arun) aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] = arun | ((unsigned long long)lown << 44);
+                    atail += __popc(ba);
+                    __syncwarp();
+                    continue;
+                }
+                const bool drain = last_round && pav == 0u;
+                if (cav >= 32u || (drain && cav > 0u)) {
+                    if ((unsigned)lane < cav) eval_CD<R, STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
+                    head += cav < 32u ? cav : 32u;
+                    __syncwarp();
+                    continue;
+                }
+                if (aav >= 32u || (drain && aav > 0u)) {
+                    if ((unsigned)lane < aav) eval_A<R, STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
+                    ahead += aav < 32u ? aav : 32u;
+                    __syncwarp();
+                    continue;
+                }
+                break;
+            }
+        }
+        // (the next block_scan's barrier orders this phase before the next one)
+    }
+    __syncthreads();  // every warp has finished the line phase: the boxes are complete
+}
+
+// How a round's boxes are flushed.  FLUSH_CLOSE_ROUND: the round's own mass closure (FP32 path:
+// the closed-form masses of its tetrahedra minus the sum of their pieces, spread over the pieces).
+// FLUSH_SUM_ONLY: the pieces are only summed into (s_hi, s_lo, s_abs) and cleared (first pass over
+// the tiles of a large tetrahedron).  FLUSH_SCALED: the pieces are flushed with the given closure
+// scale, and summed as well (second pass).
+enum FlushMode { FLUSH_CLOSE_ROUND = 0, FLUSH_SUM_ONLY = 1, FLUSH_SCALED = 2 };
+
+// (hi, lo) as a two-float sum and asum summed over the block; every thread gets the totals
+__device__ __forceinline__ void block_sum2(float& hi, float& lo, float& asum, float (*red)[TB_WARPS]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(FULL, hi, o), olo = __shfl_xor_sync(FULL, lo, o);
+        lo += olo;
+        two_sum_acc(hi, lo, ohi);
+        asum += __shfl_xor_sync(FULL, asum, o);
+    }
+    __syncthreads();  // red is free
+    if (lane == 0) {
+        red[0][warp] = hi;
+        red[1][warp] = lo;
+        red[2][warp] = asum;
+    }
+    __syncthreads();
+    hi = 0.f;
+    lo = 0.f;
+    asum = 0.f;
+    for (int w = 0; w < TB_WARPS; ++w) {
+        lo += red[1][w];
+        two_sum_acc(hi, lo, red[0][w]);
+        asum += red[2][w];
+    }
+}
+
+// Flush every box of the round: one FP64 atomic per non-zero piece (FP32 path: and one more for its
+// share of the mass-closure residual, `scale` |piece|).  Every thread of the block calls it; the
+// piece sums of FLUSH_SUM_ONLY / FLUSH_SCALED are added into `sums` by thread 0.  With
+// `whole` (one unit, a tile) the whole block flushes that unit's box; otherwise each warp flushes
+// the boxes of every TB_WARPS-th unit.
+template <typename R>
+__device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g, double* out, bool in, int pre_box,
+                                            int mode, float scale, bool whole, float* sums) {
+    constexpr bool fp32 = sizeof(R) == 4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the round's units are a prefix of the box slots: the last one ends at the largest pre_box
+    int used_slots = 0;
+    {
+        int m = in ? pre_box : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+        if (lane == 0) sh->wsum[warp] = m;
+        __syncthreads();
+        for (int w = 0; w < TB_WARPS; ++w) used_slots = max(used_slots, sh->wsum[w]);
+    }
+    if (fp32 && mode != FLUSH_SCALED) {
+        // FP32 pieces of the round minus the closed-form masses of its tetrahedra, summed as two
+        // floats (exact enough, FP32 arithmetic only); the residual is then spread over the pieces
+        // in proportion to their magnitude
+        float hi = 0.f, lo = 0.f, asum = 0.f;
+        if (in && mode == FLUSH_CLOSE_ROUND) {
+            two_sum_acc(hi, lo, -sh->geo[tid].mexact_hi);
+            lo -= sh->geo[tid].mexact_lo;
+        }
+        for (int e = tid; e < used_slots; e += TB_THREADS) {
+            const float v = (float)sh->box[e];
+            if (mode == FLUSH_SUM_ONLY) sh->box[e] = R(0);
+            two_sum_acc(hi, lo, v);
+            asum += fabsf(v);
+        }
+        block_sum2(hi, lo, asum, sh->red);
+        if (mode == FLUSH_SUM_ONLY) {
+            if (tid == 0) {
+                sums[1] += lo;
+                two_sum_acc(sums[0], sums[1], hi);
+                sums[2] += asum;
+            }
+            return;
+        }
+        const float resid = -(hi + lo);
+        if (asum > 0.f) {
+            scale = resid * __frcp_rn(asum);
+        } else if (tid == 0) {
+            // no piece to carry it: the cell of vertex 0 of the round's first unit
+            int t = 0;
+            while (t < TB_NT - 1 && sh->boff[t] < 0) ++t;
+            const TetGeo<R>& G = sh->geo[t];
+            const long long idx =
+                flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1], G.anchor[2] + G.cell[0][2]);
+            if (idx >= 0) atomicAdd(out + idx, (double)resid);
+        }
+    }
+    const int gsize = whole ? TB_THREADS : 32, glane = whole ? tid : lane;
+    float f_hi = 0.f, f_lo = 0.f, f_abs = 0.f;  // FLUSH_SCALED: the flushed pieces
+#pragma unroll 1
+    for (int t = whole ? 0 : warp; t < (whole ? 1 : TB_NT); t += TB_WARPS) {
+        const int base = sh->boff[t];
+        if (base < 0) continue;
+        const TetGeo<R>& G = sh->geo[t];
+        const int ex = sh->td[t][0], ey = sh->td[t][1], ez = sh->td[t][2];
+        const int size = ex * ey * ez;
+        const int ax = G.anchor[0], ay = G.anchor[1], az = G.anchor[2];
+        const float inv_ex = __frcp_rn((float)ex), inv_ey = __frcp_rn((float)ey);
+        // a box inside the grid needs no wrap: flat index = base + (x n1 + y) n2 + z
+        const bool inside =
+            ax >= 0 && ay >= 0 && az >= 0 && ax + ex <= g.n[0] && ay + ey <= g.n[1] && az + ez <= g.n[2];
+        const long long cbase = ((long long)ax * g.n[1] + ay) * g.n[2] + az;
+#pragma unroll 1
+        for (int e = glane; e < size; e += gsize) {
+            const R v = sh->box[base + e];
+            if (v == R(0)) continue;
+            sh->box[base + e] = R(0);
+            if (fp32 && mode == FLUSH_SCALED) {
+                two_sum_acc(f_hi, f_lo, (float)v);
+                f_abs += fabsf((float)v);
+            }
+            // e = x + ex (y + ey z): quotients from float reciprocals, corrected exactly
+            int r = (int)((float)e * inv_ex);
+            r += (r + 1) * ex <= e ? 1 : 0;
+            r -= r * ex > e ? 1 : 0;
+            const int x = e - r * ex;
+            int z = (int)((float)r * inv_ey);
+            z += (z + 1) * ey <= r ? 1 : 0;
+            z -= z * ey > r ? 1 : 0;
+            const int y = r - z * ey;
+            double* cell;
+            if (inside) {
+                cell = out + cbase + ((long long)x * g.n[1] + y) * g.n[2] + z;
+            } else {
+                bool ok = true;
+                const int cx = wrap_axis(ax + x, g.n[0], g.periodic, ok);
+                const int cy = wrap_axis(ay + y, g.n[1], g.periodic, ok);
+                const int cz = wrap_axis(az + z, g.n[2], g.periodic, ok);
+                if (!ok) continue;
+                cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
+            }
+            if constexpr (fp32) {
+                atomicAdd(cell, f32_to_f64((float)v));
+                // the piece's share of the closure residual (FP64 atomics are cheap here)
+                atomicAdd(cell, f32_to_f64(scale * fabsf((float)v)));
+            } else {
+                atomicAdd(cell, (double)v);
+            }
+        }
+    }
+    if (fp32 && mode == FLUSH_SCALED) {
+        block_sum2(f_hi, f_lo, f_abs, sh->red);
+        if (tid == 0) {
+            sums[1] += f_lo;
+            two_sum_acc(sums[0], sums[1], f_hi);
+            sums[2] += f_abs;
+        }
+    }
+    // (the next round's barriers order the flush before new box writes)
+}
+
 }  // namespace
 
 // One thread per tetrahedron of the batch [s0, s0 + nb): canonicalise it (exact orientation, periodic
@@ -565,289 +897,178 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
     }
 }
 
+// Thread 0 of a block in tiling mode, once the tiles of the current pass are done: switch the FP32
+// path from the summing pass to the flush pass (with the tetrahedron's closure scale), or close the
+// tetrahedron (FP32: the FP64 remainder to the cell of vertex 0) and take the next one of the list
+// (bs.ntiles < 0 when the list is exhausted).
+template <typename R, bool STATS>
+__device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g, long long nv, const int* simp,
+                                            const VertexRec* V, const int* big_list, long long big_cap,
+                                            double* out, Counters* ctr, int te) {
+    constexpr bool fp32 = sizeof(R) == 4;
+    BigState& b = sh->bs;
+    if (fp32 && b.ntiles > 0) {
+        const TetGeo<R>& G = sh->geo[0];  // mexact is the same in every tile's record
+        if (b.pass == 0) {
+            b.scale = b.s[2] > 0.f ? ((G.mexact_hi - b.s[0]) + (G.mexact_lo - b.s[1])) / b.s[2] : 0.f;
+            b.pass = 1;
+            b.tile = 0;
+            b.s[0] = b.s[1] = b.s[2] = 0.f;
+            return;
+        }
+        // what the rounded pieces of the flush pass still miss of the closed-form mass, in FP64
+        const Tet& S = sh->big;
+        const double left =
+            (G.mexact - ((double)b.s[0] + (double)b.s[1])) - (double)b.scale * (double)b.s[2];
+        const long long idx =
+            flat_cell(g, S.anchor[0] + S.cell[0][0], S.anchor[1] + S.cell[0][1], S.anchor[2] + S.cell[0][2]);
+        if (idx >= 0) atomicAdd(out + idx, left);
+    }
+    // the next tetrahedron of the list (complete: every batch was set up before this launch)
+    const long long listed = (long long)*(volatile unsigned*)&ctr->big_count;
+    const long long nbig = listed < big_cap ? listed : big_cap;
+    const long long bi = nbig > 0 ? (long long)atomicAdd(&ctr->big_next, 1u) : 0;
+    if (bi >= nbig) {
+        b.ntiles = -1;
+        return;
+    }
+    const long long s = big_list[bi];
+    const VertexRec* v[4];
+    bool ok = true;
+    for (int k = 0; k < 4; ++k) {
+        const int id = __ldg(simp + s * 4 + k);
+        ok = ok && id >= 0 && id < nv;
+        v[k] = V + (ok ? id : 0);
+    }
+    // (the set-up kernel listed it after the same checks: no tile when they fail)
+    const bool good = ok && canon_tet<1>(g, v, sh->big) == 0;
+    int n = 1;
+    for (int a = 0; a < 3; ++a) {
+        b.ext[a] = good ? sh->big.hi[a] - sh->big.lo[a] + 1 : 0;
+        b.nt[a] = (b.ext[a] + te - 1) / te;
+        n *= b.nt[a];
+    }
+    b.ntiles = n;
+    b.tile = 0;
+    b.pass = fp32 ? 0 : 1;
+    b.scale = 0.f;
+    b.s[0] = b.s[1] = b.s[2] = 0.f;
+    sh->boff[0] = 0;
+    for (int t = 1; t < TB_NT; ++t) sh->boff[t] = -1;
+    if (STATS) atomicAdd(&ctr->n_big_tiles, (unsigned long long)n);
+}
+
 template <typename R, bool STATS>
 __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
-    k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
-                  double* __restrict__ out, UnitCounts* __restrict__ stats) {
+    k_project_tet(GridDesc g, long long nb, long long nv, const TetGeo<R>* __restrict__ geo,
+                  const int* __restrict__ need_in, const int* __restrict__ simp, const VertexRec* __restrict__ V,
+                  const int* __restrict__ big_list, long long big_cap, double* __restrict__ out,
+                  Counters* __restrict__ ctr, UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr bool fp32 = sizeof(R) == 4;
     constexpr int BOX = BoxCap<R>::value;
+    // tile edge (cells) of a tetrahedron whose bounding box exceeds TB_MAX_CELLS (the same in both
+    // precisions, so that both take the same decisions tile by tile)
+    constexpr int TE = 18;
+    static_assert(TE * TE * TE <= BOX, "a tile must fit the block's slots");
     TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    Rec* const q = sh->q[warp];
-    unsigned long long* const aq = sh->aq[warp];
-    unsigned long long* const pq = sh->pq[warp];
+    const int tid = threadIdx.x;
     for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
-    UnitCounts cnt = {0, 0, 0, 0, 0};     // corner counts (registers)
-    UnitCounts xcnt = {0, 0, 0, 0, 0};    // exact-predicate count, updated through a pointer
+    if (tid == 0) {
+        sh->bs.ntiles = 0;
+        sh->bs.tile = 0;
+    }
+    UnitCounts cnt = {0, 0, 0, 0, 0};       // corner counts of the chunks (registers)
+    UnitCounts cnt_big = {0, 0, 0, 0, 0};   // of the tiles of large tetrahedra (flush pass)
+    UnitCounts cnt_none = {0, 0, 0, 0, 0};  // (FP32 summing pass: not counted)
+    UnitCounts xcnt = {0, 0, 0, 0, 0};      // exact-predicate count, updated through a pointer
     UnitCounts* pc = STATS ? &xcnt : nullptr;
     const long long nchunks = (nb + TB_NT - 1) / TB_NT;
-    const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-        // ---- the chunk's geometry records (written by k_tet_setup) into shared memory; thread
-        // t < TB_NT speaks for tetrahedron t of the chunk
-        const long long first = chunk * TB_NT;
-        const long long last = first + TB_NT < nb ? first + TB_NT : nb;
-        __syncthreads();  // the previous chunk is done with the records
-        {
-            constexpr int W = sizeof(TetGeo<R>) / 8;
-            static_assert(sizeof(TetGeo<R>) % 8 == 0, "geometry records are copied in 8-byte words");
-            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(geo + first);
-            unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh->geo);
-            const int words = (int)(last - first) * W;
-            for (int w = tid; w < words; w += TB_THREADS) dst[w] = __ldg(src + w);
-        }
-        const int need = (tid < TB_NT && first + tid < nb) ? __ldg(need_in + first + tid) : 0;
-        __syncthreads();
-        if (need > 0) {
-            const TetGeo<R>& G = sh->geo[tid];
-            int run = 0;
+    // chunk mode: thread t < TB_NT speaks for tetrahedron t of the block's current chunk.  Then
+    // tiling mode: the tetrahedra of the large-simplex list, one at a time, in tiles of TE^3 cells
+    // (FP32 path in two passes: the tiles' piece sums, then the flush with the closure scale).
+    long long chunk = (long long)blockIdx.x - gridDim.x;
+    int need = 0, n_cross = 0, n_lines = 0;
+    bool pending = false, tiling = false;
 #pragma unroll 1
-            for (int p = 0; p < 18; ++p) {
-                const int e = p / 3, k = p - 3 * e;
-                int a, b, pp, qq;
-                tet_edge(e, a, b, pp, qq);
-                const int d = G.cell[a][k] - G.cell[b][k];
-                run += d < 0 ? -d : d;
-                sh->xcum[tid][p] = (unsigned short)run;
+    for (;;) {
+        bool in;
+        int pre_box, mode;
+        if (!tiling) {
+            if (!__syncthreads_or(pending)) {
+                // ---- next chunk: its geometry records (written by k_tet_setup) into shared memory
+                // (the barrier above: the previous chunk is done with them)
+                chunk += gridDim.x;
+                if (chunk >= nchunks) {
+                    tiling = true;
+                    continue;
+                }
+                const long long first = chunk * TB_NT;
+                const long long last = first + TB_NT < nb ? first + TB_NT : nb;
+                {
+                    constexpr int W = sizeof(TetGeo<R>) / 8;
+                    static_assert(sizeof(TetGeo<R>) % 8 == 0, "geometry records are copied in 8-byte words");
+                    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(geo + first);
+                    unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh->geo);
+                    const int words = (int)(last - first) * W;
+                    for (int w = tid; w < words; w += TB_THREADS) dst[w] = __ldg(src + w);
+                }
+                need = (tid < TB_NT && first + tid < nb) ? __ldg(need_in + first + tid) : 0;
+                __syncthreads();
+                if (need > 0) {
+                    for (int a = 0; a < 3; ++a) sh->td[tid][a] = sh->geo[tid].hi[a] + 1;
+                    unit_prepare(sh, tid, n_cross, n_lines);
+                }
+                pending = need > 0;
+                continue;
             }
-        }
-        bool pending = need > 0;
-        // ---- rounds: tetrahedra in chunk order while their boxes fit the block's slots together
-#pragma unroll 1
-        while (__syncthreads_or(pending)) {
-            const int pre_box = block_scan(pending ? need : 0, sh->wsum);
-            const bool in = pending && pre_box <= BOX;
+            // ---- a round: tetrahedra in chunk order while their boxes fit the block's slots together
+            pre_box = block_scan(pending ? need : 0, sh->wsum);
+            in = pending && pre_box <= BOX;
             pending = pending && !in;
             if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
-            // item counts of the three phases
-            int n_ph1 = 0, n_ph2 = 0;
+            mode = FLUSH_CLOSE_ROUND;
+        } else {
+            const bool advance = sh->bs.tile >= sh->bs.ntiles;
+            __syncthreads();  // every thread has read the state; the previous round is done
+            if (advance) {
+                if (tid == 0) big_advance<R, STATS>(sh, g, nv, simp, V, big_list, big_cap, out, ctr, TE);
+                __syncthreads();
+                if (sh->bs.ntiles < 0) break;
+                continue;
+            }
+            // ---- a tile round: thread 0 sets up the tile's record, clipped to the tile
+            mode = sh->bs.pass == 0 ? FLUSH_SUM_ONLY : FLUSH_SCALED;
+            in = tid == 0;
+            pre_box = 0;
             if (in) {
-                const TetGeo<R>& G = sh->geo[tid];
-                n_ph1 = sh->xcum[tid][17];
-                n_ph2 = G.hi[1] * G.hi[2] + G.hi[0] * G.hi[2] + G.hi[0] * G.hi[1];
+                BigState& b = sh->bs;
+                const int i0 = b.tile % b.nt[0], r = b.tile / b.nt[0], i1 = r % b.nt[1], i2 = r / b.nt[1];
+                const int T[3] = {sh->big.lo[0] + i0 * TE, sh->big.lo[1] + i1 * TE, sh->big.lo[2] + i2 * TE};
+                tet_setup<R, 1>(sh->big, T, sh->geo[0]);
+                sh->td[0][0] = min(TE, b.ext[0] - i0 * TE);
+                sh->td[0][1] = min(TE, b.ext[1] - i1 * TE);
+                sh->td[0][2] = min(TE, b.ext[2] - i2 * TE);
+                pre_box = sh->td[0][0] * sh->td[0][1] * sh->td[0][2];
+                unit_prepare(sh, 0, n_cross, n_lines);
+                ++b.tile;
             }
-        #pragma unroll 1
-            for (int ph = 0; ph < 3; ++ph) {
-                const int mine = in ? (ph == 0 ? 4 : (ph == 1 ? n_ph1 : n_ph2)) : 0;
-                const int pre = block_scan(mine, sh->wsum);
-                if (tid < TB_NT) sh->pre[tid] = pre;
-                __syncthreads();
-                const int tot = sh->pre[TB_NT - 1];
-                // item rounds of 32 dealt to the warps in turn; each warp queues and evaluates its
-                // own located corners
-                const int nrounds = (tot + 31) >> 5;
-                const int my_rounds = nrounds > warp ? (nrounds - warp + TB_WARPS - 1) / TB_WARPS : 0;
-                unsigned head = 0, tail = 0, ahead = 0, atail = 0, phead = 0, ptail = 0;
-#pragma unroll 1
-                for (int i = 0; i < my_rounds; ++i) {
-                    const int u = ((warp + i * TB_WARPS) << 5) + lane;
-                    Rec r0 = 0;
-                    unsigned long long pline = 0;
-                    int own = 0;
-                    if (u < tot) {
-                        own = upper_index(sh->pre, u);
-                        const int t = u - (own > 0 ? sh->pre[own - 1] : 0);
-                        if (ph == 0) {
-                            item_vertex(sh, own, t);
-                            if (STATS) cnt.b++;
-                        } else if (ph == 1) {
-                            r0 = item_crossing(sh, own, t, pc);
-                        } else {
-                            pline = item_line_test(sh, own, t, pc);
-                        }
-                    }
-                    // append located corners (C) or pierced lines to the warp's queues
-                    // (warp-aggregated, no atomics)
-                    {
-                        const unsigned bc = __ballot_sync(FULL, r0 != 0);
-                        if (r0) q[(tail + __popc(bc & lt_mask)) & (TB_QCAP - 1)] = r0 | ((Rec)own << 40);
-                        tail += __popc(bc);
-                        const unsigned bp = __ballot_sync(FULL, pline != 0);
-                        if (pline)
-                            pq[(ptail + __popc(bp & lt_mask)) & (TB_PCAP - 1)] = pline | ((unsigned long long)own << 28);
-                        ptail += __popc(bp);
-                    }
-                    __syncwarp();
-                    const bool last_round = i + 1 == my_rounds;
-                    // Work off the queues in full batches of 32 (after the warp's last items, down to
-                    // empty): facet searches of pierced lines (which feed the D and A queues, when they
-                    // have room), then C / D corners, then runs of A nodes.  One call site each.
-#pragma unroll 1
-                    for (;;) {
-                        const unsigned pav = ptail - phead, cav = tail - head, aav = atail - ahead;
-                        const bool p_ready = pav >= 32u || (last_round && pav > 0u);
-                        if (p_ready && cav <= TB_QCAP - 64u && aav <= TB_ACAP - 32u) {
-                            Rec d0 = 0, d1 = 0;
-                            unsigned long long arun = 0;
-                            int nr = 0, lown = 0;
-                            if ((unsigned)lane < pav) {
-                                const unsigned long long pr = pq[(phead + lane) & (TB_PCAP - 1)];
-                                lown = (int)((pr >> 28) & ((1u << TB_OWN_BITS) - 1u));
-                                nr = item_line_facets(sh, lown, pr, d0, d1, arun, pc);
-                            }
-                            phead += pav < 32u ? pav : 32u;
-                            const Rec ob = (Rec)lown << 40;
-                            const unsigned b0 = __ballot_sync(FULL, nr >= 1), b1 = __ballot_sync(FULL, nr >= 2);
-                            const unsigned off = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
-                            if (nr >= 1) q[(tail + off) & (TB_QCAP - 1)] = d0 | ob;
-                            if (nr >= 2) q[(tail + off + 1) & (TB_QCAP - 1)] = d1 | ob;
-                            tail += __popc(b0) + __popc(b1);
-                            const unsigned ba = __ballot_sync(FULL, arun != 0);
-                            if (arun)
-                                aq[(atail + __popc(ba & lt_mask)) & (TB_ACAP - 1)] =
-                                    arun | ((unsigned long long)lown << 44);
-                            atail += __popc(ba);
-                            __syncwarp();
-                            continue;
-                        }
-                        const bool drain = last_round && pav == 0u;
-                        if (cav >= 32u || (drain && cav > 0u)) {
-                            if ((unsigned)lane < cav) eval_CD<R, STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
-                            head += cav < 32u ? cav : 32u;
-                            __syncwarp();
-                            continue;
-                        }
-                        if (aav >= 32u || (drain && aav > 0u)) {
-                            if ((unsigned)lane < aav) eval_A<R, STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
-                            ahead += aav < 32u ? aav : 32u;
-                            __syncwarp();
-                            continue;
-                        }
-                        break;
-                    }
-                }
-                // (the next block_scan's barrier orders this phase before the next one)
-            }
-            // ---- flush every box of the round: one FP64 atomic per non-zero piece (FP32 path: and
-            // one more for its share of the round's mass-closure residual).  pre[t] becomes the end
-            // of tetrahedron t's slots, clamped to the round's last slot, so that the owner of a
-            // slot is the first t with pre[t] above it.
-            __syncthreads();  // every warp has finished the line phase
-            int used_slots = 0;
-            {
-                // the round's tetrahedra are a prefix (in chunk order) of the pending ones: the last
-                // in-round end is the largest pre_box <= BOX among them
-                const int mine_end = in ? pre_box : 0;
-                int m = mine_end;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
-                if (lane == 0) sh->wsum[warp] = m;
-                __syncthreads();
-                for (int w = 0; w < TB_WARPS; ++w) used_slots = max(used_slots, sh->wsum[w]);
-            }
-            if (tid < TB_NT) {
-                // tetrahedra outside the round own no slot
-                const int end = in ? pre_box : min(pre_box, used_slots);
-                sh->pre[tid] = end;
-            }
-            float scale = 0.f;
-            if (fp32) {
-                // FP32 pieces of the round minus the closed-form masses of its tetrahedra, summed as
-                // two floats (exact enough, FP32 arithmetic only); the residual is then spread over
-                // the pieces in proportion to their magnitude
-                float hi = 0.f, lo = 0.f, asum = 0.f;
-                if (in) {
-                    two_sum_acc(hi, lo, -sh->geo[tid].mexact_hi);
-                    lo -= sh->geo[tid].mexact_lo;
-                }
-                for (int e = tid; e < used_slots; e += TB_THREADS) {
-                    const float v = (float)sh->box[e];
-                    two_sum_acc(hi, lo, v);
-                    asum += fabsf(v);
-                }
-#pragma unroll 1
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ohi = __shfl_xor_sync(FULL, hi, o), olo = __shfl_xor_sync(FULL, lo, o);
-                    lo += olo;
-                    two_sum_acc(hi, lo, ohi);
-                    asum += __shfl_xor_sync(FULL, asum, o);
-                }
-                __syncthreads();  // wsum reads above are done; red is free
-                if (lane == 0) {
-                    sh->red[0][warp] = hi;
-                    sh->red[1][warp] = lo;
-                    sh->red[2][warp] = asum;
-                }
-                __syncthreads();
-                hi = 0.f;
-                lo = 0.f;
-                asum = 0.f;
-                for (int w = 0; w < TB_WARPS; ++w) {
-                    lo += sh->red[1][w];
-                    two_sum_acc(hi, lo, sh->red[0][w]);
-                    asum += sh->red[2][w];
-                }
-                const float resid = -(hi + lo);
-                if (asum > 0.f) {
-                    scale = resid * __frcp_rn(asum);
-                } else if (tid == 0) {
-                    const TetGeo<R>& G = sh->geo[upper_index(sh->pre, 0)];
-                    const long long idx = flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1],
-                                                    G.anchor[2] + G.cell[0][2]);
-                    if (idx >= 0) atomicAdd(out + idx, (double)resid);
-                }
-            } else {
-                __syncthreads();
-            }
-            // each warp flushes the boxes of every TB_WARPS-th tetrahedron of the round
-#pragma unroll 1
-            for (int t = warp; t < TB_NT; t += TB_WARPS) {
-                const int base = sh->boff[t];
-                if (base < 0) continue;
-                const TetGeo<R>& G = sh->geo[t];
-                const int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
-                const int size = ex * ey * (G.hi[2] + 1);
-                const int ax = G.anchor[0], ay = G.anchor[1], az = G.anchor[2];
-                const float inv_ex = __frcp_rn((float)ex), inv_ey = __frcp_rn((float)ey);
-                // a box inside the grid needs no wrap: flat index = base + (x n1 + y) n2 + z
-                const bool inside = ax >= 0 && ay >= 0 && az >= 0 && ax + ex <= g.n[0] && ay + ey <= g.n[1] &&
-                                    az + (G.hi[2] + 1) <= g.n[2];
-                const long long cbase = ((long long)ax * g.n[1] + ay) * g.n[2] + az;
-#pragma unroll 1
-                for (int e = lane; e < size; e += 32) {
-                    const R v = sh->box[base + e];
-                    if (v == R(0)) continue;
-                    sh->box[base + e] = R(0);
-                    // e = x + ex (y + ey z): quotients from float reciprocals, corrected exactly
-                    int r = (int)((float)e * inv_ex);
-                    r += (r + 1) * ex <= e ? 1 : 0;
-                    r -= r * ex > e ? 1 : 0;
-                    const int x = e - r * ex;
-                    int z = (int)((float)r * inv_ey);
-                    z += (z + 1) * ey <= r ? 1 : 0;
-                    z -= z * ey > r ? 1 : 0;
-                    const int y = r - z * ey;
-                    double* cell;
-                    if (inside) {
-                        cell = out + cbase + ((long long)x * g.n[1] + y) * g.n[2] + z;
-                    } else {
-                        bool ok = true;
-                        const int cx = wrap_axis(ax + x, g.n[0], g.periodic, ok);
-                        const int cy = wrap_axis(ay + y, g.n[1], g.periodic, ok);
-                        const int cz = wrap_axis(az + z, g.n[2], g.periodic, ok);
-                        if (!ok) continue;
-                        cell = out + ((long long)cx * g.n[1] + cy) * g.n[2] + cz;
-                    }
-                    if constexpr (fp32) {
-                        atomicAdd(cell, f32_to_f64((float)v));
-                        // the piece's share of the closure residual (FP64 atomics are cheap here)
-                        atomicAdd(cell, f32_to_f64(scale * fabsf((float)v)));
-                    } else {
-                        atomicAdd(cell, (double)v);
-                    }
-                }
-            }
-            // (the next round's block_scan barrier orders the flush before new box writes)
         }
+        // ---- the round's three phases, then its flush (one call site each)
+        round_phases<R, STATS>(sh, in, n_cross, n_lines, !tiling ? cnt : (sh->bs.pass == 0 ? cnt_none : cnt_big),
+                               tiling && sh->bs.pass == 0 ? nullptr : pc);
+        round_flush<R>(sh, g, out, in, pre_box, mode, tiling ? sh->bs.scale : 0.f, tiling, sh->bs.s);
     }
     if (STATS) {
-        if (cnt.a) atomicAdd(&stats->a, cnt.a);
-        if (cnt.b) atomicAdd(&stats->b, cnt.b);
-        if (cnt.c) atomicAdd(&stats->c, cnt.c);
-        if (cnt.d) atomicAdd(&stats->d, cnt.d);
-        if (xcnt.exact) atomicAdd(&stats->exact, xcnt.exact);
+        if (cnt.a) atomicAdd(&stats[0].a, cnt.a);
+        if (cnt.b) atomicAdd(&stats[0].b, cnt.b);
+        if (cnt.c) atomicAdd(&stats[0].c, cnt.c);
+        if (cnt.d) atomicAdd(&stats[0].d, cnt.d);
+        if (xcnt.exact) atomicAdd(&stats[0].exact, xcnt.exact);
+        if (cnt_big.a) atomicAdd(&stats[1].a, cnt_big.a);
+        if (cnt_big.b) atomicAdd(&stats[1].b, cnt_big.b);
+        if (cnt_big.c) atomicAdd(&stats[1].c, cnt_big.c);
+        if (cnt_big.d) atomicAdd(&stats[1].d, cnt_big.d);
     }
 }
 
@@ -895,20 +1116,27 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
     for (long long s0 = 0; s0 < L.ns; s0 += batch) {
         const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
+        const bool last = s0 + nb >= L.ns;
         k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, 128 * sizeof(TetGeo<R>), st>>>(
             L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, reinterpret_cast<TetGeo<R>*>(L.geo), L.need,
             L.big_list, L.big_cap, L.stats != nullptr);
         if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
-        long long blocks = (nb + TB_NT - 1) / TB_NT;
+        // the last batch's launch also projects the listed large tetrahedra (the list is complete
+        // once every batch is set up), on the whole persistent grid: blocks left without a chunk
+        // start on them at once
         const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
-        if (blocks > cap) blocks = cap;
+        long long blocks = (nb + TB_NT - 1) / TB_NT;
+        if (last || blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
+        const int* list = last ? L.big_list : nullptr;
+        const long long list_cap = last ? L.big_cap : 0;
+        const TetGeo<R>* G = reinterpret_cast<const TetGeo<R>*>(L.geo);
         if (L.stats)
             k_project_tet<R, true><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-                L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, L.stats);
+                L.g, nb, L.nv, G, L.need, L.simplices, L.verts, list, list_cap, L.out, L.ctr, L.stats);
         else
             k_project_tet<R, false><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-                L.g, nb, reinterpret_cast<const TetGeo<R>*>(L.geo), L.need, L.out, nullptr);
+                L.g, nb, L.nv, G, L.need, L.simplices, L.verts, list, list_cap, L.out, L.ctr, nullptr);
     }
     return cudaGetLastError();
 }

@@ -233,6 +233,33 @@ CDP_HD float low_part<float>(i64 L, float hi) {
 template <>
 CDP_HD double low_part<double>(i64, double) { return 0.0; }
 
+// Rounded coordinates of the working set from its exact ones (Lt).
+template <typename R>
+CDP_HD void tet_round_coords(TetGeo<R>& G) {
+    for (int k = 0; k < 4; ++k)
+        for (int a = 0; a < 3; ++a) {
+            G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
+            G.xl[k][a] = low_part<R>(G.Lt[k][a], G.x[k][a]);
+        }
+}
+
+// Fields of the working set that depend on the tile's frame besides the coordinates: the centroid
+// and the filter bounds (from the largest coordinate magnitude in cells).
+template <typename R>
+CDP_HD void tet_frame_bounds(TetGeo<R>& G) {
+    for (int a = 0; a < 3; ++a) G.c[a] = R(0.25) * (G.x[0][a] + G.x[1][a] + G.x[2][a] + G.x[3][a]);
+    int m = 1;
+    for (int a = 0; a < 3; ++a) {
+        int v = G.lo[a] < 0 ? -G.lo[a] : G.lo[a];
+        int w = G.hi[a] + 1 < 0 ? -(G.hi[a] + 1) : G.hi[a] + 1;
+        m = v > m ? v : m;
+        m = w > m ? w : m;
+    }
+    R Rm = R(m + 1);
+    G.B2 = Eps<R>::k2 * Rm * Rm;
+    G.B3 = Eps<R>::k3 * Rm;
+}
+
 // Fill the working set for the tile whose lowest cell is T (relative to the anchor).  COPY only
 // gives a caller its own out-of-line instance (register allocation of its own).
 template <typename R, int COPY = 0>
@@ -240,10 +267,9 @@ CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
     for (int k = 0; k < 4; ++k)
         for (int a = 0; a < 3; ++a) {
             G.Lt[k][a] = S.L[k][a] - ((i64)T[a] << CDP_Q);
-            G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
-            G.xl[k][a] = low_part<R>(G.Lt[k][a], G.x[k][a]);
             G.cell[k][a] = S.cell[k][a] - T[a];
         }
+    tet_round_coords(G);
     for (int a = 0; a < 3; ++a) {
         G.lo[a] = S.lo[a] - T[a];
         G.hi[a] = S.hi[a] - T[a];
@@ -272,21 +298,9 @@ CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
     for (int a = 0; a < 3; ++a) G.anchor[a] = S.anchor[a] + T[a];
     for (int k = 0; k < 4; ++k) G.rho[k] = (R)S.rho[k];
     R d1 = G.rho[1] - G.rho[0], d2 = G.rho[2] - G.rho[0], d3 = G.rho[3] - G.rho[0];
-    for (int a = 0; a < 3; ++a) {
-        G.g[a] = (d1 * nr[1][a] + d2 * nr[2][a] + d3 * nr[3][a]) * invD;
-        G.c[a] = R(0.25) * (G.x[0][a] + G.x[1][a] + G.x[2][a] + G.x[3][a]);
-    }
+    for (int a = 0; a < 3; ++a) G.g[a] = (d1 * nr[1][a] + d2 * nr[2][a] + d3 * nr[3][a]) * invD;
     G.rhoc = R(0.25) * (G.rho[0] + G.rho[1] + G.rho[2] + G.rho[3]);
-    int m = 1;
-    for (int a = 0; a < 3; ++a) {
-        int v = G.lo[a] < 0 ? -G.lo[a] : G.lo[a];
-        int w = G.hi[a] + 1 < 0 ? -(G.hi[a] + 1) : G.hi[a] + 1;
-        m = v > m ? v : m;
-        m = w > m ? w : m;
-    }
-    R Rm = R(m + 1);
-    G.B2 = Eps<R>::k2 * Rm * Rm;
-    G.B3 = Eps<R>::k3 * Rm;
+    tet_frame_bounds(G);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -55,6 +55,11 @@ static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS, "chunk index d
 // largest bounding box (cells) projected by the main kernel, and the block's box slots (FP32: sized
 // with the rest of the block's shared memory for three resident blocks per SM)
 constexpr int TB_MAX_CELLS = 1280;
+// tile edge (cells) of a tetrahedron whose bounding box exceeds TB_MAX_CELLS (the same in both
+// precisions, so that both take the same decisions tile by tile), and the x lines of one tile
+constexpr int TB_TE = 18;
+constexpr int TB_RUNS = (TB_TE + 1) * (TB_TE + 1);
+
 template <typename R>
 struct BoxCap {
     static constexpr int value = sizeof(R) == 4 ? 6144 : TB_MAX_CELLS * TB_WARPS;
@@ -83,7 +88,10 @@ struct TetShared {
     int lr[TB_NT][6];                // grid-line ranges of each unit (unit_line_ranges: r0[3], n[3])
     int td[TB_NT][3];                // box (tile) dimensions of each unit: its bounding box, or one tile
                                      // of a tetrahedron whose bounding box exceeds TB_MAX_CELLS
-    Tet big;                         // the large tetrahedron being tiled
+    TetGeo<R> big0;                  // the large tetrahedron being tiled, in the frame of its tile 0
+    short2 runs[TB_RUNS];            // tile rounds: grid nodes inside the tetrahedron on the x line
+                                     // through (y, z) = (j, k) of the tile, entry j + (TB_TE + 1) k:
+                                     // the node range [x, y] clipped to the tile (empty: x > y)
     BigState bs;                     // its tiling state
     int pre[TB_NT];                  // inclusive prefix of the current phase's item counts; in the
                                      // flush, of the round's box sizes
@@ -408,8 +416,8 @@ __device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>*
 // A pierced line (record of item_line_test): its D records (one per pierced facet, the cell along
 // the line located with the exact-sign search) and the run of A nodes between them (x lines only).
 template <typename R>
-__device__ __forceinline__ int item_line_facets(const TetShared<R>* sh, int own, unsigned long long pr, Rec& r0,
-                                                Rec& r1, unsigned long long& arun, UnitCounts* cnt) {
+__device__ __forceinline__ int item_line_facets(TetShared<R>* sh, int own, unsigned long long pr, Rec& r0,
+                                                Rec& r1, unsigned long long& arun, bool cells, UnitCounts* cnt) {
     const TetGeo<R>& G = sh->geo[own];
     const unsigned hits = (unsigned)(pr & 15u);
     const int l = (int)((pr >> 4) & 3u), dj = (int)((pr >> 6) & 2047u), dk = (int)((pr >> 17) & 2047u);
@@ -447,11 +455,16 @@ __device__ __forceinline__ int item_line_facets(const TetShared<R>* sh, int own,
         ++nr;
     }
     // grid nodes strictly inside: (cx, dj, dk) for cx in [mlo + 1, mhi] within the unit's box
-    // [0, td_0] (x lines only); bit 51 marks the record as present
+    // [0, td_0] (x lines only): a run of A nodes (bit 51 marks the record as present), or in a tile
+    // round the line's entry of the run table
     const int cx0 = mlo + 1 > 0 ? mlo + 1 : 0, cx1 = mhi < sh->td[own][0] ? mhi : sh->td[own][0];
-    if (l == 0 && npierced == 2 && cx1 >= cx0)
-        arun = (unsigned long long)cx0 | ((unsigned long long)cx1 << 11) | ((unsigned long long)dj << 22) |
-               ((unsigned long long)dk << 33) | (1ull << 51);
+    if (l == 0 && npierced == 2 && cx1 >= cx0) {
+        if (cells)
+            sh->runs[dj + (TB_TE + 1) * dk] = make_short2((short)cx0, (short)cx1);
+        else
+            arun = (unsigned long long)cx0 | ((unsigned long long)cx1 << 11) | ((unsigned long long)dj << 22) |
+                   ((unsigned long long)dk << 33) | (1ull << 51);
+    }
     return nr;
 }
 
@@ -498,6 +511,69 @@ __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, U
         }
         if (STATS) cnt.a += 8;
     }
+}
+
+// Column t = y + td_1 z of the tile (unit 0, tile rounds): the cells (x, y, z), x in [0, td_0), with
+// their A corners from the run table.  A cell whose eight corners are all inside the tetrahedron
+// lies inside it: its piece is the integral of rho over the cell, rho at its centre (the eight A
+// terms sum to exactly that).  Otherwise the A terms of its inside corners are summed with the
+// cell's piece origin.  Columns are disjoint and the round's other phases are done, so the box
+// entries are updated without atomics.  Returns the number of (A corner, cell) incidences.
+template <typename R>
+__device__ __noinline__ unsigned item_column(TetShared<R>* sh, int t) {
+    const int ex = sh->td[0][0], ey = sh->td[0][1];
+    const int z = t / ey, y = t - z * ey;
+    short2 run[4];
+    int amin = 1 << 20, bmax = -(1 << 20), amax = -(1 << 20), bmin = 1 << 20;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        run[w] = sh->runs[(y + (w & 1)) + (TB_TE + 1) * (z + (w >> 1))];
+        if (run[w].x <= run[w].y) {
+            amin = min(amin, (int)run[w].x);
+            bmax = max(bmax, (int)run[w].y);
+        }
+        amax = max(amax, (int)run[w].x);  // (an empty run, (1, 0), leaves no cell entirely inside)
+        bmin = min(bmin, (int)run[w].y);
+    }
+    if (amin > bmax) return 0u;
+    const int x0 = max(amin - 1, 0), x1 = min(bmax, ex - 1);
+    const int flo = amax, fhi = bmin - 1;  // the cells with all eight corners inside
+    const TetFrame<R> F = tet_frame(sh->geo[0]);
+    const R ryz = F.rhoc + F.g[1] * ((R(y) + R(0.5)) - F.c[1]) + F.g[2] * ((R(z) + R(0.5)) - F.c[2]);
+    R* col = sh->box + sh->boff[0] + ex * (y + ey * z);
+    unsigned n = 0;
+#pragma unroll 1
+    for (int x = x0; x <= x1; ++x) {
+        R v;
+        if (x >= flo && x <= fhi) {
+            v = ryz + F.g[0] * ((R(x) + R(0.5)) - F.c[0]);
+            n += 8u;
+        } else {
+            // bit 2 w + o: corner x + o on the line (y + (w & 1), z + (w >> 1))
+            unsigned mask = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                mask |= (run[w].x <= x && x <= run[w].y ? 1u : 0u) << (2 * w);
+                mask |= (run[w].x <= x + 1 && x + 1 <= run[w].y ? 1u : 0u) << (2 * w + 1);
+            }
+            if (!mask) continue;
+            R O[3];
+            piece_origin(F, x, y, z, O);
+            v = R(0);
+#pragma unroll 1
+            for (int b = 0; b < 8; ++b) {
+                if (!((mask >> b) & 1u)) continue;
+                // the corner is the cell's upper one along an axis where its offset is 1
+                const int ox = b & 1, oy = (b >> 1) & 1, oz = b >> 2;
+                const R P[3] = {R(x + ox) - O[0], R(y + oy) - O[1], R(z + oz) - O[2]};
+                const R sg = R((ox ? 1 : -1) * (oy ? 1 : -1) * (oz ? 1 : -1));
+                v += tet_corner_A(F, P, rho_from_P(F, P, O), sg);
+            }
+            n += __popc(mask);
+        }
+        col[x] += v;
+    }
+    return n;
 }
 
 // absolute cell index along one axis (periodic wrap without a division in the common case)
@@ -566,16 +642,17 @@ __device__ __forceinline__ int upper_index(const int* pre, int u) {
 // < TB_NT) has `in` set: items dealt to the warps 32 at a time, located corners queued per warp and
 // evaluated in full batches into the units' boxes.  Every thread of the block calls it.
 template <typename R, bool STATS>
-__device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cross, int n_lines, UnitCounts& cnt,
-                                             UnitCounts* pc) {
+__device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cross, int n_lines, bool cells,
+                                             UnitCounts& cnt, UnitCounts* pc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Rec* const q = sh->q[warp];
     unsigned long long* const aq = sh->aq[warp];
     unsigned long long* const pq = sh->pq[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll 1
-    for (int ph = 0; ph < 3; ++ph) {
-        const int mine = in ? (ph == 0 ? 4 : (ph == 1 ? n_cross : n_lines)) : 0;
+    for (int ph = 0; ph < (cells ? 4 : 3); ++ph) {
+        const int mine =
+            in ? (ph == 0 ? 4 : (ph == 1 ? n_cross : (ph == 2 ? n_lines : sh->td[0][1] * sh->td[0][2]))) : 0;
         const int pre = block_scan(mine, sh->wsum);
         if (tid < TB_NT) sh->pre[tid] = pre;
         __syncthreads();
@@ -599,8 +676,11 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                     if (STATS) cnt.b++;
                 } else if (ph == 1) {
                     r0 = item_crossing(sh, own, t, pc);
-                } else {
+                } else if (ph == 2) {
                     pline = item_line_test(sh, own, t, pc);
+                } else {
+                    const unsigned na = item_column(sh, t);
+                    if (STATS) cnt.a += na;
                 }
             }
             // append located corners (C) or pierced lines to the warp's queues (warp-aggregated,
@@ -629,7 +709,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                     if ((unsigned)lane < pav) {
                         const unsigned long long pr = pq[(phead + lane) & (TB_PCAP - 1)];
                         lown = (int)((pr >> 28) & ((1u << TB_OWN_BITS) - 1u));
-                        nr = item_line_facets(sh, lown, pr, d0, d1, arun, pc);
+                        nr = item_line_facets(sh, lown, pr, d0, d1, arun, cells, pc);
                     }
                     phead += pav < 32u ? pav : 32u;
                     const Rec ob = (Rec)lown << 40;
@@ -897,6 +977,121 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
     }
 }
 
+// Whether the tetrahedron B (in the frame of its tile 0) certainly misses tile t of its tiling: the
+// tile's box lies more than 1/16 cell outside the plane of one of its facets (then every piece of
+// the tile's cells is zero; the margin covers the rounding of the unit normals and coordinates, far
+// below it for extents up to CDP_MAX_EXTENT cells).
+template <typename R>
+__device__ __forceinline__ bool tile_misses(const TetGeo<R>& B, const BigState& b, int t) {
+    const int i0 = t % b.nt[0], r = t / b.nt[0], i1 = r % b.nt[1], i2 = r / b.nt[1];
+    const int lo[3] = {i0 * TB_TE, i1 * TB_TE, i2 * TB_TE};
+    const int hi[3] = {min(lo[0] + TB_TE, b.ext[0]), min(lo[1] + TB_TE, b.ext[1]), min(lo[2] + TB_TE, b.ext[2])};
+    bool miss = false;
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        const int va = f == 0 ? 1 : 0;
+        float m = 0.f;  // largest signed distance over the box from the plane of facet f (inward)
+        for (int a = 0; a < 3; ++a) {
+            const float n = (float)B.n[f][a];
+            m += n * ((float)(n > 0.f ? hi[a] : lo[a]) - (float)B.x[va][a]);
+        }
+        miss = miss || m < -0.0625f;
+    }
+    return miss;
+}
+
+// Warp 0 of a tile round: the first tile at or after bs.tile that the tetrahedron may meet (32
+// candidates tested at a time), and its unit: the record of the tetrahedron in the tile's frame (the
+// values tet_setup gives for that tile: the frame moves the exact coordinates, cells, box and
+// anchor, and the fields rounded from them, one coordinate per lane; the normals, gradient,
+// densities and mass do not depend on it), its box, and the item counts of unit_prepare (one
+// (edge, axis) pair per lane).  Returns whether a tile was found; lane 0 gets n_cross,
+// n_lines and pre_box, and moves bs.tile past the tile.
+template <typename R>
+__device__ __forceinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int& n_lines, int& pre_box) {
+    const int lane = threadIdx.x & 31;
+    BigState& b = sh->bs;
+    const TetGeo<R>& B = sh->big0;
+    const int ntiles = b.ntiles;
+    int t = b.tile;
+#pragma unroll 1
+    for (; t < ntiles; t += 32) {
+        const int c = t + lane;
+        const unsigned live = __ballot_sync(FULL, c < ntiles && !tile_misses(B, b, c));
+        if (live) {
+            t += __ffs(live) - 1;
+            break;
+        }
+    }
+    __syncwarp();  // every lane has read bs
+    if (t >= ntiles) {
+        if (lane == 0) {
+            b.tile = ntiles;
+            sh->boff[0] = -1;  // an empty round
+        }
+        return false;
+    }
+    const int i0 = t % b.nt[0], r = t / b.nt[0], i1 = r % b.nt[1], i2 = r / b.nt[1];
+    const int dT[3] = {i0 * TB_TE, i1 * TB_TE, i2 * TB_TE};
+    TetGeo<R>& G = sh->geo[0];
+    {
+        constexpr int W = sizeof(TetGeo<R>) / 8;
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&B);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&G);
+        for (int w = lane; w < W; w += 32) dst[w] = src[w];
+    }
+    __syncwarp();
+    if (lane < 12) {
+        const int k = lane / 3, a = lane - 3 * k;
+        const int d = pick3(dT[0], dT[1], dT[2], a);
+        G.Lt[k][a] = B.Lt[k][a] - ((i64)d << CDP_Q);
+        G.x[k][a] = i64_to_real<R>(G.Lt[k][a], CDP_Q);
+        G.xl[k][a] = low_part<R>(G.Lt[k][a], G.x[k][a]);
+        G.cell[k][a] = B.cell[k][a] - d;
+    } else if (lane < 15) {
+        const int a = lane - 12;
+        const int d = pick3(dT[0], dT[1], dT[2], a);
+        G.lo[a] = B.lo[a] - d;
+        G.hi[a] = B.hi[a] - d;
+        G.anchor[a] = B.anchor[a] + d;
+        sh->td[0][a] = min(TB_TE, pick3(b.ext[0], b.ext[1], b.ext[2], a) - d);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        tet_frame_bounds(G);
+        sh->boff[0] = 0;
+        b.tile = t + 1;
+    }
+    // crossings of the (edge, axis) pairs with the tile's planes, as running counts
+    int run = 0;
+    if (lane < 18) {
+        const int e = lane / 3, k = lane - 3 * e;
+        int a, bb, pp, qq;
+        tet_edge(e, a, bb, pp, qq);
+        const int ca = G.cell[a][k], cb = G.cell[bb][k];
+        const int lo = (ca < cb ? ca : cb) + 1, hi = ca < cb ? cb : ca;
+        const int tdk = sh->td[0][k];
+        const int c0 = lo > 0 ? lo : 0, c1 = hi < tdk ? hi : tdk;
+        run = c1 >= c0 ? c1 - c0 + 1 : 0;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, run, o);
+        if (lane >= o) run += u;
+    }
+    if (lane < 18) sh->xcum[0][lane] = (unsigned short)run;
+    n_cross = __shfl_sync(FULL, run, 17);
+    int r0[3], n[3];
+    unit_line_ranges(G, sh->td[0], r0, n);
+    if (lane < 3) {
+        sh->lr[0][lane] = pick3(r0[0], r0[1], r0[2], lane);
+        sh->lr[0][3 + lane] = pick3(n[0], n[1], n[2], lane);
+    }
+    n_lines = n[1] * n[2] + n[0] * n[2] + n[0] * n[1];
+    pre_box = sh->td[0][0] * sh->td[0][1] * sh->td[0][2];
+    return true;
+}
+
 // Thread 0 of a block in tiling mode, once the tiles of the current pass are done: switch the FP32
 // path from the summing pass to the flush pass (with the tetrahedron's closure scale), or close the
 // tetrahedron (FP32: the FP64 remainder to the cell of vertex 0) and take the next one of the list
@@ -917,11 +1112,11 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
             return;
         }
         // what the rounded pieces of the flush pass still miss of the closed-form mass, in FP64
-        const Tet& S = sh->big;
+        const TetGeo<R>& B = sh->big0;
         const double left =
             (G.mexact - ((double)b.s[0] + (double)b.s[1])) - (double)b.scale * (double)b.s[2];
         const long long idx =
-            flat_cell(g, S.anchor[0] + S.cell[0][0], S.anchor[1] + S.cell[0][1], S.anchor[2] + S.cell[0][2]);
+            flat_cell(g, B.anchor[0] + B.cell[0][0], B.anchor[1] + B.cell[0][1], B.anchor[2] + B.cell[0][2]);
         if (idx >= 0) atomicAdd(out + idx, left);
     }
     // the next tetrahedron of the list (complete: every batch was set up before this launch)
@@ -941,21 +1136,21 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
         v[k] = V + (ok ? id : 0);
     }
     // (the set-up kernel listed it after the same checks: no tile when they fail)
-    const bool good = ok && canon_tet<1>(g, v, sh->big) == 0;
+    Tet S;
+    const bool good = ok && canon_tet<1>(g, v, S) == 0;
+    if (good) tet_setup<R, 1>(S, S.lo, sh->big0);
     int n = 1;
     for (int a = 0; a < 3; ++a) {
-        b.ext[a] = good ? sh->big.hi[a] - sh->big.lo[a] + 1 : 0;
+        b.ext[a] = good ? S.hi[a] - S.lo[a] + 1 : 0;
         b.nt[a] = (b.ext[a] + te - 1) / te;
         n *= b.nt[a];
     }
     b.ntiles = n;
-    b.tile = 0;
     b.pass = fp32 ? 0 : 1;
+    b.tile = 0;
     b.scale = 0.f;
     b.s[0] = b.s[1] = b.s[2] = 0.f;
-    sh->boff[0] = 0;
     for (int t = 1; t < TB_NT; ++t) sh->boff[t] = -1;
-    if (STATS) atomicAdd(&ctr->n_big_tiles, (unsigned long long)n);
 }
 
 template <typename R, bool STATS>
@@ -966,10 +1161,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
                   Counters* __restrict__ ctr, UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int BOX = BoxCap<R>::value;
-    // tile edge (cells) of a tetrahedron whose bounding box exceeds TB_MAX_CELLS (the same in both
-    // precisions, so that both take the same decisions tile by tile)
-    constexpr int TE = 18;
-    static_assert(TE * TE * TE <= BOX, "a tile must fit the block's slots");
+    static_assert(TB_TE * TB_TE * TB_TE <= BOX, "a tile must fit the block's slots");
     TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
     const int tid = threadIdx.x;
     for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
@@ -985,7 +1177,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
     const long long nchunks = (nb + TB_NT - 1) / TB_NT;
 
     // chunk mode: thread t < TB_NT speaks for tetrahedron t of the block's current chunk.  Then
-    // tiling mode: the tetrahedra of the large-simplex list, one at a time, in tiles of TE^3 cells
+    // tiling mode: the tetrahedra of the large-simplex list, one at a time, in tiles of TB_TE^3 cells
     // (FP32 path in two passes: the tiles' piece sums, then the flush with the closure scale).
     long long chunk = (long long)blockIdx.x - gridDim.x;
     int need = 0, n_cross = 0, n_lines = 0;
@@ -1032,30 +1224,25 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             const bool advance = sh->bs.tile >= sh->bs.ntiles;
             __syncthreads();  // every thread has read the state; the previous round is done
             if (advance) {
-                if (tid == 0) big_advance<R, STATS>(sh, g, nv, simp, V, big_list, big_cap, out, ctr, TE);
+                if (tid == 0) big_advance<R, STATS>(sh, g, nv, simp, V, big_list, big_cap, out, ctr, TB_TE);
                 __syncthreads();
                 if (sh->bs.ntiles < 0) break;
                 continue;
             }
-            // ---- a tile round: thread 0 sets up the tile's record, clipped to the tile
+            // ---- a tile round: warp 0 finds the next tile the tetrahedron may meet and sets up its
+            // unit (thread 0), clipped to the tile; no unit when none is left (an empty round)
             mode = sh->bs.pass == 0 ? FLUSH_SUM_ONLY : FLUSH_SCALED;
-            in = tid == 0;
+            in = false;
             pre_box = 0;
-            if (in) {
-                BigState& b = sh->bs;
-                const int i0 = b.tile % b.nt[0], r = b.tile / b.nt[0], i1 = r % b.nt[1], i2 = r / b.nt[1];
-                const int T[3] = {sh->big.lo[0] + i0 * TE, sh->big.lo[1] + i1 * TE, sh->big.lo[2] + i2 * TE};
-                tet_setup<R, 1>(sh->big, T, sh->geo[0]);
-                sh->td[0][0] = min(TE, b.ext[0] - i0 * TE);
-                sh->td[0][1] = min(TE, b.ext[1] - i1 * TE);
-                sh->td[0][2] = min(TE, b.ext[2] - i2 * TE);
-                pre_box = sh->td[0][0] * sh->td[0][1] * sh->td[0][2];
-                unit_prepare(sh, 0, n_cross, n_lines);
-                ++b.tile;
+            for (int i = tid; i < TB_RUNS; i += TB_THREADS) sh->runs[i] = make_short2(1, 0);
+            if (tid < 32) {
+                const bool found = tile_setup_warp(sh, n_cross, n_lines, pre_box);
+                in = found && tid == 0;
+                if (STATS && in && sh->bs.pass == 1) atomicAdd(&ctr->n_big_tiles, 1ull);
             }
         }
         // ---- the round's three phases, then its flush (one call site each)
-        round_phases<R, STATS>(sh, in, n_cross, n_lines, !tiling ? cnt : (sh->bs.pass == 0 ? cnt_none : cnt_big),
+        round_phases<R, STATS>(sh, in, n_cross, n_lines, tiling, !tiling ? cnt : (sh->bs.pass == 0 ? cnt_none : cnt_big),
                                tiling && sh->bs.pass == 0 ? nullptr : pc);
         round_flush<R>(sh, g, out, in, pre_box, mode, tiling ? sh->bs.scale : 0.f, tiling, sh->bs.s);
     }
@@ -1071,6 +1258,9 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         if (cnt_big.d) atomicAdd(&stats[1].d, cnt_big.d);
     }
 }
+
+// three FP32 blocks per SM: 228 KB of shared memory per SM, 1 KB of it reserved per block
+static_assert(3 * (sizeof(TetShared<float>) + 1024) <= 228 * 1024, "three FP32 blocks per SM");
 
 template <typename R>
 static size_t tet_shared_bytes() {

@@ -19,6 +19,10 @@ pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-11, 1: 1e-5}
 TOTAL_TOL = 1e-12
+# Cases whose simplices cross the walls of a non-periodic box.  The FP32-mixed path closes the mass
+# of every simplex, not of its part inside the box, so there its total inside the box is only as
+# exact as its cells (FP32 tolerance); the FP64 path keeps 1e-12.
+CLIPPED = {"rand3d_huge_walls"}
 
 
 @pytest.fixture(scope="module")
@@ -75,6 +79,10 @@ def _cases():
                                   (1.0,) * 3, False),
         "ragged_grid": mg.Mesh(*(lambda m: (m.pos, m.simplices, m.rho))(mg.make_config("c2", 8)), (29, 31, 33),
                                (0.0,) * 3, (1.0,) * 3, True),
+        # tetrahedra spanning many 18^3 tiles, with many cells entirely inside them (periodic, and
+        # clipped by the walls of a non-periodic box)
+        "rand3d_huge": mg.random_simplices(3, 6, 48, 22.0, np.random.default_rng(71)),
+        "rand3d_huge_walls": mg.random_simplices(3, 5, 40, 30.0, np.random.default_rng(72), periodic=False),
     }
 
 
@@ -91,10 +99,12 @@ def test_parity(proj, name, prec):
     err = np.max(np.abs(got - ref)) / scale
     assert err <= TOL[prec], f"{name}: max rel error {err:.3e}"
     tot = abs(got.sum() - ref.sum()) / abs(ref.sum())
-    assert tot <= TOTAL_TOL, f"{name}: total mass rel error {tot:.3e}"
+    ttol = TOL[1] if (prec == 1 and name in CLIPPED) else TOTAL_TOL
+    assert tot <= ttol, f"{name}: total mass rel error {tot:.3e}"
 
 
-@pytest.mark.parametrize("name", ["c2", "rand3d_tiled", "aligned_kuhn_16", "c1b", "rand2d_tiled"])
+@pytest.mark.parametrize("name", ["c2", "rand3d_tiled", "aligned_kuhn_16", "c1b", "rand2d_tiled", "rand3d_huge",
+                                  "rand3d_huge_walls"])
 def test_same_decisions_both_precisions(proj, name):
     mesh = CASES[name]
     _, s64 = _run(proj, mesh, 0, stats=True)

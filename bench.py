@@ -356,14 +356,12 @@ def run_ours(a):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the tetrahedron projection kernel, which also tiles the large
-    # tetrahedra: its incidences are all corners)
-    names = ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>"]
-    kern32 = kern32[:3]
-    kern64 = kern64[:3]
+    # roofline of the dominant kernel (the tetrahedron projection kernel; its incidences are all
+    # corners but those found on the tiles of the large tetrahedra, by k_project_big)
+    names = ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>", "k_project_big<float>"]
     dom = int(np.argmax(kern32))
     if dom == 2:
-        inc = {k: st32["corners_" + k] for k in "abcd"}
+        inc = {k: st32["corners_" + k] - st32["large_corners"][i] for i, k in enumerate("abcd")}
     else:
         inc = None
     if inc is not None:
@@ -397,7 +395,7 @@ def run_ours(a):
                                          "n_small", "n_large", "n_zero_volume", "exact_fallbacks")},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 3 * a.steps,  # vertex records, set-up, main kernel (one batch: <= 2^24 tets)
+        "gpu_launches": 4 * a.steps,  # vertex records, set-up, main kernel, large tetrahedra (one batch)
         "e2e": e2e,
     }
     if not a.no_batched:

@@ -93,7 +93,7 @@ typedef struct {
     uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
     uint64_t n_small;         /* simplices projected by the main kernel (3D: bounding box <= 1280 cells) */
     uint64_t n_large;         /* tetrahedra with a larger bounding box: projected tile by tile (18^3 cells)
-                                 by the main kernel after its chunks */
+                                 by the large-tetrahedron kernel */
     uint64_t n_large_tiles;   /* tiles of those tetrahedra */
     uint64_t corners_a;       /* (corner, cell) incidences of type A: grid node inside a simplex */
     uint64_t corners_b;       /* type B: simplex vertex */
@@ -217,7 +217,7 @@ CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 /* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 4:
  * [0] vertex records, [1] per-simplex set-up (3D: the first batch's; the single-cell closed form
  * is applied there), [2] main projection kernel (3D: with the set-up of any later batch),
- * [3] always ~0 (kept for the layout: the large tetrahedra are projected inside the main kernel).  *calls receives the number of timed cdp_project calls.
+ * [3] the large-tetrahedron kernel (3D: tetrahedra with a bounding box above 1280 cells, in tiles).  *calls receives the number of timed cdp_project calls.
  * Returns the number of slots written. */
 CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
 

@@ -180,6 +180,7 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     int fp32 = precision == CDP_FP32_MIXED;
     // a persistent grid: every resident block slot of the device, four times over
     L.small_blocks_per_sm = 4 * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
+    L.resident_per_sm = p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32];
     L.big_list = c->queue;
     L.big_cap = (long long)c->queue_cap;
     L.geo = c->geo;

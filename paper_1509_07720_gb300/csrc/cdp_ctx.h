@@ -48,7 +48,7 @@ struct cdp_ctx {
     cdp::Counters* h_ctr;     // pinned host mirrors
     cdp::UnitCounts* h_stats;
     // per-kernel timing: CDP_TEV events per timed call (before the vertex records, after them,
-    // after the set-up kernel, after the main kernel, and once more at the end), folded into
+    // after the set-up kernel, after the main kernel, after the large-tetrahedron kernel), folded into
     // totals[CDP_TEV - 1] when read
     int timing;
     std::vector<cudaEvent_t>* pending;

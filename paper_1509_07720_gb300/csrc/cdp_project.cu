@@ -588,9 +588,7 @@ cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaE
         return cudaSuccess;
     }
     if (L.g.dim == 3) {
-        cudaError_t e = launch_tet(L, fp32, st, after_setup);
-        if (mid) cudaEventRecord(mid, st);
-        return e;
+        return launch_tet(L, fp32, st, after_setup, mid);
     }
     if (after_setup) cudaEventRecord(after_setup, st);
     return fp32 ? launch_dim<2, float>(L, st, mid) : launch_dim<2, double>(L, st, mid);

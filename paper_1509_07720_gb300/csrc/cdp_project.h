@@ -33,7 +33,8 @@ struct LaunchArgs {
     Counters* ctr;
     UnitCounts* stats;  // may be null (else two blocks: chunks of the main kernel, tiled large tetrahedra)
     int num_sms;
-    int small_blocks_per_sm;
+    int small_blocks_per_sm;  // blocks per SM of the main kernel's grid (a multiple of resident_per_sm)
+    int resident_per_sm;      // resident blocks per SM of the main kernel
     int* big_list;      // tetrahedra whose bounding box exceeds the shared box (capacity big_cap),
                         // projected tile by tile by the main kernel
     long long big_cap;
@@ -50,13 +51,14 @@ cudaError_t configure_tet();
 int resident_blocks_tet(int fp32);
 // bytes of one geometry record of the tetrahedron kernel
 size_t tet_geo_bytes(int fp32);
-// set-up and main kernel over batches of geo_cap tetrahedra; `after_setup` (optional) is recorded
-// after the first batch's set-up kernel
-cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup);
+// set-up and main kernel over batches of geo_cap tetrahedra, then the large-tetrahedron kernel;
+// `after_setup` and `mid` (optional) are recorded after the first batch's set-up kernel and before
+// the large-tetrahedron kernel
+cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid);
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
                         const double* rho, cudaStream_t st);
 // `after_setup` and `mid` (optional) are recorded after the (first) set-up kernel and after the
-// main kernel
+// main kernel (3D: before the large-tetrahedron kernel)
 cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,
                            cudaEvent_t mid);
 

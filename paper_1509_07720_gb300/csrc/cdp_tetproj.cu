@@ -21,10 +21,13 @@
 // the end of the round the boxes are flushed with one FP64 global atomic per non-zero
 // (tetrahedron, cell) piece.
 //
-// Once its chunks are done, a block takes the large tetrahedra of the list one at a time and
-// projects each in tiles of 18^3 cells: one unit per tile, its record set up in the tile's frame,
-// its items (planes, lines, vertices) clipped to the tile, its box flushed by the whole block.
-// A corner on a tile face is evaluated in both tiles, each keeping the cells of its own.
+// k_project_big, launched after it, takes the large tetrahedra of the list one at a time per block
+// and projects each in tiles of 18^3 cells: one unit per tile, its record in the tile's frame, its
+// items (planes, lines, vertices) clipped to the tile, its box flushed by the whole block.  A
+// corner on a tile face is evaluated in both tiles, each keeping the cells of its own.  Tiles
+// outside a facet plane are skipped; the x lines leave their runs of inside grid nodes in a table,
+// from which a last phase takes the tile's cells column by column (a cell with all eight corners
+// inside gets its closed-form mass).
 //
 // FP32-mixed path only: the mass closure (not in the paper).  The FP64 closed-form masses of the
 // tetrahedra of a round minus the (two-float, exact enough) sum of their FP32 pieces is spread over
@@ -415,9 +418,9 @@ __device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>*
 
 // A pierced line (record of item_line_test): its D records (one per pierced facet, the cell along
 // the line located with the exact-sign search) and the run of A nodes between them (x lines only).
-template <typename R>
+template <typename R, bool TILE>
 __device__ __forceinline__ int item_line_facets(TetShared<R>* sh, int own, unsigned long long pr, Rec& r0,
-                                                Rec& r1, unsigned long long& arun, bool cells, UnitCounts* cnt) {
+                                                Rec& r1, unsigned long long& arun, UnitCounts* cnt) {
     const TetGeo<R>& G = sh->geo[own];
     const unsigned hits = (unsigned)(pr & 15u);
     const int l = (int)((pr >> 4) & 3u), dj = (int)((pr >> 6) & 2047u), dk = (int)((pr >> 17) & 2047u);
@@ -459,7 +462,7 @@ __device__ __forceinline__ int item_line_facets(TetShared<R>* sh, int own, unsig
     // round the line's entry of the run table
     const int cx0 = mlo + 1 > 0 ? mlo + 1 : 0, cx1 = mhi < sh->td[own][0] ? mhi : sh->td[own][0];
     if (l == 0 && npierced == 2 && cx1 >= cx0) {
-        if (cells)
+        if (TILE)
             sh->runs[dj + (TB_TE + 1) * dk] = make_short2((short)cx0, (short)cx1);
         else
             arun = (unsigned long long)cx0 | ((unsigned long long)cx1 << 11) | ((unsigned long long)dj << 22) |
@@ -641,18 +644,17 @@ __device__ __forceinline__ int upper_index(const int* pre, int u) {
 // The three phases of one round over the units of the block's shared records whose thread (index
 // < TB_NT) has `in` set: items dealt to the warps 32 at a time, located corners queued per warp and
 // evaluated in full batches into the units' boxes.  Every thread of the block calls it.
-template <typename R, bool STATS>
-__device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cross, int n_lines, bool cells,
-                                             UnitCounts& cnt, UnitCounts* pc) {
+template <typename R, bool STATS, bool TILE>
+__device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cross, int n_lines, UnitCounts& cnt,
+                                             UnitCounts* pc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Rec* const q = sh->q[warp];
     unsigned long long* const aq = sh->aq[warp];
     unsigned long long* const pq = sh->pq[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll 1
-    for (int ph = 0; ph < (cells ? 4 : 3); ++ph) {
-        const int mine =
-            in ? (ph == 0 ? 4 : (ph == 1 ? n_cross : (ph == 2 ? n_lines : sh->td[0][1] * sh->td[0][2]))) : 0;
+    for (int ph = 0; ph < 3; ++ph) {
+        const int mine = in ? (ph == 0 ? 4 : (ph == 1 ? n_cross : n_lines)) : 0;
         const int pre = block_scan(mine, sh->wsum);
         if (tid < TB_NT) sh->pre[tid] = pre;
         __syncthreads();
@@ -676,11 +678,8 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                     if (STATS) cnt.b++;
                 } else if (ph == 1) {
                     r0 = item_crossing(sh, own, t, pc);
-                } else if (ph == 2) {
-                    pline = item_line_test(sh, own, t, pc);
                 } else {
-                    const unsigned na = item_column(sh, t);
-                    if (STATS) cnt.a += na;
+                    pline = item_line_test(sh, own, t, pc);
                 }
             }
             // append located corners (C) or pierced lines to the warp's queues (warp-aggregated,
@@ -709,7 +708,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                     if ((unsigned)lane < pav) {
                         const unsigned long long pr = pq[(phead + lane) & (TB_PCAP - 1)];
                         lown = (int)((pr >> 28) & ((1u << TB_OWN_BITS) - 1u));
-                        nr = item_line_facets(sh, lown, pr, d0, d1, arun, cells, pc);
+                        nr = item_line_facets<R, TILE>(sh, lown, pr, d0, d1, arun, pc);
                     }
                     phead += pav < 32u ? pav : 32u;
                     const Rec ob = (Rec)lown << 40;
@@ -1008,7 +1007,7 @@ __device__ __forceinline__ bool tile_misses(const TetGeo<R>& B, const BigState& 
 // (edge, axis) pair per lane).  Returns whether a tile was found; lane 0 gets n_cross,
 // n_lines and pre_box, and moves bs.tile past the tile.
 template <typename R>
-__device__ __forceinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int& n_lines, int& pre_box) {
+__device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int& n_lines, int& pre_box) {
     const int lane = threadIdx.x & 31;
     BigState& b = sh->bs;
     const TetGeo<R>& B = sh->big0;
@@ -1096,14 +1095,14 @@ __device__ __forceinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, 
 // path from the summing pass to the flush pass (with the tetrahedron's closure scale), or close the
 // tetrahedron (FP32: the FP64 remainder to the cell of vertex 0) and take the next one of the list
 // (bs.ntiles < 0 when the list is exhausted).
-template <typename R, bool STATS>
+template <typename R>
 __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g, long long nv, const int* simp,
                                             const VertexRec* V, const int* big_list, long long big_cap,
-                                            double* out, Counters* ctr, int te) {
+                                            double* out, Counters* ctr) {
     constexpr bool fp32 = sizeof(R) == 4;
     BigState& b = sh->bs;
     if (fp32 && b.ntiles > 0) {
-        const TetGeo<R>& G = sh->geo[0];  // mexact is the same in every tile's record
+        const TetGeo<R>& G = sh->big0;
         if (b.pass == 0) {
             b.scale = b.s[2] > 0.f ? ((G.mexact_hi - b.s[0]) + (G.mexact_lo - b.s[1])) / b.s[2] : 0.f;
             b.pass = 1;
@@ -1112,11 +1111,10 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
             return;
         }
         // what the rounded pieces of the flush pass still miss of the closed-form mass, in FP64
-        const TetGeo<R>& B = sh->big0;
         const double left =
             (G.mexact - ((double)b.s[0] + (double)b.s[1])) - (double)b.scale * (double)b.s[2];
         const long long idx =
-            flat_cell(g, B.anchor[0] + B.cell[0][0], B.anchor[1] + B.cell[0][1], B.anchor[2] + B.cell[0][2]);
+            flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1], G.anchor[2] + G.cell[0][2]);
         if (idx >= 0) atomicAdd(out + idx, left);
     }
     // the next tetrahedron of the list (complete: every batch was set up before this launch)
@@ -1142,7 +1140,7 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
     int n = 1;
     for (int a = 0; a < 3; ++a) {
         b.ext[a] = good ? S.hi[a] - S.lo[a] + 1 : 0;
-        b.nt[a] = (b.ext[a] + te - 1) / te;
+        b.nt[a] = (b.ext[a] + TB_TE - 1) / TB_TE;
         n *= b.nt[a];
     }
     b.ntiles = n;
@@ -1153,10 +1151,70 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
     for (int t = 1; t < TB_NT; ++t) sh->boff[t] = -1;
 }
 
+// The chunks: block b takes chunks b, b + gridDim.x, ... of the batch's geometry records (thread
+// t < TB_NT speaks for tetrahedron t of the chunk) and projects them in rounds whose boxes fit
+// the block's slots together.
 template <typename R, bool STATS>
 __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
-    k_project_tet(GridDesc g, long long nb, long long nv, const TetGeo<R>* __restrict__ geo,
-                  const int* __restrict__ need_in, const int* __restrict__ simp, const VertexRec* __restrict__ V,
+    k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
+                  double* __restrict__ out, UnitCounts* __restrict__ stats) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int BOX = BoxCap<R>::value;
+    TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
+    UnitCounts cnt = {0, 0, 0, 0, 0};   // corner counts (registers)
+    UnitCounts xcnt = {0, 0, 0, 0, 0};  // exact-predicate count, updated through a pointer
+    UnitCounts* pc = STATS ? &xcnt : nullptr;
+    const long long nchunks = (nb + TB_NT - 1) / TB_NT;
+#pragma unroll 1
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        // ---- the chunk's geometry records (written by k_tet_setup) into shared memory
+        const long long first = chunk * TB_NT;
+        const long long last = first + TB_NT < nb ? first + TB_NT : nb;
+        __syncthreads();  // the previous chunk is done with the records
+        {
+            constexpr int W = sizeof(TetGeo<R>) / 8;
+            static_assert(sizeof(TetGeo<R>) % 8 == 0, "geometry records are copied in 8-byte words");
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(geo + first);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh->geo);
+            const int words = (int)(last - first) * W;
+            for (int w = tid; w < words; w += TB_THREADS) dst[w] = __ldg(src + w);
+        }
+        const int need = (tid < TB_NT && first + tid < nb) ? __ldg(need_in + first + tid) : 0;
+        __syncthreads();
+        int n_cross = 0, n_lines = 0;
+        if (need > 0) {
+            for (int a = 0; a < 3; ++a) sh->td[tid][a] = sh->geo[tid].hi[a] + 1;
+            unit_prepare(sh, tid, n_cross, n_lines);
+        }
+        bool pending = need > 0;
+        // ---- rounds: tetrahedra in chunk order while their boxes fit the block's slots together
+#pragma unroll 1
+        while (__syncthreads_or(pending)) {
+            const int pre_box = block_scan(pending ? need : 0, sh->wsum);
+            const bool in = pending && pre_box <= BOX;
+            pending = pending && !in;
+            if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
+            round_phases<R, STATS, false>(sh, in, n_cross, n_lines, cnt, pc);
+            round_flush<R>(sh, g, out, in, pre_box, FLUSH_CLOSE_ROUND, 0.f, false, nullptr);
+        }
+    }
+    if (STATS) {
+        if (cnt.a) atomicAdd(&stats->a, cnt.a);
+        if (cnt.b) atomicAdd(&stats->b, cnt.b);
+        if (cnt.c) atomicAdd(&stats->c, cnt.c);
+        if (cnt.d) atomicAdd(&stats->d, cnt.d);
+        if (xcnt.exact) atomicAdd(&stats->exact, xcnt.exact);
+    }
+}
+
+// The large tetrahedra of the list, taken one at a time by the blocks, each in tiles of TB_TE^3
+// cells: one unit per tile (thread 0 speaks for it), the block's rounds one tile each.  FP32 path in
+// two passes over a tetrahedron's tiles (the pieces' sums, then the flush with its closure scale).
+template <typename R, bool STATS>
+__global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
+    k_project_big(GridDesc g, long long nv, const int* __restrict__ simp, const VertexRec* __restrict__ V,
                   const int* __restrict__ big_list, long long big_cap, double* __restrict__ out,
                   Counters* __restrict__ ctr, UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1169,93 +1227,51 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         sh->bs.ntiles = 0;
         sh->bs.tile = 0;
     }
-    UnitCounts cnt = {0, 0, 0, 0, 0};       // corner counts of the chunks (registers)
-    UnitCounts cnt_big = {0, 0, 0, 0, 0};   // of the tiles of large tetrahedra (flush pass)
+    __syncthreads();  // the state is set before any thread reads it
+    UnitCounts cnt = {0, 0, 0, 0, 0};       // corner counts of the flush pass (registers)
     UnitCounts cnt_none = {0, 0, 0, 0, 0};  // (FP32 summing pass: not counted)
     UnitCounts xcnt = {0, 0, 0, 0, 0};      // exact-predicate count, updated through a pointer
     UnitCounts* pc = STATS ? &xcnt : nullptr;
-    const long long nchunks = (nb + TB_NT - 1) / TB_NT;
-
-    // chunk mode: thread t < TB_NT speaks for tetrahedron t of the block's current chunk.  Then
-    // tiling mode: the tetrahedra of the large-simplex list, one at a time, in tiles of TB_TE^3 cells
-    // (FP32 path in two passes: the tiles' piece sums, then the flush with the closure scale).
-    long long chunk = (long long)blockIdx.x - gridDim.x;
-    int need = 0, n_cross = 0, n_lines = 0;
-    bool pending = false, tiling = false;
+    int n_cross = 0, n_lines = 0;
 #pragma unroll 1
     for (;;) {
-        bool in;
-        int pre_box, mode;
-        if (!tiling) {
-            if (!__syncthreads_or(pending)) {
-                // ---- next chunk: its geometry records (written by k_tet_setup) into shared memory
-                // (the barrier above: the previous chunk is done with them)
-                chunk += gridDim.x;
-                if (chunk >= nchunks) {
-                    tiling = true;
-                    continue;
-                }
-                const long long first = chunk * TB_NT;
-                const long long last = first + TB_NT < nb ? first + TB_NT : nb;
-                {
-                    constexpr int W = sizeof(TetGeo<R>) / 8;
-                    static_assert(sizeof(TetGeo<R>) % 8 == 0, "geometry records are copied in 8-byte words");
-                    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(geo + first);
-                    unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh->geo);
-                    const int words = (int)(last - first) * W;
-                    for (int w = tid; w < words; w += TB_THREADS) dst[w] = __ldg(src + w);
-                }
-                need = (tid < TB_NT && first + tid < nb) ? __ldg(need_in + first + tid) : 0;
-                __syncthreads();
-                if (need > 0) {
-                    for (int a = 0; a < 3; ++a) sh->td[tid][a] = sh->geo[tid].hi[a] + 1;
-                    unit_prepare(sh, tid, n_cross, n_lines);
-                }
-                pending = need > 0;
-                continue;
-            }
-            // ---- a round: tetrahedra in chunk order while their boxes fit the block's slots together
-            pre_box = block_scan(pending ? need : 0, sh->wsum);
-            in = pending && pre_box <= BOX;
-            pending = pending && !in;
-            if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
-            mode = FLUSH_CLOSE_ROUND;
-        } else {
-            const bool advance = sh->bs.tile >= sh->bs.ntiles;
-            __syncthreads();  // every thread has read the state; the previous round is done
-            if (advance) {
-                if (tid == 0) big_advance<R, STATS>(sh, g, nv, simp, V, big_list, big_cap, out, ctr, TB_TE);
-                __syncthreads();
-                if (sh->bs.ntiles < 0) break;
-                continue;
-            }
-            // ---- a tile round: warp 0 finds the next tile the tetrahedron may meet and sets up its
-            // unit (thread 0), clipped to the tile; no unit when none is left (an empty round)
-            mode = sh->bs.pass == 0 ? FLUSH_SUM_ONLY : FLUSH_SCALED;
-            in = false;
-            pre_box = 0;
-            for (int i = tid; i < TB_RUNS; i += TB_THREADS) sh->runs[i] = make_short2(1, 0);
-            if (tid < 32) {
-                const bool found = tile_setup_warp(sh, n_cross, n_lines, pre_box);
-                in = found && tid == 0;
-                if (STATS && in && sh->bs.pass == 1) atomicAdd(&ctr->n_big_tiles, 1ull);
-            }
+        const bool advance = sh->bs.tile >= sh->bs.ntiles;
+        __syncthreads();  // every thread has read the state; the previous round is done
+        if (advance) {
+            if (tid == 0) big_advance<R>(sh, g, nv, simp, V, big_list, big_cap, out, ctr);
+            __syncthreads();
+            if (sh->bs.ntiles < 0) break;
+            continue;
         }
-        // ---- the round's three phases, then its flush (one call site each)
-        round_phases<R, STATS>(sh, in, n_cross, n_lines, tiling, !tiling ? cnt : (sh->bs.pass == 0 ? cnt_none : cnt_big),
-                               tiling && sh->bs.pass == 0 ? nullptr : pc);
-        round_flush<R>(sh, g, out, in, pre_box, mode, tiling ? sh->bs.scale : 0.f, tiling, sh->bs.s);
+        // ---- a tile round: warp 0 finds the next tile the tetrahedron may meet and sets up its unit
+        // (thread 0), clipped to the tile; no unit when none is left (an empty round)
+        const int mode = sh->bs.pass == 0 ? FLUSH_SUM_ONLY : FLUSH_SCALED;
+        bool in = false;
+        int pre_box = 0;
+        for (int i = tid; i < TB_RUNS; i += TB_THREADS) sh->runs[i] = make_short2(1, 0);
+        if (tid < 32) {
+            const bool found = tile_setup_warp(sh, n_cross, n_lines, pre_box);
+            in = found && tid == 0;
+            if (STATS && in && sh->bs.pass == 1) atomicAdd(&ctr->n_big_tiles, 1ull);
+        }
+        const bool counted = sh->bs.pass == 1;
+        round_phases<R, STATS, true>(sh, in, n_cross, n_lines, counted ? cnt : cnt_none, counted ? pc : nullptr);
+        // the cells of the tile, column by column, from the run table of the line phase
+        {
+            const int ncol = sh->boff[0] >= 0 ? sh->td[0][1] * sh->td[0][2] : 0;
+            unsigned na = 0;
+            for (int c = tid; c < ncol; c += TB_THREADS) na += item_column(sh, c);
+            if (STATS && counted) cnt.a += na;
+            __syncthreads();
+        }
+        round_flush<R>(sh, g, out, in, pre_box, mode, sh->bs.scale, true, sh->bs.s);
     }
     if (STATS) {
-        if (cnt.a) atomicAdd(&stats[0].a, cnt.a);
-        if (cnt.b) atomicAdd(&stats[0].b, cnt.b);
-        if (cnt.c) atomicAdd(&stats[0].c, cnt.c);
-        if (cnt.d) atomicAdd(&stats[0].d, cnt.d);
-        if (xcnt.exact) atomicAdd(&stats[0].exact, xcnt.exact);
-        if (cnt_big.a) atomicAdd(&stats[1].a, cnt_big.a);
-        if (cnt_big.b) atomicAdd(&stats[1].b, cnt_big.b);
-        if (cnt_big.c) atomicAdd(&stats[1].c, cnt_big.c);
-        if (cnt_big.d) atomicAdd(&stats[1].d, cnt_big.d);
+        if (cnt.a) atomicAdd(&stats->a, cnt.a);
+        if (cnt.b) atomicAdd(&stats->b, cnt.b);
+        if (cnt.c) atomicAdd(&stats->c, cnt.c);
+        if (cnt.d) atomicAdd(&stats->d, cnt.d);
+        if (xcnt.exact) atomicAdd(&stats->exact, xcnt.exact);
     }
 }
 
@@ -1269,7 +1285,10 @@ static size_t tet_shared_bytes() {
 
 template <typename R, bool STATS>
 static cudaError_t configure_one() {
-    return cudaFuncSetAttribute(k_project_tet<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_project_tet<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tet_shared_bytes<R>());
+    if (e) return e;
+    return cudaFuncSetAttribute(k_project_big<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tet_shared_bytes<R>());
 }
 
@@ -1302,37 +1321,41 @@ int resident_blocks_tet(int fp32) {
 size_t tet_geo_bytes(int fp32) { return fp32 ? sizeof(TetGeo<float>) : sizeof(TetGeo<double>); }
 
 template <typename R>
-static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_t after_setup) {
+static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid) {
     const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
+    const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
     for (long long s0 = 0; s0 < L.ns; s0 += batch) {
         const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
-        const bool last = s0 + nb >= L.ns;
         k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, 128 * sizeof(TetGeo<R>), st>>>(
             L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, reinterpret_cast<TetGeo<R>*>(L.geo), L.need,
             L.big_list, L.big_cap, L.stats != nullptr);
         if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
-        // the last batch's launch also projects the listed large tetrahedra (the list is complete
-        // once every batch is set up), on the whole persistent grid: blocks left without a chunk
-        // start on them at once
-        const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
         long long blocks = (nb + TB_NT - 1) / TB_NT;
-        if (last || blocks > cap) blocks = cap;
+        if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        const int* list = last ? L.big_list : nullptr;
-        const long long list_cap = last ? L.big_cap : 0;
         const TetGeo<R>* G = reinterpret_cast<const TetGeo<R>*>(L.geo);
         if (L.stats)
-            k_project_tet<R, true><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-                L.g, nb, L.nv, G, L.need, L.simplices, L.verts, list, list_cap, L.out, L.ctr, L.stats);
+            k_project_tet<R, true><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(L.g, nb, G, L.need,
+                                                                                               L.out, L.stats);
         else
-            k_project_tet<R, false><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-                L.g, nb, L.nv, G, L.need, L.simplices, L.verts, list, list_cap, L.out, L.ctr, nullptr);
+            k_project_tet<R, false><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(L.g, nb, G, L.need,
+                                                                                                L.out, nullptr);
     }
+    if (mid) cudaEventRecord(mid, st);
+    // the large tetrahedra listed by every batch's set-up (their number is read on the device; a
+    // block that finds the list exhausted exits at once): one block per resident slot
+    const long long big_blocks = (long long)L.num_sms * (L.resident_per_sm > 0 ? L.resident_per_sm : 1);
+    if (L.stats)
+        k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
+            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.ctr, L.stats + 1);
+    else
+        k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
+            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.ctr, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup) {
-    return fp32 ? launch_tet_r<float>(L, st, after_setup) : launch_tet_r<double>(L, st, after_setup);
+cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid) {
+    return fp32 ? launch_tet_r<float>(L, st, after_setup, mid) : launch_tet_r<double>(L, st, after_setup, mid);
 }
 
 }  // namespace cdp

@@ -172,7 +172,7 @@ def cdp_timing_enable(ctx, enable: bool) -> int:
 
 
 def cdp_timing_read(ctx):
-    """(per-kernel totals in ms [vertex records, set-up, main kernel, large-simplex pass], timed calls)."""
+    """(per-kernel totals in ms [vertex records, set-up, main kernel, large tetrahedra (3D)], timed calls)."""
     buf = (ctypes.c_double * 4)()
     calls = ctypes.c_int(0)
     rc = load_library().cdp_timing_read(ctx, buf, 4, ctypes.byref(calls))

@@ -903,7 +903,7 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
 
 // One thread per tetrahedron of the batch [s0, s0 + nb): canonicalise it (exact orientation, periodic
 // unwrap, cells), deposit a tetrahedron inside one cell at once (Algorithm 2, step 1), list one
-// whose bounding box exceeds the shared box for the large-simplex pass, and write the geometry of
+// whose bounding box exceeds the shared box as large (for k_project_big), and write the geometry of
 // every other one to geo[i] with need[i] = its bounding-box cell count (0: nothing more to do).
 template <typename R>
 __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, long long nb, long long nv,

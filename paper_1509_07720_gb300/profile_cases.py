@@ -1,0 +1,73 @@
+"""Named projection cases for profiling (ncu) and timing: ``python -m paper_1509_07720_gb300.profile_cases``.
+
+Each case builds its seeded synthetic mesh, puts it on ``cuda:0`` and projects it ``--reps`` times
+through the public API (``Projector.project``) with CUDA events around every call, then prints one
+JSON line with the times.  Cases:
+
+  c3           the 128^3 Kuhn lattice of the headline benchmark (``--scale n``: an n^3 lattice)
+  c5           one problem of the 64-problem batched workload (``--problem i``), projected alone
+  c5_3d        the 32 three-dimensional problems of that workload, one after the other
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def _device_mesh(torch, mesh):
+    d = torch.device("cuda:0")
+    return (torch.from_numpy(np.ascontiguousarray(mesh.pos)).to(d),
+            torch.from_numpy(np.ascontiguousarray(mesh.simplices)).to(d),
+            torch.from_numpy(np.ascontiguousarray(mesh.rho)).to(d),
+            torch.empty(tuple(mesh.grid), dtype=torch.float64, device=d))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["c3", "c5", "c5_3d"])
+    ap.add_argument("--scale", type=int, default=None, help="c3: lattice size (default 128)")
+    ap.add_argument("--problem", type=int, default=0, help="c5: problem index in [0, 64)")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import paper_1509_07720_gb300 as pkg
+    from paper_1509_07720_gb300 import build
+    from paper_1509_07720_gb300 import meshgen as mg
+
+    if not torch.cuda.is_available():
+        raise SystemExit("profile_cases needs a CUDA device")
+    build.build_library()
+    if a.case == "c3":
+        meshes = [mg.make_config("c3", a.scale)]
+    else:
+        batch = mg.make_batch("c5")
+        meshes = [batch[a.problem].mesh] if a.case == "c5" else [p.mesh for p in batch if p.mesh.dim == 3]
+    data = [(m, *_device_mesh(torch, m)) for m in meshes]
+    prec = pkg.CDP_FP32_MIXED if a.prec == "fp32" else pkg.CDP_FP64
+    proj = pkg.Projector(0)
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(a.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for m, pos, simp, rho, out in data:
+            proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec, out=out,
+                         stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    proj.check(stream)
+    print(json.dumps({"case": a.case, "scale": a.scale, "problem": a.problem if a.case == "c5" else None,
+                      "prec": a.prec, "simplices": int(sum(m.n_simplices for m in meshes)),
+                      "ms_per_rep": times}), flush=True)
+    proj.close()
+
+
+if __name__ == "__main__":
+    main()

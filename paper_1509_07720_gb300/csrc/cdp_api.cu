@@ -120,6 +120,13 @@ int grow_geo(cdp_ctx* c, size_t ns) {
     return grow(&c->need, &c->need_cap, n);
 }
 
+// the slots in which each block of the FP32 large-tetrahedron kernel keeps its tiles' pieces
+// between the two passes (CDP_TILE_STORE_PER_BLOCK tiles per resident block)
+int grow_tiles(cdp_ctx* c) {
+    const size_t blocks = (size_t)c->num_sms * (size_t)(c->blocks_small[1] > 0 ? c->blocks_small[1] : 1);
+    return grow(&c->tiles, &c->tiles_cap, blocks * cdp::CDP_TILE_STORE_PER_BLOCK * cdp::tet_tile_cells());
+}
+
 }  // namespace
 
 namespace cdp {
@@ -135,9 +142,12 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
         if ((size_t)probs[i].n_verts > nv) nv = (size_t)probs[i].n_verts;
         if ((size_t)probs[i].n_simplices > ns) ns = (size_t)probs[i].n_simplices;
     }
+    bool any3d = false;
+    for (int i = 0; i < n; ++i) any3d = any3d || probs[i].dim == 3;
     int rc = grow(&c->verts, &c->verts_cap, nv);
     if (rc) return rc;
     if ((rc = grow(&c->queue, &c->queue_cap, ns))) return rc;
+    if (any3d && (rc = grow_tiles(c))) return rc;
     return grow_geo(c, ns);
 }
 
@@ -148,6 +158,7 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     if (p->dim == 3 && ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1))) ||
                         (rc = grow_geo(c, (size_t)p->n_simplices))))
         return rc;
+    if (p->dim == 3 && precision == CDP_FP32_MIXED && (rc = grow_tiles(c))) return rc;
 
     LaunchArgs L;
     memset(&L, 0, sizeof(L));
@@ -185,6 +196,9 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     L.big_cap = (long long)c->queue_cap;
     L.geo = c->geo;
     L.need = c->need;
+    L.tile_store = c->tiles;
+    L.tile_store_cap = c->tiles_cap;
+    L.tile_store_per_block = cdp::CDP_TILE_STORE_PER_BLOCK;
     {
         size_t rec = cdp::tet_geo_bytes(fp32);
         long long by_bytes = rec ? (long long)(c->geo_cap / rec) : 0;
@@ -358,6 +372,7 @@ void cdp_destroy(cdp_ctx* c) {
     if (c->queue) cudaFree(c->queue);
     if (c->geo) cudaFree(c->geo);
     if (c->need) cudaFree(c->need);
+    if (c->tiles) cudaFree(c->tiles);
     if (c->ctr) cudaFree(c->ctr);
     if (c->stats) cudaFree(c->stats);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);

@@ -43,6 +43,8 @@ struct cdp_ctx {
     size_t geo_cap;
     int* need;            // their box sizes
     size_t need_cap;
+    float* tiles;         // FP32 pieces of large-tetrahedron tiles kept between the two passes
+    size_t tiles_cap;     // (floats)
     cdp::Counters* ctr;       // device
     cdp::UnitCounts* stats;   // device
     cdp::Counters* h_ctr;     // pinned host mirrors

@@ -38,6 +38,9 @@ struct LaunchArgs {
     int* big_list;      // tetrahedra whose bounding box exceeds the shared box (capacity big_cap),
                         // projected tile by tile by the main kernel
     long long big_cap;
+    float* tile_store;        // FP32 pieces of tiles kept between the two passes over a large tetrahedron
+    size_t tile_store_cap;    // (floats; null / 0: every tile is computed twice)
+    int tile_store_per_block; // tiles kept per block of the large-tetrahedron kernel
     void* geo;          // geometry records of one batch of tetrahedra (capacity geo_cap records)
     int* need;          // their box sizes (geo_cap entries)
     long long geo_cap;
@@ -51,6 +54,10 @@ cudaError_t configure_tet();
 int resident_blocks_tet(int fp32);
 // bytes of one geometry record of the tetrahedron kernel
 size_t tet_geo_bytes(int fp32);
+// cells of one tile of a large tetrahedron
+size_t tet_tile_cells();
+// tiles of a large tetrahedron whose FP32 pieces a block keeps between the two passes
+constexpr int CDP_TILE_STORE_PER_BLOCK = 64;
 // set-up and main kernel over batches of geo_cap tetrahedra, then the large-tetrahedron kernel;
 // `after_setup` and `mid` (optional) are recorded after the first batch's set-up kernel and before
 // the large-tetrahedron kernel

@@ -62,6 +62,7 @@ constexpr int TB_MAX_CELLS = 1280;
 // precisions, so that both take the same decisions tile by tile), and the x lines of one tile
 constexpr int TB_TE = 18;
 constexpr int TB_RUNS = (TB_TE + 1) * (TB_TE + 1);
+constexpr int TB_TILE_CELLS = TB_TE * TB_TE * TB_TE;
 
 template <typename R>
 struct BoxCap {
@@ -74,6 +75,7 @@ static_assert(BoxCap<float>::value >= TB_MAX_CELLS, "one tetrahedron's box must 
 struct BigState {
     int ext[3], nt[3];  // bounding-box extent (cells) and tiles along each axis
     int ntiles, tile;   // tiles, next tile; ntiles < 0: the list is exhausted
+    int live;           // tiles set up so far in this pass (those the tetrahedron may meet)
     int pass;           // FP32 path: 0 sums the tiles' pieces, 1 flushes them (FP64 path: always 1)
     float scale;        // closure scale of the flush pass
     float s[3];         // sum of the pieces as two floats (hi, lo) and the sum of their magnitudes
@@ -780,12 +782,13 @@ __device__ __forceinline__ void block_sum2(float& hi, float& lo, float& asum, fl
 
 // Flush every box of the round: one FP64 atomic per non-zero piece (FP32 path: and one more for its
 // share of the mass-closure residual, `scale` |piece|).  Every thread of the block calls it; the
-// piece sums of FLUSH_SUM_ONLY / FLUSH_SCALED are added into `sums` by thread 0.  With
+// piece sums of FLUSH_SUM_ONLY / FLUSH_SCALED are added into `sums` by thread 0, and FLUSH_SUM_ONLY
+// also copies the box to `store` when it is given.  With
 // `whole` (one unit, a tile) the whole block flushes that unit's box; otherwise each warp flushes
 // the boxes of every TB_WARPS-th unit.
 template <typename R>
 __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g, double* out, bool in, int pre_box,
-                                            int mode, float scale, bool whole, float* sums) {
+                                            int mode, float scale, bool whole, float* sums, float* store) {
     constexpr bool fp32 = sizeof(R) == 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // the round's units are a prefix of the box slots: the last one ends at the largest pre_box
@@ -809,7 +812,10 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
         }
         for (int e = tid; e < used_slots; e += TB_THREADS) {
             const float v = (float)sh->box[e];
-            if (mode == FLUSH_SUM_ONLY) sh->box[e] = R(0);
+            if (mode == FLUSH_SUM_ONLY) {
+                sh->box[e] = R(0);
+                if (store) store[e] = v;
+            }
             two_sum_acc(hi, lo, v);
             asum += fabsf(v);
         }
@@ -1060,6 +1066,7 @@ __device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int
         tet_frame_bounds(G);
         sh->boff[0] = 0;
         b.tile = t + 1;
+        b.live += 1;
     }
     // crossings of the (edge, axis) pairs with the tile's planes, as running counts
     int run = 0;
@@ -1107,6 +1114,7 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
             b.scale = b.s[2] > 0.f ? ((G.mexact_hi - b.s[0]) + (G.mexact_lo - b.s[1])) / b.s[2] : 0.f;
             b.pass = 1;
             b.tile = 0;
+            b.live = 0;
             b.s[0] = b.s[1] = b.s[2] = 0.f;
             return;
         }
@@ -1146,6 +1154,7 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
     b.ntiles = n;
     b.pass = fp32 ? 0 : 1;
     b.tile = 0;
+    b.live = 0;
     b.scale = 0.f;
     b.s[0] = b.s[1] = b.s[2] = 0.f;
     for (int t = 1; t < TB_NT; ++t) sh->boff[t] = -1;
@@ -1197,7 +1206,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             pending = pending && !in;
             if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
             round_phases<R, STATS, false>(sh, in, n_cross, n_lines, cnt, pc);
-            round_flush<R>(sh, g, out, in, pre_box, FLUSH_CLOSE_ROUND, 0.f, false, nullptr);
+            round_flush<R>(sh, g, out, in, pre_box, FLUSH_CLOSE_ROUND, 0.f, false, nullptr, nullptr);
         }
     }
     if (STATS) {
@@ -1216,10 +1225,12 @@ template <typename R, bool STATS>
 __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_project_big(GridDesc g, long long nv, const int* __restrict__ simp, const VertexRec* __restrict__ V,
                   const int* __restrict__ big_list, long long big_cap, double* __restrict__ out,
-                  Counters* __restrict__ ctr, UnitCounts* __restrict__ stats) {
+                  float* __restrict__ tile_store, int store_tiles, Counters* __restrict__ ctr,
+                  UnitCounts* __restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool fp32 = sizeof(R) == 4;
     constexpr int BOX = BoxCap<R>::value;
-    static_assert(TB_TE * TB_TE * TB_TE <= BOX, "a tile must fit the block's slots");
+    static_assert(TB_TILE_CELLS <= BOX, "a tile must fit the block's slots");
     TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
     const int tid = threadIdx.x;
     for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
@@ -1228,8 +1239,8 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         sh->bs.tile = 0;
     }
     __syncthreads();  // the state is set before any thread reads it
-    UnitCounts cnt = {0, 0, 0, 0, 0};       // corner counts of the flush pass (registers)
-    UnitCounts cnt_none = {0, 0, 0, 0, 0};  // (FP32 summing pass: not counted)
+    UnitCounts cnt = {0, 0, 0, 0, 0};       // corner counts of the counted pass (registers)
+    UnitCounts cnt_none = {0, 0, 0, 0, 0};  // (FP32 second pass: not counted)
     UnitCounts xcnt = {0, 0, 0, 0, 0};      // exact-predicate count, updated through a pointer
     UnitCounts* pc = STATS ? &xcnt : nullptr;
     int n_cross = 0, n_lines = 0;
@@ -1249,22 +1260,34 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         bool in = false;
         int pre_box = 0;
         for (int i = tid; i < TB_RUNS; i += TB_THREADS) sh->runs[i] = make_short2(1, 0);
+        // the corners are counted in the first pass (FP32: the second may reuse the stored pieces)
+        const int pass = sh->bs.pass;
+        const bool counted = fp32 ? pass == 0 : true;
         if (tid < 32) {
             const bool found = tile_setup_warp(sh, n_cross, n_lines, pre_box);
             in = found && tid == 0;
-            if (STATS && in && sh->bs.pass == 1) atomicAdd(&ctr->n_big_tiles, 1ull);
+            if (STATS && in && counted) atomicAdd(&ctr->n_big_tiles, 1ull);
         }
-        const bool counted = sh->bs.pass == 1;
-        round_phases<R, STATS, true>(sh, in, n_cross, n_lines, counted ? cnt : cnt_none, counted ? pc : nullptr);
-        // the cells of the tile, column by column, from the run table of the line phase
-        {
+        __syncthreads();  // the tile's unit (or its absence) is set up
+        // FP32: the first store_tiles tiles of a pass keep their pieces in the block's slots of
+        // tile_store between the two passes
+        const int j = sh->bs.live - 1;
+        const bool stored = fp32 && sh->boff[0] >= 0 && j < store_tiles;
+        float* const slot = stored ? tile_store + ((size_t)blockIdx.x * store_tiles + j) * TB_TILE_CELLS : nullptr;
+        if (pass == 1 && stored) {
+            // the pieces of the first pass, as they were
+            const int size = sh->td[0][0] * sh->td[0][1] * sh->td[0][2];
+            for (int e = tid; e < size; e += TB_THREADS) sh->box[e] = slot[e];
+        } else {
+            round_phases<R, STATS, true>(sh, in, n_cross, n_lines, counted ? cnt : cnt_none, counted ? pc : nullptr);
+            // the cells of the tile, column by column, from the run table of the line phase
             const int ncol = sh->boff[0] >= 0 ? sh->td[0][1] * sh->td[0][2] : 0;
             unsigned na = 0;
             for (int c = tid; c < ncol; c += TB_THREADS) na += item_column(sh, c);
             if (STATS && counted) cnt.a += na;
             __syncthreads();
         }
-        round_flush<R>(sh, g, out, in, pre_box, mode, sh->bs.scale, true, sh->bs.s);
+        round_flush<R>(sh, g, out, in, pre_box, mode, sh->bs.scale, true, sh->bs.s, pass == 0 ? slot : nullptr);
     }
     if (STATS) {
         if (cnt.a) atomicAdd(&stats->a, cnt.a);
@@ -1320,6 +1343,8 @@ int resident_blocks_tet(int fp32) {
 
 size_t tet_geo_bytes(int fp32) { return fp32 ? sizeof(TetGeo<float>) : sizeof(TetGeo<double>); }
 
+size_t tet_tile_cells() { return TB_TILE_CELLS; }
+
 template <typename R>
 static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid) {
     const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
@@ -1345,12 +1370,20 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     // the large tetrahedra listed by every batch's set-up (their number is read on the device; a
     // block that finds the list exhausted exits at once): one block per resident slot
     const long long big_blocks = (long long)L.num_sms * (L.resident_per_sm > 0 ? L.resident_per_sm : 1);
+    // FP32: each block keeps the pieces of up to tile_store_per_block tiles between the two passes
+    // of a tetrahedron (slots of TB_TILE_CELLS floats, per block index)
+    const int store_tiles = sizeof(R) == 4 && L.tile_store &&
+                                    L.tile_store_cap >= (size_t)big_blocks * L.tile_store_per_block * TB_TILE_CELLS
+                                ? L.tile_store_per_block
+                                : 0;
     if (L.stats)
         k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.ctr, L.stats + 1);
+            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
+            L.stats + 1);
     else
         k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.ctr, nullptr);
+            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
+            nullptr);
     return cudaGetLastError();
 }
 

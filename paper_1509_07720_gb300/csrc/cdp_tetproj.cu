@@ -179,6 +179,13 @@ __device__ __forceinline__ int cross_cell_regs(const TetGeo<R>& G, int a, int b,
     int d = guess < lo ? lo : (guess > hi ? hi : guess);
     const R du = xbj - xaj, dv = xbk - xak;
     const R A = du * (R(c) - xak);
+    {
+        // the common case: both planes around the guess decided by the filter, the crossing
+        // between them (the same expressions and decisions as the search below)
+        const R v0 = A - dv * (R(d) - xaj), v1 = A - dv * (R(d + 1) - xaj);
+        const R s0 = dirk > 0 ? v0 : -v0, s1 = dirk > 0 ? v1 : -v1;
+        if ((d == lo || s0 > B2) && (d == hi || s1 < -B2)) return d;
+    }
     bool upper = false;  // false: checking plane d (want the crossing above it), true: plane d + 1
 #pragma unroll 1
     for (int it = 0; it < 2 * (hi - lo) + 4; ++it) {
@@ -223,6 +230,16 @@ __device__ __forceinline__ int facet_line_cell_regs(const TetGeo<R>& G, int f, i
                                                     int lo, int hi, int up, const R nf[3], const R xf[3], R B3,
                                                     UnitCounts* cnt) {
     int m = guess < lo ? lo : (guess > hi ? hi : guess);
+    {
+        // the common case: the nodes m and m + 1 decided by the filter, on either side of the
+        // facet (the same expressions and decisions as the search below)
+        const int g00 = l == 0 ? m : dj, g01 = l == 1 ? m : (l == 0 ? dj : dk), g02 = l == 2 ? m : dk;
+        const int g10 = l == 0 ? m + 1 : dj, g11 = l == 1 ? m + 1 : (l == 0 ? dj : dk), g12 = l == 2 ? m + 1 : dk;
+        const R v0 = nf[0] * (R(g00) - xf[0]) + nf[1] * (R(g01) - xf[1]) + nf[2] * (R(g02) - xf[2]);
+        const R v1 = nf[0] * (R(g10) - xf[0]) + nf[1] * (R(g11) - xf[1]) + nf[2] * (R(g12) - xf[2]);
+        const R s0 = up > 0 ? v0 : -v0, s1 = up > 0 ? v1 : -v1;
+        if ((m == lo || s0 < -B3) && (m == hi || s1 > B3)) return m;
+    }
     bool upper = false;
 #pragma unroll 1
     for (int it = 0; it < 2 * (hi - lo) + 4; ++it) {

@@ -789,7 +789,10 @@ CDP_HD R facet_face_terms(const R n[3], int k, R su, R sigma, const R P[3], R Pn
 }
 
 // D corner (facet f pierced by the grid line along l at (dj, dk), in cell column m): the values
-// of the 4 cells (oj, ok) = (0,0), (0,1), (1,0), (1,1), passed to acc(cell, value)
+// of the 4 cells (oj, ok) = (0,0), (0,1), (1,0), (1,1), passed to acc(cell, value).  The cells
+// share the slab m along l and, pairwise, their columns along j and k, so their piece origins (and
+// the corner's offsets P from them) take 1 + 2 + 2 values; the density at the corner is the same for
+// all four.
 template <typename R, class Acc>
 CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m, Acc& acc) {
     int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
@@ -804,23 +807,30 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
     R hj = cross_comp(g, n, j), hk = cross_comp(g, n, k);
     R irj2 = rcp_fast(nk * nk + nl * nl), irk2 = rcp_fast(nj * nj + nl * nl);
     R gj = pick3(g[0], g[1], g[2], j), gk = pick3(g[0], g[1], g[2], k), gl = pick3(g[0], g[1], g[2], l);
-    R xl_ = G.x[va][l], xll = G.xl[va][l] + off;
     const TetFrame<R> F = tet_frame(G);
+    const R cl = pick3(F.c[0], F.c[1], F.c[2], l), cj = pick3(F.c[0], F.c[1], F.c[2], j),
+            ck = pick3(F.c[0], F.c[1], F.c[2], k);
+    // piece origins (the centroid clamped into the central half of each cell) and offsets of the
+    // corner from them, along l (shared) and along j, k (two values each)
+    const R Ol = clamp_r(cl, R(m) + R(0.25), R(m) + R(0.75));
+    const R Pl = (G.x[va][l] - Ol) + (G.xl[va][l] + off);
+    const R Oj0 = clamp_r(cj, R(dj - 1) + R(0.25), R(dj - 1) + R(0.75)), Oj1 = clamp_r(cj, R(dj) + R(0.25), R(dj) + R(0.75));
+    const R Ok0 = clamp_r(ck, R(dk - 1) + R(0.25), R(dk - 1) + R(0.75)), Ok1 = clamp_r(ck, R(dk) + R(0.25), R(dk) + R(0.75));
+    const R Pj0 = R(dj) - Oj0, Pj1 = R(dj) - Oj1, Pk0 = R(dk) - Ok0, Pk1 = R(dk) - Ok1;
+    // the density at the corner
+    const R rhoX = F.rhoc + gl * (Pl + (Ol - cl)) + gj * (Pj0 + (Oj0 - cj)) + gk * (Pk0 + (Ok0 - ck));
+    const R PnL = Pl * nl;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
-        int oj = q >> 1, ok = q & 1;
-        int vj = dj - 1 + oj, vk = dk - 1 + ok;
-        int v0 = l == 0 ? m : vj;
-        int v1 = l == 1 ? m : (l == 0 ? vj : vk);
-        int v2 = l == 2 ? m : vk;
-        R O[3];
-        piece_origin(F, v0, v1, v2, O);
-        R Pl = (xl_ - pick3(O[0], O[1], O[2], l)) + xll;
-        R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
+        const int oj = q >> 1, ok = q & 1;
+        const int vj = dj - 1 + oj, vk = dk - 1 + ok;
+        const int v0 = l == 0 ? m : vj;
+        const int v1 = l == 1 ? m : (l == 0 ? vj : vk);
+        const int v2 = l == 2 ? m : vk;
+        const R Pj = oj ? Pj1 : Pj0, Pk = ok ? Pk1 : Pk0;
         const R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
-        R rhoX = rho_from_P(F, P, O);
-        R sj = oj ? R(1) : R(-1), sk = ok ? R(1) : R(-1);
-        R Pn = dot3(P, n);
+        const R sj = oj ? R(1) : R(-1), sk = ok ? R(1) : R(-1);
+        const R Pn = PnL + Pj * nj + Pk * nk;
         R s12 = tau * sj * sk * Pj * Pk * Pl * (R(2) * rhoX - R(1.5) * Pl * gl - R(0.75) * (Pj * gj + Pk * gk));
         // facet/face_j line oriented towards the k side (sign sk eps tau), facet/face_k towards j
         R s34 = facet_face_terms(n, j, sk * eps * tau, sj, P, Pn, gn, hj, irj2, rhoX, g);
@@ -868,22 +878,37 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
     const R xa[3] = {G.x[a][0], G.x[a][1], G.x[a][2]};
     const R dx[3] = {G.xl[a][0] + t * ev[0], G.xl[a][1] + t * ev[1], G.xl[a][2] + t * ev[2]};
     const TetFrame<R> F = tet_frame(G);
+    // the two cells differ only along k: the piece origins share their other components, and so do
+    // the corner's offsets P from them; the dot products with P share those terms
+    R P[3];
+    {
+        const int vv0 = j1 == 0 ? cj1 : cj2, vv1 = j1 == 1 ? cj1 : cj2, vv2 = j1 == 2 ? cj1 : cj2;
+        R O[3];
+        piece_origin(F, vv0, vv1, vv2, O);  // (its k component is replaced below)
+        for (int w = 0; w < 3; ++w) P[w] = (xa[w] - O[w]) + dx[w];
+    }
+    P[0] = k == 0 ? R(0) : P[0];
+    P[1] = k == 1 ? R(0) : P[1];
+    P[2] = k == 2 ? R(0) : P[2];
+    const R ek = pick3(eu[0], eu[1], eu[2], k), mpk = pick3(mp[0], mp[1], mp[2], k),
+            mqk = pick3(mq[0], mq[1], mq[2], k), npk = pick3(np_[0], np_[1], np_[2], k),
+            nqk = pick3(nq_[0], nq_[1], nq_[2], k);
+    const R Pe0 = dot3(P, eu), Pmp0 = dot3(P, mp), Pmq0 = dot3(P, mq), Pnp0 = dot3(P, np_), Pnq0 = dot3(P, nq_);
+    const R ckc = pick3(F.c[0], F.c[1], F.c[2], k);
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         int vk = side ? c : c - 1;
         int v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
         int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
         int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
-        R O[3], P[3];
-        piece_origin(F, v0, v1, v2, O);
-        for (int w = 0; w < 3; ++w) P[w] = (xa[w] - O[w]) + dx[w];
-        R Pk = R(c) - pick3(O[0], O[1], O[2], k);
+        const R Pk = R(c) - clamp_r(ckc, R(vk) + R(0.25), R(vk) + R(0.75));
         P[0] = k == 0 ? Pk : P[0];
         P[1] = k == 1 ? Pk : P[1];
         P[2] = k == 2 ? Pk : P[2];
         R sigma = side ? R(1) : R(-1);
         R so = sigma * R(dirk);
-        R Pe = dot3(P, eu), Pmp = dot3(P, mp), Pmq = dot3(P, mq), Pnp = dot3(P, np_), Pnq = dot3(P, nq_);
+        R Pe = Pe0 + Pk * ek, Pmp = Pmp0 + Pk * mpk, Pmq = Pmq0 + Pk * mqk, Pnp = Pnp0 + Pk * npk,
+          Pnq = Pnq0 + Pk * nqk;
         // the simplex edge with its two facets
         R s12 = so * Pe *
                 (Pmp * Pnp * (rhoX - R(0.75) * Pe * ge - R(0.5) * Pmp * gmp - R(0.25) * Pnp * gnp) +

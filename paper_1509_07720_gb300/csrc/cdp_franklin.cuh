@@ -772,21 +772,12 @@ CDP_HD R cross_comp(const R a[3], const R b[3], int i) {
     return pick3(c0, c1, c2, i);
 }
 
-// Facet-face triples of one simplex facet (unit normal n) meeting the cell face normal to axis k:
-// the line facet/face oriented by `su`, sigma = side of the cell, P and g, Pn = P.n, gn = g.n,
-// h = (g x n)_k, ir2 = 1 / (1 - n_k^2).  Returns the sum of the two triple terms (times -6).
-template <typename R>
-CDP_HD R facet_face_terms(const R n[3], int k, R su, R sigma, const R P[3], R Pn, R gn, R h, R ir2, R rhoX,
-                          const R g[3]) {
-    R nk = pick3(n[0], n[1], n[2], k), Pk = pick3(P[0], P[1], P[2], k), gk = pick3(g[0], g[1], g[2], k);
-    R cpk = cross_comp(P, n, k);
-    R lead = R(0.75) * cpk * h * ir2;
-    R d3 = Pk - nk * Pn, e3 = gk - nk * gn;
-    R d4 = Pn - nk * Pk, e4 = gn - nk * gk;
-    R br3 = rhoX - lead - R(0.5) * d3 * e3 * ir2 - R(0.25) * Pn * gn;
-    R br4 = rhoX - lead - R(0.5) * d4 * e4 * ir2 - R(0.25) * Pk * gk;
-    return su * sigma * cpk * ir2 * (d3 * Pn * br3 + d4 * Pk * br4);
-}
+// Facet-face triples: a simplex facet (unit normal n) meets the cell face normal to axis a along a
+// line, oriented by su, on the side sigma of the cell.  With Pn = P.n, gn = g.n, h = (g x n)_a,
+// ir2 = 1 / (1 - n_a^2), c = (P x n)_a, d3 = P_a - n_a Pn, d4 = Pn - n_a P_a, e3 = g_a - n_a gn,
+// e4 = gn - n_a g_a and b = rho(X) - (3/4) c h ir2, its two triples sum (times -6) to
+//   su sigma c ir2 [d3 Pn (b - d3 e3 ir2 / 2 - Pn gn / 4) + d4 P_a (b - d4 e4 ir2 / 2 - P_a g_a / 4)].
+// tet_eval_D4 and tet_eval_C2 write this out with the factors their cells share taken out.
 
 // D corner (facet f pierced by the grid line along l at (dj, dk), in cell column m): the values
 // of the 4 cells (oj, ok) = (0,0), (0,1), (1,0), (1,1), passed to acc(cell, value).  The cells
@@ -820,6 +811,15 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
     // the density at the corner
     const R rhoX = F.rhoc + gl * (Pl + (Ol - cl)) + gj * (Pj0 + (Oj0 - cj)) + gk * (Pk0 + (Ok0 - ck));
     const R PnL = Pl * nl;
+    // the facet-face triples of the two cell faces through the line (normal to j and to k): their
+    // per-record factors, and the cross-product components
+    // (P x n)_j = eps (Pk nl - Pl nk), (P x n)_k = eps (Pl nj - Pj nl), whose sign eps cancels
+    // against the orientation of the facet/face lines
+    const R Lj = R(0.75) * eps * hj * irj2, Lk = R(0.75) * eps * hk * irk2;
+    const R hj3 = R(0.5) * (gj - nj * gn) * irj2, hj4 = R(0.5) * (gn - nj * gj) * irj2;
+    const R hk3 = R(0.5) * (gk - nk * gn) * irk2, hk4 = R(0.5) * (gn - nk * gk) * irk2;
+    const R qgn = R(0.25) * gn, qgj = R(0.25) * gj, qgk = R(0.25) * gk;
+    const R T0 = R(2) * rhoX - R(1.5) * Pl * gl;
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
         const int oj = q >> 1, ok = q & 1;
@@ -828,14 +828,19 @@ CDP_HD void tet_eval_D4(const TetGeo<R>& G, int f, int l, int dj, int dk, int m,
         const int v1 = l == 1 ? m : (l == 0 ? vj : vk);
         const int v2 = l == 2 ? m : vk;
         const R Pj = oj ? Pj1 : Pj0, Pk = ok ? Pk1 : Pk0;
-        const R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
-        const R sj = oj ? R(1) : R(-1), sk = ok ? R(1) : R(-1);
         const R Pn = PnL + Pj * nj + Pk * nk;
-        R s12 = tau * sj * sk * Pj * Pk * Pl * (R(2) * rhoX - R(1.5) * Pl * gl - R(0.75) * (Pj * gj + Pk * gk));
-        // facet/face_j line oriented towards the k side (sign sk eps tau), facet/face_k towards j
-        R s34 = facet_face_terms(n, j, sk * eps * tau, sj, P, Pn, gn, hj, irj2, rhoX, g);
-        R s56 = facet_face_terms(n, k, -sj * eps * tau, sk, P, Pn, gn, hk, irk2, rhoX, g);
-        acc(v0, v1, v2, R(-1.0 / 6.0) * (s12 + s34 + s56));
+        // the facet with the two faces' line
+        const R s12 = Pj * Pk * Pl * (T0 - R(0.75) * (Pj * gj + Pk * gk));
+        // facet / face normal to j
+        const R Cj = Pk * nl - Pl * nk;
+        const R d3j = Pj - nj * Pn, d4j = Pn - nj * Pj, b0j = rhoX - Lj * Cj;
+        const R Fj = d3j * Pn * (b0j - d3j * hj3 - Pn * qgn) + d4j * Pj * (b0j - d4j * hj4 - Pj * qgj);
+        // facet / face normal to k
+        const R Ck = Pl * nj - Pj * nl;
+        const R d3k = Pk - nk * Pn, d4k = Pn - nk * Pk, b0k = rhoX - Lk * Ck;
+        const R Fk = d3k * Pn * (b0k - d3k * hk3 - Pn * qgn) + d4k * Pk * (b0k - d4k * hk4 - Pk * qgk);
+        const R sgn = (oj == ok ? tau : -tau) * R(-1.0 / 6.0);
+        acc(v0, v1, v2, sgn * (s12 + Cj * irj2 * Fj - Ck * irk2 * Fk));
     }
 }
 
@@ -895,6 +900,15 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
             nqk = pick3(nq_[0], nq_[1], nq_[2], k);
     const R Pe0 = dot3(P, eu), Pmp0 = dot3(P, mp), Pmq0 = dot3(P, mq), Pnp0 = dot3(P, np_), Pnq0 = dot3(P, nq_);
     const R ckc = pick3(F.c[0], F.c[1], F.c[2], k);
+    // the facet-face triples of the two facets with the face normal to k: (P x n)_k has no P_k in
+    // it, so it and the bracket's lead b are the same for both cells
+    const R gkk = pick3(g[0], g[1], g[2], k), qgk = R(0.25) * gkk;
+    const R cpp = cross_comp(P, np_, k), cpq = cross_comp(P, nq_, k);
+    const R bp = rhoX - R(0.75) * cpp * hp * irp2, bq = rhoX - R(0.75) * cpq * hq * irq2;
+    const R hp3 = R(0.5) * (gkk - npk * gnp) * irp2, hp4 = R(0.5) * (gnp - npk * gkk) * irp2;
+    const R hq3 = R(0.5) * (gkk - nqk * gnq) * irq2, hq4 = R(0.5) * (gnq - nqk * gkk) * irq2;
+    const R qgnp = R(0.25) * gnp, qgnq = R(0.25) * gnq;
+    const R Wp = lam * cpp * irp2, Wq = -lam * cpq * irq2;
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         int vk = side ? c : c - 1;
@@ -902,9 +916,6 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
         int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
         int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
         const R Pk = R(c) - clamp_r(ckc, R(vk) + R(0.25), R(vk) + R(0.75));
-        P[0] = k == 0 ? Pk : P[0];
-        P[1] = k == 1 ? Pk : P[1];
-        P[2] = k == 2 ? Pk : P[2];
         R sigma = side ? R(1) : R(-1);
         R so = sigma * R(dirk);
         R Pe = Pe0 + Pk * ek, Pmp = Pmp0 + Pk * mpk, Pmq = Pmq0 + Pk * mqk, Pnp = Pnp0 + Pk * npk,
@@ -913,8 +924,9 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
         R s12 = so * Pe *
                 (Pmp * Pnp * (rhoX - R(0.75) * Pe * ge - R(0.5) * Pmp * gmp - R(0.25) * Pnp * gnp) +
                  Pmq * Pnq * (rhoX - R(0.75) * Pe * ge - R(0.5) * Pmq * gmq - R(0.25) * Pnq * gnq));
-        R s34 = facet_face_terms(np_, k, lam, sigma, P, Pnp, gnp, hp, irp2, rhoX, g);
-        R s56 = facet_face_terms(nq_, k, -lam, sigma, P, Pnq, gnq, hq, irq2, rhoX, g);
+        const R d3p = Pk - npk * Pnp, d4p = Pnp - npk * Pk, d3q = Pk - nqk * Pnq, d4q = Pnq - nqk * Pk;
+        const R s34 = sigma * Wp * (d3p * Pnp * (bp - d3p * hp3 - Pnp * qgnp) + d4p * Pk * (bp - d4p * hp4 - Pk * qgk));
+        const R s56 = sigma * Wq * (d3q * Pnq * (bq - d3q * hq3 - Pnq * qgnq) + d4q * Pk * (bq - d4q * hq4 - Pk * qgk));
         acc(v0, v1, v2, R(-1.0 / 6.0) * (s12 + s34 + s56));
     }
 }

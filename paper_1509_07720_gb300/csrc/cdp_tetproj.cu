@@ -107,12 +107,20 @@ struct TetShared {
 // ------------------------------------------------------------------------------------------
 // accumulation into the box of tetrahedron `own` (cell (x, y, z) of its bounding box)
 // ------------------------------------------------------------------------------------------
+// The box of unit `own` with its dimensions read once: add(x, y, z, v) accumulates v into cell
+// (x, y, z) of the unit's box (bounds-checked; cells outside the box, which a tile clips, are
+// dropped).
 template <typename R>
-__device__ __forceinline__ void box_add(TetShared<R>* sh, int own, int x, int y, int z, R v) {
-    const int ex = sh->td[own][0], ey = sh->td[own][1], ez = sh->td[own][2];
-    if ((unsigned)x < (unsigned)ex && (unsigned)y < (unsigned)ey && (unsigned)z < (unsigned)ez)
-        atomicAdd(&sh->box[sh->boff[own] + x + ex * (y + ey * z)], v);
-}
+struct BoxAcc {
+    R* box;
+    int ex, ey, ez;
+    __device__ __forceinline__ BoxAcc(TetShared<R>* sh, int own)
+        : box(sh->box + sh->boff[own]), ex(sh->td[own][0]), ey(sh->td[own][1]), ez(sh->td[own][2]) {}
+    __device__ __forceinline__ void operator()(int x, int y, int z, R v) const {
+        if ((unsigned)x < (unsigned)ex && (unsigned)y < (unsigned)ey && (unsigned)z < (unsigned)ez)
+            atomicAdd(&box[x + ex * (y + ey * z)], v);
+    }
+};
 
 // ------------------------------------------------------------------------------------------
 // items
@@ -328,7 +336,8 @@ __device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
     R O[3], P[3];
     piece_origin(G, v0, v1, v2, O);
     for (int a = 0; a < 3; ++a) P[a] = (G.x[i][a] - O[a]) + G.xl[i][a];
-    box_add(sh, own, v0, v1, v2, tet_corner_B(G, i, P));
+    BoxAcc<R> acc(sh, own);
+    acc(v0, v1, v2, tet_corner_B(G, i, P));
 }
 
 // crossing t of tetrahedron own: its C record (the crossing point's cells along the two other axes
@@ -498,7 +507,7 @@ template <typename R, bool STATS>
 __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, UnitCounts& cnt) {
     const int own = (int)((r >> 40) & ((1 << TB_OWN_BITS) - 1));
     const TetGeo<R>& G = sh->geo[own];
-    auto acc = [&](int x, int y, int z, R v) { box_add(sh, own, x, y, z, v); };
+    BoxAcc<R> acc(sh, own);
     if (is_c) {
         int e, k, c, cj1, cj2;
         decode_C(r, e, k, c, cj1, cj2);
@@ -519,17 +528,27 @@ __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, U
     const int cx0 = (int)(r & 2047), cx1 = (int)((r >> 11) & 2047);
     const int dj = (int)((r >> 22) & 2047), dk = (int)((r >> 33) & 2047);
     const TetFrame<R> F = tet_frame(sh->geo[own]);
+    BoxAcc<R> acc(sh, own);
+    // the cells of the run's nodes share their columns along y and z: two piece-origin components
+    // along each (the centroid clamped into the central half of the cell), and the offsets of the
+    // nodes from them; the density at a node is the same for its 8 cells
+    const R Py0 = R(dj) - clamp_r(F.c[1], R(dj - 1) + R(0.25), R(dj - 1) + R(0.75)),
+            Py1 = R(dj) - clamp_r(F.c[1], R(dj) + R(0.25), R(dj) + R(0.75));
+    const R Pz0 = R(dk) - clamp_r(F.c[2], R(dk - 1) + R(0.25), R(dk - 1) + R(0.75)),
+            Pz1 = R(dk) - clamp_r(F.c[2], R(dk) + R(0.25), R(dk) + R(0.75));
+    const R ryz = F.rhoc + F.g[1] * (R(dj) - F.c[1]) + F.g[2] * (R(dk) - F.c[2]);
 #pragma unroll 1
     for (int cx = cx0; cx <= cx1; ++cx) {
+        const R Px0 = R(cx) - clamp_r(F.c[0], R(cx - 1) + R(0.25), R(cx - 1) + R(0.75)),
+                Px1 = R(cx) - clamp_r(F.c[0], R(cx) + R(0.25), R(cx) + R(0.75));
+        const R rhoX = ryz + F.g[0] * (R(cx) - F.c[0]);
 #pragma unroll 1
         for (int o = 0; o < 8; ++o) {
-            const int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
-            R O[3];
-            piece_origin(F, v0, v1, v2, O);
-            const R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            const R P[3] = {ox ? Px1 : Px0, oy ? Py1 : Py0, oz ? Pz1 : Pz0};
             // the node is the cell's upper corner along a when the cell index is node - 1
-            const R sg = R(((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1));
-            box_add(sh, own, v0, v1, v2, tet_corner_A(F, P, rho_from_P(F, P, O), sg));
+            const R sg = R((ox ? -1 : 1) * (oy ? -1 : 1) * (oz ? -1 : 1));
+            acc(cx - 1 + ox, dj - 1 + oy, dk - 1 + oz, tet_corner_A(F, P, rhoX, sg));
         }
         if (STATS) cnt.a += 8;
     }

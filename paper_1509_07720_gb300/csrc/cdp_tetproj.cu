@@ -369,21 +369,40 @@ __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, in
     const R evk = (xbk - xak) + (G.xl[b][k] - G.xl[a][k]);
     const R tt = div_guess((R(c) - xak) - G.xl[a][k], evk);
     const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-    int cj0 = 0, cj1 = 0;
-#pragma unroll 1
+    // the cells along the two other axes: both rounded guesses decided by the filter side by side
+    // (the common case), else the search of cross_cell_regs for the undecided one(s)
+    int cjw[2];
+    bool okw[2];
+#pragma unroll
     for (int w = 0; w < 2; ++w) {
         const int j = w == 0 ? j1 : j2;
         const R xaj = pick3(xa0, xa1, xa2, j), xbj = pick3(xb0, xb1, xb2, j);
         const R evj = (xbj - xaj) + (G.xl[b][j] - G.xl[a][j]);
         const int caj = pick3(ca0, ca1, ca2, j), cbj = pick3(cb0, cb1, cb2, j);
         const int lo = caj < cbj ? caj : cbj, hi = caj < cbj ? cbj : caj;
-        const int cw = cross_cell_regs(G, a, b, j, k, c, xaj, xak, xbj, xbk, lo, hi, (int)floor_r(xaj + tt * evj),
-                                       dirk, B2, cnt);
-        if (w == 0)
-            cj0 = cw;
-        else
-            cj1 = cw;
+        const int guess = (int)floor_r(xaj + tt * evj);
+        const int d = guess < lo ? lo : (guess > hi ? hi : guess);
+        const R du = xbj - xaj, dv = xbk - xak;
+        const R A = du * (R(c) - xak);
+        const R v0 = A - dv * (R(d) - xaj), v1 = A - dv * (R(d + 1) - xaj);
+        const R s0 = dirk > 0 ? v0 : -v0, s1 = dirk > 0 ? v1 : -v1;
+        cjw[w] = d;
+        okw[w] = (d == lo || s0 > B2) && (d == hi || s1 < -B2);
     }
+    if (!(okw[0] && okw[1])) {
+#pragma unroll 1
+        for (int w = 0; w < 2; ++w) {
+            if (okw[w]) continue;
+            const int j = w == 0 ? j1 : j2;
+            const R xaj = pick3(xa0, xa1, xa2, j), xbj = pick3(xb0, xb1, xb2, j);
+            const R evj = (xbj - xaj) + (G.xl[b][j] - G.xl[a][j]);
+            const int caj = pick3(ca0, ca1, ca2, j), cbj = pick3(cb0, cb1, cb2, j);
+            const int lo = caj < cbj ? caj : cbj, hi = caj < cbj ? cbj : caj;
+            cjw[w] = cross_cell_regs(G, a, b, j, k, c, xaj, xak, xbj, xbk, lo, hi, (int)floor_r(xaj + tt * evj), dirk,
+                                     B2, cnt);
+        }
+    }
+    const int cj0 = cjw[0], cj1 = cjw[1];
     if ((unsigned)cj0 >= (unsigned)sh->td[own][j1] || (unsigned)cj1 >= (unsigned)sh->td[own][j2]) return 0;
     // bit 39 marks the record as present (every field may be 0 in a tile)
     return (Rec)c | ((Rec)cj0 << 11) | ((Rec)cj1 << 22) | ((Rec)k << 34) | ((Rec)e << 36) | (1ull << 39);

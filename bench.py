@@ -7,8 +7,8 @@ beside it in the same run). Workload (synthetic, seeded): a 128^3 Lagrangian lat
 power spectrum k^-2 for |k| <= 16 and rms 4 Lagrangian cells (post shell-crossing), lognormal
 vertex density (sigma = 0.5), periodic unit box, 256^3 FP64 output grid.
 
-One step = one full projection: zeroing the grid, vertex preparation and the warp-cooperative
-projection kernel, all through the C ABI. Inputs (201 MB of simplices, 67 MB of vertex records,
+One step = one full projection: zeroing the grid, vertex records, the per-tetrahedron set-up, the
+block-cooperative projection kernel and the tiled large-tetrahedron kernel, all through the C ABI. Inputs (201 MB of simplices, 67 MB of vertex records,
 134 MB grid) exceed the 129 MB L2, so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -190,6 +190,24 @@ def _cpu_baseline(mesh, target_s=12.0, seed=5):
                       f"projected onto the full 256^3 grid in {dt:.1f} s"}
 
 
+def max_over_ranks(v: float, ws: int, device) -> float:
+    """The largest of the ranks' values of v (an all-reduce MAX on `device`); v itself on one rank."""
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws: int, units_per_rank: int, ms_max: float) -> float:
+    """Whole-job units per second: every rank processes units_per_rank in a step, and the step takes
+    the slowest rank's ms_max."""
+    return ws * units_per_rank / (ms_max / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -268,15 +286,6 @@ def run_ours(a):
 
             dist.barrier()
 
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # one instrumented pass for the corner counts (outside every timed region)
     _, st32 = proj.project(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, True,
                            precision=pkg.CDP_FP32_MIXED, out=out, stream=stream, stats=True)
@@ -307,13 +316,13 @@ def run_ours(a):
     ms32, kern32 = timed(pkg.CDP_FP32_MIXED, a.steps, a.warmup)
     clocks = clk.stop()
     proj.check(stream)
-    ms32 = max_over_ranks(ms32)
-    value = ws * ns / (ms32 / 1000.0)
+    ms32 = max_over_ranks(ms32, ws, dev)
+    value = job_throughput(ws, ns, ms32)
 
     # FP64 plain path on the same GPU, same workload (fewer steps: it is much slower)
     k64 = max(1, a.fp64_steps)
     ms64, kern64 = timed(pkg.CDP_FP64, k64, 1)
-    ms64 = max_over_ranks(ms64)
+    ms64 = max_over_ranks(ms64, ws, dev)
 
     # end to end through the C ABI from pinned host buffers: H2D inputs, project, D2H grid
     e2e = None
@@ -346,9 +355,9 @@ def run_ours(a):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        mse = max_over_ranks(e0.elapsed_time(e1) / a.steps)
+        mse = max_over_ranks(e0.elapsed_time(e1) / a.steps, ws, dev)
         hb = hp.numel() * 8 + hs.numel() * 4 + hr.numel() * 8
-        e2e = {"value": ws * ns / (mse / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(hb),
+        e2e = {"value": job_throughput(ws, ns, mse), "unit": UNIT, "h2d_bytes_per_step": int(hb),
                "d2h_bytes_per_step": int(ho.numel() * 8), "ms_per_step": mse}
 
     # the batched workload (every rank runs its own replica; rank 0 reports its own)
@@ -388,7 +397,7 @@ def run_ours(a):
                                "sigma 0.5, periodic, 256^3 FP64 grid" if a.scale is None else f"c3 scale {a.scale}",
                    "tets": ns, "grid": list(mesh.grid), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
-        "fp64_plain": {"value": ws * ns / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64,
+        "fp64_plain": {"value": job_throughput(ws, ns, ms64), "unit": UNIT, "ms_per_step": ms64,
                        "kernel_ms": kern64, "speedup_fp32_mixed_vs_fp64": ms64 / ms32},
         "kernel_ms": dict(zip(names, kern32)),
         "corners": {k: st32[k] for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell",

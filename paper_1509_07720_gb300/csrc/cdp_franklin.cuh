@@ -177,7 +177,7 @@ constexpr unsigned tet_edge_odd_mask() {
 // parity4(a, b, p, q) of edge e: +1 even, -1 odd
 CDP_HD int tet_edge_parity(int e) { return ((tet_edge_odd_mask() >> e) & 1u) ? -1 : 1; }
 
-CDP_HD int tet_edge_index(int i, int j) {
+CDP_HD constexpr int tet_edge_index(int i, int j) {
     int a = i < j ? i : j, b = i < j ? j : i;
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
@@ -304,11 +304,13 @@ CDP_COLD void tet_setup(const Tet& S, const int T[3], TetGeo<R>& G) {
 }
 
 // ------------------------------------------------------------------------------------------
-// predicates with a floating-point filter and the exact fallback
+// exact stages of the two predicates (Sect. 3.3, with SoS): the orient2d of a grid point against
+// a projected edge (side2) and the orient3d of a grid node against a facet (side3).  The kernels
+// evaluate a floating-point filter (bounds B2, B3 of the working set) and take these only when it
+// is inconclusive (out of line: rarely reached, and kept out of the hot loops' instruction
+// footprint).
 // ------------------------------------------------------------------------------------------
 
-// exact stages of the two predicates below (out of line: rarely reached, and kept out of the hot
-// loops' instruction footprint)
 template <typename R>
 CDP_COLD int tet_side2_exact(const TetGeo<R>& G, int i, int j, int u, int v, int pu, int pv) {
     return side2_exact(G.Lt[i][u], G.Lt[i][v], G.Lt[j][u], G.Lt[j][v], (i64)pu << CDP_Q, (i64)pv << CDP_Q);
@@ -321,85 +323,6 @@ CDP_COLD int tet_side3_exact(const TetGeo<R>& G, int f, int g0, int g1, int g2) 
     i128 nE[3];
     facet_normal_exact(G.Lt, f, nE);
     return side3_exact(nE, G.Lt[a], gp);
-}
-
-// perturbed orient2d of grid point (pu, pv) (integers, tile frame) against edge (i -> j) of the
-// projection on axes u < v
-template <typename R>
-CDP_HD int tet_side2(const TetGeo<R>& G, int i, int j, int u, int v, int pu, int pv, UnitCounts* cnt) {
-    R du = G.x[j][u] - G.x[i][u], dv = G.x[j][v] - G.x[i][v];
-    R val = du * (R(pv) - G.x[i][v]) - dv * (R(pu) - G.x[i][u]);
-    if (val > G.B2) return 1;
-    if (val < -G.B2) return -1;
-    if (cnt) cnt->exact++;
-    return tet_side2_exact(G, i, j, u, v, pu, pv);
-}
-
-// perturbed side of grid node (g0, g1, g2) (tile frame) w.r.t. facet f: > 0 inside
-template <typename R>
-CDP_HD int tet_side3(const TetGeo<R>& G, int f, int g0, int g1, int g2, UnitCounts* cnt) {
-    int a = f == 0 ? 1 : 0;  // a vertex of facet f
-    R val = G.n[f][0] * (R(g0) - G.x[a][0]) + G.n[f][1] * (R(g1) - G.x[a][1]) + G.n[f][2] * (R(g2) - G.x[a][2]);
-    if (val > G.B3) return 1;
-    if (val < -G.B3) return -1;
-    if (cnt) cnt->exact++;
-    return tet_side3_exact(G, f, g0, g1, g2);
-}
-
-// sign(X_j - d) for the crossing X of edge (a -> b) with grid plane x_k = c (perturbed)
-template <typename R>
-CDP_HD int tet_cross_side(const TetGeo<R>& G, int a, int b, int k, int c, int j, int d, int dirk,
-                          UnitCounts* cnt) {
-    int s = j < k ? tet_side2(G, a, b, j, k, d, c, cnt) : -tet_side2(G, a, b, k, j, c, d, cnt);
-    return dirk * s;
-}
-
-// cell index along j of the crossing of edge (a -> b) with plane x_k = c; `guess` from the
-// rounded crossing point, corrected by the exact predicate
-template <typename R>
-CDP_HD int tet_cross_cell(const TetGeo<R>& G, int a, int b, int k, int c, int j, int guess, int dirk,
-                          UnitCounts* cnt) {
-    int lo = G.cell[a][j] < G.cell[b][j] ? G.cell[a][j] : G.cell[b][j];
-    int hi = G.cell[a][j] < G.cell[b][j] ? G.cell[b][j] : G.cell[a][j];
-    int d = guess < lo ? lo : (guess > hi ? hi : guess);
-    // invariant wanted: side(d) > 0 (crossing above plane d) and side(d+1) < 0
-    for (int it = 0; it <= hi - lo + 1; ++it) {
-        if (d > lo && tet_cross_side(G, a, b, k, c, j, d, dirk, cnt) < 0) {
-            --d;
-            continue;
-        }
-        if (d < hi && tet_cross_side(G, a, b, k, c, j, d + 1, dirk, cnt) > 0) {
-            ++d;
-            continue;
-        }
-        break;
-    }
-    return d;
-}
-
-// cell index along l of the crossing of facet f with the grid line along l through (dj, dk)
-template <typename R>
-CDP_HD int tet_facet_line_cell(const TetGeo<R>& G, int f, int l, int dj, int dk, int guess, UnitCounts* cnt) {
-    int lo = G.lo[l], hi = G.hi[l];
-    int m = guess < lo ? lo : (guess > hi ? hi : guess);
-    int up = G.ns[f][l] > 0 ? 1 : -1;  // side3 grows along +l when the normal's l component is > 0
-    // node (coordinate t along l) in (x, y, z): l = 0 -> (t, dj, dk), l = 1 -> (dj, t, dk), l = 2 -> (dj, dk, t)
-    for (int it = 0; it <= hi - lo + 1; ++it) {
-        int s0 = l == 0 ? tet_side3(G, f, m, dj, dk, cnt)
-                        : (l == 1 ? tet_side3(G, f, dj, m, dk, cnt) : tet_side3(G, f, dj, dk, m, cnt));
-        if (m > lo && s0 == up) {  // node m already past the crossing
-            --m;
-            continue;
-        }
-        int s1 = l == 0 ? tet_side3(G, f, m + 1, dj, dk, cnt)
-                        : (l == 1 ? tet_side3(G, f, dj, m + 1, dk, cnt) : tet_side3(G, f, dj, dk, m + 1, cnt));
-        if (m < hi && s1 == -up) {
-            ++m;
-            continue;
-        }
-        break;
-    }
-    return m;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -469,98 +392,6 @@ CDP_COLD R tet_corner_B(const TetGeo<R>& G, int i, const R P[3]) {
     return R(-1.0 / 6.0) * s;
 }
 
-// C: edge e crossing the face x_k = c (cell on side sigma); ev = unit edge vector (a -> b)
-template <typename R>
-CDP_HD R tet_corner_C(const TetGeo<R>& G, int e, int k, int dirk, R sigma, const R ev[3], const R P[3], R rhoX) {
-    int a, b, p, q;
-    tet_edge(e, a, b, p, q);
-    R s = 0;
-    // the simplex edge, oriented into the cell, with its two facets (f_p contains q, f_q contains p)
-    R so = sigma * R(dirk);
-    const R T[3] = {so * ev[0], so * ev[1], so * ev[2]};
-    const R np_[3] = {G.n[p][0], G.n[p][1], G.n[p][2]};
-    const R nq_[3] = {G.n[q][0], G.n[q][1], G.n[q][2]};
-    R N[3];
-    cross3(np_, ev, N);
-    R pp = R(parity4(a, b, q, p));
-    for (int t = 0; t < 3; ++t) N[t] *= pp;
-    s += trip3(P, T, N, np_, rhoX, G.g);
-    cross3(nq_, ev, N);
-    R pq = R(parity4(a, b, p, q));
-    for (int t = 0; t < 3; ++t) N[t] *= pq;
-    s += trip3(P, T, N, nq_, rhoX, G.g);
-    // facet-face lines u_p (towards q's side) and u_q (towards p's side)
-    R lam = R(-parity4(a, b, p, q)) * R(dirk);
-    const R ek[3] = {R(k == 0), R(k == 1), R(k == 2)};
-    const R Bk[3] = {sigma * ek[0], sigma * ek[1], sigma * ek[2]};
-    for (int w = 0; w < 2; ++w) {
-        const R* n = w == 0 ? np_ : nq_;
-        R su = w == 0 ? lam : -lam;
-        R nk = pick3(n[0], n[1], n[2], k);
-        R r2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2] - nk * nk;
-        R ir = rsqrt_r<R>(r2);
-        R U[3];
-        cross3(n, ek, U);
-        for (int t = 0; t < 3; ++t) U[t] *= su * ir;
-        R N1[3], N2[3];
-        for (int t = 0; t < 3; ++t) {
-            N1[t] = sigma * (ek[t] - nk * n[t]) * ir;  // in the facet, towards the cell face side
-            N2[t] = (n[t] - nk * ek[t]) * ir;          // in the face, towards the facet side
-        }
-        s += trip3(P, U, N1, n, rhoX, G.g);
-        s += trip3(P, U, N2, Bk, rhoX, G.g);
-    }
-    return R(-1.0 / 6.0) * s;
-}
-
-// D: facet f crossing the grid line along l (other axes j < k); cell on sides (sj, sk)
-template <typename R>
-CDP_HD R tet_corner_D(const TetGeo<R>& G, int f, int l, int j, int k, R sj, R sk, const R P[3], R rhoX) {
-    const R n[3] = {G.n[f][0], G.n[f][1], G.n[f][2]};
-    R tau = G.ns[f][l] > 0 ? R(1) : R(-1);
-    R eps = (l == 1) ? R(-1) : R(1);  // Levi-Civita of (j, k, l) with j < k
-    const R ej[3] = {R(j == 0), R(j == 1), R(j == 2)};
-    const R ek[3] = {R(k == 0), R(k == 1), R(k == 2)};
-    const R El[3] = {tau * R(l == 0), tau * R(l == 1), tau * R(l == 2)};
-    const R Ej[3] = {sj * ej[0], sj * ej[1], sj * ej[2]};
-    const R Ek[3] = {sk * ek[0], sk * ek[1], sk * ek[2]};
-    R nj = pick3(n[0], n[1], n[2], j), nk = pick3(n[0], n[1], n[2], k), nl = pick3(n[0], n[1], n[2], l);
-    R s = 0;
-    s += trip3(P, El, Ek, Ej, rhoX, G.g);  // grid line with face j
-    s += trip3(P, El, Ej, Ek, rhoX, G.g);  // grid line with face k
-    // facet/face_j line, oriented towards the k side of the cell
-    {
-        R ir = rsqrt_r<R>(nk * nk + nl * nl);
-        R U[3];
-        cross3(n, ej, U);
-        R su = sk * eps * tau * ir;
-        for (int t = 0; t < 3; ++t) U[t] *= su;
-        R N1[3], N2[3];
-        for (int t = 0; t < 3; ++t) {
-            N1[t] = sj * (ej[t] - nj * n[t]) * ir;
-            N2[t] = (n[t] - nj * ej[t]) * ir;
-        }
-        s += trip3(P, U, N1, n, rhoX, G.g);
-        s += trip3(P, U, N2, Ej, rhoX, G.g);
-    }
-    // facet/face_k line, oriented towards the j side of the cell
-    {
-        R ir = rsqrt_r<R>(nj * nj + nl * nl);
-        R U[3];
-        cross3(n, ek, U);
-        R su = -sj * eps * tau * ir;
-        for (int t = 0; t < 3; ++t) U[t] *= su;
-        R N1[3], N2[3];
-        for (int t = 0; t < 3; ++t) {
-            N1[t] = sk * (ek[t] - nk * n[t]) * ir;
-            N2[t] = (n[t] - nk * ek[t]) * ir;
-        }
-        s += trip3(P, U, N1, n, rhoX, G.g);
-        s += trip3(P, U, N2, Ek, rhoX, G.g);
-    }
-    return R(-1.0 / 6.0) * s;
-}
-
 // A: grid node inside the simplex; cell on side s (sgn = product of s_a, s_a = +1 when the node is
 // the cell's upper corner along a)
 template <typename R>
@@ -586,110 +417,10 @@ CDP_HD R tet_corner_A(const TetFrame<R>& F, const R P[3], R rhoX, R sgn) {
     return sgn * P[0] * P[1] * P[2] * (rhoX - R(0.5) * dot3(F.g, P));
 }
 
-// ------------------------------------------------------------------------------------------
-// The work of one unit (the part of a tetrahedron's projection that falls in the tile [0, td),
-// tile frame) comes in three kinds of independent items, so that a warp can spread them over its
-// lanes:  a vertex (corner B), a (edge, axis, plane) crossing (corner C), a grid line along one
-// axis (corners D where it pierces two facets, and for lines along x the grid nodes between them,
-// corners A).  acc(vx, vy, vz, value) receives every (corner, cell) contribution.
-// ------------------------------------------------------------------------------------------
-
-template <typename R, class Acc>
-CDP_HD void tet_item_vertex(const TetGeo<R>& G, int i, const int td[3], Acc& acc, UnitCounts* cnt) {
-    const int v0 = G.cell[i][0], v1 = G.cell[i][1], v2 = G.cell[i][2];
-    if (v0 >= 0 && v0 < td[0] && v1 >= 0 && v1 < td[1] && v2 >= 0 && v2 < td[2]) {
-        R O[3], P[3];
-        piece_origin(G, v0, v1, v2, O);
-        for (int a = 0; a < 3; ++a) P[a] = (G.x[i][a] - O[a]) + G.xl[i][a];
-        acc(v0, v1, v2, tet_corner_B(G, i, P));
-        if (cnt) cnt->b++;
-    }
-}
-
-// number of grid planes x_k = c crossed by edge e inside the tile
-template <typename R>
-CDP_HD int tet_crossings(const TetGeo<R>& G, int e, int k, const int td[3], int& c0) {
-    int a, b, p, q;
-    tet_edge(e, a, b, p, q);
-    int ca = G.cell[a][k], cb = G.cell[b][k];
-    c0 = (ca < cb ? ca : cb) + 1;
-    int c1 = ca < cb ? cb : ca;
-    if (c0 < 0) c0 = 0;
-    int tk = pick3(td[0], td[1], td[2], k);
-    if (c1 > tk) c1 = tk;
-    return c1 >= c0 ? c1 - c0 + 1 : 0;
-}
-
-template <typename R, class Acc>
-CDP_HD void tet_item_crossing(const TetGeo<R>& G, int e, int k, int c, const int td[3], Acc& acc, UnitCounts* cnt) {
-    int a, b, p, q;
-    tet_edge(e, a, b, p, q);
-    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
-    int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-    R ev[3];
-    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
-    R evk = pick3(ev[0], ev[1], ev[2], k);
-    R t = ((R(c) - G.x[a][k]) - G.xl[a][k]) / evk;
-    // rounded crossing point (for the cell guesses and rho) and its exact-ish offsets from vertex a
-    R d[3] = {t * ev[0], t * ev[1], t * ev[2]};
-    R X1 = G.x[a][j1] + pick3(d[0], d[1], d[2], j1);
-    R X2 = G.x[a][j2] + pick3(d[0], d[1], d[2], j2);
-    int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X1), dirk, cnt);
-    if (cj1 < 0 || cj1 >= pick3(td[0], td[1], td[2], j1)) return;
-    int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X2), dirk, cnt);
-    if (cj2 < 0 || cj2 >= pick3(td[0], td[1], td[2], j2)) return;
-    R rhoX = G.rho[a] + t * (G.rho[b] - G.rho[a]);
-    R inv = rsqrt_r<R>(dot3(ev, ev));
-    R eu[3] = {ev[0] * inv, ev[1] * inv, ev[2] * inv};
-    int tk = pick3(td[0], td[1], td[2], k);
-    for (int side = 0; side < 2; ++side) {
-        int vk = side == 0 ? c - 1 : c;
-        if (vk < 0 || vk >= tk) continue;
-        int v0 = k == 0 ? vk : (j1 == 0 ? cj1 : cj2);
-        int v1 = k == 1 ? vk : (j1 == 1 ? cj1 : cj2);
-        int v2 = k == 2 ? vk : (j1 == 2 ? cj1 : cj2);
-        R O[3], P[3];
-        piece_origin(G, v0, v1, v2, O);
-        for (int w = 0; w < 3; ++w) P[w] = (G.x[a][w] - O[w]) + (G.xl[a][w] + d[w]);
-        // the crossing lies exactly on the plane
-        R Pk = R(c) - pick3(O[0], O[1], O[2], k);
-        P[0] = k == 0 ? Pk : P[0];
-        P[1] = k == 1 ? Pk : P[1];
-        P[2] = k == 2 ? Pk : P[2];
-        acc(v0, v1, v2, tet_corner_C(G, e, k, dirk, side == 0 ? R(-1) : R(1), eu, P, rhoX));
-        if (cnt) cnt->c++;
-    }
-}
-
-// grid lines along axis l inside the tile: (dj, dk) in [dj0, dj1] x [dk0, dk1]
-template <typename R>
-CDP_HD int tet_lines(const TetGeo<R>& G, int l, const int td[3], int& dj0, int& nj, int& dk0) {
-    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    dj0 = G.lo[j] + 1 > 0 ? G.lo[j] + 1 : 0;
-    int tj = pick3(td[0], td[1], td[2], j), tk = pick3(td[0], td[1], td[2], k);
-    int dj1 = G.hi[j] < tj ? G.hi[j] : tj;
-    dk0 = G.lo[k] + 1 > 0 ? G.lo[k] + 1 : 0;
-    int dk1 = G.hi[k] < tk ? G.hi[k] : tk;
-    nj = dj1 >= dj0 ? dj1 - dj0 + 1 : 0;
-    int nk = dk1 >= dk0 ? dk1 - dk0 + 1 : 0;
-    return nj * nk;
-}
-
-// signs of the 6 projected edges against the line point (dj, dk): bit e set when positive
-template <typename R>
-CDP_HD unsigned tet_line_signs(const TetGeo<R>& G, int j, int k, int dj, int dk, UnitCounts* cnt) {
-    unsigned m = 0;
-#pragma unroll 1
-    for (int e = 0; e < 6; ++e) {
-        int a, b, p, q;
-        tet_edge(e, a, b, p, q);
-        if (tet_side2(G, a, b, j, k, dj, dk, cnt) > 0) m |= 1u << e;
-    }
-    return m;
-}
-
-// facets pierced by the line: bit f set (projection of facet f contains the line point)
-CDP_HD unsigned tet_pierced(unsigned sgn) {
+// Facets pierced by a grid line, from the signs of the 6 projected edges against the line point
+// (bit e of sgn set when positive, tet_edge order): bit f set when the projection of facet f
+// contains the point, i.e. its three edges, oriented around it, have one sign.
+CDP_HD constexpr unsigned tet_pierced(unsigned sgn) {
     unsigned hits = 0;
     for (int f = 0; f < 4; ++f) {
         int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, cc = f == 3 ? 2 : 3;
@@ -701,68 +432,12 @@ CDP_HD unsigned tet_pierced(unsigned sgn) {
     return hits;
 }
 
-template <typename R, class Acc>
-CDP_HD void tet_item_line(const TetGeo<R>& G, int l, int dj, int dk, const int td[3], Acc& acc, UnitCounts* cnt) {
-    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    unsigned hits = tet_pierced(tet_line_signs(G, j, k, dj, dk, cnt));
-    if (!hits) return;
-    int mlo = 0, mhi = -1;
-    int tj = pick3(td[0], td[1], td[2], j), tk = pick3(td[0], td[1], td[2], k), tl = pick3(td[0], td[1], td[2], l);
-    for (int f = 0; f < 4; ++f) {
-        if (!((hits >> f) & 1u)) continue;
-        int va = f == 0 ? 1 : 0;
-        R nj = G.n[f][j], nk = G.n[f][k], nl = G.n[f][l];
-        // crossing coordinate along l, relative to vertex va: exact-ish offset
-        R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
-        R Xl = G.x[va][l] + off;
-        int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(Xl), cnt);
-        if (G.ns[f][l] > 0)
-            mlo = m;  // entry: nodes above m are inside w.r.t. this facet
-        else
-            mhi = m;  // exit: nodes up to m are inside
-        if (m < 0 || m >= tl) continue;
-        for (int oj = 0; oj < 2; ++oj)
-            for (int ok = 0; ok < 2; ++ok) {
-                int vj = dj - 1 + oj, vk = dk - 1 + ok;
-                if (vj < 0 || vj >= tj || vk < 0 || vk >= tk) continue;
-                int v0 = l == 0 ? m : vj;
-                int v1 = l == 1 ? m : (l == 0 ? vj : vk);
-                int v2 = l == 2 ? m : vk;
-                R O[3];
-                piece_origin(G, v0, v1, v2, O);
-                R Pl = (G.x[va][l] - pick3(O[0], O[1], O[2], l)) + (G.xl[va][l] + off);
-                R Pj = R(dj) - pick3(O[0], O[1], O[2], j), Pk = R(dk) - pick3(O[0], O[1], O[2], k);
-                R P[3] = {l == 0 ? Pl : Pj, l == 1 ? Pl : (l == 0 ? Pj : Pk), l == 2 ? Pl : Pk};
-                R rhoX = rho_from_P(G, P, O);
-                // cell above plane j (oj = 1) has inward normal +e_j there
-                acc(v0, v1, v2, tet_corner_D(G, f, l, j, k, oj ? R(1) : R(-1), ok ? R(1) : R(-1), P, rhoX));
-                if (cnt) cnt->d++;
-            }
-    }
-    // A: for lines along x, the grid nodes between the entry and the exit facet
-    if (l != 0 || ((hits & 1u) + ((hits >> 1) & 1u) + ((hits >> 2) & 1u) + ((hits >> 3) & 1u)) != 2u) return;
-    int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
-    for (int cx = n0; cx <= n1; ++cx) {
-        for (int o = 0; o < 8; ++o) {
-            int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
-            if (v0 < 0 || v0 >= td[0] || v1 < 0 || v1 >= td[1] || v2 < 0 || v2 >= td[2]) continue;
-            R O[3];
-            piece_origin(G, v0, v1, v2, O);
-            R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
-            // node is the cell's upper corner along a when the cell index is node-1
-            R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
-            acc(v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
-            if (cnt) cnt->a++;
-        }
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // Closed forms of the C and D corners for all the cells around the corner at once.  The six
 // (vertex, edge, facet) triples of such a corner are built from the unit normal(s) of the
 // simplex facet(s) and the cell faces; expanding them gives short polynomials in P (the corner
 // relative to its piece's origin) whose coefficients depend only on the corner, so they are
-// computed once for the 4 (D) or 2 (C) cells.  Same values as tet_corner_D / tet_corner_C.
+// computed once for the 4 (D) or 2 (C) cells.
 // ------------------------------------------------------------------------------------------
 
 // (a x b) component i
@@ -943,64 +618,6 @@ CDP_HD void tet_eval_C2(const TetGeo<R>& G, int e, int k, int c, int cj1, int cj
 // ------------------------------------------------------------------------------------------
 typedef unsigned long long Rec;
 
-template <typename R, class Push>
-CDP_HD void tet_locate_crossing(const TetGeo<R>& G, int e, int k, int c, const int td[3], Push& push,
-                                UnitCounts* cnt) {
-    int a, b, p, q;
-    tet_edge(e, a, b, p, q);
-    int dirk = G.cell[b][k] > G.cell[a][k] ? 1 : -1;
-    int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-    R ev[3];
-    for (int w = 0; w < 3; ++w) ev[w] = (G.x[b][w] - G.x[a][w]) + (G.xl[b][w] - G.xl[a][w]);
-    R evk = pick3(ev[0], ev[1], ev[2], k);
-    R t = div_guess(((R(c) - G.x[a][k]) - G.xl[a][k]), evk);
-    R X1 = G.x[a][j1] + t * pick3(ev[0], ev[1], ev[2], j1);
-    R X2 = G.x[a][j2] + t * pick3(ev[0], ev[1], ev[2], j2);
-    int cj1 = tet_cross_cell(G, a, b, k, c, j1, (int)floor_r(X1), dirk, cnt);
-    if (cj1 < 0 || cj1 >= pick3(td[0], td[1], td[2], j1)) return;
-    int cj2 = tet_cross_cell(G, a, b, k, c, j2, (int)floor_r(X2), dirk, cnt);
-    if (cj2 < 0 || cj2 >= pick3(td[0], td[1], td[2], j2)) return;
-    push((Rec)c | ((Rec)cj1 << 11) | ((Rec)cj2 << 22) | ((Rec)k << 34) | ((Rec)e << 36));
-}
-
-// locate the D corners of a grid line (records pushed) and add its A corners (grid nodes) directly
-template <typename R, class Push, class Acc>
-CDP_HD void tet_locate_line(const TetGeo<R>& G, int l, int dj, int dk, const int td[3], Push& push, Acc& acc,
-                            UnitCounts* cnt) {
-    int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
-    unsigned hits = tet_pierced(tet_line_signs(G, j, k, dj, dk, cnt));
-    if (!hits) return;
-    int mlo = 0, mhi = -1;
-    int tj = pick3(td[0], td[1], td[2], j), tk = pick3(td[0], td[1], td[2], k), tl = pick3(td[0], td[1], td[2], l);
-    for (int f = 0; f < 4; ++f) {
-        if (!((hits >> f) & 1u)) continue;
-        int va = f == 0 ? 1 : 0;
-        R nj = G.n[f][j], nk = G.n[f][k], nl = G.n[f][l];
-        R off = -(nj * ((R(dj) - G.x[va][j]) - G.xl[va][j]) + nk * ((R(dk) - G.x[va][k]) - G.xl[va][k])) / nl;
-        int m = tet_facet_line_cell(G, f, l, dj, dk, (int)floor_r(G.x[va][l] + off), cnt);
-        if (G.ns[f][l] > 0)
-            mlo = m;
-        else
-            mhi = m;
-        if (m < 0 || m >= tl) continue;
-        push((Rec)m | ((Rec)dj << 11) | ((Rec)dk << 22) | ((Rec)l << 35) | ((Rec)f << 37));
-    }
-    if (l != 0 || ((hits & 1u) + ((hits >> 1) & 1u) + ((hits >> 2) & 1u) + ((hits >> 3) & 1u)) != 2u) return;
-    int n0 = mlo + 1 > 0 ? mlo + 1 : 0, n1 = mhi < td[0] ? mhi : td[0];
-    for (int cx = n0; cx <= n1; ++cx) {
-        for (int o = 0; o < 8; ++o) {
-            int v0 = cx - 1 + (o & 1), v1 = dj - 1 + ((o >> 1) & 1), v2 = dk - 1 + ((o >> 2) & 1);
-            if (v0 < 0 || v0 >= td[0] || v1 < 0 || v1 >= td[1] || v2 < 0 || v2 >= td[2]) continue;
-            R O[3];
-            piece_origin(G, v0, v1, v2, O);
-            R P[3] = {R(cx) - O[0], R(dj) - O[1], R(dk) - O[2]};
-            R sg = ((o & 1) ? -1 : 1) * (((o >> 1) & 1) ? -1 : 1) * (((o >> 2) & 1) ? -1 : 1);
-            acc(v0, v1, v2, tet_corner_A(G, P, rho_from_P(G, P, O), sg));
-            if (cnt) cnt->a++;
-        }
-    }
-}
-
 CDP_HD void decode_C(Rec r, int& e, int& k, int& c, int& cj1, int& cj2) {
     c = (int)(r & 2047);
     cj1 = (int)((r >> 11) & 2047);
@@ -1015,22 +632,6 @@ CDP_HD void decode_D(Rec r, int& f, int& l, int& dj, int& dk, int& m) {
     dk = (int)((r >> 22) & 2047);
     l = (int)((r >> 35) & 3);
     f = (int)((r >> 37) & 3);
-}
-
-// all items of a unit, one after the other (host reference runs and single-thread use)
-template <typename R, class Acc>
-CDP_HD void tet_unit(const TetGeo<R>& G, const int td[3], Acc& acc, UnitCounts* cnt) {
-    for (int i = 0; i < 4; ++i) tet_item_vertex(G, i, td, acc, cnt);
-    for (int e = 0; e < 6; ++e)
-        for (int k = 0; k < 3; ++k) {
-            int c0, n = tet_crossings(G, e, k, td, c0);
-            for (int c = c0; c < c0 + n; ++c) tet_item_crossing(G, e, k, c, td, acc, cnt);
-        }
-    for (int l = 0; l < 3; ++l) {
-        int dj0, nj, dk0;
-        int n = tet_lines(G, l, td, dj0, nj, dk0);
-        for (int t = 0; t < n; ++t) tet_item_line(G, l, dj0 + t % nj, dk0 + t / nj, td, acc, cnt);
-    }
 }
 
 // ==========================================================================================

@@ -1,7 +1,8 @@
 // Kernels of the projection (Sect. 3; Algorithm 2 organised per simplex instead of per vertex).
 //
 //  k_prep_vertices   one thread per vertex: world coordinates -> 32-byte fixed-point records.
-//  k_project_warp    warp-cooperative projection of chunks of simplices (see below).
+//  k_project_warp    warp-cooperative projection of chunks of triangles (2D; see below).  Tetrahedra
+//                    are projected by the kernels of cdp_tetproj.cu.
 #include <cuda_runtime.h>
 
 #include "cdp_mesh.cuh"
@@ -47,10 +48,6 @@ constexpr int MAX_PROBES = 64;
 
 template <int DIM, typename R>
 struct GeoOf;
-template <typename R>
-struct GeoOf<3, R> {
-    typedef TetGeo<R> T;
-};
 template <typename R>
 struct GeoOf<2, R> {
     typedef TriGeo<R> T;
@@ -160,24 +157,7 @@ __device__ __forceinline__ int owner_of(int pre, int u) {
     return own > 31 ? 31 : own;
 }
 
-// per-simplex item counts of the three phases
-template <typename R>
-__device__ __forceinline__ void tet_counts(const TetGeo<R>& G, int n[3]) {
-    const int td[3] = {G.hi[0] + 1, G.hi[1] + 1, G.hi[2] + 1};
-    n[0] = 4;
-    n[1] = 0;
-    for (int e = 0; e < 6; ++e)
-        for (int k = 0; k < 3; ++k) {
-            int c0;
-            n[1] += tet_crossings(G, e, k, td, c0);
-        }
-    n[2] = 0;
-    for (int l = 0; l < 3; ++l) {
-        int dj0, nj, dk0;
-        n[2] += tet_lines(G, l, td, dj0, nj, dk0);
-    }
-}
-
+// per-triangle item counts of the three phases
 template <typename R>
 __device__ __forceinline__ void tri_counts(const TriGeo<R>& G, int n[3]) {
     const int td[2] = {G.hi[0] + 1, G.hi[1] + 1};
@@ -192,57 +172,6 @@ __device__ __forceinline__ void tri_counts(const TriGeo<R>& G, int n[3]) {
     n[2] = tri_rows(G, td, dy0);
 }
 
-// item t of phase `ph` of one simplex
-template <typename R, class Acc>
-__device__ __forceinline__ void tet_item(const TetGeo<R>& G, int ph, int t, Acc& acc, UnitCounts* cnt) {
-    const int td[3] = {G.hi[0] + 1, G.hi[1] + 1, G.hi[2] + 1};
-    if (ph == 0) {
-        tet_item_vertex(G, t, td, acc, cnt);
-    } else if (ph == 1) {
-        for (int e = 0; e < 6; ++e)
-            for (int k = 0; k < 3; ++k) {
-                int c0, n = tet_crossings(G, e, k, td, c0);
-                if (t < n) {
-                    tet_item_crossing(G, e, k, c0 + t, td, acc, cnt);
-                    return;
-                }
-                t -= n;
-            }
-    } else {
-        for (int l = 0; l < 3; ++l) {
-            int dj0, nj, dk0;
-            int n = tet_lines(G, l, td, dj0, nj, dk0);
-            if (t < n) {
-                tet_item_line(G, l, dj0 + t % nj, dk0 + t / nj, td, acc, cnt);
-                return;
-            }
-            t -= n;
-        }
-    }
-}
-
-template <typename R, class Acc>
-__device__ __forceinline__ void tri_item(const TriGeo<R>& G, int ph, int t, Acc& acc, UnitCounts* cnt) {
-    const int td[2] = {G.hi[0] + 1, G.hi[1] + 1};
-    if (ph == 0) {
-        tri_item_vertex(G, t, td, acc, cnt);
-    } else if (ph == 1) {
-        for (int o = 0; o < 3; ++o)
-            for (int k = 0; k < 2; ++k) {
-                int c0, n = tri_crossings(G, o, k, td, c0);
-                if (t < n) {
-                    tri_item_crossing(G, o, k, c0 + t, td, acc, cnt);
-                    return;
-                }
-                t -= n;
-            }
-    } else {
-        int dy0;
-        tri_rows(G, td, dy0);
-        tri_item_row(G, dy0 + t, td, acc, cnt);
-    }
-}
-
 template <int DIM, typename R>
 __device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int own, const GridDesc& g, double* out,
                                                     bool closure) {
@@ -252,7 +181,7 @@ __device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int 
     acc.owner = own;
     acc.ex = G.hi[0] + 1;
     acc.ey = G.hi[1] + 1;
-    long long cells = (long long)acc.ex * acc.ey * (DIM == 3 ? (G.hi[DIM - 1] + 1) : 1);
+    long long cells = (long long)acc.ex * acc.ey;
     acc.direct_only = cells >= (1ll << KEY_BITS);
     acc.g = &g;
     acc.out = out;
@@ -260,36 +189,7 @@ __device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int 
     return acc;
 }
 
-// phase items with the queue: 0 vertex (evaluated), 1 crossing (queued), 2 line (D queued, A evaluated)
-template <typename R, class Acc, class Push>
-__device__ __forceinline__ void tet_phase_item(const TetGeo<R>& G, int ph, int t, Acc& acc, Push& push,
-                                               UnitCounts* cnt) {
-    const int td[3] = {G.hi[0] + 1, G.hi[1] + 1, G.hi[2] + 1};
-    if (ph == 0) {
-        tet_item_vertex(G, t, td, acc, cnt);
-    } else if (ph == 1) {
-        for (int e = 0; e < 6; ++e)
-            for (int k = 0; k < 3; ++k) {
-                int c0, n = tet_crossings(G, e, k, td, c0);
-                if (t < n) {
-                    tet_locate_crossing(G, e, k, c0 + t, td, push, cnt);
-                    return;
-                }
-                t -= n;
-            }
-    } else {
-        for (int l = 0; l < 3; ++l) {
-            int dj0, nj, dk0;
-            int n = tet_lines(G, l, td, dj0, nj, dk0);
-            if (t < n) {
-                tet_locate_line(G, l, dj0 + t % nj, dk0 + t / nj, td, push, acc, cnt);
-                return;
-            }
-            t -= n;
-        }
-    }
-}
-
+// phase items with the queue: 0 vertex (evaluated), 1 crossing (queued), 2 row (evaluated)
 template <typename R, class Acc, class Push>
 __device__ __forceinline__ void tri_phase_item(const TriGeo<R>& G, int ph, int t, Acc& acc, Push& push,
                                                UnitCounts* cnt) {
@@ -320,24 +220,11 @@ __device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned lon
     const int own = (int)((r >> 40) & 31);
     const typename GeoOf<DIM, R>::T& G = sh->geo[own];
     WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, closure);
-    if constexpr (DIM == 3) {
-        if (ph == 1) {
-            int e, k, c, cj1, cj2;
-            decode_C(r, e, k, c, cj1, cj2);
-            tet_eval_C2(G, e, k, c, cj1, cj2, acc);
-            if (cnt) cnt->c += 2;
-        } else {
-            int f, l, dj, dk, m;
-            decode_D(r, f, l, dj, dk, m);
-            tet_eval_D4(G, f, l, dj, dk, m, acc);
-            if (cnt) cnt->d += 4;
-        }
-    } else {
-        int v0, v1, v2;
-        R val = tri_eval_crossing(G, r, v0, v1, v2);
-        if (cnt) cnt->c++;
-        acc(v0, v1, v2, val);
-    }
+    (void)ph;
+    int v0, v1, v2;
+    R val = tri_eval_crossing(G, r, v0, v1, v2);
+    if (cnt) cnt->c++;
+    acc(v0, v1, v2, val);
 }
 
 template <int DIM, typename R>
@@ -345,8 +232,8 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                                                             const int* __restrict__ simp,
                                                             const VertexRec* __restrict__ V,
                                                             double* __restrict__ out, Counters* __restrict__ ctr,
-                                                            UnitCounts* __restrict__ stats,
-                                                            const int* __restrict__ list, long long list_cap) {
+                                                            UnitCounts* __restrict__ stats) {
+    static_assert(DIM == 2, "tetrahedra are projected by the kernels of cdp_tetproj.cu");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
@@ -360,13 +247,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
     UnitCounts cnt = {0, 0, 0, 0, 0};
     UnitCounts* pc = stats ? &cnt : nullptr;
     unsigned long long n0 = 0, nact = 0, nzero = 0;
-    if (list) {
-        // large-simplex pass: the simplices listed by the main kernel
-        const long long cnt_listed = (long long)*(volatile unsigned*)&ctr->big_count;
-        ns = cnt_listed < list_cap ? cnt_listed : list_cap;
-    }
-    // the large-simplex pass gives each listed simplex a warp of its own
-    const int cs = list ? 1 : CDP_CHUNK;
+    const int cs = CDP_CHUNK;
     const long long nchunks = (ns + cs - 1) / cs;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
@@ -377,25 +258,8 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
         int n[3] = {0, 0, 0};
         if (lane < cs && s < ns) {
             const VertexRec* v[4];
-            if (!fetch_vertices(simp, list ? (long long)list[s] : s, DIM + 1, nv, V, v)) {
+            if (!fetch_vertices(simp, s, DIM + 1, nv, V, v)) {
                 atomicOr(&ctr->flags, CDP_FLAG_INDEX);
-            } else if constexpr (DIM == 3) {
-                Tet S;
-                unsigned rc = canon_tet(g, v, S);
-                if (rc == 1) {
-                    ++nzero;
-                } else if (rc) {
-                    atomicOr(&ctr->flags, rc);
-                } else if (S.lo[0] == S.hi[0] && S.lo[1] == S.hi[1] && S.lo[2] == S.hi[2]) {
-                    long long idx = flat_cell(g, S.anchor[0] + S.lo[0], S.anchor[1] + S.lo[1], S.anchor[2] + S.lo[2]);
-                    if (idx >= 0) atomicAdd(out + idx, tet_mass_cells(S));
-                    ++n0;
-                } else {
-                    TetGeo<R>& G = sh->geo[lane];
-                    tet_setup(S, S.lo, G);
-                    tet_counts(G, n);
-                    active = true;
-                }
             } else {
                 Tri S;
                 unsigned rc = canon_tri(g, v, S);
@@ -445,10 +309,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                     WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, fp32);
                     QueuePush push{sh->queue, &sh->qtail, (unsigned long long)own << 40};
                     const int t = u - before;
-                    if constexpr (DIM == 3)
-                        tet_phase_item(G, ph, t, acc, push, pc);
-                    else
-                        tri_phase_item(G, ph, t, acc, push, pc);
+                    tri_phase_item(G, ph, t, acc, push, pc);
                 }
                 __syncwarp();
                 // evaluate every full batch of queued records
@@ -516,7 +377,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
     if (stats) {
         add_counts(stats, cnt);
         if (n0) atomicAdd(&ctr->n_class0, n0);
-        if (nact && !list) atomicAdd(&ctr->n_small, nact);  // listed ones are counted as large
+        if (nact) atomicAdd(&ctr->n_small, nact);
         if (nzero) atomicAdd(&ctr->n_zero, nzero);
     }
 }
@@ -566,7 +427,7 @@ static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t 
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(
-        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, nullptr, 0);
+        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats);
     if (mid) cudaEventRecord(mid, st);
     return cudaGetLastError();
 }

@@ -126,23 +126,11 @@ struct BoxAcc {
 // items
 // ------------------------------------------------------------------------------------------
 
-// Facets pierced by a grid line, as a function of the signs of the 6 projected edges (the rule of
-// tet_pierced), packed 4 bits per sign mask into four 64-bit words at compile time.
+// The facets pierced by a grid line (tet_pierced) for every sign mask of the 6 projected edges,
+// packed 4 bits per mask into four 64-bit words at compile time.
 constexpr unsigned long long pierced_word(int w) {
     unsigned long long v = 0;
-    for (int i = 0; i < 16; ++i) {
-        const unsigned sgn = (unsigned)(w * 16 + i);
-        unsigned hits = 0;
-        for (int f = 0; f < 4; ++f) {
-            const int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, c = f == 3 ? 2 : 3;
-            const int eab = a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
-            const int ebc = b == 0 ? c - 1 : (b == 1 ? c + 1 : 5);
-            const int eac = a == 0 ? c - 1 : (a == 1 ? c + 1 : 5);
-            const unsigned sab = (sgn >> eab) & 1u, sbc = (sgn >> ebc) & 1u, sac = (sgn >> eac) & 1u;
-            if (sab == sbc && sbc != sac) hits |= 1u << f;
-        }
-        v |= (unsigned long long)hits << (4 * i);
-    }
+    for (int i = 0; i < 16; ++i) v |= (unsigned long long)tet_pierced((unsigned)(w * 16 + i)) << (4 * i);
     return v;
 }
 
@@ -155,7 +143,8 @@ __device__ __forceinline__ unsigned pierced_lut(unsigned sgn) {
 }
 
 // Exact stage of the crossing-side predicate: sign(X_j - d) (before the dirk orientation) for the
-// crossing X of edge a -> b with the grid plane x_k = c, with the argument order of tet_cross_side.
+// crossing X of edge a -> b with the grid plane x_k = c: the orient2d, in the axes (j, k), of the
+// grid point (d, c) against the projected edge (tet_side2_exact's argument order: axes ascending).
 template <typename R>
 CDP_COLD int cross_side_exact(const TetGeo<R>& G, int a, int b, int j, int k, int c, int d) {
     return j < k ? tet_side2_exact(G, a, b, j, k, d, c) : -tet_side2_exact(G, a, b, k, j, c, d);
@@ -179,7 +168,8 @@ CDP_COLD unsigned line_signs_exact(const TetGeo<R>& G, int j, int k, int dj, int
 
 // Cell along axis j of the crossing of edge a -> b (coordinates in registers: xa_j, xa_k, xb_j, xb_k)
 // with the grid plane x_k = c: the d in [lo, hi] with the crossing above plane d and below plane
-// d + 1, found from `guess` by the exact-sign search of tet_cross_cell (one predicate per step).
+// d + 1, found from `guess` by an exact-sign search (one predicate per step: the filtered orient2d of
+// the grid point (plane, c) against the projected edge, else its exact stage).
 template <typename R>
 __device__ __forceinline__ int cross_cell_regs(const TetGeo<R>& G, int a, int b, int j, int k, int c, R xaj, R xak,
                                                R xbj, R xbk, int lo, int hi, int guess, int dirk, R B2,
@@ -203,7 +193,7 @@ __device__ __forceinline__ int cross_cell_regs(const TetGeo<R>& G, int a, int b,
         }
         if (upper && d == hi) break;
         const int dd = upper ? d + 1 : d;
-        // orient2d of (dd, c) against the projected edge, the expression of tet_side2
+        // orient2d of the grid point (dd, c) against the projected edge, filtered by B2
         const R val = A - dv * (R(dd) - xaj);
         int sd;
         if (val > B2) {
@@ -232,7 +222,8 @@ __device__ __forceinline__ int cross_cell_regs(const TetGeo<R>& G, int a, int b,
 
 // Cell along l of the crossing of facet f (unit normal nf, reference vertex xf) with the grid line
 // along l through (dj, dk): the m in [lo, hi] with node m on the near side and node m + 1 on the
-// far side, found from `guess` by the search of tet_facet_line_cell (one predicate per step).
+// far side, found from `guess` by an exact-sign search (one predicate per step: the filtered
+// orient3d of the node against the facet, else its exact stage).
 template <typename R>
 __device__ __forceinline__ int facet_line_cell_regs(const TetGeo<R>& G, int f, int l, int dj, int dk, int guess,
                                                     int lo, int hi, int up, const R nf[3], const R xf[3], R B3,
@@ -257,7 +248,7 @@ __device__ __forceinline__ int facet_line_cell_regs(const TetGeo<R>& G, int f, i
         }
         if (upper && m == hi) break;
         const int t = upper ? m + 1 : m;
-        // node (t along l, dj, dk) in axis order, the expression of tet_side3
+        // node (t along l, dj, dk) in axis order against the facet's plane, filtered by B3
         const int g0 = l == 0 ? t : dj, g1 = l == 1 ? t : (l == 0 ? dj : dk), g2 = l == 2 ? t : dk;
         const R val = nf[0] * (R(g0) - xf[0]) + nf[1] * (R(g1) - xf[1]) + nf[2] * (R(g2) - xf[2]);
         int st;
@@ -432,7 +423,7 @@ __device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>*
     const int j = l == 0 ? 1 : 0, k = l == 2 ? 1 : 2;
     const int tq = t / nj;
     const int dj = pick3(r0[0], r0[1], r0[2], j) + t - tq * nj, dk = pick3(r0[0], r0[1], r0[2], k) + tq;
-    // signs of the 6 projected edges against (dj, dk) (the filtered orient2d of tet_side2, from the
+    // signs of the 6 projected edges against (dj, dk) (the filtered orient2d of the edge, from the
     // projected vertices read once; inconclusive ones settled exactly)
     unsigned sgn = 0, amb = 0;
     {

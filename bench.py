@@ -38,10 +38,10 @@ UNIT = "tets/s"
 # product (3) = 42 flops each; the type-A closed form is 12 flops.
 FLOPS_PER_INCIDENCE = {"a": 12, "b": 252, "c": 252, "d": 252}
 # DRAM bytes (read + write) of one k_project_tet<float> launch per tetrahedron, from the ncu capture
-# summarised in profiles/k_project_tet_c3s64_full.md (1,572,864 tetrahedra: 712.7 MB read, 86.8 MB
+# summarised in profiles/k_project_tet_c3s64_full.md (1,572,864 tetrahedra: 713.1 MB read, 86.9 MB
 # written); the traffic is the geometry records plus the grid atomics, so it scales with the
 # tetrahedron count.  None while the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_TET = (712.741120e6 + 86.792704e6) / 1572864
+TRAFFIC_BYTES_PER_TET = (713.054976e6 + 86.854400e6) / 1572864
 # ALU peaks derived from unit counts and the maximum SM clock (no measured FP32 figure exists):
 # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 1.25 TFLOP/s nominal.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12

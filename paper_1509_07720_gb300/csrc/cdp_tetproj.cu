@@ -12,9 +12,9 @@
 // phases of independent items -- the vertices (corners B), the (edge, axis, plane) crossings
 // (corners C) and the grid lines (corners D, and along x the grid nodes between the two pierced
 // facets, corners A) -- whose items of all tetrahedra of the round are numbered consecutively and
-// dealt to the block's warps 32 at a time.  All warps of a block run the same phase between two
-// barriers: the instruction footprint of the block is that phase's code, and the items are
-// balanced over the warps.  Locating a corner costs a few exact-sign predicates; evaluating it
+// dealt to the block's warps 32 at a time (the three item counts of every unit scanned once per
+// round; a warp goes from one phase to the next without waiting for the others), so that the items
+// are balanced over the warps.  Locating a corner costs a few exact-sign predicates; evaluating it
 // (all the cells around it at once) costs most of the arithmetic, so each warp queues the corners
 // it locates as compact records and evaluates them in full batches of 32 identical evaluations.
 // Every (corner, cell) contribution is one shared-memory add into the box of its tetrahedron.  At
@@ -98,9 +98,9 @@ struct TetShared {
                                      // through (y, z) = (j, k) of the tile, entry j + (TB_TE + 1) k:
                                      // the node range [x, y] clipped to the tile (empty: x > y)
     BigState bs;                     // its tiling state
-    int pre[TB_NT];                  // inclusive prefix of the current phase's item counts; in the
-                                     // flush, of the round's box sizes
     int wsum[TB_WARPS];              // block-scan scratch
+    int wsum3[3];                    // the three phases' item counts of units 0..31
+    int pre3[3][TB_NT];              // inclusive prefixes of the three phases' item counts
     float red[3][TB_WARPS];          // block-reduction scratch of the mass closure
 };
 
@@ -700,13 +700,43 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
     unsigned long long* const aq = sh->aq[warp];
     unsigned long long* const pq = sh->pq[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
+    // the item counts of the three phases of the round's units (threads 0..63), scanned at once
+    {
+        int m0 = in ? 4 : 0, m1 = in ? n_cross : 0, m2 = in ? n_lines : 0;
+        if (warp < 2) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t0 = __shfl_up_sync(FULL, m0, o), t1 = __shfl_up_sync(FULL, m1, o),
+                          t2 = __shfl_up_sync(FULL, m2, o);
+                if (lane >= o) {
+                    m0 += t0;
+                    m1 += t1;
+                    m2 += t2;
+                }
+            }
+            if (warp == 0 && lane == 31) {
+                sh->wsum3[0] = m0;
+                sh->wsum3[1] = m1;
+                sh->wsum3[2] = m2;
+            }
+        }
+        __syncthreads();
+        if (warp == 1) {
+            m0 += sh->wsum3[0];
+            m1 += sh->wsum3[1];
+            m2 += sh->wsum3[2];
+        }
+        if (warp < 2) {
+            sh->pre3[0][tid] = m0;
+            sh->pre3[1][tid] = m1;
+            sh->pre3[2][tid] = m2;
+        }
+        __syncthreads();
+    }
 #pragma unroll 1
     for (int ph = 0; ph < 3; ++ph) {
-        const int mine = in ? (ph == 0 ? 4 : (ph == 1 ? n_cross : n_lines)) : 0;
-        const int pre = block_scan(mine, sh->wsum);
-        if (tid < TB_NT) sh->pre[tid] = pre;
-        __syncthreads();
-        const int tot = sh->pre[TB_NT - 1];
+        const int* const pre_ph = sh->pre3[ph];
+        const int tot = pre_ph[TB_NT - 1];
         // item rounds of 32 dealt to the warps in turn; each warp queues and evaluates its own
         // located corners
         const int nrounds = (tot + 31) >> 5;
@@ -719,8 +749,8 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
             unsigned long long pline = 0;
             int own = 0;
             if (u < tot) {
-                own = upper_index(sh->pre, u);
-                const int t = u - (own > 0 ? sh->pre[own - 1] : 0);
+                own = upper_index(pre_ph, u);
+                const int t = u - (own > 0 ? pre_ph[own - 1] : 0);
                 if (ph == 0) {
                     item_vertex(sh, own, t);
                     if (STATS) cnt.b++;
@@ -787,7 +817,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                 break;
             }
         }
-        // (the next block_scan's barrier orders this phase before the next one)
+        // (no barrier: a warp goes on to the next phase at once)
     }
     __syncthreads();  // every warp has finished the line phase: the boxes are complete
 }

@@ -217,9 +217,21 @@ CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 /* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 4:
  * [0] vertex records, [1] per-simplex set-up (3D: the first batch's; the single-cell closed form
  * is applied there), [2] main projection kernel (3D: with the set-up of any later batch),
- * [3] the large-tetrahedron kernel (3D: tetrahedra with a bounding box above 1280 cells, in tiles).  *calls receives the number of timed cdp_project calls.
- * Returns the number of slots written. */
+ * [3] the large-tetrahedron kernel (3D: tetrahedra with a bounding box above 1280 cells, in
+ * tiles).  *calls receives the number of timed cdp_project calls.  Returns the number of slots
+ * written. */
 CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
+
+/* Launch-shape tuning (no counterpart in the paper: the choice of a GPU launch shape).  Times the
+ * projection of `prob` (into its own cell_mass, which is overwritten) with the main kernel's
+ * persistent grid at 1, 2, 4 and 8 times the device's resident blocks, and keeps the fastest for
+ * the later projections of ctx with the same dimension and precision (default 4).  With a
+ * non-null cache_path the choice is first looked up in that text file (lines
+ * "<device> dim<D> <precision> <multiplier>"; the last entry of a key wins) and, when tuned, appended
+ * to it.  Synchronises with the device.  *chosen (optional) receives the multiplier.  Returns
+ * CDP_OK, CDP_ERR_ARG, an error of the projection, or CDP_ERR_CUDA. */
+CDP_API int cdp_autotune(cdp_ctx* ctx, const cdp_problem* prob, int precision, const char* cache_path,
+                         int* chosen);
 
 /* Human-readable name of a return code (static string). */
 CDP_API const char* cdp_strerror(int code);

@@ -19,7 +19,7 @@ __all__ = [
     "cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror", "cdp_timing_enable",
     "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density", "cdp_poisson", "cdp_force", "cdp_drift",
     "cdp_kick", "cdp_step_batched", "cdp_step_problem", "Projector", "EXPORTED_SYMBOLS",
-    "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS", "CDP_NOALLOC_MAX_SIMPLICES",
+    "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS", "CDP_NOALLOC_MAX_SIMPLICES", "cdp_autotune",
 ]
 
 CDP_FP64 = 0
@@ -33,7 +33,7 @@ _lib = None
 EXPORTED_SYMBOLS = ("cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror",
                     "cdp_timing_enable", "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density",
                     "cdp_poisson", "cdp_force", "cdp_drift", "cdp_kick", "cdp_step_batched",
-                    "cdp_project_noalloc")
+                    "cdp_project_noalloc", "cdp_autotune")
 
 
 class CdpError(RuntimeError):
@@ -107,6 +107,9 @@ def load_library(path: str | None = None):
     lib.cdp_timing_enable.restype = ctypes.c_int
     lib.cdp_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.cdp_timing_read.restype = ctypes.c_int
+    lib.cdp_autotune.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_char_p,
+                                 ctypes.POINTER(ctypes.c_int)]
+    lib.cdp_autotune.restype = ctypes.c_int
     dp = ctypes.c_void_p
     arr3 = ctypes.c_void_p * 3
     lib.cdp_project_batched.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_int, vp]
@@ -179,6 +182,14 @@ def cdp_timing_read(ctx):
     if rc < 0:
         raise CdpError(rc, "cdp_timing_read")
     return list(buf), int(calls.value)
+
+
+def cdp_autotune(ctx, prob, precision: int, cache_path=None) -> tuple:
+    """(return code, chosen grid multiplier) of the C call of the same name."""
+    chosen = ctypes.c_int(0)
+    path = None if cache_path is None else os.fsencode(cache_path)
+    rc = load_library().cdp_autotune(ctx, ctypes.byref(prob), int(precision), path, ctypes.byref(chosen))
+    return rc, int(chosen.value)
 
 
 def _i3(v):
@@ -334,6 +345,22 @@ class Projector:
 
     def check(self, stream=None):
         _raise(cdp_check(self._ctx, _stream_handle(stream)), "cdp_check")
+
+    def autotune(self, pos, simplices, rho, grid, box_lo=None, box_len=None, periodic=True,
+                 precision=CDP_FP32_MIXED, out=None, cache_path=None):
+        """Tune the main kernel's grid for this context on the given problem (its projection is written
+        into `out`); returns the chosen multiplier of the resident blocks."""
+        import torch
+
+        dim = len(grid)
+        box_lo = box_lo if box_lo is not None else (0.0,) * dim
+        box_len = box_len if box_len is not None else (1.0,) * dim
+        if out is None:
+            out = torch.empty(tuple(grid), dtype=torch.float64, device=f"cuda:{self.device}")
+        prob = self.make_problem(pos, simplices, rho, grid, box_lo, box_len, periodic, out)
+        rc, chosen = cdp_autotune(self._ctx, prob, precision, cache_path)
+        _raise(rc, "cdp_autotune")
+        return chosen
 
     def timing(self, enable=None):
         """Enable/disable per-kernel timing, or (enable=None) read the totals."""

@@ -2,6 +2,7 @@
 // the launch sequence of the projection.
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <new>
@@ -189,8 +190,9 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     L.stats = want_stats ? c->stats : nullptr;
     L.num_sms = c->num_sms;
     int fp32 = precision == CDP_FP32_MIXED;
-    // a persistent grid: every resident block slot of the device, four times over
-    L.small_blocks_per_sm = 4 * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
+    // a persistent grid: every resident block slot of the device, grid_mult times over
+    L.small_blocks_per_sm =
+        c->grid_mult[p->dim == 3][fp32] * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
     L.resident_per_sm = p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32];
     L.big_list = c->queue;
     L.big_cap = (long long)c->queue_cap;
@@ -339,6 +341,8 @@ int cdp_create(cdp_ctx** out, int device) {
     c->blocks_small[1] = cdp::resident_blocks(3, 1);
     c->blocks_big[0] = cdp::resident_blocks(2, 0);
     c->blocks_big[1] = cdp::resident_blocks(2, 1);
+    for (int d3 = 0; d3 < 2; ++d3)
+        for (int f = 0; f < 2; ++f) c->grid_mult[d3][f] = 4;
     if (cudaMalloc(&c->ctr, sizeof(cdp::Counters)) != cudaSuccess ||
         cudaMalloc(&c->stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess ||
         cudaMallocHost(&c->h_ctr, sizeof(cdp::Counters)) != cudaSuccess ||
@@ -417,6 +421,93 @@ int cdp_project(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate,
     return read_stats(c, st, stats);
 }
 
+int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* cache_path, int* chosen) {
+    if (!c) return CDP_ERR_ARG;
+    int rc = check_problem(p);
+    if (rc) return rc;
+    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    DeviceGuard guard(c->device);
+    const int d3 = p->dim == 3 ? 1 : 0, fp32 = precision == CDP_FP32_MIXED ? 1 : 0;
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+    char key[96];
+    snprintf(key, sizeof(key), "sm%d%d-%dsm dim%d %s", major, minor, c->num_sms, p->dim, fp32 ? "fp32mixed" : "fp64");
+    static const int kMults[] = {1, 2, 4, 8};
+    // the cache: lines "<key> <multiplier>", the last entry of a key wins
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "r");
+        if (f) {
+            char line[160];
+            int found = 0;
+            while (fgets(line, sizeof(line), f)) {
+                const size_t n = strlen(key);
+                int m = 0;
+                if (strncmp(line, key, n) == 0 && line[n] == ' ' && sscanf(line + n, "%d", &m) == 1 &&
+                    (m == 1 || m == 2 || m == 4 || m == 8))
+                    found = m;
+            }
+            fclose(f);
+            if (found) {
+                c->grid_mult[d3][fp32] = found;
+                if (chosen) *chosen = found;
+                return CDP_OK;
+            }
+        }
+    }
+    // time the projection of this problem (into its own cell_mass) with every multiplier: one
+    // warm-up call and three timed calls each, on a stream of its own, after the work already
+    // queued on the device (the problem's inputs may still be in flight on another stream)
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_CUDA;
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        if (st) cudaStreamDestroy(st);
+        return CDP_ERR_CUDA;
+    }
+    const int timing = c->timing;
+    c->timing = 0;  // the tuning calls stay out of the per-kernel totals
+    const int before = c->grid_mult[d3][fp32];
+    int best = before;
+    float best_ms = 0.f;
+    for (int i = 0; i < 4 && rc == CDP_OK; ++i) {
+        c->grid_mult[d3][fp32] = kMults[i];
+        rc = cdp::project_enqueue(c, p, precision, 0, st, false);
+        if (rc == CDP_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = CDP_ERR_CUDA;
+        for (int r = 0; r < 3 && rc == CDP_OK; ++r) rc = cdp::project_enqueue(c, p, precision, 0, st, false);
+        float ms = 0.f;
+        if (rc == CDP_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = CDP_ERR_CUDA;
+        if (rc == CDP_OK && (i == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = kMults[i];
+        }
+    }
+    c->timing = timing;
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaGetLastError();
+    c->grid_mult[d3][fp32] = rc == CDP_OK ? best : before;
+    if (rc) return rc;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %d\n", key, best);
+            fclose(f);
+        }
+    }
+    if (chosen) *chosen = best;
+    return CDP_OK;
+}
 int cdp_project_batched(cdp_ctx* c, const cdp_problem* probs, int n, int precision, void* stream) {
     if (!c || n < 0 || (n > 0 && !probs)) return CDP_ERR_ARG;
     if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;

@@ -192,7 +192,7 @@ def test_aligned_kuhn_lattice(lag, grid):
 
 
 # ------------------------------------------------------------------------------------------
-# P7 shift equivariance, P8 linearity and vertex-order invariance
+# P7 shift, permutation and reflection equivariance, P8 linearity and vertex-order invariance
 # ------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -218,6 +218,22 @@ def test_axis_permutation():
     pm = mg.Mesh(mesh.pos[list(perm)].copy(), mesh.simplices, mesh.rho, mesh.grid, mesh.box_lo, mesh.box_len, True)
     out = oracle.project(pm)
     assert np.max(np.abs(out - np.transpose(base, perm))) <= 1e-14 * base.max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_axis_reflection(dim):
+    """Reflecting the periodic box along an axis (x -> 1 - x) reflects the cells (i -> N - 1 - i);
+    every simplex changes orientation, and its mass stays positive."""
+    rng = np.random.default_rng(24)
+    mesh = mg.random_simplices(dim, 200, 8, 2.0, rng)
+    base = oracle.project(mesh)
+    for ax in range(dim):
+        pos = mesh.pos.copy()
+        pos[ax] = np.mod(1.0 - pos[ax], 1.0)
+        rm = mg.Mesh(pos, mesh.simplices, mesh.rho, mesh.grid, mesh.box_lo, mesh.box_len, True)
+        out = oracle.project(rm)
+        assert np.max(np.abs(out - np.flip(base, axis=ax))) <= 1e-14 * base.max()
+        assert abs(out.sum() - base.sum()) <= 1e-13 * base.sum()
 
 
 @pytest.mark.parametrize("dim", [2, 3])

@@ -185,9 +185,17 @@ def _cpu_baseline(mesh, target_s=12.0, seed=5):
     t0 = time.perf_counter()
     oracle.project(mesh.subset(idx))
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, on a sample of a few seconds (comparable to a per-thread figure)
+    n1 = int(min(ns, max(1000, n2 / max(oracle.max_threads(), 1) / 3)))
+    idx1 = np.sort(rng.choice(ns, n1, replace=False))
+    t1 = time.perf_counter()
+    oracle.project(mesh.subset(idx1), nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": n2 / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{n2} of {ns} tetrahedra of the workload, chosen uniformly at random (seed {seed}), "
-                      f"projected onto the full 256^3 grid in {dt:.1f} s"}
+                      f"projected onto the full 256^3 grid in {dt:.1f} s",
+            "one_thread": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                           "sample": f"{n1} random tetrahedra of the workload in {dt1:.1f} s"}}
 
 
 def max_over_ranks(v: float, ws: int, device) -> float:

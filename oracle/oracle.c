@@ -319,8 +319,9 @@ int cdo_project(int dim, long long nv, long long ns, const double* px, const dou
     int err = ORACLE_OK;
     long long pieces = 0, tested = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 256) reduction(+ : pieces, tested)
+    /* the thread count of this call only (the process-wide default stays as it was) */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 256) reduction(+ : pieces, tested)
 #endif
     for (long long s = 0; s < ns; ++s) {
         double u[4][3], r[4];
@@ -387,8 +388,9 @@ int cdo_project_cells(int dim, long long nv, long long ns, const double* px, con
     double cv = cell_volume(&P);
     int err = ORACLE_OK;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4096)
+    /* the thread count of this call only (the process-wide default stays as it was) */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4096)
 #endif
     for (long long s = 0; s < ns; ++s) {
         double u[4][3], r[4];

@@ -366,3 +366,12 @@ def test_errors():
         oracle.project(_mesh(pos, [[0, 1, 2]], [1, 1, 1], (4, 4)))
     with pytest.raises(oracle.OracleError):  # vertex index out of range
         oracle.project(_mesh(pos, [[0, 1, 5]], [1, 1, 1], (4, 4)))
+
+
+def test_thread_count_is_per_call():
+    """A call on one thread gives the same cells and leaves the process-wide thread count as it was."""
+    mesh = mg.random_simplices(3, 300, 8, 2.0, np.random.default_rng(25))
+    before = oracle.max_threads()
+    one = oracle.project(mesh, nthreads=1)
+    assert oracle.max_threads() == before
+    assert np.max(np.abs(one - oracle.project(mesh))) <= 1e-14 * one.max()

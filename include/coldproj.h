@@ -225,7 +225,7 @@ CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
 /* Launch-shape tuning (no counterpart in the paper: the choice of a GPU launch shape).  Times the
  * projection of `prob` (into its own cell_mass, which is overwritten) with the main kernel's
  * persistent grid at 1, 2, 4 and 8 times the device's resident blocks, and keeps the fastest for
- * the later projections of ctx with the same dimension and precision (default 4).  With a
+ * the later projections of ctx with the same dimension and precision (default 8).  With a
  * non-null cache_path the choice is first looked up in that text file (lines
  * "<device> dim<D> <precision> <multiplier>"; the last entry of a key wins) and, when tuned, appended
  * to it.  Synchronises with the device.  *chosen (optional) receives the multiplier.  Returns

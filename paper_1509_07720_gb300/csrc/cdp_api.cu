@@ -342,7 +342,7 @@ int cdp_create(cdp_ctx** out, int device) {
     c->blocks_big[0] = cdp::resident_blocks(2, 0);
     c->blocks_big[1] = cdp::resident_blocks(2, 1);
     for (int d3 = 0; d3 < 2; ++d3)
-        for (int f = 0; f < 2; ++f) c->grid_mult[d3][f] = 4;
+        for (int f = 0; f < 2; ++f) c->grid_mult[d3][f] = 8;
     if (cudaMalloc(&c->ctr, sizeof(cdp::Counters)) != cudaSuccess ||
         cudaMalloc(&c->stats, 2 * sizeof(cdp::UnitCounts)) != cudaSuccess ||
         cudaMallocHost(&c->h_ctr, sizeof(cdp::Counters)) != cudaSuccess ||

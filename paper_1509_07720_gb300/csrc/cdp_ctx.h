@@ -36,7 +36,7 @@ struct cdp_ctx {
     int blocks_small[2];  // resident blocks per SM of the 3D kernel (fp64, fp32)
     int blocks_big[2];    // of the 2D kernel
     int grid_mult[2][2];  // [dim == 3][fp32]: the main kernel's persistent grid, in multiples of its
-                          // resident blocks (4 unless cdp_autotune chose another)
+                          // resident blocks (8 unless cdp_autotune chose another)
     cdp::VertexRec* verts;
     size_t verts_cap;
     int* queue;           // list of the large tetrahedra (tiled by the main kernel)

@@ -118,7 +118,7 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     L.stats = nullptr;
     L.num_sms = s->num_sms;
     int fp32 = precision == CDP_FP32_MIXED;
-    L.small_blocks_per_sm = 4 * s->blocks[p->dim == 3][fp32];
+    L.small_blocks_per_sm = 8 * s->blocks[p->dim == 3][fp32];
     L.resident_per_sm = s->blocks[p->dim == 3][fp32];
     L.big_list = (int*)(s->scratch + kListOffset);
     L.big_cap = kMaxSimplices;

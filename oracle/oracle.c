@@ -3,9 +3,9 @@
  * regular grid.  TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
  * baseline call it; the library never does.  It shares no code with the CUDA path.
  *
- * What it computes is the plain definition of the projection (Sect. 3, Eq. firstOrder; the
- * output of Algorithm 2, "the exact projection of the linear interpolation of rho_i over M
- * onto the voxels of G"):
+ * What it computes is the plain definition of the projection (Sect. 3, Eq. firstOrder; what
+ * Algorithm 2 outputs: for every grid cell, the exact mass of the piecewise-linear interpolant of
+ * the vertex densities over the mesh):
  *
  *     m_V = sum_S  integral over (S intersect V) of rho_S(x) dx,
  *

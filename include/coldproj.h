@@ -156,7 +156,7 @@ CDP_API int cdp_project_noalloc(const cdp_problem* prob, int precision, int accu
                                 void* stream);
 
 /* Vertex densities from simplex masses (Sect. 4.4): rho_out[j] = sum of simplex_mass[i] over the
- * simplices incident to vertex j divided by the sum of their volumes |V_i| (world units,
+ * simplices i that have vertex j, divided by the sum of their volumes |V_i| (world units,
  * periodic minimal image when prob->periodic).  Uses dim, n_verts, n_simplices, pos, simplices,
  * box_len and periodic of `prob` (its rho and cell_mass are ignored).  simplex_mass: device
  * double[n_simplices]; rho_out: device double[n_verts] (0 for a vertex with no simplex).

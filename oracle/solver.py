@@ -26,7 +26,7 @@ import numpy as np
 
 
 def vertex_density(pos, simplices, masses, box_len, periodic=True):
-    """rho_j = (sum_i M_i) / (sum_i |V_i|) over the simplices incident to vertex j.
+    """rho_j = (sum_i M_i) / (sum_i |V_i|), the sums taken over the simplices i that have vertex j.
 
     pos [D, Nv], simplices [Ns, D+1], masses [Ns]. Vertices with no simplex get 0."""
     d = pos.shape[0]

@@ -227,6 +227,17 @@ static int load_simplex(const problem* P, long long s, double u[4][3], double r[
                 if (fabs(d) >= 0.5 * N) return ORACLE_ERR_EXTENT;
                 u[i][a] = u[0][a] + d;
             }
+        /* the unwrapped simplex must span less than half the box along every axis: then every
+           vertex is also the minimal image of every other one, and the simplex does not depend on
+           which vertex is listed first */
+        for (int a = 0; a < P->dim; ++a) {
+            double mn = u[0][a], mx = u[0][a];
+            for (int i = 1; i < nvs; ++i) {
+                mn = u[i][a] < mn ? u[i][a] : mn;
+                mx = u[i][a] > mx ? u[i][a] : mx;
+            }
+            if (mx - mn >= 0.5 * (double)P->n[a]) return ORACLE_ERR_EXTENT;
+        }
     }
     return ORACLE_OK;
 }

@@ -68,6 +68,16 @@ CDP_HD bool unwrap(i64& d, int n, int periodic) {
     return d != half && d != -half;
 }
 
+// On a periodic axis the unwrapped simplex must span less than half the box: then every vertex is
+// also the minimal image of every other one, so the simplex (and its projection) does not depend on
+// which vertex is listed first.
+CDP_HD bool extent_ok(i64 a, i64 b, i64 c, i64 d, int n, int periodic) {
+    if (!periodic) return true;
+    const i64 ab0 = a < b ? a : b, cd0 = c < d ? c : d, ab1 = a < b ? b : a, cd1 = c < d ? d : c;
+    const i64 mn = ab0 < cd0 ? ab0 : cd0, mx = ab1 < cd1 ? cd1 : ab1;
+    return mx - mn < ((i64)n << (CDP_Q - 1));
+}
+
 // Canonical tetrahedron from its 4 vertex records.  Returns 0 (ok), 1 (zero volume: contributes
 // nothing) or an error flag.  COPY only gives a caller its own out-of-line instance.
 template <int COPY = 0>
@@ -85,6 +95,7 @@ CDP_COLD unsigned canon_tet(const GridDesc& g, const VertexRec* v[4], Tet& S) {
             if (d > lim || d < -lim) return CDP_FLAG_EXTENT;
             S.L[k][a] = base + d;
         }
+        if (!extent_ok(S.L[0][a], S.L[1][a], S.L[2][a], S.L[3][a], g.n[a], g.periodic)) return CDP_FLAG_EXTENT;
     }
     for (int k = 0; k < 4; ++k) S.rho[k] = v[k]->rho;
     // orientation: sign of (x3-x0) . ((x1-x0) x (x2-x0)); make it positive by swapping 2 and 3
@@ -135,6 +146,7 @@ CDP_COLD unsigned canon_tri(const GridDesc& g, const VertexRec* v[3], Tri& S) {
             if (d > lim || d < -lim) return CDP_FLAG_EXTENT;
             S.L[k][a] = base + d;
         }
+        if (!extent_ok(S.L[0][a], S.L[1][a], S.L[2][a], S.L[2][a], g.n[a], g.periodic)) return CDP_FLAG_EXTENT;
     }
     for (int k = 0; k < 3; ++k) S.rho[k] = v[k]->rho;
     i128 D = mul64(S.L[1][0] - S.L[0][0], S.L[2][1] - S.L[0][1]) -

@@ -8,10 +8,23 @@ power spectrum k^-2 for |k| <= 16 and rms 4 Lagrangian cells (post shell-crossin
 vertex density (sigma = 0.5), periodic unit box, 256^3 FP64 output grid.
 
 One step = one full projection: zeroing the grid, vertex records, the per-tetrahedron set-up, the
-block-cooperative projection kernel and the tiled large-tetrahedron kernel, all through the C ABI. Inputs (201 MB of simplices, 67 MB of vertex records,
-134 MB grid) exceed the 129 MB L2, so no flush is needed between steps.
+block-cooperative projection kernel and the tiled large-tetrahedron kernel, all through the C ABI.
+Inputs (201 MB of simplices, 67 MB of vertex records, 134 MB grid) exceed the 129 MB L2, so no
+flush is needed between steps.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+``--config`` selects another workload of the same family, each printed as its own JSON line of the
+same form (``all``: every one, the headline first):
+  c1a / c1b  2D: 64^2 Lagrangian squares (8,192 triangles), two sine waves (single / multi-stream),
+             128^2 grid
+  c2         3D: 32^3 Kuhn cubes (196,608 tets), GRF rms 0.5 cell, 128^3 grid
+  c3         the headline workload above
+  c4         3D: a 64^3 Kuhn base bisected to 50,331,953 tets (volumes over four decades), 512^3
+             grid
+  c5         64 independent 2D/3D problems (18.3M simplices): their projections in one call, and one
+             time step of all of them (drift, vertex density, projection, Poisson, force, kick,
+             drift) replayed as one CUDA graph
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
 Under torchrun every rank projects its own replica (weak scaling; no collective on the data path).
 """
 from __future__ import annotations
@@ -32,86 +45,35 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "c3"
 METRIC = "tetrahedra projected/s on 256^3 grid, FP32-mixed vs FP64 plain, same GB300"
 UNIT = "tets/s"
+CONFIG_CHOICES = ("c3", "c1a", "c1b", "c2", "c4", "c5", "all")
 
-# Algorithmic FP32 work of the Franklin evaluation per (corner, cell) incidence: six
-# (vertex, edge, facet) triples of 3+3 dot products (5 flops each), the bracket (9) and the triple
-# product (3) = 42 flops each; the type-A closed form is 12 flops.
-FLOPS_PER_INCIDENCE = {"a": 12, "b": 252, "c": 252, "d": 252}
-# DRAM bytes (read + write) of one k_project_tet<float> launch per tetrahedron, from the ncu capture
-# summarised in profiles/k_project_tet_c3s64_full.md (1,572,864 tetrahedra: 713.1 MB read, 86.9 MB
-# written); the traffic is the geometry records plus the grid atomics, so it scales with the
-# tetrahedron count.  None while the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_TET = (713.054976e6 + 86.854400e6) / 1572864
-# ALU peaks derived from unit counts and the maximum SM clock (no measured FP32 figure exists):
-# 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 1.25 TFLOP/s nominal.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# Algorithmic FP32 work per (corner, cell) incidence of the Franklin evaluation: the upper figure
+# of the 100-200 flops a B, C or D incidence takes (six (vertex, edge, facet) triples, each three
+# projections of the corner and three of the gradient on its frame, the bracket and the triple
+# product), and 12 flops for the closed form of an A incidence (the corner's three offsets, their
+# product, the bracket).
+FLOPS_PER_INCIDENCE = {"a": 12, "b": 200, "c": 200, "d": 200}
+# Per-tetrahedron counters of one k_project_tet<float> launch, from the ncu capture summarised in
+# profiles/k_project_tet_c3sub8_full.md (a random 1/8 of the headline workload's tetrahedra,
+# 1,572,864, on its own 256^3 grid): DRAM bytes read + written, and warp instructions issued.
+# They scale with the tetrahedron count.  None while the kernel has changed since the capture.
+TRAFFIC_BYTES_PER_TET = None
+WARP_INST_PER_TET = None
 
 
-def _args():
+def _args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=WORKLOAD, choices=CONFIG_CHOICES)
     ap.add_argument("--scale", type=int, default=None, help="Lagrangian lattice size override (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 plain path")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-problem step (c5)")
-    return ap.parse_args()
-
-
-def _batched_step(pkg, mg, proj, dev, stream, steps=3, warmup=3):
-    """The batched workload c5: 64 independent 2D/3D problems advanced by one time step each (drift,
-    vertex density, FP32-mixed projection, FFT Poisson, force, kick, drift) as one replayed CUDA
-    graph.  Inputs resident on the device; CUDA events around the replays."""
-    import torch
-
-    batch = mg.make_batch("c5")
-    dt = mg.cfl_dt(batch)
-    keep = []
-    probs = []
-    for p in batch:
-        m = p.mesh
-        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-        pos = [t(m.pos[a]) for a in range(m.dim)]
-        vel = [t(p.vel[a]) for a in range(m.dim)]
-        acc = [torch.zeros(m.n_verts, dtype=torch.float64, device=dev) for _ in range(m.dim)]
-        simp, mass = t(m.simplices), t(p.masses)
-        rho = torch.zeros(m.n_verts, dtype=torch.float64, device=dev)
-        cm = torch.zeros(m.grid, dtype=torch.float64, device=dev)
-        phi = torch.zeros(m.grid, dtype=torch.float64, device=dev)
-        sp = pkg.cdp_step_problem()
-        sp.mesh = pkg.Projector.make_problem(pos, simp, rho, m.grid, m.box_lo, m.box_len, True, cm)
-        for a in range(m.dim):
-            sp.vel[a] = vel[a].data_ptr()
-            sp.acc[a] = acc[a].data_ptr()
-        sp.simplex_mass = mass.data_ptr()
-        sp.phi = phi.data_ptr()
-        probs.append(sp)
-        keep.append((pos, vel, acc, simp, mass, rho, cm, phi))
-    arr = (pkg.cdp_step_problem * len(probs))(*probs)
-    st = stream.cuda_stream
-    for _ in range(warmup):  # the first call captures the graph
-        rc = pkg.cdp_step_batched(proj._ctx, arr, pkg.CDP_FP32_MIXED, dt, 1.0, True, st)
-        if rc:
-            raise RuntimeError(f"cdp_step_batched: {rc}")
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        pkg.cdp_step_batched(proj._ctx, arr, pkg.CDP_FP32_MIXED, dt, 1.0, True, st)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / steps
-    ns = sum(p.mesh.n_simplices for p in batch)
-    del keep
-    return {"workload": "c5: 64 problems (32 3D Kuhn/GRF, 32 2D two-sine), simplex counts log-uniform "
-                        "in [1e3, 2e6], grids 64..256 per axis; one time step each as one CUDA graph",
-            "problems": len(batch), "simplices": ns, "ms_per_step": ms, "simplices_per_s": ns / (ms / 1000.0),
-            "dtype": "f32-mixed projection, f64 solver", "steps": steps, "warmup": warmup}
+    return ap.parse_args(argv)
 
 
 class ClockSampler:
@@ -160,9 +122,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _measured_peaks():
+def _json_file(name):
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        with open(os.path.join(ROOT, name)) as f:
             return json.load(f)
     except OSError:
         return {}
@@ -192,10 +154,10 @@ def _cpu_baseline(mesh, target_s=12.0, seed=5):
     oracle.project(mesh.subset(idx1), nthreads=1)
     dt1 = time.perf_counter() - t1
     return {"value": n2 / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{n2} of {ns} tetrahedra of the workload, chosen uniformly at random (seed {seed}), "
-                      f"projected onto the full 256^3 grid in {dt:.1f} s",
+            "sample": f"{n2} of {ns} simplices of the workload, chosen uniformly at random (seed {seed}), "
+                      f"projected onto the full grid in {dt:.1f} s",
             "one_thread": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
-                           "sample": f"{n1} random tetrahedra of the workload in {dt1:.1f} s"}}
+                           "sample": f"{n1} random simplices of the workload in {dt1:.1f} s"}}
 
 
 def max_over_ranks(v: float, ws: int, device) -> float:
@@ -223,6 +185,16 @@ def _dist():
     return ws, rank, local
 
 
+def workload_text(name, mesh=None, scale=None):
+    from paper_1509_07720_gb300 import meshgen as mg
+
+    if name == "c5":
+        return ("c5: 64 problems (32 3D Kuhn/GRF, 32 2D two-sine), simplex counts log-uniform in [1e3, 2e6], grids "
+                "64..256 per axis")
+    txt = mg.CONFIG_NAMES[name] + ", periodic, FP64 grid"
+    return txt if scale is None else f"{txt} (lattice scale {scale})"
+
+
 def run_reference(a):
     """Reference arm: the CPU oracle timed on this machine's host cores, each step a bounded sample."""
     ws, rank, _ = _dist()
@@ -231,7 +203,8 @@ def run_reference(a):
     import oracle
     from paper_1509_07720_gb300 import meshgen as mg
 
-    mesh = mg.make_config(WORKLOAD, a.scale)
+    name = WORKLOAD if a.config in ("all", "c5") else a.config
+    mesh = mg.make_config(name, a.scale)
     rng = np.random.default_rng(17)
     ns = mesh.n_simplices
     per_step = min(ns, 40000)
@@ -250,39 +223,84 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1000 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "128^3 Kuhn lattice (12,582,912 tets), GRF k^-2 k<=16 rms 4 cells, lognormal rho "
-                               "sigma 0.5, 256^3 grid; each step a random sample of %d tets" % per_step},
+        "config": {"workload": workload_text(name) + "; each step a random sample of %d simplices" % per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                         "sample": f"{per_step} random tetrahedra per step of the {ns}-tet workload"},
+                         "sample": f"{per_step} random simplices per step of the {ns}-simplex workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_ours(a):
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+
+KERNELS = {3: ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>", "k_project_big<float>"],
+           2: ["k_prep_vertices", "-", "k_project_warp<2,float>", "-"]}
+
+
+def roofline(dim, st, kern_ms, ns, peaks):
+    """The ceiling of the kernel that takes most of the step: issue-bound FP32 arithmetic for the
+    projection kernels, from the exact corner incidences of the statistics pass."""
+    dom = int(np.argmax(kern_ms))
+    fp32_peak = peaks.get("fp32_fma_tflops")
+    src = "measured (ALU_PEAKS.json, bench_peaks.cu)"
+    if fp32_peak is None:
+        fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (ALU_PEAKS.json absent)"
+    if dom == 0:
+        hbm = _json_file("MEASURED_PEAKS.json").get("hbm_gbs", 6800.0)
+        achieved = st["n_verts"] * (3 * 8 + 8 + 32) / (kern_ms[0] / 1000.0) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": KERNELS[dim][0]}
+    if dim == 3 and dom == 3:
+        inc = {k: st["large_corners"][i] for i, k in enumerate("abcd")}
+    elif dim == 3:
+        inc = {k: st["corners_" + k] - st["large_corners"][i] for i, k in enumerate("abcd")}
+    else:
+        inc = {k: st["corners_" + k] for k in "abcd"}
+    flops = sum(FLOPS_PER_INCIDENCE[k] * v for k, v in inc.items())
+    sec = kern_ms[dom] / 1000.0
+    achieved = flops / sec / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None, "kernel": KERNELS[dim][dom],
+            "kernel_ms": kern_ms[dom], "flops_per_launch": flops,
+            "flops_per_incidence": FLOPS_PER_INCIDENCE, "peak_source": src,
+            "peak_clock_mhz": peaks.get("sm_mhz_median")}
+    headline = dim == 3 and dom == 2
+    if headline and TRAFFIC_BYTES_PER_TET is not None:
+        roof["traffic"] = TRAFFIC_BYTES_PER_TET * ns
+        roof["traffic_unit"] = ("bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1/8 random "
+                                "subset of the workload's tetrahedra on its own grid, scaled by tetrahedra")
+    if headline and WARP_INST_PER_TET is not None and peaks.get("warp_issue_ginst"):
+        inst = WARP_INST_PER_TET * ns / sec / 1e9
+        roof["issue"] = {"achieved_ginst": inst, "peak_ginst": peaks["warp_issue_ginst"],
+                         "frac": inst / peaks["warp_issue_ginst"],
+                         "unit": "warp instructions per second (peak: one per scheduler per clock, measured with "
+                                 "FP32 FMAs)"}
+    if st.get("n_pieces") and peaks.get("red_f64_run32_gps"):
+        red = 2 * st["n_pieces"] / (sum(kern_ms[2:]) / 1000.0) / 1e9
+        roof["l2_reductions"] = {"achieved_gps": red, "peak_gps": peaks["red_f64_run32_gps"],
+                                 "frac": red / peaks["red_f64_run32_gps"],
+                                 "unit": "FP64 reductions per second (two per FP32 piece: the piece and its "
+                                         "closure share)"}
+    return roof
+
+
+def _to_dev(torch, dev, mesh):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    return t(mesh.pos), t(mesh.simplices), t(mesh.rho), torch.empty(mesh.grid, dtype=torch.float64, device=dev)
+
+
+def bench_projection(a, pkg, proj, dev, stream, name, ws, rank, headline):
+    """One workload: FP32-mixed timed, FP64 plain beside it, e2e from pinned host buffers."""
     import torch
 
-    import paper_1509_07720_gb300 as pkg
-    from paper_1509_07720_gb300 import build, meshgen as mg
+    from paper_1509_07720_gb300 import meshgen as mg
 
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
-    build.build_library()
-
-    mesh = mg.make_config(WORKLOAD, a.scale)
+    mesh = mg.make_config(name, a.scale)
     ns = mesh.n_simplices
-    pos = torch.from_numpy(np.ascontiguousarray(mesh.pos)).to(dev)
-    simp = torch.from_numpy(np.ascontiguousarray(mesh.simplices)).to(dev)
-    rho = torch.from_numpy(np.ascontiguousarray(mesh.rho)).to(dev)
-    out = torch.empty(mesh.grid, dtype=torch.float64, device=dev)
-    proj = pkg.Projector(local)
-    stream = torch.cuda.current_stream(dev)
+    pos, simp, rho, out = _to_dev(torch, dev, mesh)
 
     def step(prec):
         proj.project(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, True, precision=prec, out=out,
@@ -297,6 +315,7 @@ def run_ours(a):
     # one instrumented pass for the corner counts (outside every timed region)
     _, st32 = proj.project(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, True,
                            precision=pkg.CDP_FP32_MIXED, out=out, stream=stream, stats=True)
+    st32["n_verts"] = mesh.n_verts
 
     def timed(prec, steps, warmup):
         for _ in range(warmup):
@@ -319,29 +338,24 @@ def run_ours(a):
         proj.timing(False)
         return ms, [k / max(calls, 1) for k in kern]
 
-    clk = ClockSampler(local)
+    clk = ClockSampler(dev.index)
     clk.start()
     ms32, kern32 = timed(pkg.CDP_FP32_MIXED, a.steps, a.warmup)
     clocks = clk.stop()
     proj.check(stream)
     ms32 = max_over_ranks(ms32, ws, dev)
     value = job_throughput(ws, ns, ms32)
-
-    # FP64 plain path on the same GPU, same workload (fewer steps: it is much slower)
     k64 = max(1, a.fp64_steps)
     ms64, kern64 = timed(pkg.CDP_FP64, k64, 1)
     ms64 = max_over_ranks(ms64, ws, dev)
 
-    # end to end through the C ABI from pinned host buffers: H2D inputs, project, D2H grid
     e2e = None
     if not a.no_e2e:
         hp = torch.from_numpy(np.ascontiguousarray(mesh.pos)).pin_memory()
         hs = torch.from_numpy(np.ascontiguousarray(mesh.simplices)).pin_memory()
         hr = torch.from_numpy(np.ascontiguousarray(mesh.rho)).pin_memory()
         ho = torch.empty(mesh.grid, dtype=torch.float64).pin_memory()
-        dpos = torch.empty_like(pos)
-        dsimp = torch.empty_like(simp)
-        drho = torch.empty_like(rho)
+        dpos, dsimp, drho = torch.empty_like(pos), torch.empty_like(simp), torch.empty_like(rho)
 
         def e2e_step():
             dpos.copy_(hp, non_blocking=True)
@@ -367,59 +381,161 @@ def run_ours(a):
         hb = hp.numel() * 8 + hs.numel() * 4 + hr.numel() * 8
         e2e = {"value": job_throughput(ws, ns, mse), "unit": UNIT, "h2d_bytes_per_step": int(hb),
                "d2h_bytes_per_step": int(ho.numel() * 8), "ms_per_step": mse}
+        del hp, hs, hr, ho, dpos, dsimp, drho
 
-    # the batched workload (every rank runs its own replica; rank 0 reports its own)
-    batched = None if a.no_batched else _batched_step(pkg, mg, proj, dev, stream)
-
-    if rank != 0:
-        return
-    # roofline of the dominant kernel (the tetrahedron projection kernel; its incidences are all
-    # corners but those found on the tiles of the large tetrahedra, by k_project_big)
-    names = ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>", "k_project_big<float>"]
-    dom = int(np.argmax(kern32))
-    if dom == 2:
-        inc = {k: st32["corners_" + k] - st32["large_corners"][i] for i, k in enumerate("abcd")}
-    else:
-        inc = None
-    if inc is not None:
-        flops = sum(FLOPS_PER_INCIDENCE[k] * v for k, v in inc.items())
-        achieved = flops / (kern32[dom] / 1000.0) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None if TRAFFIC_BYTES_PER_TET is None else TRAFFIC_BYTES_PER_TET * ns,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                "scale-64 capture scaled by tetrahedra)", "kernel": names[dom],
-                "kernel_ms": kern32[dom], "flops_per_launch": flops,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    else:
-        hbm = _measured_peaks().get("hbm_gbs", 6800.0)
-        byts = mesh.n_verts * (3 * 8 + 8 + 32)
-        achieved = byts / (kern32[0] / 1000.0) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": names[0]}
+    peaks = _json_file("ALU_PEAKS.json")
+    dim = mesh.dim
+    launches_per_step = (3 if dim == 2 else 4) + (0 if dim == 2 else max(0, (ns - 1) // (1 << 24)) * 2)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC if headline else f"simplices projected/s ({name}), FP32-mixed vs FP64 plain, same GB300",
+        "value": value, "unit": UNIT if dim == 3 else "triangles/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-mixed (f64 accumulate)", "data": "synthetic",
-        "config": {"workload": "128^3 Kuhn lattice (12,582,912 tets), GRF k^-2 k<=16 rms 4 cells, lognormal rho "
-                               "sigma 0.5, periodic, 256^3 FP64 grid" if a.scale is None else f"c3 scale {a.scale}",
-                   "tets": ns, "grid": list(mesh.grid), "l2": "inputs larger than L2 (no flush)",
+        "config": {"workload": workload_text(name, mesh, a.scale), "name": name, "simplices": ns,
+                   "grid": list(mesh.grid),
+                   "l2": "inputs larger than L2 (no flush)" if ns * 16 > 129e6 else
+                         "inputs smaller than L2: steps back to back, warm L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
         "fp64_plain": {"value": job_throughput(ws, ns, ms64), "unit": UNIT, "ms_per_step": ms64,
                        "kernel_ms": kern64, "speedup_fp32_mixed_vs_fp64": ms64 / ms32},
-        "kernel_ms": dict(zip(names, kern32)),
+        "kernel_ms": {k: v for k, v in zip(KERNELS[dim], kern32) if k != "-"},
         "corners": {k: st32[k] for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell",
-                                         "n_small", "n_large", "n_zero_volume", "exact_fallbacks")},
-        "roofline": roof,
+                                         "n_small", "n_large", "n_large_tiles", "n_zero_volume", "exact_fallbacks",
+                                         "n_pieces") if k in st32},
+        "roofline": roofline(dim, st32, kern32, ns, peaks),
         "clocks": clocks,
-        "gpu_launches": 4 * a.steps,  # vertex records, set-up, main kernel, large tetrahedra (one batch)
+        "gpu_launches": launches_per_step * a.steps,
         "e2e": e2e,
     }
-    if not a.no_batched:
-        line["batched"] = batched
-    if ws == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(mesh)
-    print(json.dumps(line), flush=True)
+    del pos, simp, rho, out
+    return line, mesh
+
+
+def bench_batch(a, pkg, proj, dev, stream, ws, steps=3, warmup=3):
+    """The batched workload c5: (1) the 64 projections in one cdp_project_batched call, FP32-mixed and
+    FP64; (2) one time step of all 64 problems (drift, vertex density, FP32-mixed projection, FFT
+    Poisson, force, kick, drift) replayed as one CUDA graph.  Inputs resident on the device; CUDA
+    events around the calls."""
+    import torch
+
+    from paper_1509_07720_gb300 import meshgen as mg
+
+    batch = mg.make_batch("c5")
+    dt = mg.cfl_dt(batch)
+    keep = []
+    probs = []
+    flat = []
+    for p in batch:
+        m = p.mesh
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        pos = [t(m.pos[a_]) for a_ in range(m.dim)]
+        vel = [t(p.vel[a_]) for a_ in range(m.dim)]
+        acc = [torch.zeros(m.n_verts, dtype=torch.float64, device=dev) for _ in range(m.dim)]
+        simp, mass = t(m.simplices), t(p.masses)
+        rho = torch.zeros(m.n_verts, dtype=torch.float64, device=dev)
+        rho0 = t(m.rho)
+        cm = torch.zeros(m.grid, dtype=torch.float64, device=dev)
+        cm2 = torch.zeros(m.grid, dtype=torch.float64, device=dev)
+        phi = torch.zeros(m.grid, dtype=torch.float64, device=dev)
+        sp = pkg.cdp_step_problem()
+        sp.mesh = pkg.Projector.make_problem(pos, simp, rho, m.grid, m.box_lo, m.box_len, True, cm)
+        for a_ in range(m.dim):
+            sp.vel[a_] = vel[a_].data_ptr()
+            sp.acc[a_] = acc[a_].data_ptr()
+        sp.simplex_mass = mass.data_ptr()
+        sp.phi = phi.data_ptr()
+        probs.append(sp)
+        flat.append(pkg.Projector.make_problem(pos, simp, rho0, m.grid, m.box_lo, m.box_len, True, cm2))
+        keep.append((pos, vel, acc, simp, mass, rho, rho0, cm, cm2, phi))
+    ns = sum(p.mesh.n_simplices for p in batch)
+    st = stream.cuda_stream
+
+    def time_calls(fn, n_steps, n_warm):
+        for _ in range(n_warm):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n_steps
+
+    def project_all(prec):
+        rc = pkg.cdp_project_batched(proj._ctx, flat, prec, st)
+        if rc:
+            raise RuntimeError(f"cdp_project_batched: {rc}")
+
+    clk = ClockSampler(dev.index)
+    clk.start()
+    ms_p32 = time_calls(lambda: project_all(pkg.CDP_FP32_MIXED), steps, warmup)
+    clocks = clk.stop()
+    ms_p64 = time_calls(lambda: project_all(pkg.CDP_FP64), 1, 1)
+    arr = (pkg.cdp_step_problem * len(probs))(*probs)
+
+    def step():
+        rc = pkg.cdp_step_batched(proj._ctx, arr, pkg.CDP_FP32_MIXED, dt, 1.0, True, st)
+        if rc:
+            raise RuntimeError(f"cdp_step_batched: {rc}")
+
+    ms_step = time_calls(step, steps, warmup)  # the first warm-up call captures the graph
+    proj.check(stream)
+    ms_p32 = max_over_ranks(ms_p32, ws, dev)
+    ms_step = max_over_ranks(ms_step, ws, dev)
+    del keep
+    return {"workload": workload_text("c5"), "problems": len(batch), "simplices": ns,
+            "projection": {"ms_per_step": ms_p32, "simplices_per_s": job_throughput(ws, ns, ms_p32),
+                           "fp64_ms_per_step": ms_p64, "fp64_simplices_per_s": job_throughput(ws, ns, ms_p64),
+                           "speedup_fp32_mixed_vs_fp64": ms_p64 / ms_p32},
+            "step": {"ms_per_step": ms_step, "simplices_per_s": job_throughput(ws, ns, ms_step),
+                     "what": "drift, vertex density, FP32-mixed projection, FFT Poisson, force, kick, drift; "
+                             "one CUDA graph"},
+            "dtype": "f32-mixed projection, f64 solver", "steps": steps, "warmup": warmup, "clocks": clocks}
+
+
+def run_ours(a):
+    import torch
+
+    import paper_1509_07720_gb300 as pkg
+    from paper_1509_07720_gb300 import build
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    build.build_library()
+    proj = pkg.Projector(local)
+    stream = torch.cuda.current_stream(dev)
+    names = ["c3", "c1a", "c1b", "c2", "c4", "c5"] if a.config == "all" else [a.config]
+    for name in names:
+        if name == "c5":
+            b = bench_batch(a, pkg, proj, dev, stream, ws, steps=max(3, min(a.steps, 10)), warmup=max(3, a.warmup))
+            if rank == 0:
+                line = {"metric": "simplices projected/s, 64 independent problems (c5), FP32-mixed, same GB300",
+                        "value": b["projection"]["simplices_per_s"], "unit": "simplices/s", "n_gpus": ws,
+                        "steps": b["steps"], "warmup": b["warmup"], "ms_per_step": b["projection"]["ms_per_step"],
+                        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                        "dtype": "f32-mixed (f64 accumulate)", "data": "synthetic",
+                        "config": {"workload": b["workload"], "name": "c5", "simplices": b["simplices"],
+                                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+                        "batched": b, "clocks": b["clocks"], "e2e": None}
+                print(json.dumps(line), flush=True)
+            continue
+        headline = name == WORKLOAD
+        line, mesh = bench_projection(a, pkg, proj, dev, stream, name, ws, rank, headline)
+        if headline and a.config != "all" and not a.no_batched:
+            line["batched"] = bench_batch(a, pkg, proj, dev, stream, ws)
+        if rank == 0:
+            if headline and ws == 1 and not a.no_cpu_baseline:
+                line["cpu_baseline"] = _cpu_baseline(mesh)
+            print(json.dumps(line), flush=True)
+        del mesh
     proj.close()
 
 

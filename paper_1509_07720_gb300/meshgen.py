@@ -449,3 +449,177 @@ def random_simplices(dim: int, ns: int, grid: int, size: float, rng, periodic: b
     simp = np.arange(ns * (dim + 1), dtype=np.int32).reshape(ns, dim + 1)
     rho = lognormal_density(ns * (dim + 1), rho_sigma, rng) if rho_sigma > 0 else np.ones(ns * (dim + 1))
     return Mesh(pos, simp, rho, (grid,) * dim, (0.0,) * dim, (1.0,) * dim, periodic, "random")
+
+
+# --------------------------------------------------------------------------------------------
+# Degenerate and transformed inputs (parity edge cases)
+# --------------------------------------------------------------------------------------------
+
+def _dyadic(v, bits: int):
+    """v rounded to a multiple of 2^-bits (exactly representable, and exact under shifts by
+    multiples of 2^-bits that stay in range)."""
+    return np.round(np.asarray(v, dtype=np.float64) * (1 << bits)) / float(1 << bits)
+
+
+def quantize_positions(mesh: Mesh, bits: int = 30) -> Mesh:
+    """The mesh with every coordinate rounded to a multiple of 2^-bits box lengths (unit box)."""
+    return dataclasses.replace(mesh, pos=np.ascontiguousarray(_wrap(_dyadic(mesh.pos, bits))))
+
+
+def shift_mesh(mesh: Mesh, cells) -> Mesh:
+    """The periodic unit-box mesh translated by an integer number of grid cells per axis (exact for
+    dyadic coordinates and power-of-two grids)."""
+    off = np.array([c / g for c, g in zip(cells, mesh.grid)], dtype=np.float64)[:, None]
+    return dataclasses.replace(mesh, pos=np.ascontiguousarray(_wrap(mesh.pos + off)))
+
+
+def permute_vertex_order(mesh: Mesh, rng) -> Mesh:
+    """The same simplices with the vertex indices of each one listed in a random order (even and
+    odd permutations alike)."""
+    d1 = mesh.simplices.shape[1]
+    keys = rng.random(mesh.simplices.shape)
+    order = np.argsort(keys, axis=1)
+    simp = np.take_along_axis(mesh.simplices, order, axis=1)
+    return dataclasses.replace(mesh, simplices=np.ascontiguousarray(simp.astype(np.int32)))
+
+
+def stratified_subset(mesh: Mesh, fraction_inv: int, rng) -> Mesh:
+    """About 1/fraction_inv of the simplices, drawn at random within each volume class (classes =
+    rounded log2 of the volume below the largest), so that every refinement level is represented."""
+    vol = simplex_volumes(mesh)
+    vmax = float(vol.max()) if vol.size else 1.0
+    cls = np.round(np.log2(vmax / np.maximum(vol, vmax * 2.0 ** -60))).astype(np.int64)
+    idx = []
+    for c in np.unique(cls):
+        ii = np.flatnonzero(cls == c)
+        k = (ii.size + fraction_inv - 1) // fraction_inv
+        idx.append(rng.choice(ii, k, replace=False))
+    idx = np.sort(np.concatenate(idx)) if idx else np.zeros(0, dtype=np.int64)
+    return mesh.subset(idx)
+
+
+def _assemble(dim, groups, grid, rng, periodic=True, rho_sigma=0.5):
+    """Mesh from a list of simplices given by their vertex coordinates ([n, D+1, D] arrays in box
+    units) plus index-level degeneracies: each group is (coords, index_pattern) where
+    index_pattern (or None) rewrites the simplex's index row, e.g. (0, 0, 1, 2) repeats vertex 0."""
+    pos_list, simp_list, nv = [], [], 0
+    for coords, pattern in groups:
+        n = coords.shape[0]
+        pos_list.append(coords.reshape(n * (dim + 1), dim).T)
+        base = nv + (dim + 1) * np.arange(n)[:, None]
+        rows = base + np.arange(dim + 1)[None, :]
+        if pattern is not None:
+            rows = base + np.asarray(pattern)[None, :]
+        simp_list.append(rows)
+        nv += n * (dim + 1)
+    pos = np.concatenate(pos_list, axis=1)
+    if periodic:
+        pos = _wrap(pos)
+    simp = np.concatenate(simp_list).astype(np.int32)
+    rho = lognormal_density(nv, rho_sigma, rng)
+    return Mesh(np.ascontiguousarray(pos), np.ascontiguousarray(simp), rho, (grid,) * dim, (0.0,) * dim,
+                (1.0,) * dim, periodic, "degenerate")
+
+
+def degenerate_meshes(dim: int, grid: int, rng) -> dict:
+    """Named meshes of the degenerate configurations the method must handle (Sect. 3.3), each as
+    (mesh, number of zero-volume simplices it contains by construction):
+
+      zero_volume  generic simplices mixed with flat ones on dyadic coordinates (all vertices on
+                   one plane in 3D, one line in 2D: exactly flat after the fixed-point conversion),
+                   simplices naming one vertex twice, simplices with two distinct vertices at one
+                   position, and (3D) simplices with three collinear vertices
+      slivers      nearly flat simplices: a flat dyadic base and an apex 2^-30 or 1.3e-7 cells off
+                   its plane (line), and needles with nearly collinear vertices
+      grid_planes  simplices with a facet (3D) / an edge (2D) exactly in a grid plane (line) at
+                   off-lattice positions, in pairs on both sides of that plane
+      grid_lines   3D: simplices with an edge exactly along a grid line at off-lattice positions,
+                   and facets through a grid node; 2D: vertices on grid lines and nodes, and edges
+                   through a grid node
+    Coordinates are in the periodic unit box with `grid` cells per axis (a power-of-two grid keeps
+    the dyadic coordinates exact in grid units)."""
+    h = 1.0 / grid
+    D = dim
+
+    def generic(n, size):
+        # vertex 0 uniform in the box, the others within `size` cells of it
+        v0 = rng.random((n, 1, D))
+        return np.concatenate([v0, v0 + (rng.random((n, D, D)) * 2 - 1) * size * h], axis=1)
+
+    def on_hyperplane(n, m, size):
+        # m points per simplex on the hyperplane x_{D-1} = c + slope . (x_0 .. x_{D-2}), with a
+        # dyadic anchor c, dyadic slopes and dyadic in-plane offsets: the coordinates are exact
+        anchor = _dyadic(rng.random((n, 1, D)), 12)
+        slope = _dyadic(rng.uniform(-1, 1, (n, 1, D - 1)), 3)
+        t = _dyadic((rng.random((n, m, D - 1)) * 2 - 1) * size * h, 12)
+        pts = np.empty((n, m, D))
+        pts[:, :, :D - 1] = anchor[:, :, :D - 1] + t
+        pts[:, :, D - 1] = anchor[:, :, D - 1] + np.sum(slope * t, axis=2)
+        return pts
+
+    out = {}
+    # ---- zero volume
+    groups = [(generic(40, 3.0), None), (on_hyperplane(20, D + 1, 3.0), None)]
+    groups.append((generic(10, 2.5), (0, 0) + tuple(range(1, D))))    # vertex 0 named twice
+    same = generic(10, 2.5)
+    same[:, 1] = same[:, 0]                                           # two vertices at one position
+    groups.append((same, None))
+    nzero = 40
+    if D == 3:
+        col = _dyadic(generic(10, 2.5), 12)
+        col[:, 2] = col[:, 0] + 0.5 * (col[:, 1] - col[:, 0])          # midpoint of edge 01: exact
+        groups.append((col, None))
+        nzero += 10
+    out["zero_volume"] = (_assemble(D, groups, grid, rng), nzero)
+    # ---- slivers
+    s_groups = [(generic(20, 3.0), None)]
+    for height in (2.0 ** -30, 1.3e-7):
+        base = on_hyperplane(30, D, 3.0)
+        apex = base.mean(axis=1, keepdims=True)
+        apex[:, :, D - 1] += height * h
+        s_groups.append((np.concatenate([base, apex], axis=1), None))
+    nd = generic(30, 4.0)
+    nd[:, 2] = nd[:, 0] + (0.5 + 1e-7 * rng.standard_normal((30, D))) * (nd[:, 1] - nd[:, 0])
+    s_groups.append((nd, None))                                       # needles
+    out["slivers"] = (_assemble(D, s_groups, grid, rng), 0)
+    # ---- facets (edges) in grid planes (lines), in pairs on both sides
+    g_groups = []
+    for ax in range(D):
+        n = 20
+        face = generic(n, 3.0)[:, :D]
+        face[:, :, ax] = rng.integers(0, grid, (n, 1)) * h
+        others = [a for a in range(D) if a != ax]
+        for side in (1.0, -1.0):
+            apex = face.mean(axis=1, keepdims=True)
+            apex[:, :, ax] += side * rng.uniform(0.3, 3.0, (n, 1)) * h
+            apex[:, :, others] += (rng.random((n, 1, D - 1)) - 0.5) * h
+            g_groups.append((np.concatenate([face, apex], axis=1), None))
+    out["grid_planes"] = (_assemble(D, g_groups, grid, rng), 0)
+    # ---- edges along grid lines and through grid nodes
+    l_groups = []
+    node = lambda n: rng.integers(0, grid, (n, 1, D)) * h
+    if D == 3:
+        for ax in range(3):
+            n = 20
+            edge = np.repeat(node(n), 2, axis=1)
+            edge[:, :, ax] = rng.random((n, 1)) + np.array([0.0, 1.0]) * rng.uniform(0.5, 4.0, (n, 1)) * h
+            rest = edge.mean(axis=1, keepdims=True) + (rng.random((n, 2, 3)) * 2 - 1) * 2.5 * h
+            l_groups.append((np.concatenate([edge, rest], axis=1), None))
+        n = 20
+        c = node(n)
+        u = _dyadic((rng.random((n, 2, 3)) * 2 - 1) * 2.0 * h, 14)
+        tri = np.concatenate([c + u[:, :1], c + u[:, 1:], c - u[:, :1] - u[:, 1:]], axis=1)  # centroid on the node
+        apex = c + _dyadic((rng.random((n, 1, 3)) * 2 - 1) * 2.0 * h, 14)
+        l_groups.append((np.concatenate([tri, apex], axis=1), None))
+    else:
+        n = 30
+        v = generic(n, 3.0)
+        v[:, 0, 0] = np.round(v[:, 0, 0] * grid) * h                  # vertex 0 on a grid line
+        v[:, 1] = np.round(v[:, 1] * grid) * h                        # vertex 1 on a grid node
+        l_groups.append((v, None))
+        c = node(n)
+        u = _dyadic((rng.random((n, 1, 2)) * 2 - 1) * 2.5 * h, 14)
+        w = _dyadic((rng.random((n, 1, 2)) * 2 - 1) * 2.5 * h, 14)
+        l_groups.append((np.concatenate([c + u, c - u, c + w], axis=1), None))  # edge 01 through the node
+    out["grid_lines"] = (_assemble(D, l_groups, grid, rng), 0)
+    return out

@@ -1,10 +1,13 @@
-"""Named projection cases for profiling (ncu) and timing: ``python -m paper_1509_07720_gb300.profile_cases``.
+"""Named projection cases for profiling (ncu) and timing: ``python profile_cases.py <case>``.
 
-Each case builds its seeded synthetic mesh, puts it on ``cuda:0`` and projects it ``--reps`` times
-through the public API (``Projector.project``) with CUDA events around every call, then prints one
-JSON line with the times.  Cases:
+Measurement harness beside ``bench.py``, not part of the library: each case builds its seeded
+synthetic mesh, puts it on ``cuda:0`` and projects it ``--reps`` times through the public API
+(``Projector.project``) with CUDA events around every call, then prints one JSON line with the
+times.  Cases:
 
-  c3           the 128^3 Kuhn lattice of the headline benchmark (``--scale n``: an n^3 lattice)
+  c3           the 128^3 Kuhn lattice of the headline benchmark (``--scale n``: an n^3 lattice;
+               ``--subset k``: a seeded random 1/k of its tetrahedra on the same grid, the size an
+               ncu capture of the full kernel allows)
   c5           one problem of the 64-problem batched workload (``--problem i``), projected alone
   c5_3d        the 32 three-dimensional problems of that workload, one after the other
 """
@@ -28,13 +31,18 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["c3", "c5", "c5_3d"])
     ap.add_argument("--scale", type=int, default=None, help="c3: lattice size (default 128)")
+    ap.add_argument("--subset", type=int, default=1, help="c3: keep a random 1/k of the tetrahedra (seed 8)")
     ap.add_argument("--problem", type=int, default=0, help="c5: problem index in [0, 64)")
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args(argv)
 
+    import os
+    import sys
+
     import torch
 
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
     import paper_1509_07720_gb300 as pkg
     from paper_1509_07720_gb300 import build
     from paper_1509_07720_gb300 import meshgen as mg
@@ -43,7 +51,11 @@ def main(argv=None):
         raise SystemExit("profile_cases needs a CUDA device")
     build.build_library()
     if a.case == "c3":
-        meshes = [mg.make_config("c3", a.scale)]
+        m = mg.make_config("c3", a.scale)
+        if a.subset > 1:
+            rng = np.random.default_rng(8)
+            m = m.subset(np.sort(rng.choice(m.n_simplices, m.n_simplices // a.subset, replace=False)))
+        meshes = [m]
     else:
         batch = mg.make_batch("c5")
         meshes = [batch[a.problem].mesh] if a.case == "c5" else [p.mesh for p in batch if p.mesh.dim == 3]
@@ -63,7 +75,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     proj.check(stream)
-    print(json.dumps({"case": a.case, "scale": a.scale, "problem": a.problem if a.case == "c5" else None,
+    print(json.dumps({"case": a.case, "scale": a.scale, "subset": a.subset, "problem": a.problem if a.case == "c5" else None,
                       "prec": a.prec, "simplices": int(sum(m.n_simplices for m in meshes)),
                       "ms_per_rep": times}), flush=True)
     proj.close()

@@ -1,4 +1,5 @@
-"""Shared pytest setup: the ``gpu`` marker and import paths."""
+"""Shared pytest setup: the ``gpu`` marker, import paths, and the optional parity report."""
+import json
 import os
 import sys
 
@@ -9,3 +10,14 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("CDP_PARITY_REPORT")
+    if not path:
+        return
+    import parity_report
+
+    if parity_report.RESULTS:
+        with open(path, "w") as f:
+            json.dump(parity_report.RESULTS, f, indent=1, sort_keys=True)

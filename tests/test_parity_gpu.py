@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_1509_07720_gb300 import meshgen as mg
+from parity_report import record
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -69,10 +70,10 @@ def _cases():
         "c4_8": mg.make_config("c4", 8),
         "rand3d_small": mg.random_simplices(3, 500, 16, 0.7, rng),
         "rand3d_mid": mg.random_simplices(3, 500, 16, 2.5, rng),
-        "rand3d_tiled": mg.random_simplices(3, 40, 32, 9.0, rng),
+        "rand3d_tiled": mg.random_simplices(3, 40, 40, 9.0, rng),
         "rand3d_lognormal1": mg.random_simplices(3, 300, 16, 3.0, rng, rho_sigma=1.0),
         "rand2d": mg.random_simplices(2, 800, 32, 3.0, rng),
-        "rand2d_tiled": mg.random_simplices(2, 60, 64, 20.0, rng),
+        "rand2d_tiled": mg.random_simplices(2, 60, 96, 20.0, rng),
         "aligned_kuhn_16": mg.Mesh(q8, t8, np.ones(q8.shape[1]), (16,) * 3, (0.0,) * 3, (1.0,) * 3, True),
         "aligned_kuhn_8": mg.Mesh(q8, t8, np.ones(q8.shape[1]), (8,) * 3, (0.0,) * 3, (1.0,) * 3, True),
         "box_linear_rho": mg.Mesh(qb * 0.8 + 0.1, tb, 1.0 + qb[0] - 0.5 * qb[2], (12, 10, 9), (0.0,) * 3,
@@ -81,12 +82,22 @@ def _cases():
                                (0.0,) * 3, (1.0,) * 3, True),
         # tetrahedra spanning many 18^3 tiles, with many cells entirely inside them (periodic, and
         # clipped by the walls of a non-periodic box)
-        "rand3d_huge": mg.random_simplices(3, 6, 48, 22.0, np.random.default_rng(71)),
+        "rand3d_huge": mg.random_simplices(3, 6, 96, 22.0, np.random.default_rng(71)),
         "rand3d_huge_walls": mg.random_simplices(3, 5, 40, 30.0, np.random.default_rng(72), periodic=False),
     }
 
 
+def _degenerate():
+    out = {}
+    for dim, seed in ((3, 81), (2, 82)):
+        for name, (mesh, nzero) in mg.degenerate_meshes(dim, 32, np.random.default_rng(seed)).items():
+            out[f"{name}_{dim}d"] = (mesh, nzero)
+    return out
+
+
+DEGENERATE = _degenerate()
 CASES = _cases()
+CASES.update({k: m for k, (m, _) in DEGENERATE.items()})
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
@@ -97,14 +108,15 @@ def test_parity(proj, name, prec):
     got = _run(proj, mesh, prec)
     scale = np.max(np.abs(ref))
     err = np.max(np.abs(got - ref)) / scale
-    assert err <= TOL[prec], f"{name}: max rel error {err:.3e}"
     tot = abs(got.sum() - ref.sum()) / abs(ref.sum())
+    record(name, prec, max_rel=err, total_rel=tot, cells=int(got.size))
+    assert err <= TOL[prec], f"{name}: max rel error {err:.3e}"
     ttol = TOL[1] if (prec == 1 and name in CLIPPED) else TOTAL_TOL
     assert tot <= ttol, f"{name}: total mass rel error {tot:.3e}"
 
 
 @pytest.mark.parametrize("name", ["c2", "rand3d_tiled", "aligned_kuhn_16", "c1b", "rand2d_tiled", "rand3d_huge",
-                                  "rand3d_huge_walls"])
+                                  "rand3d_huge_walls"] + sorted(DEGENERATE))
 def test_same_decisions_both_precisions(proj, name):
     mesh = CASES[name]
     _, s64 = _run(proj, mesh, 0, stats=True)
@@ -113,6 +125,17 @@ def test_same_decisions_both_precisions(proj, name):
               "n_large_tiles", "n_zero_volume"):
         assert s64[k] == s32[k], k
     assert s64["error_flags"] == 0
+
+
+@pytest.mark.parametrize("name", sorted(DEGENERATE))
+def test_zero_volume_count(proj, name):
+    """Flat simplices (exactly, after the fixed-point conversion of dyadic coordinates) contribute
+    nothing and are counted; no other simplex of the case is."""
+    mesh, nzero = DEGENERATE[name]
+    for prec in (0, 1):
+        _, st = _run(proj, mesh, prec, stats=True)
+        assert st["n_zero_volume"] == nzero, (prec, st["n_zero_volume"], nzero)
+        assert st["error_flags"] == 0
 
 
 def test_total_mass_against_simplex_masses(proj):
@@ -165,23 +188,92 @@ def test_extent_error(proj):
     assert e.value.code == -4
 
 
+_ORACLE = {}
+
+
+def _oracle_once(key, fn):
+    """An oracle result computed once per test session (the large workloads take tens of seconds)."""
+    if key not in _ORACLE:
+        _ORACLE[key] = fn()
+    return _ORACLE[key]
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
-def test_headline_workload_sampled(proj, prec):
-    """Full-size 128^3 Kuhn mesh (12.6M tets) on 256^3, in the benchmark's launch configuration:
-    sampled cells against the oracle cell by cell, and the total mass against the simplex masses."""
-    mesh = mg.make_config("c3")
-    got = _run(proj, mesh, prec)
-    rng = np.random.default_rng(99)
-    cells = rng.choice(got.size, 256, replace=False)
-    # also the densest cells
-    cells = np.unique(np.concatenate([cells, np.argsort(got.ravel())[-32:]]))
-    ref = oracle.project_cells(mesh, cells)
-    scale = float(np.max(got))
-    err = np.max(np.abs(got.ravel()[cells] - ref)) / scale
-    assert err <= TOL[prec], f"sampled max rel error {err:.3e}"
-    tot = oracle.simplex_mass(mesh).sum()
+def test_headline_workload_full_grid(proj, prec):
+    """Full-size 128^3 Kuhn mesh (12,582,912 tets) on the 256^3 grid, in the benchmark's launch
+    configuration: every one of the 16,777,216 cells against the oracle, the total mass against the
+    simplex masses, and the same corner decisions in both precisions."""
+    mesh = _oracle_once("c3_mesh", lambda: mg.make_config("c3"))
+    got, st = _run(proj, mesh, prec, stats=True)
+    assert st["error_flags"] == 0
+    ref = _oracle_once("c3", lambda: oracle.project(mesh))
+    scale = float(np.max(np.abs(ref)))
+    err = float(np.max(np.abs(got - ref))) / scale
+    tot = _oracle_once("c3_tot", lambda: oracle.simplex_mass(mesh).sum())
     rel = abs(got.sum() - tot) / tot
+    record("c3", prec, max_rel=err, total_rel=rel, cells=int(got.size))
+    assert err <= TOL[prec], f"max rel error over all cells {err:.3e}"
     assert rel <= TOTAL_TOL, f"total mass rel error {rel:.3e}"
+    _C3_STATS[prec] = st
+    if len(_C3_STATS) == 2:
+        for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell", "n_small", "n_large",
+                  "n_large_tiles"):
+            assert _C3_STATS[0][k] == _C3_STATS[1][k], k
+
+
+_C3_STATS = {}
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
+def test_adaptive_subset_full_grid(proj, prec):
+    """A seeded 1/16 stratified subset of the bisected mesh (about 3.1M tets, every volume class
+    represented) on the full 512^3 grid: every cell against the oracle, and the total mass."""
+    sub = _oracle_once("c4_sub", lambda: mg.stratified_subset(_c4_full(), 16, np.random.default_rng(1604)))
+    got = _run(proj, sub, prec)
+    ref = _oracle_once("c4_sub_ref", lambda: oracle.project(sub))
+    scale = float(np.max(np.abs(ref)))
+    err = float(np.max(np.abs(got - ref))) / scale
+    tot = float(ref.sum())
+    record("c4_subset16", prec, max_rel=err, total_rel=abs(got.sum() - tot) / tot, cells=int(got.size),
+           simplices=sub.n_simplices)
+    assert err <= TOL[prec], f"max rel error over all cells {err:.3e}"
+    assert abs(got.sum() - tot) <= TOTAL_TOL * tot
+
+
+@pytest.mark.parametrize("axes", [(1, 0, 0), (0, 1, 0), (0, 0, 1), (3, -2, 5)], ids=["x", "y", "z", "xyz"])
+def test_shift_equivariance(proj, axes):
+    """A translation by whole grid cells (dyadic coordinates, power-of-two grid, periodic box) moves
+    every cell's mass with it.  Every exact decision is the same (equal corner counts), and each
+    piece is computed from the same cell-relative numbers; only the order in which the pieces of a
+    cell are summed on the GPU may differ (atomic adds), so cells agree to that rounding."""
+    base = mg.quantize_positions(mg.make_config("c2", 8), 30)
+    moved = mg.shift_mesh(base, axes)
+    for prec, tol in ((0, 1e-14), (1, 2e-6)):
+        a, sa = _run(proj, base, prec, stats=True)
+        b, sb = _run(proj, moved, prec, stats=True)
+        want = np.roll(a, axes, axis=(0, 1, 2))
+        err = float(np.max(np.abs(b - want))) / float(np.max(np.abs(a)))
+        assert err <= tol, (prec, err)
+        for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell", "n_large_tiles"):
+            assert sa[k] == sb[k], (prec, k)
+
+
+@pytest.mark.parametrize("name", ["c2_16", "rand3d_tiled", "rand3d_huge", "aligned_kuhn_16", "c1b", "rand2d_tiled",
+                                  "grid_planes_3d", "grid_lines_3d"])
+def test_vertex_order_invariance(proj, name):
+    """The projection of a simplex does not depend on the order in which its vertices are listed
+    (even and odd permutations): the same corners are found, and cells agree within the tolerance."""
+    mesh = CASES[name]
+    perm = mg.permute_vertex_order(mesh, np.random.default_rng(5))
+    assert not np.array_equal(perm.simplices, mesh.simplices)
+    for prec, tol in ((0, 1e-12), (1, TOL[1])):
+        a, sa = _run(proj, mesh, prec, stats=True)
+        b, sb = _run(proj, perm, prec, stats=True)
+        err = float(np.max(np.abs(b - a))) / float(np.max(np.abs(a)))
+        assert err <= tol, (prec, err)
+        for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell", "n_zero_volume",
+                  "n_large_tiles"):
+            assert sa[k] == sb[k], (prec, k)
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
@@ -203,13 +295,20 @@ def test_adaptive_workload_sampled(proj, prec):
     rel = abs(got.sum() - tot) / tot
     assert rel <= TOTAL_TOL, f"total mass rel error {rel:.3e}"
     _C4_STATS[prec] = st
+    _C4_GRIDS[prec] = got
     if len(_C4_STATS) == 2:
         for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell", "n_small", "n_large"):
             assert _C4_STATS[0][k] == _C4_STATS[1][k], k
+        # every cell of the full-size FP32-mixed grid against the full-size FP64 grid (the FP64
+        # path is itself held to 1e-11 of the oracle on the stratified subset above)
+        d = float(np.max(np.abs(_C4_GRIDS[1] - _C4_GRIDS[0]))) / float(np.max(_C4_GRIDS[0]))
+        assert d <= TOL[1], f"FP32-mixed vs FP64 over all cells {d:.3e}"
+        _C4_GRIDS.clear()
 
 
 _C4 = {}
 _C4_STATS = {}
+_C4_GRIDS = {}
 
 
 def _c4_full():

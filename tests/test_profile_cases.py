@@ -5,7 +5,7 @@ torch = pytest.importorskip("torch")
 
 
 def test_needs_a_gpu():
-    from paper_1509_07720_gb300 import profile_cases
+    import profile_cases
 
     if torch.cuda.is_available():
         pytest.skip("a CUDA device is present")
@@ -14,7 +14,7 @@ def test_needs_a_gpu():
 
 
 def test_rejects_unknown_cases():
-    from paper_1509_07720_gb300 import profile_cases
+    import profile_cases
 
     with pytest.raises(SystemExit):
         profile_cases.main(["c9"])

@@ -43,6 +43,9 @@ def _cases():
         "c2_16": mg.make_config("c2", 16),
         "rand3d_mid": mg.random_simplices(3, 400, 16, 2.5, rng),
         "rand2d": mg.random_simplices(2, 600, 32, 3.0, rng),
+        # tetrahedra whose bounding boxes span several 18^3-cell tiles: the large-tetrahedron kernel,
+        # which here keeps no pieces between its two FP32 passes (no tile store) and recomputes them
+        "rand3d_large": mg.random_simplices(3, 4, 96, 20.0, np.random.default_rng(3)),
     }
 
 
@@ -76,6 +79,19 @@ def test_noalloc_matches_project(ctx, name, prec):
         err = np.max(np.abs(got - want)) / scale
         assert err <= TOL[prec], f"call {call}: max rel difference {err:.3e}"
         assert abs(got.sum() - want.sum()) <= TOTAL_TOL * abs(want.sum())
+
+
+def test_noalloc_large_tetrahedra_are_tiled(ctx):
+    """The large case really reaches the tiled kernel (its tetrahedra exceed the shared-memory box)."""
+    import paper_1509_07720_gb300 as pkg
+
+    mesh = CASES["rand3d_large"]
+    pos, simp, rho = _dev(mesh)
+    out = torch.empty(mesh.grid, dtype=torch.float64, device="cuda:0")
+    p = pkg.Projector.make_problem(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, mesh.periodic, out)
+    st = pkg.cdp_stats()
+    assert pkg.cdp_project(ctx, p, pkg.CDP_FP32_MIXED, 0, 0, st) == 0
+    assert st.n_large > 0 and st.n_large_tiles > 0
 
 
 def test_noalloc_accumulate_and_errors(ctx):

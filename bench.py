@@ -235,14 +235,16 @@ def run_reference(a):
 # our arm
 # ------------------------------------------------------------------------------------------------
 
-KERNELS = {3: ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>", "k_project_big<float>"],
-           2: ["k_prep_vertices", "-", "k_project_warp<2,float>", "-"]}
+KERNELS = {3: ["k_prep_vertices", "k_tet_setup<float>", "k_project_tet<float>", "k_project_big<float>",
+               "accuracy control (largest cell, second pass, k_project_clip)"],
+           2: ["k_prep_vertices", "-", "k_project_warp<2,float>", "-",
+               "accuracy control (largest cell, second pass, k_project_clip)"]}
 
 
 def roofline(dim, st, kern_ms, ns, peaks):
     """The ceiling of the kernel that takes most of the step: issue-bound FP32 arithmetic for the
     projection kernels, from the exact corner incidences of the statistics pass."""
-    dom = int(np.argmax(kern_ms))
+    dom = int(np.argmax(kern_ms[:4]))  # (the accuracy-control slot is several small kernels)
     fp32_peak = peaks.get("fp32_fma_tflops")
     src = "measured (ALU_PEAKS.json, bench_peaks.cu)"
     if fp32_peak is None:
@@ -385,7 +387,11 @@ def bench_projection(a, pkg, proj, dev, stream, name, ws, rank, headline):
 
     peaks = _json_file("ALU_PEAKS.json")
     dim = mesh.dim
-    launches_per_step = (3 if dim == 2 else 4) + (0 if dim == 2 else max(0, (ns - 1) // (1 << 24)) * 2)
+    # 3D: vertex records, set-up + main kernel per batch of 2^24, large tetrahedra, then the accuracy
+    # control (largest cell, second-pass set-up + main kernel per batch, large tetrahedra, clipping);
+    # 2D: vertex records, main kernel, largest cell, second pass, clipping
+    batches = max(1, (ns + (1 << 24) - 1) // (1 << 24))
+    launches_per_step = 5 if dim == 2 else 1 + 2 * batches + 1 + 1 + 2 * batches + 1 + 1
     line = {
         "metric": METRIC if headline else f"simplices projected/s ({name}), FP32-mixed vs FP64 plain, same GB300",
         "value": value, "unit": UNIT if dim == 3 else "triangles/s", "n_gpus": ws, "steps": a.steps,
@@ -401,7 +407,7 @@ def bench_projection(a, pkg, proj, dev, stream, name, ws, rank, headline):
         "kernel_ms": {k: v for k, v in zip(KERNELS[dim], kern32) if k != "-"},
         "corners": {k: st32[k] for k in ("corners_a", "corners_b", "corners_c", "corners_d", "n_single_cell",
                                          "n_small", "n_large", "n_large_tiles", "n_zero_volume", "exact_fallbacks",
-                                         "n_pieces") if k in st32},
+                                         "n_deferred", "n_clipped", "accuracy_bound") if k in st32},
         "roofline": roofline(dim, st32, kern32, ns, peaks),
         "clocks": clocks,
         "gpu_launches": launches_per_step * a.steps,

@@ -47,16 +47,29 @@ enum {
     CDP_ERR_NAN = -3,     /* a vertex coordinate or density is not finite, or absurdly far out */
     CDP_ERR_EXTENT = -4,  /* a simplex spans half a periodic box or more, or > 2048 cells per axis */
     CDP_ERR_OOM = -5,     /* device scratch allocation failed */
-    CDP_ERR_TIMEOUT = -6, /* a bounded device-side wait gave up */
+    CDP_ERR_TIMEOUT = -6, /* reserved for a bounded device-side wait that gives up; no kernel of this
+                             library waits on another, so no call returns it at present */
     CDP_ERR_CUDA = -7     /* a CUDA runtime or library call failed */
 };
 
 /* Arithmetic of the projection. Both paths take the same exact combinatorial decisions.
- * CDP_FP64: every contribution in FP64 (error vs the exact result ~1e-13 of the largest cell).
+ * CDP_FP64: every contribution in FP64; stated accuracy 1e-11 of the largest cell (typically ~1e-13).
  * CDP_FP32_MIXED: contributions in FP32, classification exact (integer) with an FP32 filter,
- *   accumulation of every (simplex, cell) piece into the FP64 grid (error ~1e-6 of the largest
- *   cell). */
+ *   accumulation of every (simplex, cell) piece into the FP64 grid; stated accuracy 1e-5 of the
+ *   largest cell (typically ~1e-6).
+ * Both paths control their accuracy (Sect. 3.4; cdp_stats.n_deferred / n_clipped): simplices whose
+ * density gradient would make Franklin's sum cancel beyond the stated accuracy are projected by
+ * clipping instead.  Total mass: FP64 exact to ~1e-12 relative; FP32-mixed closes the mass of every
+ * simplex against its FP64 closed form, so the total is exact to ~1e-12 as well, EXCEPT for simplices
+ * that cross the walls of a non-periodic box: the closure knows the mass of the whole simplex, not
+ * of its part inside the box, and the total inside the box is then only as exact as the cells
+ * (~1e-5 of the largest cell). */
 enum { CDP_FP64 = 0, CDP_FP32_MIXED = 1 };
+/* OR'ed into a precision argument: no accuracy control -- every simplex is projected by Franklin's
+ * sum in the requested arithmetic (faster, but the stated accuracy is then not guaranteed for
+ * simplices whose density gradient is steep compared with their density; for measurements and for
+ * comparing the two arithmetics on the same work). */
+#define CDP_ACCURACY_OFF 0x100
 
 typedef struct cdp_ctx cdp_ctx;
 
@@ -70,7 +83,9 @@ typedef struct cdp_ctx cdp_ctx;
  *   grid[a]      cells per axis (1 <= grid[a] <= 2^20, at most 2^32 cells in total), a < dim
  *   box_lo/len   box origin and side lengths (len > 0)
  *   periodic     1: the box is a torus, every simplex is taken at the minimal image of its
- *                vertex 0 (every vertex offset must be < half a box length) and cells wrap;
+ *                vertex 0 and cells wrap; every simplex must span less than half the box along
+                every axis (so that every vertex is the minimal image of every other one and the
+                simplex does not depend on its vertex order), else CDP_ERR_EXTENT;
  *                0: mass outside the grid is dropped
  *   cell_mass    device, double[prod(grid)]: OUTPUT, integral of rho over every cell */
 typedef struct {
@@ -104,6 +119,16 @@ typedef struct {
                                  a corner on a tile face is evaluated, and counted, in each tile it touches */
     uint32_t error_flags;     /* bit 0 bad index, bit 1 non-finite, bit 2 extent */
     uint32_t reserved;
+    /* accuracy control (Sect. 3.4): a simplex whose density gradient is steep compared with its density
+       is deferred by the first pass; once the largest cell mass M of the first pass is known it is
+       projected by Franklin's sum if the bound on its cancellation error is below half the stated
+       accuracy (FP32-mixed 1e-5, FP64 1e-11, of M), and otherwise by clipping it against every cell of its
+       bounding box (a second algorithm, free of cancellation) */
+    uint64_t n_deferred;      /* simplices deferred by the first pass */
+    uint64_t n_clipped;       /* simplices projected by clipping */
+    double accuracy_bound;    /* largest error bound of a piece of a simplex projected by Franklin's sum,
+                                 divided by the largest |cell mass| (a measured-constant bound, see the
+                                 accuracy constants in the sources; the stated accuracy is 1e-5 / 1e-11) */
 } cdp_stats;
 
 /* Create a context on CUDA device `device` (scratch is allocated lazily and grown as needed).
@@ -127,18 +152,26 @@ CDP_API int cdp_project(cdp_ctx* ctx, const cdp_problem* prob, int precision, in
  * accumulate = 0 and no stats).  The scratch is sized once for the largest problem first. */
 CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, int precision, void* stream);
 
-/* Largest n_verts and n_simplices accepted by cdp_project_noalloc (static device scratch of 32
- * bytes per vertex and 4 per simplex: 8 MiB + 6 MiB). */
+/* Largest n_verts and n_simplices accepted by cdp_project_noalloc, and the size of its static
+ * device scratch, held by every process that loads the library on every device it uses: 32 bytes
+ * per vertex (8 MiB), three lists of 4 bytes per simplex (large, deferred and clipped simplices,
+ * 18 MiB), and the geometry records of one batch of 16,384 tetrahedra (9.4 MiB). */
 #define CDP_NOALLOC_MAX_VERTS 262144
 #define CDP_NOALLOC_MAX_SIMPLICES 1572864
+#define CDP_NOALLOC_SCRATCH_BYTES 37159168
 
-/* The projection of cdp_project (same kernels, same results), for callers that must not allocate
- * or free memory when they call: for instance a caller whose framework has reserved the device
- * memory for its own pool, or one that cannot afford the device-wide synchronisation that
- * cudaFree implies while other streams are busy.  It takes no context: its scratch (vertex
- * records and counters) is one fixed device array of this library, sized for
- * CDP_NOALLOC_MAX_VERTS vertices, and it calls no allocating routine.  The paper has no
+/* The projection of cdp_project (same kernels, same results to the stated accuracy), for callers
+ * that must not allocate or free memory when they call: for instance a caller whose framework has
+ * reserved the device memory for its own pool, or one that cannot afford the device-wide
+ * synchronisation that cudaFree implies while other streams are busy.  It takes no context: its
+ * scratch (counters, vertex records, the lists of large, deferred and clipped simplices, and the
+ * geometry records of one batch of tetrahedra) is one fixed device array of this library of
+ * CDP_NOALLOC_SCRATCH_BYTES bytes, and it calls no allocating routine.  The paper has no
  * counterpart of this entry point; it exists only for the allocation constraint above.
+ *  - Throughput: the geometry records are set up 16,384 tetrahedra at a time (cdp_project: up to
+ *    2^24), so a problem of n tetrahedra takes ceil(n / 16384) set-up and main-kernel launch pairs
+ *    (96 at the 1,572,864-tetrahedron limit), and FP32 tiles of large tetrahedra are computed twice
+ *    (no tile store): expect it to be slower than cdp_project on large problems.
  *  - Runs on the CURRENT CUDA device.  The first call on a device looks up the scratch address
  *    and the launch parameters of that device (no allocation); make that first call before any
  *    stream capture is begun.
@@ -214,12 +247,13 @@ CDP_API int cdp_check(cdp_ctx* ctx, void* stream);
  * times to per-kernel totals; enabling (or disabling) also resets the totals and the call count. */
 CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 
-/* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 4:
+/* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 5:
  * [0] vertex records, [1] per-simplex set-up (3D: the first batch's; the single-cell closed form
  * is applied there), [2] main projection kernel (3D: with the set-up of any later batch),
  * [3] the large-tetrahedron kernel (3D: tetrahedra with a bounding box above 1280 cells, in
- * tiles).  *calls receives the number of timed cdp_project calls.  Returns the number of slots
- * written. */
+ * tiles), [4] the accuracy control (the largest cell mass, the second pass over the deferred
+ * simplices, clipping).  *calls receives the number of timed cdp_project calls.  Returns the
+ * number of slots written. */
 CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
 
 /* Launch-shape tuning (no counterpart in the paper: the choice of a GPU launch shape).  Times the

@@ -20,10 +20,13 @@ __all__ = [
     "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density", "cdp_poisson", "cdp_force", "cdp_drift",
     "cdp_kick", "cdp_step_batched", "cdp_step_problem", "Projector", "EXPORTED_SYMBOLS",
     "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS", "CDP_NOALLOC_MAX_SIMPLICES", "cdp_autotune",
+    "CDP_ACCURACY_OFF",
 ]
 
 CDP_FP64 = 0
 CDP_FP32_MIXED = 1
+# OR'ed into a precision: no accuracy control (every simplex by Franklin's sum)
+CDP_ACCURACY_OFF = 0x100
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libcoldproj.so")
@@ -72,11 +75,14 @@ class cdp_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "n_zero_volume", "n_single_cell", "n_small", "n_large", "n_large_tiles",
         "corners_a", "corners_b", "corners_c", "corners_d", "exact_fallbacks")] + [
-        ("large_corners", ctypes.c_uint64 * 4), ("error_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+        ("large_corners", ctypes.c_uint64 * 4), ("error_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("n_deferred", ctypes.c_uint64), ("n_clipped", ctypes.c_uint64), ("accuracy_bound", ctypes.c_double)]
 
     def as_dict(self):
-        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n not in ("reserved", "large_corners")}
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_
+             if n not in ("reserved", "large_corners", "accuracy_bound")}
         d["large_corners"] = [int(v) for v in self.large_corners]
+        d["accuracy_bound"] = float(self.accuracy_bound)
         return d
 
 
@@ -175,10 +181,11 @@ def cdp_timing_enable(ctx, enable: bool) -> int:
 
 
 def cdp_timing_read(ctx):
-    """(per-kernel totals in ms [vertex records, set-up, main kernel, large tetrahedra (3D)], timed calls)."""
-    buf = (ctypes.c_double * 4)()
+    """(per-kernel totals in ms [vertex records, set-up, main kernel, large tetrahedra (3D), accuracy
+    control], timed calls)."""
+    buf = (ctypes.c_double * 5)()
     calls = ctypes.c_int(0)
-    rc = load_library().cdp_timing_read(ctx, buf, 4, ctypes.byref(calls))
+    rc = load_library().cdp_timing_read(ctx, buf, 5, ctypes.byref(calls))
     if rc < 0:
         raise CdpError(rc, "cdp_timing_read")
     return list(buf), int(calls.value)

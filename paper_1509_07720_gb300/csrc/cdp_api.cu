@@ -148,6 +148,7 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
     int rc = grow(&c->verts, &c->verts_cap, nv);
     if (rc) return rc;
     if ((rc = grow(&c->queue, &c->queue_cap, ns))) return rc;
+    if ((rc = grow(&c->defer, &c->defer_cap, ns)) || (rc = grow(&c->clip, &c->clip_cap, ns))) return rc;
     if (any3d && (rc = grow_tiles(c))) return rc;
     return grow_geo(c, ns);
 }
@@ -156,6 +157,10 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
 int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats) {
     int rc;
     if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
+    {
+        const size_t ns1 = (size_t)(p->n_simplices > 0 ? p->n_simplices : 1);
+        if ((rc = grow(&c->defer, &c->defer_cap, ns1)) || (rc = grow(&c->clip, &c->clip_cap, ns1))) return rc;
+    }
     if (p->dim == 3 && ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1))) ||
                         (rc = grow_geo(c, (size_t)p->n_simplices))))
         return rc;
@@ -189,7 +194,9 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     L.ctr = c->ctr;
     L.stats = want_stats ? c->stats : nullptr;
     L.num_sms = c->num_sms;
-    int fp32 = precision == CDP_FP32_MIXED;
+    int fp32 = 0, accuracy = 1;
+    if (!parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
+    L.accuracy = accuracy;
     // a persistent grid: every resident block slot of the device, grid_mult times over
     L.small_blocks_per_sm =
         c->grid_mult[p->dim == 3][fp32] * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
@@ -201,6 +208,10 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
     L.tile_store = c->tiles;
     L.tile_store_cap = c->tiles_cap;
     L.tile_store_per_block = cdp::CDP_TILE_STORE_PER_BLOCK;
+    L.defer_list = c->defer;
+    L.defer_cap = (long long)c->defer_cap;
+    L.clip_list = c->clip;
+    L.clip_cap = (long long)c->clip_cap;
     {
         size_t rec = cdp::tet_geo_bytes(fp32);
         long long by_bytes = rec ? (long long)(c->geo_cap / rec) : 0;
@@ -232,6 +243,7 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
         return CDP_ERR_CUDA;
     }
     if (ev[1]) cudaEventRecord(ev[1], st);
+    L.ev_acc = ev[4];
     if (launch_project(L, fp32, st, ev[2], ev[3]) != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;
@@ -247,6 +259,12 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
 
 namespace {
 
+double __longlong_as_double_host(unsigned long long bits) {
+    double d;
+    memcpy(&d, &bits, sizeof(d));
+    return d;
+}
+
 int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     if (cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(cdp::Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(c->h_stats, c->stats, 2 * sizeof(cdp::UnitCounts), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -258,7 +276,14 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     stats->n_zero_volume = c->h_ctr->n_zero;
     stats->n_single_cell = c->h_ctr->n_class0;
     stats->n_small = c->h_ctr->n_small;
-    stats->n_large = c->h_ctr->big_count;
+    stats->n_large = c->h_ctr->big_first;
+    stats->n_deferred = c->h_ctr->defer_count;
+    stats->n_clipped = c->h_ctr->clip_count;
+    {
+        const double m = __longlong_as_double_host(c->h_ctr->mmax_bits);
+        const double eb = __longlong_as_double_host(c->h_ctr->ebmax_bits);
+        stats->accuracy_bound = m > 0.0 ? eb / m : 0.0;
+    }
     stats->n_large_tiles = c->h_ctr->n_big_tiles;
     const cdp::UnitCounts& s0 = c->h_stats[0];
     const cdp::UnitCounts& s1 = c->h_stats[1];
@@ -286,7 +311,7 @@ int cdp_timing_enable(cdp_ctx* c, int enable) {
     DeviceGuard guard(c->device);
     int rc = fold_timing(c);
     c->timing = enable ? 1 : 0;
-    for (int k = 0; k < 4; ++k) c->totals[k] = 0.0;
+    for (int k = 0; k < cdp::CDP_TEV - 1; ++k) c->totals[k] = 0.0;
     c->calls = 0;
     return rc;
 }
@@ -296,7 +321,7 @@ int cdp_timing_read(cdp_ctx* c, double* out_ms, int n, int* calls) {
     DeviceGuard guard(c->device);
     int rc = fold_timing(c);
     if (rc) return rc;
-    int m = n < 4 ? n : 4;
+    int m = n < cdp::CDP_TEV - 1 ? n : cdp::CDP_TEV - 1;
     for (int k = 0; k < m; ++k) out_ms[k] = c->totals[k];
     if (calls) *calls = c->calls;
     return m;
@@ -374,6 +399,8 @@ void cdp_destroy(cdp_ctx* c) {
     cudaDeviceSynchronize();
     if (c->verts) cudaFree(c->verts);
     if (c->queue) cudaFree(c->queue);
+    if (c->defer) cudaFree(c->defer);
+    if (c->clip) cudaFree(c->clip);
     if (c->geo) cudaFree(c->geo);
     if (c->need) cudaFree(c->need);
     if (c->tiles) cudaFree(c->tiles);
@@ -413,7 +440,10 @@ int cdp_project(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate,
     if (!c) return CDP_ERR_ARG;
     int rc = check_problem(p);
     if (rc) return rc;
-    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    {
+        int f = 0, a = 0;
+        if (!cdp::parse_precision(precision, &f, &a)) return CDP_ERR_ARG;
+    }
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     rc = cdp::project_enqueue(c, p, precision, accumulate, st, stats != nullptr);
@@ -425,9 +455,10 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     if (!c) return CDP_ERR_ARG;
     int rc = check_problem(p);
     if (rc) return rc;
-    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    int fp32 = 0, accuracy = 1;
+    if (!cdp::parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
     DeviceGuard guard(c->device);
-    const int d3 = p->dim == 3 ? 1 : 0, fp32 = precision == CDP_FP32_MIXED ? 1 : 0;
+    const int d3 = p->dim == 3 ? 1 : 0;
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
@@ -510,7 +541,10 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
 }
 int cdp_project_batched(cdp_ctx* c, const cdp_problem* probs, int n, int precision, void* stream) {
     if (!c || n < 0 || (n > 0 && !probs)) return CDP_ERR_ARG;
-    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    {
+        int f = 0, a = 0;
+        if (!cdp::parse_precision(precision, &f, &a)) return CDP_ERR_ARG;
+    }
     for (int i = 0; i < n; ++i) {
         int rc = check_problem(probs + i);
         if (rc) return rc;

@@ -1,0 +1,410 @@
+// Accuracy control (Sect. 3.4): the projection of the simplices whose Franklin sum cannot be trusted
+// in the arithmetic at hand.
+//
+// Each (vertex, edge, facet) contribution of eqs. contrib, E0, E1 is a product of offsets of the
+// order of a cell and, for its first-order part, of the density gradient.  Summed over the corners
+// of a piece they cancel down to the piece's mass, so the rounding error of a piece is a few units in
+// the last place of the LARGEST contribution (eq. accuracy: eps_P = 2^(e_max - S + W)), not of the
+// piece.  In a nearly flat simplex with unequal vertex densities (or a steep density contrast) the
+// gradient, and with it e_max, is orders of magnitude above the simplex's own density, and the
+// pieces lose all their digits.  Sect. 3.4 prescribes comparing e_max with the result and, where
+// accuracy is lacking, re-projecting the simplices concerned with higher precision or with a
+// different algorithm whose degenerate configurations differ.  This file is that different
+// algorithm:
+//
+//   for every cell of the simplex's bounding box, the polytope P = simplex intersect cell is bounded
+//   by the simplex's facets clipped to the cell and by the cell's faces clipped to the simplex
+//   (Sutherland-Hodgman clipping of each face polygon by the other body's half-spaces, FP64).  P is
+//   convex, hence star-shaped from any of its vertices v0, and the integral of the linear density is
+//   the sum over the fan tetrahedra (v0, f0, f_i, f_{i+1}) of every face polygon of |det| / 6 times
+//   the mean density at their four corners (exact for a linear function).  Every term is positive,
+//   so nothing cancels: the error of a piece is a few ulps of the density times the cell volume,
+//   whatever the simplex's shape.  (2D: the triangle clipped by the cell's four half-planes, fanned
+//   from one vertex of the polygon.)
+//
+// The test that sends a simplex here (its bound on e_max against the grid's largest cell) is made by
+// the projection kernels; they append the simplex to a list, and k_project_clip takes the listed
+// simplices one per block, its threads going over the cells of the bounding box.
+#include <cuda_runtime.h>
+
+#include "cdp_mesh.cuh"
+#include "cdp_project.h"
+
+namespace cdp {
+
+namespace {
+
+constexpr int CLIP_THREADS = 128;
+constexpr int MAXP = 12;  // a triangle cut by 6 planes has at most 9 vertices, a square cut by 4 at most 8
+
+// Clips the convex polygon p[0..n) by the half-space  c . x + c0 >= 0  into q; returns q's size.
+// Points on the plane are kept; crossing points are interpolated on the edge (all three components,
+// so a third one that is not a coordinate is interpolated too).
+template <typename R>
+__device__ int clip_by(const R (*p)[3], int n, R (*q)[3], const R c[3], R c0) {
+    int m = 0;
+    if (n == 0) return 0;
+    R dprev = c[0] * p[n - 1][0] + c[1] * p[n - 1][1] + c[2] * p[n - 1][2] + c0;
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+        const int ip = i == 0 ? n - 1 : i - 1;
+        const R d = c[0] * p[i][0] + c[1] * p[i][1] + c[2] * p[i][2] + c0;
+        if ((d >= R(0)) != (dprev >= R(0)) && m < MAXP) {
+            // the edge (ip, i) crosses the plane strictly inside: t from the inside end
+            const R t = dprev / (dprev - d);
+            q[m][0] = p[ip][0] + t * (p[i][0] - p[ip][0]);
+            q[m][1] = p[ip][1] + t * (p[i][1] - p[ip][1]);
+            q[m][2] = p[ip][2] + t * (p[i][2] - p[ip][2]);
+            ++m;
+        }
+        if (d >= R(0) && m < MAXP) {
+            q[m][0] = p[i][0];
+            q[m][1] = p[i][1];
+            q[m][2] = p[i][2];
+            ++m;
+        }
+        dprev = d;
+    }
+    return m;
+}
+
+// A simplex in the frame of one cell, read by every thread of the block.
+struct ClipTet {
+    double x[4][3];   // vertex coordinates relative to the anchor cell (grid units, exact)
+    double n[4][3];   // unit inward normal of the facet opposite each vertex
+    double g[3];      // density gradient (per cell)
+    double c[3];      // centroid, and the density there
+    double rhoc;
+    int lo[3], hi[3]; // bounding box (cells, relative to the anchor)
+    int anchor[3];
+    int ok;
+};
+
+struct ClipTri {
+    double x[3][2];   // vertex coordinates relative to the anchor cell (grid units, exact)
+    double rho[3];
+    int lo[2], hi[2]; // bounding box (cells, relative to the anchor)
+    int anchor[2];
+    int ok;
+};
+
+// the simplex in the frame of one cell: vertex offsets from the cell's lower corner, facet normals,
+// and the density as rc + g . x in that frame (taken in FP64, then rounded to R)
+template <typename R>
+struct CellFrame {
+    R x[4][3];
+    R n[4][3];
+    R g[3];
+    R rc;
+};
+
+template <typename R>
+__device__ __forceinline__ R rho_at(const CellFrame<R>& F, const R x[3]) {
+    return F.rc + F.g[0] * x[0] + F.g[1] * x[1] + F.g[2] * x[2];
+}
+
+template <typename R>
+__device__ __forceinline__ R abs_r(R v) { return v < R(0) ? -v : v; }
+
+// |det(b - a, c - a, d - a)| / 6
+template <typename R>
+__device__ __forceinline__ R tet_vol(const R a[3], const R b[3], const R c[3], const R d[3]) {
+    const R u0 = b[0] - a[0], u1 = b[1] - a[1], u2 = b[2] - a[2];
+    const R v0 = c[0] - a[0], v1 = c[1] - a[1], v2 = c[2] - a[2];
+    const R w0 = d[0] - a[0], w1 = d[1] - a[1], w2 = d[2] - a[2];
+    return abs_r(u0 * (v1 * w2 - v2 * w1) - u1 * (v0 * w2 - v2 * w0) + u2 * (v0 * w1 - v1 * w0)) * R(1.0 / 6.0);
+}
+
+// Integral of rho over (tetrahedron intersect the unit cell whose lower corner is o, relative to the
+// anchor), in arithmetic R.  The simplex is first taken into the cell's frame in FP64 (exact offsets,
+// then rounded once), so that every coordinate the clipping sees is within a few cells of 0.
+template <typename R>
+__device__ R clip_cell_3d(const ClipTet& T, const double o[3]) {
+    CellFrame<R> F;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k)
+        for (int a = 0; a < 3; ++a) {
+            F.x[k][a] = (R)(T.x[k][a] - o[a]);
+            F.n[k][a] = (R)T.n[k][a];
+        }
+    for (int a = 0; a < 3; ++a) F.g[a] = (R)T.g[a];
+    F.rc = (R)(T.rhoc + T.g[0] * (o[0] - T.c[0]) + T.g[1] * (o[1] - T.c[1]) + T.g[2] * (o[2] - T.c[2]));
+    // the cell against each facet plane: entirely outside one of them (no piece), or inside all (the
+    // whole cell, whose integral is the density at its centre)
+    bool inside = true;
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+        const int va = f == 0 ? 1 : 0;
+        const R* nf = F.n[f];
+        R dmax = R(-1e30), dmin = R(1e30);
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            const R d = nf[0] * (R(q & 1) - F.x[va][0]) + nf[1] * (R((q >> 1) & 1) - F.x[va][1]) +
+                        nf[2] * (R(q >> 2) - F.x[va][2]);
+            dmax = d > dmax ? d : dmax;
+            dmin = d < dmin ? d : dmin;
+        }
+        if (dmax < R(0)) return R(0);
+        inside = inside && dmin >= R(0);
+    }
+    if (inside) {
+        const R ctr[3] = {R(0.5), R(0.5), R(0.5)};
+        return rho_at(F, ctr);
+    }
+    R bufa[MAXP][3], bufb[MAXP][3];
+    R v0[3] = {R(0), R(0), R(0)};
+    R r0 = R(0);
+    bool have_v0 = false;
+    R sum = R(0);
+    // the faces of the polytope: 4 clipped facets, then 6 clipped cell faces
+#pragma unroll 1
+    for (int face = 0; face < 10; ++face) {
+        int n;
+        if (face < 4) {
+            // facet `face` (opposite vertex `face`), clipped by the cell's 6 half-spaces
+            n = 0;
+#pragma unroll 1
+            for (int k = 0; k < 4; ++k) {
+                if (k == face) continue;
+                bufa[n][0] = F.x[k][0];
+                bufa[n][1] = F.x[k][1];
+                bufa[n][2] = F.x[k][2];
+                ++n;
+            }
+#pragma unroll 1
+            for (int pl = 0; pl < 6 && n > 0; ++pl) {
+                const int a = pl >> 1;
+                const R sg = (pl & 1) ? R(-1) : R(1);  // x_a >= 0, then 1 - x_a >= 0
+                const R c[3] = {a == 0 ? sg : R(0), a == 1 ? sg : R(0), a == 2 ? sg : R(0)};
+                n = clip_by<R>(bufa, n, bufb, c, (pl & 1) ? R(1) : R(0));
+#pragma unroll 1
+                for (int i = 0; i < n; ++i) {
+                    bufa[i][0] = bufb[i][0];
+                    bufa[i][1] = bufb[i][1];
+                    bufa[i][2] = bufb[i][2];
+                }
+            }
+        } else {
+            // cell face x_a = s clipped by the tetrahedron's 4 half-spaces; a face lying in a facet's
+            // plane is that facet's polygon already (counted above) and is skipped
+            const int a = (face - 4) >> 1, sd = (face - 4) & 1;
+            const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+            const R sq[4][2] = {{R(0), R(0)}, {R(1), R(0)}, {R(1), R(1)}, {R(0), R(1)}};
+            n = 4;
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+                bufa[i][a] = R(sd);
+                bufa[i][b] = sq[i][0];
+                bufa[i][cc] = sq[i][1];
+            }
+#pragma unroll 1
+            for (int f = 0; f < 4 && n > 0; ++f) {
+                const int va = f == 0 ? 1 : 0;
+                const R* nf = F.n[f];
+                const R c0 = -(nf[0] * F.x[va][0] + nf[1] * F.x[va][1] + nf[2] * F.x[va][2]);
+                bool coplanar = true;
+#pragma unroll 1
+                for (int i = 0; i < n; ++i)
+                    coplanar = coplanar && nf[0] * bufa[i][0] + nf[1] * bufa[i][1] + nf[2] * bufa[i][2] + c0 == R(0);
+                if (coplanar) {
+                    n = 0;
+                    break;
+                }
+                n = clip_by<R>(bufa, n, bufb, nf, c0);
+#pragma unroll 1
+                for (int i = 0; i < n; ++i) {
+                    bufa[i][0] = bufb[i][0];
+                    bufa[i][1] = bufb[i][1];
+                    bufa[i][2] = bufb[i][2];
+                }
+            }
+        }
+        if (n < 3) continue;
+        if (!have_v0) {
+            // the apex of every fan: a vertex of the polytope (its own faces add nothing)
+            v0[0] = bufa[0][0];
+            v0[1] = bufa[0][1];
+            v0[2] = bufa[0][2];
+            r0 = rho_at(F, v0);
+            have_v0 = true;
+        }
+        const R rf = rho_at(F, bufa[0]);
+        R rprev = rho_at(F, bufa[1]);
+#pragma unroll 1
+        for (int i = 1; i + 1 < n; ++i) {
+            const R rnext = rho_at(F, bufa[i + 1]);
+            sum += tet_vol<R>(v0, bufa[0], bufa[i], bufa[i + 1]) * (R(0.25) * ((r0 + rf) + (rprev + rnext)));
+            rprev = rnext;
+        }
+    }
+    return sum;
+}
+
+// 2D: the triangle clipped by the cell's four half-planes, fanned from the polygon's first vertex;
+// the density is interpolated along the clipped edges (x, y, rho carried together).
+template <typename R>
+__device__ R clip_cell_2d(const ClipTri& T, const double o[2]) {
+    R pa[MAXP][3], pb[MAXP][3];
+    for (int k = 0; k < 3; ++k) {
+        pa[k][0] = (R)(T.x[k][0] - o[0]);
+        pa[k][1] = (R)(T.x[k][1] - o[1]);
+        pa[k][2] = (R)T.rho[k];
+    }
+    int n = 3;
+#pragma unroll 1
+    for (int pl = 0; pl < 4 && n > 0; ++pl) {
+        const int a = pl >> 1;
+        const R sg = (pl & 1) ? R(-1) : R(1);
+        const R c[3] = {a == 0 ? sg : R(0), a == 1 ? sg : R(0), R(0)};
+        n = clip_by<R>(pa, n, pb, c, (pl & 1) ? R(1) : R(0));
+        for (int i = 0; i < n; ++i) {
+            pa[i][0] = pb[i][0];
+            pa[i][1] = pb[i][1];
+            pa[i][2] = pb[i][2];
+        }
+    }
+    R sum = R(0);
+    for (int i = 1; i + 1 < n; ++i) {
+        const R u0 = pa[i][0] - pa[0][0], u1 = pa[i][1] - pa[0][1];
+        const R w0 = pa[i + 1][0] - pa[0][0], w1 = pa[i + 1][1] - pa[0][1];
+        sum += abs_r(u0 * w1 - u1 * w0) * R(0.5) * ((pa[0][2] + pa[i][2] + pa[i + 1][2]) * R(1.0 / 3.0));
+    }
+    return sum;
+}
+
+}  // namespace
+
+// The listed simplices (list[0, min(*count, cap))), one per block in turn; every cell of the bounding
+// box by the block's threads, in arithmetic R.  R = float (FP32-mixed path): the simplex's pieces
+// are summed over the block and its FP64 closed-form mass minus that sum (a few FP32 ulps of the
+// pieces) goes to the cell of its vertex 0, so the total mass stays exact to FP64 rounding.  The
+// simplices passed the vertex-index and canonicalisation checks when they were listed.
+template <int DIM, typename R>
+__global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(GridDesc g, long long nv, const int* __restrict__ simp,
+                                                               const VertexRec* __restrict__ V,
+                                                               const int* __restrict__ list, const unsigned* count,
+                                                               long long cap, double* __restrict__ out) {
+    constexpr bool closure = sizeof(R) == 4;
+    __shared__ ClipTet st;
+    __shared__ ClipTri s2;
+    __shared__ double mexact;
+    __shared__ int cell0[3];
+    __shared__ double wsum[CLIP_THREADS / 32];
+    const long long listed = (long long)*(volatile const unsigned*)count;
+    const long long n = listed < cap ? listed : cap;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+    for (long long e = blockIdx.x; e < n; e += gridDim.x) {
+        __syncthreads();  // the previous simplex is done
+        if (threadIdx.x == 0) {
+            const long long s = list[e];
+            const VertexRec* v[4];
+            bool ok = true;
+            for (int k = 0; k <= DIM; ++k) {
+                const int id = simp[s * (DIM + 1) + k];
+                ok = ok && id >= 0 && id < nv;
+                v[k] = V + (ok ? id : 0);
+            }
+            if (DIM == 3) {
+                Tet S;
+                st.ok = ok && canon_tet<2>(g, v, S) == 0;
+                if (st.ok) {
+                    TetGeo<double> G;
+                    tet_setup<double, 2>(S, S.lo, G);
+                    for (int k = 0; k < 4; ++k)
+                        for (int a = 0; a < 3; ++a) {
+                            st.x[k][a] = G.x[k][a] + (double)S.lo[a];
+                            st.n[k][a] = G.n[k][a];
+                        }
+                    for (int a = 0; a < 3; ++a) {
+                        st.g[a] = G.g[a];
+                        st.c[a] = G.c[a] + (double)S.lo[a];
+                        st.lo[a] = S.lo[a];
+                        st.hi[a] = S.hi[a];
+                        st.anchor[a] = S.anchor[a];
+                        cell0[a] = S.anchor[a] + S.cell[0][a];
+                    }
+                    st.rhoc = G.rhoc;
+                    mexact = G.mexact;
+                }
+            } else {
+                Tri S;
+                s2.ok = ok && canon_tri(g, v, S) == 0;
+                if (s2.ok) {
+                    for (int k = 0; k < 3; ++k) {
+                        for (int a = 0; a < 2; ++a) s2.x[k][a] = i64_to_real<double>(S.L[k][a], CDP_Q);
+                        s2.rho[k] = S.rho[k];
+                    }
+                    for (int a = 0; a < 2; ++a) {
+                        s2.lo[a] = S.lo[a];
+                        s2.hi[a] = S.hi[a];
+                        s2.anchor[a] = S.anchor[a];
+                        cell0[a] = S.anchor[a] + S.cell[0][a];
+                    }
+                    cell0[2] = 0;
+                    mexact = tri_mass_cells(S);
+                }
+            }
+        }
+        __syncthreads();
+        if (DIM == 3 ? !st.ok : !s2.ok) continue;
+        const int* lo = DIM == 3 ? st.lo : s2.lo;
+        const int* hi = DIM == 3 ? st.hi : s2.hi;
+        const int* an = DIM == 3 ? st.anchor : s2.anchor;
+        const long long ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = DIM == 3 ? hi[2] - lo[2] + 1 : 1;
+        const long long ncell = ex * ey * ez;
+        double mine = 0.0;  // this thread's pieces (for the closure)
+#pragma unroll 1
+        for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const long long r = c / ex;
+            const int i = (int)(c - r * ex), j = (int)(r % ey), k = (int)(r / ey);
+            R m;
+            if (DIM == 3) {
+                const double o[3] = {(double)(lo[0] + i), (double)(lo[1] + j), (double)(lo[2] + k)};
+                m = clip_cell_3d<R>(st, o);
+            } else {
+                const double o[2] = {(double)(lo[0] + i), (double)(lo[1] + j)};
+                m = clip_cell_2d<R>(s2, o);
+            }
+            if (m == R(0)) continue;
+            mine += (double)m;
+            const long long idx = flat_cell(g, an[0] + lo[0] + i, an[1] + lo[1] + j, DIM == 3 ? an[2] + lo[2] + k : 0);
+            if (idx >= 0) atomicAdd(out + idx, (double)m);
+        }
+        if (closure) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+            if (lane == 0) wsum[warp] = mine;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < CLIP_THREADS / 32; ++w) tot += wsum[w];
+                const long long idx = flat_cell(g, cell0[0], cell0[1], cell0[2]);
+                if (idx >= 0) atomicAdd(out + idx, mexact - tot);
+            }
+        }
+    }
+}
+
+cudaError_t launch_clip(const LaunchArgs& L, int fp32, cudaStream_t st) {
+    if (!L.clip_list || !L.ctr) return cudaSuccess;
+    const unsigned blocks = (unsigned)(L.num_sms * 4);
+    if (L.g.dim == 3) {
+        if (fp32)
+            k_project_clip<3, float><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
+                                                                     &L.ctr->clip_count, L.clip_cap, L.out);
+        else
+            k_project_clip<3, double><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
+                                                                      &L.ctr->clip_count, L.clip_cap, L.out);
+    } else {
+        if (fp32)
+            k_project_clip<2, float><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
+                                                                     &L.ctr->clip_count, L.clip_cap, L.out);
+        else
+            k_project_clip<2, double><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
+                                                                      &L.ctr->clip_count, L.clip_cap, L.out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cdp

@@ -25,7 +25,7 @@ struct cdp_ctx;
 struct cdp_problem_tag;
 
 namespace cdp {
-constexpr int CDP_TEV = 5;
+constexpr int CDP_TEV = 6;
 void solver_release(cdp_ctx* c);
 void step_release(cdp_ctx* c);
 }  // namespace cdp
@@ -45,6 +45,10 @@ struct cdp_ctx {
     size_t geo_cap;
     int* need;            // their box sizes
     size_t need_cap;
+    int* defer;           // simplices deferred by the first pass (accuracy control)
+    size_t defer_cap;
+    int* clip;            // simplices projected by clipping
+    size_t clip_cap;
     float* tiles;         // FP32 pieces of large-tetrahedron tiles kept between the two passes
     size_t tiles_cap;     // (floats)
     cdp::Counters* ctr;       // device
@@ -52,12 +56,12 @@ struct cdp_ctx {
     cdp::Counters* h_ctr;     // pinned host mirrors
     cdp::UnitCounts* h_stats;
     // per-kernel timing: CDP_TEV events per timed call (before the vertex records, after them,
-    // after the set-up kernel, after the main kernel, after the large-tetrahedron kernel), folded into
-    // totals[CDP_TEV - 1] when read
+    // after the set-up kernel, after the main kernel, after the large-tetrahedron kernel, after the
+    // accuracy control), folded into totals[CDP_TEV - 1] when read
     int timing;
     std::vector<cudaEvent_t>* pending;
     std::vector<cudaEvent_t>* pool;
-    double totals[4];
+    double totals[cdp::CDP_TEV - 1];
     int calls;
     // solver scratch
     std::vector<cdp::FftPlan>* plans;

@@ -1,8 +1,8 @@
 // Projection entry point that allocates nothing (declared in include/coldproj.h as
-// cdp_project_noalloc).  Its scratch (the per-call counters, the vertex records, the list of the
-// large tetrahedra and the geometry records of one batch of tetrahedra) is one
-// statically sized device array of this module instead of context-owned memory; the kernels are
-// the ones cdp_project launches.
+// cdp_project_noalloc).  Its scratch (the per-call counters, the vertex records, the lists of the
+// large, deferred and clipped simplices and the geometry records of one batch of 16,384
+// tetrahedra) is one statically sized device array of this module instead of context-owned memory;
+// the kernels are the ones cdp_project launches.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -24,13 +24,16 @@ constexpr long long kGeoBatch = 16384;  // tetrahedra set up per batch
 constexpr size_t kGeoRec = sizeof(cdp::TetGeo<double>) > sizeof(cdp::TetGeo<float>) ? sizeof(cdp::TetGeo<double>)
                                                                                      : sizeof(cdp::TetGeo<float>);
 constexpr size_t kListOffset = kCounterBytes + (size_t)kMaxVerts * sizeof(cdp::VertexRec);
-constexpr size_t kNeedOffset = kListOffset + (size_t)kMaxSimplices * sizeof(int);
+constexpr size_t kDeferOffset = kListOffset + (size_t)kMaxSimplices * sizeof(int);
+constexpr size_t kClipOffset = kDeferOffset + (size_t)kMaxSimplices * sizeof(int);
+constexpr size_t kNeedOffset = kClipOffset + (size_t)kMaxSimplices * sizeof(int);
 constexpr size_t kGeoOffset = (kNeedOffset + (size_t)kGeoBatch * sizeof(int) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kGeoOffset + (size_t)kGeoBatch * kGeoRec;
 static_assert(sizeof(cdp::Counters) <= kCounterBytes, "counters do not fit their slot");
+static_assert(kScratchBytes == CDP_NOALLOC_SCRATCH_BYTES, "the static scratch differs from the size the header states");
 
-// [counters | vertex records | list of large tetrahedra | box sizes | geometry records of one batch];
-// shared by every call on the device
+// [counters | vertex records | list of large tetrahedra | deferred list | clip list | box sizes |
+//  geometry records of one batch]; shared by every call on the device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -78,7 +81,10 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
                                    void* stream) {
     int rc = cdp::check_problem_args(p);
     if (rc) return rc;
-    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    {
+        int f = 0, a = 0;
+        if (!cdp::parse_precision(precision, &f, &a)) return CDP_ERR_ARG;
+    }
     if (p->n_verts > kMaxVerts || p->n_simplices > kMaxSimplices) return CDP_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -117,11 +123,17 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     L.out = p->cell_mass;
     L.stats = nullptr;
     L.num_sms = s->num_sms;
-    int fp32 = precision == CDP_FP32_MIXED;
+    int fp32 = 0, accuracy = 1;
+    cdp::parse_precision(precision, &fp32, &accuracy);
+    L.accuracy = accuracy;
     L.small_blocks_per_sm = 8 * s->blocks[p->dim == 3][fp32];
     L.resident_per_sm = s->blocks[p->dim == 3][fp32];
     L.big_list = (int*)(s->scratch + kListOffset);
     L.big_cap = kMaxSimplices;
+    L.defer_list = (int*)(s->scratch + kDeferOffset);
+    L.defer_cap = kMaxSimplices;
+    L.clip_list = (int*)(s->scratch + kClipOffset);
+    L.clip_cap = kMaxSimplices;
     L.need = (int*)(s->scratch + kNeedOffset);
     L.geo = s->scratch + kGeoOffset;
     L.geo_cap = kGeoBatch;

@@ -227,12 +227,23 @@ __device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned lon
     acc(v0, v1, v2, val);
 }
 
+// The lists of the accuracy control and the pass of the 2D kernel (second pass: the simplices of
+// the deferred list, their number read on the device).
+struct WarpPass {
+    AccCtl acc;
+    int second;
+    int* defer_list;
+    long long defer_cap;
+    int* clip_list;
+    long long clip_cap;
+};
+
 template <int DIM, typename R>
 __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long long ns, long long nv,
                                                             const int* __restrict__ simp,
                                                             const VertexRec* __restrict__ V,
                                                             double* __restrict__ out, Counters* __restrict__ ctr,
-                                                            UnitCounts* __restrict__ stats) {
+                                                            UnitCounts* __restrict__ stats, WarpPass wp) {
     static_assert(DIM == 2, "tetrahedra are projected by the kernels of cdp_tetproj.cu");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
@@ -247,16 +258,24 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
     UnitCounts cnt = {0, 0, 0, 0, 0};
     UnitCounts* pc = stats ? &cnt : nullptr;
     unsigned long long n0 = 0, nact = 0, nzero = 0;
+    double ebm = 0.0;  // the largest error bound of the simplices this lane set up for Franklin's sum
+    if (wp.second) {
+        const long long listed = (long long)*(volatile const unsigned*)&ctr->defer_count;
+        ns = listed < wp.defer_cap ? listed : wp.defer_cap;
+    }
+    const double mfirst = wp.second ? __longlong_as_double((long long)*(volatile const unsigned long long*)&ctr->mmax_bits)
+                                    : 0.0;
     const int cs = CDP_CHUNK;
     const long long nchunks = (ns + cs - 1) / cs;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
          chunk += warps) {
         // ---- setup: one simplex per lane
-        const long long s = chunk * cs + lane;
+        const long long item = chunk * cs + lane;
         bool active = false;
         int n[3] = {0, 0, 0};
-        if (lane < cs && s < ns) {
+        if (lane < cs && item < ns) {
+            const long long s = wp.second ? (long long)wp.defer_list[item] : item;
             const VertexRec* v[4];
             if (!fetch_vertices(simp, s, DIM + 1, nv, V, v)) {
                 atomicOr(&ctr->flags, CDP_FLAG_INDEX);
@@ -274,8 +293,21 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                 } else {
                     TriGeo<R>& G = sh->geo[lane];
                     tri_setup(S, S.lo, G);
-                    tri_counts(G, n);
-                    active = true;
+                    // accuracy control (AccCtl): first pass, a steep simplex is deferred; second
+                    // pass, one whose cancellation bound exceeds the accepted error is clipped
+                    const float rmax = fmaxf(fabsf((float)G.rho[0]), fmaxf(fabsf((float)G.rho[1]), fabsf((float)G.rho[2])));
+                    const float gn = sqrtf((float)G.g[0] * (float)G.g[0] + (float)G.g[1] * (float)G.g[1]);
+                    if (!wp.second && gn > wp.acc.defer_ratio * rmax) {
+                        const unsigned at = atomicAdd(&ctr->defer_count, 1u);
+                        if ((long long)at < wp.defer_cap) wp.defer_list[at] = (int)s;
+                    } else if (wp.second && wp.acc.eps_k_grad * (double)gn > wp.acc.tau * mfirst) {
+                        const unsigned at = atomicAdd(&ctr->clip_count, 1u);
+                        if ((long long)at < wp.clip_cap) wp.clip_list[at] = (int)s;
+                    } else {
+                        ebm = fmax(ebm, wp.acc.eps_k_rho * (double)rmax + wp.acc.eps_k_grad * (double)gn);
+                        tri_counts(G, n);
+                        active = true;
+                    }
                 }
             }
         }
@@ -374,6 +406,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
         }
         __syncwarp();
     }
+    if (ebm > 0.0) atomicMax(&ctr->ebmax_bits, (unsigned long long)__double_as_longlong(ebm));
     if (stats) {
         add_counts(stats, cnt);
         if (n0) atomicAdd(&ctr->n_class0, n0);
@@ -419,6 +452,8 @@ int resident_blocks(int dim, int fp32) {
     return n > 0 ? n : 1;
 }
 
+// First pass over every triangle (steep ones deferred), the largest cell mass, second pass over the
+// deferred ones (the grid of the first pass's size: the count is read on the device), clipping.
 template <int DIM, typename R>
 static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t mid) {
     long long chunks = (L.ns + CDP_CHUNK - 1) / CDP_CHUNK;
@@ -426,10 +461,20 @@ static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t 
     long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    WarpPass wp = {acc_ctl(sizeof(R) == 4), 0, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
+    if (!L.accuracy) wp.acc.defer_ratio = 3.0e38f;  // nothing is deferred
     k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(
-        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats);
+        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, wp);
     if (mid) cudaEventRecord(mid, st);
-    return cudaGetLastError();
+    if (L.ev_acc) cudaEventRecord(L.ev_acc, st);
+    if (!L.accuracy) return cudaGetLastError();
+    cudaError_t e = launch_pass_boundary(L, st);
+    if (e != cudaSuccess) return e;
+    wp.second = 1;
+    k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(
+        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, wp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_clip(L, sizeof(R) == 4, st);
 }
 
 cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
@@ -446,6 +491,7 @@ cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaE
     if (L.ns == 0) {
         if (after_setup) cudaEventRecord(after_setup, st);
         if (mid) cudaEventRecord(mid, st);
+        if (L.ev_acc) cudaEventRecord(L.ev_acc, st);
         return cudaSuccess;
     }
     if (L.g.dim == 3) {

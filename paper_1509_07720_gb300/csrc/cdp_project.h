@@ -18,9 +18,52 @@ struct Counters {
     unsigned flags;       // CDP_FLAG_* bits
     unsigned big_count;   // tetrahedra listed as large (bounding box above the main kernel's box)
     unsigned big_next;    // next entry of that list to be tiled by the main kernel's blocks
-    unsigned pad;
+    unsigned defer_count; // simplices deferred by the first pass (steep density gradient)
     unsigned long long n_class0, n_small, n_zero, n_big_tiles;
+    unsigned clip_count;  // simplices re-projected by clipping (accuracy control)
+    unsigned big_first;   // large tetrahedra listed by the first pass (big_count is reused after it)
+    unsigned long long mmax_bits;   // largest |cell mass| after the first pass (FP64 bits, >= 0)
+    unsigned long long ebmax_bits;  // largest error bound of a simplex projected by Franklin's sum
 };
+
+// Accuracy control (Sect. 3.4, eqs. accuracy, accuracy2).  The rounding error of the pieces of a
+// simplex projected by Franklin's sum is bounded, per piece, by
+//     eb = eps_R (k_rho rho_max + k_grad |grad rho|)
+// (rho premultiplied by the cell volume, the gradient per cell): the first term is the fixed-point
+// rounding of the vertex positions and the rounding of contributions of the size of the density,
+// the second the cancellation of contributions carrying the gradient.  The constants were measured
+// (the number W of wrong trailing bits found statistically, as Sect. 3.4 does) on simplices of
+// every shape -- generic, nearly flat, needle-like, with facets nearly parallel to grid planes, and
+// density contrasts up to e^6 -- each alone in its block of cells, against the oracle: largest
+// ratios 26 (FP32, with the mass closure of the chunk rounds) and 6400 (FP64) for the first term,
+// 2.1 (FP32) and 4 (FP64) for the second; the constants below take those with a margin of 1.5 to 2.
+//   A simplex whose gradient exceeds defer_ratio times its density is deferred by the first pass
+// (its pieces are not flushed); once the first pass has given the largest cell mass M, a deferred
+// simplex is projected by Franklin's sum when eps_R k_grad |grad rho| <= tau M, and by clipping
+// (cdp_clip.cu, no cancellation) otherwise.  tau is half the stated accuracy (1e-5 of the largest
+// cell for FP32-mixed, 1e-11 for FP64).
+struct AccCtl {
+    float defer_ratio;  // |grad rho| / rho_max above which the first pass defers a simplex
+    double eps_k_rho;   // eps_R k_rho
+    double eps_k_grad;  // eps_R k_grad
+    double tau;         // accepted cancellation error, relative to the largest cell
+};
+
+__host__ __device__ inline AccCtl acc_ctl(int fp32) {
+    AccCtl a;
+    if (fp32) {
+        a.defer_ratio = 30.f;
+        a.eps_k_rho = 48.0 * 5.9604644775390625e-08;   // 48 eps_32
+        a.eps_k_grad = 4.0 * 5.9604644775390625e-08;   // 4 eps_32
+        a.tau = 5e-6;
+    } else {
+        a.defer_ratio = 30.f;
+        a.eps_k_rho = 9800.0 * 1.1102230246251565e-16;  // 9800 eps_64
+        a.eps_k_grad = 8.0 * 1.1102230246251565e-16;    // 8 eps_64
+        a.tau = 5e-12;
+    }
+    return a;
+}
 
 struct LaunchArgs {
     GridDesc g;
@@ -44,7 +87,23 @@ struct LaunchArgs {
     void* geo;          // geometry records of one batch of tetrahedra (capacity geo_cap records)
     int* need;          // their box sizes (geo_cap entries)
     long long geo_cap;
+    int* defer_list;    // simplices deferred by the first pass (capacity defer_cap)
+    long long defer_cap;
+    int* clip_list;     // simplices projected by clipping (capacity clip_cap)
+    long long clip_cap;
+    int accuracy;       // 1: accuracy control (AccCtl); 0: every simplex by Franklin's sum
+    cudaEvent_t ev_acc; // optional: recorded where the accuracy control starts (timing)
 };
+
+// precision argument of the C ABI: arithmetic (CDP_FP64 / CDP_FP32_MIXED) and the accuracy-control
+// flag; false for an invalid value
+inline bool parse_precision(int precision, int* fp32, int* accuracy) {
+    const int base = precision & 0xff;
+    if ((precision & ~0x1ff) != 0 || (base != 0 && base != 1)) return false;
+    *fp32 = base;
+    *accuracy = (precision & 0x100) ? 0 : 1;
+    return true;
+}
 
 cudaError_t configure_all();
 // resident blocks per SM of the projection kernel of dimension `dim` (occupancy calculator)
@@ -68,5 +127,10 @@ cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py,
 // main kernel (3D: before the large-tetrahedron kernel)
 cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,
                            cudaEvent_t mid);
+// between the two passes: the largest |cell mass| of the grid into ctr->mmax_bits, and the first
+// pass's count of large tetrahedra kept while the list is emptied for the second pass
+cudaError_t launch_pass_boundary(const LaunchArgs& L, cudaStream_t st);
+// the simplices of clip_list (cdp_clip.cu)
+cudaError_t launch_clip(const LaunchArgs& L, int fp32, cudaStream_t st);
 
 }  // namespace cdp

@@ -122,7 +122,10 @@ void step_release(cdp_ctx* c) {
 extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision, double dt,
                                 double four_pi_G, int use_graph, void* stream) {
     if (!c || n < 0 || (n > 0 && !probs)) return CDP_ERR_ARG;
-    if (precision != CDP_FP64 && precision != CDP_FP32_MIXED) return CDP_ERR_ARG;
+    {
+        int f = 0, a = 0;
+        if (!cdp::parse_precision(precision, &f, &a)) return CDP_ERR_ARG;
+    }
     if (!(dt == dt) || !(four_pi_G == four_pi_G)) return CDP_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         int rc = check_step_problem(probs[i]);

@@ -81,6 +81,16 @@ struct BigState {
     float s[3];         // sum of the pieces as two floats (hi, lo) and the sum of their magnitudes
 };
 
+// The pass of the large-tetrahedron kernel and the lists of the accuracy control.
+struct BigPass {
+    AccCtl acc;
+    int second;
+    int* defer_list;
+    long long defer_cap;
+    int* clip_list;
+    long long clip_cap;
+};
+
 template <typename R>
 struct TetShared {
     TetGeo<R> geo[TB_NT];
@@ -823,11 +833,17 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
 }
 
 // How a round's boxes are flushed.  FLUSH_CLOSE_ROUND: the round's own mass closure (FP32 path:
-// the closed-form masses of its tetrahedra minus the sum of their pieces, spread over the pieces).
-// FLUSH_SUM_ONLY: the pieces are only summed into (s_hi, s_lo, s_abs) and cleared (first pass over
-// the tiles of a large tetrahedron).  FLUSH_SCALED: the pieces are flushed with the given closure
-// scale, and summed as well (second pass).
-enum FlushMode { FLUSH_CLOSE_ROUND = 0, FLUSH_SUM_ONLY = 1, FLUSH_SCALED = 2 };
+// the closed-form masses of its tetrahedra minus the sum of their pieces, spread over the pieces;
+// the accuracy control keeps tetrahedra whose pieces may carry a large rounding error out of the
+// rounds, so the round's residual is a few FP32 ulps of its pieces).  FLUSH_SUM_ONLY: the pieces are
+// only summed into (s_hi, s_lo, s_abs) and cleared (first pass over the tiles of a large
+// tetrahedron).  FLUSH_SCALED: the pieces are flushed with the given closure scale, and summed as
+// well (second pass).
+// FLUSH_CLOSE_UNITS: every tetrahedron's own closure (its residual spread over its own pieces), for
+// the second pass, whose rounds hold only the deferred tetrahedra: their pieces may carry the
+// larger rounding the accuracy control accepted, which a round's closure would spread over the
+// round's other tetrahedra.
+enum FlushMode { FLUSH_CLOSE_ROUND = 0, FLUSH_SUM_ONLY = 1, FLUSH_SCALED = 2, FLUSH_CLOSE_UNITS = 3 };
 
 // (hi, lo) as a two-float sum and asum summed over the block; every thread gets the totals
 __device__ __forceinline__ void block_sum2(float& hi, float& lo, float& asum, float (*red)[TB_WARPS]) {
@@ -856,6 +872,36 @@ __device__ __forceinline__ void block_sum2(float& hi, float& lo, float& asum, fl
     }
 }
 
+// The quantities of the accuracy control of one simplex (AccCtl): its largest |density| and the
+// norm of its density gradient (both premultiplied by the cell volume; gradient per cell).
+template <typename R>
+__device__ __forceinline__ void acc_terms(const TetGeo<R>& G, float& rmax, float& gn) {
+    rmax = fmaxf(fmaxf(fabsf((float)G.rho[0]), fabsf((float)G.rho[1])), fmaxf(fabsf((float)G.rho[2]), fabsf((float)G.rho[3])));
+    const float g0 = (float)G.g[0], g1 = (float)G.g[1], g2 = (float)G.g[2];
+    gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
+}
+
+// The largest |cell mass| after the first pass (0 before it has been taken).
+__device__ __forceinline__ double first_pass_max(const Counters* ctr) {
+    return __longlong_as_double((long long)*(volatile const unsigned long long*)&ctr->mmax_bits);
+}
+
+// Where the set-up sends a simplex whose box fits the chunks: 0 the chunks (Franklin's sum in this
+// pass), 1 the deferred list (first pass: its gradient is steep), 2 the clip list (second pass: its
+// cancellation bound exceeds the accepted error).
+template <typename R>
+__device__ __forceinline__ int acc_route(const TetGeo<R>& G, const AccCtl& acc, bool second, const Counters* ctr) {
+    float rmax, gn;
+    acc_terms(G, rmax, gn);
+    if (!second) return gn > acc.defer_ratio * rmax ? 1 : 0;
+    return acc.eps_k_grad * (double)gn > acc.tau * first_pass_max(ctr) ? 2 : 0;
+}
+
+__device__ __forceinline__ void list_append(int* list, long long cap, unsigned* count, int s) {
+    const unsigned at = atomicAdd(count, 1u);
+    if ((long long)at < cap) list[at] = s;
+}
+
 // Flush every box of the round: one FP64 atomic per non-zero piece (FP32 path: and one more for its
 // share of the mass-closure residual, `scale` |piece|).  Every thread of the block calls it; the
 // piece sums of FLUSH_SUM_ONLY / FLUSH_SCALED are added into `sums` by thread 0, and FLUSH_SUM_ONLY
@@ -877,7 +923,7 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
         __syncthreads();
         for (int w = 0; w < TB_WARPS; ++w) used_slots = max(used_slots, sh->wsum[w]);
     }
-    if (fp32 && mode != FLUSH_SCALED) {
+    if (fp32 && mode != FLUSH_SCALED && mode != FLUSH_CLOSE_UNITS) {
         // FP32 pieces of the round minus the closed-form masses of its tetrahedra, summed as two
         // floats (exact enough, FP32 arithmetic only); the residual is then spread over the pieces
         // in proportion to their magnitude
@@ -924,9 +970,37 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
         const int base = sh->boff[t];
         if (base < 0) continue;
         const TetGeo<R>& G = sh->geo[t];
+
         const int ex = sh->td[t][0], ey = sh->td[t][1], ez = sh->td[t][2];
         const int size = ex * ey * ez;
         const int ax = G.anchor[0], ay = G.anchor[1], az = G.anchor[2];
+        if (fp32 && mode == FLUSH_CLOSE_UNITS) {
+            // this tetrahedron's closure: its closed-form mass minus the two-float sum of its pieces,
+            // spread over them in proportion to their magnitude (the warp's lanes share the box)
+            float hi = 0.f, lo = 0.f, asum = 0.f;
+            if (lane == 0) {
+                two_sum_acc(hi, lo, -G.mexact_hi);
+                lo -= G.mexact_lo;
+            }
+            for (int e = lane; e < size; e += 32) {
+                const float v = (float)sh->box[base + e];
+                two_sum_acc(hi, lo, v);
+                asum += fabsf(v);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ohi = __shfl_xor_sync(FULL, hi, o), olo = __shfl_xor_sync(FULL, lo, o);
+                lo += olo;
+                two_sum_acc(hi, lo, ohi);
+                asum += __shfl_xor_sync(FULL, asum, o);
+            }
+            const float resid = -(hi + lo);
+            scale = asum > 0.f ? resid * __frcp_rn(asum) : 0.f;
+            if (!(asum > 0.f) && lane == 0) {
+                const long long idx = flat_cell(g, ax + G.cell[0][0], ay + G.cell[0][1], az + G.cell[0][2]);
+                if (idx >= 0) atomicAdd(out + idx, (double)resid);
+            }
+        }
         const float inv_ex = __frcp_rn((float)ex), inv_ey = __frcp_rn((float)ey);
         // a box inside the grid needs no wrap: flat index = base + (x n1 + y) n2 + z
         const bool inside =
@@ -983,23 +1057,44 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
 
 }  // namespace
 
-// One thread per tetrahedron of the batch [s0, s0 + nb): canonicalise it (exact orientation, periodic
-// unwrap, cells), deposit a tetrahedron inside one cell at once (Algorithm 2, step 1), list one
-// whose bounding box exceeds the shared box as large (for k_project_big), and write the geometry of
-// every other one to geo[i] with need[i] = its bounding-box cell count (0: nothing more to do).
+// One pass of the set-up over the tetrahedra of one batch (thread i < nb for the batch's tetrahedron
+// i):
+//  first pass  (list == null) the batch is [s0, s0 + nb) of the mesh.  Canonicalise (exact
+//              orientation, periodic unwrap, cells); a tetrahedron inside one cell deposits its
+//              mass at once (Algorithm 2, step 1); one whose bounding box exceeds TB_MAX_CELLS is
+//              listed as large (k_project_big); one with a steep gradient is deferred; every other
+//              one gets its geometry record geo[i] and need[i] = its bounding-box cell count.
+//  second pass (list = the deferred list) the batch is entries [s0, s0 + nb) of the list, nb
+//              capped by the list's count on the device.  A large one is listed again (the list was
+//              emptied between the passes); the others get their record, or are sent to the clip
+//              list when their cancellation bound exceeds the accepted error (AccCtl).
+// need[i] = 0 for every tetrahedron with nothing left for the chunks.
 template <typename R>
 __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, long long nb, long long nv,
                                                    const int* __restrict__ simp, const VertexRec* __restrict__ V,
                                                    double* __restrict__ out, Counters* __restrict__ ctr,
                                                    TetGeo<R>* __restrict__ geo, int* __restrict__ need,
-                                                   int* __restrict__ big_list, long long big_cap, int count) {
+                                                   int* __restrict__ big_list, long long big_cap, int count,
+                                                   const int* __restrict__ list, AccCtl acc, int* __restrict__ defer_list,
+                                                   long long defer_cap, int* __restrict__ clip_list, long long clip_cap) {
     // the block's records are assembled in shared memory and written out with coalesced stores
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TetGeo<R>* stage = reinterpret_cast<TetGeo<R>*>(smem_raw);
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool second = list != nullptr;
+    if (second) {
+        const long long listed = (long long)*(volatile const unsigned*)&ctr->defer_count;
+        const long long avail = (listed < defer_cap ? listed : defer_cap) - s0;
+        nb = avail < 0 ? 0 : (avail < nb ? avail : nb);
+    }
     int n_zero = 0, n_single = 0, n_box = 0;
+    double ebm = 0.0;  // the largest error bound (AccCtl) of the tetrahedra sent to the chunks
+    // groups of 128 consecutive tetrahedra, one per block in turn
+#pragma unroll 1
+    for (long long first = (long long)blockIdx.x * blockDim.x; first < nb; first += (long long)gridDim.x * blockDim.x) {
+    const long long i = first + threadIdx.x;
+    __syncthreads();  // the stage is free
     if (i < nb) {
-        const long long s = s0 + i;
+        const long long s = second ? (long long)list[s0 + i] : s0 + i;
         int my_need = 0;
         const VertexRec* v[4];
         bool ok = true;
@@ -1026,12 +1121,21 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
                 const long long cells =
                     (long long)(S.hi[0] - S.lo[0] + 1) * (S.hi[1] - S.lo[1] + 1) * (S.hi[2] - S.lo[2] + 1);
                 if (cells > TB_MAX_CELLS) {
-                    const unsigned at = atomicAdd(&ctr->big_count, 1u);
-                    if ((long long)at < big_cap) big_list[at] = (int)s;
+                    list_append(big_list, big_cap, &ctr->big_count, (int)s);
                 } else {
                     tet_setup(S, S.lo, stage[threadIdx.x]);
-                    my_need = (int)cells;
-                    n_box = 1;
+                    const int route = acc_route(stage[threadIdx.x], acc, second, ctr);
+                    if (route == 1) {
+                        list_append(defer_list, defer_cap, &ctr->defer_count, (int)s);
+                    } else if (route == 2) {
+                        list_append(clip_list, clip_cap, &ctr->clip_count, (int)s);
+                    } else {
+                        my_need = (int)cells;
+                        n_box = 1;
+                        float rmax, gn;
+                        acc_terms(stage[threadIdx.x], rmax, gn);
+                        ebm = fmax(ebm, acc.eps_k_rho * (double)rmax + acc.eps_k_grad * (double)gn);
+                    }
                 }
             }
         }
@@ -1040,12 +1144,15 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
     __syncthreads();
     {
         constexpr int W = sizeof(TetGeo<R>) / 8;
-        const long long first = (long long)blockIdx.x * blockDim.x;
         const int n = (int)(nb - first < (long long)blockDim.x ? nb - first : (long long)blockDim.x);
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(stage);
         unsigned long long* dst = reinterpret_cast<unsigned long long*>(geo + first);
         for (int w = threadIdx.x; w < n * W; w += blockDim.x) dst[w] = src[w];
     }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ebm = fmax(ebm, __shfl_xor_sync(FULL, ebm, o));
+    if ((threadIdx.x & 31) == 0 && ebm > 0.0) atomicMax(&ctr->ebmax_bits, (unsigned long long)__double_as_longlong(ebm));
     if (count) {
         n_zero = __reduce_add_sync(FULL, n_zero);
         n_single = __reduce_add_sync(FULL, n_single);
@@ -1055,6 +1162,25 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
             if (n_single) atomicAdd(&ctr->n_class0, (unsigned long long)n_single);
             if (n_box) atomicAdd(&ctr->n_small, (unsigned long long)n_box);
         }
+    }
+}
+
+// Between the two passes: the largest |cell mass| of the grid (after the first pass) into
+// ctr->mmax_bits, and (block 0) the first pass's count of large tetrahedra kept in big_first while
+// the list of large tetrahedra is emptied for the second pass.
+__global__ void __launch_bounds__(256) k_pass_boundary(const double* __restrict__ out, long long ncells,
+                                                        Counters* __restrict__ ctr) {
+    double m = 0.0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+         c += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(out[c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&ctr->mmax_bits, (unsigned long long)__double_as_longlong(m));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->big_first = ctr->big_count;
+        ctr->big_count = 0u;
+        ctr->big_next = 0u;
     }
 }
 
@@ -1178,10 +1304,13 @@ __device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int
 // path from the summing pass to the flush pass (with the tetrahedron's closure scale), or close the
 // tetrahedron (FP32: the FP64 remainder to the cell of vertex 0) and take the next one of the list
 // (bs.ntiles < 0 when the list is exhausted).
+//   The accuracy control (AccCtl) on the taken tetrahedron: first pass, a steep one is deferred;
+//   second pass, one whose cancellation bound exceeds the accepted error goes to the clip list.
+//   Either way it gets no tile (ntiles = 0) and the next one is taken at the next round.
 template <typename R>
 __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g, long long nv, const int* simp,
                                             const VertexRec* V, const int* big_list, long long big_cap,
-                                            double* out, Counters* ctr) {
+                                            double* out, Counters* ctr, const BigPass& bp) {
     constexpr bool fp32 = sizeof(R) == 4;
     BigState& b = sh->bs;
     if (fp32 && b.ntiles > 0) {
@@ -1219,8 +1348,23 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
     }
     // (the set-up kernel listed it after the same checks: no tile when they fail)
     Tet S;
-    const bool good = ok && canon_tet<1>(g, v, S) == 0;
-    if (good) tet_setup<R, 1>(S, S.lo, sh->big0);
+    bool good = ok && canon_tet<1>(g, v, S) == 0;
+    if (good) {
+        tet_setup<R, 1>(S, S.lo, sh->big0);
+        const int route = acc_route(sh->big0, bp.acc, bp.second != 0, ctr);
+        if (route == 1) {
+            list_append(bp.defer_list, bp.defer_cap, &ctr->defer_count, (int)s);
+            good = false;
+        } else if (route == 2) {
+            list_append(bp.clip_list, bp.clip_cap, &ctr->clip_count, (int)s);
+            good = false;
+        } else {
+            float rmax, gn;
+            acc_terms(sh->big0, rmax, gn);
+            const double eb = bp.acc.eps_k_rho * (double)rmax + bp.acc.eps_k_grad * (double)gn;
+            atomicMax(&ctr->ebmax_bits, (unsigned long long)__double_as_longlong(eb));
+        }
+    }
     int n = 1;
     for (int a = 0; a < 3; ++a) {
         b.ext[a] = good ? S.hi[a] - S.lo[a] + 1 : 0;
@@ -1239,14 +1383,22 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
 // The chunks: block b takes chunks b, b + gridDim.x, ... of the batch's geometry records (thread
 // t < TB_NT speaks for tetrahedron t of the chunk) and projects them in rounds whose boxes fit
 // the block's slots together.
-template <typename R, bool STATS>
+//   SECOND: the batch holds the records of deferred tetrahedra (entries [list_off, list_off + nb) of
+//   the deferred list, nb capped by the list's count on the device), each closed on its own.
+template <typename R, bool STATS, bool SECOND>
 __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
-                  double* __restrict__ out, UnitCounts* __restrict__ stats) {
+                  double* __restrict__ out, UnitCounts* __restrict__ stats, const Counters* __restrict__ ctr,
+                  long long list_off, long long list_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int BOX = BoxCap<R>::value;
     TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
     const int tid = threadIdx.x;
+    if (SECOND) {
+        const long long listed = (long long)*(volatile const unsigned*)&ctr->defer_count;
+        const long long avail = (listed < list_cap ? listed : list_cap) - list_off;
+        nb = avail < 0 ? 0 : (avail < nb ? avail : nb);
+    }
     for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
     UnitCounts cnt = {0, 0, 0, 0, 0};   // corner counts (registers)
     UnitCounts xcnt = {0, 0, 0, 0, 0};  // exact-predicate count, updated through a pointer
@@ -1282,7 +1434,8 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             pending = pending && !in;
             if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
             round_phases<R, STATS, false>(sh, in, n_cross, n_lines, cnt, pc);
-            round_flush<R>(sh, g, out, in, pre_box, FLUSH_CLOSE_ROUND, 0.f, false, nullptr, nullptr);
+            round_flush<R>(sh, g, out, in, pre_box, SECOND ? FLUSH_CLOSE_UNITS : FLUSH_CLOSE_ROUND, 0.f, false,
+                           nullptr, nullptr);
         }
     }
     if (STATS) {
@@ -1302,7 +1455,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_project_big(GridDesc g, long long nv, const int* __restrict__ simp, const VertexRec* __restrict__ V,
                   const int* __restrict__ big_list, long long big_cap, double* __restrict__ out,
                   float* __restrict__ tile_store, int store_tiles, Counters* __restrict__ ctr,
-                  UnitCounts* __restrict__ stats) {
+                  UnitCounts* __restrict__ stats, BigPass bp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
     constexpr int BOX = BoxCap<R>::value;
@@ -1325,7 +1478,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         const bool advance = sh->bs.tile >= sh->bs.ntiles;
         __syncthreads();  // every thread has read the state; the previous round is done
         if (advance) {
-            if (tid == 0) big_advance<R>(sh, g, nv, simp, V, big_list, big_cap, out, ctr);
+            if (tid == 0) big_advance<R>(sh, g, nv, simp, V, big_list, big_cap, out, ctr, bp);
             __syncthreads();
             if (sh->bs.ntiles < 0) break;
             continue;
@@ -1384,8 +1537,11 @@ static size_t tet_shared_bytes() {
 
 template <typename R, bool STATS>
 static cudaError_t configure_one() {
-    cudaError_t e = cudaFuncSetAttribute(k_project_tet<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_project_tet<R, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tet_shared_bytes<R>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(k_project_tet<R, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tet_shared_bytes<R>());
     if (e) return e;
     return cudaFuncSetAttribute(k_project_big<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tet_shared_bytes<R>());
@@ -1406,9 +1562,9 @@ cudaError_t configure_tet() {
 
 int resident_blocks_tet(int fp32) {
     int n = 0;
-    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<float, false>,
+    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<float, false, false>,
                                                                          TB_THREADS, tet_shared_bytes<float>())
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<double, false>,
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_project_tet<double, false, false>,
                                                                          TB_THREADS, tet_shared_bytes<double>());
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1425,41 +1581,90 @@ template <typename R>
 static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid) {
     const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
     const long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
-    for (long long s0 = 0; s0 < L.ns; s0 += batch) {
-        const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
-        k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, 128 * sizeof(TetGeo<R>), st>>>(
-            L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, reinterpret_cast<TetGeo<R>*>(L.geo), L.need,
-            L.big_list, L.big_cap, L.stats != nullptr);
-        if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
+    AccCtl acc = acc_ctl(sizeof(R) == 4);
+    if (!L.accuracy) acc.defer_ratio = 3.0e38f;  // nothing is deferred
+    TetGeo<R>* G = reinterpret_cast<TetGeo<R>*>(L.geo);
+    const size_t stage = 128 * sizeof(TetGeo<R>);
+    // the main kernel over a batch of nb records (second pass: nb capped on the device)
+    auto chunks = [&](long long nb, int second, long long off) {
         long long blocks = (nb + TB_NT - 1) / TB_NT;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        const TetGeo<R>* G = reinterpret_cast<const TetGeo<R>*>(L.geo);
-        if (L.stats)
-            k_project_tet<R, true><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(L.g, nb, G, L.need,
-                                                                                               L.out, L.stats);
-        else
-            k_project_tet<R, false><<<(unsigned)blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(L.g, nb, G, L.need,
-                                                                                                L.out, nullptr);
-    }
-    if (mid) cudaEventRecord(mid, st);
-    // the large tetrahedra listed by every batch's set-up (their number is read on the device; a
-    // block that finds the list exhausted exits at once): one block per resident slot
+        const unsigned b = (unsigned)blocks;
+        const size_t sm = tet_shared_bytes<R>();
+        if (second) {
+            if (L.stats)
+                k_project_tet<R, true, true><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, L.stats, L.ctr, off,
+                                                                       L.defer_cap);
+            else
+                k_project_tet<R, false, true><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, nullptr, L.ctr, off,
+                                                                        L.defer_cap);
+        } else {
+            if (L.stats)
+                k_project_tet<R, true, false><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, L.stats, L.ctr, 0, 0);
+            else
+                k_project_tet<R, false, false><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, nullptr, L.ctr, 0,
+                                                                         0);
+        }
+    };
+    // the large tetrahedra of the list (their number is read on the device; a block that finds the
+    // list exhausted exits at once): one block per resident slot.  FP32: each block keeps the pieces
+    // of up to tile_store_per_block tiles between the two passes over a tetrahedron's tiles.
     const long long big_blocks = (long long)L.num_sms * (L.resident_per_sm > 0 ? L.resident_per_sm : 1);
-    // FP32: each block keeps the pieces of up to tile_store_per_block tiles between the two passes
-    // of a tetrahedron (slots of TB_TILE_CELLS floats, per block index)
     const int store_tiles = sizeof(R) == 4 && L.tile_store &&
                                     L.tile_store_cap >= (size_t)big_blocks * L.tile_store_per_block * TB_TILE_CELLS
                                 ? L.tile_store_per_block
                                 : 0;
-    if (L.stats)
-        k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
-            L.stats + 1);
-    else
-        k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-            L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
-            nullptr);
+    auto big = [&](int second) {
+        const BigPass bp = {acc, second, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
+        if (L.stats)
+            k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
+                L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
+                L.stats + 1, bp);
+        else
+            k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
+                L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
+                nullptr, bp);
+    };
+    // first pass: every tetrahedron, batch by batch; steep ones are deferred
+    for (long long s0 = 0; s0 < L.ns; s0 += batch) {
+        const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
+        k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, stage, st>>>(
+            L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, G, L.need, L.big_list, L.big_cap, L.stats != nullptr,
+            nullptr, acc, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
+        if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
+        chunks(nb, 0, 0);
+    }
+    if (mid) cudaEventRecord(mid, st);
+    big(0);
+    if (L.ev_acc) cudaEventRecord(L.ev_acc, st);
+    if (!L.accuracy) return cudaGetLastError();
+    cudaError_t e = launch_pass_boundary(L, st);
+    if (e != cudaSuccess) return e;
+    // second pass: the deferred tetrahedra (at most min(ns, defer_cap)), batch by batch of the
+    // geometry buffer, then the deferred large ones, then those sent to clipping
+    const long long most = L.ns < L.defer_cap ? L.ns : L.defer_cap;
+    for (long long s0 = 0; s0 < most; s0 += batch) {
+        long long blocks = (batch + 127) / 128;
+        if (blocks > (long long)L.num_sms * 16) blocks = (long long)L.num_sms * 16;
+        k_tet_setup<R><<<(unsigned)blocks, 128, stage, st>>>(L.g, s0, batch, L.nv, L.simplices, L.verts, L.out, L.ctr, G,
+                                                            L.need, L.big_list, L.big_cap, L.stats != nullptr,
+                                                            L.defer_list, acc, L.defer_list, L.defer_cap, L.clip_list,
+                                                            L.clip_cap);
+        chunks(batch, 1, s0);
+    }
+    big(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_clip(L, sizeof(R) == 4, st);
+}
+
+// the largest |cell mass| after the first pass, and the list of large tetrahedra emptied
+cudaError_t launch_pass_boundary(const LaunchArgs& L, cudaStream_t st) {
+    long long cells = 1;
+    for (int a = 0; a < L.g.dim; ++a) cells *= L.g.n[a];
+    long long blocks = (cells + 255) / 256;
+    if (blocks > (long long)L.num_sms * 8) blocks = (long long)L.num_sms * 8;
+    k_pass_boundary<<<(unsigned)blocks, 256, 0, st>>>(L.out, cells, L.ctr);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,12 @@ __all__ = [
     "simplex_volumes",
     "make_batch",
     "cfl_dt",
+    "quantize_positions",
+    "shift_mesh",
+    "permute_vertex_order",
+    "stratified_subset",
+    "degenerate_meshes",
+    "isolated_simplices",
 ]
 
 
@@ -623,3 +629,53 @@ def degenerate_meshes(dim: int, grid: int, rng) -> dict:
         l_groups.append((np.concatenate([c + u, c - u, c + w], axis=1), None))  # edge 01 through the node
     out["grid_lines"] = (_assemble(D, l_groups, grid, rng), 0)
     return out
+
+
+def isolated_simplices(dim: int, blocks: int, block_cells: int, rng):
+    """One simplex in each cubic block of `block_cells` cells of a (blocks * block_cells)^dim grid
+    (unit box, not periodic), so that every block's cells hold the pieces of one simplex only.
+    Shapes cycle through five kinds (returned per simplex): 0 generic (edges 1-5 cells), 1 nearly
+    flat (an apex 10^-9 .. 1 times the size off the plane of the other vertices), 2 needle-like
+    (vertices nearly on a line), 3 a facet nearly parallel to a grid plane, 4 small (under a cell).
+    Densities are lognormal with sigma in {0.3, 1, 2} per simplex.  Returns (mesh, kinds, vertex
+    coordinates [n, dim + 1, dim] in grid units)."""
+    n = blocks ** dim
+    grid = blocks * block_cells
+    idx = np.stack(np.meshgrid(*[np.arange(blocks)] * dim, indexing="ij"), axis=0).reshape(dim, -1).T
+    kind = rng.integers(0, 5, n)
+    V = np.zeros((n, dim + 1, dim))
+    for i in range(n):
+        c = idx[i] * block_cells + block_cells / 2.0 + rng.uniform(-1.5, 1.5, dim)
+        k = kind[i]
+        size = rng.uniform(1.0, 5.0)
+        if k == 0:
+            V[i] = c + rng.uniform(-size, size, (dim + 1, dim))
+        elif k == 1:
+            base = rng.uniform(-size, size, (dim, dim))
+            nrm = np.linalg.svd(base - base.mean(0))[2][-1]
+            apex = base.mean(0) + rng.uniform(-0.3, 0.3, dim) * size
+            apex = apex - np.dot(apex - base[0], nrm) * nrm + nrm * 10.0 ** (-rng.uniform(0, 9)) * size
+            V[i] = c + np.vstack([base, apex])
+        elif k == 2:
+            a = rng.uniform(-size, size, dim)
+            b = rng.uniform(-size, size, dim)
+            pts = [a, b] + [a + rng.uniform(0.2, 0.8) * (b - a) + 10.0 ** (-rng.uniform(0, 7)) * rng.standard_normal(dim)
+                            for _ in range(dim - 1)]
+            V[i] = c + np.array(pts)
+        elif k == 3:
+            ax = rng.integers(0, dim)
+            base = rng.uniform(-size, size, (dim, dim))
+            base[:, ax] = rng.uniform(-1, 1) + 10.0 ** (-rng.uniform(0, 8)) * rng.standard_normal(dim)
+            V[i] = c + np.vstack([base, rng.uniform(-size, size, dim)])
+        else:
+            V[i] = c + rng.uniform(-0.6, 0.6, (dim + 1, dim))
+        lo = idx[i] * block_cells + 0.5
+        hi = (idx[i] + 1) * block_cells - 0.5
+        if np.any(V[i] < lo) or np.any(V[i] > hi):  # keep every simplex inside its own block
+            V[i] = idx[i] * block_cells + block_cells / 2.0 + rng.uniform(-2.0, 2.0, (dim + 1, dim))
+            kind[i] = 0
+    pos = np.ascontiguousarray((V.reshape(-1, dim) / grid).T)
+    simp = np.arange(n * (dim + 1), dtype=np.int32).reshape(n, dim + 1)
+    sig = rng.choice([0.3, 1.0, 2.0], n)
+    rho = np.exp(np.repeat(sig, dim + 1) * rng.standard_normal(n * (dim + 1)))
+    return Mesh(pos, simp, rho, (grid,) * dim, (0.0,) * dim, (1.0,) * dim, False, "isolated"), kind, V

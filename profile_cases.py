@@ -35,6 +35,8 @@ def main(argv=None):
     ap.add_argument("--problem", type=int, default=0, help="c5: problem index in [0, 64)")
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--stats", action="store_true", help="also one instrumented pass and per-kernel times")
+    ap.add_argument("--accuracy-off", action="store_true", help="no accuracy control")
     a = ap.parse_args(argv)
 
     import os
@@ -61,6 +63,8 @@ def main(argv=None):
         meshes = [batch[a.problem].mesh] if a.case == "c5" else [p.mesh for p in batch if p.mesh.dim == 3]
     data = [(m, *_device_mesh(torch, m)) for m in meshes]
     prec = pkg.CDP_FP32_MIXED if a.prec == "fp32" else pkg.CDP_FP64
+    if a.accuracy_off:
+        prec |= pkg.CDP_ACCURACY_OFF
     proj = pkg.Projector(0)
     stream = torch.cuda.current_stream()
     times = []
@@ -75,7 +79,18 @@ def main(argv=None):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     proj.check(stream)
-    print(json.dumps({"case": a.case, "scale": a.scale, "subset": a.subset, "problem": a.problem if a.case == "c5" else None,
+    extra = {}
+    if a.stats:
+        proj.timing(True)
+        for m, pos, simp, rho, out in data:
+            proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec, out=out,
+                         stream=stream)
+        kern, calls = proj.timing()
+        proj.timing(False)
+        extra["kernel_ms"] = dict(zip(["vertex records", "set-up", "main", "large", "accuracy control"], kern))
+        extra["stats"] = [proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec,
+                                       out=out, stream=stream, stats=True)[1] for m, pos, simp, rho, out in data]
+    print(json.dumps({**extra, "case": a.case, "scale": a.scale, "subset": a.subset, "problem": a.problem if a.case == "c5" else None,
                       "prec": a.prec, "simplices": int(sum(m.n_simplices for m in meshes)),
                       "ms_per_rep": times}), flush=True)
     proj.close()

@@ -54,9 +54,23 @@ def test_argument_errors_without_gpu(lib):
     assert lib.cdp_check(None, None) == -1
 
 
-def test_struct_layout_matches_header():
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler gives the header's structs."""
     import ctypes
+    import subprocess
 
-    # int, pad, 2 x int64, 3 pointers, 2 pointers, 3 int32, pad, 6 doubles, int, pad, pointer
-    assert ctypes.sizeof(pkg.cdp_problem) == 8 + 16 + 24 + 16 + 16 + 48 + 8 + 8
-    assert ctypes.sizeof(pkg.cdp_stats) == 14 * 8 + 8
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "coldproj.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cdp_problem), sizeof(cdp_stats),\n'
+        "         offsetof(cdp_problem, cell_mass), offsetof(cdp_stats, error_flags), offsetof(cdp_stats, n_deferred),\n"
+        "         offsetof(cdp_stats, accuracy_bound), sizeof(cdp_step_problem));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
+    want = [ctypes.sizeof(pkg.cdp_problem), ctypes.sizeof(pkg.cdp_stats), pkg.cdp_problem.cell_mass.offset,
+            pkg.cdp_stats.error_flags.offset, pkg.cdp_stats.n_deferred.offset, pkg.cdp_stats.accuracy_bound.offset,
+            ctypes.sizeof(pkg.cdp_step_problem)]
+    assert got == want

@@ -158,7 +158,7 @@ CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, i
  * 18 MiB), and the geometry records of one batch of 16,384 tetrahedra (9.4 MiB). */
 #define CDP_NOALLOC_MAX_VERTS 262144
 #define CDP_NOALLOC_MAX_SIMPLICES 1572864
-#define CDP_NOALLOC_SCRATCH_BYTES 37159168
+#define CDP_NOALLOC_SCRATCH_BYTES 37291008
 
 /* The projection of cdp_project (same kernels, same results to the stated accuracy), for callers
  * that must not allocate or free memory when they call: for instance a caller whose framework has
@@ -257,13 +257,19 @@ CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
 
 /* Launch-shape tuning (no counterpart in the paper: the choice of a GPU launch shape).  Times the
- * projection of `prob` (into its own cell_mass, which is overwritten) with the main kernel's
- * persistent grid at 1, 2, 4 and 8 times the device's resident blocks, and keeps the fastest for
- * the later projections of ctx with the same dimension and precision (default 8).  With a
- * non-null cache_path the choice is first looked up in that text file (lines
- * "<device> dim<D> <precision> <multiplier>"; the last entry of a key wins) and, when tuned, appended
- * to it.  Synchronises with the device.  *chosen (optional) receives the multiplier.  Returns
- * CDP_OK, CDP_ERR_ARG, an error of the projection, or CDP_ERR_CUDA. */
+ * projection of `prob` (into its own cell_mass, which is overwritten) while tuning, one after the
+ * other, three knobs of the context's later projections with the same dimension and precision:
+ *   - the main kernel's persistent grid: 1, 2, 4 or 8 times the device's resident blocks (default 8);
+ *   - 3D, the size-class threshold: the largest bounding box (cells) a tetrahedron of the main kernel
+ *     may have -- larger ones are tiled by the large-tetrahedron kernel -- among 640, 1280 (the
+ *     default), 2560 and the block's box slots (6144 FP32, 10240 FP64);
+ *   - 3D, the tile edge of the large tetrahedra: 12 or 18 cells (default 18).
+ * Each setting is kept only if it is faster than the best so far.  With a non-null cache_path the
+ * choice is first looked up in that text file (lines "<device> dim<D> <precision> <multiplier>
+ * <threshold> <edge>"; the last entry of a key wins) and, when tuned, appended to it.
+ * Synchronises with the device.  chosen (optional) receives int[3]: the multiplier, the threshold and
+ * the edge (the last two 0 in 2D).  Returns CDP_OK, CDP_ERR_ARG, an error of the projection, or
+ * CDP_ERR_CUDA. */
 CDP_API int cdp_autotune(cdp_ctx* ctx, const cdp_problem* prob, int precision, const char* cache_path,
                          int* chosen);
 

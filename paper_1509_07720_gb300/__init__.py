@@ -114,7 +114,7 @@ def load_library(path: str | None = None):
     lib.cdp_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.cdp_timing_read.restype = ctypes.c_int
     lib.cdp_autotune.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_char_p,
-                                 ctypes.POINTER(ctypes.c_int)]
+                                 ctypes.POINTER(ctypes.c_int * 3)]
     lib.cdp_autotune.restype = ctypes.c_int
     dp = ctypes.c_void_p
     arr3 = ctypes.c_void_p * 3
@@ -192,11 +192,11 @@ def cdp_timing_read(ctx):
 
 
 def cdp_autotune(ctx, prob, precision: int, cache_path=None) -> tuple:
-    """(return code, chosen grid multiplier) of the C call of the same name."""
-    chosen = ctypes.c_int(0)
+    """(return code, (grid multiplier, size-class threshold, tile edge)) of the C call of the same name."""
+    chosen = (ctypes.c_int * 3)()
     path = None if cache_path is None else os.fsencode(cache_path)
-    rc = load_library().cdp_autotune(ctx, ctypes.byref(prob), int(precision), path, ctypes.byref(chosen))
-    return rc, int(chosen.value)
+    rc = load_library().cdp_autotune(ctx, ctypes.byref(prob), int(precision), path, chosen)
+    return rc, tuple(int(v) for v in chosen)
 
 
 def _i3(v):
@@ -355,8 +355,8 @@ class Projector:
 
     def autotune(self, pos, simplices, rho, grid, box_lo=None, box_len=None, periodic=True,
                  precision=CDP_FP32_MIXED, out=None, cache_path=None):
-        """Tune the main kernel's grid for this context on the given problem (its projection is written
-        into `out`); returns the chosen multiplier of the resident blocks."""
+        """Tune the launch shape of this context on the given problem (its projection is written into
+        `out`); returns (grid multiplier, size-class threshold, tile edge)."""
         import torch
 
         dim = len(grid)

@@ -135,16 +135,17 @@ namespace cdp {
 // argument check of one problem, for the entry points defined in other translation units
 int check_problem_args(const cdp_problem* p) { return check_problem(p); }
 
-// grow the scratch to hold the largest of `n` problems (allocation happens here, never inside
-// a captured sequence)
+// grow the scratch to hold the groups of `n` problems (allocation happens here, never inside a
+// captured sequence): every buffer sized for the totals of all the problems, at least what any of
+// their groups needs
 int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
     size_t nv = 1, ns = 1;
-    for (int i = 0; i < n; ++i) {
-        if ((size_t)probs[i].n_verts > nv) nv = (size_t)probs[i].n_verts;
-        if ((size_t)probs[i].n_simplices > ns) ns = (size_t)probs[i].n_simplices;
-    }
     bool any3d = false;
-    for (int i = 0; i < n; ++i) any3d = any3d || probs[i].dim == 3;
+    for (int i = 0; i < n; ++i) {
+        nv += (size_t)probs[i].n_verts;
+        ns += (size_t)probs[i].n_simplices + 64;  // (with the chunk alignment of each problem)
+        any3d = any3d || probs[i].dim == 3;
+    }
     int rc = grow(&c->verts, &c->verts_cap, nv);
     if (rc) return rc;
     if ((rc = grow(&c->queue, &c->queue_cap, ns))) return rc;
@@ -153,54 +154,83 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
     return grow_geo(c, ns);
 }
 
-// enqueue one projection on `st` (arguments already checked)
-int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats) {
-    int rc;
-    if ((rc = grow(&c->verts, &c->verts_cap, (size_t)(p->n_verts > 0 ? p->n_verts : 1)))) return rc;
-    {
-        const size_t ns1 = (size_t)(p->n_simplices > 0 ? p->n_simplices : 1);
-        if ((rc = grow(&c->defer, &c->defer_cap, ns1)) || (rc = grow(&c->clip, &c->clip_cap, ns1))) return rc;
+// the table of a group of problems of one dimension (at most CDP_GROUP, arguments already checked):
+// their grids, pointers and offsets in the group's vertex, simplex and cell numberings.  Each
+// problem's simplices start at a multiple of the chunk size (3D), so that no chunk of the main
+// kernel mixes two problems.  CDP_ERR_ARG when the group's simplex numbering exceeds 2^31 - 1.
+int build_table(const cdp_problem* const* probs, int n, ProbTable& T) {  // (also used by cdp_noalloc.cu)
+    memset(&T, 0, sizeof(T));
+    T.n = n;
+    T.dim = probs[0]->dim;
+    const long long align = T.dim == 3 ? 64 : 1;
+    long long nv = 0, ns = 0, nc = 0;
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem* p = probs[i];
+        ProbEntry& e = T.p[i];
+        GridDesc& g = e.g;
+        g.dim = p->dim;
+        g.periodic = p->periodic ? 1 : 0;
+        double cellvol = 1.0;
+        long long cells = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (a < p->dim) {
+                g.n[a] = p->grid[a];
+                g.lo[a] = p->box_lo[a];
+                g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
+                cellvol *= p->box_len[a] / (double)p->grid[a];
+                cells *= p->grid[a];
+            } else {
+                g.n[a] = 1;
+                g.lo[a] = 0.0;
+                g.inv_h[a] = 1.0;
+            }
+        }
+        g.cell_volume = cellvol;
+        e.simplices = p->simplices;
+        e.out = p->cell_mass;
+        for (int a = 0; a < 3; ++a) e.pos[a] = a < p->dim ? p->pos[a] : nullptr;
+        e.rho = p->rho;
+        e.nv = p->n_verts;
+        e.ns = p->n_simplices;
+        e.v_off = nv;
+        e.s_off = (ns + align - 1) / align * align;
+        e.c_off = nc;
+        nv += p->n_verts;
+        ns = e.s_off + p->n_simplices;
+        nc += cells;
     }
-    if (p->dim == 3 && ((rc = grow(&c->queue, &c->queue_cap, (size_t)(p->n_simplices > 0 ? p->n_simplices : 1))) ||
-                        (rc = grow_geo(c, (size_t)p->n_simplices))))
-        return rc;
-    if (p->dim == 3 && precision == CDP_FP32_MIXED && (rc = grow_tiles(c))) return rc;
+    T.nv = nv;
+    T.ns = ns;
+    T.ncells = nc;
+    return ns <= (long long)0x7fffffff ? CDP_OK : CDP_ERR_ARG;
+}
+
+// enqueue the projection of one group on `st` (arguments already checked; a single projection is a
+// group of one)
+int project_group(cdp_ctx* c, const ProbTable& T, int precision, int accumulate, cudaStream_t st, bool want_stats) {
+    int rc;
+    const size_t nv1 = (size_t)(T.nv > 0 ? T.nv : 1), ns1 = (size_t)(T.ns > 0 ? T.ns : 1);
+    if ((rc = grow(&c->verts, &c->verts_cap, nv1))) return rc;
+    if ((rc = grow(&c->defer, &c->defer_cap, ns1)) || (rc = grow(&c->clip, &c->clip_cap, ns1))) return rc;
+    int fp32 = 0, accuracy = 1;
+    if (!parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
+    if (T.dim == 3 && ((rc = grow(&c->queue, &c->queue_cap, ns1)) || (rc = grow_geo(c, ns1)))) return rc;
+    if (T.dim == 3 && fp32 && (rc = grow_tiles(c))) return rc;
 
     LaunchArgs L;
     memset(&L, 0, sizeof(L));
-    L.g.dim = p->dim;
-    L.g.periodic = p->periodic ? 1 : 0;
-    long long cells = 1;
-    L.cellvol = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        if (a < p->dim) {
-            L.g.n[a] = p->grid[a];
-            L.g.lo[a] = p->box_lo[a];
-            L.g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
-            L.cellvol *= p->box_len[a] / (double)p->grid[a];
-            cells *= p->grid[a];
-        } else {
-            L.g.n[a] = 1;
-            L.g.lo[a] = 0.0;
-            L.g.inv_h[a] = 1.0;
-        }
-    }
-    L.g.cell_volume = L.cellvol;
-    L.nv = p->n_verts;
-    L.ns = p->n_simplices;
-    L.simplices = p->simplices;
+    L.T = T;
+    L.accuracy = accuracy;
     L.verts = c->verts;
-    L.out = p->cell_mass;
     L.ctr = c->ctr;
     L.stats = want_stats ? c->stats : nullptr;
     L.num_sms = c->num_sms;
-    int fp32 = 0, accuracy = 1;
-    if (!parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
-    L.accuracy = accuracy;
     // a persistent grid: every resident block slot of the device, grid_mult times over
     L.small_blocks_per_sm =
-        c->grid_mult[p->dim == 3][fp32] * (p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
-    L.resident_per_sm = p->dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32];
+        c->grid_mult[T.dim == 3][fp32] * (T.dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32]);
+    L.resident_per_sm = T.dim == 3 ? c->blocks_small[fp32] : c->blocks_big[fp32];
+    L.max_cells = c->max_cells[fp32];
+    L.tile_edge = c->tile_edge[fp32];
     L.big_list = c->queue;
     L.big_cap = (long long)c->queue_cap;
     L.geo = c->geo;
@@ -223,22 +253,25 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
         cudaSuccess)
         return CDP_ERR_CUDA;
     if (want_stats && cudaMemsetAsync(c->stats, 0, 2 * sizeof(UnitCounts), st) != cudaSuccess) return CDP_ERR_CUDA;
-    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
-        return CDP_ERR_CUDA;
-    constexpr int T = CDP_TEV;
-    cudaEvent_t ev[T] = {};
+    if (!accumulate)
+        for (int i = 0; i < T.n; ++i) {
+            const long long cells = (i + 1 < T.n ? T.p[i + 1].c_off : T.ncells) - T.p[i].c_off;
+            if (cudaMemsetAsync(T.p[i].out, 0, (size_t)cells * sizeof(double), st) != cudaSuccess) return CDP_ERR_CUDA;
+        }
+    constexpr int TE = CDP_TEV;
+    cudaEvent_t ev[TE] = {};
     if (c->timing) {
         if (c->pending->size() >= 4096) fold_timing(c);
         bool ok = true;
-        for (int k = 0; k < T; ++k) ok = (ev[k] = take_event(c)) != nullptr && ok;
+        for (int k = 0; k < TE; ++k) ok = (ev[k] = take_event(c)) != nullptr && ok;
         if (!ok) {
-            for (int k = 0; k < T; ++k)
+            for (int k = 0; k < TE; ++k)
                 if (ev[k]) c->pool->push_back(ev[k]);
             return CDP_ERR_CUDA;
         }
         cudaEventRecord(ev[0], st);
     }
-    if (launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess) {
+    if (launch_prep(L, st) != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;
     }
@@ -248,11 +281,43 @@ int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumul
         cudaGetLastError();
         return CDP_ERR_CUDA;
     }
-    if (ev[T - 1]) {
-        cudaEventRecord(ev[T - 1], st);
-        for (int k = 0; k < T; ++k) c->pending->push_back(ev[k]);
+    if (ev[TE - 1]) {
+        cudaEventRecord(ev[TE - 1], st);
+        for (int k = 0; k < TE; ++k) c->pending->push_back(ev[k]);
     }
     return CDP_OK;
+}
+
+// enqueue one projection on `st` (arguments already checked)
+int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats) {
+    ProbTable* T = new (std::nothrow) ProbTable;
+    if (!T) return CDP_ERR_OOM;
+    int rc = build_table(&p, 1, *T);
+    if (rc == CDP_OK) rc = project_group(c, *T, precision, accumulate, st, want_stats);
+    delete T;
+    return rc;
+}
+
+// enqueue the projections of n problems (arguments already checked, accumulate = 0), grouped by
+// dimension into groups of at most CDP_GROUP problems: a group is one launch of every kernel of the
+// projection
+int project_batch(cdp_ctx* c, const cdp_problem* probs, int n, int precision, cudaStream_t st) {
+    std::vector<const cdp_problem*> list;
+    ProbTable* T = new (std::nothrow) ProbTable;
+    if (!T) return CDP_ERR_OOM;
+    int rc = CDP_OK;
+    for (int dim = 2; dim <= 3 && rc == CDP_OK; ++dim) {
+        list.clear();
+        for (int i = 0; i < n; ++i)
+            if (probs[i].dim == dim) list.push_back(probs + i);
+        for (size_t g0 = 0; g0 < list.size() && rc == CDP_OK; g0 += CDP_GROUP) {
+            const int m = (int)(list.size() - g0 < (size_t)CDP_GROUP ? list.size() - g0 : (size_t)CDP_GROUP);
+            rc = build_table(list.data() + g0, m, *T);
+            if (rc == CDP_OK) rc = project_group(c, *T, precision, 0, st, false);
+        }
+    }
+    delete T;
+    return rc;
 }
 
 }  // namespace cdp
@@ -280,7 +345,7 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
     stats->n_deferred = c->h_ctr->defer_count;
     stats->n_clipped = c->h_ctr->clip_count;
     {
-        const double m = __longlong_as_double_host(c->h_ctr->mmax_bits);
+        const double m = __longlong_as_double_host(c->h_ctr->mmax_bits[0]);
         const double eb = __longlong_as_double_host(c->h_ctr->ebmax_bits);
         stats->accuracy_bound = m > 0.0 ? eb / m : 0.0;
     }
@@ -464,31 +529,47 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
     char key[96];
     snprintf(key, sizeof(key), "sm%d%d-%dsm dim%d %s", major, minor, c->num_sms, p->dim, fp32 ? "fp32mixed" : "fp64");
-    static const int kMults[] = {1, 2, 4, 8};
-    // the cache: lines "<key> <multiplier>", the last entry of a key wins
+    const int slots = cdp::tet_box_slots(fp32);
+    auto report = [&]() {
+        if (chosen) {
+            chosen[0] = c->grid_mult[d3][fp32];
+            chosen[1] = d3 ? (c->max_cells[fp32] ? c->max_cells[fp32] : 1280) : 0;
+            chosen[2] = d3 ? (c->tile_edge[fp32] ? c->tile_edge[fp32] : 18) : 0;
+        }
+    };
+    // the cache: lines "<key> <multiplier> <threshold> <tile edge>", the last entry of a key wins
     if (cache_path) {
         FILE* f = fopen(cache_path, "r");
         if (f) {
-            char line[160];
-            int found = 0;
+            char line[200];
+            int found = 0, fmc = 0, fte = 0;
             while (fgets(line, sizeof(line), f)) {
                 const size_t n = strlen(key);
-                int m = 0;
-                if (strncmp(line, key, n) == 0 && line[n] == ' ' && sscanf(line + n, "%d", &m) == 1 &&
-                    (m == 1 || m == 2 || m == 4 || m == 8))
+                int m = 0, mc = 0, te = 0;
+                if (strncmp(line, key, n) == 0 && line[n] == ' ' && sscanf(line + n, "%d %d %d", &m, &mc, &te) == 3 &&
+                    (m == 1 || m == 2 || m == 4 || m == 8) && mc >= 0 && mc <= slots && (te == 0 || (te >= 4 && te <= 18))) {
                     found = m;
+                    fmc = mc;
+                    fte = te;
+                }
             }
             fclose(f);
             if (found) {
                 c->grid_mult[d3][fp32] = found;
-                if (chosen) *chosen = found;
+                if (d3) {
+                    c->max_cells[fp32] = fmc;
+                    c->tile_edge[fp32] = fte;
+                }
+                report();
                 return CDP_OK;
             }
         }
     }
-    // time the projection of this problem (into its own cell_mass) with every multiplier: one
-    // warm-up call and three timed calls each, on a stream of its own, after the work already
-    // queued on the device (the problem's inputs may still be in flight on another stream)
+    // time the projection of this problem (into its own cell_mass) with each setting: one warm-up
+    // call and three timed calls each, on a stream of its own, after the work already queued on the
+    // device (the problem's inputs may still be in flight on another stream).  The knobs are tuned
+    // one after the other (coordinate descent): the grid multiplier, then (3D) the size-class
+    // threshold, then the tile edge of the large tetrahedra.
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;
@@ -504,22 +585,52 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     }
     const int timing = c->timing;
     c->timing = 0;  // the tuning calls stay out of the per-kernel totals
-    const int before = c->grid_mult[d3][fp32];
-    int best = before;
+    const int before[3] = {c->grid_mult[d3][fp32], c->max_cells[fp32], c->tile_edge[fp32]};
+    auto time_now = [&](float* ms) -> int {
+        int r = cdp::project_enqueue(c, p, precision, 0, st, false);
+        if (r == CDP_OK && cudaEventRecord(e0, st) != cudaSuccess) r = CDP_ERR_CUDA;
+        for (int k = 0; k < 3 && r == CDP_OK; ++k) r = cdp::project_enqueue(c, p, precision, 0, st, false);
+        if (r == CDP_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+            r = CDP_ERR_CUDA;
+        return r;
+    };
+    static const int kMults[] = {1, 2, 4, 8};
+    const int kCells[] = {640, 1280, 2560, slots};
+    static const int kEdges[] = {12, 18};
     float best_ms = 0.f;
+    bool have = false;
     for (int i = 0; i < 4 && rc == CDP_OK; ++i) {
+        const int keep = c->grid_mult[d3][fp32];
         c->grid_mult[d3][fp32] = kMults[i];
-        rc = cdp::project_enqueue(c, p, precision, 0, st, false);
-        if (rc == CDP_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = CDP_ERR_CUDA;
-        for (int r = 0; r < 3 && rc == CDP_OK; ++r) rc = cdp::project_enqueue(c, p, precision, 0, st, false);
         float ms = 0.f;
-        if (rc == CDP_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-            rc = CDP_ERR_CUDA;
-        if (rc == CDP_OK && (i == 0 || ms < best_ms)) {
+        rc = time_now(&ms);
+        if (rc == CDP_OK && (!have || ms < best_ms)) {
             best_ms = ms;
-            best = kMults[i];
+            have = true;
+        } else {
+            c->grid_mult[d3][fp32] = keep;
         }
+    }
+    for (int i = 0; d3 && i < 4 && rc == CDP_OK; ++i) {
+        const int keep = c->max_cells[fp32];
+        c->max_cells[fp32] = kCells[i];
+        float ms = 0.f;
+        rc = time_now(&ms);
+        if (rc == CDP_OK && ms < best_ms)
+            best_ms = ms;
+        else
+            c->max_cells[fp32] = keep;
+    }
+    for (int i = 0; d3 && i < 2 && rc == CDP_OK; ++i) {
+        const int keep = c->tile_edge[fp32];
+        c->tile_edge[fp32] = kEdges[i];
+        float ms = 0.f;
+        rc = time_now(&ms);
+        if (rc == CDP_OK && ms < best_ms)
+            best_ms = ms;
+        else
+            c->tile_edge[fp32] = keep;
     }
     c->timing = timing;
     cudaStreamSynchronize(st);
@@ -527,16 +638,25 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
     cudaGetLastError();
-    c->grid_mult[d3][fp32] = rc == CDP_OK ? best : before;
-    if (rc) return rc;
+    if (rc) {
+        c->grid_mult[d3][fp32] = before[0];
+        c->max_cells[fp32] = before[1];
+        c->tile_edge[fp32] = before[2];
+        return rc;
+    }
+    report();
     if (cache_path) {
         FILE* f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %d\n", key, best);
+            int ch[3] = {0, 0, 0};
+            int* keep_chosen = chosen;
+            chosen = ch;
+            report();
+            chosen = keep_chosen;
+            fprintf(f, "%s %d %d %d\n", key, ch[0], ch[1], ch[2]);
             fclose(f);
         }
     }
-    if (chosen) *chosen = best;
     return CDP_OK;
 }
 int cdp_project_batched(cdp_ctx* c, const cdp_problem* probs, int n, int precision, void* stream) {
@@ -553,11 +673,7 @@ int cdp_project_batched(cdp_ctx* c, const cdp_problem* probs, int n, int precisi
     cudaStream_t st = (cudaStream_t)stream;
     int rc = cdp::reserve_scratch(c, probs, n);
     if (rc) return rc;
-    for (int i = 0; i < n; ++i) {
-        rc = cdp::project_enqueue(c, probs + i, precision, 0, st, false);
-        if (rc) return rc;
-    }
-    return CDP_OK;
+    return cdp::project_batch(c, probs, n, precision, st);
 }
 
 }  // extern "C"

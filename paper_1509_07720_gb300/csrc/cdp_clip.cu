@@ -72,6 +72,8 @@ __device__ int clip_by(const R (*p)[3], int n, R (*q)[3], const R c[3], R c0) {
 struct ClipTet {
     double x[4][3];   // vertex coordinates relative to the anchor cell (grid units, exact)
     double n[4][3];   // unit inward normal of the facet opposite each vertex
+    double nx[4];     // n_f . x of a vertex of facet f
+    double hw[4];     // (|n_0| + |n_1| + |n_2|) / 2: half the spread of n_f . x over a unit cell
     double g[3];      // density gradient (per cell)
     double c[3];      // centroid, and the density there
     double rhoc;
@@ -120,6 +122,21 @@ __device__ __forceinline__ R tet_vol(const R a[3], const R b[3], const R c[3], c
 // then rounded once), so that every coordinate the clipping sees is within a few cells of 0.
 template <typename R>
 __device__ R clip_cell_3d(const ClipTet& T, const double o[3]) {
+    // the cell against each facet plane, in FP64: entirely outside one of them (no piece), or inside
+    // all (the whole cell, whose integral is the density at its centre).  Over the corners of the
+    // unit cell the signed distance n . x - n . x_f ranges over its value at the centre +- hw.
+    {
+        bool inside = true;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const double dc = T.n[f][0] * (o[0] + 0.5) + T.n[f][1] * (o[1] + 0.5) + T.n[f][2] * (o[2] + 0.5) - T.nx[f];
+            if (dc + T.hw[f] < 0.0) return R(0);
+            inside = inside && dc - T.hw[f] >= 0.0;
+        }
+        if (inside)
+            return (R)(T.rhoc + T.g[0] * ((o[0] + 0.5) - T.c[0]) + T.g[1] * ((o[1] + 0.5) - T.c[1]) +
+                       T.g[2] * ((o[2] + 0.5) - T.c[2]));
+    }
     CellFrame<R> F;
 #pragma unroll 1
     for (int k = 0; k < 4; ++k)
@@ -129,28 +146,6 @@ __device__ R clip_cell_3d(const ClipTet& T, const double o[3]) {
         }
     for (int a = 0; a < 3; ++a) F.g[a] = (R)T.g[a];
     F.rc = (R)(T.rhoc + T.g[0] * (o[0] - T.c[0]) + T.g[1] * (o[1] - T.c[1]) + T.g[2] * (o[2] - T.c[2]));
-    // the cell against each facet plane: entirely outside one of them (no piece), or inside all (the
-    // whole cell, whose integral is the density at its centre)
-    bool inside = true;
-#pragma unroll 1
-    for (int f = 0; f < 4; ++f) {
-        const int va = f == 0 ? 1 : 0;
-        const R* nf = F.n[f];
-        R dmax = R(-1e30), dmin = R(1e30);
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            const R d = nf[0] * (R(q & 1) - F.x[va][0]) + nf[1] * (R((q >> 1) & 1) - F.x[va][1]) +
-                        nf[2] * (R(q >> 2) - F.x[va][2]);
-            dmax = d > dmax ? d : dmax;
-            dmin = d < dmin ? d : dmin;
-        }
-        if (dmax < R(0)) return R(0);
-        inside = inside && dmin >= R(0);
-    }
-    if (inside) {
-        const R ctr[3] = {R(0.5), R(0.5), R(0.5)};
-        return rho_at(F, ctr);
-    }
     R bufa[MAXP][3], bufb[MAXP][3];
     R v0[3] = {R(0), R(0), R(0)};
     R r0 = R(0);
@@ -280,15 +275,16 @@ __device__ R clip_cell_2d(const ClipTri& T, const double o[2]) {
 // pieces) goes to the cell of its vertex 0, so the total mass stays exact to FP64 rounding.  The
 // simplices passed the vertex-index and canonicalisation checks when they were listed.
 template <int DIM, typename R>
-__global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(GridDesc g, long long nv, const int* __restrict__ simp,
+__global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(const __grid_constant__ ProbTable T,
                                                                const VertexRec* __restrict__ V,
                                                                const int* __restrict__ list, const unsigned* count,
-                                                               long long cap, double* __restrict__ out) {
+                                                               long long cap) {
     constexpr bool closure = sizeof(R) == 4;
     __shared__ ClipTet st;
     __shared__ ClipTri s2;
     __shared__ double mexact;
     __shared__ int cell0[3];
+    __shared__ int prob;
     __shared__ double wsum[CLIP_THREADS / 32];
     const long long listed = (long long)*(volatile const unsigned*)count;
     const long long n = listed < cap ? listed : cap;
@@ -297,13 +293,17 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(GridDesc g, long 
     for (long long e = blockIdx.x; e < n; e += gridDim.x) {
         __syncthreads();  // the previous simplex is done
         if (threadIdx.x == 0) {
-            const long long s = list[e];
+            const long long sg = list[e];  // in the group's numbering
+            prob = find_simplex(T, sg);
+            const ProbEntry& P = T.p[prob];
+            const GridDesc& g = P.g;
+            const long long s = sg - P.s_off;
             const VertexRec* v[4];
             bool ok = true;
             for (int k = 0; k <= DIM; ++k) {
-                const int id = simp[s * (DIM + 1) + k];
-                ok = ok && id >= 0 && id < nv;
-                v[k] = V + (ok ? id : 0);
+                const int id = P.simplices[s * (DIM + 1) + k];
+                ok = ok && id >= 0 && id < P.nv;
+                v[k] = V + P.v_off + (ok ? id : 0);
             }
             if (DIM == 3) {
                 Tet S;
@@ -316,6 +316,11 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(GridDesc g, long 
                             st.x[k][a] = G.x[k][a] + (double)S.lo[a];
                             st.n[k][a] = G.n[k][a];
                         }
+                    for (int f = 0; f < 4; ++f) {
+                        const int va = f == 0 ? 1 : 0;
+                        st.nx[f] = st.n[f][0] * st.x[va][0] + st.n[f][1] * st.x[va][1] + st.n[f][2] * st.x[va][2];
+                        st.hw[f] = 0.5 * (fabs(st.n[f][0]) + fabs(st.n[f][1]) + fabs(st.n[f][2]));
+                    }
                     for (int a = 0; a < 3; ++a) {
                         st.g[a] = G.g[a];
                         st.c[a] = G.c[a] + (double)S.lo[a];
@@ -348,6 +353,8 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(GridDesc g, long 
         }
         __syncthreads();
         if (DIM == 3 ? !st.ok : !s2.ok) continue;
+        const GridDesc& g = T.p[prob].g;
+        double* const out = T.p[prob].out;
         const int* lo = DIM == 3 ? st.lo : s2.lo;
         const int* hi = DIM == 3 ? st.hi : s2.hi;
         const int* an = DIM == 3 ? st.anchor : s2.anchor;
@@ -389,20 +396,17 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(GridDesc g, long 
 cudaError_t launch_clip(const LaunchArgs& L, int fp32, cudaStream_t st) {
     if (!L.clip_list || !L.ctr) return cudaSuccess;
     const unsigned blocks = (unsigned)(L.num_sms * 4);
-    if (L.g.dim == 3) {
+    const unsigned* cnt = &L.ctr->clip_count;
+    if (L.T.dim == 3) {
         if (fp32)
-            k_project_clip<3, float><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
-                                                                     &L.ctr->clip_count, L.clip_cap, L.out);
+            k_project_clip<3, float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
         else
-            k_project_clip<3, double><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
-                                                                      &L.ctr->clip_count, L.clip_cap, L.out);
+            k_project_clip<3, double><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
     } else {
         if (fp32)
-            k_project_clip<2, float><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
-                                                                     &L.ctr->clip_count, L.clip_cap, L.out);
+            k_project_clip<2, float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
         else
-            k_project_clip<2, double><<<blocks, CLIP_THREADS, 0, st>>>(L.g, L.nv, L.simplices, L.verts, L.clip_list,
-                                                                      &L.ctr->clip_count, L.clip_cap, L.out);
+            k_project_clip<2, double><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
     }
     return cudaGetLastError();
 }

@@ -202,6 +202,7 @@ struct TetGeo {
     int lo[3], hi[3];      // bounding box relative to the tile origin
     int anchor[3];         // absolute cell of the tile origin
     signed char ns[4][3];  // signs of the exact normal components
+    int prob;              // the problem of the batch the tetrahedron belongs to
     double mexact;         // |V| mean(rho) in FP64 (closed form, for the mass closure)
     float mexact_hi;       // (float)mexact
     float mexact_lo;       // mexact - mexact_hi: mexact as an unevaluated sum of two floats
@@ -660,6 +661,7 @@ struct TriGeo {
     int cell[3][2];
     int lo[2], hi[2];
     int anchor[3];  // absolute cell of the tile origin (third entry 0)
+    int prob;       // the problem of the batch the triangle belongs to
     double mexact;  // |V| mean(rho) in FP64
 };
 

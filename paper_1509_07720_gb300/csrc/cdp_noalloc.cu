@@ -13,13 +13,14 @@
 
 namespace cdp {
 int check_problem_args(const cdp_problem* p);
+int build_table(const cdp_problem* const* probs, int n, ProbTable& T);
 }
 
 namespace {
 
 constexpr long long kMaxVerts = CDP_NOALLOC_MAX_VERTS;
 constexpr long long kMaxSimplices = CDP_NOALLOC_MAX_SIMPLICES;
-constexpr size_t kCounterBytes = 256;  // the counters, padded so that the records stay 256-aligned
+constexpr size_t kCounterBytes = 1024;  // the counters, padded so that the records stay 256-aligned
 constexpr long long kGeoBatch = 16384;  // tetrahedra set up per batch
 constexpr size_t kGeoRec = sizeof(cdp::TetGeo<double>) > sizeof(cdp::TetGeo<float>) ? sizeof(cdp::TetGeo<double>)
                                                                                      : sizeof(cdp::TetGeo<float>);
@@ -97,30 +98,9 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
 
     cdp::LaunchArgs L;
     memset(&L, 0, sizeof(L));
-    L.g.dim = p->dim;
-    L.g.periodic = p->periodic ? 1 : 0;
-    long long cells = 1;
-    L.cellvol = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        if (a < p->dim) {
-            L.g.n[a] = p->grid[a];
-            L.g.lo[a] = p->box_lo[a];
-            L.g.inv_h[a] = (double)p->grid[a] / p->box_len[a];
-            L.cellvol *= p->box_len[a] / (double)p->grid[a];
-            cells *= p->grid[a];
-        } else {
-            L.g.n[a] = 1;
-            L.g.lo[a] = 0.0;
-            L.g.inv_h[a] = 1.0;
-        }
-    }
-    L.g.cell_volume = L.cellvol;
-    L.nv = p->n_verts;
-    L.ns = p->n_simplices;
-    L.simplices = p->simplices;
+    if ((rc = cdp::build_table(&p, 1, L.T))) return rc;
     L.ctr = (cdp::Counters*)s->scratch;
     L.verts = (cdp::VertexRec*)(s->scratch + kCounterBytes);
-    L.out = p->cell_mass;
     L.stats = nullptr;
     L.num_sms = s->num_sms;
     int fp32 = 0, accuracy = 1;
@@ -140,9 +120,9 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
 
     // every counter, the error word included, starts at zero on each call
     if (cudaMemsetAsync(s->scratch, 0, sizeof(cdp::Counters), st) != cudaSuccess) return CDP_ERR_CUDA;
-    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)cells * sizeof(double), st) != cudaSuccess)
+    if (!accumulate && cudaMemsetAsync(p->cell_mass, 0, (size_t)L.T.ncells * sizeof(double), st) != cudaSuccess)
         return CDP_ERR_CUDA;
-    if (cdp::launch_prep(L, p->pos[0], p->pos[1], p->dim == 3 ? p->pos[2] : nullptr, p->rho, st) != cudaSuccess ||
+    if (cdp::launch_prep(L, st) != cudaSuccess ||
         cdp::launch_project(L, fp32, st, nullptr, nullptr) != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;

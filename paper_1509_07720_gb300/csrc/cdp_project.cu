@@ -10,15 +10,17 @@
 
 namespace cdp {
 
-__global__ void k_prep_vertices(GridDesc g, long long nv, const double* __restrict__ px,
-                                const double* __restrict__ py, const double* __restrict__ pz,
-                                const double* __restrict__ rho, VertexRec* __restrict__ out,
+// One thread per vertex of the group: world coordinates -> 32-byte fixed-point record (its problem's
+// grid), at the vertex's place in the group's numbering.
+__global__ void k_prep_vertices(const __grid_constant__ ProbTable T, VertexRec* __restrict__ out,
                                 unsigned* __restrict__ flags) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv) return;
-    double p[3] = {px[i], py[i], g.dim == 3 ? pz[i] : 0.0};
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T.nv) return;
+    const ProbEntry& P = T.p[find_vertex(T, i)];
+    const long long v = i - P.v_off;
+    double p[3] = {P.pos[0][v], P.pos[1][v], P.g.dim == 3 ? P.pos[2][v] : 0.0};
     VertexRec r;
-    unsigned f = vertex_to_fixed(g, p, rho[i], r);
+    unsigned f = vertex_to_fixed(P.g, p, P.rho[v], r);
     out[i] = r;
     if (f) atomicOr(flags, f);
 }
@@ -85,7 +87,7 @@ struct WarpAcc {
     int owner;
     int ex, ey;
     bool direct_only;
-    const GridDesc* g;
+    const GridDesc* g;  // the owner's problem's grid
     double* out;
     bool closure;
 
@@ -173,7 +175,7 @@ __device__ __forceinline__ void tri_counts(const TriGeo<R>& G, int n[3]) {
 }
 
 template <int DIM, typename R>
-__device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int own, const GridDesc& g, double* out,
+__device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int own, const ProbTable& T,
                                                     bool closure) {
     const typename GeoOf<DIM, R>::T& G = sh->geo[own];
     WarpAcc<DIM, R> acc;
@@ -183,8 +185,8 @@ __device__ __forceinline__ WarpAcc<DIM, R> make_acc(WarpShared<DIM, R>* sh, int 
     acc.ey = G.hi[1] + 1;
     long long cells = (long long)acc.ex * acc.ey;
     acc.direct_only = cells >= (1ll << KEY_BITS);
-    acc.g = &g;
-    acc.out = out;
+    acc.g = &T.p[G.prob].g;
+    acc.out = T.p[G.prob].out;
     acc.closure = closure;
     return acc;
 }
@@ -215,11 +217,11 @@ __device__ __forceinline__ void tri_phase_item(const TriGeo<R>& G, int ph, int t
 
 // evaluate one queued corner record of phase ph and add its cells to its simplex's pieces
 template <int DIM, typename R>
-__device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned long long r, int ph, const GridDesc& g,
-                                            double* out, bool closure, UnitCounts* cnt) {
+__device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned long long r, int ph, const ProbTable& T,
+                                            bool closure, UnitCounts* cnt) {
     const int own = (int)((r >> 40) & 31);
     const typename GeoOf<DIM, R>::T& G = sh->geo[own];
-    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, closure);
+    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, T, closure);
     (void)ph;
     int v0, v1, v2;
     R val = tri_eval_crossing(G, r, v0, v1, v2);
@@ -239,10 +241,9 @@ struct WarpPass {
 };
 
 template <int DIM, typename R>
-__global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long long ns, long long nv,
-                                                            const int* __restrict__ simp,
+__global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(const __grid_constant__ ProbTable T,
                                                             const VertexRec* __restrict__ V,
-                                                            double* __restrict__ out, Counters* __restrict__ ctr,
+                                                            Counters* __restrict__ ctr,
                                                             UnitCounts* __restrict__ stats, WarpPass wp) {
     static_assert(DIM == 2, "tetrahedra are projected by the kernels of cdp_tetproj.cu");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -259,12 +260,11 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
     UnitCounts* pc = stats ? &cnt : nullptr;
     unsigned long long n0 = 0, nact = 0, nzero = 0;
     double ebm = 0.0;  // the largest error bound of the simplices this lane set up for Franklin's sum
+    long long ns = T.ns;
     if (wp.second) {
         const long long listed = (long long)*(volatile const unsigned*)&ctr->defer_count;
         ns = listed < wp.defer_cap ? listed : wp.defer_cap;
     }
-    const double mfirst = wp.second ? __longlong_as_double((long long)*(volatile const unsigned long long*)&ctr->mmax_bits)
-                                    : 0.0;
     const int cs = CDP_CHUNK;
     const long long nchunks = (ns + cs - 1) / cs;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -275,9 +275,13 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
         bool active = false;
         int n[3] = {0, 0, 0};
         if (lane < cs && item < ns) {
-            const long long s = wp.second ? (long long)wp.defer_list[item] : item;
+            const long long sg = wp.second ? (long long)wp.defer_list[item] : item;  // in the group's numbering
+            const int prob = find_simplex(T, sg);
+            const ProbEntry& P = T.p[prob];
+            const GridDesc& g = P.g;
+            const long long s = sg - P.s_off;
             const VertexRec* v[4];
-            if (!fetch_vertices(simp, s, DIM + 1, nv, V, v)) {
+            if (!fetch_vertices(P.simplices, s, DIM + 1, P.nv, V + P.v_off, v)) {
                 atomicOr(&ctr->flags, CDP_FLAG_INDEX);
             } else {
                 Tri S;
@@ -288,21 +292,24 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                     atomicOr(&ctr->flags, rc);
                 } else if (S.lo[0] == S.hi[0] && S.lo[1] == S.hi[1]) {
                     long long idx = flat_cell(g, S.anchor[0] + S.lo[0], S.anchor[1] + S.lo[1], 0);
-                    if (idx >= 0) atomicAdd(out + idx, tri_mass_cells(S));
+                    if (idx >= 0) atomicAdd(P.out + idx, tri_mass_cells(S));
                     ++n0;
                 } else {
                     TriGeo<R>& G = sh->geo[lane];
                     tri_setup(S, S.lo, G);
+                    G.prob = prob;
                     // accuracy control (AccCtl): first pass, a steep simplex is deferred; second
                     // pass, one whose cancellation bound exceeds the accepted error is clipped
                     const float rmax = fmaxf(fabsf((float)G.rho[0]), fmaxf(fabsf((float)G.rho[1]), fabsf((float)G.rho[2])));
                     const float gn = sqrtf((float)G.g[0] * (float)G.g[0] + (float)G.g[1] * (float)G.g[1]);
                     if (!wp.second && gn > wp.acc.defer_ratio * rmax) {
                         const unsigned at = atomicAdd(&ctr->defer_count, 1u);
-                        if ((long long)at < wp.defer_cap) wp.defer_list[at] = (int)s;
-                    } else if (wp.second && wp.acc.eps_k_grad * (double)gn > wp.acc.tau * mfirst) {
+                        if ((long long)at < wp.defer_cap) wp.defer_list[at] = (int)sg;
+                    } else if (wp.second &&
+                               wp.acc.eps_k_grad * (double)gn >
+                                   wp.acc.tau * __longlong_as_double((long long)*(volatile const unsigned long long*)&ctr->mmax_bits[prob])) {
                         const unsigned at = atomicAdd(&ctr->clip_count, 1u);
-                        if ((long long)at < wp.clip_cap) wp.clip_list[at] = (int)s;
+                        if ((long long)at < wp.clip_cap) wp.clip_list[at] = (int)sg;
                     } else {
                         ebm = fmax(ebm, wp.acc.eps_k_rho * (double)rmax + wp.acc.eps_k_grad * (double)gn);
                         tri_counts(G, n);
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                 const int before = __shfl_sync(0xffffffffu, pre - mine, own);
                 if (u < tot) {
                     const typename GeoOf<DIM, R>::T& G = sh->geo[own];
-                    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, g, out, fp32);
+                    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, T, fp32);
                     QueuePush push{sh->queue, &sh->qtail, (unsigned long long)own << 40};
                     const int t = u - before;
                     tri_phase_item(G, ph, t, acc, push, pc);
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                 // evaluate every full batch of queued records
                 const unsigned tail = *(volatile unsigned*)&sh->qtail;
                 while (tail - head >= 32u) {
-                    eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, g, out, fp32, pc);
+                    eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, T, fp32, pc);
                     head += 32u;
                 }
                 __syncwarp();
@@ -355,7 +362,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
             // the last partial batch of the phase
             const unsigned tail = *(volatile unsigned*)&sh->qtail;
             if ((unsigned)lane < tail - head)
-                eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, g, out, fp32, pc);
+                eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, T, fp32, pc);
             head = tail;
             __syncwarp();
         }
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
                 } else {
                     sh->resid[lane] = 0.0;
                     if (sh->cmax[lane] != 0ull)
-                        atomicAdd(out + (long long)(unsigned)(sh->cmax[lane] & 0xffffffffull), r);
+                        atomicAdd(T.p[sh->geo[lane].prob].out + (long long)(unsigned)(sh->cmax[lane] & 0xffffffffull), r);
                 }
             }
             __syncwarp();
@@ -395,14 +402,15 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(GridDesc g, long
             int own = (int)(k >> KEY_BITS);
             unsigned lk = k & ((1u << KEY_BITS) - 1u);
             const typename GeoOf<DIM, R>::T& G = sh->geo[own];
+            const ProbEntry& P = T.p[G.prob];
             int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
             int x = (int)(lk % (unsigned)ex), r = (int)(lk / (unsigned)ex);
             int y = r % ey, z = r / ey;
-            long long idx = flat_cell(g, G.anchor[0] + x, G.anchor[1] + y, G.anchor[2] + z);
+            long long idx = flat_cell(P.g, G.anchor[0] + x, G.anchor[1] + y, G.anchor[2] + z);
             if (idx < 0) continue;
             double dv = (double)v;
             if (fp32) dv += sh->resid[own] * (double)fabsf((float)v);
-            if (dv != 0.0) atomicAdd(out + idx, dv);
+            if (dv != 0.0) atomicAdd(P.out + idx, dv);
         }
         __syncwarp();
     }
@@ -456,45 +464,44 @@ int resident_blocks(int dim, int fp32) {
 // deferred ones (the grid of the first pass's size: the count is read on the device), clipping.
 template <int DIM, typename R>
 static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t mid) {
-    long long chunks = (L.ns + CDP_CHUNK - 1) / CDP_CHUNK;
+    long long chunks = (L.T.ns + CDP_CHUNK - 1) / CDP_CHUNK;
     long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
     long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     WarpPass wp = {acc_ctl(sizeof(R) == 4), 0, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
     if (!L.accuracy) wp.acc.defer_ratio = 3.0e38f;  // nothing is deferred
-    k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(
-        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, wp);
+    k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(L.T, L.verts, L.ctr, L.stats,
+                                                                                       wp);
     if (mid) cudaEventRecord(mid, st);
     if (L.ev_acc) cudaEventRecord(L.ev_acc, st);
     if (!L.accuracy) return cudaGetLastError();
     cudaError_t e = launch_pass_boundary(L, st);
     if (e != cudaSuccess) return e;
     wp.second = 1;
-    k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(
-        L.g, L.ns, L.nv, L.simplices, L.verts, L.out, L.ctr, L.stats, wp);
+    k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(L.T, L.verts, L.ctr, L.stats,
+                                                                                       wp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_clip(L, sizeof(R) == 4, st);
 }
 
-cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
-                        const double* rho, cudaStream_t st) {
-    if (L.nv > 0) {
-        unsigned blocks = (unsigned)((L.nv + 255) / 256);
-        k_prep_vertices<<<blocks, 256, 0, st>>>(L.g, L.nv, px, py, pz, rho, L.verts, &L.ctr->flags);
+cudaError_t launch_prep(const LaunchArgs& L, cudaStream_t st) {
+    if (L.T.nv > 0) {
+        unsigned blocks = (unsigned)((L.T.nv + 255) / 256);
+        k_prep_vertices<<<blocks, 256, 0, st>>>(L.T, L.verts, &L.ctr->flags);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,
                            cudaEvent_t mid) {
-    if (L.ns == 0) {
+    if (L.T.ns == 0) {
         if (after_setup) cudaEventRecord(after_setup, st);
         if (mid) cudaEventRecord(mid, st);
         if (L.ev_acc) cudaEventRecord(L.ev_acc, st);
         return cudaSuccess;
     }
-    if (L.g.dim == 3) {
+    if (L.T.dim == 3) {
         return launch_tet(L, fp32, st, after_setup, mid);
     }
     if (after_setup) cudaEventRecord(after_setup, st);

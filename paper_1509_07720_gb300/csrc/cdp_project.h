@@ -13,6 +13,54 @@ constexpr int CDP_LOG_WTBL = 10;  // per-warp piece table: 2^10 entries
 constexpr int CDP_WTBL = 1 << CDP_LOG_WTBL;
 constexpr int CDP_QCAP = 512;     // per-warp queue of (corner, cell) records (power of two)
 
+// Problems projected together (cdp_project_batched, cdp_step_batched; a single projection is a
+// group of one): up to CDP_GROUP problems of one dimension per launch.  The kernels take the table
+// by value (a __grid_constant__ parameter, read in place) and map a global vertex, simplex or cell
+// index to its problem by a binary search over the offsets.
+constexpr int CDP_GROUP = 64;
+
+struct ProbEntry {
+    GridDesc g;
+    const int* simplices;  // caller's (dim + 1) indices per simplex, local to the problem
+    double* out;           // the problem's grid
+    const double* pos[3];  // caller's coordinates
+    const double* rho;
+    long long nv, ns;
+    long long v_off;       // first vertex record of the problem (the group's records are concatenated)
+    long long s_off;       // first simplex of the problem in the group's simplex numbering
+    long long c_off;       // first cell of the problem in the group's cell numbering
+};
+
+struct ProbTable {
+    int n;                 // problems (1 .. CDP_GROUP)
+    int dim;
+    long long nv, ns, ncells;  // totals over the group
+    ProbEntry p[CDP_GROUP];
+};
+
+// the problem holding global index i of the numbering whose first indices are off(p) (n >= 1)
+template <class Off>
+__host__ __device__ __forceinline__ int table_find(const ProbTable& T, long long i, Off off) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off(T.p[mid]) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+__host__ __device__ __forceinline__ int find_vertex(const ProbTable& T, long long i) {
+    return table_find(T, i, [](const ProbEntry& e) { return e.v_off; });
+}
+__host__ __device__ __forceinline__ int find_simplex(const ProbTable& T, long long i) {
+    return table_find(T, i, [](const ProbEntry& e) { return e.s_off; });
+}
+__host__ __device__ __forceinline__ int find_cell(const ProbTable& T, long long i) {
+    return table_find(T, i, [](const ProbEntry& e) { return e.c_off; });
+}
+
 // Per-call device counters (zeroed at the start of every projection).
 struct Counters {
     unsigned flags;       // CDP_FLAG_* bits
@@ -22,7 +70,8 @@ struct Counters {
     unsigned long long n_class0, n_small, n_zero, n_big_tiles;
     unsigned clip_count;  // simplices re-projected by clipping (accuracy control)
     unsigned big_first;   // large tetrahedra listed by the first pass (big_count is reused after it)
-    unsigned long long mmax_bits;   // largest |cell mass| after the first pass (FP64 bits, >= 0)
+    unsigned long long mmax_bits[CDP_GROUP];  // per problem: largest |cell mass| after the first pass
+                                              // (FP64 bits, >= 0)
     unsigned long long ebmax_bits;  // largest error bound of a simplex projected by Franklin's sum
 };
 
@@ -66,13 +115,8 @@ __host__ __device__ inline AccCtl acc_ctl(int fp32) {
 }
 
 struct LaunchArgs {
-    GridDesc g;
-    long long nv, ns;
-    const int* simplices;
-    VertexRec* verts;
-    double* out;
-    double cellvol;
-    int* queue;
+    ProbTable T;        // the problems (their grids, inputs and offsets)
+    VertexRec* verts;   // vertex records of the whole group
     Counters* ctr;
     UnitCounts* stats;  // may be null (else two blocks: chunks of the main kernel, tiled large tetrahedra)
     int num_sms;
@@ -92,6 +136,9 @@ struct LaunchArgs {
     int* clip_list;     // simplices projected by clipping (capacity clip_cap)
     long long clip_cap;
     int accuracy;       // 1: accuracy control (AccCtl); 0: every simplex by Franklin's sum
+    int max_cells;      // 3D size-class threshold: largest bounding box (cells) of the main kernel
+                        // (0: the default; at most the block's box slots, tet_box_slots)
+    int tile_edge;      // tile edge (cells) of the large tetrahedra (0: the default; 4 .. 18)
     cudaEvent_t ev_acc; // optional: recorded where the accuracy control starts (timing)
 };
 
@@ -113,16 +160,17 @@ cudaError_t configure_tet();
 int resident_blocks_tet(int fp32);
 // bytes of one geometry record of the tetrahedron kernel
 size_t tet_geo_bytes(int fp32);
-// cells of one tile of a large tetrahedron
+// cells of one tile of a large tetrahedron (of the largest edge)
 size_t tet_tile_cells();
+// box slots of a block of the main kernel (the largest size-class threshold)
+int tet_box_slots(int fp32);
 // tiles of a large tetrahedron whose FP32 pieces a block keeps between the two passes
 constexpr int CDP_TILE_STORE_PER_BLOCK = 64;
 // set-up and main kernel over batches of geo_cap tetrahedra, then the large-tetrahedron kernel;
 // `after_setup` and `mid` (optional) are recorded after the first batch's set-up kernel and before
 // the large-tetrahedron kernel
 cudaError_t launch_tet(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid);
-cudaError_t launch_prep(const LaunchArgs& L, const double* px, const double* py, const double* pz,
-                        const double* rho, cudaStream_t st);
+cudaError_t launch_prep(const LaunchArgs& L, cudaStream_t st);
 // `after_setup` and `mid` (optional) are recorded after the (first) set-up kernel and after the
 // main kernel (3D: before the large-tetrahedron kernel)
 cudaError_t launch_project(const LaunchArgs& L, int fp32, cudaStream_t st, cudaEvent_t after_setup,

@@ -12,7 +12,7 @@
 
 namespace cdp {
 int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n);
-int project_enqueue(cdp_ctx* c, const cdp_problem* p, int precision, int accumulate, cudaStream_t st, bool want_stats);
+int project_batch(cdp_ctx* c, const cdp_problem* probs, int n, int precision, cudaStream_t st);
 int poisson_enqueue(cdp_ctx* c, int dim, const int32_t grid[3], const double box_len[3], double four_pi_G,
                     const double* mass, double* phi, cudaStream_t st);
 int force_enqueue(int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3], const double* phi,
@@ -63,7 +63,16 @@ int enqueue_step(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision
         const cdp_problem& m = probs[i].mesh;
         if ((rc = cdp::vertex_density_enqueue(c, &m, probs[i].simplex_mass, const_cast<double*>(m.rho), st)))
             return rc;
-        if ((rc = cdp::project_enqueue(c, &m, precision, 0, st, false))) return rc;
+    }
+    // the projections of all the meshes, grouped (one launch of each projection kernel per group of
+    // up to 64 meshes of one dimension)
+    {
+        std::vector<cdp_problem> meshes((size_t)n);
+        for (int i = 0; i < n; ++i) meshes[(size_t)i] = probs[i].mesh;
+        if ((rc = cdp::project_batch(c, meshes.data(), n, precision, st))) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem& m = probs[i].mesh;
         if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st)))
             return rc;
         if ((rc = cdp::force_enqueue(m.dim, m.grid, m.box_lo, m.box_len, probs[i].phi, m.n_verts, m.pos,

@@ -55,11 +55,13 @@ constexpr int TB_OWN_BITS = 7;              // tetrahedron-of-chunk index in a q
 constexpr unsigned FULL = 0xffffffffu;
 static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS, "chunk index does not fit");
 
-// largest bounding box (cells) projected by the main kernel, and the block's box slots (FP32: sized
+// default largest bounding box (cells) projected by the main kernel (the size-class threshold; the
+// launch may choose another up to the block's box slots), and the block's box slots (FP32: sized
 // with the rest of the block's shared memory for three resident blocks per SM)
 constexpr int TB_MAX_CELLS = 1280;
-// tile edge (cells) of a tetrahedron whose bounding box exceeds TB_MAX_CELLS (the same in both
-// precisions, so that both take the same decisions tile by tile), and the x lines of one tile
+// largest tile edge (cells) of a tetrahedron whose bounding box exceeds the threshold (the launch
+// chooses its edge up to this; both precisions take the same default, so that they take the same
+// decisions tile by tile), and the x lines of one tile of that edge
 constexpr int TB_TE = 18;
 constexpr int TB_RUNS = (TB_TE + 1) * (TB_TE + 1);
 constexpr int TB_TILE_CELLS = TB_TE * TB_TE * TB_TE;
@@ -73,6 +75,7 @@ static_assert(BoxCap<float>::value >= TB_MAX_CELLS, "one tetrahedron's box must 
 // Tiling state of a block's current large tetrahedron: uniform over the block, written by thread 0
 // only, between barriers.
 struct BigState {
+    int te;             // tile edge (cells) of this launch
     int ext[3], nt[3];  // bounding-box extent (cells) and tiles along each axis
     int ntiles, tile;   // tiles, next tile; ntiles < 0: the list is exhausted
     int live;           // tiles set up so far in this pass (those the tetrahedron may meet)
@@ -85,6 +88,7 @@ struct BigState {
 struct BigPass {
     AccCtl acc;
     int second;
+    int te;             // tile edge (cells), at most TB_TE
     int* defer_list;
     long long defer_cap;
     int* clip_list;
@@ -881,9 +885,9 @@ __device__ __forceinline__ void acc_terms(const TetGeo<R>& G, float& rmax, float
     gn = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
 }
 
-// The largest |cell mass| after the first pass (0 before it has been taken).
-__device__ __forceinline__ double first_pass_max(const Counters* ctr) {
-    return __longlong_as_double((long long)*(volatile const unsigned long long*)&ctr->mmax_bits);
+// The largest |cell mass| of problem p after the first pass (0 before it has been taken).
+__device__ __forceinline__ double first_pass_max(const Counters* ctr, int p) {
+    return __longlong_as_double((long long)*(volatile const unsigned long long*)&ctr->mmax_bits[p]);
 }
 
 // Where the set-up sends a simplex whose box fits the chunks: 0 the chunks (Franklin's sum in this
@@ -894,7 +898,7 @@ __device__ __forceinline__ int acc_route(const TetGeo<R>& G, const AccCtl& acc, 
     float rmax, gn;
     acc_terms(G, rmax, gn);
     if (!second) return gn > acc.defer_ratio * rmax ? 1 : 0;
-    return acc.eps_k_grad * (double)gn > acc.tau * first_pass_max(ctr) ? 2 : 0;
+    return acc.eps_k_grad * (double)gn > acc.tau * first_pass_max(ctr, G.prob) ? 2 : 0;
 }
 
 __device__ __forceinline__ void list_append(int* list, long long cap, unsigned* count, int s) {
@@ -907,9 +911,11 @@ __device__ __forceinline__ void list_append(int* list, long long cap, unsigned* 
 // piece sums of FLUSH_SUM_ONLY / FLUSH_SCALED are added into `sums` by thread 0, and FLUSH_SUM_ONLY
 // also copies the box to `store` when it is given.  With
 // `whole` (one unit, a tile) the whole block flushes that unit's box; otherwise each warp flushes
-// the boxes of every TB_WARPS-th unit.
+// the boxes of every TB_WARPS-th unit.  Each unit's grid is its problem's (T); the units of a round of
+// the first pass belong to one problem (a problem's tetrahedra start a new chunk), so the round's
+// closure keeps every problem's mass.
 template <typename R>
-__device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g, double* out, bool in, int pre_box,
+__device__ __forceinline__ void round_flush(TetShared<R>* sh, const ProbTable& T, bool in, int pre_box,
                                             int mode, float scale, bool whole, float* sums, float* store) {
     constexpr bool fp32 = sizeof(R) == 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -958,9 +964,10 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
             int t = 0;
             while (t < TB_NT - 1 && sh->boff[t] < 0) ++t;
             const TetGeo<R>& G = sh->geo[t];
+            const ProbEntry& P = T.p[G.prob];
             const long long idx =
-                flat_cell(g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1], G.anchor[2] + G.cell[0][2]);
-            if (idx >= 0) atomicAdd(out + idx, (double)resid);
+                flat_cell(P.g, G.anchor[0] + G.cell[0][0], G.anchor[1] + G.cell[0][1], G.anchor[2] + G.cell[0][2]);
+            if (idx >= 0) atomicAdd(P.out + idx, (double)resid);
         }
     }
     const int gsize = whole ? TB_THREADS : 32, glane = whole ? tid : lane;
@@ -970,7 +977,8 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
         const int base = sh->boff[t];
         if (base < 0) continue;
         const TetGeo<R>& G = sh->geo[t];
-
+        const GridDesc& g = T.p[G.prob].g;
+        double* const out = T.p[G.prob].out;
         const int ex = sh->td[t][0], ey = sh->td[t][1], ez = sh->td[t][2];
         const int size = ex * ey * ez;
         const int ax = G.anchor[0], ay = G.anchor[1], az = G.anchor[2];
@@ -1059,7 +1067,9 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
 
 // One pass of the set-up over the tetrahedra of one batch (thread i < nb for the batch's tetrahedron
 // i):
-//  first pass  (list == null) the batch is [s0, s0 + nb) of the mesh.  Canonicalise (exact
+// Indices are in the group's simplex numbering (T: each problem's simplices from its s_off, a
+// multiple of TB_NT; the indices between two problems are no simplex and get need = 0).
+//  first pass  (list == null) the batch is [s0, s0 + nb) of the numbering.  Canonicalise (exact
 //              orientation, periodic unwrap, cells); a tetrahedron inside one cell deposits its
 //              mass at once (Algorithm 2, step 1); one whose bounding box exceeds TB_MAX_CELLS is
 //              listed as large (k_project_big); one with a steep gradient is deferred; every other
@@ -1070,12 +1080,12 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const GridDesc& g,
 //              list when their cancellation bound exceeds the accepted error (AccCtl).
 // need[i] = 0 for every tetrahedron with nothing left for the chunks.
 template <typename R>
-__global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, long long nb, long long nv,
-                                                   const int* __restrict__ simp, const VertexRec* __restrict__ V,
-                                                   double* __restrict__ out, Counters* __restrict__ ctr,
+__global__ void __launch_bounds__(128) k_tet_setup(const __grid_constant__ ProbTable T, long long s0, long long nb,
+                                                   const VertexRec* __restrict__ V, Counters* __restrict__ ctr,
                                                    TetGeo<R>* __restrict__ geo, int* __restrict__ need,
                                                    int* __restrict__ big_list, long long big_cap, int count,
-                                                   const int* __restrict__ list, AccCtl acc, int* __restrict__ defer_list,
+                                                   int max_cells, const int* __restrict__ list, AccCtl acc,
+                                                   int* __restrict__ defer_list,
                                                    long long defer_cap, int* __restrict__ clip_list, long long clip_cap) {
     // the block's records are assembled in shared memory and written out with coalesced stores
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1094,16 +1104,22 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
     const long long i = first + threadIdx.x;
     __syncthreads();  // the stage is free
     if (i < nb) {
-        const long long s = second ? (long long)list[s0 + i] : s0 + i;
+        const long long sg = second ? (long long)list[s0 + i] : s0 + i;  // in the group's numbering
+        const int prob = find_simplex(T, sg);
+        const ProbEntry& P = T.p[prob];
+        const GridDesc& g = P.g;
+        const long long s = sg - P.s_off;
         int my_need = 0;
         const VertexRec* v[4];
-        bool ok = true;
-        for (int k = 0; k < 4; ++k) {
-            const int id = __ldg(simp + s * 4 + k);
-            if (id < 0 || id >= nv) ok = false;
-            v[k] = V + (ok ? id : 0);
+        bool ok = s < P.ns;
+        for (int k = 0; k < 4 && ok; ++k) {
+            const int id = __ldg(P.simplices + s * 4 + k);
+            if (id < 0 || id >= P.nv) ok = false;
+            v[k] = V + P.v_off + (ok ? id : 0);
         }
-        if (!ok) {
+        if (s >= P.ns) {
+            // (an index between two problems)
+        } else if (!ok) {
             atomicOr(&ctr->flags, CDP_FLAG_INDEX);
         } else {
             Tet S;
@@ -1115,20 +1131,21 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
             } else if (S.lo[0] == S.hi[0] && S.lo[1] == S.hi[1] && S.lo[2] == S.hi[2]) {
                 const long long idx =
                     flat_cell(g, S.anchor[0] + S.lo[0], S.anchor[1] + S.lo[1], S.anchor[2] + S.lo[2]);
-                if (idx >= 0) atomicAdd(out + idx, tet_mass_cells(S));
+                if (idx >= 0) atomicAdd(P.out + idx, tet_mass_cells(S));
                 n_single = 1;
             } else {
                 const long long cells =
                     (long long)(S.hi[0] - S.lo[0] + 1) * (S.hi[1] - S.lo[1] + 1) * (S.hi[2] - S.lo[2] + 1);
-                if (cells > TB_MAX_CELLS) {
-                    list_append(big_list, big_cap, &ctr->big_count, (int)s);
+                if (cells > max_cells) {
+                    list_append(big_list, big_cap, &ctr->big_count, (int)sg);
                 } else {
                     tet_setup(S, S.lo, stage[threadIdx.x]);
+                    stage[threadIdx.x].prob = prob;
                     const int route = acc_route(stage[threadIdx.x], acc, second, ctr);
                     if (route == 1) {
-                        list_append(defer_list, defer_cap, &ctr->defer_count, (int)s);
+                        list_append(defer_list, defer_cap, &ctr->defer_count, (int)sg);
                     } else if (route == 2) {
-                        list_append(clip_list, clip_cap, &ctr->clip_count, (int)s);
+                        list_append(clip_list, clip_cap, &ctr->clip_count, (int)sg);
                     } else {
                         my_need = (int)cells;
                         n_box = 1;
@@ -1165,18 +1182,37 @@ __global__ void __launch_bounds__(128) k_tet_setup(GridDesc g, long long s0, lon
     }
 }
 
-// Between the two passes: the largest |cell mass| of the grid (after the first pass) into
-// ctr->mmax_bits, and (block 0) the first pass's count of large tetrahedra kept in big_first while
-// the list of large tetrahedra is emptied for the second pass.
-__global__ void __launch_bounds__(256) k_pass_boundary(const double* __restrict__ out, long long ncells,
-                                                        Counters* __restrict__ ctr) {
+// Between the two passes: the largest |cell mass| of every problem's grid (after the first pass)
+// into ctr->mmax_bits[p], and (block 0) the first pass's count of large tetrahedra kept in
+// big_first while the list of large tetrahedra is emptied for the second pass.  The cells of all
+// the grids are taken in the group's cell numbering.
+__global__ void __launch_bounds__(256) k_pass_boundary(const __grid_constant__ ProbTable T, Counters* __restrict__ ctr) {
+    // each thread: a running maximum while its cells stay in one problem
     double m = 0.0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
-         c += (long long)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(out[c]));
+    int pcur = -1;
+    long long pbeg = 0, pend = 0;
+#pragma unroll 1
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < T.ncells;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (c < pbeg || c >= pend) {
+            if (pcur >= 0 && m > 0.0) atomicMax(&ctr->mmax_bits[pcur], (unsigned long long)__double_as_longlong(m));
+            pcur = find_cell(T, c);
+            pbeg = T.p[pcur].c_off;
+            pend = pcur + 1 < T.n ? T.p[pcur + 1].c_off : T.ncells;
+            m = 0.0;
+        }
+        m = fmax(m, fabs(T.p[pcur].out[c - pbeg]));
+    }
+    // a warp whose lanes ended in one problem reduces first
+    const int p0 = __shfl_sync(FULL, pcur, 0);
+    if (__all_sync(FULL, pcur == p0)) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&ctr->mmax_bits, (unsigned long long)__double_as_longlong(m));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+        if ((threadIdx.x & 31) == 0 && p0 >= 0 && m > 0.0)
+            atomicMax(&ctr->mmax_bits[p0], (unsigned long long)__double_as_longlong(m));
+    } else if (pcur >= 0 && m > 0.0) {
+        atomicMax(&ctr->mmax_bits[pcur], (unsigned long long)__double_as_longlong(m));
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->big_first = ctr->big_count;
         ctr->big_count = 0u;
@@ -1191,8 +1227,9 @@ __global__ void __launch_bounds__(256) k_pass_boundary(const double* __restrict_
 template <typename R>
 __device__ __forceinline__ bool tile_misses(const TetGeo<R>& B, const BigState& b, int t) {
     const int i0 = t % b.nt[0], r = t / b.nt[0], i1 = r % b.nt[1], i2 = r / b.nt[1];
-    const int lo[3] = {i0 * TB_TE, i1 * TB_TE, i2 * TB_TE};
-    const int hi[3] = {min(lo[0] + TB_TE, b.ext[0]), min(lo[1] + TB_TE, b.ext[1]), min(lo[2] + TB_TE, b.ext[2])};
+    const int te = b.te;
+    const int lo[3] = {i0 * te, i1 * te, i2 * te};
+    const int hi[3] = {min(lo[0] + te, b.ext[0]), min(lo[1] + te, b.ext[1]), min(lo[2] + te, b.ext[2])};
     bool miss = false;
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
@@ -1239,7 +1276,7 @@ __device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int
         return false;
     }
     const int i0 = t % b.nt[0], r = t / b.nt[0], i1 = r % b.nt[1], i2 = r / b.nt[1];
-    const int dT[3] = {i0 * TB_TE, i1 * TB_TE, i2 * TB_TE};
+    const int dT[3] = {i0 * b.te, i1 * b.te, i2 * b.te};
     TetGeo<R>& G = sh->geo[0];
     {
         constexpr int W = sizeof(TetGeo<R>) / 8;
@@ -1261,7 +1298,7 @@ __device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int
         G.lo[a] = B.lo[a] - d;
         G.hi[a] = B.hi[a] - d;
         G.anchor[a] = B.anchor[a] + d;
-        sh->td[0][a] = min(TB_TE, pick3(b.ext[0], b.ext[1], b.ext[2], a) - d);
+        sh->td[0][a] = min(b.te, pick3(b.ext[0], b.ext[1], b.ext[2], a) - d);
     }
     __syncwarp();
     if (lane == 0) {
@@ -1308,13 +1345,15 @@ __device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int
 //   second pass, one whose cancellation bound exceeds the accepted error goes to the clip list.
 //   Either way it gets no tile (ntiles = 0) and the next one is taken at the next round.
 template <typename R>
-__device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g, long long nv, const int* simp,
-                                            const VertexRec* V, const int* big_list, long long big_cap,
-                                            double* out, Counters* ctr, const BigPass& bp) {
+__device__ __forceinline__ void big_advance(TetShared<R>* sh, const ProbTable& T, const VertexRec* V,
+                                            const int* big_list, long long big_cap, Counters* ctr,
+                                            const BigPass& bp) {
     constexpr bool fp32 = sizeof(R) == 4;
     BigState& b = sh->bs;
     if (fp32 && b.ntiles > 0) {
         const TetGeo<R>& G = sh->big0;
+        const GridDesc& g = T.p[G.prob].g;
+        double* const out = T.p[G.prob].out;
         if (b.pass == 0) {
             b.scale = b.s[2] > 0.f ? ((G.mexact_hi - b.s[0]) + (G.mexact_lo - b.s[1])) / b.s[2] : 0.f;
             b.pass = 1;
@@ -1338,25 +1377,29 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
         b.ntiles = -1;
         return;
     }
-    const long long s = big_list[bi];
+    const long long sg = big_list[bi];  // in the group's numbering
+    const int prob = find_simplex(T, sg);
+    const ProbEntry& P = T.p[prob];
+    const long long s = sg - P.s_off;
     const VertexRec* v[4];
     bool ok = true;
     for (int k = 0; k < 4; ++k) {
-        const int id = __ldg(simp + s * 4 + k);
-        ok = ok && id >= 0 && id < nv;
-        v[k] = V + (ok ? id : 0);
+        const int id = __ldg(P.simplices + s * 4 + k);
+        ok = ok && id >= 0 && id < P.nv;
+        v[k] = V + P.v_off + (ok ? id : 0);
     }
     // (the set-up kernel listed it after the same checks: no tile when they fail)
     Tet S;
-    bool good = ok && canon_tet<1>(g, v, S) == 0;
+    bool good = ok && canon_tet<1>(P.g, v, S) == 0;
     if (good) {
         tet_setup<R, 1>(S, S.lo, sh->big0);
+        sh->big0.prob = prob;
         const int route = acc_route(sh->big0, bp.acc, bp.second != 0, ctr);
         if (route == 1) {
-            list_append(bp.defer_list, bp.defer_cap, &ctr->defer_count, (int)s);
+            list_append(bp.defer_list, bp.defer_cap, &ctr->defer_count, (int)sg);
             good = false;
         } else if (route == 2) {
-            list_append(bp.clip_list, bp.clip_cap, &ctr->clip_count, (int)s);
+            list_append(bp.clip_list, bp.clip_cap, &ctr->clip_count, (int)sg);
             good = false;
         } else {
             float rmax, gn;
@@ -1366,9 +1409,10 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
         }
     }
     int n = 1;
+    b.te = bp.te;
     for (int a = 0; a < 3; ++a) {
         b.ext[a] = good ? S.hi[a] - S.lo[a] + 1 : 0;
-        b.nt[a] = (b.ext[a] + TB_TE - 1) / TB_TE;
+        b.nt[a] = (b.ext[a] + b.te - 1) / b.te;
         n *= b.nt[a];
     }
     b.ntiles = n;
@@ -1387,8 +1431,8 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const GridDesc& g,
 //   the deferred list, nb capped by the list's count on the device), each closed on its own.
 template <typename R, bool STATS, bool SECOND>
 __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
-    k_project_tet(GridDesc g, long long nb, const TetGeo<R>* __restrict__ geo, const int* __restrict__ need_in,
-                  double* __restrict__ out, UnitCounts* __restrict__ stats, const Counters* __restrict__ ctr,
+    k_project_tet(const __grid_constant__ ProbTable T, long long nb, const TetGeo<R>* __restrict__ geo,
+                  const int* __restrict__ need_in, UnitCounts* __restrict__ stats, const Counters* __restrict__ ctr,
                   long long list_off, long long list_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int BOX = BoxCap<R>::value;
@@ -1434,8 +1478,8 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             pending = pending && !in;
             if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
             round_phases<R, STATS, false>(sh, in, n_cross, n_lines, cnt, pc);
-            round_flush<R>(sh, g, out, in, pre_box, SECOND ? FLUSH_CLOSE_UNITS : FLUSH_CLOSE_ROUND, 0.f, false,
-                           nullptr, nullptr);
+            round_flush<R>(sh, T, in, pre_box, SECOND ? FLUSH_CLOSE_UNITS : FLUSH_CLOSE_ROUND, 0.f, false, nullptr,
+                           nullptr);
         }
     }
     if (STATS) {
@@ -1452,10 +1496,9 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
 // two passes over a tetrahedron's tiles (the pieces' sums, then the flush with its closure scale).
 template <typename R, bool STATS>
 __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
-    k_project_big(GridDesc g, long long nv, const int* __restrict__ simp, const VertexRec* __restrict__ V,
-                  const int* __restrict__ big_list, long long big_cap, double* __restrict__ out,
-                  float* __restrict__ tile_store, int store_tiles, Counters* __restrict__ ctr,
-                  UnitCounts* __restrict__ stats, BigPass bp) {
+    k_project_big(const __grid_constant__ ProbTable T, const VertexRec* __restrict__ V,
+                  const int* __restrict__ big_list, long long big_cap, float* __restrict__ tile_store, int store_tiles,
+                  Counters* __restrict__ ctr, UnitCounts* __restrict__ stats, BigPass bp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
     constexpr int BOX = BoxCap<R>::value;
@@ -1478,7 +1521,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         const bool advance = sh->bs.tile >= sh->bs.ntiles;
         __syncthreads();  // every thread has read the state; the previous round is done
         if (advance) {
-            if (tid == 0) big_advance<R>(sh, g, nv, simp, V, big_list, big_cap, out, ctr, bp);
+            if (tid == 0) big_advance<R>(sh, T, V, big_list, big_cap, ctr, bp);
             __syncthreads();
             if (sh->bs.ntiles < 0) break;
             continue;
@@ -1516,7 +1559,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             if (STATS && counted) cnt.a += na;
             __syncthreads();
         }
-        round_flush<R>(sh, g, out, in, pre_box, mode, sh->bs.scale, true, sh->bs.s, pass == 0 ? slot : nullptr);
+        round_flush<R>(sh, T, in, pre_box, mode, sh->bs.scale, true, sh->bs.s, pass == 0 ? slot : nullptr);
     }
     if (STATS) {
         if (cnt.a) atomicAdd(&stats->a, cnt.a);
@@ -1577,6 +1620,8 @@ size_t tet_geo_bytes(int fp32) { return fp32 ? sizeof(TetGeo<float>) : sizeof(Te
 
 size_t tet_tile_cells() { return TB_TILE_CELLS; }
 
+int tet_box_slots(int fp32) { return fp32 ? BoxCap<float>::value : BoxCap<double>::value; }
+
 template <typename R>
 static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_t after_setup, cudaEvent_t mid) {
     const long long batch = L.geo_cap > 0 ? L.geo_cap : 1;
@@ -1585,6 +1630,9 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     if (!L.accuracy) acc.defer_ratio = 3.0e38f;  // nothing is deferred
     TetGeo<R>* G = reinterpret_cast<TetGeo<R>*>(L.geo);
     const size_t stage = 128 * sizeof(TetGeo<R>);
+    // the size-class threshold (at most the block's box slots) and the tile edge (at most TB_TE)
+    const int max_cells = L.max_cells > 0 && L.max_cells <= BoxCap<R>::value ? L.max_cells : TB_MAX_CELLS;
+    const int te = L.tile_edge >= 4 && L.tile_edge <= TB_TE ? L.tile_edge : TB_TE;
     // the main kernel over a batch of nb records (second pass: nb capped on the device)
     auto chunks = [&](long long nb, int second, long long off) {
         long long blocks = (nb + TB_NT - 1) / TB_NT;
@@ -1594,17 +1642,16 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
         const size_t sm = tet_shared_bytes<R>();
         if (second) {
             if (L.stats)
-                k_project_tet<R, true, true><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, L.stats, L.ctr, off,
+                k_project_tet<R, true, true><<<b, TB_THREADS, sm, st>>>(L.T, nb, G, L.need, L.stats, L.ctr, off,
                                                                        L.defer_cap);
             else
-                k_project_tet<R, false, true><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, nullptr, L.ctr, off,
+                k_project_tet<R, false, true><<<b, TB_THREADS, sm, st>>>(L.T, nb, G, L.need, nullptr, L.ctr, off,
                                                                         L.defer_cap);
         } else {
             if (L.stats)
-                k_project_tet<R, true, false><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, L.stats, L.ctr, 0, 0);
+                k_project_tet<R, true, false><<<b, TB_THREADS, sm, st>>>(L.T, nb, G, L.need, L.stats, L.ctr, 0, 0);
             else
-                k_project_tet<R, false, false><<<b, TB_THREADS, sm, st>>>(L.g, nb, G, L.need, L.out, nullptr, L.ctr, 0,
-                                                                         0);
+                k_project_tet<R, false, false><<<b, TB_THREADS, sm, st>>>(L.T, nb, G, L.need, nullptr, L.ctr, 0, 0);
         }
     };
     // the large tetrahedra of the list (their number is read on the device; a block that finds the
@@ -1616,22 +1663,21 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
                                 ? L.tile_store_per_block
                                 : 0;
     auto big = [&](int second) {
-        const BigPass bp = {acc, second, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
+        const BigPass bp = {acc, second, te, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
         if (L.stats)
             k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-                L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
-                L.stats + 1, bp);
+                L.T, L.verts, L.big_list, L.big_cap, L.tile_store, store_tiles, L.ctr, L.stats + 1, bp);
         else
             k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
-                L.g, L.nv, L.simplices, L.verts, L.big_list, L.big_cap, L.out, L.tile_store, store_tiles, L.ctr,
-                nullptr, bp);
+                L.T, L.verts, L.big_list, L.big_cap, L.tile_store, store_tiles, L.ctr, nullptr, bp);
     };
     // first pass: every tetrahedron, batch by batch; steep ones are deferred
-    for (long long s0 = 0; s0 < L.ns; s0 += batch) {
-        const long long nb = L.ns - s0 < batch ? L.ns - s0 : batch;
+    const long long ns = L.T.ns;  // (the group's numbering, gaps between problems included)
+    for (long long s0 = 0; s0 < ns; s0 += batch) {
+        const long long nb = ns - s0 < batch ? ns - s0 : batch;
         k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, stage, st>>>(
-            L.g, s0, nb, L.nv, L.simplices, L.verts, L.out, L.ctr, G, L.need, L.big_list, L.big_cap, L.stats != nullptr,
-            nullptr, acc, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
+            L.T, s0, nb, L.verts, L.ctr, G, L.need, L.big_list, L.big_cap, L.stats != nullptr, max_cells, nullptr, acc,
+            L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
         if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
         chunks(nb, 0, 0);
     }
@@ -1643,14 +1689,13 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     if (e != cudaSuccess) return e;
     // second pass: the deferred tetrahedra (at most min(ns, defer_cap)), batch by batch of the
     // geometry buffer, then the deferred large ones, then those sent to clipping
-    const long long most = L.ns < L.defer_cap ? L.ns : L.defer_cap;
+    const long long most = ns < L.defer_cap ? ns : L.defer_cap;
     for (long long s0 = 0; s0 < most; s0 += batch) {
         long long blocks = (batch + 127) / 128;
         if (blocks > (long long)L.num_sms * 16) blocks = (long long)L.num_sms * 16;
-        k_tet_setup<R><<<(unsigned)blocks, 128, stage, st>>>(L.g, s0, batch, L.nv, L.simplices, L.verts, L.out, L.ctr, G,
-                                                            L.need, L.big_list, L.big_cap, L.stats != nullptr,
-                                                            L.defer_list, acc, L.defer_list, L.defer_cap, L.clip_list,
-                                                            L.clip_cap);
+        k_tet_setup<R><<<(unsigned)blocks, 128, stage, st>>>(L.T, s0, batch, L.verts, L.ctr, G, L.need, L.big_list,
+                                                            L.big_cap, L.stats != nullptr, max_cells, L.defer_list,
+                                                            acc, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
         chunks(batch, 1, s0);
     }
     big(1);
@@ -1660,11 +1705,10 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
 
 // the largest |cell mass| after the first pass, and the list of large tetrahedra emptied
 cudaError_t launch_pass_boundary(const LaunchArgs& L, cudaStream_t st) {
-    long long cells = 1;
-    for (int a = 0; a < L.g.dim; ++a) cells *= L.g.n[a];
-    long long blocks = (cells + 255) / 256;
+    long long blocks = (L.T.ncells + 255) / 256;
     if (blocks > (long long)L.num_sms * 8) blocks = (long long)L.num_sms * 8;
-    k_pass_boundary<<<(unsigned)blocks, 256, 0, st>>>(L.out, cells, L.ctr);
+    if (blocks < 1) blocks = 1;
+    k_pass_boundary<<<(unsigned)blocks, 256, 0, st>>>(L.T, L.ctr);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
-"""cdp_autotune: the launch-shape tuning of the main kernel's grid, its cache file, and projections
-made with the tuned grid (they agree with those of an untuned context to the parity tolerances)."""
+"""cdp_autotune: the launch-shape tuning (grid multiplier, size-class threshold, tile edge of the large
+tetrahedra), its cache file, and projections made with the tuned shape (they agree with those of an
+untuned context to the parity tolerances)."""
 import numpy as np
 import pytest
 
@@ -29,20 +30,29 @@ def _dev(mesh):
             torch.from_numpy(np.ascontiguousarray(mesh.rho)).to(d))
 
 
+def _mesh(name):
+    if name == "c2_16":
+        return mg.make_config("c2", 16)
+    if name == "rand3d_large":  # tetrahedra of a few to a hundred thousand cells: both size classes
+        return mg.random_simplices(3, 60, 96, 12.0, np.random.default_rng(6))
+    return mg.random_simplices(2, 600, 32, 3.0, np.random.default_rng(5))
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
-@pytest.mark.parametrize("name", ["c2_16", "rand2d"])
+@pytest.mark.parametrize("name", ["c2_16", "rand3d_large", "rand2d"])
 def test_autotune_then_project(pkg, tmp_path, name, prec):
-    mesh = mg.make_config("c2", 16) if name == "c2_16" else mg.random_simplices(2, 600, 32, 3.0,
-                                                                                  np.random.default_rng(5))
+    mesh = _mesh(name)
     pos, simp, rho = _dev(mesh)
     cache = tmp_path / "tune.txt"
     tuned = pkg.Projector(0)
     try:
         m = tuned.autotune(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, mesh.periodic, precision=prec,
                            cache_path=str(cache))
-        assert m in (1, 2, 4, 8)
+        assert m[0] in (1, 2, 4, 8)
+        if mesh.dim == 3:
+            assert m[1] in (640, 1280, 2560, 6144 if prec == 1 else 10240) and m[2] in (12, 18)
         lines = cache.read_text().splitlines()
-        assert len(lines) == 1 and lines[0].endswith(f" {m}") and f"dim{mesh.dim}" in lines[0]
+        assert len(lines) == 1 and lines[0].endswith(" %d %d %d" % m) and f"dim{mesh.dim}" in lines[0]
         # a second context takes the cached choice without timing (the file is not appended to)
         other = pkg.Projector(0)
         try:

@@ -314,3 +314,36 @@ def _c4_full():
     if "m" not in _C4:
         _C4["m"] = mg.make_config("c4")
     return _C4["m"]
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])
+def test_batched_matches_single(proj, prec):
+    """cdp_project_batched projects its problems in groups (one launch of each kernel per group of up
+    to 64 problems of one dimension): every problem's grid equals its projection alone, for a mix of
+    2D and 3D problems (tiled and deferred/clipped simplices included) and more than one group."""
+    import paper_1509_07720_gb300 as pkg
+
+    names = ["c1a", "c2_16", "rand3d_mid", "rand2d", "rand3d_tiled", "aligned_kuhn_8", "box_linear_rho",
+             "slivers_3d", "slivers_2d", "zero_volume_3d", "rand3d_huge", "c4_4"]
+    meshes = [CASES[n] for n in names]
+    rng = np.random.default_rng(90)
+    meshes += [mg.random_simplices(3, 30, 16, 2.0, rng) for _ in range(66)]  # 3D: more than one group
+    d = torch.device("cuda:0")
+    keep, probs, outs = [], [], []
+    for m in meshes:
+        pos, simp, rho = _dev(m)
+        out = torch.full(m.grid, 3.0, dtype=torch.float64, device=d)  # must be overwritten
+        probs.append(pkg.Projector.make_problem(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, out))
+        keep.append((pos, simp, rho))
+        outs.append(out)
+    st = torch.cuda.current_stream().cuda_stream
+    assert pkg.cdp_project_batched(proj._ctx, probs, prec, st) == 0
+    torch.cuda.synchronize()
+    proj.check()
+    tol = 1e-13 if prec == 0 else 1e-6
+    for i, m in enumerate(meshes):
+        want = _run(proj, m, prec)
+        got = outs[i].cpu().numpy()
+        scale = float(np.max(np.abs(want)))
+        assert np.max(np.abs(got - want)) <= tol * scale, i
+        assert abs(got.sum() - want.sum()) <= 1e-13 * abs(want.sum()), i

@@ -152,6 +152,26 @@ CDP_API int cdp_project(cdp_ctx* ctx, const cdp_problem* prob, int precision, in
  * accumulate = 0 and no stats).  The scratch is sized once for the largest problem first. */
 CDP_API int cdp_project_batched(cdp_ctx* ctx, const cdp_problem* probs, int n, int precision, void* stream);
 
+/* Projection through a hierarchy of coarser grids and donor-cell gather onto prob's grid (Sect. 4.4,
+ * calculation of the acceleration: the AMR grid is refined down to the smallest perpendicular height
+ * of the simplices crossing it, the projection onto its cells is exact, and the Poisson grid takes
+ * their masses by a donor-cell gather).  Level l (0 .. max_level) is prob's grid with every axis
+ * divided by 2^l.  Each simplex is projected exactly onto one level: the coarsest whose cells are no
+ * larger than its smallest perpendicular height eta (D |volume| / largest facet measure, in cells of
+ * prob's grid), i.e. l = min(max_level, floor(log2 eta)), and l = 0 for eta < 2.  Then every cell of
+ * prob's grid receives its own mass plus, for each l >= 1, the mass of the level-l cell containing
+ * it divided by 2^(D l).  The total mass is that of cdp_project; the mass inside a level-l cell is
+ * spread evenly over the 2^(D l) cells it covers.
+ *   max_level    0 .. CDP_AMR_MAX_LEVEL; every prob->grid[a] must be divisible by 2^max_level
+ *                (CDP_ERR_ARG otherwise); 0 is exactly cdp_project
+ *   precision, accumulate, stream, stats   as cdp_project (the stats count the simplices of all
+ *                levels; accuracy_bound is relative to the largest cell mass of prob's grid)
+ * Scratch (context-owned): the coarse levels' cells (8 bytes each, under 1/7 of prob's grid in 3D)
+ * and one byte per simplex; the vertex records are made once per level. */
+#define CDP_AMR_MAX_LEVEL 6
+CDP_API int cdp_project_amr(cdp_ctx* ctx, const cdp_problem* prob, int precision, int max_level, int accumulate,
+                            void* stream, cdp_stats* stats);
+
 /* Largest n_verts and n_simplices accepted by cdp_project_noalloc, and the size of its static
  * device scratch, held by every process that loads the library on every device it uses: 32 bytes
  * per vertex (8 MiB), three lists of 4 bytes per simplex (large, deferred and clipped simplices,

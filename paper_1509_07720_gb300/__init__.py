@@ -20,13 +20,15 @@ __all__ = [
     "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density", "cdp_poisson", "cdp_force", "cdp_drift",
     "cdp_kick", "cdp_step_batched", "cdp_step_problem", "Projector", "EXPORTED_SYMBOLS",
     "cdp_project_noalloc", "CDP_NOALLOC_MAX_VERTS", "CDP_NOALLOC_MAX_SIMPLICES", "cdp_autotune",
-    "CDP_ACCURACY_OFF",
+    "CDP_ACCURACY_OFF", "cdp_project_amr", "CDP_AMR_MAX_LEVEL",
 ]
 
 CDP_FP64 = 0
 CDP_FP32_MIXED = 1
 # OR'ed into a precision: no accuracy control (every simplex by Franklin's sum)
 CDP_ACCURACY_OFF = 0x100
+# deepest level of cdp_project_amr (grids divided by 2^level)
+CDP_AMR_MAX_LEVEL = 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libcoldproj.so")
@@ -36,7 +38,7 @@ _lib = None
 EXPORTED_SYMBOLS = ("cdp_create", "cdp_destroy", "cdp_project", "cdp_check", "cdp_strerror",
                     "cdp_timing_enable", "cdp_timing_read", "cdp_project_batched", "cdp_vertex_density",
                     "cdp_poisson", "cdp_force", "cdp_drift", "cdp_kick", "cdp_step_batched",
-                    "cdp_project_noalloc", "cdp_autotune")
+                    "cdp_project_noalloc", "cdp_autotune", "cdp_project_amr")
 
 
 class CdpError(RuntimeError):
@@ -107,6 +109,9 @@ def load_library(path: str | None = None):
     lib.cdp_project.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_int, vp,
                                 ctypes.POINTER(cdp_stats)]
     lib.cdp_project.restype = ctypes.c_int
+    lib.cdp_project_amr.argtypes = [vp, ctypes.POINTER(cdp_problem), ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                    ctypes.POINTER(cdp_stats)]
+    lib.cdp_project_amr.restype = ctypes.c_int
     lib.cdp_check.argtypes = [vp, vp]
     lib.cdp_check.restype = ctypes.c_int
     lib.cdp_timing_enable.argtypes = [vp, ctypes.c_int]
@@ -170,6 +175,13 @@ def cdp_project(ctx, prob: cdp_problem, precision: int, accumulate: int = 0, str
     """Raw call; returns the ABI's status code (0 = ok)."""
     return load_library().cdp_project(ctx, ctypes.byref(prob), int(precision), int(accumulate),
                                       ctypes.c_void_p(stream), ctypes.byref(stats) if stats is not None else None)
+
+
+def cdp_project_amr(ctx, prob: cdp_problem, precision: int, max_level: int, accumulate: int = 0, stream: int = 0,
+                    stats: cdp_stats | None = None) -> int:
+    """Raw call; returns the ABI's status code (0 = ok)."""
+    return load_library().cdp_project_amr(ctx, ctypes.byref(prob), int(precision), int(max_level), int(accumulate),
+                                          ctypes.c_void_p(stream), ctypes.byref(stats) if stats is not None else None)
 
 
 def cdp_check(ctx, stream: int = 0) -> int:
@@ -346,6 +358,26 @@ class Projector:
         st = cdp_stats() if stats else None
         rc = cdp_project(self._ctx, prob, precision, int(bool(accumulate)), _stream_handle(stream), st)
         _raise(rc, "cdp_project")
+        if stats:
+            return out, st.as_dict()
+        return out
+
+    def project_amr(self, pos, simplices, rho, grid, max_level, box_lo=None, box_len=None, periodic=True,
+                    precision=CDP_FP32_MIXED, out=None, accumulate=False, stream=None, stats=False):
+        """Projection through the levels 0 .. max_level (grid / 2^level) and donor-cell gather onto
+        `grid` (cdp_project_amr)."""
+        import torch
+
+        dim = len(grid)
+        box_lo = box_lo if box_lo is not None else (0.0,) * dim
+        box_len = box_len if box_len is not None else (1.0,) * dim
+        if out is None:
+            out = torch.empty(tuple(grid), dtype=torch.float64, device=f"cuda:{self.device}")
+        prob = self.make_problem(pos, simplices, rho, grid, box_lo, box_len, periodic, out)
+        st = cdp_stats() if stats else None
+        rc = cdp_project_amr(self._ctx, prob, precision, int(max_level), int(bool(accumulate)),
+                             _stream_handle(stream), st)
+        _raise(rc, "cdp_project_amr")
         if stats:
             return out, st.as_dict()
         return out

@@ -154,6 +154,12 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
     return grow_geo(c, ns);
 }
 
+// scratch of an AMR projection: the coarse levels' grids and the level of every simplex
+int reserve_amr(cdp_ctx* c, size_t coarse_cells, size_t n_simplices) {
+    int rc = grow(&c->amr, &c->amr_cap, coarse_cells > 0 ? coarse_cells : 1);
+    return rc ? rc : grow(&c->levels, &c->levels_cap, n_simplices > 0 ? n_simplices : 1);
+}
+
 // the table of a group of problems of one dimension (at most CDP_GROUP, arguments already checked):
 // their grids, pointers and offsets in the group's vertex, simplex and cell numberings.  Each
 // problem's simplices start at a multiple of the chunk size (3D), so that no chunk of the main
@@ -206,8 +212,11 @@ int build_table(const cdp_problem* const* probs, int n, ProbTable& T) {  // (als
 }
 
 // enqueue the projection of one group on `st` (arguments already checked; a single projection is a
-// group of one)
-int project_group(cdp_ctx* c, const ProbTable& T, int precision, int accumulate, cudaStream_t st, bool want_stats) {
+// group of one).  With `amr_levels`, the group is the levels 0 .. max_level of one mesh (an AMR
+// projection, cdp_amr.cu): the level of every simplex is written there after the vertex records,
+// and every entry sets up the simplices of its own level only.
+int project_group(cdp_ctx* c, const ProbTable& T, int precision, int accumulate, cudaStream_t st, bool want_stats,
+                  unsigned char* amr_levels = nullptr, int max_level = 0) {
     int rc;
     const size_t nv1 = (size_t)(T.nv > 0 ? T.nv : 1), ns1 = (size_t)(T.ns > 0 ? T.ns : 1);
     if ((rc = grow(&c->verts, &c->verts_cap, nv1))) return rc;
@@ -234,6 +243,7 @@ int project_group(cdp_ctx* c, const ProbTable& T, int precision, int accumulate,
     L.big_list = c->queue;
     L.big_cap = (long long)c->queue_cap;
     L.geo = c->geo;
+    L.geo_bytes = c->geo_cap;
     L.need = c->need;
     L.tile_store = c->tiles;
     L.tile_store_cap = c->tiles_cap;
@@ -274,6 +284,13 @@ int project_group(cdp_ctx* c, const ProbTable& T, int precision, int accumulate,
     if (launch_prep(L, st) != cudaSuccess) {
         cudaGetLastError();
         return CDP_ERR_CUDA;
+    }
+    if (amr_levels) {
+        if (launch_amr_levels(L, max_level, amr_levels, st) != cudaSuccess) {
+            cudaGetLastError();
+            return CDP_ERR_CUDA;
+        }
+        L.levels = amr_levels;
     }
     if (ev[1]) cudaEventRecord(ev[1], st);
     L.ev_acc = ev[4];
@@ -368,6 +385,10 @@ int read_stats(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) {
 }
 
 }  // namespace
+
+namespace cdp {
+int read_stats_ctx(cdp_ctx* c, cudaStream_t st, cdp_stats* stats) { return read_stats(c, st, stats); }
+}  // namespace cdp
 
 extern "C" {
 
@@ -469,6 +490,8 @@ void cdp_destroy(cdp_ctx* c) {
     if (c->geo) cudaFree(c->geo);
     if (c->need) cudaFree(c->need);
     if (c->tiles) cudaFree(c->tiles);
+    if (c->amr) cudaFree(c->amr);
+    if (c->levels) cudaFree(c->levels);
     if (c->ctr) cudaFree(c->ctr);
     if (c->stats) cudaFree(c->stats);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);

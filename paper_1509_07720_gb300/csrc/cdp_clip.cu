@@ -77,8 +77,11 @@ struct ClipTet {
     double g[3];      // density gradient (per cell)
     double c[3];      // centroid, and the density there
     double rhoc;
+    double mexact;    // |V| mean(rho), FP64 closed form (the FP32 closure)
     int lo[3], hi[3]; // bounding box (cells, relative to the anchor)
     int anchor[3];
+    int cell0[3];     // absolute cell of vertex 0
+    int prob;         // the problem of the group
     int ok;
 };
 
@@ -269,11 +272,110 @@ __device__ R clip_cell_2d(const ClipTri& T, const double o[2]) {
 
 }  // namespace
 
-// The listed simplices (list[0, min(*count, cap))), one per block in turn; every cell of the bounding
-// box by the block's threads, in arithmetic R.  R = float (FP32-mixed path): the simplex's pieces
+// 2D: the listed triangles (list[0, min(*count, cap))), one per block in turn; every cell of the
+// bounding box by the block's threads, in arithmetic R.  R = float (FP32-mixed path): the simplex's pieces
 // are summed over the block and its FP64 closed-form mass minus that sum (a few FP32 ulps of the
 // pieces) goes to the cell of its vertex 0, so the total mass stays exact to FP64 rounding.  The
 // simplices passed the vertex-index and canonicalisation checks when they were listed.
+// One thread per listed tetrahedron of entries [e0, e0 + cap) of the clip list (the list's count read
+// on the device): canonicalise and set up in FP64, into recs[e - e0].  (The set-up is long FP64
+// and 128-bit integer work; one thread each keeps the SMs busy with it.)
+__global__ void __launch_bounds__(128) k_clip_setup3(const __grid_constant__ ProbTable T, const VertexRec* __restrict__ V,
+                                                      const int* __restrict__ list, const unsigned* count,
+                                                      long long list_cap, long long e0, long long cap,
+                                                      ClipTet* __restrict__ recs) {
+    const long long listed = (long long)*(volatile const unsigned*)count;
+    const long long n = (listed < list_cap ? listed : list_cap) - e0;
+    const long long m = n < cap ? n : cap;
+#pragma unroll 1
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        ClipTet& st = recs[i];
+        const long long sg = list[e0 + i];  // in the group's numbering
+        const int prob = find_simplex(T, sg);
+        const ProbEntry& P = T.p[prob];
+        const long long s = sg - P.s_off;
+        const VertexRec* v[4];
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) {
+            const int id = P.simplices[s * 4 + k];
+            ok = ok && id >= 0 && id < P.nv;
+            v[k] = V + P.v_off + (ok ? id : 0);
+        }
+        Tet S;
+        st.ok = ok && canon_tet<2>(P.g, v, S) == 0;
+        st.prob = prob;
+        if (!st.ok) continue;
+        TetGeo<double> G;
+        tet_setup<double, 2>(S, S.lo, G);
+        for (int k = 0; k < 4; ++k)
+            for (int a = 0; a < 3; ++a) {
+                st.x[k][a] = G.x[k][a] + (double)S.lo[a];
+                st.n[k][a] = G.n[k][a];
+            }
+        for (int f = 0; f < 4; ++f) {
+            const int va = f == 0 ? 1 : 0;
+            st.nx[f] = st.n[f][0] * st.x[va][0] + st.n[f][1] * st.x[va][1] + st.n[f][2] * st.x[va][2];
+            st.hw[f] = 0.5 * (fabs(st.n[f][0]) + fabs(st.n[f][1]) + fabs(st.n[f][2]));
+        }
+        for (int a = 0; a < 3; ++a) {
+            st.g[a] = G.g[a];
+            st.c[a] = G.c[a] + (double)S.lo[a];
+            st.lo[a] = S.lo[a];
+            st.hi[a] = S.hi[a];
+            st.anchor[a] = S.anchor[a];
+            st.cell0[a] = S.anchor[a] + S.cell[0][a];
+        }
+        st.rhoc = G.rhoc;
+        st.mexact = G.mexact;
+    }
+}
+
+// One warp per record of k_clip_setup3 (records [0, min(n, cap)), n the clip list's count less e0):
+// every cell of the bounding box by the warp's lanes, in arithmetic R.  R = float: the tetrahedron's
+// pieces are summed over the warp and its FP64 closed-form mass minus that sum goes to the cell of
+// its vertex 0.
+template <typename R>
+__global__ void __launch_bounds__(CLIP_THREADS) k_project_clip3(const __grid_constant__ ProbTable T,
+                                                                const ClipTet* __restrict__ recs, const unsigned* count,
+                                                                long long list_cap, long long e0, long long cap) {
+    constexpr bool closure = sizeof(R) == 4;
+    const long long listed = (long long)*(volatile const unsigned*)count;
+    const long long n0 = (listed < list_cap ? listed : list_cap) - e0;
+    const long long n = n0 < cap ? n0 : cap;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+#pragma unroll 1
+    for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += warps) {
+        const ClipTet& st = recs[e];
+        if (!st.ok) continue;
+        const GridDesc& g = T.p[st.prob].g;
+        double* const out = T.p[st.prob].out;
+        const long long ex = st.hi[0] - st.lo[0] + 1, ey = st.hi[1] - st.lo[1] + 1, ez = st.hi[2] - st.lo[2] + 1;
+        const long long ncell = ex * ey * ez;
+        double mine = 0.0;
+#pragma unroll 1
+        for (long long c = lane; c < ncell; c += 32) {
+            const long long r = c / ex;
+            const int i = (int)(c - r * ex), j = (int)(r % ey), k = (int)(r / ey);
+            const double o[3] = {(double)(st.lo[0] + i), (double)(st.lo[1] + j), (double)(st.lo[2] + k)};
+            const R m = clip_cell_3d<R>(st, o);
+            if (m == R(0)) continue;
+            mine += (double)m;
+            const long long idx = flat_cell(g, st.anchor[0] + st.lo[0] + i, st.anchor[1] + st.lo[1] + j,
+                                            st.anchor[2] + st.lo[2] + k);
+            if (idx >= 0) atomicAdd(out + idx, (double)m);
+        }
+        if (closure) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+            if (lane == 0) {
+                const long long idx = flat_cell(g, st.cell0[0], st.cell0[1], st.cell0[2]);
+                if (idx >= 0) atomicAdd(out + idx, st.mexact - mine);
+            }
+        }
+    }
+}
+
 template <int DIM, typename R>
 __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(const __grid_constant__ ProbTable T,
                                                                const VertexRec* __restrict__ V,
@@ -395,14 +497,26 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(const __grid_cons
 
 cudaError_t launch_clip(const LaunchArgs& L, int fp32, cudaStream_t st) {
     if (!L.clip_list || !L.ctr) return cudaSuccess;
-    const unsigned blocks = (unsigned)(L.num_sms * 4);
     const unsigned* cnt = &L.ctr->clip_count;
     if (L.T.dim == 3) {
-        if (fp32)
-            k_project_clip<3, float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
-        else
-            k_project_clip<3, double><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
+        // records in the geometry buffer (free once the second pass is done), batch by batch; the
+        // clip list holds at most min(ns, clip_cap) entries, its count read on the device
+        const long long cap = (long long)(L.geo_bytes / sizeof(ClipTet));
+        if (cap < 1) return cudaErrorInvalidValue;
+        ClipTet* recs = reinterpret_cast<ClipTet*>(L.geo);
+        const long long most = L.T.ns < L.clip_cap ? L.T.ns : L.clip_cap;
+        for (long long e0 = 0; e0 < most; e0 += cap) {
+            long long sb = (cap + 127) / 128;
+            if (sb > (long long)L.num_sms * 16) sb = (long long)L.num_sms * 16;
+            k_clip_setup3<<<(unsigned)sb, 128, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap, e0, cap, recs);
+            const unsigned blocks = (unsigned)(L.num_sms * 8);
+            if (fp32)
+                k_project_clip3<float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, recs, cnt, L.clip_cap, e0, cap);
+            else
+                k_project_clip3<double><<<blocks, CLIP_THREADS, 0, st>>>(L.T, recs, cnt, L.clip_cap, e0, cap);
+        }
     } else {
+        const unsigned blocks = (unsigned)(L.num_sms * 4);
         if (fp32)
             k_project_clip<2, float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
         else

@@ -51,6 +51,10 @@ struct cdp_ctx {
     size_t defer_cap;
     int* clip;            // simplices projected by clipping
     size_t clip_cap;
+    double* amr;          // coarse levels' grids of an AMR projection (cdp_project_amr)
+    size_t amr_cap;
+    unsigned char* levels;  // level of every simplex of an AMR projection
+    size_t levels_cap;
     float* tiles;         // FP32 pieces of large-tetrahedron tiles kept between the two passes
     size_t tiles_cap;     // (floats)
     cdp::Counters* ctr;       // device

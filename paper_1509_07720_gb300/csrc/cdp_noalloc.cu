@@ -116,6 +116,7 @@ extern "C" int cdp_project_noalloc(const cdp_problem* p, int precision, int accu
     L.clip_cap = kMaxSimplices;
     L.need = (int*)(s->scratch + kNeedOffset);
     L.geo = s->scratch + kGeoOffset;
+    L.geo_bytes = (size_t)kGeoBatch * kGeoRec;
     L.geo_cap = kGeoBatch;
 
     // every counter, the error word included, starts at zero on each call

@@ -234,6 +234,7 @@ __device__ __forceinline__ void eval_record(WarpShared<DIM, R>* sh, unsigned lon
 struct WarpPass {
     AccCtl acc;
     int second;
+    const unsigned char* levels;  // AMR projection: the level of every simplex (entry p = level p)
     int* defer_list;
     long long defer_cap;
     int* clip_list;
@@ -281,7 +282,9 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(const __grid_con
             const GridDesc& g = P.g;
             const long long s = sg - P.s_off;
             const VertexRec* v[4];
-            if (!fetch_vertices(P.simplices, s, DIM + 1, P.nv, V + P.v_off, v)) {
+            if (s >= P.ns || (wp.levels && (int)wp.levels[s] != prob)) {
+                // (an index between two problems, or a simplex of another level of an AMR projection)
+            } else if (!fetch_vertices(P.simplices, s, DIM + 1, P.nv, V + P.v_off, v)) {
                 atomicOr(&ctr->flags, CDP_FLAG_INDEX);
             } else {
                 Tri S;
@@ -469,7 +472,7 @@ static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t 
     long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    WarpPass wp = {acc_ctl(sizeof(R) == 4), 0, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
+    WarpPass wp = {acc_ctl(sizeof(R) == 4), 0, L.levels, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
     if (!L.accuracy) wp.acc.defer_ratio = 3.0e38f;  // nothing is deferred
     k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(L.T, L.verts, L.ctr, L.stats,
                                                                                        wp);
@@ -479,6 +482,7 @@ static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t 
     cudaError_t e = launch_pass_boundary(L, st);
     if (e != cudaSuccess) return e;
     wp.second = 1;
+    wp.levels = nullptr;  // (the deferred list holds the right entries only)
     k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(L.T, L.verts, L.ctr, L.stats,
                                                                                        wp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -128,7 +128,9 @@ struct LaunchArgs {
     float* tile_store;        // FP32 pieces of tiles kept between the two passes over a large tetrahedron
     size_t tile_store_cap;    // (floats; null / 0: every tile is computed twice)
     int tile_store_per_block; // tiles kept per block of the large-tetrahedron kernel
-    void* geo;          // geometry records of one batch of tetrahedra (capacity geo_cap records)
+    void* geo;          // geometry records of one batch of tetrahedra (capacity geo_cap records;
+                        // geo_bytes bytes, also the clip records of the accuracy control in 3D)
+    size_t geo_bytes;
     int* need;          // their box sizes (geo_cap entries)
     long long geo_cap;
     int* defer_list;    // simplices deferred by the first pass (capacity defer_cap)
@@ -139,6 +141,9 @@ struct LaunchArgs {
     int max_cells;      // 3D size-class threshold: largest bounding box (cells) of the main kernel
                         // (0: the default; at most the block's box slots, tet_box_slots)
     int tile_edge;      // tile edge (cells) of the large tetrahedra (0: the default; 4 .. 18)
+    const unsigned char* levels;  // AMR projection (cdp_amr.cu): the level of every simplex of the
+                        // mesh; the table's entry p is level p and sets up only the simplices of
+                        // that level (null: every simplex in every entry)
     cudaEvent_t ev_acc; // optional: recorded where the accuracy control starts (timing)
 };
 
@@ -151,6 +156,10 @@ inline bool parse_precision(int precision, int* fp32, int* accuracy) {
     *accuracy = (precision & 0x100) ? 0 : 1;
     return true;
 }
+
+// AMR projection (cdp_amr.cu): the level (0 .. max_level) of every simplex of the mesh of the
+// table's entry 0, from its vertex records (launch_prep)
+cudaError_t launch_amr_levels(const LaunchArgs& L, int max_level, unsigned char* levels, cudaStream_t st);
 
 cudaError_t configure_all();
 // resident blocks per SM of the projection kernel of dimension `dim` (occupancy calculator)

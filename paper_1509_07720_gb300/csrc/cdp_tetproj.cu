@@ -1084,7 +1084,8 @@ __global__ void __launch_bounds__(128) k_tet_setup(const __grid_constant__ ProbT
                                                    const VertexRec* __restrict__ V, Counters* __restrict__ ctr,
                                                    TetGeo<R>* __restrict__ geo, int* __restrict__ need,
                                                    int* __restrict__ big_list, long long big_cap, int count,
-                                                   int max_cells, const int* __restrict__ list, AccCtl acc,
+                                                   int max_cells, const unsigned char* __restrict__ levels,
+                                                   const int* __restrict__ list, AccCtl acc,
                                                    int* __restrict__ defer_list,
                                                    long long defer_cap, int* __restrict__ clip_list, long long clip_cap) {
     // the block's records are assembled in shared memory and written out with coalesced stores
@@ -1111,14 +1112,15 @@ __global__ void __launch_bounds__(128) k_tet_setup(const __grid_constant__ ProbT
         const long long s = sg - P.s_off;
         int my_need = 0;
         const VertexRec* v[4];
-        bool ok = s < P.ns;
+        // (an index between two problems, or a simplex of another level of an AMR projection)
+        const bool mine = s < P.ns && (!levels || (int)levels[s] == prob);
+        bool ok = mine;
         for (int k = 0; k < 4 && ok; ++k) {
             const int id = __ldg(P.simplices + s * 4 + k);
             if (id < 0 || id >= P.nv) ok = false;
             v[k] = V + P.v_off + (ok ? id : 0);
         }
-        if (s >= P.ns) {
-            // (an index between two problems)
+        if (!mine) {
         } else if (!ok) {
             atomicOr(&ctr->flags, CDP_FLAG_INDEX);
         } else {
@@ -1676,8 +1678,8 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     for (long long s0 = 0; s0 < ns; s0 += batch) {
         const long long nb = ns - s0 < batch ? ns - s0 : batch;
         k_tet_setup<R><<<(unsigned)((nb + 127) / 128), 128, stage, st>>>(
-            L.T, s0, nb, L.verts, L.ctr, G, L.need, L.big_list, L.big_cap, L.stats != nullptr, max_cells, nullptr, acc,
-            L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
+            L.T, s0, nb, L.verts, L.ctr, G, L.need, L.big_list, L.big_cap, L.stats != nullptr, max_cells, L.levels,
+            nullptr, acc, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
         if (after_setup && s0 == 0) cudaEventRecord(after_setup, st);
         chunks(nb, 0, 0);
     }
@@ -1694,8 +1696,9 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
         long long blocks = (batch + 127) / 128;
         if (blocks > (long long)L.num_sms * 16) blocks = (long long)L.num_sms * 16;
         k_tet_setup<R><<<(unsigned)blocks, 128, stage, st>>>(L.T, s0, batch, L.verts, L.ctr, G, L.need, L.big_list,
-                                                            L.big_cap, L.stats != nullptr, max_cells, L.defer_list,
-                                                            acc, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap);
+                                                            L.big_cap, L.stats != nullptr, max_cells, nullptr,
+                                                            L.defer_list, acc, L.defer_list, L.defer_cap, L.clip_list,
+                                                            L.clip_cap);
         chunks(batch, 1, s0);
     }
     big(1);

@@ -51,6 +51,8 @@ __all__ = [
     "stratified_subset",
     "degenerate_meshes",
     "isolated_simplices",
+    "mixed_size_simplices",
+    "concat_meshes",
 ]
 
 
@@ -679,3 +681,22 @@ def isolated_simplices(dim: int, blocks: int, block_cells: int, rng):
     sig = rng.choice([0.3, 1.0, 2.0], n)
     rho = np.exp(np.repeat(sig, dim + 1) * rng.standard_normal(n * (dim + 1)))
     return Mesh(pos, simp, rho, (grid,) * dim, (0.0,) * dim, (1.0,) * dim, False, "isolated"), kind, V
+
+
+def concat_meshes(meshes) -> Mesh:
+    """One mesh holding the simplices of several meshes on the same grid and box (vertices kept
+    apart, indices offset)."""
+    m0 = meshes[0]
+    pos = np.concatenate([m.pos for m in meshes], axis=1)
+    offs = np.cumsum([0] + [m.n_verts for m in meshes[:-1]])
+    simp = np.concatenate([m.simplices + o for m, o in zip(meshes, offs)]).astype(np.int32)
+    rho = np.concatenate([m.rho for m in meshes])
+    return Mesh(pos, simp, rho, m0.grid, m0.box_lo, m0.box_len, m0.periodic, "concat")
+
+
+def mixed_size_simplices(dim: int, grid: int, counts_sizes, rng, periodic: bool = True) -> Mesh:
+    """Random simplices of several sizes in one mesh: ``counts_sizes`` = [(count, size in cells), ...]
+    as ``random_simplices`` (smallest perpendicular heights spread over the levels of a hierarchy
+    of grids)."""
+    return concat_meshes([random_simplices(dim, n, grid, s, rng, periodic) for n, s in counts_sizes])
+

@@ -3,13 +3,18 @@
 Measurement harness beside ``bench.py``, not part of the library: each case builds its seeded
 synthetic mesh, puts it on ``cuda:0`` and projects it ``--reps`` times through the public API
 (``Projector.project``) with CUDA events around every call, then prints one JSON line with the
-times.  Cases:
+times.  ``--amr L`` projects through the levels 0 .. L with donor-cell gather
+(``Projector.project_amr``) instead of the exact projection.  Cases:
 
   c3           the 128^3 Kuhn lattice of the headline benchmark (``--scale n``: an n^3 lattice;
                ``--subset k``: a seeded random 1/k of its tetrahedra on the same grid, the size an
                ncu capture of the full kernel allows)
+  c4           the bisected adaptive mesh (simplex volumes over four decades; ``--scale n``: an n^3
+               base lattice, default 64, grid 8n)
   c5           one problem of the 64-problem batched workload (``--problem i``), projected alone
   c5_3d        the 32 three-dimensional problems of that workload, one after the other
+  c5_batch     all 64 problems in one cdp_project_batched call (one launch of each kernel per group
+               of problems of one dimension)
 """
 from __future__ import annotations
 
@@ -29,7 +34,7 @@ def _device_mesh(torch, mesh):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c3", "c5", "c5_3d"])
+    ap.add_argument("case", choices=["c3", "c4", "c5", "c5_3d", "c5_batch"])
     ap.add_argument("--scale", type=int, default=None, help="c3: lattice size (default 128)")
     ap.add_argument("--subset", type=int, default=1, help="c3: keep a random 1/k of the tetrahedra (seed 8)")
     ap.add_argument("--problem", type=int, default=0, help="c5: problem index in [0, 64)")
@@ -37,6 +42,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--stats", action="store_true", help="also one instrumented pass and per-kernel times")
     ap.add_argument("--accuracy-off", action="store_true", help="no accuracy control")
+    ap.add_argument("--amr", type=int, default=None, help="project through the levels 0 .. AMR (grid / 2^level)")
     a = ap.parse_args(argv)
 
     import os
@@ -52,15 +58,20 @@ def main(argv=None):
     if not torch.cuda.is_available():
         raise SystemExit("profile_cases needs a CUDA device")
     build.build_library()
-    if a.case == "c3":
-        m = mg.make_config("c3", a.scale)
+    if a.case in ("c3", "c4"):
+        m = mg.make_config(a.case, a.scale)
         if a.subset > 1:
             rng = np.random.default_rng(8)
             m = m.subset(np.sort(rng.choice(m.n_simplices, m.n_simplices // a.subset, replace=False)))
         meshes = [m]
     else:
         batch = mg.make_batch("c5")
-        meshes = [batch[a.problem].mesh] if a.case == "c5" else [p.mesh for p in batch if p.mesh.dim == 3]
+        if a.case == "c5":
+            meshes = [batch[a.problem].mesh]
+        elif a.case == "c5_3d":
+            meshes = [p.mesh for p in batch if p.mesh.dim == 3]
+        else:
+            meshes = [p.mesh for p in batch]
     data = [(m, *_device_mesh(torch, m)) for m in meshes]
     prec = pkg.CDP_FP32_MIXED if a.prec == "fp32" else pkg.CDP_FP64
     if a.accuracy_off:
@@ -68,13 +79,24 @@ def main(argv=None):
     proj = pkg.Projector(0)
     stream = torch.cuda.current_stream()
     times = []
+    probs = [pkg.Projector.make_problem(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, out)
+             for m, pos, simp, rho, out in data]
     for _ in range(a.reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for m, pos, simp, rho, out in data:
-            proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec, out=out,
-                         stream=stream)
+        if a.case == "c5_batch":
+            rc = pkg.cdp_project_batched(proj._ctx, probs, prec, stream.cuda_stream)
+            if rc:
+                raise SystemExit(f"cdp_project_batched: {rc}")
+        elif a.amr is not None:
+            for m, pos, simp, rho, out in data:
+                proj.project_amr(pos, simp, rho, m.grid, a.amr, m.box_lo, m.box_len, m.periodic, precision=prec,
+                                 out=out, stream=stream)
+        else:
+            for m, pos, simp, rho, out in data:
+                proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec, out=out,
+                             stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -83,16 +105,25 @@ def main(argv=None):
     if a.stats:
         proj.timing(True)
         for m, pos, simp, rho, out in data:
-            proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec, out=out,
-                         stream=stream)
+            if a.amr is not None:
+                proj.project_amr(pos, simp, rho, m.grid, a.amr, m.box_lo, m.box_len, m.periodic, precision=prec,
+                                 out=out, stream=stream)
+            else:
+                proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec, out=out,
+                             stream=stream)
         kern, calls = proj.timing()
         proj.timing(False)
         extra["kernel_ms"] = dict(zip(["vertex records", "set-up", "main", "large", "accuracy control"], kern))
-        extra["stats"] = [proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec,
-                                       out=out, stream=stream, stats=True)[1] for m, pos, simp, rho, out in data]
+        if a.amr is not None:
+            extra["stats"] = [proj.project_amr(pos, simp, rho, m.grid, a.amr, m.box_lo, m.box_len, m.periodic,
+                                               precision=prec, out=out, stream=stream, stats=True)[1]
+                              for m, pos, simp, rho, out in data]
+        else:
+            extra["stats"] = [proj.project(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, precision=prec,
+                                           out=out, stream=stream, stats=True)[1] for m, pos, simp, rho, out in data]
     print(json.dumps({**extra, "case": a.case, "scale": a.scale, "subset": a.subset, "problem": a.problem if a.case == "c5" else None,
                       "prec": a.prec, "simplices": int(sum(m.n_simplices for m in meshes)),
-                      "ms_per_rep": times}), flush=True)
+                      "amr": a.amr, "ms_per_rep": times}), flush=True)
     proj.close()
 
 

@@ -34,60 +34,66 @@ namespace {
 // Level of every simplex from the vertex records of the output grid (entry 0 of the table): its
 // smallest perpendicular height eta = D |V| / (largest facet measure), in output cells (3D: 6|V| over
 // the largest |facet normal| = twice the facet area; 2D: 2|A| over the longest edge), and the level
-// l = min(max_level, floor(log2 eta)) (0 when eta < 2).  The volume is exact (fixed point, 128-bit);
-// zero-volume and invalid simplices get level 0 (the set-up skips or reports them there).
+// l = min(max_level, floor(log2 eta)) (0 when eta < 2).  The edge vectors are the fixed-point
+// differences to vertex 0 at its minimal image (exact in FP64: below 2^53), the rest is FP64
+// arithmetic (relative error ~1e-15: a simplex whose height is that close to a power of two may take
+// either level).  Invalid simplices get level 0; the set-up reports them there.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_amr_levels(const __grid_constant__ ProbTable T, const VertexRec* __restrict__ V,
                                                      int max_level, unsigned char* __restrict__ levels) {
     const ProbEntry& P = T.p[0];
+    const GridDesc& g = P.g;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < P.ns; s += (long long)gridDim.x * blockDim.x) {
-        int level = 0;
-        const VertexRec* v[4];
+        int id[DIM + 1];
         bool ok = true;
         for (int k = 0; k <= DIM; ++k) {
-            const int id = P.simplices[s * (DIM + 1) + k];
-            ok = ok && id >= 0 && id < P.nv;
-            v[k] = V + P.v_off + (ok ? id : 0);
+            id[k] = __ldg(P.simplices + s * (DIM + 1) + k);
+            ok = ok && id[k] >= 0 && id[k] < P.nv;
         }
         double eta = 0.0;
-        if (ok && DIM == 3) {
-            Tet S;
-            if (canon_tet<3>(P.g, v, S) == 0) {
-                i64 e[3][3];
-                for (int k = 0; k < 3; ++k)
-                    for (int a = 0; a < 3; ++a) e[k][a] = S.L[k + 1][a] - S.L[0][a];
-                i128 n3[3];
-                cross_exact(e[0], e[1], n3);
-                const double D = wide_to_double(dot3_wide(n3, e[2]), 3 * CDP_Q);  // 6 |V|, cells^3
-                double amax = 0.0;
-                for (int f = 0; f < 4; ++f) {
-                    i128 nf[3];
-                    facet_normal_exact(S.L, f, nf);
-                    double q = 0.0;
-                    for (int a = 0; a < 3; ++a) {
-                        const double c = i128_to_real<double>(nf[a], 2 * CDP_Q);
-                        q += c * c;
+        if (ok) {
+            const VertexRec* v0 = V + P.v_off + id[0];
+            double e[DIM][3];
+            for (int k = 1; k <= DIM; ++k) {
+                const VertexRec* vk = V + P.v_off + id[k];
+                for (int a = 0; a < DIM; ++a) {
+                    i64 d = vk->x[a] - v0->x[a];
+                    if (g.periodic) {
+                        const i64 NQ = (i64)g.n[a] << CDP_Q, half = (i64)g.n[a] << (CDP_Q - 1);
+                        if (d > half) d -= NQ;
+                        if (d < -half) d += NQ;
                     }
-                    amax = fmax(amax, sqrt(q));  // twice the facet's area, cells^2
+                    e[k - 1][a] = ldexp((double)d, -CDP_Q);
                 }
-                eta = amax > 0.0 ? D / amax : 0.0;
             }
-        } else if (ok) {
-            Tri S;
-            if (canon_tri(P.g, v, S) == 0) {
-                const i128 Dq = mul64(S.L[1][0] - S.L[0][0], S.L[2][1] - S.L[0][1]) -
-                                mul64(S.L[1][1] - S.L[0][1], S.L[2][0] - S.L[0][0]);
-                const double D = i128_to_real<double>(Dq, 2 * CDP_Q);  // 2 |A|, cells^2
-                double lmax = 0.0;
-                for (int k = 0; k < 3; ++k) {
-                    const int a = (k + 1) % 3, b = (k + 2) % 3;
-                    const double dx = i64_to_real<double>(S.L[b][0] - S.L[a][0], CDP_Q);
-                    const double dy = i64_to_real<double>(S.L[b][1] - S.L[a][1], CDP_Q);
-                    lmax = fmax(lmax, sqrt(dx * dx + dy * dy));
+            if (DIM == 3) {
+                // facet normals: n_f = (p_b - p_a) x (p_c - p_a) over the facets (a, b, c), p_0 = 0
+                const double z[3] = {0.0, 0.0, 0.0};
+                const double* p[4] = {z, e[0], e[1], e[2 % DIM]};
+                double amax = 0.0, vol6 = 0.0;
+                for (int f = 0; f < 4; ++f) {
+                    const int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, c = f <= 2 ? 3 : 2;
+                    double u[3], w[3];
+                    for (int i = 0; i < 3; ++i) {
+                        u[i] = p[b][i] - p[a][i];
+                        w[i] = p[c][i] - p[a][i];
+                    }
+                    const double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2],
+                                 n2 = u[0] * w[1] - u[1] * w[0];
+                    amax = fmax(amax, sqrt(n0 * n0 + n1 * n1 + n2 * n2));
+                    if (f == 3) vol6 = fabs(n0 * e[2 % DIM][0] + n1 * e[2 % DIM][1] + n2 * e[2 % DIM][2]);
                 }
-                eta = lmax > 0.0 ? D / lmax : 0.0;
+                eta = amax > 0.0 ? vol6 / amax : 0.0;
+            } else {
+                const double area2 = fabs(e[0][0] * e[1 % DIM][1] - e[0][1] * e[1 % DIM][0]);
+                const double dx = e[1 % DIM][0] - e[0][0], dy = e[1 % DIM][1] - e[0][1];
+                const double lmax = sqrt(fmax(fmax(e[0][0] * e[0][0] + e[0][1] * e[0][1],
+                                                   e[1 % DIM][0] * e[1 % DIM][0] + e[1 % DIM][1] * e[1 % DIM][1]),
+                                              dx * dx + dy * dy));
+                eta = lmax > 0.0 ? area2 / lmax : 0.0;
             }
         }
+        int level = 0;
         while (level < max_level && eta >= (double)(2 << level)) ++level;
         levels[s] = (unsigned char)level;
     }

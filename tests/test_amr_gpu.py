@@ -98,7 +98,9 @@ def test_level_zero_is_the_projection(proj, prec):
     a = proj.project(pos, simp, rho, mesh.grid, precision=prec)
     b = proj.project_amr(pos, simp, rho, mesh.grid, 0, precision=prec)
     torch.cuda.synchronize()
-    assert float((a - b).abs().max()) <= 1e-13 * float(a.abs().max())
+    # (two FP32-mixed projections of the same mesh differ by the order of their FP32 shared-memory
+    # adds: a few FP32 ulps of a piece)
+    assert float((a - b).abs().max()) <= {0: 1e-13, 1: 1e-6}[prec] * float(a.abs().max())
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32mixed"])

@@ -43,8 +43,10 @@ CDP_HD unsigned vertex_to_fixed(const GridDesc& g, const double p[3], double rho
             u = 0.0;
         }
         if (g.periodic) {
-            double N = (double)g.n[a];
-            u -= N * floor(u / N);
+            // wrap into [0, N) (a coordinate already inside takes no division: the FP64 divide is
+            // slow, and the fixed-point wrap below gives the same code either way)
+            const double N = (double)g.n[a];
+            if (!(u >= 0.0 && u < N)) u -= N * floor(u / N);
         }
         i64 X = (i64)llrint(ldexp(u, CDP_Q));
         if (g.periodic) {

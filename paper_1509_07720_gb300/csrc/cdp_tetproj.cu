@@ -1189,21 +1189,32 @@ __global__ void __launch_bounds__(128) k_tet_setup(const __grid_constant__ ProbT
 // big_first while the list of large tetrahedra is emptied for the second pass.  The cells of all
 // the grids are taken in the group's cell numbering.
 __global__ void __launch_bounds__(256) k_pass_boundary(const __grid_constant__ ProbTable T, Counters* __restrict__ ctr) {
-    // each thread: a running maximum while its cells stay in one problem
+    // each thread: a running maximum while its cells stay in one problem, four independent loads in
+    // flight per step
     double m = 0.0;
     int pcur = -1;
     long long pbeg = 0, pend = 0;
+    const double* out = nullptr;  // the current problem's grid, indexed by the group's cell number
+    const long long stride = (long long)gridDim.x * blockDim.x;
 #pragma unroll 1
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < T.ncells;
-         c += (long long)gridDim.x * blockDim.x) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < T.ncells;) {
         if (c < pbeg || c >= pend) {
             if (pcur >= 0 && m > 0.0) atomicMax(&ctr->mmax_bits[pcur], (unsigned long long)__double_as_longlong(m));
             pcur = find_cell(T, c);
             pbeg = T.p[pcur].c_off;
             pend = pcur + 1 < T.n ? T.p[pcur + 1].c_off : T.ncells;
+            out = T.p[pcur].out - pbeg;
             m = 0.0;
         }
-        m = fmax(m, fabs(T.p[pcur].out[c - pbeg]));
+        if (c + 3 * stride < pend) {
+            const double a = out[c], b = out[c + stride], d = out[c + 2 * stride],
+                         e = out[c + 3 * stride];
+            m = fmax(fmax(m, fmax(fabs(a), fabs(b))), fmax(fabs(d), fabs(e)));
+            c += 4 * stride;
+        } else {
+            m = fmax(m, fabs(out[c]));
+            c += stride;
+        }
     }
     // a warp whose lanes ended in one problem reduces first
     const int p0 = __shfl_sync(FULL, pcur, 0);

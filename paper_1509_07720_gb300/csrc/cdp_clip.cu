@@ -23,8 +23,10 @@
 //   from one vertex of the polygon.)
 //
 // The test that sends a simplex here (its bound on e_max against the grid's largest cell) is made by
-// the projection kernels; they append the simplex to a list, and k_project_clip takes the listed
-// simplices one per block, its threads going over the cells of the bounding box.
+// the projection kernels; they append the simplex to a list.  Tetrahedra: k_clip_setup3 sets up one
+// record per listed tetrahedron, and k_project_clip3 takes each with one warp, classifying the cells
+// of its bounding box and clipping the crossed ones 32 at a time.  Triangles: k_project_clip2 takes
+// each with one block, its threads going over the cells of the bounding box.
 #include <cuda_runtime.h>
 
 #include "cdp_mesh.cuh"
@@ -120,26 +122,30 @@ __device__ __forceinline__ R tet_vol(const R a[3], const R b[3], const R c[3], c
     return abs_r(u0 * (v1 * w2 - v2 * w1) - u1 * (v0 * w2 - v2 * w0) + u2 * (v0 * w1 - v1 * w0)) * R(1.0 / 6.0);
 }
 
+// The unit cell whose lower corner is o (relative to the anchor) against each facet plane of the
+// tetrahedron, in FP64: entirely outside one of them (0: no piece), inside all (1: the whole cell,
+// whose integral, the density at its centre, goes to *whole), or crossed (2).  Over the corners of
+// the unit cell the signed distance n . x - n . x_f ranges over its value at the centre +- hw.
+__device__ __forceinline__ int clip_classify(const ClipTet& T, const double o[3], double* whole) {
+    bool inside = true;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const double dc = T.n[f][0] * (o[0] + 0.5) + T.n[f][1] * (o[1] + 0.5) + T.n[f][2] * (o[2] + 0.5) - T.nx[f];
+        if (dc + T.hw[f] < 0.0) return 0;
+        inside = inside && dc - T.hw[f] >= 0.0;
+    }
+    if (!inside) return 2;
+    *whole = T.rhoc + T.g[0] * ((o[0] + 0.5) - T.c[0]) + T.g[1] * ((o[1] + 0.5) - T.c[1]) +
+             T.g[2] * ((o[2] + 0.5) - T.c[2]);
+    return 1;
+}
+
 // Integral of rho over (tetrahedron intersect the unit cell whose lower corner is o, relative to the
-// anchor), in arithmetic R.  The simplex is first taken into the cell's frame in FP64 (exact offsets,
-// then rounded once), so that every coordinate the clipping sees is within a few cells of 0.
+// anchor), for a cell the facets cross (clip_classify 2), in arithmetic R.  The simplex is first
+// taken into the cell's frame in FP64 (exact offsets, then rounded once), so that every coordinate
+// the clipping sees is within a few cells of 0.
 template <typename R>
 __device__ R clip_cell_3d(const ClipTet& T, const double o[3]) {
-    // the cell against each facet plane, in FP64: entirely outside one of them (no piece), or inside
-    // all (the whole cell, whose integral is the density at its centre).  Over the corners of the
-    // unit cell the signed distance n . x - n . x_f ranges over its value at the centre +- hw.
-    {
-        bool inside = true;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const double dc = T.n[f][0] * (o[0] + 0.5) + T.n[f][1] * (o[1] + 0.5) + T.n[f][2] * (o[2] + 0.5) - T.nx[f];
-            if (dc + T.hw[f] < 0.0) return R(0);
-            inside = inside && dc - T.hw[f] >= 0.0;
-        }
-        if (inside)
-            return (R)(T.rhoc + T.g[0] * ((o[0] + 0.5) - T.c[0]) + T.g[1] * ((o[1] + 0.5) - T.c[1]) +
-                       T.g[2] * ((o[2] + 0.5) - T.c[2]));
-    }
     CellFrame<R> F;
 #pragma unroll 1
     for (int k = 0; k < 4; ++k)
@@ -331,18 +337,21 @@ __global__ void __launch_bounds__(128) k_clip_setup3(const __grid_constant__ Pro
 }
 
 // One warp per record of k_clip_setup3 (records [0, min(n, cap)), n the clip list's count less e0):
-// every cell of the bounding box by the warp's lanes, in arithmetic R.  R = float: the tetrahedron's
-// pieces are summed over the warp and its FP64 closed-form mass minus that sum goes to the cell of
-// its vertex 0.
+// the cells of the bounding box are classified by the warp's lanes 32 at a time (outside, inside:
+// the closed form at once, crossed); the crossed ones are queued in shared memory and clipped 32 at a
+// time, one per lane, in arithmetic R.  R = float: the tetrahedron's pieces are summed over the warp
+// and its FP64 closed-form mass minus that sum goes to the cell of its vertex 0.
 template <typename R>
 __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip3(const __grid_constant__ ProbTable T,
                                                                 const ClipTet* __restrict__ recs, const unsigned* count,
                                                                 long long list_cap, long long e0, long long cap) {
     constexpr bool closure = sizeof(R) == 4;
+    __shared__ long long crossed[CLIP_THREADS / 32][64];  // crossed cells awaiting their clipping, per warp
     const long long listed = (long long)*(volatile const unsigned*)count;
     const long long n0 = (listed < list_cap ? listed : list_cap) - e0;
     const long long n = n0 < cap ? n0 : cap;
     const int lane = threadIdx.x & 31;
+    long long* const q = crossed[threadIdx.x >> 5];
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
 #pragma unroll 1
     for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += warps) {
@@ -352,18 +361,69 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip3(const __grid_con
         double* const out = T.p[st.prob].out;
         const long long ex = st.hi[0] - st.lo[0] + 1, ey = st.hi[1] - st.lo[1] + 1, ez = st.hi[2] - st.lo[2] + 1;
         const long long ncell = ex * ey * ez;
-        double mine = 0.0;
-#pragma unroll 1
-        for (long long c = lane; c < ncell; c += 32) {
+        // cell c of the box: (i, j, k) = (c mod ex, (c / ex) mod ey, c / (ex ey)); its lower corner
+        auto corner = [&](long long c, double o[3], long long& idx) {
             const long long r = c / ex;
             const int i = (int)(c - r * ex), j = (int)(r % ey), k = (int)(r / ey);
-            const double o[3] = {(double)(st.lo[0] + i), (double)(st.lo[1] + j), (double)(st.lo[2] + k)};
-            const R m = clip_cell_3d<R>(st, o);
-            if (m == R(0)) continue;
-            mine += (double)m;
-            const long long idx = flat_cell(g, st.anchor[0] + st.lo[0] + i, st.anchor[1] + st.lo[1] + j,
-                                            st.anchor[2] + st.lo[2] + k);
-            if (idx >= 0) atomicAdd(out + idx, (double)m);
+            o[0] = (double)(st.lo[0] + i);
+            o[1] = (double)(st.lo[1] + j);
+            o[2] = (double)(st.lo[2] + k);
+            idx = flat_cell(g, st.anchor[0] + st.lo[0] + i, st.anchor[1] + st.lo[1] + j, st.anchor[2] + st.lo[2] + k);
+        };
+        double mine = 0.0;
+        int nq = 0;  // queued crossed cells (the same in every lane)
+#pragma unroll 1
+        for (long long base = 0; base < ncell; base += 32) {
+            const long long c = base + lane;
+            int cls = 0;
+            if (c < ncell) {
+                double o[3], whole = 0.0;
+                long long idx;
+                corner(c, o, idx);
+                cls = clip_classify(st, o, &whole);
+                if (cls == 1) {
+                    const R m = (R)whole;
+                    mine += (double)m;
+                    if (idx >= 0) atomicAdd(out + idx, (double)m);
+                }
+            }
+            const unsigned cm = __ballot_sync(0xffffffffu, cls == 2);
+            if (cls == 2) q[nq + __popc(cm & ((1u << lane) - 1u))] = c;
+            nq += __popc(cm);
+            __syncwarp();
+            // a full batch (or, after the last cells, what is left): one crossed cell per lane
+            const bool last = base + 32 >= ncell;
+            if (nq >= 32 || (last && nq > 0)) {
+                if (lane < nq) {
+                    double o[3];
+                    long long idx;
+                    corner(q[lane], o, idx);
+                    const R m = clip_cell_3d<R>(st, o);
+                    if (m != R(0)) {
+                        mine += (double)m;
+                        if (idx >= 0) atomicAdd(out + idx, (double)m);
+                    }
+                }
+                __syncwarp();
+                const int left = nq > 32 ? nq - 32 : 0;
+                if (lane < left) q[lane] = q[32 + lane];
+                nq = left;
+                __syncwarp();
+                if (last && nq > 0) {  // (at most 31 after a full batch of the last cells)
+                    if (lane < nq) {
+                        double o[3];
+                        long long idx;
+                        corner(q[lane], o, idx);
+                        const R m = clip_cell_3d<R>(st, o);
+                        if (m != R(0)) {
+                            mine += (double)m;
+                            if (idx >= 0) atomicAdd(out + idx, (double)m);
+                        }
+                    }
+                    nq = 0;
+                    __syncwarp();
+                }
+            }
         }
         if (closure) {
 #pragma unroll
@@ -376,13 +436,12 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip3(const __grid_con
     }
 }
 
-template <int DIM, typename R>
-__global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(const __grid_constant__ ProbTable T,
+template <typename R>
+__global__ void __launch_bounds__(CLIP_THREADS) k_project_clip2(const __grid_constant__ ProbTable T,
                                                                const VertexRec* __restrict__ V,
                                                                const int* __restrict__ list, const unsigned* count,
                                                                long long cap) {
     constexpr bool closure = sizeof(R) == 4;
-    __shared__ ClipTet st;
     __shared__ ClipTri s2;
     __shared__ double mexact;
     __shared__ int cell0[3];
@@ -400,41 +459,14 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(const __grid_cons
             const ProbEntry& P = T.p[prob];
             const GridDesc& g = P.g;
             const long long s = sg - P.s_off;
-            const VertexRec* v[4];
+            const VertexRec* v[3];
             bool ok = true;
-            for (int k = 0; k <= DIM; ++k) {
-                const int id = P.simplices[s * (DIM + 1) + k];
+            for (int k = 0; k < 3; ++k) {
+                const int id = P.simplices[s * 3 + k];
                 ok = ok && id >= 0 && id < P.nv;
                 v[k] = V + P.v_off + (ok ? id : 0);
             }
-            if (DIM == 3) {
-                Tet S;
-                st.ok = ok && canon_tet<2>(g, v, S) == 0;
-                if (st.ok) {
-                    TetGeo<double> G;
-                    tet_setup<double, 2>(S, S.lo, G);
-                    for (int k = 0; k < 4; ++k)
-                        for (int a = 0; a < 3; ++a) {
-                            st.x[k][a] = G.x[k][a] + (double)S.lo[a];
-                            st.n[k][a] = G.n[k][a];
-                        }
-                    for (int f = 0; f < 4; ++f) {
-                        const int va = f == 0 ? 1 : 0;
-                        st.nx[f] = st.n[f][0] * st.x[va][0] + st.n[f][1] * st.x[va][1] + st.n[f][2] * st.x[va][2];
-                        st.hw[f] = 0.5 * (fabs(st.n[f][0]) + fabs(st.n[f][1]) + fabs(st.n[f][2]));
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        st.g[a] = G.g[a];
-                        st.c[a] = G.c[a] + (double)S.lo[a];
-                        st.lo[a] = S.lo[a];
-                        st.hi[a] = S.hi[a];
-                        st.anchor[a] = S.anchor[a];
-                        cell0[a] = S.anchor[a] + S.cell[0][a];
-                    }
-                    st.rhoc = G.rhoc;
-                    mexact = G.mexact;
-                }
-            } else {
+            {
                 Tri S;
                 s2.ok = ok && canon_tri(g, v, S) == 0;
                 if (s2.ok) {
@@ -454,30 +486,24 @@ __global__ void __launch_bounds__(CLIP_THREADS) k_project_clip(const __grid_cons
             }
         }
         __syncthreads();
-        if (DIM == 3 ? !st.ok : !s2.ok) continue;
+        if (!s2.ok) continue;
         const GridDesc& g = T.p[prob].g;
         double* const out = T.p[prob].out;
-        const int* lo = DIM == 3 ? st.lo : s2.lo;
-        const int* hi = DIM == 3 ? st.hi : s2.hi;
-        const int* an = DIM == 3 ? st.anchor : s2.anchor;
-        const long long ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = DIM == 3 ? hi[2] - lo[2] + 1 : 1;
-        const long long ncell = ex * ey * ez;
+        const int* lo = s2.lo;
+        const int* hi = s2.hi;
+        const int* an = s2.anchor;
+        const long long ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1;
+        const long long ncell = ex * ey;
         double mine = 0.0;  // this thread's pieces (for the closure)
 #pragma unroll 1
         for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
             const long long r = c / ex;
-            const int i = (int)(c - r * ex), j = (int)(r % ey), k = (int)(r / ey);
-            R m;
-            if (DIM == 3) {
-                const double o[3] = {(double)(lo[0] + i), (double)(lo[1] + j), (double)(lo[2] + k)};
-                m = clip_cell_3d<R>(st, o);
-            } else {
-                const double o[2] = {(double)(lo[0] + i), (double)(lo[1] + j)};
-                m = clip_cell_2d<R>(s2, o);
-            }
+            const int i = (int)(c - r * ex), j = (int)r;
+            const double o[2] = {(double)(lo[0] + i), (double)(lo[1] + j)};
+            const R m = clip_cell_2d<R>(s2, o);
             if (m == R(0)) continue;
             mine += (double)m;
-            const long long idx = flat_cell(g, an[0] + lo[0] + i, an[1] + lo[1] + j, DIM == 3 ? an[2] + lo[2] + k : 0);
+            const long long idx = flat_cell(g, an[0] + lo[0] + i, an[1] + lo[1] + j, 0);
             if (idx >= 0) atomicAdd(out + idx, (double)m);
         }
         if (closure) {
@@ -518,9 +544,9 @@ cudaError_t launch_clip(const LaunchArgs& L, int fp32, cudaStream_t st) {
     } else {
         const unsigned blocks = (unsigned)(L.num_sms * 4);
         if (fp32)
-            k_project_clip<2, float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
+            k_project_clip2<float><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
         else
-            k_project_clip<2, double><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
+            k_project_clip2<double><<<blocks, CLIP_THREADS, 0, st>>>(L.T, L.verts, L.clip_list, cnt, L.clip_cap);
     }
     return cudaGetLastError();
 }

@@ -73,6 +73,9 @@ def _args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 plain path")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-problem step (c5)")
+    ap.add_argument("--amr", type=int, default=None,
+                    help="also time the projection through the levels 0..AMR with donor-cell gather (cdp_project_amr); "
+                         "default: 3 for the c2 and c4 workloads, none otherwise")
     return ap.parse_args(argv)
 
 
@@ -385,6 +388,49 @@ def bench_projection(a, pkg, proj, dev, stream, name, ws, rank, headline):
                "d2h_bytes_per_step": int(ho.numel() * 8), "ms_per_step": mse}
         del hp, hs, hr, ho, dpos, dsimp, drho
 
+    amr = None
+    lmax = a.amr if a.amr is not None else (3 if name in ("c2", "c4") else 0)
+    while lmax > 0 and any(n % (1 << lmax) for n in mesh.grid):
+        lmax -= 1
+    if lmax > 0:
+        # the AMR projection (Sect. 4.4): timed like the exact one, and compared with it: block sums
+        # over the coarsest level's cells agree, single cells differ where coarse levels spread mass
+        exact = out.clone()
+        proj.project(pos, simp, rho, mesh.grid, mesh.box_lo, mesh.box_len, True, precision=pkg.CDP_FP32_MIXED,
+                     out=exact, stream=stream)
+        _, sta = proj.project_amr(pos, simp, rho, mesh.grid, lmax, mesh.box_lo, mesh.box_len, True,
+                                  precision=pkg.CDP_FP32_MIXED, out=out, stream=stream, stats=True)
+        b = 1 << lmax
+        shp = []
+        for n in mesh.grid:
+            shp += [n // b, b]
+        red = tuple(range(1, 2 * mesh.dim, 2))
+        bs_e, bs_a = exact.reshape(shp).sum(dim=red), out.reshape(shp).sum(dim=red)
+        scale_e = float(exact.abs().max())
+        step_amr = lambda: proj.project_amr(pos, simp, rho, mesh.grid, lmax, mesh.box_lo, mesh.box_len, True,
+                                            precision=pkg.CDP_FP32_MIXED, out=out, stream=stream)
+        for _ in range(a.warmup):
+            step_amr()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            step_amr()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        msa = max_over_ranks(e0.elapsed_time(e1) / a.steps, ws, dev)
+        amr = {"max_level": lmax, "ms_per_step": msa, "value": job_throughput(ws, ns, msa), "unit": UNIT,
+               "speedup_vs_exact": ms32 / msa,
+               "corners": {k: sta[k] for k in ("corners_a", "corners_b", "corners_c", "corners_d")},
+               "block_sum_max_rel_diff": float((bs_e - bs_a).abs().max()) / float(bs_e.abs().max()),
+               "cell_max_rel_diff": float((exact - out).abs().max()) / scale_e,
+               "what": f"cdp_project_amr, FP32-mixed: every simplex projected exactly onto grid / 2^l, "
+                       f"l = min({lmax}, floor(log2 of its smallest height in cells)), then donor-cell gather"}
+        del exact, bs_e, bs_a
+
     peaks = _json_file("ALU_PEAKS.json")
     dim = mesh.dim
     # 3D: vertex records, set-up + main kernel per batch of 2^24, large tetrahedra, then the accuracy
@@ -413,6 +459,8 @@ def bench_projection(a, pkg, proj, dev, stream, name, ws, rank, headline):
         "gpu_launches": launches_per_step * a.steps,
         "e2e": e2e,
     }
+    if amr is not None:
+        line["amr"] = amr
     del pos, simp, rho, out
     return line, mesh
 

@@ -36,8 +36,8 @@ namespace {
 // the largest |facet normal| = twice the facet area; 2D: 2|A| over the longest edge), and the level
 // l = min(max_level, floor(log2 eta)) (0 when eta < 2).  The edge vectors are the fixed-point
 // differences to vertex 0 at its minimal image (exact in FP64: below 2^53), the rest is FP64
-// arithmetic (relative error ~1e-15: a simplex whose height is that close to a power of two may take
-// either level).  Invalid simplices get level 0; the set-up reports them there.
+// arithmetic on squares (relative error ~1e-15: a simplex whose height is that close to a power of
+// two may take either level).  Invalid simplices get level 0; the set-up reports them there.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_amr_levels(const __grid_constant__ ProbTable T, const VertexRec* __restrict__ V,
                                                      int max_level, unsigned char* __restrict__ levels) {
@@ -50,7 +50,9 @@ __global__ void __launch_bounds__(256) k_amr_levels(const __grid_constant__ Prob
             id[k] = __ldg(P.simplices + s * (DIM + 1) + k);
             ok = ok && id[k] >= 0 && id[k] < P.nv;
         }
-        double eta = 0.0;
+        // D |V| and the largest facet measure, squared (no square root or division: the level is the
+        // number of l in 1 .. max_level with (D |V|)^2 >= 4^l (largest facet measure)^2)
+        double h2 = 0.0, a2 = 0.0;
         if (ok) {
             const VertexRec* v0 = V + P.v_off + id[0];
             double e[DIM][3];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(256) k_amr_levels(const __grid_constant__ Prob
                 // facet normals: n_f = (p_b - p_a) x (p_c - p_a) over the facets (a, b, c), p_0 = 0
                 const double z[3] = {0.0, 0.0, 0.0};
                 const double* p[4] = {z, e[0], e[1], e[2 % DIM]};
-                double amax = 0.0, vol6 = 0.0;
+                double vol6 = 0.0;
                 for (int f = 0; f < 4; ++f) {
                     const int a = f == 0 ? 1 : 0, b = f <= 1 ? 2 : 1, c = f <= 2 ? 3 : 2;
                     double u[3], w[3];
@@ -80,21 +82,21 @@ __global__ void __launch_bounds__(256) k_amr_levels(const __grid_constant__ Prob
                     }
                     const double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2],
                                  n2 = u[0] * w[1] - u[1] * w[0];
-                    amax = fmax(amax, sqrt(n0 * n0 + n1 * n1 + n2 * n2));
-                    if (f == 3) vol6 = fabs(n0 * e[2 % DIM][0] + n1 * e[2 % DIM][1] + n2 * e[2 % DIM][2]);
+                    a2 = fmax(a2, n0 * n0 + n1 * n1 + n2 * n2);
+                    if (f == 3) vol6 = n0 * e[2 % DIM][0] + n1 * e[2 % DIM][1] + n2 * e[2 % DIM][2];
                 }
-                eta = amax > 0.0 ? vol6 / amax : 0.0;
+                h2 = vol6 * vol6;
             } else {
-                const double area2 = fabs(e[0][0] * e[1 % DIM][1] - e[0][1] * e[1 % DIM][0]);
+                const double area2 = e[0][0] * e[1 % DIM][1] - e[0][1] * e[1 % DIM][0];
                 const double dx = e[1 % DIM][0] - e[0][0], dy = e[1 % DIM][1] - e[0][1];
-                const double lmax = sqrt(fmax(fmax(e[0][0] * e[0][0] + e[0][1] * e[0][1],
-                                                   e[1 % DIM][0] * e[1 % DIM][0] + e[1 % DIM][1] * e[1 % DIM][1]),
-                                              dx * dx + dy * dy));
-                eta = lmax > 0.0 ? area2 / lmax : 0.0;
+                a2 = fmax(fmax(e[0][0] * e[0][0] + e[0][1] * e[0][1],
+                               e[1 % DIM][0] * e[1 % DIM][0] + e[1 % DIM][1] * e[1 % DIM][1]),
+                          dx * dx + dy * dy);
+                h2 = area2 * area2;
             }
         }
         int level = 0;
-        while (level < max_level && eta >= (double)(2 << level)) ++level;
+        while (level < max_level && a2 > 0.0 && h2 >= (double)(1 << (2 * level + 2)) * a2) ++level;
         levels[s] = (unsigned char)level;
     }
 }

@@ -175,7 +175,8 @@ CDP_API int cdp_project_amr(cdp_ctx* ctx, const cdp_problem* prob, int precision
 /* Largest n_verts and n_simplices accepted by cdp_project_noalloc, and the size of its static
  * device scratch, held by every process that loads the library on every device it uses: 32 bytes
  * per vertex (8 MiB), three lists of 4 bytes per simplex (large, deferred and clipped simplices,
- * 18 MiB), and the geometry records of one batch of 16,384 tetrahedra (9.4 MiB). */
+ * 18 MiB), and the geometry records of one batch of 16,384 tetrahedra (9.5 MiB), 37,291,008 bytes
+ * in all with the counters and box sizes. */
 #define CDP_NOALLOC_MAX_VERTS 262144
 #define CDP_NOALLOC_MAX_SIMPLICES 1572864
 #define CDP_NOALLOC_SCRATCH_BYTES 37291008

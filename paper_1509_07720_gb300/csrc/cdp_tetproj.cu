@@ -53,7 +53,7 @@ constexpr int TB_ACAP = 64;                 // runs of A nodes awaiting evaluati
 constexpr int TB_PCAP = 64;                 // pierced grid lines awaiting their facet searches, per warp
 constexpr int TB_OWN_BITS = 7;              // tetrahedron-of-chunk index in a queued record
 constexpr unsigned FULL = 0xffffffffu;
-static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS, "chunk index does not fit");
+static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS && TB_NT % 32 == 0, "chunk index does not fit");
 
 // default largest bounding box (cells) projected by the main kernel (the size-class threshold; the
 // launch may choose another up to the block's box slots), and the block's box slots (FP32: sized
@@ -113,7 +113,7 @@ struct TetShared {
                                      // the node range [x, y] clipped to the tile (empty: x > y)
     BigState bs;                     // its tiling state
     int wsum[TB_WARPS];              // block-scan scratch
-    int wsum3[3];                    // the three phases' item counts of units 0..31
+    int wsum3[TB_NT / 32][3];        // the three phases' item counts of each scanning warp's 32 units
     int pre3[3][TB_NT];              // inclusive prefixes of the three phases' item counts
     float red[3][TB_WARPS];          // block-reduction scratch of the mass closure
 };
@@ -714,10 +714,11 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
     unsigned long long* const aq = sh->aq[warp];
     unsigned long long* const pq = sh->pq[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
-    // the item counts of the three phases of the round's units (threads 0..63), scanned at once
+    // the item counts of the three phases of the round's units (threads 0 .. TB_NT - 1), scanned at once
     {
+        constexpr int SW = TB_NT / 32;  // the warps that scan, one unit per thread
         int m0 = in ? 4 : 0, m1 = in ? n_cross : 0, m2 = in ? n_lines : 0;
-        if (warp < 2) {
+        if (warp < SW) {
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int t0 = __shfl_up_sync(FULL, m0, o), t1 = __shfl_up_sync(FULL, m1, o),
@@ -728,19 +729,19 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                     m2 += t2;
                 }
             }
-            if (warp == 0 && lane == 31) {
-                sh->wsum3[0] = m0;
-                sh->wsum3[1] = m1;
-                sh->wsum3[2] = m2;
+            if (lane == 31) {
+                sh->wsum3[warp][0] = m0;
+                sh->wsum3[warp][1] = m1;
+                sh->wsum3[warp][2] = m2;
             }
         }
         __syncthreads();
-        if (warp == 1) {
-            m0 += sh->wsum3[0];
-            m1 += sh->wsum3[1];
-            m2 += sh->wsum3[2];
-        }
-        if (warp < 2) {
+        if (warp < SW) {
+            for (int w = 0; w < warp; ++w) {
+                m0 += sh->wsum3[w][0];
+                m1 += sh->wsum3[w][1];
+                m2 += sh->wsum3[w][2];
+            }
             sh->pre3[0][tid] = m0;
             sh->pre3[1][tid] = m1;
             sh->pre3[2][tid] = m2;

@@ -107,7 +107,7 @@ typedef struct {
     uint64_t n_zero_volume;   /* simplices of zero volume (no contribution) */
     uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
     uint64_t n_small;         /* simplices projected by the main kernel (3D: bounding box <= 1280 cells) */
-    uint64_t n_large;         /* tetrahedra with a larger bounding box: projected tile by tile (18^3 cells)
+    uint64_t n_large;         /* tetrahedra with a larger bounding box: projected tile by tile (23^3 cells)
                                  by the large-tetrahedron kernel */
     uint64_t n_large_tiles;   /* tiles of those tetrahedra */
     uint64_t corners_a;       /* (corner, cell) incidences of type A: grid node inside a simplex */
@@ -284,7 +284,7 @@ CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
  *   - 3D, the size-class threshold: the largest bounding box (cells) a tetrahedron of the main kernel
  *     may have -- larger ones are tiled by the large-tetrahedron kernel -- among 640, 1280 (the
  *     default), 2560 and the block's box slots (6144 FP32, 10240 FP64);
- *   - 3D, the tile edge of the large tetrahedra: 12 or 18 cells (default 18).
+ *   - 3D, the tile edge of the large tetrahedra: 18 or 23 cells (default 23).
  * Each setting is kept only if it is faster than the best so far.  With a non-null cache_path the
  * choice is first looked up in that text file (lines "<device> dim<D> <precision> <multiplier>
  * <threshold> <edge>"; the last entry of a key wins) and, when tuned, appended to it.

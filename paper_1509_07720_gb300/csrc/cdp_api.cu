@@ -557,7 +557,7 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
         if (chosen) {
             chosen[0] = c->grid_mult[d3][fp32];
             chosen[1] = d3 ? (c->max_cells[fp32] ? c->max_cells[fp32] : 1280) : 0;
-            chosen[2] = d3 ? (c->tile_edge[fp32] ? c->tile_edge[fp32] : 18) : 0;
+            chosen[2] = d3 ? (c->tile_edge[fp32] ? c->tile_edge[fp32] : cdp::tet_tile_edge()) : 0;
         }
     };
     // the cache: lines "<key> <multiplier> <threshold> <tile edge>", the last entry of a key wins
@@ -570,7 +570,7 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
                 const size_t n = strlen(key);
                 int m = 0, mc = 0, te = 0;
                 if (strncmp(line, key, n) == 0 && line[n] == ' ' && sscanf(line + n, "%d %d %d", &m, &mc, &te) == 3 &&
-                    (m == 1 || m == 2 || m == 4 || m == 8) && mc >= 0 && mc <= slots && (te == 0 || (te >= 4 && te <= 18))) {
+                    (m == 1 || m == 2 || m == 4 || m == 8) && mc >= 0 && mc <= slots && (te == 0 || (te >= 4 && te <= cdp::tet_tile_edge()))) {
                     found = m;
                     fmc = mc;
                     fte = te;
@@ -620,7 +620,7 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     };
     static const int kMults[] = {1, 2, 4, 8};
     const int kCells[] = {640, 1280, 2560, slots};
-    static const int kEdges[] = {12, 18};
+    const int kEdges[] = {18, cdp::tet_tile_edge()};
     float best_ms = 0.f;
     bool have = false;
     for (int i = 0; i < 4 && rc == CDP_OK; ++i) {

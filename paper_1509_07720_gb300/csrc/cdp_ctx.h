@@ -38,7 +38,7 @@ struct cdp_ctx {
     int grid_mult[2][2];  // [dim == 3][fp32]: the main kernel's persistent grid, in multiples of its
                           // resident blocks (8 unless cdp_autotune chose another)
     int max_cells[2];     // [fp32]: 3D size-class threshold (0: the default, 1280 cells)
-    int tile_edge[2];     // [fp32]: tile edge of the large tetrahedra (0: the default, 18 cells)
+    int tile_edge[2];     // [fp32]: tile edge of the large tetrahedra (0: the default, tet_tile_edge() cells)
     cdp::VertexRec* verts;
     size_t verts_cap;
     int* queue;           // list of the large tetrahedra (tiled by the main kernel)

@@ -140,7 +140,7 @@ struct LaunchArgs {
     int accuracy;       // 1: accuracy control (AccCtl); 0: every simplex by Franklin's sum
     int max_cells;      // 3D size-class threshold: largest bounding box (cells) of the main kernel
                         // (0: the default; at most the block's box slots, tet_box_slots)
-    int tile_edge;      // tile edge (cells) of the large tetrahedra (0: the default; 4 .. 18)
+    int tile_edge;      // tile edge (cells) of the large tetrahedra (0: the default; 4 .. tet_tile_edge())
     const unsigned char* levels;  // AMR projection (cdp_amr.cu): the level of every simplex of the
                         // mesh; the table's entry p is level p and sets up only the simplices of
                         // that level (null: every simplex in every entry)
@@ -169,12 +169,13 @@ cudaError_t configure_tet();
 int resident_blocks_tet(int fp32);
 // bytes of one geometry record of the tetrahedron kernel
 size_t tet_geo_bytes(int fp32);
-// cells of one tile of a large tetrahedron (of the largest edge)
+// cells of one tile of a large tetrahedron (of the largest edge), and that edge
 size_t tet_tile_cells();
+int tet_tile_edge();
 // box slots of a block of the main kernel (the largest size-class threshold)
 int tet_box_slots(int fp32);
 // tiles of a large tetrahedron whose FP32 pieces a block keeps between the two passes
-constexpr int CDP_TILE_STORE_PER_BLOCK = 64;
+constexpr int CDP_TILE_STORE_PER_BLOCK = 32;
 // set-up and main kernel over batches of geo_cap tetrahedra, then the large-tetrahedron kernel;
 // `after_setup` and `mid` (optional) are recorded after the first batch's set-up kernel and before
 // the large-tetrahedron kernel

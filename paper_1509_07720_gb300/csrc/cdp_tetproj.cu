@@ -22,7 +22,7 @@
 // (tetrahedron, cell) piece.
 //
 // k_project_big, launched after it, takes the large tetrahedra of the list one at a time per block
-// and projects each in tiles of 18^3 cells: one unit per tile, its record in the tile's frame, its
+// and projects each in tiles of TB_TE^3 cells: one unit per tile, its record in the tile's frame, its
 // items (planes, lines, vertices) clipped to the tile, its box flushed by the whole block.  A
 // corner on a tile face is evaluated in both tiles, each keeping the cells of its own.  Tiles
 // outside a facet plane are skipped; the x lines leave their runs of inside grid nodes in a table,
@@ -61,9 +61,11 @@ static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS && TB_NT % 32 =
 constexpr int TB_MAX_CELLS = 1280;
 // largest tile edge (cells) of a tetrahedron whose bounding box exceeds the threshold (the launch
 // chooses its edge up to this; both precisions take the same default, so that they take the same
-// decisions tile by tile), and the x lines of one tile of that edge
-constexpr int TB_TE = 18;
-constexpr int TB_RUNS = (TB_TE + 1) * (TB_TE + 1);
+// decisions tile by tile), and the cells of one tile of that edge.  The large-tetrahedron kernel
+// has a shared-memory layout of its own (one unit, no chunk records) whose box holds such a tile:
+// the work of a tile grows with its surface (its grid lines), its cells with its volume, so the
+// largest tile that leaves three FP32 blocks per SM is the fastest.
+constexpr int TB_TE = 23;
 constexpr int TB_TILE_CELLS = TB_TE * TB_TE * TB_TE;
 
 template <typename R>
@@ -95,28 +97,41 @@ struct BigPass {
     long long clip_cap;
 };
 
-template <typename R>
-struct TetShared {
-    TetGeo<R> geo[TB_NT];
-    R box[BoxCap<R>::value];
+// The block's shared memory: NT units of a round (their records, box placements and item counts), a
+// box of BOXN slots, the warps' queues, and for the tile rounds a run table of tiles of edge up to TE.
+template <typename R, int NT, int BOXN, int TE>
+struct TetSharedT {
+    using Real = R;
+    static constexpr int kNT = NT;                     // units of a round
+    static constexpr int kScan = NT < 32 ? 32 : NT;    // entries of the round's item-count scan
+    static constexpr int kBox = BOXN;                  // box slots
+    static constexpr int kTE = TE;                     // largest tile edge of the run table
+    static constexpr int kRuns = (TE + 1) * (TE + 1);  // its x lines
+    TetGeo<R> geo[NT];
+    R box[BOXN];
     Rec q[TB_WARPS][TB_QCAP];
     unsigned long long aq[TB_WARPS][TB_ACAP];
     unsigned long long pq[TB_WARPS][TB_PCAP];  // pierced lines awaiting their facet searches
-    unsigned short xcum[TB_NT][18];  // running count of the crossings of the (edge, axis) pairs
-    int boff[TB_NT];                 // first box slot of each tetrahedron of the round
-    int lr[TB_NT][6];                // grid-line ranges of each unit (unit_line_ranges: r0[3], n[3])
-    int td[TB_NT][3];                // box (tile) dimensions of each unit: its bounding box, or one tile
+    unsigned short xcum[NT][18];     // running count of the crossings of the (edge, axis) pairs
+    int boff[NT];                    // first box slot of each tetrahedron of the round
+    int lr[NT][6];                   // grid-line ranges of each unit (unit_line_ranges: r0[3], n[3])
+    int td[NT][3];                   // box (tile) dimensions of each unit: its bounding box, or one tile
                                      // of a tetrahedron whose bounding box exceeds TB_MAX_CELLS
     TetGeo<R> big0;                  // the large tetrahedron being tiled, in the frame of its tile 0
-    short2 runs[TB_RUNS];            // tile rounds: grid nodes inside the tetrahedron on the x line
-                                     // through (y, z) = (j, k) of the tile, entry j + (TB_TE + 1) k:
+    short2 runs[kRuns];              // tile rounds: grid nodes inside the tetrahedron on the x line
+                                     // through (y, z) = (j, k) of the tile, entry j + (TE + 1) k:
                                      // the node range [x, y] clipped to the tile (empty: x > y)
     BigState bs;                     // its tiling state
     int wsum[TB_WARPS];              // block-scan scratch
-    int wsum3[TB_NT / 32][3];        // the three phases' item counts of each scanning warp's 32 units
-    int pre3[3][TB_NT];              // inclusive prefixes of the three phases' item counts
+    int wsum3[kScan / 32][3];        // the three phases' item counts of each scanning warp's 32 units
+    int pre3[3][kScan];              // inclusive prefixes of the three phases' item counts
     float red[3][TB_WARPS];          // block-reduction scratch of the mass closure
 };
+// the chunk kernel's layout (no tile rounds) and the large-tetrahedron kernel's (one unit per round)
+template <typename R>
+using TetShared = TetSharedT<R, TB_NT, BoxCap<R>::value, 1>;
+template <typename R>
+using TetSharedBig = TetSharedT<R, 1, TB_TILE_CELLS, TB_TE>;
 
 // ------------------------------------------------------------------------------------------
 // accumulation into the box of tetrahedron `own` (cell (x, y, z) of its bounding box)
@@ -128,7 +143,8 @@ template <typename R>
 struct BoxAcc {
     R* box;
     int ex, ey, ez;
-    __device__ __forceinline__ BoxAcc(TetShared<R>* sh, int own)
+    template <class SH>
+    __device__ __forceinline__ BoxAcc(SH* sh, int own)
         : box(sh->box + sh->boff[own]), ex(sh->td[own][0]), ey(sh->td[own][1]), ez(sh->td[own][2]) {}
     __device__ __forceinline__ void operator()(int x, int y, int z, R v) const {
         if ((unsigned)x < (unsigned)ex && (unsigned)y < (unsigned)ey && (unsigned)z < (unsigned)ez)
@@ -304,8 +320,9 @@ __device__ __forceinline__ void unit_line_ranges(const TetGeo<R>& G, const int t
 
 // Item counts of a unit (its crossings per (edge, axis) pair, as running counts in xcum, and its
 // grid lines, whose ranges go to lr), with the planes and lines clipped to the unit's box.
-template <typename R>
-__device__ __forceinline__ void unit_prepare(TetShared<R>* sh, int u, int& n_cross, int& n_lines) {
+template <class SH>
+__device__ __forceinline__ void unit_prepare(SH* sh, int u, int& n_cross, int& n_lines) {
+    using R = typename SH::Real;
     const TetGeo<R>& G = sh->geo[u];
     const int* td = sh->td[u];
     int run = 0;
@@ -331,8 +348,9 @@ __device__ __forceinline__ void unit_prepare(TetShared<R>* sh, int u, int& n_cro
 }
 
 // B: vertex i of tetrahedron own
-template <typename R>
-__device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
+template <class SH>
+__device__ __forceinline__ void item_vertex(SH* sh, int own, int i) {
+    using R = typename SH::Real;
     const TetGeo<R>& G = sh->geo[own];
     const int v0 = G.cell[i][0], v1 = G.cell[i][1], v2 = G.cell[i][2];
     if ((unsigned)v0 >= (unsigned)sh->td[own][0] || (unsigned)v1 >= (unsigned)sh->td[own][1] ||
@@ -347,8 +365,9 @@ __device__ __forceinline__ void item_vertex(TetShared<R>* sh, int own, int i) {
 
 // crossing t of tetrahedron own: its C record (the crossing point's cells along the two other axes
 // located with the exact-sign search, vertex coordinates read once into registers)
-template <typename R>
-__device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, int t, UnitCounts* cnt) {
+template <class SH>
+__device__ __forceinline__ Rec item_crossing(const SH* sh, int own, int t, UnitCounts* cnt) {
+    using R = typename SH::Real;
     const unsigned short* cum = sh->xcum[own];
     // first (edge, axis) pair whose running count exceeds t
     int p = 0;
@@ -415,9 +434,10 @@ __device__ __forceinline__ Rec item_crossing(const TetShared<R>* sh, int own, in
 
 // Line t of tetrahedron own: which facets the grid line pierces.  Returns the pierced-line record
 // (facet mask in bits 0-3, l in 4-5, dj in 6-16, dk in 17-27; 0 when the line misses).
-template <typename R>
-__device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>* sh, int own, int t,
+template <class SH>
+__device__ __forceinline__ unsigned long long item_line_test(const SH* sh, int own, int t,
                                                              UnitCounts* cnt) {
+    using R = typename SH::Real;
     const TetGeo<R>& G = sh->geo[own];
     // lines along l through the grid points (dj, dk) inside the bounding box and the unit's box
     const int* lr = sh->lr[own];
@@ -470,9 +490,10 @@ __device__ __forceinline__ unsigned long long item_line_test(const TetShared<R>*
 
 // A pierced line (record of item_line_test): its D records (one per pierced facet, the cell along
 // the line located with the exact-sign search) and the run of A nodes between them (x lines only).
-template <typename R, bool TILE>
-__device__ __forceinline__ int item_line_facets(TetShared<R>* sh, int own, unsigned long long pr, Rec& r0,
+template <bool TILE, class SH>
+__device__ __forceinline__ int item_line_facets(SH* sh, int own, unsigned long long pr, Rec& r0,
                                                 Rec& r1, unsigned long long& arun, UnitCounts* cnt) {
+    using R = typename SH::Real;
     const TetGeo<R>& G = sh->geo[own];
     const unsigned hits = (unsigned)(pr & 15u);
     const int l = (int)((pr >> 4) & 3u), dj = (int)((pr >> 6) & 2047u), dk = (int)((pr >> 17) & 2047u);
@@ -515,7 +536,7 @@ __device__ __forceinline__ int item_line_facets(TetShared<R>* sh, int own, unsig
     const int cx0 = mlo + 1 > 0 ? mlo + 1 : 0, cx1 = mhi < sh->td[own][0] ? mhi : sh->td[own][0];
     if (l == 0 && npierced == 2 && cx1 >= cx0) {
         if (TILE)
-            sh->runs[dj + (TB_TE + 1) * dk] = make_short2((short)cx0, (short)cx1);
+            sh->runs[dj + (SH::kTE + 1) * dk] = make_short2((short)cx0, (short)cx1);
         else
             arun = (unsigned long long)cx0 | ((unsigned long long)cx1 << 11) | ((unsigned long long)dj << 22) |
                    ((unsigned long long)dk << 33) | (1ull << 51);
@@ -527,8 +548,9 @@ __device__ __forceinline__ int item_line_facets(TetShared<R>* sh, int own, unsig
 // evaluation of queued corners
 // ------------------------------------------------------------------------------------------
 
-template <typename R, bool STATS>
-__device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, UnitCounts& cnt) {
+template <bool STATS, class SH>
+__device__ __forceinline__ void eval_CD(SH* sh, Rec r, bool is_c, UnitCounts& cnt) {
+    using R = typename SH::Real;
     const int own = (int)((r >> 40) & ((1 << TB_OWN_BITS) - 1));
     const TetGeo<R>& G = sh->geo[own];
     BoxAcc<R> acc(sh, own);
@@ -546,8 +568,9 @@ __device__ __forceinline__ void eval_CD(TetShared<R>* sh, Rec r, bool is_c, Unit
 }
 
 // a run of A nodes (grid nodes inside the tetrahedron on one x line): the 8 cells of each node
-template <typename R, bool STATS>
-__device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, UnitCounts& cnt) {
+template <bool STATS, class SH>
+__device__ __forceinline__ void eval_A(SH* sh, unsigned long long r, UnitCounts& cnt) {
+    using R = typename SH::Real;
     const int own = (int)((r >> 44) & ((1 << TB_OWN_BITS) - 1));
     const int cx0 = (int)(r & 2047), cx1 = (int)((r >> 11) & 2047);
     const int dj = (int)((r >> 22) & 2047), dk = (int)((r >> 33) & 2047);
@@ -584,15 +607,16 @@ __device__ __forceinline__ void eval_A(TetShared<R>* sh, unsigned long long r, U
 // terms sum to exactly that).  Otherwise the A terms of its inside corners are summed with the
 // cell's piece origin.  Columns are disjoint and the round's other phases are done, so the box
 // entries are updated without atomics.  Returns the number of (A corner, cell) incidences.
-template <typename R>
-__device__ __noinline__ unsigned item_column(TetShared<R>* sh, int t) {
+template <class SH>
+__device__ __noinline__ unsigned item_column(SH* sh, int t) {
+    using R = typename SH::Real;
     const int ex = sh->td[0][0], ey = sh->td[0][1];
     const int z = t / ey, y = t - z * ey;
     short2 run[4];
     int amin = 1 << 20, bmax = -(1 << 20), amax = -(1 << 20), bmin = 1 << 20;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        run[w] = sh->runs[(y + (w & 1)) + (TB_TE + 1) * (z + (w >> 1))];
+        run[w] = sh->runs[(y + (w & 1)) + (SH::kTE + 1) * (z + (w >> 1))];
         if (run[w].x <= run[w].y) {
             amin = min(amin, (int)run[w].x);
             bmax = max(bmax, (int)run[w].y);
@@ -695,10 +719,11 @@ __device__ __forceinline__ int block_scan(int v, int* wsum) {
 }
 
 // first index t of the non-decreasing pre[0, TB_NT) with pre[t] > u (u < pre[TB_NT - 1])
+template <int N>
 __device__ __forceinline__ int upper_index(const int* pre, int u) {
     int pos = 0;
 #pragma unroll
-    for (int step = TB_NT / 2; step > 0; step >>= 1)
+    for (int step = N / 2; step > 0; step >>= 1)
         if (pre[pos + step - 1] <= u) pos += step;
     return pos;
 }
@@ -706,8 +731,8 @@ __device__ __forceinline__ int upper_index(const int* pre, int u) {
 // The three phases of one round over the units of the block's shared records whose thread (index
 // < TB_NT) has `in` set: items dealt to the warps 32 at a time, located corners queued per warp and
 // evaluated in full batches into the units' boxes.  Every thread of the block calls it.
-template <typename R, bool STATS, bool TILE>
-__device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cross, int n_lines, UnitCounts& cnt,
+template <bool STATS, bool TILE, class SH>
+__device__ __forceinline__ void round_phases(SH* sh, bool in, int n_cross, int n_lines, UnitCounts& cnt,
                                              UnitCounts* pc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Rec* const q = sh->q[warp];
@@ -716,7 +741,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
     const unsigned lt_mask = (1u << lane) - 1u;
     // the item counts of the three phases of the round's units (threads 0 .. TB_NT - 1), scanned at once
     {
-        constexpr int SW = TB_NT / 32;  // the warps that scan, one unit per thread
+        constexpr int SW = SH::kScan / 32;  // the warps that scan, one unit per thread
         int m0 = in ? 4 : 0, m1 = in ? n_cross : 0, m2 = in ? n_lines : 0;
         if (warp < SW) {
 #pragma unroll
@@ -751,7 +776,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
 #pragma unroll 1
     for (int ph = 0; ph < 3; ++ph) {
         const int* const pre_ph = sh->pre3[ph];
-        const int tot = pre_ph[TB_NT - 1];
+        const int tot = pre_ph[SH::kScan - 1];
         // item rounds of 32 dealt to the warps in turn; each warp queues and evaluates its own
         // located corners
         const int nrounds = (tot + 31) >> 5;
@@ -764,7 +789,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
             unsigned long long pline = 0;
             int own = 0;
             if (u < tot) {
-                own = upper_index(pre_ph, u);
+                own = upper_index<SH::kScan>(pre_ph, u);
                 const int t = u - (own > 0 ? pre_ph[own - 1] : 0);
                 if (ph == 0) {
                     item_vertex(sh, own, t);
@@ -801,7 +826,7 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                     if ((unsigned)lane < pav) {
                         const unsigned long long pr = pq[(phead + lane) & (TB_PCAP - 1)];
                         lown = (int)((pr >> 28) & ((1u << TB_OWN_BITS) - 1u));
-                        nr = item_line_facets<R, TILE>(sh, lown, pr, d0, d1, arun, pc);
+                        nr = item_line_facets<TILE>(sh, lown, pr, d0, d1, arun, pc);
                     }
                     phead += pav < 32u ? pav : 32u;
                     const Rec ob = (Rec)lown << 40;
@@ -818,13 +843,13 @@ __device__ __forceinline__ void round_phases(TetShared<R>* sh, bool in, int n_cr
                 }
                 const bool drain = last_round && pav == 0u;
                 if (cav >= 32u || (drain && cav > 0u)) {
-                    if ((unsigned)lane < cav) eval_CD<R, STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
+                    if ((unsigned)lane < cav) eval_CD<STATS>(sh, q[(head + lane) & (TB_QCAP - 1)], ph == 1, cnt);
                     head += cav < 32u ? cav : 32u;
                     __syncwarp();
                     continue;
                 }
                 if (aav >= 32u || (drain && aav > 0u)) {
-                    if ((unsigned)lane < aav) eval_A<R, STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
+                    if ((unsigned)lane < aav) eval_A<STATS>(sh, aq[(ahead + lane) & (TB_ACAP - 1)], cnt);
                     ahead += aav < 32u ? aav : 32u;
                     __syncwarp();
                     continue;
@@ -915,9 +940,10 @@ __device__ __forceinline__ void list_append(int* list, long long cap, unsigned* 
 // the boxes of every TB_WARPS-th unit.  Each unit's grid is its problem's (T); the units of a round of
 // the first pass belong to one problem (a problem's tetrahedra start a new chunk), so the round's
 // closure keeps every problem's mass.
-template <typename R>
-__device__ __forceinline__ void round_flush(TetShared<R>* sh, const ProbTable& T, bool in, int pre_box,
+template <class SH>
+__device__ __forceinline__ void round_flush(SH* sh, const ProbTable& T, bool in, int pre_box,
                                             int mode, float scale, bool whole, float* sums, float* store) {
+    using R = typename SH::Real;
     constexpr bool fp32 = sizeof(R) == 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // the round's units are a prefix of the box slots: the last one ends at the largest pre_box
@@ -963,7 +989,7 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const ProbTable& T
         } else if (tid == 0) {
             // no piece to carry it: the cell of vertex 0 of the round's first unit
             int t = 0;
-            while (t < TB_NT - 1 && sh->boff[t] < 0) ++t;
+            while (t < SH::kNT - 1 && sh->boff[t] < 0) ++t;
             const TetGeo<R>& G = sh->geo[t];
             const ProbEntry& P = T.p[G.prob];
             const long long idx =
@@ -974,7 +1000,7 @@ __device__ __forceinline__ void round_flush(TetShared<R>* sh, const ProbTable& T
     const int gsize = whole ? TB_THREADS : 32, glane = whole ? tid : lane;
     float f_hi = 0.f, f_lo = 0.f, f_abs = 0.f;  // FLUSH_SCALED: the flushed pieces
 #pragma unroll 1
-    for (int t = whole ? 0 : warp; t < (whole ? 1 : TB_NT); t += TB_WARPS) {
+    for (int t = whole ? 0 : warp; t < (whole ? 1 : SH::kNT); t += TB_WARPS) {
         const int base = sh->boff[t];
         if (base < 0) continue;
         const TetGeo<R>& G = sh->geo[t];
@@ -1265,8 +1291,9 @@ __device__ __forceinline__ bool tile_misses(const TetGeo<R>& B, const BigState& 
 // densities and mass do not depend on it), its box, and the item counts of unit_prepare (one
 // (edge, axis) pair per lane).  Returns whether a tile was found; lane 0 gets n_cross,
 // n_lines and pre_box, and moves bs.tile past the tile.
-template <typename R>
-__device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int& n_lines, int& pre_box) {
+template <class SH>
+__device__ __noinline__ bool tile_setup_warp(SH* sh, int& n_cross, int& n_lines, int& pre_box) {
+    using R = typename SH::Real;
     const int lane = threadIdx.x & 31;
     BigState& b = sh->bs;
     const TetGeo<R>& B = sh->big0;
@@ -1358,10 +1385,11 @@ __device__ __noinline__ bool tile_setup_warp(TetShared<R>* sh, int& n_cross, int
 //   The accuracy control (AccCtl) on the taken tetrahedron: first pass, a steep one is deferred;
 //   second pass, one whose cancellation bound exceeds the accepted error goes to the clip list.
 //   Either way it gets no tile (ntiles = 0) and the next one is taken at the next round.
-template <typename R>
-__device__ __forceinline__ void big_advance(TetShared<R>* sh, const ProbTable& T, const VertexRec* V,
+template <class SH>
+__device__ __forceinline__ void big_advance(SH* sh, const ProbTable& T, const VertexRec* V,
                                             const int* big_list, long long big_cap, Counters* ctr,
                                             const BigPass& bp) {
+    using R = typename SH::Real;
     constexpr bool fp32 = sizeof(R) == 4;
     BigState& b = sh->bs;
     if (fp32 && b.ntiles > 0) {
@@ -1435,7 +1463,7 @@ __device__ __forceinline__ void big_advance(TetShared<R>* sh, const ProbTable& T
     b.live = 0;
     b.scale = 0.f;
     b.s[0] = b.s[1] = b.s[2] = 0.f;
-    for (int t = 1; t < TB_NT; ++t) sh->boff[t] = -1;
+    for (int t = 1; t < SH::kNT; ++t) sh->boff[t] = -1;
 }
 
 // The chunks: block b takes chunks b, b + gridDim.x, ... of the batch's geometry records (thread
@@ -1491,8 +1519,8 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             const bool in = pending && pre_box <= BOX;
             pending = pending && !in;
             if (tid < TB_NT) sh->boff[tid] = in ? pre_box - need : -1;
-            round_phases<R, STATS, false>(sh, in, n_cross, n_lines, cnt, pc);
-            round_flush<R>(sh, T, in, pre_box, SECOND ? FLUSH_CLOSE_UNITS : FLUSH_CLOSE_ROUND, 0.f, false, nullptr,
+            round_phases<STATS, false>(sh, in, n_cross, n_lines, cnt, pc);
+            round_flush(sh, T, in, pre_box, SECOND ? FLUSH_CLOSE_UNITS : FLUSH_CLOSE_ROUND, 0.f, false, nullptr,
                            nullptr);
         }
     }
@@ -1515,9 +1543,10 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
                   Counters* __restrict__ ctr, UnitCounts* __restrict__ stats, BigPass bp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp32 = sizeof(R) == 4;
-    constexpr int BOX = BoxCap<R>::value;
+    using SH = TetSharedBig<R>;
+    constexpr int BOX = SH::kBox;
     static_assert(TB_TILE_CELLS <= BOX, "a tile must fit the block's slots");
-    TetShared<R>* sh = reinterpret_cast<TetShared<R>*>(smem_raw);
+    SH* sh = reinterpret_cast<SH*>(smem_raw);
     const int tid = threadIdx.x;
     for (int e = tid; e < BOX; e += TB_THREADS) sh->box[e] = R(0);
     if (tid == 0) {
@@ -1535,7 +1564,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         const bool advance = sh->bs.tile >= sh->bs.ntiles;
         __syncthreads();  // every thread has read the state; the previous round is done
         if (advance) {
-            if (tid == 0) big_advance<R>(sh, T, V, big_list, big_cap, ctr, bp);
+            if (tid == 0) big_advance(sh, T, V, big_list, big_cap, ctr, bp);
             __syncthreads();
             if (sh->bs.ntiles < 0) break;
             continue;
@@ -1545,7 +1574,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
         const int mode = sh->bs.pass == 0 ? FLUSH_SUM_ONLY : FLUSH_SCALED;
         bool in = false;
         int pre_box = 0;
-        for (int i = tid; i < TB_RUNS; i += TB_THREADS) sh->runs[i] = make_short2(1, 0);
+        for (int i = tid; i < SH::kRuns; i += TB_THREADS) sh->runs[i] = make_short2(1, 0);
         // the corners are counted in the first pass (FP32: the second may reuse the stored pieces)
         const int pass = sh->bs.pass;
         const bool counted = fp32 ? pass == 0 : true;
@@ -1565,7 +1594,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             const int size = sh->td[0][0] * sh->td[0][1] * sh->td[0][2];
             for (int e = tid; e < size; e += TB_THREADS) sh->box[e] = slot[e];
         } else {
-            round_phases<R, STATS, true>(sh, in, n_cross, n_lines, counted ? cnt : cnt_none, counted ? pc : nullptr);
+            round_phases<STATS, true>(sh, in, n_cross, n_lines, counted ? cnt : cnt_none, counted ? pc : nullptr);
             // the cells of the tile, column by column, from the run table of the line phase
             const int ncol = sh->boff[0] >= 0 ? sh->td[0][1] * sh->td[0][2] : 0;
             unsigned na = 0;
@@ -1573,7 +1602,7 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             if (STATS && counted) cnt.a += na;
             __syncthreads();
         }
-        round_flush<R>(sh, T, in, pre_box, mode, sh->bs.scale, true, sh->bs.s, pass == 0 ? slot : nullptr);
+        round_flush(sh, T, in, pre_box, mode, sh->bs.scale, true, sh->bs.s, pass == 0 ? slot : nullptr);
     }
     if (STATS) {
         if (cnt.a) atomicAdd(&stats->a, cnt.a);
@@ -1584,12 +1613,18 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
     }
 }
 
-// three FP32 blocks per SM: 228 KB of shared memory per SM, 1 KB of it reserved per block
-static_assert(3 * (sizeof(TetShared<float>) + 1024) <= 228 * 1024, "three FP32 blocks per SM");
+// three FP32 blocks per SM, for both kernels: 228 KB of shared memory per SM, 1 KB of it reserved
+// per block
+static_assert(3 * (sizeof(TetShared<float>) + 1024) <= 228 * 1024, "three FP32 chunk blocks per SM");
+static_assert(3 * (sizeof(TetSharedBig<float>) + 1024) <= 228 * 1024, "three FP32 tile blocks per SM");
 
 template <typename R>
 static size_t tet_shared_bytes() {
     return sizeof(TetShared<R>);
+}
+template <typename R>
+static size_t big_shared_bytes() {
+    return sizeof(TetSharedBig<R>);
 }
 
 template <typename R, bool STATS>
@@ -1601,7 +1636,7 @@ static cudaError_t configure_one() {
                              (int)tet_shared_bytes<R>());
     if (e) return e;
     return cudaFuncSetAttribute(k_project_big<R, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tet_shared_bytes<R>());
+                                (int)big_shared_bytes<R>());
 }
 
 cudaError_t configure_tet() {
@@ -1633,6 +1668,8 @@ int resident_blocks_tet(int fp32) {
 size_t tet_geo_bytes(int fp32) { return fp32 ? sizeof(TetGeo<float>) : sizeof(TetGeo<double>); }
 
 size_t tet_tile_cells() { return TB_TILE_CELLS; }
+
+int tet_tile_edge() { return TB_TE; }
 
 int tet_box_slots(int fp32) { return fp32 ? BoxCap<float>::value : BoxCap<double>::value; }
 
@@ -1679,10 +1716,10 @@ static cudaError_t launch_tet_r(const LaunchArgs& L, cudaStream_t st, cudaEvent_
     auto big = [&](int second) {
         const BigPass bp = {acc, second, te, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
         if (L.stats)
-            k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
+            k_project_big<R, true><<<(unsigned)big_blocks, TB_THREADS, big_shared_bytes<R>(), st>>>(
                 L.T, L.verts, L.big_list, L.big_cap, L.tile_store, store_tiles, L.ctr, L.stats + 1, bp);
         else
-            k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, tet_shared_bytes<R>(), st>>>(
+            k_project_big<R, false><<<(unsigned)big_blocks, TB_THREADS, big_shared_bytes<R>(), st>>>(
                 L.T, L.verts, L.big_list, L.big_cap, L.tile_store, store_tiles, L.ctr, nullptr, bp);
     };
     // first pass: every tetrahedron, batch by batch; steep ones are deferred

@@ -81,7 +81,7 @@ def _cases():
                                   (1.0,) * 3, False),
         "ragged_grid": mg.Mesh(*(lambda m: (m.pos, m.simplices, m.rho))(mg.make_config("c2", 8)), (29, 31, 33),
                                (0.0,) * 3, (1.0,) * 3, True),
-        # tetrahedra spanning many 18^3 tiles, with many cells entirely inside them (periodic, and
+        # tetrahedra spanning several 23^3 tiles, with many cells entirely inside them (periodic, and
         # clipped by the walls of a non-periodic box)
         "rand3d_huge": mg.random_simplices(3, 6, 96, 22.0, np.random.default_rng(71)),
         "rand3d_huge_walls": mg.random_simplices(3, 5, 40, 30.0, np.random.default_rng(72), periodic=False),

@@ -43,7 +43,7 @@ def _cases():
         "c2_16": mg.make_config("c2", 16),
         "rand3d_mid": mg.random_simplices(3, 400, 16, 2.5, rng),
         "rand2d": mg.random_simplices(2, 600, 32, 3.0, rng),
-        # tetrahedra whose bounding boxes span several 18^3-cell tiles: the large-tetrahedron kernel,
+        # tetrahedra whose bounding boxes span several 23^3-cell tiles: the large-tetrahedron kernel,
         # which here keeps no pieces between its two FP32 passes (no tile store) and recomputes them
         "rand3d_large": mg.random_simplices(3, 4, 96, 20.0, np.random.default_rng(3)),
     }

@@ -106,7 +106,7 @@ typedef struct {
 typedef struct {
     uint64_t n_zero_volume;   /* simplices of zero volume (no contribution) */
     uint64_t n_single_cell;   /* simplices inside one cell (closed form, Algorithm 2 step 1) */
-    uint64_t n_small;         /* simplices projected by the main kernel (3D: bounding box <= 1280 cells) */
+    uint64_t n_small;         /* simplices projected by the main kernel (3D: bounding box <= 1920 cells) */
     uint64_t n_large;         /* tetrahedra with a larger bounding box: projected tile by tile (23^3 cells)
                                  by the large-tetrahedron kernel */
     uint64_t n_large_tiles;   /* tiles of those tetrahedra */
@@ -271,7 +271,7 @@ CDP_API int cdp_timing_enable(cdp_ctx* ctx, int enable);
 /* Synchronise the recorded events and copy the totals (milliseconds) into out_ms[0..n-1], n <= 5:
  * [0] vertex records, [1] per-simplex set-up (3D: the first batch's; the single-cell closed form
  * is applied there), [2] main projection kernel (3D: with the set-up of any later batch),
- * [3] the large-tetrahedron kernel (3D: tetrahedra with a bounding box above 1280 cells, in
+ * [3] the large-tetrahedron kernel (3D: tetrahedra with a bounding box above 1920 cells, in
  * tiles), [4] the accuracy control (the largest cell mass, the second pass over the deferred
  * simplices, clipping).  *calls receives the number of timed cdp_project calls.  Returns the
  * number of slots written. */
@@ -282,8 +282,8 @@ CDP_API int cdp_timing_read(cdp_ctx* ctx, double* out_ms, int n, int* calls);
  * other, three knobs of the context's later projections with the same dimension and precision:
  *   - the main kernel's persistent grid: 1, 2, 4 or 8 times the device's resident blocks (default 8);
  *   - 3D, the size-class threshold: the largest bounding box (cells) a tetrahedron of the main kernel
- *     may have -- larger ones are tiled by the large-tetrahedron kernel -- among 640, 1280 (the
- *     default), 2560 and the block's box slots (6144 FP32, 10240 FP64);
+ *     may have -- larger ones are tiled by the large-tetrahedron kernel -- among 960, 1920 (the
+ *     default), 3840 and the block's box slots (6144 FP32, 10240 FP64);
  *   - 3D, the tile edge of the large tetrahedra: 18 or 23 cells (default 23).
  * Each setting is kept only if it is faster than the best so far.  With a non-null cache_path the
  * choice is first looked up in that text file (lines "<device> dim<D> <precision> <multiplier>

@@ -556,7 +556,7 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     auto report = [&]() {
         if (chosen) {
             chosen[0] = c->grid_mult[d3][fp32];
-            chosen[1] = d3 ? (c->max_cells[fp32] ? c->max_cells[fp32] : 1280) : 0;
+            chosen[1] = d3 ? (c->max_cells[fp32] ? c->max_cells[fp32] : cdp::tet_max_cells()) : 0;
             chosen[2] = d3 ? (c->tile_edge[fp32] ? c->tile_edge[fp32] : cdp::tet_tile_edge()) : 0;
         }
     };
@@ -619,7 +619,7 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
         return r;
     };
     static const int kMults[] = {1, 2, 4, 8};
-    const int kCells[] = {640, 1280, 2560, slots};
+    const int kCells[] = {960, 1920, 3840, slots};
     const int kEdges[] = {18, cdp::tet_tile_edge()};
     float best_ms = 0.f;
     bool have = false;

@@ -37,7 +37,7 @@ struct cdp_ctx {
     int blocks_big[2];    // of the 2D kernel
     int grid_mult[2][2];  // [dim == 3][fp32]: the main kernel's persistent grid, in multiples of its
                           // resident blocks (8 unless cdp_autotune chose another)
-    int max_cells[2];     // [fp32]: 3D size-class threshold (0: the default, 1280 cells)
+    int max_cells[2];     // [fp32]: 3D size-class threshold (0: the default, tet_max_cells())
     int tile_edge[2];     // [fp32]: tile edge of the large tetrahedra (0: the default, tet_tile_edge() cells)
     cdp::VertexRec* verts;
     size_t verts_cap;

@@ -172,6 +172,8 @@ size_t tet_geo_bytes(int fp32);
 // cells of one tile of a large tetrahedron (of the largest edge), and that edge
 size_t tet_tile_cells();
 int tet_tile_edge();
+// the default size-class threshold (cells of a bounding box) of the main kernel
+int tet_max_cells();
 // box slots of a block of the main kernel (the largest size-class threshold)
 int tet_box_slots(int fp32);
 // tiles of a large tetrahedron whose FP32 pieces a block keeps between the two passes

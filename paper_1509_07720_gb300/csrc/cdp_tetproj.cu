@@ -58,7 +58,7 @@ static_assert(TB_NT <= (1 << TB_OWN_BITS) && TB_NT <= TB_THREADS && TB_NT % 32 =
 // default largest bounding box (cells) projected by the main kernel (the size-class threshold; the
 // launch may choose another up to the block's box slots), and the block's box slots (FP32: sized
 // with the rest of the block's shared memory for three resident blocks per SM)
-constexpr int TB_MAX_CELLS = 1280;
+constexpr int TB_MAX_CELLS = 1920;
 // largest tile edge (cells) of a tetrahedron whose bounding box exceeds the threshold (the launch
 // chooses its edge up to this; both precisions take the same default, so that they take the same
 // decisions tile by tile), and the cells of one tile of that edge.  The large-tetrahedron kernel
@@ -70,7 +70,7 @@ constexpr int TB_TILE_CELLS = TB_TE * TB_TE * TB_TE;
 
 template <typename R>
 struct BoxCap {
-    static constexpr int value = sizeof(R) == 4 ? 6144 : TB_MAX_CELLS * TB_WARPS;
+    static constexpr int value = sizeof(R) == 4 ? 6144 : 10240;
 };
 static_assert(BoxCap<float>::value >= TB_MAX_CELLS, "one tetrahedron's box must fit the block's slots");
 
@@ -1216,42 +1216,35 @@ __global__ void __launch_bounds__(128) k_tet_setup(const __grid_constant__ ProbT
 // big_first while the list of large tetrahedra is emptied for the second pass.  The cells of all
 // the grids are taken in the group's cell numbering.
 __global__ void __launch_bounds__(256) k_pass_boundary(const __grid_constant__ ProbTable T, Counters* __restrict__ ctr) {
-    // each thread: a running maximum while its cells stay in one problem, four independent loads in
-    // flight per step
-    double m = 0.0;
-    int pcur = -1;
-    long long pbeg = 0, pend = 0;
-    const double* out = nullptr;  // the current problem's grid, indexed by the group's cell number
+    // problem by problem: the grid's threads stride over its cells (four independent loads in flight
+    // per step), then one maximum per block goes to the problem's word (a thread-level atomic on
+    // the few words of a group would serialise)
+    __shared__ double wmax[8];
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 1
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < T.ncells;) {
-        if (c < pbeg || c >= pend) {
-            if (pcur >= 0 && m > 0.0) atomicMax(&ctr->mmax_bits[pcur], (unsigned long long)__double_as_longlong(m));
-            pcur = find_cell(T, c);
-            pbeg = T.p[pcur].c_off;
-            pend = pcur + 1 < T.n ? T.p[pcur + 1].c_off : T.ncells;
-            out = T.p[pcur].out - pbeg;
-            m = 0.0;
-        }
-        if (c + 3 * stride < pend) {
-            const double a = out[c], b = out[c + stride], d = out[c + 2 * stride],
-                         e = out[c + 3 * stride];
+    for (int p = 0; p < T.n; ++p) {
+        const double* const out = T.p[p].out;
+        const long long n = (p + 1 < T.n ? T.p[p + 1].c_off : T.ncells) - T.p[p].c_off;
+        double m = 0.0;
+        long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll 1
+        for (; c + 3 * stride < n; c += 4 * stride) {
+            const double a = out[c], b = out[c + stride], d = out[c + 2 * stride], e = out[c + 3 * stride];
             m = fmax(fmax(m, fmax(fabs(a), fabs(b))), fmax(fabs(d), fabs(e)));
-            c += 4 * stride;
-        } else {
-            m = fmax(m, fabs(out[c]));
-            c += stride;
         }
-    }
-    // a warp whose lanes ended in one problem reduces first
-    const int p0 = __shfl_sync(FULL, pcur, 0);
-    if (__all_sync(FULL, pcur == p0)) {
+#pragma unroll 1
+        for (; c < n; c += stride) m = fmax(m, fabs(out[c]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
-        if ((threadIdx.x & 31) == 0 && p0 >= 0 && m > 0.0)
-            atomicMax(&ctr->mmax_bits[p0], (unsigned long long)__double_as_longlong(m));
-    } else if (pcur >= 0 && m > 0.0) {
-        atomicMax(&ctr->mmax_bits[pcur], (unsigned long long)__double_as_longlong(m));
+        if (lane == 0) wmax[warp] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bm = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) bm = fmax(bm, wmax[w]);
+            if (bm > 0.0) atomicMax(&ctr->mmax_bits[p], (unsigned long long)__double_as_longlong(bm));
+        }
+        __syncthreads();  // wmax is free
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->big_first = ctr->big_count;
@@ -1670,6 +1663,8 @@ size_t tet_geo_bytes(int fp32) { return fp32 ? sizeof(TetGeo<float>) : sizeof(Te
 size_t tet_tile_cells() { return TB_TILE_CELLS; }
 
 int tet_tile_edge() { return TB_TE; }
+
+int tet_max_cells() { return TB_MAX_CELLS; }
 
 int tet_box_slots(int fp32) { return fp32 ? BoxCap<float>::value : BoxCap<double>::value; }
 

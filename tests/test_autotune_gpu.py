@@ -50,7 +50,7 @@ def test_autotune_then_project(pkg, tmp_path, name, prec):
                            cache_path=str(cache))
         assert m[0] in (1, 2, 4, 8)
         if mesh.dim == 3:
-            assert m[1] in (640, 1280, 2560, 6144 if prec == 1 else 10240) and m[2] in (18, 23)
+            assert m[1] in (960, 1920, 3840, 6144 if prec == 1 else 10240) and m[2] in (18, 23)
         lines = cache.read_text().splitlines()
         assert len(lines) == 1 and lines[0].endswith(" %d %d %d" % m) and f"dim{mesh.dim}" in lines[0]
         # a second context takes the cached choice without timing (the file is not appended to)

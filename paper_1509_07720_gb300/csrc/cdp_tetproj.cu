@@ -740,7 +740,8 @@ __device__ __forceinline__ void round_phases(SH* sh, bool in, int n_cross, int n
     unsigned long long* const pq = sh->pq[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
     // the item counts of the three phases of the round's units (threads 0 .. TB_NT - 1), scanned at once
-    {
+    // (a tile round's one unit: its counts are in pre3 already, written by the warp that set it up)
+    if (!TILE) {
         constexpr int SW = SH::kScan / 32;  // the warps that scan, one unit per thread
         int m0 = in ? 4 : 0, m1 = in ? n_cross : 0, m2 = in ? n_lines : 0;
         if (warp < SW) {
@@ -948,7 +949,10 @@ __device__ __forceinline__ void round_flush(SH* sh, const ProbTable& T, bool in,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // the round's units are a prefix of the box slots: the last one ends at the largest pre_box
     int used_slots = 0;
-    {
+    if (whole) {
+        // one unit, set up before the round's barriers
+        used_slots = sh->boff[0] >= 0 ? sh->td[0][0] * sh->td[0][1] * sh->td[0][2] : 0;
+    } else {
         int m = in ? pre_box : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
@@ -1575,6 +1579,11 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             const bool found = tile_setup_warp(sh, n_cross, n_lines, pre_box);
             in = found && tid == 0;
             if (STATS && in && counted) atomicAdd(&ctr->n_big_tiles, 1ull);
+            // the round's item counts (one unit: every prefix entry is the unit's count)
+            static_assert(SH::kScan == 32, "one warp writes the tile round's item counts");
+            sh->pre3[0][tid] = found ? 4 : 0;
+            sh->pre3[1][tid] = found ? n_cross : 0;
+            sh->pre3[2][tid] = found ? n_lines : 0;
         }
         __syncthreads();  // the tile's unit (or its absence) is set up
         // FP32: the first store_tiles tiles of a pass keep their pieces in the block's slots of

@@ -12,7 +12,6 @@
 // Total mass is kept exactly; the density inside a coarse cell is only resolved at its level, which
 // is the accuracy the AMR trades for speed (a large simplex meets far fewer coarse cells).
 #include <cuda_runtime.h>
-#include <string.h>
 
 #include <new>
 
@@ -149,8 +148,10 @@ extern "C" int cdp_project_amr(cdp_ctx* c, const cdp_problem* p, int precision, 
     if (!c) return CDP_ERR_ARG;
     int rc = check_problem_args(p);
     if (rc) return rc;
-    int fp32 = 0, accuracy = 1;
-    if (!parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
+    {
+        int f = 0, a = 0;
+        if (!parse_precision(precision, &f, &a)) return CDP_ERR_ARG;
+    }
     if (max_level < 0 || max_level > CDP_AMR_MAX_LEVEL) return CDP_ERR_ARG;
     for (int a = 0; a < p->dim; ++a)
         if (p->grid[a] % (1 << max_level) != 0) return CDP_ERR_ARG;
@@ -192,7 +193,8 @@ extern "C" int cdp_project_amr(cdp_ctx* c, const cdp_problem* p, int precision, 
         }
         rc = build_table(lp, max_level + 1, *T);
     }
-    // the coarse grids always start from zero (the output grid only unless accumulating)
+    // every level's grid starts from zero: without accumulate the group's projection zeroes them all;
+    // with it the output grid keeps what it holds and only the coarse ones are zeroed here
     if (rc == CDP_OK && accumulate && cudaMemsetAsync(c->amr, 0, (size_t)coarse * sizeof(double), st) != cudaSuccess)
         rc = CDP_ERR_CUDA;
     if (rc == CDP_OK) rc = project_group(c, *T, precision, accumulate, st, stats != nullptr, c->levels, max_level);

@@ -1502,6 +1502,16 @@ __global__ void __launch_bounds__(TB_THREADS, sizeof(R) == 4 ? 3 : 1)
             for (int w = tid; w < words; w += TB_THREADS) dst[w] = __ldg(src + w);
         }
         const int need = (tid < TB_NT && first + tid < nb) ? __ldg(need_in + first + tid) : 0;
+        {
+            // the block's next chunk of records toward L2 while this one is projected
+            const long long nfirst = (chunk + gridDim.x) * TB_NT;
+            if (nfirst < nb) {
+                const long long nlast = nfirst + TB_NT < nb ? nfirst + TB_NT : nb;
+                const long long bytes = (nlast - nfirst) * (long long)sizeof(TetGeo<R>);
+                const char* base = reinterpret_cast<const char*>(geo + nfirst);
+                if ((long long)tid * 128 < bytes) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + tid * 128));
+            }
+        }
         __syncthreads();
         int n_cross = 0, n_lines = 0;
         if (need > 0) {

@@ -57,8 +57,8 @@ FLOPS_PER_INCIDENCE = {"a": 12, "b": 200, "c": 200, "d": 200}
 # profiles/k_project_tet_c3sub8_full.md (a random 1/8 of the headline workload's tetrahedra,
 # 1,572,864, on its own 256^3 grid): DRAM bytes read + written, and warp instructions issued.
 # They scale with the tetrahedron count.  None while the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_TET = 646.0
-WARP_INST_PER_TET = 2738.8
+TRAFFIC_BYTES_PER_TET = 655.6
+WARP_INST_PER_TET = 2738.9
 
 
 def _args(argv=None):

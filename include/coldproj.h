@@ -255,7 +255,11 @@ typedef struct {
  * vertices, kick dt (eq. kick), drift dt/2 (eq. drift2).  use_graph != 0: the first call with a
  * given argument array captures the whole sequence into a CUDA graph owned by the context and
  * every later call with byte-identical arguments (dt may differ) replays it in one launch.  The
- * first call also creates the FFT plans and sizes the scratch outside the capture. */
+ * first call also creates the FFT plans and sizes the scratch outside the capture.
+ *   precision   CDP_FP64: every step in FP64.  CDP_FP32_MIXED: the projection in FP32-mixed and the
+ *               Poisson transforms in single precision (the source and the potential stay FP64
+ *               arrays; the potential is then accurate to about 1e-6 of its largest value, below the
+ *               FP32-mixed projection's own 1e-5); the other steps in FP64. */
 CDP_API int cdp_step_batched(cdp_ctx* ctx, const cdp_step_problem* probs, int n, int precision, double dt,
                              double four_pi_G, int use_graph, void* stream);
 

@@ -17,6 +17,11 @@ struct FftPlan {
     cufftHandle r2c, c2r;
     cufftDoubleComplex* spec;
     size_t spec_elems;
+    // single-precision transforms of the FP32-mixed time step (made on first use)
+    int have32;
+    cufftHandle r2c32, c2r32;
+    cufftComplex* spec32;
+    float* real32;  // the source, then the potential, in FP32
 };
 
 }  // namespace cdp

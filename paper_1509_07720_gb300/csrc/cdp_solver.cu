@@ -42,8 +42,8 @@ int check_grid(int dim, const int32_t grid[3], const double box_len[3]) {
 // ---------------------------------------------------------------------------------------------
 // Poisson: spectrum of the cell masses times -four_pi_G / (k^2 * cell volume * N), zero mode 0
 // ---------------------------------------------------------------------------------------------
-__global__ void k_green(cufftDoubleComplex* __restrict__ spec, int dim, int n0, int n1, int n2h, int n2,
-                        double k0, double k1, double k2, double scale) {
+template <typename C, typename R>
+__global__ void k_green(C* __restrict__ spec, int dim, int n0, int n1, int n2h, int n2, R k0, R k1, R k2, R scale) {
     long long total = (long long)n0 * n1 * n2h;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -51,21 +51,57 @@ __global__ void k_green(cufftDoubleComplex* __restrict__ spec, int dim, int n0, 
         long long r = t / n2h;
         int b = (int)(r % n1);
         int a = (int)(r / n1);
-        double kk;
+        R kk;
         if (dim == 3) {
             int fa = a <= n0 / 2 ? a : a - n0;
             int fb = b <= n1 / 2 ? b : b - n1;
-            double ka = k0 * fa, kb = k1 * fb, kc = k2 * c;
+            R ka = k0 * fa, kb = k1 * fb, kc = k2 * c;
             kk = ka * ka + kb * kb + kc * kc;
         } else {  // 2D: (n0, n1h) with n1 = 1 placeholder: a = row, c = half column
             int fa = a <= n0 / 2 ? a : a - n0;
-            double ka = k0 * fa, kc = k2 * c;
+            R ka = k0 * fa, kc = k2 * c;
             kk = ka * ka + kc * kc;
         }
-        double gfac = kk > 0.0 ? scale / kk : 0.0;
+        R gfac = kk > R(0) ? scale / kk : R(0);
         spec[t].x *= gfac;
         spec[t].y *= gfac;
     }
+}
+
+// the FP64 source and potential to and from the FP32 transforms' buffer
+__global__ void k_to_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+__global__ void k_to_f64(long long n, const float* __restrict__ x, double* __restrict__ y) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+
+// the single-precision transforms and buffers of a plan (made once)
+int add_plan32(FftPlan& p) {
+    if (p.have32) return CDP_OK;
+    int n[3] = {p.n[0], p.n[1], p.dim == 3 ? p.n[2] : 1};
+    size_t cells = 1;
+    for (int a = 0; a < p.dim; ++a) cells *= (size_t)n[a];
+    if (cudaMalloc(&p.spec32, p.spec_elems * sizeof(cufftComplex)) != cudaSuccess ||
+        cudaMalloc(&p.real32, cells * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        if (p.spec32) cudaFree(p.spec32);
+        p.spec32 = nullptr;
+        p.real32 = nullptr;
+        return CDP_ERR_OOM;
+    }
+    if (cufftPlanMany(&p.r2c32, p.dim, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1) != CUFFT_SUCCESS ||
+        cufftPlanMany(&p.c2r32, p.dim, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1) != CUFFT_SUCCESS) {
+        cudaFree(p.spec32);
+        cudaFree(p.real32);
+        p.spec32 = nullptr;
+        p.real32 = nullptr;
+        return CDP_ERR_CUDA;
+    }
+    p.have32 = 1;
+    return CDP_OK;
 }
 
 FftPlan* get_plan(cdp_ctx* c, int dim, const int32_t grid[3], int* rc) {
@@ -240,40 +276,47 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 
 }  // namespace
 
-// internal: used by cdp_step_batched
+// internal: used by cdp_step_batched.  fp32: the transforms in single precision (the FP32-mixed
+// time step), the source and the potential still FP64 arrays
 int poisson_enqueue(cdp_ctx* c, int dim, const int32_t grid[3], const double box_len[3], double four_pi_G,
-                    const double* mass, double* phi, cudaStream_t st) {
+                    const double* mass, double* phi, cudaStream_t st, bool fp32) {
     int rc = CDP_OK;
     FftPlan* p = get_plan(c, dim, grid, &rc);
     if (!p) return rc;
-    if (cufftSetStream(p->r2c, st) != CUFFT_SUCCESS || cufftSetStream(p->c2r, st) != CUFFT_SUCCESS)
-        return CDP_ERR_CUDA;
-    if (cufftExecD2Z(p->r2c, const_cast<double*>(mass), p->spec) != CUFFT_SUCCESS) return CDP_ERR_CUDA;
+    if (fp32 && (rc = add_plan32(*p))) return rc;
     double ntot = 1.0, cellvol = 1.0;
     for (int a = 0; a < dim; ++a) {
         ntot *= grid[a];
         cellvol *= box_len[a] / grid[a];
     }
+    const long long cells = (long long)ntot;
+    const unsigned cb = blocks_for(cells, 256) > 65535u * 16u ? 65535u * 16u : blocks_for(cells, 256);
     double scale = -four_pi_G / (cellvol * ntot);
     const double twopi = 6.283185307179586476925286766559;
-    if (dim == 3) {
-        int n2h = grid[2] / 2 + 1;
-        long long tot = (long long)grid[0] * grid[1] * n2h;
-        unsigned b = blocks_for(tot, 256);
-        if (b > 65535u * 16u) b = 65535u * 16u;
-        k_green<<<b, 256, 0, st>>>(p->spec, 3, grid[0], grid[1], n2h, grid[2], twopi / box_len[0],
-                                   twopi / box_len[1], twopi / box_len[2], scale);
+    // the Green function on the half spectrum: (n0, n1, n2 / 2 + 1) in 3D, (n0, n1 / 2 + 1) in 2D
+    const int nh = grid[dim - 1] / 2 + 1;
+    const long long tot = dim == 3 ? (long long)grid[0] * grid[1] * nh : (long long)grid[0] * nh;
+    unsigned b = blocks_for(tot, 256);
+    if (b > 65535u * 16u) b = 65535u * 16u;
+    const double k0 = twopi / box_len[0], k1 = dim == 3 ? twopi / box_len[1] : 0.0, k2 = twopi / box_len[dim - 1];
+    const int n1 = dim == 3 ? grid[1] : 1, n2 = grid[dim - 1];
+    if (fp32) {
+        if (cufftSetStream(p->r2c32, st) != CUFFT_SUCCESS || cufftSetStream(p->c2r32, st) != CUFFT_SUCCESS)
+            return CDP_ERR_CUDA;
+        k_to_f32<<<cb, 256, 0, st>>>(cells, mass, p->real32);
+        if (cufftExecR2C(p->r2c32, p->real32, p->spec32) != CUFFT_SUCCESS) return CDP_ERR_CUDA;
+        k_green<cufftComplex, float><<<b, 256, 0, st>>>(p->spec32, dim, grid[0], n1, nh, n2, (float)k0, (float)k1,
+                                                        (float)k2, (float)scale);
+        if (cufftExecC2R(p->c2r32, p->spec32, p->real32) != CUFFT_SUCCESS) return CDP_ERR_CUDA;
+        k_to_f64<<<cb, 256, 0, st>>>(cells, p->real32, phi);
     } else {
-        int n1h = grid[1] / 2 + 1;
-        long long tot = (long long)grid[0] * n1h;
-        unsigned b = blocks_for(tot, 256);
-        if (b > 65535u * 16u) b = 65535u * 16u;
-        k_green<<<b, 256, 0, st>>>(p->spec, 2, grid[0], 1, n1h, grid[1], twopi / box_len[0], 0.0,
-                                   twopi / box_len[1], scale);
+        if (cufftSetStream(p->r2c, st) != CUFFT_SUCCESS || cufftSetStream(p->c2r, st) != CUFFT_SUCCESS)
+            return CDP_ERR_CUDA;
+        if (cufftExecD2Z(p->r2c, const_cast<double*>(mass), p->spec) != CUFFT_SUCCESS) return CDP_ERR_CUDA;
+        k_green<cufftDoubleComplex, double><<<b, 256, 0, st>>>(p->spec, dim, grid[0], n1, nh, n2, k0, k1, k2, scale);
+        if (cufftExecZ2D(p->c2r, p->spec, phi) != CUFFT_SUCCESS) return CDP_ERR_CUDA;
     }
-    if (cudaGetLastError() != cudaSuccess) return CDP_ERR_CUDA;
-    if (cufftExecZ2D(p->c2r, p->spec, phi) != CUFFT_SUCCESS) return CDP_ERR_CUDA;
-    return CDP_OK;
+    return cudaGetLastError() == cudaSuccess ? CDP_OK : CDP_ERR_CUDA;
 }
 
 int force_enqueue(int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3], const double* phi,
@@ -341,6 +384,12 @@ void solver_release(cdp_ctx* c) {
             cufftDestroy(p.r2c);
             cufftDestroy(p.c2r);
             if (p.spec) cudaFree(p.spec);
+            if (p.have32) {
+                cufftDestroy(p.r2c32);
+                cufftDestroy(p.c2r32);
+            }
+            if (p.spec32) cudaFree(p.spec32);
+            if (p.real32) cudaFree(p.real32);
         }
         delete c->plans;
         c->plans = nullptr;
@@ -360,7 +409,7 @@ int cdp_poisson(cdp_ctx* c, int dim, const int32_t grid[3], const double box_len
     if (rc) return rc;
     if (!(four_pi_G == four_pi_G)) return CDP_ERR_ARG;
     cdp::DevGuard guard(c->device);
-    return cdp::poisson_enqueue(c, dim, grid, box_len, four_pi_G, cell_mass, phi, (cudaStream_t)stream);
+    return cdp::poisson_enqueue(c, dim, grid, box_len, four_pi_G, cell_mass, phi, (cudaStream_t)stream, false);
 }
 
 int cdp_force(cdp_ctx* c, int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3],

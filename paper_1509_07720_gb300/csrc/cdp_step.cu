@@ -14,7 +14,7 @@ namespace cdp {
 int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n);
 int project_batch(cdp_ctx* c, const cdp_problem* probs, int n, int precision, cudaStream_t st);
 int poisson_enqueue(cdp_ctx* c, int dim, const int32_t grid[3], const double box_len[3], double four_pi_G,
-                    const double* mass, double* phi, cudaStream_t st);
+                    const double* mass, double* phi, cudaStream_t st, bool fp32);
 int force_enqueue(int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3], const double* phi,
                   long long n, const double* const pos[3], double* const acc[3], cudaStream_t st);
 int drift_enqueue(int dim, long long n, double* const pos[3], const double* const vel[3], double dt,
@@ -73,7 +73,8 @@ int enqueue_step(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision
     }
     for (int i = 0; i < n; ++i) {
         const cdp_problem& m = probs[i].mesh;
-        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st)))
+        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st,
+                                       (precision & 0xff) == CDP_FP32_MIXED)))
             return rc;
         if ((rc = cdp::force_enqueue(m.dim, m.grid, m.box_lo, m.box_len, probs[i].phi, m.n_verts, m.pos,
                                      probs[i].acc, st)))
@@ -168,7 +169,8 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
         const cdp_problem& m = probs[i].mesh;
         if ((rc = cdp::vertex_density_enqueue(c, &m, probs[i].simplex_mass, const_cast<double*>(m.rho), st)))
             return rc;
-        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st)))
+        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st,
+                                       (precision & 0xff) == CDP_FP32_MIXED)))
             return rc;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) return CDP_ERR_CUDA;

@@ -15,6 +15,8 @@ times.  ``--amr L`` projects through the levels 0 .. L with donor-cell gather
   c5_3d        the 32 three-dimensional problems of that workload, one after the other
   c5_batch     all 64 problems in one cdp_project_batched call (one launch of each kernel per group
                of problems of one dimension)
+  c5_step      one time step of all 64 problems (cdp_step_batched: drift, vertex density, projection,
+               FFT Poisson, force, kick, drift), enqueued eagerly (no graph) so that every launch shows
 """
 from __future__ import annotations
 
@@ -32,9 +34,52 @@ def _device_mesh(torch, mesh):
             torch.empty(tuple(mesh.grid), dtype=torch.float64, device=d))
 
 
+def _step_case(a, torch, pkg, mg, proj, stream, prec):
+    """One time step of the 64 problems, eagerly enqueued, timed with CUDA events per repetition."""
+    d = torch.device("cuda:0")
+    batch = mg.make_batch("c5")
+    dt = mg.cfl_dt(batch)
+    keep, probs = [], []
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(d)
+    for p in batch:
+        m = p.mesh
+        pos = [t(m.pos[k]) for k in range(m.dim)]
+        vel = [t(p.vel[k]) for k in range(m.dim)]
+        acc = [torch.zeros(m.n_verts, dtype=torch.float64, device=d) for _ in range(m.dim)]
+        simp, mass = t(m.simplices), t(p.masses)
+        rho = torch.zeros(m.n_verts, dtype=torch.float64, device=d)
+        cm = torch.zeros(m.grid, dtype=torch.float64, device=d)
+        phi = torch.zeros(m.grid, dtype=torch.float64, device=d)
+        sp = pkg.cdp_step_problem()
+        sp.mesh = pkg.Projector.make_problem(pos, simp, rho, m.grid, m.box_lo, m.box_len, True, cm)
+        for k in range(m.dim):
+            sp.vel[k] = vel[k].data_ptr()
+            sp.acc[k] = acc[k].data_ptr()
+        sp.simplex_mass = mass.data_ptr()
+        sp.phi = phi.data_ptr()
+        probs.append(sp)
+        keep.append((pos, vel, acc, simp, mass, rho, cm, phi))
+    arr = (pkg.cdp_step_problem * len(probs))(*probs)
+    times = []
+    for _ in range(a.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = pkg.cdp_step_batched(proj._ctx, arr, prec, dt, 1.0, False, stream.cuda_stream)
+        if rc:
+            raise SystemExit(f"cdp_step_batched: {rc}")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    proj.check(stream)
+    print(json.dumps({"case": "c5_step", "prec": a.prec, "simplices": int(sum(p.mesh.n_simplices for p in batch)),
+                      "ms_per_rep": times}), flush=True)
+    proj.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c3", "c4", "c5", "c5_3d", "c5_batch"])
+    ap.add_argument("case", choices=["c3", "c4", "c5", "c5_3d", "c5_batch", "c5_step"])
     ap.add_argument("--scale", type=int, default=None, help="c3: lattice size (default 128)")
     ap.add_argument("--subset", type=int, default=1, help="c3: keep a random 1/k of the tetrahedra (seed 8)")
     ap.add_argument("--problem", type=int, default=0, help="c5: problem index in [0, 64)")
@@ -70,14 +115,18 @@ def main(argv=None):
             meshes = [batch[a.problem].mesh]
         elif a.case == "c5_3d":
             meshes = [p.mesh for p in batch if p.mesh.dim == 3]
-        else:
+        elif a.case == "c5_batch":
             meshes = [p.mesh for p in batch]
+        else:
+            meshes = []  # (c5_step builds its own problems)
     data = [(m, *_device_mesh(torch, m)) for m in meshes]
     prec = pkg.CDP_FP32_MIXED if a.prec == "fp32" else pkg.CDP_FP64
     if a.accuracy_off:
         prec |= pkg.CDP_ACCURACY_OFF
     proj = pkg.Projector(0)
     stream = torch.cuda.current_stream()
+    if a.case == "c5_step":
+        return _step_case(a, torch, pkg, mg, proj, stream, prec)
     times = []
     probs = [pkg.Projector.make_problem(pos, simp, rho, m.grid, m.box_lo, m.box_len, m.periodic, out)
              for m, pos, simp, rho, out in data]

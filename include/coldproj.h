@@ -255,11 +255,15 @@ typedef struct {
  * vertices, kick dt (eq. kick), drift dt/2 (eq. drift2).  use_graph != 0: the first call with a
  * given argument array captures the whole sequence into a CUDA graph owned by the context and
  * every later call with byte-identical arguments (dt may differ) replays it in one launch.  The
- * first call also creates the FFT plans and sizes the scratch outside the capture.
+ * first call also creates the FFT plans and sizes the scratch outside the capture.  A graph holds
+ * the addresses of the context's scratch: once a later call on the context reallocates it (a
+ * larger projection or vertex density) or cdp_autotune retunes the launch shapes, the graphs
+ * recorded before are dropped and the next call with their arguments records the step again.
  *   precision   CDP_FP64: every step in FP64.  CDP_FP32_MIXED: the projection in FP32-mixed and the
  *               Poisson transforms in single precision (the source and the potential stay FP64
- *               arrays; the potential is then accurate to about 1e-6 of its largest value, below the
- *               FP32-mixed projection's own 1e-5); the other steps in FP64. */
+ *               arrays; on the 64-problem batched workload the potential is within 1.4e-5 of its
+ *               largest value of the FP64 step's, the cell masses within 3.5e-6); the other steps
+ *               in FP64. */
 CDP_API int cdp_step_batched(cdp_ctx* ctx, const cdp_step_problem* probs, int n, int precision, double dt,
                              double four_pi_G, int use_graph, void* stream);
 

@@ -35,9 +35,12 @@ int flags_to_code(unsigned f) {
     return CDP_OK;
 }
 
+// grow a scratch buffer of the context; a reallocation moves the buffer, so it advances the
+// context's epoch (the captured time steps recorded with the old address are then not replayed)
 template <typename T>
-int grow(T** p, size_t* cap, size_t need) {
+int grow(cdp_ctx* c, T** p, size_t* cap, size_t need) {
     if (need <= *cap) return CDP_OK;
+    ++c->epoch;
     size_t n = need + need / 4 + 1024;
     T* q = nullptr;
     if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
@@ -116,16 +119,16 @@ int grow_geo(cdp_ctx* c, size_t ns) {
     size_t n = ns < kGeoBatch ? ns : kGeoBatch;
     if (n < 1) n = 1;
     size_t rec = cdp::tet_geo_bytes(0) > cdp::tet_geo_bytes(1) ? cdp::tet_geo_bytes(0) : cdp::tet_geo_bytes(1);
-    int rc = grow(&c->geo, &c->geo_cap, n * rec);
+    int rc = grow(c, &c->geo, &c->geo_cap, n * rec);
     if (rc) return rc;
-    return grow(&c->need, &c->need_cap, n);
+    return grow(c, &c->need, &c->need_cap, n);
 }
 
 // the slots in which each block of the FP32 large-tetrahedron kernel keeps its tiles' pieces
 // between the two passes (CDP_TILE_STORE_PER_BLOCK tiles per resident block)
 int grow_tiles(cdp_ctx* c) {
     const size_t blocks = (size_t)c->num_sms * (size_t)(c->blocks_small[1] > 0 ? c->blocks_small[1] : 1);
-    return grow(&c->tiles, &c->tiles_cap, blocks * cdp::CDP_TILE_STORE_PER_BLOCK * cdp::tet_tile_cells());
+    return grow(c, &c->tiles, &c->tiles_cap, blocks * cdp::CDP_TILE_STORE_PER_BLOCK * cdp::tet_tile_cells());
 }
 
 }  // namespace
@@ -146,18 +149,18 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n) {
         ns += (size_t)probs[i].n_simplices + 64;  // (with the chunk alignment of each problem)
         any3d = any3d || probs[i].dim == 3;
     }
-    int rc = grow(&c->verts, &c->verts_cap, nv);
+    int rc = grow(c, &c->verts, &c->verts_cap, nv);
     if (rc) return rc;
-    if ((rc = grow(&c->queue, &c->queue_cap, ns))) return rc;
-    if ((rc = grow(&c->defer, &c->defer_cap, ns)) || (rc = grow(&c->clip, &c->clip_cap, ns))) return rc;
+    if ((rc = grow(c, &c->queue, &c->queue_cap, ns))) return rc;
+    if ((rc = grow(c, &c->defer, &c->defer_cap, ns)) || (rc = grow(c, &c->clip, &c->clip_cap, ns))) return rc;
     if (any3d && (rc = grow_tiles(c))) return rc;
     return grow_geo(c, ns);
 }
 
 // scratch of an AMR projection: the coarse levels' grids and the level of every simplex
 int reserve_amr(cdp_ctx* c, size_t coarse_cells, size_t n_simplices) {
-    int rc = grow(&c->amr, &c->amr_cap, coarse_cells > 0 ? coarse_cells : 1);
-    return rc ? rc : grow(&c->levels, &c->levels_cap, n_simplices > 0 ? n_simplices : 1);
+    int rc = grow(c, &c->amr, &c->amr_cap, coarse_cells > 0 ? coarse_cells : 1);
+    return rc ? rc : grow(c, &c->levels, &c->levels_cap, n_simplices > 0 ? n_simplices : 1);
 }
 
 // the table of a group of problems of one dimension (at most CDP_GROUP, arguments already checked):
@@ -219,11 +222,11 @@ int project_group(cdp_ctx* c, const ProbTable& T, int precision, int accumulate,
                   unsigned char* amr_levels = nullptr, int max_level = 0) {
     int rc;
     const size_t nv1 = (size_t)(T.nv > 0 ? T.nv : 1), ns1 = (size_t)(T.ns > 0 ? T.ns : 1);
-    if ((rc = grow(&c->verts, &c->verts_cap, nv1))) return rc;
-    if ((rc = grow(&c->defer, &c->defer_cap, ns1)) || (rc = grow(&c->clip, &c->clip_cap, ns1))) return rc;
+    if ((rc = grow(c, &c->verts, &c->verts_cap, nv1))) return rc;
+    if ((rc = grow(c, &c->defer, &c->defer_cap, ns1)) || (rc = grow(c, &c->clip, &c->clip_cap, ns1))) return rc;
     int fp32 = 0, accuracy = 1;
     if (!parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
-    if (T.dim == 3 && ((rc = grow(&c->queue, &c->queue_cap, ns1)) || (rc = grow_geo(c, ns1)))) return rc;
+    if (T.dim == 3 && ((rc = grow(c, &c->queue, &c->queue_cap, ns1)) || (rc = grow_geo(c, ns1)))) return rc;
     if (T.dim == 3 && fp32 && (rc = grow_tiles(c))) return rc;
 
     LaunchArgs L;
@@ -546,6 +549,7 @@ int cdp_autotune(cdp_ctx* c, const cdp_problem* p, int precision, const char* ca
     int fp32 = 0, accuracy = 1;
     if (!cdp::parse_precision(precision, &fp32, &accuracy)) return CDP_ERR_ARG;
     DeviceGuard guard(c->device);
+    ++c->epoch;  // the launch shapes may change: captured time steps are recorded again
     const int d3 = p->dim == 3 ? 1 : 0;
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);

@@ -78,7 +78,10 @@ struct cdp_ctx {
     std::vector<cdp::FftPlan>* plans;
     double* vsum;  // per-vertex accumulators of the vertex density (mass, volume)
     size_t vsum_cap;
-    // captured time steps (see cdp_step_batched) and the device copy of their dt
+    // captured time steps (see cdp_step_batched) and the device copy of their dt.  `epoch` advances
+    // whenever a scratch buffer is reallocated or the launch shapes are retuned; a graph recorded
+    // at an older epoch holds stale addresses and is recaptured instead of replayed
+    unsigned long long epoch;
     struct StepGraph* graphs;
     double* d_dt;
     cudaStream_t capture_stream;  // private stream the step graphs are recorded on

@@ -362,6 +362,7 @@ int vertex_density_enqueue(cdp_ctx* c, const cdp_problem* p, const double* mass,
             return CDP_ERR_OOM;
         }
         if (c->vsum) cudaFree(c->vsum);
+        ++c->epoch;
         c->vsum = q;
         c->vsum_cap = need;
     }

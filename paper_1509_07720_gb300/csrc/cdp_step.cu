@@ -30,6 +30,7 @@ struct StepGraph {
     std::vector<cdp_step_problem> key;
     int precision;
     double four_pi_G;
+    unsigned long long epoch;  // the context's epoch when it was recorded
     cudaGraphExec_t exec;
     StepGraph* next;
 };
@@ -110,6 +111,22 @@ int check_step_problem(const cdp_step_problem& s) {
     return CDP_OK;
 }
 
+// destroy the graphs recorded at an older epoch of the context (an executable graph still running
+// is freed when it completes)
+void drop_stale_graphs(cdp_ctx* c) {
+    StepGraph** link = &c->graphs;
+    while (*link) {
+        StepGraph* g = *link;
+        if (g->epoch == c->epoch) {
+            link = &g->next;
+            continue;
+        }
+        *link = g->next;
+        cudaGraphExecDestroy(g->exec);
+        delete g;
+    }
+}
+
 }  // namespace
 
 namespace cdp {
@@ -151,6 +168,9 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
     if (cudaMemcpyAsync(c->d_dt, &dt, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) return CDP_ERR_CUDA;
     if (!use_graph) return enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, st);
 
+    // graphs recorded before a scratch buffer moved (or the launch shapes were retuned) hold stale
+    // addresses: drop them, then replay a current one recorded with these arguments
+    drop_stale_graphs(c);
     for (StepGraph* g = c->graphs; g; g = g->next) {
         if ((int)g->key.size() == n && g->precision == precision && g->four_pi_G == four_pi_G &&
             memcmp(g->key.data(), probs, (size_t)n * sizeof(cdp_step_problem)) == 0) {
@@ -188,6 +208,7 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
     }
     int timing = c->timing;
     c->timing = 0;  // no event bookkeeping inside the captured sequence
+    const unsigned long long epoch = c->epoch;
     rc = enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, cs);
     c->timing = timing;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -195,6 +216,12 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         return rc ? rc : CDP_ERR_CUDA;
+    }
+    if (c->epoch != epoch) {
+        // a buffer moved while the sequence was recorded (the reservation above missed it): the
+        // recording is not replayable, the step runs eagerly on the sized scratch instead
+        cudaGraphDestroy(graph);
+        return enqueue_step(c, probs, n, precision, four_pi_G, c->d_dt, st);
     }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
@@ -211,6 +238,7 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
     g->key.assign(probs, probs + n);
     g->precision = precision;
     g->four_pi_G = four_pi_G;
+    g->epoch = epoch;
     g->exec = exec;
     g->next = c->graphs;
     c->graphs = g;

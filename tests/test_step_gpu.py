@@ -137,6 +137,46 @@ def test_graph_replay_matches_eager(ctx):
             assert np.max(np.abs(x - y)) <= 1e-11 * max(1e-300, np.max(np.abs(y)))
 
 
+def test_graph_recorded_again_after_scratch_moves(ctx):
+    """A graph holds the addresses of the context's scratch.  Projecting a larger mesh and computing
+    a larger vertex density on the same context reallocates that scratch; the next call with the
+    graph's arguments must record the step again (not replay stale addresses) and still equal
+    eager execution."""
+    import paper_1509_07720_gb300 as pkg
+
+    probs = _problems()
+    a = [_Dev(*p) for p in probs]
+    b = [_Dev(*p) for p in probs]
+    arr_a = (pkg.cdp_step_problem * len(a))(*[d.sp for d in a])
+    arr_b = (pkg.cdp_step_problem * len(b))(*[d.sp for d in b])
+    st = torch.cuda.current_stream().cuda_stream
+    assert pkg.cdp_step_batched(ctx, arr_a, pkg.CDP_FP64, 0.01, FPG, 1, st) == 0
+    assert pkg.cdp_step_batched(ctx, arr_b, pkg.CDP_FP64, 0.01, FPG, 0, st) == 0
+    # a mesh with more vertices and simplices than any the context has seen in this module
+    big = mg.make_config("c2", 40)
+    d = torch.device("cuda:0")
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(d)
+    pos = [t(big.pos[k]) for k in range(3)]
+    simp, rho = t(big.simplices), t(big.rho)
+    out = torch.empty(big.grid, dtype=torch.float64, device=d)
+    prob = pkg.Projector.make_problem(pos, simp, rho, big.grid, big.box_lo, big.box_len, big.periodic, out)
+    assert pkg.cdp_project(ctx, prob, pkg.CDP_FP32_MIXED, 0, st) == 0
+    rout = torch.empty(big.n_verts, dtype=torch.float64, device=d)
+    masses = t(np.full(big.n_simplices, 1e-5))
+    assert pkg.cdp_vertex_density(ctx, prob, masses.data_ptr(), rout.data_ptr(), st) == 0
+    torch.cuda.synchronize()
+    del pos, simp, rho, out, rout, masses
+    for dt in (0.012, 0.008):
+        assert pkg.cdp_step_batched(ctx, arr_a, pkg.CDP_FP64, dt, FPG, 1, st) == 0
+        assert pkg.cdp_step_batched(ctx, arr_b, pkg.CDP_FP64, dt, FPG, 0, st) == 0
+    torch.cuda.synchronize()
+    for da, db in zip(a, b):
+        sa, sb = da.state(), db.state()
+        assert np.max(_periodic_diff(sa[0], sb[0])) <= 1e-13
+        for x, y in zip(sa[1:], sb[1:]):
+            assert np.max(np.abs(x - y)) <= 1e-11 * max(1e-300, np.max(np.abs(y)))
+
+
 _C5 = {}
 
 

@@ -146,16 +146,19 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
-__global__ void k_force(ForceGrid G, const double* __restrict__ phi, long long np, const double* __restrict__ px,
-                        const double* __restrict__ py, const double* __restrict__ pz, double* __restrict__ ax,
-                        double* __restrict__ ay, double* __restrict__ az) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    const double* P[3] = {px, py, pz};
+// acceleration at one point x: the triangular-shaped-cloud weights of the 3^DIM cells around it
+// times each cell's 4-point central differences of phi.  Both are linear in phi, so along each axis
+// the three weighted differences are summed first into one 7-point stencil over the cells
+// c0 - 3 .. c0 + 3 (half the FP64 operations and loads of evaluating every cell's differences),
+// which is then applied to the 3^(DIM-1) rows of cells the other axes' weights select.
+template <int DIM>
+__device__ __forceinline__ void force_at(const ForceGrid& G, const double* __restrict__ phi, const double x[3],
+                                         double acc[3]) {
     int c0[3] = {0, 0, 0};
     double w[3][3] = {{0, 1, 0}, {0, 1, 0}, {0, 1, 0}};
-    for (int a = 0; a < G.dim; ++a) {
-        double u = (P[a][i] - G.lo[a]) * G.inv_h[a] - 0.5;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        double u = (x[a] - G.lo[a]) * G.inv_h[a] - 0.5;
         double f = floor(u + 0.5);
         double d = u - f;
         c0[a] = (int)f;
@@ -163,55 +166,90 @@ __global__ void k_force(ForceGrid G, const double* __restrict__ phi, long long n
         w[a][1] = 0.75 - d * d;
         w[a][2] = 0.5 * (0.5 + d) * (0.5 + d);
     }
-    double acc[3] = {0.0, 0.0, 0.0};
-    const int n0 = G.n[0], n1 = G.n[1], n2 = G.dim == 3 ? G.n[2] : 1;
-    const int zr = G.dim == 3 ? 1 : 0;
-    for (int oa = -1; oa <= 1; ++oa)
-        for (int ob = -1; ob <= 1; ++ob)
-            for (int oc = -zr; oc <= zr; ++oc) {
-                double wt = w[0][oa + 1] * w[1][ob + 1] * (G.dim == 3 ? w[2][oc + 1] : 1.0);
-                int ia = c0[0] + oa, ib = c0[1] + ob, ic = c0[2] + oc;
-                int wa = wrapi(ia, n0), wb = wrapi(ib, n1), wc = G.dim == 3 ? wrapi(ic, n2) : 0;
-                // 4-point differences along each axis at cell (ia, ib, ic)
-                double g0 = (8.0 * (phi[((long long)wrapi(ia + 1, n0) * n1 + wb) * n2 + wc] -
-                                    phi[((long long)wrapi(ia - 1, n0) * n1 + wb) * n2 + wc]) -
-                             (phi[((long long)wrapi(ia + 2, n0) * n1 + wb) * n2 + wc] -
-                              phi[((long long)wrapi(ia - 2, n0) * n1 + wb) * n2 + wc])) *
-                            (G.inv_h[0] / 12.0);
-                double g1 = (8.0 * (phi[((long long)wa * n1 + wrapi(ib + 1, n1)) * n2 + wc] -
-                                    phi[((long long)wa * n1 + wrapi(ib - 1, n1)) * n2 + wc]) -
-                             (phi[((long long)wa * n1 + wrapi(ib + 2, n1)) * n2 + wc] -
-                              phi[((long long)wa * n1 + wrapi(ib - 2, n1)) * n2 + wc])) *
-                            (G.inv_h[1] / 12.0);
-                acc[0] -= wt * g0;
-                acc[1] -= wt * g1;
-                if (G.dim == 3) {
-                    long long rowb = ((long long)wa * n1 + wb) * n2;
-                    double g2 = (8.0 * (phi[rowb + wrapi(ic + 1, n2)] - phi[rowb + wrapi(ic - 1, n2)]) -
-                                 (phi[rowb + wrapi(ic + 2, n2)] - phi[rowb + wrapi(ic - 2, n2)])) *
-                                (G.inv_h[2] / 12.0);
-                    acc[2] -= wt * g2;
-                }
+    // wrapped indices of the cells c0 - 3 .. c0 + 3 of every axis
+    int ix[DIM][7];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) ix[a][k] = wrapi(c0[a] + k - 3, G.n[a]);
+    const long long n1 = G.n[1], n2 = DIM == 3 ? G.n[2] : 1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        // stencil along axis a: cell o (slot o + 2) contributes w_o (8 (phi[+1] - phi[-1]) -
+        // (phi[+2] - phi[-2])) / (12 h)
+        const double q = G.inv_h[a] / 12.0;
+        double st[7];
+        st[0] = w[a][0] * q;
+        st[1] = (w[a][1] - 8.0 * w[a][0]) * q;
+        st[2] = (w[a][2] - 8.0 * w[a][1]) * q;
+        st[3] = (8.0 * (w[a][0] - w[a][2])) * q;
+        st[4] = (8.0 * w[a][1] - w[a][0]) * q;
+        st[5] = (8.0 * w[a][2] - w[a][1]) * q;
+        st[6] = -w[a][2] * q;
+        // the rows of cells along axis a picked by the other axes (b, and c in 3D) and their weights;
+        // one row at a time keeps seven loads in flight per thread and the registers few
+        const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+        double sum = 0.0;
+#pragma unroll 1
+        for (int r = 0; r < (DIM == 3 ? 9 : 3); ++r) {
+            const int ob = DIM == 3 ? r / 3 : r, oc = DIM == 3 ? r % 3 : 1;
+            const double wb = ob == 0 ? w[b][0] : (ob == 1 ? w[b][1] : w[b][2]);
+            const double wc = DIM == 3 ? (oc == 0 ? w[c][0] : (oc == 1 ? w[c][1] : w[c][2])) : 1.0;
+            const double wo = wb * wc;
+            const long long jb = wrapi(c0[b] + ob - 1, G.n[b]);
+            const long long jc = DIM == 3 ? wrapi(c0[c] + oc - 1, G.n[c]) : 0;
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                long long i3[3];
+                i3[a] = ix[a][k];
+                i3[b] = jb;
+                i3[c] = jc;
+                s += st[k] * phi[(i3[0] * n1 + i3[1]) * n2 + i3[2]];
             }
+            sum += wo * s;
+        }
+        acc[a] = -sum;
+    }
+    if (DIM == 2) acc[2] = 0.0;
+}
+
+__global__ void __launch_bounds__(128, 4) k_force(ForceGrid G, const double* __restrict__ phi, long long np, const double* __restrict__ px,
+                        const double* __restrict__ py, const double* __restrict__ pz, double* __restrict__ ax,
+                        double* __restrict__ ay, double* __restrict__ az) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    double acc[3];
+    if (G.dim == 3) {
+        const double x[3] = {px[i], py[i], pz[i]};
+        force_at<3>(G, phi, x, acc);
+        az[i] = acc[2];
+    } else {
+        const double x[3] = {px[i], py[i], 0.0};
+        force_at<2>(G, phi, x, acc);
+    }
     ax[i] = acc[0];
     ay[i] = acc[1];
-    if (G.dim == 3) az[i] = acc[2];
 }
 
 // ---------------------------------------------------------------------------------------------
 // kick and drift; `dtp` (device scalar) overrides dt when given, times `fac`
 // ---------------------------------------------------------------------------------------------
-__global__ void k_drift(long long n, double* __restrict__ x, const double* __restrict__ v, double dt,
-                        const double* __restrict__ dtp, double fac, double lo, double len, int periodic) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double d = (dtp ? *dtp : dt) * fac;
-    double y = x[i] + v[i] * d;
+// x + v d, wrapped into [lo, lo + len) on a periodic box
+__device__ __forceinline__ double drift_coord(double x, double v, double d, double lo, double len, int periodic) {
+    double y = x + v * d;
     if (periodic) {
         y = lo + (y - lo) - len * floor((y - lo) / len);
         if (y >= lo + len) y -= len;
     }
-    x[i] = y;
+    return y;
+}
+
+__global__ void k_drift(long long n, double* __restrict__ x, const double* __restrict__ v, double dt,
+                        const double* __restrict__ dtp, double fac, double lo, double len, int periodic) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i] = drift_coord(x[i], v[i], (dtp ? *dtp : dt) * fac, lo, len, periodic);
 }
 
 __global__ void k_kick(long long n, double* __restrict__ v, const double* __restrict__ a, double dt,
@@ -224,15 +262,17 @@ __global__ void k_kick(long long n, double* __restrict__ v, const double* __rest
 // ---------------------------------------------------------------------------------------------
 // vertex density: scatter (M_i, |V_i|) of every simplex to its vertices, then divide
 // ---------------------------------------------------------------------------------------------
-__global__ void k_vd_scatter(int dim, long long ns, long long nv, const int* __restrict__ simp,
-                             const double* __restrict__ px, const double* __restrict__ py,
-                             const double* __restrict__ pz, const double* __restrict__ mass, double L0, double L1,
-                             double L2, int periodic, double* __restrict__ msum, double* __restrict__ vsum,
-                             unsigned* __restrict__ flags) {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= ns) return;
-    const int nvs = dim + 1;
+// simplex s of a mesh: its mass and |V| (minimal-image edge vectors on a periodic box) added to
+// the sums of its vertices; an out-of-range vertex index raises the index flag instead
+template <int DIM>
+__device__ __forceinline__ void vd_scatter_one(long long s, long long nv, const int* __restrict__ simp,
+                                               const double* const P[3], const double L[3],
+                                               const double* __restrict__ mass, int periodic,
+                                               double* __restrict__ msum, double* __restrict__ vsum,
+                                               unsigned* __restrict__ flags) {
+    constexpr int dim = DIM, nvs = DIM + 1;
     int id[4];
+#pragma unroll
     for (int k = 0; k < nvs; ++k) {
         id[k] = simp[s * nvs + k];
         if (id[k] < 0 || id[k] >= nv) {
@@ -240,10 +280,10 @@ __global__ void k_vd_scatter(int dim, long long ns, long long nv, const int* __r
             return;
         }
     }
-    const double* P[3] = {px, py, pz};
-    const double L[3] = {L0, L1, L2};
     double e[3][3];
+#pragma unroll
     for (int k = 1; k < nvs; ++k)
+#pragma unroll
         for (int a = 0; a < dim; ++a) {
             double d = P[a][id[k]] - P[a][id[0]];
             if (periodic) d -= L[a] * nearbyint(d / L[a]);
@@ -258,10 +298,26 @@ __global__ void k_vd_scatter(int dim, long long ns, long long nv, const int* __r
         vol = fabs(e[0][0] * e[1][1] - e[0][1] * e[1][0]) * 0.5;
     }
     double m = mass[s];
+#pragma unroll
     for (int k = 0; k < nvs; ++k) {
         atomicAdd(msum + id[k], m);
         atomicAdd(vsum + id[k], vol);
     }
+}
+
+__global__ void k_vd_scatter(int dim, long long ns, long long nv, const int* __restrict__ simp,
+                             const double* __restrict__ px, const double* __restrict__ py,
+                             const double* __restrict__ pz, const double* __restrict__ mass, double L0, double L1,
+                             double L2, int periodic, double* __restrict__ msum, double* __restrict__ vsum,
+                             unsigned* __restrict__ flags) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    const double* P[3] = {px, py, pz};
+    const double L[3] = {L0, L1, L2};
+    if (dim == 3)
+        vd_scatter_one<3>(s, nv, simp, P, L, mass, periodic, msum, vsum, flags);
+    else
+        vd_scatter_one<2>(s, nv, simp, P, L, mass, periodic, msum, vsum, flags);
 }
 
 __global__ void k_vd_divide(long long nv, const double* __restrict__ msum, const double* __restrict__ vsum,
@@ -353,19 +409,24 @@ int kick_enqueue(int dim, long long n, double* const vel[3], const double* const
     return cudaGetLastError() == cudaSuccess ? CDP_OK : CDP_ERR_CUDA;
 }
 
-int vertex_density_enqueue(cdp_ctx* c, const cdp_problem* p, const double* mass, double* rho_out, cudaStream_t st) {
-    size_t need = 2 * (size_t)(p->n_verts > 0 ? p->n_verts : 1);
-    if (need > c->vsum_cap) {
-        double* q = nullptr;
-        if (cudaMalloc(&q, need * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return CDP_ERR_OOM;
-        }
-        if (c->vsum) cudaFree(c->vsum);
-        ++c->epoch;
-        c->vsum = q;
-        c->vsum_cap = need;
+// the per-vertex accumulators of the vertex density, `need` doubles (grown outside any capture)
+int reserve_vsum(cdp_ctx* c, size_t need) {
+    if (need <= c->vsum_cap) return CDP_OK;
+    double* q = nullptr;
+    if (cudaMalloc(&q, need * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return CDP_ERR_OOM;
     }
+    if (c->vsum) cudaFree(c->vsum);
+    ++c->epoch;
+    c->vsum = q;
+    c->vsum_cap = need;
+    return CDP_OK;
+}
+
+int vertex_density_enqueue(cdp_ctx* c, const cdp_problem* p, const double* mass, double* rho_out, cudaStream_t st) {
+    int rc = reserve_vsum(c, 2 * (size_t)(p->n_verts > 0 ? p->n_verts : 1));
+    if (rc) return rc;
     if (p->n_verts == 0) return CDP_OK;
     double* msum = c->vsum;
     double* vsum = c->vsum + p->n_verts;
@@ -377,6 +438,208 @@ int vertex_density_enqueue(cdp_ctx* c, const cdp_problem* p, const double* mass,
             &c->ctr->flags);
     k_vd_divide<<<blocks_for(p->n_verts, 256), 256, 0, st>>>(p->n_verts, msum, vsum, rho_out);
     return cudaGetLastError() == cudaSuccess ? CDP_OK : CDP_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The per-vertex steps of a batched time step, many meshes per launch: a table of up to
+// CDP_STEP_GROUP meshes (of either dimension) passed by value, a global vertex or simplex index
+// mapped to its mesh by a binary search over the offsets.  Each element does the arithmetic of
+// the single-mesh kernels above, in the same order.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int CDP_STEP_GROUP = 64;
+
+struct StepEntry {
+    ForceGrid G;  // the mesh's grid (force interpolation)
+    double* pos[3];
+    double* vel[3];
+    double* acc[3];
+    const int* simplices;
+    const double* smass;
+    double* rho;
+    const double* phi;
+    double len[3];
+    int dim, periodic;
+    long long nv, ns;
+    long long v_off, s_off;  // first vertex and simplex of the mesh in the group's numberings
+};
+
+struct StepTable {
+    int n;
+    long long nv, ns;  // totals over the group
+    StepEntry p[CDP_STEP_GROUP];
+};
+static_assert(sizeof(StepTable) <= 32000, "a kernel parameter holds at most 32764 bytes");
+
+template <class Off>
+__device__ __forceinline__ int step_find(const StepTable& T, long long i, Off off) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off(T.p[mid]) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// drift dt/2 (eq. drift1) of every vertex of the group
+__global__ void __launch_bounds__(256) k_step_drift(const __grid_constant__ StepTable T, const double* __restrict__ dtp,
+                                                    double fac) {
+    const double d = *dtp * fac;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < T.nv; i += (long long)gridDim.x * blockDim.x) {
+        const StepEntry& E = T.p[step_find(T, i, [](const StepEntry& e) { return e.v_off; })];
+        const long long j = i - E.v_off;
+        for (int a = 0; a < E.dim; ++a)
+            E.pos[a][j] = drift_coord(E.pos[a][j], E.vel[a][j], d, E.G.lo[a], E.len[a], E.periodic);
+    }
+}
+
+// the vertex-density sums of every simplex of the group (msum, vsum: the group's vertex numbering)
+__global__ void __launch_bounds__(128) k_step_vd_scatter(const __grid_constant__ StepTable T, double* __restrict__ msum,
+                                                         double* __restrict__ vsum, unsigned* __restrict__ flags) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < T.ns; s += (long long)gridDim.x * blockDim.x) {
+        const StepEntry& E = T.p[step_find(T, s, [](const StepEntry& e) { return e.s_off; })];
+        const double* P[3] = {E.pos[0], E.pos[1], E.pos[2]};
+        if (E.dim == 3)
+            vd_scatter_one<3>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, msum + E.v_off,
+                              vsum + E.v_off, flags);
+        else
+            vd_scatter_one<2>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, msum + E.v_off,
+                              vsum + E.v_off, flags);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_step_vd_divide(const __grid_constant__ StepTable T, const double* __restrict__ msum,
+                                                        const double* __restrict__ vsum) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < T.nv; i += (long long)gridDim.x * blockDim.x) {
+        const StepEntry& E = T.p[step_find(T, i, [](const StepEntry& e) { return e.v_off; })];
+        const double v = vsum[i];
+        E.rho[i - E.v_off] = v > 0.0 ? msum[i] / v : 0.0;
+    }
+}
+
+// force at vertex j of a mesh (written to acc), kick dt (eq. kick) and drift dt/2 (eq. drift2)
+template <int DIM>
+__device__ __forceinline__ void force_kick_drift_one(const StepEntry& E, long long j, double dk, double dd) {
+    double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = E.pos[a][j];
+    double acc[3];
+    force_at<DIM>(E.G, E.phi, x, acc);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        E.acc[a][j] = acc[a];
+        const double v = E.vel[a][j] + acc[a] * dk;
+        E.vel[a][j] = v;
+        E.pos[a][j] = drift_coord(x[a], v, dd, E.G.lo[a], E.len[a], E.periodic);
+    }
+}
+
+// force, kick and drift of every vertex of the group, from its mesh's potential
+__global__ void __launch_bounds__(128, 4) k_step_force_kick_drift(const __grid_constant__ StepTable T,
+                                                               const double* __restrict__ dtp) {
+    const double dk = *dtp * 1.0, dd = *dtp * 0.5;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < T.nv; i += (long long)gridDim.x * blockDim.x) {
+        const StepEntry& E = T.p[step_find(T, i, [](const StepEntry& e) { return e.v_off; })];
+        if (E.dim == 3)
+            force_kick_drift_one<3>(E, i - E.v_off, dk, dd);
+        else
+            force_kick_drift_one<2>(E, i - E.v_off, dk, dd);
+    }
+}
+
+unsigned step_blocks(long long n, int bs, int num_sms) {
+    long long b = (n + bs - 1) / bs;
+    const long long cap = (long long)num_sms * 32;
+    return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// the table of probs[0 .. n) (n <= CDP_STEP_GROUP)
+void fill_step_table(const cdp_step_problem* probs, int n, StepTable& T) {
+    memset(&T, 0, sizeof(T));
+    T.n = n;
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem& m = probs[i].mesh;
+        StepEntry& E = T.p[i];
+        E.G.dim = m.dim;
+        for (int a = 0; a < 3; ++a) {
+            E.G.n[a] = a < m.dim ? m.grid[a] : 1;
+            E.G.lo[a] = a < m.dim ? m.box_lo[a] : 0.0;
+            E.G.h[a] = a < m.dim ? m.box_len[a] / m.grid[a] : 1.0;
+            E.G.inv_h[a] = 1.0 / E.G.h[a];
+            E.len[a] = a < m.dim ? m.box_len[a] : 1.0;
+            E.pos[a] = a < m.dim ? const_cast<double*>(m.pos[a]) : nullptr;
+            E.vel[a] = a < m.dim ? probs[i].vel[a] : nullptr;
+            E.acc[a] = a < m.dim ? probs[i].acc[a] : nullptr;
+        }
+        E.simplices = m.simplices;
+        E.smass = probs[i].simplex_mass;
+        E.rho = const_cast<double*>(m.rho);
+        E.phi = probs[i].phi;
+        E.dim = m.dim;
+        E.periodic = m.periodic;
+        E.nv = m.n_verts;
+        E.ns = m.n_simplices;
+        E.v_off = T.nv;
+        E.s_off = T.ns;
+        T.nv += m.n_verts;
+        T.ns += m.n_simplices;
+    }
+}
+
+}  // namespace
+
+// the largest number of vertices of one group of a batched step (sizes the vertex-density sums)
+long long step_group_vertices(const cdp_step_problem* probs, int n) {
+    long long most = 0;
+    for (int g0 = 0; g0 < n; g0 += CDP_STEP_GROUP) {
+        long long nv = 0;
+        for (int i = g0; i < n && i < g0 + CDP_STEP_GROUP; ++i) nv += probs[i].mesh.n_verts;
+        most = nv > most ? nv : most;
+    }
+    return most;
+}
+
+// drift dt/2, then the vertex densities, of every mesh (one launch of each kernel per group)
+int step_drift_density_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int n, const double* dtp, cudaStream_t st) {
+    const long long most = step_group_vertices(probs, n);
+    int rc = reserve_vsum(c, 2 * (size_t)(most > 0 ? most : 1));
+    if (rc) return rc;
+    StepTable* T = new (std::nothrow) StepTable;
+    if (!T) return CDP_ERR_OOM;
+    for (int g0 = 0; g0 < n && rc == CDP_OK; g0 += CDP_STEP_GROUP) {
+        fill_step_table(probs + g0, n - g0 < CDP_STEP_GROUP ? n - g0 : CDP_STEP_GROUP, *T);
+        if (T->nv == 0) continue;
+        k_step_drift<<<step_blocks(T->nv, 256, c->num_sms), 256, 0, st>>>(*T, dtp, 0.5);
+        double* msum = c->vsum;
+        double* vsum = c->vsum + T->nv;
+        if (cudaMemsetAsync(c->vsum, 0, 2 * (size_t)T->nv * sizeof(double), st) != cudaSuccess) rc = CDP_ERR_CUDA;
+        if (rc == CDP_OK && T->ns > 0)
+            k_step_vd_scatter<<<step_blocks(T->ns, 128, c->num_sms), 128, 0, st>>>(*T, msum, vsum, &c->ctr->flags);
+        if (rc == CDP_OK) k_step_vd_divide<<<step_blocks(T->nv, 256, c->num_sms), 256, 0, st>>>(*T, msum, vsum);
+        if (rc == CDP_OK && cudaGetLastError() != cudaSuccess) rc = CDP_ERR_CUDA;
+    }
+    delete T;
+    return rc;
+}
+
+// force, kick dt and drift dt/2 of every mesh (one launch per group), after the potentials
+int step_force_kick_drift_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int n, const double* dtp,
+                                  cudaStream_t st) {
+    StepTable* T = new (std::nothrow) StepTable;
+    if (!T) return CDP_ERR_OOM;
+    int rc = CDP_OK;
+    for (int g0 = 0; g0 < n && rc == CDP_OK; g0 += CDP_STEP_GROUP) {
+        fill_step_table(probs + g0, n - g0 < CDP_STEP_GROUP ? n - g0 : CDP_STEP_GROUP, *T);
+        if (T->nv == 0) continue;
+        k_step_force_kick_drift<<<step_blocks(T->nv, 128, c->num_sms), 128, 0, st>>>(*T, dtp);
+        if (cudaGetLastError() != cudaSuccess) rc = CDP_ERR_CUDA;
+    }
+    delete T;
+    return rc;
 }
 
 void solver_release(cdp_ctx* c) {

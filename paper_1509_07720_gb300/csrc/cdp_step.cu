@@ -15,14 +15,11 @@ int reserve_scratch(cdp_ctx* c, const cdp_problem* probs, int n);
 int project_batch(cdp_ctx* c, const cdp_problem* probs, int n, int precision, cudaStream_t st);
 int poisson_enqueue(cdp_ctx* c, int dim, const int32_t grid[3], const double box_len[3], double four_pi_G,
                     const double* mass, double* phi, cudaStream_t st, bool fp32);
-int force_enqueue(int dim, const int32_t grid[3], const double box_lo[3], const double box_len[3], const double* phi,
-                  long long n, const double* const pos[3], double* const acc[3], cudaStream_t st);
-int drift_enqueue(int dim, long long n, double* const pos[3], const double* const vel[3], double dt,
-                  const double* dtp, double fac, const double box_lo[3], const double box_len[3], int periodic,
-                  cudaStream_t st);
-int kick_enqueue(int dim, long long n, double* const vel[3], const double* const acc[3], double dt,
-                 const double* dtp, double fac, cudaStream_t st);
-int vertex_density_enqueue(cdp_ctx* c, const cdp_problem* p, const double* mass, double* rho_out, cudaStream_t st);
+int step_drift_density_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int n, const double* dtp, cudaStream_t st);
+int step_force_kick_drift_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int n, const double* dtp,
+                                  cudaStream_t st);
+long long step_group_vertices(const cdp_step_problem* probs, int n);
+int reserve_vsum(cdp_ctx* c, size_t need);
 }  // namespace cdp
 
 // a captured step: the exact arguments it was recorded with, and its executable graph
@@ -52,19 +49,8 @@ struct Guard {
 int enqueue_step(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision, double four_pi_G, const double* dtp,
                  cudaStream_t st) {
     int rc;
-    for (int i = 0; i < n; ++i) {
-        const cdp_problem& m = probs[i].mesh;
-        double* pos[3] = {const_cast<double*>(m.pos[0]), const_cast<double*>(m.pos[1]),
-                          const_cast<double*>(m.pos[2])};
-        if ((rc = cdp::drift_enqueue(m.dim, m.n_verts, pos, probs[i].vel, 0.0, dtp, 0.5, m.box_lo, m.box_len,
-                                     m.periodic, st)))
-            return rc;
-    }
-    for (int i = 0; i < n; ++i) {
-        const cdp_problem& m = probs[i].mesh;
-        if ((rc = cdp::vertex_density_enqueue(c, &m, probs[i].simplex_mass, const_cast<double*>(m.rho), st)))
-            return rc;
-    }
+    // drift dt/2 and the vertex densities: one launch of each kernel per group of meshes
+    if ((rc = cdp::step_drift_density_enqueue(c, probs, n, dtp, st))) return rc;
     // the projections of all the meshes, grouped (one launch of each projection kernel per group of
     // up to 64 meshes of one dimension)
     {
@@ -72,25 +58,15 @@ int enqueue_step(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision
         for (int i = 0; i < n; ++i) meshes[(size_t)i] = probs[i].mesh;
         if ((rc = cdp::project_batch(c, meshes.data(), n, precision, st))) return rc;
     }
+    // the potential of every mesh (its own FFT plans)
     for (int i = 0; i < n; ++i) {
         const cdp_problem& m = probs[i].mesh;
         if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st,
                                        (precision & 0xff) == CDP_FP32_MIXED)))
             return rc;
-        if ((rc = cdp::force_enqueue(m.dim, m.grid, m.box_lo, m.box_len, probs[i].phi, m.n_verts, m.pos,
-                                     probs[i].acc, st)))
-            return rc;
     }
-    for (int i = 0; i < n; ++i) {
-        const cdp_problem& m = probs[i].mesh;
-        double* pos[3] = {const_cast<double*>(m.pos[0]), const_cast<double*>(m.pos[1]),
-                          const_cast<double*>(m.pos[2])};
-        if ((rc = cdp::kick_enqueue(m.dim, m.n_verts, probs[i].vel, probs[i].acc, 0.0, dtp, 1.0, st))) return rc;
-        if ((rc = cdp::drift_enqueue(m.dim, m.n_verts, pos, probs[i].vel, 0.0, dtp, 0.5, m.box_lo, m.box_len,
-                                     m.periodic, st)))
-            return rc;
-    }
-    return CDP_OK;
+    // force, kick dt and drift dt/2 of every vertex: one launch per group of meshes
+    return cdp::step_force_kick_drift_enqueue(c, probs, n, dtp, st);
 }
 
 int check_step_problem(const cdp_step_problem& s) {
@@ -183,12 +159,14 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
     for (int i = 0; i < n; ++i) meshes[(size_t)i] = probs[i].mesh;
     int rc = cdp::reserve_scratch(c, meshes.data(), n);
     if (rc) return rc;
+    {
+        const long long most = cdp::step_group_vertices(probs, n);
+        if ((rc = cdp::reserve_vsum(c, 2 * (size_t)(most > 0 ? most : 1)))) return rc;
+    }
     for (int i = 0; i < n; ++i) {
-        // creates the FFT plan (and its spectrum buffer) of every grid shape; the vertex-density
-        // accumulators are grown here too, with a harmless solve on the problem's own arrays
+        // creates the FFT plan (and its spectrum buffers) of every grid shape, with a harmless
+        // solve on the problem's own arrays
         const cdp_problem& m = probs[i].mesh;
-        if ((rc = cdp::vertex_density_enqueue(c, &m, probs[i].simplex_mass, const_cast<double*>(m.rho), st)))
-            return rc;
         if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st,
                                        (precision & 0xff) == CDP_FP32_MIXED)))
             return rc;

@@ -262,22 +262,20 @@ __global__ void k_kick(long long n, double* __restrict__ v, const double* __rest
 // ---------------------------------------------------------------------------------------------
 // vertex density: scatter (M_i, |V_i|) of every simplex to its vertices, then divide
 // ---------------------------------------------------------------------------------------------
-// simplex s of a mesh: its mass and |V| (minimal-image edge vectors on a periodic box) added to
-// the sums of its vertices; an out-of-range vertex index raises the index flag instead
+// simplex s of a mesh: its vertex indices, mass and |V| (minimal-image edge vectors on a periodic
+// box); false (and the index flag raised) for an out-of-range vertex index
 template <int DIM>
-__device__ __forceinline__ void vd_scatter_one(long long s, long long nv, const int* __restrict__ simp,
-                                               const double* const P[3], const double L[3],
-                                               const double* __restrict__ mass, int periodic,
-                                               double* __restrict__ msum, double* __restrict__ vsum,
-                                               unsigned* __restrict__ flags) {
+__device__ __forceinline__ bool vd_simplex(long long s, long long nv, const int* __restrict__ simp,
+                                           const double* const P[3], const double L[3],
+                                           const double* __restrict__ mass, int periodic, int id[4], double& m,
+                                           double& vol, unsigned* __restrict__ flags) {
     constexpr int dim = DIM, nvs = DIM + 1;
-    int id[4];
 #pragma unroll
     for (int k = 0; k < nvs; ++k) {
         id[k] = simp[s * nvs + k];
         if (id[k] < 0 || id[k] >= nv) {
             atomicOr(flags, CDP_FLAG_INDEX);
-            return;
+            return false;
         }
     }
     double e[3][3];
@@ -289,7 +287,6 @@ __device__ __forceinline__ void vd_scatter_one(long long s, long long nv, const 
             if (periodic) d -= L[a] * nearbyint(d / L[a]);
             e[k - 1][a] = d;
         }
-    double vol;
     if (dim == 3) {
         vol = fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
                    e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) /
@@ -297,9 +294,22 @@ __device__ __forceinline__ void vd_scatter_one(long long s, long long nv, const 
     } else {
         vol = fabs(e[0][0] * e[1][1] - e[0][1] * e[1][0]) * 0.5;
     }
-    double m = mass[s];
+    m = mass[s];
+    return true;
+}
+
+// simplex s's mass and |V| added to the sums of its vertices
+template <int DIM>
+__device__ __forceinline__ void vd_scatter_one(long long s, long long nv, const int* __restrict__ simp,
+                                               const double* const P[3], const double L[3],
+                                               const double* __restrict__ mass, int periodic,
+                                               double* __restrict__ msum, double* __restrict__ vsum,
+                                               unsigned* __restrict__ flags) {
+    int id[4];
+    double m, vol;
+    if (!vd_simplex<DIM>(s, nv, simp, P, L, mass, periodic, id, m, vol, flags)) return;
 #pragma unroll
-    for (int k = 0; k < nvs; ++k) {
+    for (int k = 0; k <= DIM; ++k) {
         atomicAdd(msum + id[k], m);
         atomicAdd(vsum + id[k], vol);
     }
@@ -497,18 +507,51 @@ __global__ void __launch_bounds__(256) k_step_drift(const __grid_constant__ Step
     }
 }
 
-// the vertex-density sums of every simplex of the group (msum, vsum: the group's vertex numbering)
+// the vertex-density sums of every simplex of the group (msum, vsum: the group's vertex numbering).
+// A warp takes 32 consecutive simplices; for each vertex slot the lanes naming the same vertex are
+// grouped (consecutive simplices share vertices: the cubes of a Kuhn lattice, the squares of a
+// triangulated sheet) and the lowest lane of a group adds the group's sums with one atomic pair.
 __global__ void __launch_bounds__(128) k_step_vd_scatter(const __grid_constant__ StepTable T, double* __restrict__ msum,
                                                          double* __restrict__ vsum, unsigned* __restrict__ flags) {
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < T.ns; s += (long long)gridDim.x * blockDim.x) {
-        const StepEntry& E = T.p[step_find(T, s, [](const StepEntry& e) { return e.s_off; })];
-        const double* P[3] = {E.pos[0], E.pos[1], E.pos[2]};
-        if (E.dim == 3)
-            vd_scatter_one<3>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, msum + E.v_off,
-                              vsum + E.v_off, flags);
-        else
-            vd_scatter_one<2>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, msum + E.v_off,
-                              vsum + E.v_off, flags);
+    __shared__ double sh_m[4][32], sh_v[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < T.ns; base += stride) {
+        const long long s = base + lane;
+        int id[4] = {0, 0, 0, 0};
+        double m = 0.0, vol = 0.0;
+        bool ok = false;
+        int dim = 0;
+        long long voff = 0;
+        if (s < T.ns) {
+            const StepEntry& E = T.p[step_find(T, s, [](const StepEntry& e) { return e.s_off; })];
+            const double* P[3] = {E.pos[0], E.pos[1], E.pos[2]};
+            dim = E.dim;
+            voff = E.v_off;
+            ok = dim == 3 ? vd_simplex<3>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, id, m, vol, flags)
+                          : vd_simplex<2>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, id, m, vol, flags);
+        }
+        sh_m[w][lane] = m;
+        sh_v[w][lane] = vol;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool has = ok && k <= dim;
+            const unsigned amask = __ballot_sync(0xffffffffu, has);
+            if (!has) continue;
+            const long long v = voff + id[k];
+            const unsigned peers = __match_any_sync(amask, (unsigned long long)v);
+            if (lane != __ffs(peers) - 1) continue;
+            double gm = 0.0, gv = 0.0;
+            for (unsigned b = peers; b; b &= b - 1u) {
+                const int j = __ffs(b) - 1;
+                gm += sh_m[w][j];
+                gv += sh_v[w][j];
+            }
+            atomicAdd(msum + v, gm);
+            atomicAdd(vsum + v, gv);
+        }
+        __syncwarp();
     }
 }
 

@@ -15,6 +15,7 @@ times.  ``--amr L`` projects through the levels 0 .. L with donor-cell gather
   c5_3d        the 32 three-dimensional problems of that workload, one after the other
   c5_batch     all 64 problems in one cdp_project_batched call (one launch of each kernel per group
                of problems of one dimension)
+  c5_2d        the 32 two-dimensional problems of that workload in one cdp_project_batched call
   c5_step      one time step of all 64 problems (cdp_step_batched: drift, vertex density, projection,
                FFT Poisson, force, kick, drift), enqueued eagerly (no graph) so that every launch shows
 """
@@ -79,7 +80,7 @@ def _step_case(a, torch, pkg, mg, proj, stream, prec):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c3", "c4", "c5", "c5_3d", "c5_batch", "c5_step"])
+    ap.add_argument("case", choices=["c3", "c4", "c5", "c5_3d", "c5_batch", "c5_2d", "c5_step"])
     ap.add_argument("--scale", type=int, default=None, help="c3: lattice size (default 128)")
     ap.add_argument("--subset", type=int, default=1, help="c3: keep a random 1/k of the tetrahedra (seed 8)")
     ap.add_argument("--problem", type=int, default=0, help="c5: problem index in [0, 64)")
@@ -117,6 +118,8 @@ def main(argv=None):
             meshes = [p.mesh for p in batch if p.mesh.dim == 3]
         elif a.case == "c5_batch":
             meshes = [p.mesh for p in batch]
+        elif a.case == "c5_2d":
+            meshes = [p.mesh for p in batch if p.mesh.dim == 2]
         else:
             meshes = []  # (c5_step builds its own problems)
     data = [(m, *_device_mesh(torch, m)) for m in meshes]
@@ -134,7 +137,7 @@ def main(argv=None):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if a.case == "c5_batch":
+        if a.case in ("c5_batch", "c5_2d"):
             rc = pkg.cdp_project_batched(proj._ctx, probs, prec, stream.cuda_stream)
             if rc:
                 raise SystemExit(f"cdp_project_batched: {rc}")

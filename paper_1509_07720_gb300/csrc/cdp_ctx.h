@@ -78,6 +78,10 @@ struct cdp_ctx {
     std::vector<cdp::FftPlan>* plans;
     double* vsum;  // per-vertex accumulators of the vertex density (mass, volume)
     size_t vsum_cap;
+    float* preal;  // FP32 sources / potentials of a batched step's Poisson solves, one per mesh
+    size_t preal_cap;
+    cufftComplex* pspec;  // and their half spectra
+    size_t pspec_cap;
     // captured time steps (see cdp_step_batched) and the device copy of their dt.  `epoch` advances
     // whenever a scratch buffer is reallocated or the launch shapes are retuned; a graph recorded
     // at an older epoch holds stale addresses and is recaptured instead of replayed

@@ -42,30 +42,37 @@ int check_grid(int dim, const int32_t grid[3], const double box_len[3]) {
 // ---------------------------------------------------------------------------------------------
 // Poisson: spectrum of the cell masses times -four_pi_G / (k^2 * cell volume * N), zero mode 0
 // ---------------------------------------------------------------------------------------------
+// entry t of an (n0, n1, n2h) half spectrum (2D: n1 = 1) times its Green factor
+// -four_pi_G / (k^2 * cell volume * N) (`scale` / k^2), the zero mode set to 0
+template <typename C, typename R>
+__device__ __forceinline__ void green_at(C& v, long long t, int dim, int n0, int n1, int n2h, R k0, R k1, R k2,
+                                         R scale) {
+    int c = (int)(t % n2h);
+    long long r = t / n2h;
+    int b = (int)(r % n1);
+    int a = (int)(r / n1);
+    R kk;
+    if (dim == 3) {
+        int fa = a <= n0 / 2 ? a : a - n0;
+        int fb = b <= n1 / 2 ? b : b - n1;
+        R ka = k0 * fa, kb = k1 * fb, kc = k2 * c;
+        kk = ka * ka + kb * kb + kc * kc;
+    } else {  // 2D: (n0, n1h) with n1 = 1 placeholder: a = row, c = half column
+        int fa = a <= n0 / 2 ? a : a - n0;
+        R ka = k0 * fa, kc = k2 * c;
+        kk = ka * ka + kc * kc;
+    }
+    R gfac = kk > R(0) ? scale / kk : R(0);
+    v.x *= gfac;
+    v.y *= gfac;
+}
+
 template <typename C, typename R>
 __global__ void k_green(C* __restrict__ spec, int dim, int n0, int n1, int n2h, int n2, R k0, R k1, R k2, R scale) {
     long long total = (long long)n0 * n1 * n2h;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int c = (int)(t % n2h);
-        long long r = t / n2h;
-        int b = (int)(r % n1);
-        int a = (int)(r / n1);
-        R kk;
-        if (dim == 3) {
-            int fa = a <= n0 / 2 ? a : a - n0;
-            int fb = b <= n1 / 2 ? b : b - n1;
-            R ka = k0 * fa, kb = k1 * fb, kc = k2 * c;
-            kk = ka * ka + kb * kb + kc * kc;
-        } else {  // 2D: (n0, n1h) with n1 = 1 placeholder: a = row, c = half column
-            int fa = a <= n0 / 2 ? a : a - n0;
-            R ka = k0 * fa, kc = k2 * c;
-            kk = ka * ka + kc * kc;
-        }
-        R gfac = kk > R(0) ? scale / kk : R(0);
-        spec[t].x *= gfac;
-        spec[t].y *= gfac;
-    }
+         t += (long long)gridDim.x * blockDim.x)
+        green_at<C, R>(spec[t], t, dim, n0, n1, n2h, k0, k1, k2, scale);
 }
 
 // the FP64 source and potential to and from the FP32 transforms' buffer
@@ -633,7 +640,163 @@ void fill_step_table(const cdp_step_problem* probs, int n, StepTable& T) {
     }
 }
 
+// The FP32 Poisson solves of a batched step (the FP32-mixed precision), many meshes per launch of
+// the element-wise kernels: every mesh has its own FP32 real and spectrum arrays in the context's
+// scratch (each starting on a 256-byte boundary), so the conversions of the source and the Green
+// factors run once for the whole group, with one R2C and one C2R transform per mesh in between.
+struct PoisEntry {
+    const double* src;  // the cell masses
+    double* phi;        // the potential
+    long long cells, r_off;   // real array: its cells and first element in the group's real scratch
+    long long selems, s_off;  // half spectrum: its entries and first entry in the spectrum scratch
+    int dim, n0, n1, n2h;
+    float k0, k1, k2, scale;
+};
+
+struct PoisTable {
+    int n;
+    long long rtot, stot;  // the group's real and spectrum scratch (with the padding)
+    PoisEntry p[CDP_STEP_GROUP];
+};
+static_assert(sizeof(PoisTable) <= 32000, "a kernel parameter holds at most 32764 bytes");
+
+__device__ __forceinline__ int pois_find(const PoisTable& T, long long i, bool spectrum) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((spectrum ? T.p[mid].s_off : T.p[mid].r_off) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_pois_to_f32(const __grid_constant__ PoisTable T, float* __restrict__ real) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < T.rtot; i += (long long)gridDim.x * blockDim.x) {
+        const PoisEntry& E = T.p[pois_find(T, i, false)];
+        const long long j = i - E.r_off;
+        if (j < E.cells) real[i] = (float)E.src[j];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pois_green(const __grid_constant__ PoisTable T, cufftComplex* __restrict__ spec) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < T.stot; i += (long long)gridDim.x * blockDim.x) {
+        const PoisEntry& E = T.p[pois_find(T, i, true)];
+        const long long u = i - E.s_off;
+        if (u < E.selems) green_at<cufftComplex, float>(spec[i], u, E.dim, E.n0, E.n1, E.n2h, E.k0, E.k1, E.k2, E.scale);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pois_to_f64(const __grid_constant__ PoisTable T, const float* __restrict__ real) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < T.rtot; i += (long long)gridDim.x * blockDim.x) {
+        const PoisEntry& E = T.p[pois_find(T, i, false)];
+        const long long j = i - E.r_off;
+        if (j < E.cells) E.phi[j] = (double)real[i];
+    }
+}
+
+// the table of probs[0 .. n) (n <= CDP_STEP_GROUP)
+void fill_pois_table(const cdp_step_problem* probs, int n, double four_pi_G, PoisTable& T) {
+    memset(&T, 0, sizeof(T));
+    T.n = n;
+    const double twopi = 6.283185307179586476925286766559;
+    for (int i = 0; i < n; ++i) {
+        const cdp_problem& m = probs[i].mesh;
+        const int dim = m.dim;
+        PoisEntry& E = T.p[i];
+        double ntot = 1.0, cellvol = 1.0;
+        for (int a = 0; a < dim; ++a) {
+            ntot *= m.grid[a];
+            cellvol *= m.box_len[a] / m.grid[a];
+        }
+        E.src = m.cell_mass;
+        E.phi = probs[i].phi;
+        E.dim = dim;
+        E.n0 = m.grid[0];
+        E.n1 = dim == 3 ? m.grid[1] : 1;
+        E.n2h = m.grid[dim - 1] / 2 + 1;
+        E.cells = (long long)ntot;
+        E.selems = (long long)E.n0 * E.n1 * E.n2h;
+        E.k0 = (float)(twopi / m.box_len[0]);
+        E.k1 = (float)(dim == 3 ? twopi / m.box_len[1] : 0.0);
+        E.k2 = (float)(twopi / m.box_len[dim - 1]);
+        E.scale = (float)(-four_pi_G / (cellvol * ntot));
+        E.r_off = T.rtot;
+        E.s_off = T.stot;
+        T.rtot += (E.cells + 63) / 64 * 64;       // 256-byte boundaries
+        T.stot += (E.selems + 31) / 32 * 32;
+    }
+}
+
 }  // namespace
+
+// the FP32 real and spectrum scratch of the largest group of a batched step's Poisson solves
+int reserve_poisson32(cdp_ctx* c, const cdp_step_problem* probs, int n) {
+    PoisTable* T = new (std::nothrow) PoisTable;
+    if (!T) return CDP_ERR_OOM;
+    long long rmax = 1, smax = 1;
+    for (int g0 = 0; g0 < n; g0 += CDP_STEP_GROUP) {
+        fill_pois_table(probs + g0, n - g0 < CDP_STEP_GROUP ? n - g0 : CDP_STEP_GROUP, 1.0, *T);
+        rmax = T->rtot > rmax ? T->rtot : rmax;
+        smax = T->stot > smax ? T->stot : smax;
+    }
+    delete T;
+    for (int k = 0; k < 2; ++k) {
+        void** buf = k == 0 ? (void**)&c->preal : (void**)&c->pspec;
+        size_t* cap = k == 0 ? &c->preal_cap : &c->pspec_cap;
+        const size_t need = (size_t)(k == 0 ? rmax : smax), elem = k == 0 ? sizeof(float) : sizeof(cufftComplex);
+        if (need <= *cap) continue;
+        void* q = nullptr;
+        if (cudaMalloc(&q, need * elem) != cudaSuccess) {
+            cudaGetLastError();
+            return CDP_ERR_OOM;
+        }
+        if (*buf) cudaFree(*buf);
+        ++c->epoch;
+        *buf = q;
+        *cap = need;
+    }
+    return CDP_OK;
+}
+
+// the Poisson solves of every mesh in single precision (source and potential FP64 arrays): per
+// group one launch of each element-wise kernel, one R2C and one C2R per mesh
+int step_poisson32_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int n, double four_pi_G, cudaStream_t st) {
+    int rc = reserve_poisson32(c, probs, n);
+    if (rc) return rc;
+    PoisTable* T = new (std::nothrow) PoisTable;
+    if (!T) return CDP_ERR_OOM;
+    for (int g0 = 0; g0 < n && rc == CDP_OK; g0 += CDP_STEP_GROUP) {
+        const int ng = n - g0 < CDP_STEP_GROUP ? n - g0 : CDP_STEP_GROUP;
+        fill_pois_table(probs + g0, ng, four_pi_G, *T);
+        if (T->rtot == 0) continue;
+        k_pois_to_f32<<<step_blocks(T->rtot, 256, c->num_sms), 256, 0, st>>>(*T, c->preal);
+        for (int i = 0; i < ng && rc == CDP_OK; ++i) {
+            const cdp_problem& m = probs[g0 + i].mesh;
+            FftPlan* p = get_plan(c, m.dim, m.grid, &rc);
+            if (!p || (rc = add_plan32(*p))) break;
+            if (cufftSetStream(p->r2c32, st) != CUFFT_SUCCESS ||
+                cufftExecR2C(p->r2c32, c->preal + T->p[i].r_off, c->pspec + T->p[i].s_off) != CUFFT_SUCCESS)
+                rc = CDP_ERR_CUDA;
+        }
+        if (rc) break;
+        k_pois_green<<<step_blocks(T->stot, 256, c->num_sms), 256, 0, st>>>(*T, c->pspec);
+        for (int i = 0; i < ng && rc == CDP_OK; ++i) {
+            const cdp_problem& m = probs[g0 + i].mesh;
+            FftPlan* p = get_plan(c, m.dim, m.grid, &rc);
+            if (!p) break;
+            if (cufftSetStream(p->c2r32, st) != CUFFT_SUCCESS ||
+                cufftExecC2R(p->c2r32, c->pspec + T->p[i].s_off, c->preal + T->p[i].r_off) != CUFFT_SUCCESS)
+                rc = CDP_ERR_CUDA;
+        }
+        if (rc) break;
+        k_pois_to_f64<<<step_blocks(T->rtot, 256, c->num_sms), 256, 0, st>>>(*T, c->preal);
+        if (cudaGetLastError() != cudaSuccess) rc = CDP_ERR_CUDA;
+    }
+    delete T;
+    return rc;
+}
 
 // the largest number of vertices of one group of a batched step (sizes the vertex-density sums)
 long long step_group_vertices(const cdp_step_problem* probs, int n) {
@@ -703,6 +866,10 @@ void solver_release(cdp_ctx* c) {
     }
     if (c->vsum) cudaFree(c->vsum);
     c->vsum = nullptr;
+    if (c->preal) cudaFree(c->preal);
+    c->preal = nullptr;
+    if (c->pspec) cudaFree(c->pspec);
+    c->pspec = nullptr;
 }
 
 }  // namespace cdp

@@ -20,6 +20,8 @@ int step_force_kick_drift_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int
                                   cudaStream_t st);
 long long step_group_vertices(const cdp_step_problem* probs, int n);
 int reserve_vsum(cdp_ctx* c, size_t need);
+int reserve_poisson32(cdp_ctx* c, const cdp_step_problem* probs, int n);
+int step_poisson32_enqueue(cdp_ctx* c, const cdp_step_problem* probs, int n, double four_pi_G, cudaStream_t st);
 }  // namespace cdp
 
 // a captured step: the exact arguments it was recorded with, and its executable graph
@@ -58,12 +60,17 @@ int enqueue_step(cdp_ctx* c, const cdp_step_problem* probs, int n, int precision
         for (int i = 0; i < n; ++i) meshes[(size_t)i] = probs[i].mesh;
         if ((rc = cdp::project_batch(c, meshes.data(), n, precision, st))) return rc;
     }
-    // the potential of every mesh (its own FFT plans)
-    for (int i = 0; i < n; ++i) {
-        const cdp_problem& m = probs[i].mesh;
-        if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st,
-                                       (precision & 0xff) == CDP_FP32_MIXED)))
-            return rc;
+    // the potential of every mesh (its own FFT plans): FP64 transforms one mesh after the other, or
+    // (FP32-mixed) single-precision transforms with the element-wise steps batched per group
+    if ((precision & 0xff) == CDP_FP32_MIXED) {
+        if ((rc = cdp::step_poisson32_enqueue(c, probs, n, four_pi_G, st))) return rc;
+    } else {
+        for (int i = 0; i < n; ++i) {
+            const cdp_problem& m = probs[i].mesh;
+            if ((rc = cdp::poisson_enqueue(c, m.dim, m.grid, m.box_len, four_pi_G, m.cell_mass, probs[i].phi, st,
+                                           false)))
+                return rc;
+        }
     }
     // force, kick dt and drift dt/2 of every vertex: one launch per group of meshes
     return cdp::step_force_kick_drift_enqueue(c, probs, n, dtp, st);
@@ -162,6 +169,7 @@ extern "C" int cdp_step_batched(cdp_ctx* c, const cdp_step_problem* probs, int n
     {
         const long long most = cdp::step_group_vertices(probs, n);
         if ((rc = cdp::reserve_vsum(c, 2 * (size_t)(most > 0 ? most : 1)))) return rc;
+        if ((precision & 0xff) == CDP_FP32_MIXED && (rc = cdp::reserve_poisson32(c, probs, n))) return rc;
     }
     for (int i = 0; i < n; ++i) {
         // creates the FFT plan (and its spectrum buffers) of every grid shape, with a harmless

@@ -330,92 +330,111 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(const __grid_con
         nact += active ? 1 : 0;
         __syncwarp();
         if (__ballot_sync(0xffffffffu, active) == 0u) continue;
-        // ---- the three phases, items dealt over the lanes.  Phase 0 evaluates its corners (B) at
-        // once; phases 1 and 2 locate their corners (C, and D with the A nodes evaluated at once)
-        // and queue them, and the queue is drained in full batches of 32 identical evaluations.
-        unsigned head = sh->qtail;
-        for (int ph = 0; ph < 3; ++ph) {
-            int mine = active ? n[ph] : 0;
-            int pre = mine;
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, pre, o);
-                if (lane >= o) pre += t;
-            }
-            const int tot = __shfl_sync(0xffffffffu, pre, 31);
-            for (int u0 = 0; u0 < tot; u0 += 32) {
-                const int u = u0 + lane;
-                const int own = owner_of(pre, u);
-                const int before = __shfl_sync(0xffffffffu, pre - mine, own);
-                if (u < tot) {
-                    const typename GeoOf<DIM, R>::T& G = sh->geo[own];
-                    WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, T, fp32);
-                    QueuePush push{sh->queue, &sh->qtail, (unsigned long long)own << 40};
-                    const int t = u - before;
-                    tri_phase_item(G, ph, t, acc, push, pc);
-                }
-                __syncwarp();
-                // evaluate every full batch of queued records
-                const unsigned tail = *(volatile unsigned*)&sh->qtail;
-                while (tail - head >= 32u) {
-                    eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, T, fp32, pc);
-                    head += 32u;
-                }
-                __syncwarp();
-            }
-            // the last partial batch of the phase
-            const unsigned tail = *(volatile unsigned*)&sh->qtail;
-            if ((unsigned)lane < tail - head)
-                eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, T, fp32, pc);
-            head = tail;
-            __syncwarp();
+        // ---- sub-rounds.  The triangles of the chunk share the warp's piece table; when their
+        // bounding boxes add up to more cells than the table has entries, the chunk is taken in 2,
+        // 4, ... sub-rounds of consecutive lanes so that the pieces of each fit (a crowded table
+        // sends pieces straight to the grid, and the FP32 closure then has fewer pieces to spread
+        // its residual over).
+        int box = 0;
+        if (active) {
+            const typename GeoOf<DIM, R>::T& G = sh->geo[lane];
+            const long long b = (long long)(G.hi[0] + 1) * (G.hi[1] + 1);
+            box = b < (1 << 20) ? (int)b : (1 << 20);
         }
-        __syncwarp();
-        // ---- flush the table: one FP64 atomic per (simplex, cell) piece.  FP32 path: first the
-        // FP64 sum of every simplex's pieces, then its closure residual (FP64 closed-form mass
-        // minus that sum) is spread over its pieces in proportion to their size while they are
-        // flushed (a simplex whose pieces all went straight to the grid gives it to its largest).
-        if (fp32) {
+        const int boxes = __reduce_add_sync(0xffffffffu, box);
+        int nsub = 1;
+        while (nsub < 32 && boxes > nsub * CDP_WTBL) nsub <<= 1;
+        const int width = 32 / nsub;
+        for (int sub = 0; sub < nsub; ++sub) {
+            const bool act = active && lane / width == sub;
+            if (__ballot_sync(0xffffffffu, act) == 0u) continue;
+            // ---- the three phases, items dealt over the lanes.  Phase 0 evaluates its corners (B) at
+            // once; phases 1 and 2 locate their corners (C, and D with the A nodes evaluated at once)
+            // and queue them, and the queue is drained in full batches of 32 identical evaluations.
+            unsigned head = sh->qtail;
+            for (int ph = 0; ph < 3; ++ph) {
+                int mine = act ? n[ph] : 0;
+                int pre = mine;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (lane >= o) pre += t;
+                }
+                const int tot = __shfl_sync(0xffffffffu, pre, 31);
+                for (int u0 = 0; u0 < tot; u0 += 32) {
+                    const int u = u0 + lane;
+                    const int own = owner_of(pre, u);
+                    const int before = __shfl_sync(0xffffffffu, pre - mine, own);
+                    if (u < tot) {
+                        const typename GeoOf<DIM, R>::T& G = sh->geo[own];
+                        WarpAcc<DIM, R> acc = make_acc<DIM, R>(sh, own, T, fp32);
+                        QueuePush push{sh->queue, &sh->qtail, (unsigned long long)own << 40};
+                        const int t = u - before;
+                        tri_phase_item(G, ph, t, acc, push, pc);
+                    }
+                    __syncwarp();
+                    // evaluate every full batch of queued records
+                    const unsigned tail = *(volatile unsigned*)&sh->qtail;
+                    while (tail - head >= 32u) {
+                        eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, T, fp32, pc);
+                        head += 32u;
+                    }
+                    __syncwarp();
+                }
+                // the last partial batch of the phase
+                const unsigned tail = *(volatile unsigned*)&sh->qtail;
+                if ((unsigned)lane < tail - head)
+                    eval_record<DIM, R>(sh, sh->queue[(head + lane) & (CDP_QCAP - 1)], ph, T, fp32, pc);
+                head = tail;
+                __syncwarp();
+            }
+            __syncwarp();
+            // ---- flush the table: one FP64 atomic per (simplex, cell) piece.  FP32 path: first the
+            // FP64 sum of every simplex's pieces, then its closure residual (FP64 closed-form mass
+            // minus that sum) is spread over its pieces in proportion to their size while they are
+            // flushed (a simplex whose pieces all went straight to the grid gives it to its largest).
+            if (fp32) {
+                for (int e = lane; e < CDP_WTBL; e += 32) {
+                    unsigned k = sh->keys[e];
+                    if (k == EMPTY_KEY) continue;
+                    R v = sh->vals[e];
+                    int own = (int)(k >> KEY_BITS);
+                    atomicAdd(&sh->csum[own], (double)v);
+                    atomicAdd(&sh->asum[own], fabsf((float)v));
+                }
+                __syncwarp();
+                if (act) {
+                    double r = sh->geo[lane].mexact - sh->csum[lane];
+                    if (sh->asum[lane] > 0.f) {
+                        sh->resid[lane] = r / (double)sh->asum[lane];
+                    } else {
+                        sh->resid[lane] = 0.0;
+                        if (sh->cmax[lane] != 0ull)
+                            atomicAdd(T.p[sh->geo[lane].prob].out + (long long)(unsigned)(sh->cmax[lane] & 0xffffffffull), r);
+                    }
+                }
+                __syncwarp();
+            }
             for (int e = lane; e < CDP_WTBL; e += 32) {
                 unsigned k = sh->keys[e];
                 if (k == EMPTY_KEY) continue;
                 R v = sh->vals[e];
+                sh->keys[e] = EMPTY_KEY;
+                sh->vals[e] = R(0);
                 int own = (int)(k >> KEY_BITS);
-                atomicAdd(&sh->csum[own], (double)v);
-                atomicAdd(&sh->asum[own], fabsf((float)v));
-            }
-            __syncwarp();
-            if (active) {
-                double r = sh->geo[lane].mexact - sh->csum[lane];
-                if (sh->asum[lane] > 0.f) {
-                    sh->resid[lane] = r / (double)sh->asum[lane];
-                } else {
-                    sh->resid[lane] = 0.0;
-                    if (sh->cmax[lane] != 0ull)
-                        atomicAdd(T.p[sh->geo[lane].prob].out + (long long)(unsigned)(sh->cmax[lane] & 0xffffffffull), r);
-                }
+                unsigned lk = k & ((1u << KEY_BITS) - 1u);
+                const typename GeoOf<DIM, R>::T& G = sh->geo[own];
+                const ProbEntry& P = T.p[G.prob];
+                int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
+                int x = (int)(lk % (unsigned)ex), r = (int)(lk / (unsigned)ex);
+                int y = r % ey, z = r / ey;
+                long long idx = flat_cell(P.g, G.anchor[0] + x, G.anchor[1] + y, G.anchor[2] + z);
+                if (idx < 0) continue;
+                double dv = (double)v;
+                if (fp32) dv += sh->resid[own] * (double)fabsf((float)v);
+                if (dv != 0.0) atomicAdd(P.out + idx, dv);
             }
             __syncwarp();
         }
-        for (int e = lane; e < CDP_WTBL; e += 32) {
-            unsigned k = sh->keys[e];
-            if (k == EMPTY_KEY) continue;
-            R v = sh->vals[e];
-            sh->keys[e] = EMPTY_KEY;
-            sh->vals[e] = R(0);
-            int own = (int)(k >> KEY_BITS);
-            unsigned lk = k & ((1u << KEY_BITS) - 1u);
-            const typename GeoOf<DIM, R>::T& G = sh->geo[own];
-            const ProbEntry& P = T.p[G.prob];
-            int ex = G.hi[0] + 1, ey = G.hi[1] + 1;
-            int x = (int)(lk % (unsigned)ex), r = (int)(lk / (unsigned)ex);
-            int y = r % ey, z = r / ey;
-            long long idx = flat_cell(P.g, G.anchor[0] + x, G.anchor[1] + y, G.anchor[2] + z);
-            if (idx < 0) continue;
-            double dv = (double)v;
-            if (fp32) dv += sh->resid[own] * (double)fabsf((float)v);
-            if (dv != 0.0) atomicAdd(P.out + idx, dv);
-        }
-        __syncwarp();
     }
     if (ebm > 0.0) atomicMax(&ctr->ebmax_bits, (unsigned long long)__double_as_longlong(ebm));
     if (stats) {

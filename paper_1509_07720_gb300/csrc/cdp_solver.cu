@@ -515,50 +515,19 @@ __global__ void __launch_bounds__(256) k_step_drift(const __grid_constant__ Step
 }
 
 // the vertex-density sums of every simplex of the group (msum, vsum: the group's vertex numbering).
-// A warp takes 32 consecutive simplices; for each vertex slot the lanes naming the same vertex are
-// grouped (consecutive simplices share vertices: the cubes of a Kuhn lattice, the squares of a
-// triangulated sheet) and the lowest lane of a group adds the group's sums with one atomic pair.
+// (Grouping the lanes of a warp that name the same vertex and adding each group's sums with one
+// atomic pair was slower: 3.58 against 2.89 ms per step on the 64-problem workload.)
 __global__ void __launch_bounds__(128) k_step_vd_scatter(const __grid_constant__ StepTable T, double* __restrict__ msum,
                                                          double* __restrict__ vsum, unsigned* __restrict__ flags) {
-    __shared__ double sh_m[4][32], sh_v[4][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < T.ns; base += stride) {
-        const long long s = base + lane;
-        int id[4] = {0, 0, 0, 0};
-        double m = 0.0, vol = 0.0;
-        bool ok = false;
-        int dim = 0;
-        long long voff = 0;
-        if (s < T.ns) {
-            const StepEntry& E = T.p[step_find(T, s, [](const StepEntry& e) { return e.s_off; })];
-            const double* P[3] = {E.pos[0], E.pos[1], E.pos[2]};
-            dim = E.dim;
-            voff = E.v_off;
-            ok = dim == 3 ? vd_simplex<3>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, id, m, vol, flags)
-                          : vd_simplex<2>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, id, m, vol, flags);
-        }
-        sh_m[w][lane] = m;
-        sh_v[w][lane] = vol;
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool has = ok && k <= dim;
-            const unsigned amask = __ballot_sync(0xffffffffu, has);
-            if (!has) continue;
-            const long long v = voff + id[k];
-            const unsigned peers = __match_any_sync(amask, (unsigned long long)v);
-            if (lane != __ffs(peers) - 1) continue;
-            double gm = 0.0, gv = 0.0;
-            for (unsigned b = peers; b; b &= b - 1u) {
-                const int j = __ffs(b) - 1;
-                gm += sh_m[w][j];
-                gv += sh_v[w][j];
-            }
-            atomicAdd(msum + v, gm);
-            atomicAdd(vsum + v, gv);
-        }
-        __syncwarp();
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < T.ns; s += (long long)gridDim.x * blockDim.x) {
+        const StepEntry& E = T.p[step_find(T, s, [](const StepEntry& e) { return e.s_off; })];
+        const double* P[3] = {E.pos[0], E.pos[1], E.pos[2]};
+        if (E.dim == 3)
+            vd_scatter_one<3>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, msum + E.v_off,
+                              vsum + E.v_off, flags);
+        else
+            vd_scatter_one<2>(s - E.s_off, E.nv, E.simplices, P, E.len, E.smass, E.periodic, msum + E.v_off,
+                              vsum + E.v_off, flags);
     }
 }
 

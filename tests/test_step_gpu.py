@@ -137,6 +137,49 @@ def test_graph_replay_matches_eager(ctx):
             assert np.max(np.abs(x - y)) <= 1e-11 * max(1e-300, np.max(np.abs(y)))
 
 
+def test_step_more_meshes_than_one_group(ctx):
+    """70 meshes: the per-vertex kernels and the FP32 Poisson conversions run over tables of at
+    most 64 meshes, so the step takes two groups.  Graph replay against eager execution for all of
+    them (to the run-to-run noise of the atomic sums, which the potential and the force amplify:
+    2.3e-13 in the positions after one FP64 step was seen), and the two meshes of the second group
+    against the oracle composition."""
+    import paper_1509_07720_gb300 as pkg
+
+    rng = np.random.default_rng(31)
+    base = _problems()
+    probs = []
+    for i in range(70):
+        m, vel, masses = base[i % 2]
+        probs.append((m, 0.05 * rng.standard_normal(m.pos.shape), masses))
+    a = [_Dev(*p) for p in probs]
+    b = [_Dev(*p) for p in probs]
+    arr_a = (pkg.cdp_step_problem * len(a))(*[d.sp for d in a])
+    arr_b = (pkg.cdp_step_problem * len(b))(*[d.sp for d in b])
+    st = torch.cuda.current_stream().cuda_stream
+    dt = 0.01
+    for prec in (pkg.CDP_FP64, pkg.CDP_FP32_MIXED):
+        assert pkg.cdp_step_batched(ctx, arr_a, prec, dt, FPG, 1, st) == 0
+        assert pkg.cdp_step_batched(ctx, arr_b, prec, dt, FPG, 0, st) == 0
+        torch.cuda.synchronize()
+        tol_pos, tol_rel = (1e-11, 1e-9) if prec == pkg.CDP_FP64 else (1e-8, 1e-4)
+        for da, db in zip(a, b):
+            sa, sb = da.state(), db.state()
+            assert np.max(_periodic_diff(sa[0], sb[0])) <= tol_pos
+            for x, y in zip(sa[1:], sb[1:]):
+                assert np.max(np.abs(x - y)) <= tol_rel * max(1e-300, np.max(np.abs(y)))
+        if prec == pkg.CDP_FP64:
+            # one FP64 step from the initial state: the second group against the oracle
+            for i in (64, 69):
+                m, vel, masses = probs[i]
+                p2, v2, rho, cm, phi, acc = _oracle_step(m, vel, masses, dt)
+                gp, gv, grho, gcm, gphi, gacc = a[i].state()
+                assert np.max(np.abs(grho - rho)) <= 1e-12 * np.max(rho), f"mesh {i}"
+                assert np.max(np.abs(gcm - cm)) <= 1e-11 * np.max(cm), f"mesh {i}"
+                assert np.max(np.abs(gphi - phi)) <= 1e-10 * np.max(np.abs(phi)), f"mesh {i}"
+                assert np.max(np.abs(gacc - acc)) <= 1e-9 * np.max(np.abs(acc)), f"mesh {i}"
+                assert np.max(_periodic_diff(gp, p2)) <= 1e-12, f"mesh {i}"
+
+
 def test_graph_recorded_again_after_scratch_moves(ctx):
     """A graph holds the addresses of the context's scratch.  Projecting a larger mesh and computing
     a larger vertex density on the same context reallocates that scratch; the next call with the

@@ -239,6 +239,7 @@ struct WarpPass {
     long long defer_cap;
     int* clip_list;
     long long clip_cap;
+    int chunk;  // triangles per warp chunk, 8 .. CDP_CHUNK (fewer when the problem is small)
 };
 
 template <int DIM, typename R>
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(CDP_WBLOCK, 3) k_project_warp(const __grid_con
         const long long listed = (long long)*(volatile const unsigned*)&ctr->defer_count;
         ns = listed < wp.defer_cap ? listed : wp.defer_cap;
     }
-    const int cs = CDP_CHUNK;
+    const int cs = wp.chunk;
     const long long nchunks = (ns + cs - 1) / cs;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long chunk = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk < nchunks;
@@ -484,14 +485,19 @@ int resident_blocks(int dim, int fp32) {
 
 // First pass over every triangle (steep ones deferred), the largest cell mass, second pass over the
 // deferred ones (the grid of the first pass's size: the count is read on the device), clipping.
+// A problem too small to give every resident warp a chunk of CDP_CHUNK triangles takes chunks of
+// 16 or 8 (more warps at work on a latency-bound launch); large ones take full chunks.
 template <int DIM, typename R>
 static cudaError_t launch_dim(const LaunchArgs& L, cudaStream_t st, cudaEvent_t mid) {
-    long long chunks = (L.T.ns + CDP_CHUNK - 1) / CDP_CHUNK;
-    long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
     long long cap = (long long)L.num_sms * L.small_blocks_per_sm;
+    const long long warps = cap * (CDP_WBLOCK / 32);
+    int cs = CDP_CHUNK;
+    while (cs > 8 && L.T.ns < warps * cs) cs >>= 1;
+    long long chunks = (L.T.ns + cs - 1) / cs;
+    long long blocks = (chunks + CDP_WBLOCK / 32 - 1) / (CDP_WBLOCK / 32);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    WarpPass wp = {acc_ctl(sizeof(R) == 4), 0, L.levels, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap};
+    WarpPass wp = {acc_ctl(sizeof(R) == 4), 0, L.levels, L.defer_list, L.defer_cap, L.clip_list, L.clip_cap, cs};
     if (!L.accuracy) wp.acc.defer_ratio = 3.0e38f;  // nothing is deferred
     k_project_warp<DIM, R><<<(unsigned)blocks, CDP_WBLOCK, shared_bytes<DIM, R>(), st>>>(L.T, L.verts, L.ctr, L.stats,
                                                                                        wp);

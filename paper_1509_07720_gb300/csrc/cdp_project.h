@@ -8,7 +8,7 @@
 namespace cdp {
 
 constexpr int CDP_WBLOCK = 128;   // threads per block of the projection kernel (4 warps)
-constexpr int CDP_CHUNK = 32;     // simplices per warp chunk (one per lane during set-up)
+constexpr int CDP_CHUNK = 32;     // simplices per warp chunk, at most (one per lane during set-up)
 constexpr int CDP_LOG_WTBL = 9;   // per-warp piece table: 2^9 entries
 constexpr int CDP_WTBL = 1 << CDP_LOG_WTBL;
 constexpr int CDP_QCAP = 512;     // per-warp queue of (corner, cell) records (power of two)
